@@ -1,0 +1,353 @@
+"""Pins of the CPU oracle against things other than itself.
+
+* Philox4x32-10 against cuRAND's host-side generator (an independent library
+  implementation of the same published generator), for the exact counters the
+  walks use.
+* The samplers against the inverse-CDF property of the weights of Sec. 2.5
+  (exact rationals / 80-digit decimals), against the hand-worked example, and
+  by chi-square on their output frequencies.
+* The index state against a hand-worked fixture and against brute force from
+  the window-set and view definitions (Sec. 2.3, 2.6) on random tiny streams.
+* Whole walks against exact enumeration of walk probabilities on tiny graphs
+  (chi-square), and against the causality invariants.
+"""
+import ctypes
+import ctypes.util
+import glob
+import json
+import math
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import brute
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox
+def _find_curand():
+    cands = []
+    for d in ("/usr/local/cuda/lib64", "/usr/local/cuda/targets/sbsa-linux/lib",
+              "/usr/local/cuda/targets/x86_64-linux/lib"):
+        cands += sorted(glob.glob(os.path.join(d, "libcurand.so*")))
+    try:
+        import nvidia  # noqa: F401
+        for p in nvidia.__path__:
+            cands += sorted(glob.glob(os.path.join(p, "**", "libcurand.so*"), recursive=True))
+    except Exception:
+        pass
+    f = ctypes.util.find_library("curand")
+    if f:
+        cands.append(f)
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    return None
+
+
+def _curand_host_block(L, seed, block):
+    """Block `block` of cuRAND's host Philox4x32-10 stream for `seed`."""
+    gen = ctypes.c_void_p()
+    assert L.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # PHILOX4_32_10
+    try:
+        assert L.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_uint64(seed)) == 0
+        assert L.curandSetGeneratorOffset(gen, ctypes.c_uint64(4 * block)) == 0
+        out = (ctypes.c_uint32 * 4)()
+        assert L.curandGenerate(gen, out, ctypes.c_size_t(4)) == 0
+        return [int(x) for x in out]
+    finally:
+        L.curandDestroyGenerator(gen)
+
+
+def test_philox_matches_curand_host_generator():
+    L = _find_curand()
+    if L is None:
+        pytest.skip("libcurand not found")
+    # cuRAND's host stream visits counter (B >> 16, 0, B & 0xffff, 0) at block
+    # B; the walks use counter (hop, 0, walk, 0) -> block hop * 65536 + walk.
+    rng = random.Random(7)
+    cases = [(0, 0, 0), (0, 1, 0), (0x123456789abcdef, 0, 0), (2**64 - 1, 79, 65535)]
+    cases += [(rng.getrandbits(64), rng.randrange(0, 100), rng.randrange(0, 65536)) for _ in range(40)]
+    for seed, hop, walk in cases:
+        want = _curand_host_block(L, seed, hop * 65536 + walk)
+        got = O.philox4x32_10([hop, 0, walk, 0], [seed & 0xffffffff, seed >> 32])
+        assert [int(x) for x in got] == want, (seed, hop, walk)
+
+
+def test_u53_range():
+    assert O.u53(0, 0) == 0.0
+    assert O.u53(0xffffffff, 0xffffffff) == 1.0 - 2.0 ** -53
+    assert O.u53(0x80000000, 0) == 0.5
+    # the low 11 bits of the second word do not enter u
+    assert O.u53(0x12345678, 0x9abcdef0) == O.u53(0x12345678, 0x9abcdef0 | 0x7ff)
+
+
+# ---------------------------------------------------------------- samplers
+def _check_cdf_property(i, u, n, bias, lam):
+    """CDF(i-1) <= u < CDF(i) for the exact distribution."""
+    uf = Fraction(u)
+    if bias in (0, 1):
+        lo = brute.cdf_exact(i - 1, n, bias) if i > 0 else Fraction(0)
+        hi = brute.cdf_exact(i, n, bias)
+        return lo <= uf < hi, min(abs(uf - lo), abs(hi - uf))
+    from decimal import Decimal
+    ud = Decimal(uf.numerator) / Decimal(uf.denominator)
+    lo = brute.cdf_exact(i - 1, n, bias, lam) if i > 0 else Decimal(0)
+    hi = brute.cdf_exact(i, n, bias, lam)
+    return lo <= ud < hi, min(abs(ud - lo), abs(hi - ud))
+
+
+@pytest.mark.parametrize("bias", [0, 1, 2])
+def test_sampler_inverse_cdf_property(bias):
+    rng = random.Random(100 + bias)
+    bad = 0
+    for trial in range(3000):
+        n = rng.choice([1, 2, 3, 5, 17, 100, 1000, rng.randrange(1, 5000)])
+        lam = rng.choice([1.0, 0.5, 0.01, 1.0 / max(n, 1), 3.0]) if bias == 2 else 1.0
+        u = rng.random()
+        i = O.sampler_index(u, n, bias, lam)
+        assert 0 <= i < n
+        ok, dist = _check_cdf_property(i, u, n, bias, lam)
+        if not ok:
+            # only allowed within rounding distance of a bucket boundary
+            assert float(dist) < 1e-12, (bias, n, lam, u, i)
+            bad += 1
+    assert bad <= 3
+
+
+def test_sampler_extreme_u():
+    for bias in (0, 1, 2):
+        for n in (1, 2, 7, 10**6, 2**31 - 1):
+            assert O.sampler_index(0.0, n, bias, 1.0) == 0
+            assert O.sampler_index(1.0 - 2.0 ** -53, n, bias, 1.0) == n - 1
+    # n == 1 always draws index 0
+    for u in (0.0, 0.3, 0.999):
+        for bias in (0, 1, 2):
+            assert O.sampler_index(u, 1, bias, 1.0) == 0
+
+
+def test_printed_eq3_is_off_by_one_but_oracle_is_not():
+    """The printed exponential sampler floor(n + ln u - 1) never returns n-1,
+    which the inverse-CDF pin rejects; the oracle's exact form passes."""
+    n, u = 10, 0.9
+    printed = math.floor(n + math.log(u) - 1)
+    ok, _ = _check_cdf_property(printed, u, n, 2, 1.0)
+    assert not ok
+    i = O.sampler_index(u, n, 2, 1.0)
+    assert i == n - 1
+    assert _check_cdf_property(i, u, n, 2, 1.0)[0]
+
+
+def test_sampler_worked_example():
+    ex = json.load(open(os.path.join(GOLDEN, "tiny_stream.json")))["sampler_example"]
+    for bias_name, bias in (("linear", 1), ("exp", 2)):
+        for u, want in ex["group_index_at_u"][bias_name]:
+            assert O.sampler_index(u, 2, bias, 1.0) == want, (bias_name, u)
+    # x lands exactly on the boundary for linear at u = 1/3
+    assert O.sampler_x(1.0 / 3.0, 2, 1, 1.0) == 1.0
+
+
+@pytest.mark.parametrize("bias,n,lam", [(0, 7, 1.0), (1, 6, 1.0), (2, 5, 1.0), (2, 40, 0.1)])
+def test_sampler_chi_square(bias, n, lam):
+    from scipy.stats import chisquare
+    draws = 200_000
+    counts = np.zeros(n, np.int64)
+    for k in range(draws):
+        r = O.philox4x32_10([k & 0xffffffff, 0, 5, 0], [123, 456])
+        counts[O.sampler_index(O.u53(r[0], r[1]), n, bias, lam)] += 1
+    w = np.array(brute.group_weights(n, bias, lam), np.float64)
+    exp = w / w.sum() * draws
+    keep = exp > 5
+    stat, p = chisquare(counts[keep], exp[keep] * counts[keep].sum() / exp[keep].sum())
+    assert p > 1e-3, (p, counts, exp)
+
+
+# ---------------------------------------------------------------- index state
+def _state_equal(st, want, directed=True):
+    for k in ("src", "dst", "ts", "ts_group_off", "node_off", "node_order", "node_group_off",
+              "node_gidx"):
+        assert list(st[k]) == list(want[k]), k
+    assert st["counts"]["dropped_late"] == want["dropped_late"]
+    assert st["counts"]["evicted"] == want["evicted"]
+    if want.get("cutoff") is not None:
+        assert st["counts"]["has_cutoff"] == 1
+        assert st["counts"]["cutoff"] == want["cutoff"]
+
+
+def test_state_hand_worked_fixture():
+    fx = json.load(open(os.path.join(GOLDEN, "tiny_stream.json")))
+    o = O.Oracle(window=fx["window"], directed=fx["directed"])
+    for b, want in zip(fx["batches"], fx["expected"]):
+        o.ingest(b["src"], b["dst"], b["ts"])
+        _state_equal(o.state(), want)
+
+
+def _random_stream(rng, n_batches, max_batch, n_nodes, ts_span, monotone):
+    out = []
+    t = 0
+    for _ in range(n_batches):
+        k = rng.randrange(0, max_batch + 1)
+        src = [rng.randrange(0, n_nodes) for _ in range(k)]
+        dst = [rng.randrange(0, n_nodes) for _ in range(k)]
+        if monotone:
+            ts = []
+            for _ in range(k):
+                t += rng.choice([0, 0, 1, 2, 5])
+                ts.append(t)
+        else:
+            ts = [rng.randrange(-ts_span // 4, ts_span) + t for _ in range(k)]
+            t += ts_span // 3
+        out.append((src, dst, ts))
+    return out
+
+
+@pytest.mark.parametrize("directed", [True, False])
+@pytest.mark.parametrize("window", [0, 6, 25, -1, -7, -30])
+def test_state_matches_brute_force(directed, window):
+    rng = random.Random(hash((directed, window)) & 0xffff)
+    for trial in range(25):
+        stream = _random_stream(rng, rng.randrange(1, 6), 12, rng.randrange(1, 7), 20,
+                                monotone=rng.random() < 0.4)
+        want = brute.window_state(stream, window, directed)
+        o = O.Oracle(window=window, directed=directed)
+        for (s, d, t), w in zip(stream, want):
+            o.ingest(s, d, t)
+            st = o.state()
+            _state_equal(st, w, directed)
+            assert st["counts"]["n_nodes"] == w["n_nodes"]
+
+
+def test_ingest_rejects_bad_input():
+    o = O.Oracle(window=0)
+    with pytest.raises(ValueError):
+        o.ingest([0, -1], [1, 1], [1, 2])
+    assert o.counts()["m"] == 0
+    o.ingest([], [], [])
+    assert o.counts()["m"] == 0
+
+
+def test_undirected_view_is_symmetric():
+    """Swapping src and dst of every edge leaves the undirected node view's
+    (node, other, ts) multiset unchanged."""
+    rng = random.Random(3)
+    s = [rng.randrange(0, 6) for _ in range(40)]
+    d = [rng.randrange(0, 6) for _ in range(40)]
+    t = [rng.randrange(0, 10) for _ in range(40)]
+
+    def view(a, b):
+        o = O.Oracle(window=0, directed=False)
+        o.ingest(a, b, t)
+        st = o.state()
+        res = []
+        for v in range(len(st["node_off"]) - 1):
+            for i in range(st["node_off"][v], st["node_off"][v + 1]):
+                slot = st["node_order"][i]
+                p = slot >> 1
+                other = st["src"][p] if slot & 1 else st["dst"][p]
+                res.append((v, int(other), int(st["ts"][p])))
+        return sorted(res)
+
+    assert view(s, d) == view(d, s)
+
+
+# ---------------------------------------------------------------- walks
+def _walk_key(node_row, ts_row, ln):
+    return tuple((int(node_row[i]), None if i == 0 else int(ts_row[i])) for i in range(ln))
+
+
+@pytest.mark.parametrize("directed,bias,policy", [
+    (True, 0, 0), (True, 1, 0), (True, 2, 0), (True, 1, 1), (True, 2, 1), (True, 0, 1),
+    (False, 0, 0), (False, 2, 1),
+])
+def test_walk_distribution_matches_enumeration(directed, bias, policy):
+    from scipy.stats import chisquare
+    # tiny graph with ties, a self-loop and a dead end
+    src = [0, 0, 0, 1, 1, 2, 2, 3, 0, 2]
+    dst = [1, 2, 1, 2, 0, 0, 3, 0, 0, 2]
+    ts = [1, 2, 2, 3, 4, 5, 5, 6, 7, 6]
+    lam_hop, lam_start = 0.7, 0.4
+    max_len = 4
+    o = O.Oracle(window=0, directed=directed)
+    o.ingest(src, dst, ts)
+    o.set_bias_params(lam_hop, lam_start)
+    live = brute.window_state([(src, dst, ts)], 0, directed)[-1]["live"]
+    dist = brute.walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start)
+    assert abs(sum(dist.values()) - 1.0) < 1e-9
+    n = 60_000
+    node, tsa, ln, _, _ = o.walks(n, max_len, bias=bias, start_policy=policy, seed=99)
+    counts = {}
+    for i in range(n):
+        k = _walk_key(node[i], tsa[i], ln[i])
+        assert k in dist, k
+        counts[k] = counts.get(k, 0) + 1
+    keys = [k for k in dist if dist[k] * n > 5]
+    obs = np.array([counts.get(k, 0) for k in keys], np.float64)
+    exp = np.array([dist[k] * n for k in keys], np.float64)
+    exp *= obs.sum() / exp.sum()
+    stat, p = chisquare(obs, exp)
+    assert p > 1e-3, p
+
+
+def _check_walk_invariants(st, directed, node, tsa, ln, max_len):
+    live = {}
+    for a, b, t in zip(st["src"], st["dst"], st["ts"]):
+        live[(int(a), int(b), int(t))] = live.get((int(a), int(b), int(t)), 0) + 1
+        if not directed:
+            live[(int(b), int(a), int(t))] = live.get((int(b), int(a), int(t)), 0) + 1
+    # per node: sorted ts of its entries, for the termination check
+    by_node = {}
+    for (a, b, t) in live:
+        by_node.setdefault(a, []).append(t)
+    for v in by_node:
+        by_node[v].sort()
+    for i in range(node.shape[0]):
+        L = int(ln[i])
+        assert 2 <= L <= max_len
+        for h in range(1, L):
+            e = (int(node[i, h - 1]), int(node[i, h]), int(tsa[i, h]))
+            assert e in live, (i, h, e)
+            if h >= 2:
+                assert tsa[i, h] > tsa[i, h - 1]
+        assert (node[i, L:] == -1).all() and (tsa[i, L:] == np.iinfo(np.int64).min).all()
+        if L < max_len:  # stopped early: no continuation exists
+            v, t = int(node[i, L - 1]), int(tsa[i, L - 1])
+            assert not any(x > t for x in by_node.get(v, [])), (i, v, t)
+
+
+@pytest.mark.parametrize("directed", [True, False])
+def test_walk_invariants_small_config(directed):
+    from paper_2605_16182_gb300 import synth
+    spec = synth.config_small(scale=0.05)
+    o = O.Oracle(window=0, directed=directed)
+    for k, s, d, t in spec.batches():
+        o.ingest(s.numpy(), d.numpy(), t.numpy())
+    st = o.state()
+    for bias in (0, 1, 2):
+        node, tsa, ln, _, _ = o.walks(2000, 12, bias=bias, seed=bias)
+        _check_walk_invariants(st, directed, node, tsa, ln, 12)
+
+
+def test_walks_by_id_subset_equal_full_run():
+    from paper_2605_16182_gb300 import synth
+    spec = synth.config_small(scale=0.05)
+    o = O.Oracle(window=0)
+    for k, s, d, t in spec.batches():
+        o.ingest(s.numpy(), d.numpy(), t.numpy())
+    full = o.walks(500, 10, bias=2, seed=5)
+    ids = np.array([3, 499, 0, 77, 77], np.int64)
+    sub = o.walks(ids=ids, max_len=10, bias=2, seed=5)
+    assert (sub[0] == full[0][ids]).all() and (sub[1] == full[1][ids]).all()
+    assert (sub[2] == full[2][ids]).all()
+
+
+def test_walks_on_empty_graph():
+    o = O.Oracle(window=0)
+    node, tsa, ln, _, _ = o.walks(4, 5, seed=1)
+    assert (ln == 0).all() and (node == -1).all()
