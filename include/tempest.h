@@ -1,0 +1,199 @@
+/*
+ * tempest.h -- C ABI of the GB300 streaming temporal random-walk engine.
+ *
+ * The engine keeps a sliding window over a temporal edge stream in GPU
+ * memory, indexes it two ways over one edge store, and draws causality-
+ * preserving random walks from it (Tempest, Sec. 2).  Every call is a plain C
+ * function taking plain pointers and sizes; no C++ or framework types cross
+ * this boundary.
+ *
+ * Conventions
+ *  - Every call returns a status: TEMPEST_OK (0) or a negative TEMPEST_E*
+ *    code.  tempest_last_error() gives a human-readable reason.  No call
+ *    aborts the process or leaves the handle half-updated on EINVAL.
+ *  - Pointers to caller data may be host or device pointers; the library
+ *    detects which (cudaPointerGetAttributes).  The caller keeps ownership.
+ *    Host inputs are copied before the call returns.  Host outputs are
+ *    complete when the call returns.  Device outputs are complete when work
+ *    queued on the handle's stream before the next call has finished
+ *    (stream order); tempest_sync() waits for it.
+ *  - All device work runs on the stream given by tempest_set_stream (the
+ *    legacy default stream when none is set).
+ *  - Node ids are int32 >= 0; timestamps are int64.  The node arrays span
+ *    [0, 1 + largest id ever ingested].  Live index entries (one per edge for
+ *    directed graphs, two for undirected) must stay below 2^31 - 1.
+ *  - The handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef TEMPEST_H
+#define TEMPEST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tempest tempest_t;
+
+enum {
+    TEMPEST_OK = 0,
+    TEMPEST_EINVAL = -1,    /* bad argument; no state changed */
+    TEMPEST_ENOMEM = -2,    /* allocation failed or HBM budget exceeded */
+    TEMPEST_ECUDA = -3,     /* a CUDA runtime call failed */
+    TEMPEST_ETIMEDOUT = -4, /* a bounded device wait gave up */
+    TEMPEST_EBUSY = -5      /* the serving queue is full */
+};
+
+/* Temporal bias of a hop (Sec. 2.5).  UNIFORM: every edge of Gamma_t(v)
+ * equally likely (Eq. 1).  LINEAR: timestamp group i of Gamma_t(v), in
+ * ascending time order, has weight i+1 (Eq. 2).  EXP: group i has weight
+ * exp(lambda*i), drawn with the exact inverse CDF
+ * x = n + log(u + (1-u) exp(-lambda n)) / lambda (Eq. 3 corrected: the printed
+ * approximation cannot return the newest group).  For LINEAR and EXP an edge
+ * is then drawn uniformly inside the chosen group (ties broken uniformly,
+ * Sec. 2.1). */
+enum { TEMPEST_BIAS_UNIFORM = 0, TEMPEST_BIAS_LINEAR = 1, TEMPEST_BIAS_EXP = 2 };
+
+/* Start-edge selection (Sec. 2.3, timestamp-grouped view).
+ * UNIFORM_EDGE: a live edge uniformly.  BIASED_TS: a timestamp group of the
+ * whole window under the walk's own bias (EXP uses the start rate), then an
+ * edge uniformly inside the group. */
+enum { TEMPEST_START_UNIFORM_EDGE = 0, TEMPEST_START_BIASED_TS = 1 };
+
+/* Walk execution form (Sec. 2.4).  The result is the same for every form:
+ * each walk draws from its own counter-based random stream. */
+enum {
+    TEMPEST_SCHED_FULL_WALK = 0, /* one thread carries one walk (Sec. 2.4.1) */
+    TEMPEST_SCHED_COOP = 1       /* per-hop regrouping by node, thread / warp /
+                                    block tiers (Sec. 2.4.3-2.4.5, Alg. 1) */
+};
+
+/* Per-batch ingest report. */
+typedef struct {
+    int64_t n_in;          /* edges passed in */
+    int64_t n_dropped_late;/* of those, older than the cut-off in force */
+    int64_t n_evicted;     /* live edges removed by this batch's cut-off */
+    int64_t n_live;        /* live edges after the batch */
+    int64_t n_ts_groups;   /* distinct timestamps among live edges */
+    int64_t n_node_groups; /* (node, timestamp) groups of the node view */
+    int64_t n_nodes;       /* 1 + largest id seen */
+    int64_t cutoff;        /* window cut-off (valid when has_cutoff) */
+    int32_t has_cutoff;
+    int32_t sorted_input;  /* the batch arrived in timestamp order */
+} tempest_ingest_stats;
+
+/* Per-call walk report (valid once the call's work has finished). */
+typedef struct {
+    int64_t n_walks;
+    int64_t hops;          /* edges traversed, start edge included */
+    int64_t model_bytes;   /* sum of the per-hop sector model over the hops */
+    int64_t launches;      /* kernels this library launched for the call */
+} tempest_walk_stats;
+
+/* Create an engine.  window > 0: duration Delta in timestamp units, the
+ * active set is {e : t - Delta <= t_e <= t} with t the largest timestamp
+ * ingested (Sec. 2.6).  window < 0: keep the -window newest edges, cutting at
+ * the timestamp of the (-window)-th newest and keeping that whole timestamp
+ * group.  window == 0: keep everything.  directed == 0 indexes every edge
+ * under both endpoints.  *out receives the handle.  EINVAL on out == NULL. */
+int tempest_create(int64_t window, int directed, tempest_t **out);
+
+/* Free the handle and all device memory it owns.  NULL is accepted. */
+int tempest_destroy(tempest_t *h);
+
+/* Queue all further device work of the handle on stream (a cudaStream_t). */
+int tempest_set_stream(tempest_t *h, void *stream);
+
+/* Route device allocations through alloc(bytes, ctx) / release(ptr, ctx)
+ * (e.g. a framework's caching allocator) and cap the handle's device memory
+ * at hbm_budget bytes (0 = no cap).  Either callback may be NULL to restore
+ * cudaMalloc / cudaFree.  Call before the first ingest. */
+int tempest_set_allocator(tempest_t *h, void *(*alloc)(size_t bytes, void *ctx),
+                          void (*release)(void *ptr, void *ctx), void *ctx, size_t hbm_budget);
+
+/* Exponential rates: lambda_hop > 0 per timestamp group for hops (1 is the
+ * paper's form); lambda_start > 0 for BIASED_TS start selection, or 0 for
+ * 1 / (number of timestamp groups in the window), i.e. one e-fold across the
+ * window.  EINVAL otherwise. */
+int tempest_set_bias_params(tempest_t *h, double lambda_hop, double lambda_start);
+
+/* Ingest one batch of n edges (Sec. 2.6): every edge gets the next arrival
+ * index; edges older than the cut-off in force are dropped and counted; the
+ * rest are sorted by timestamp (arrival order among ties) and merged into
+ * the edge store; the cut-off advances and the edges before it are evicted;
+ * both views are rebuilt (Sec. 2.3).  src, dst: int32[n] node ids >= 0;
+ * ts: int64[n].  stats may be NULL.  EINVAL (state unchanged) on n < 0, NULL
+ * arrays with n > 0, or a negative id.  Synchronises the stream. */
+int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const int64_t *ts,
+                   int64_t n, tempest_ingest_stats *stats);
+
+/* Draw n_walks walks (Sec. 2.1, 2.4, 2.5).  Walk w uses Philox4x32-10
+ * (Salmon et al., SC'11) with key = seed and counter (hop, 0, w_lo, w_hi);
+ * hop 0 selects the start edge, hop h >= 1 the h-th continuation.  From each
+ * block, u1 = (r0:r1 >> 11) * 2^-53 picks the edge or group and
+ * u2 = (r2:r3 >> 11) * 2^-53 the edge inside a group; bit 0 of r3 orients an
+ * undirected start edge.  At node v and time t the next edge comes from
+ * Gamma_t(v) = {(v, w, t') : t' > t}; the walk stops when Gamma_t(v) is
+ * empty or max_len nodes are reached.
+ * Outputs, row-major with row stride max_len: node int32[n_walks*max_len],
+ * ts int64[n_walks*max_len] (ts of node 0 is INT64_MIN; padding is node -1,
+ * ts INT64_MIN), len int32[n_walks] (nodes written; 0 on an empty window).
+ * EINVAL on n_walks < 0, max_len < 2, bad bias / start policy or NULL
+ * outputs. */
+int tempest_walks(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy,
+                  uint64_t seed, int32_t *node, int64_t *ts, int32_t *len);
+
+/* Like tempest_walks with a per-walk length cap and bias, all in one launch:
+ * max_len_arr int32[n_walks] (each in [2, max_len_cap]), bias_arr
+ * uint8[n_walks] (each a TEMPEST_BIAS_*).  Rows have stride max_len_cap. */
+int tempest_walks_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_arr,
+                        int32_t max_len_cap, const uint8_t *bias_arr, int start_policy,
+                        uint64_t seed, int32_t *node, int64_t *ts, int32_t *len);
+
+/* Select the walk execution form (TEMPEST_SCHED_*) for later walk calls. */
+int tempest_set_scheduler(tempest_t *h, int mode);
+
+/* Report of the most recent walk call; waits for its work to finish. */
+int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out);
+
+/* Live counters: out[0..9] = live edges m, timestamp groups, n_nodes, node
+ * view entries M, node groups, dropped-late total, evicted total, has_cutoff,
+ * cutoff, next arrival index. */
+int tempest_get_counts(tempest_t *h, int64_t out[10]);
+
+/* Export one array of the index state into dst (host or device) for
+ * checking: which = TEMPEST_STATE_*.  cap is dst's capacity in elements;
+ * *n receives the element count (call with dst == NULL to query it).  The
+ * arrays are the canonical forms of Sec. 2.3: the live store in (ts, arrival)
+ * order, the start offset of every timestamp group plus m, per node the start
+ * of its segment of the node view plus M, the node view as store slots
+ * (position, or 2*position + side for undirected graphs), the start of every
+ * (node, timestamp) group plus M, and per node its first group index. */
+enum {
+    TEMPEST_STATE_SRC = 0,            /* int32[m]   */
+    TEMPEST_STATE_DST = 1,            /* int32[m]   */
+    TEMPEST_STATE_TS = 2,             /* int64[m]   */
+    TEMPEST_STATE_TS_GROUP_OFF = 3,   /* int32[G+1] */
+    TEMPEST_STATE_NODE_OFF = 4,       /* int32[N+1] */
+    TEMPEST_STATE_NODE_ORDER = 5,     /* int32[M]   */
+    TEMPEST_STATE_NODE_GROUP_OFF = 6, /* int32[Gn+1] */
+    TEMPEST_STATE_NODE_GIDX = 7       /* int32[N+1] */
+};
+int tempest_export_state(tempest_t *h, int which, void *dst, int64_t cap, int64_t *n);
+
+/* Wait for all work queued on the handle's stream. */
+int tempest_sync(tempest_t *h);
+
+/* Reason for the last failing call on h (or of tempest_create when h is
+ * NULL).  Valid until the next call on h. */
+const char *tempest_last_error(tempest_t *h);
+
+/* Library version string. */
+const char *tempest_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TEMPEST_H */

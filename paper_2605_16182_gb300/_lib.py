@@ -1,0 +1,323 @@
+"""ctypes binding of libtempest.so (include/tempest.h).
+
+Argument marshalling only: every step of ingest and walk generation runs in
+the CUDA library.  If the library is missing this module raises; there is no
+CPU fallback.  The module-level functions carry the C names; ``Engine`` wraps
+a handle for torch tensors / numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+TEMPEST_OK = 0
+TEMPEST_EINVAL = -1
+TEMPEST_ENOMEM = -2
+TEMPEST_ECUDA = -3
+TEMPEST_ETIMEDOUT = -4
+TEMPEST_EBUSY = -5
+
+BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP = 0, 1, 2
+START_UNIFORM_EDGE, START_BIASED_TS = 0, 1
+SCHED_FULL_WALK, SCHED_COOP = 0, 1
+(STATE_SRC, STATE_DST, STATE_TS, STATE_TS_GROUP_OFF, STATE_NODE_OFF, STATE_NODE_ORDER,
+ STATE_NODE_GROUP_OFF, STATE_NODE_GIDX) = range(8)
+
+# every function declared in include/tempest.h
+EXPORTED = (
+    "tempest_create", "tempest_destroy", "tempest_set_stream", "tempest_set_allocator",
+    "tempest_set_bias_params", "tempest_ingest", "tempest_walks", "tempest_walks_mixed",
+    "tempest_set_scheduler", "tempest_last_walk_stats", "tempest_get_counts",
+    "tempest_export_state", "tempest_sync", "tempest_last_error", "tempest_version",
+)
+
+
+class TempestError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("tempest error %d: %s" % (code, msg))
+        self.code = code
+
+
+class IngestStats(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int64), ("n_dropped_late", ctypes.c_int64),
+                ("n_evicted", ctypes.c_int64), ("n_live", ctypes.c_int64),
+                ("n_ts_groups", ctypes.c_int64), ("n_node_groups", ctypes.c_int64),
+                ("n_nodes", ctypes.c_int64), ("cutoff", ctypes.c_int64),
+                ("has_cutoff", ctypes.c_int32), ("sorted_input", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class WalkStats(ctypes.Structure):
+    _fields_ = [("n_walks", ctypes.c_int64), ("hops", ctypes.c_int64),
+                ("model_bytes", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_L = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libtempest.so; raises if it has not been built."""
+    global _L
+    if _L is not None:
+        return _L
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libtempest.so is not built (%s); run paper_2605_16182_gb300.build.build()" % path)
+    L = ctypes.CDLL(path)
+    vp, i64, i32, u64, dbl, ci = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                  ctypes.c_double, ctypes.c_int)
+    L.tempest_create.argtypes = [i64, ci, ctypes.POINTER(vp)]
+    L.tempest_destroy.argtypes = [vp]
+    L.tempest_set_stream.argtypes = [vp, vp]
+    L.tempest_set_allocator.argtypes = [vp, ALLOC_FN, RELEASE_FN, vp, ctypes.c_size_t]
+    L.tempest_set_bias_params.argtypes = [vp, dbl, dbl]
+    L.tempest_ingest.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(IngestStats)]
+    L.tempest_walks.argtypes = [vp, i64, i32, ci, ci, u64, vp, vp, vp]
+    L.tempest_walks_mixed.argtypes = [vp, i64, vp, i32, vp, ci, u64, vp, vp, vp]
+    L.tempest_set_scheduler.argtypes = [vp, ci]
+    L.tempest_last_walk_stats.argtypes = [vp, ctypes.POINTER(WalkStats)]
+    L.tempest_get_counts.argtypes = [vp, vp]
+    L.tempest_export_state.argtypes = [vp, ci, vp, i64, ctypes.POINTER(i64)]
+    L.tempest_sync.argtypes = [vp]
+    L.tempest_last_error.argtypes = [vp]
+    L.tempest_last_error.restype = ctypes.c_char_p
+    L.tempest_version.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("tempest_last_error", "tempest_version"):
+            getattr(L, name).restype = ci
+    _L = L
+    return L
+
+
+def _check(h, rc):
+    if rc != TEMPEST_OK:
+        msg = load().tempest_last_error(h)
+        raise TempestError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ---------------------------------------------------------------- C names
+def tempest_version() -> str:
+    return load().tempest_version().decode()
+
+
+def tempest_create(window: int, directed: bool):
+    h = ctypes.c_void_p()
+    _check(None, load().tempest_create(int(window), 1 if directed else 0, ctypes.byref(h)))
+    return h
+
+
+def tempest_destroy(h):
+    return load().tempest_destroy(h)
+
+
+def tempest_set_stream(h, stream_ptr: int):
+    return _check(h, load().tempest_set_stream(h, ctypes.c_void_p(stream_ptr)))
+
+
+def tempest_set_allocator(h, alloc, release, ctx, budget: int):
+    return _check(h, load().tempest_set_allocator(h, alloc, release, ctx, ctypes.c_size_t(budget)))
+
+
+def tempest_set_bias_params(h, lambda_hop: float, lambda_start: float):
+    return _check(h, load().tempest_set_bias_params(h, float(lambda_hop), float(lambda_start)))
+
+
+def tempest_ingest(h, src_ptr, dst_ptr, ts_ptr, n: int) -> IngestStats:
+    st = IngestStats()
+    _check(h, load().tempest_ingest(h, ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr),
+                                    ctypes.c_void_p(ts_ptr), int(n), ctypes.byref(st)))
+    return st
+
+
+def tempest_walks(h, n_walks, max_len, bias, start_policy, seed, node_ptr, ts_ptr, len_ptr):
+    return _check(h, load().tempest_walks(h, int(n_walks), int(max_len), int(bias), int(start_policy),
+                                          ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                          ctypes.c_void_p(node_ptr), ctypes.c_void_p(ts_ptr),
+                                          ctypes.c_void_p(len_ptr)))
+
+
+def tempest_walks_mixed(h, n_walks, max_len_ptr, max_len_cap, bias_ptr, start_policy, seed, node_ptr,
+                        ts_ptr, len_ptr):
+    return _check(h, load().tempest_walks_mixed(h, int(n_walks), ctypes.c_void_p(max_len_ptr),
+                                                int(max_len_cap), ctypes.c_void_p(bias_ptr),
+                                                int(start_policy),
+                                                ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                                ctypes.c_void_p(node_ptr), ctypes.c_void_p(ts_ptr),
+                                                ctypes.c_void_p(len_ptr)))
+
+
+def tempest_set_scheduler(h, mode: int):
+    return _check(h, load().tempest_set_scheduler(h, int(mode)))
+
+
+def tempest_last_walk_stats(h) -> WalkStats:
+    ws = WalkStats()
+    _check(h, load().tempest_last_walk_stats(h, ctypes.byref(ws)))
+    return ws
+
+
+def tempest_get_counts(h):
+    out = (ctypes.c_int64 * 10)()
+    _check(h, load().tempest_get_counts(h, out))
+    return list(out)
+
+
+def tempest_export_state(h, which: int, dst_ptr, cap: int) -> int:
+    n = ctypes.c_int64()
+    _check(h, load().tempest_export_state(h, int(which), ctypes.c_void_p(dst_ptr) if dst_ptr else None,
+                                          int(cap), ctypes.byref(n)))
+    return n.value
+
+
+def tempest_sync(h):
+    return _check(h, load().tempest_sync(h))
+
+
+def tempest_last_error(h) -> str:
+    m = load().tempest_last_error(h)
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------- wrapper
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data
+
+
+class Engine:
+    """A handle plus tensor-friendly calls.  Inputs may be CPU or CUDA
+    tensors (or numpy arrays); outputs are allocated on `device`."""
+
+    COUNT_KEYS = ("m", "G_tot", "n_nodes", "M", "Gn", "dropped_late", "evicted", "has_cutoff",
+                  "cutoff", "seq_next")
+
+    def __init__(self, window: int = 0, directed: bool = True, device: str = "cuda",
+                 torch_allocator: bool = False, hbm_budget: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.h = tempest_create(window, directed)
+        self.directed = directed
+        self._cb = None
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        tempest_set_stream(self.h, st.cuda_stream)
+        self.stream = st
+        if torch_allocator or hbm_budget:
+            self.use_torch_allocator(hbm_budget)
+
+    def use_torch_allocator(self, budget: int = 0):
+        torch = self.torch
+        dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
+        stream = self.stream
+
+        @ALLOC_FN
+        def _alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+            except Exception:
+                return None
+
+        @RELEASE_FN
+        def _release(ptr, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._cb = (_alloc, _release)
+        tempest_set_allocator(self.h, _alloc, _release, None, int(budget))
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            tempest_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_bias_params(self, lambda_hop: float, lambda_start: float = 0.0):
+        tempest_set_bias_params(self.h, lambda_hop, lambda_start)
+
+    def set_scheduler(self, mode: int):
+        tempest_set_scheduler(self.h, mode)
+
+    def ingest(self, src, dst, ts) -> dict:
+        n = int(src.shape[0])
+        assert dst.shape[0] == n and ts.shape[0] == n
+        return tempest_ingest(self.h, _ptr(src), _ptr(dst), _ptr(ts), n).as_dict()
+
+    def walks(self, n_walks: int, max_len: int, bias: int = BIAS_UNIFORM,
+              start_policy: int = START_UNIFORM_EDGE, seed: int = 0, out=None):
+        torch = self.torch
+        if out is None:
+            node = torch.empty((n_walks, max_len), dtype=torch.int32, device=self.device)
+            ts = torch.empty((n_walks, max_len), dtype=torch.int64, device=self.device)
+            ln = torch.empty((n_walks,), dtype=torch.int32, device=self.device)
+        else:
+            node, ts, ln = out
+        tempest_walks(self.h, n_walks, max_len, bias, start_policy, seed, _ptr(node), _ptr(ts), _ptr(ln))
+        return node, ts, ln
+
+    def walks_mixed(self, max_len_arr, bias_arr, start_policy: int = START_UNIFORM_EDGE, seed: int = 0,
+                    max_len_cap: Optional[int] = None, out=None):
+        torch = self.torch
+        n = int(max_len_arr.shape[0])
+        cap = int(max_len_cap if max_len_cap is not None else (int(max_len_arr.max()) if n else 2))
+        if out is None:
+            node = torch.empty((n, cap), dtype=torch.int32, device=self.device)
+            ts = torch.empty((n, cap), dtype=torch.int64, device=self.device)
+            ln = torch.empty((n,), dtype=torch.int32, device=self.device)
+        else:
+            node, ts, ln = out
+        tempest_walks_mixed(self.h, n, _ptr(max_len_arr), cap, _ptr(bias_arr), start_policy, seed,
+                            _ptr(node), _ptr(ts), _ptr(ln))
+        return node, ts, ln
+
+    def last_walk_stats(self) -> dict:
+        return tempest_last_walk_stats(self.h).as_dict()
+
+    def counts(self) -> dict:
+        return dict(zip(self.COUNT_KEYS, tempest_get_counts(self.h)))
+
+    def export(self, which: int):
+        """One state array as a numpy array (host copy)."""
+        n = tempest_export_state(self.h, which, None, 0)
+        dt = np.int64 if which == STATE_TS else np.int32
+        out = np.zeros(max(n, 1), dt)
+        if n:
+            tempest_export_state(self.h, which, out.ctypes.data, n)
+        return out[:n]
+
+    def state(self) -> dict:
+        c = self.counts()
+        return dict(counts=c, src=self.export(STATE_SRC), dst=self.export(STATE_DST),
+                    ts=self.export(STATE_TS), ts_group_off=self.export(STATE_TS_GROUP_OFF),
+                    node_off=self.export(STATE_NODE_OFF), node_order=self.export(STATE_NODE_ORDER),
+                    node_group_off=self.export(STATE_NODE_GROUP_OFF),
+                    node_gidx=self.export(STATE_NODE_GIDX))
+
+    def sync(self):
+        tempest_sync(self.h)

@@ -1,0 +1,429 @@
+// capi.cu -- the extern "C" entry points declared in include/tempest.h, and
+// the handle's memory management.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "engine.cuh"
+#include "prims.cuh"
+
+namespace tw {
+
+__global__ void k_scan_partials(uint64_t *p, int nb)
+{
+    __shared__ uint64_t sh[33];
+    uint64_t carry = 0;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint64_t v = i < nb ? p[i] : 0;
+        uint64_t tot;
+        const uint64_t ex = block_excl_scan<uint64_t>(v, sh, tot);
+        if (i < nb) p[i] = ex + carry;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) p[nb] = carry;
+}
+
+__global__ void k_scan_u32_small(uint32_t *a, int64_t n)
+{
+    __shared__ uint32_t sh[33];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = (int64_t)threadIdx.x * per;
+    const int64_t b1 = min(n, b0 + per);
+    uint32_t s = 0;
+    for (int64_t i = b0; i < b1; i++) s += a[i];
+    uint32_t tot;
+    uint32_t ex = block_excl_scan<uint32_t>(s, sh, tot);
+    for (int64_t i = b0; i < b1; i++) {
+        const uint32_t v = a[i];
+        a[i] = ex;
+        ex += v;
+    }
+}
+
+static thread_local std::string g_create_err;
+
+int fail(tempest_t *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+int cuda_check(tempest_t *h, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return TEMPEST_OK;
+    cudaGetLastError();
+    return fail(h, TEMPEST_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void release(tempest_t *h, DBuf &b)
+{
+    if (!b.p) return;
+    if (h->release_fn) h->release_fn(b.p, h->alloc_ctx);
+    else cudaFree(b.p);
+    h->in_use -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Make b hold at least `bytes`.  Contents are not preserved.  With headroom
+// the buffer grows by 25 % beyond the request so that a slowly growing
+// window does not reallocate on every batch.
+int ensure(tempest_t *h, DBuf &b, size_t bytes, bool headroom)
+{
+    if (bytes == 0) bytes = 1;
+    if (b.p && b.bytes >= bytes) return TEMPEST_OK;
+    size_t want = bytes;
+    if (headroom && b.p) want = bytes + bytes / 4;
+    want = (want + 255) & ~(size_t)255;
+    if (h->budget && h->in_use - b.bytes + want > h->budget) {
+        want = (bytes + 255) & ~(size_t)255;
+        if (h->in_use - b.bytes + want > h->budget)
+            return fail(h, TEMPEST_ENOMEM, "HBM budget of %zu bytes exceeded (in use %zu, need %zu more)",
+                        h->budget, h->in_use - b.bytes, want);
+    }
+    release(h, b);
+    void *p = nullptr;
+    if (h->alloc_fn) {
+        p = h->alloc_fn(want, h->alloc_ctx);
+        if (!p) return fail(h, TEMPEST_ENOMEM, "allocator callback returned NULL for %zu bytes", want);
+    } else {
+        const cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, TEMPEST_ENOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+        }
+    }
+    b.p = p;
+    b.bytes = want;
+    h->in_use += want;
+    return TEMPEST_OK;
+}
+
+static void free_all(tempest_t *h)
+{
+    DBuf *bufs[] = {&h->st_src[0], &h->st_src[1], &h->st_dst[0], &h->st_dst[1], &h->st_ts[0], &h->st_ts[1],
+                    &h->ts_goff,   &h->ent,       &h->ngo,       &h->ngts,      &h->gidx,     &h->b_src,
+                    &h->b_dst,     &h->b_ts,      &h->sb_src,    &h->sb_dst,    &h->sb_ts,    &h->sk64[0],
+                    &h->sk64[1],   &h->sk32[0],   &h->sk32[1],   &h->sv[0],     &h->sv[1],    &h->hist,
+                    &h->partials,  &h->seg_node,  &h->seg_g,     &h->gcnt,      &h->dstat,    &h->wcnt,
+                    &h->out_stage, &h->in_stage,  &h->exp_stage};
+    for (DBuf *b : bufs) release(h, *b);
+}
+
+}  // namespace tw
+
+using namespace tw;
+
+extern "C" {
+
+const char *tempest_version(void) { return "tempest-gb300 0.1 (sm_103a)"; }
+
+const char *tempest_last_error(tempest_t *h)
+{
+    if (!h) return g_create_err.c_str();
+    return h->err.c_str();
+}
+
+int tempest_create(int64_t window, int directed, tempest_t **out)
+{
+    if (!out) return fail(nullptr, TEMPEST_EINVAL, "tempest_create: out is NULL");
+    *out = nullptr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, TEMPEST_ECUDA, "tempest_create: no CUDA device: %s", cudaGetErrorString(e));
+    }
+    tempest_t *h = new (std::nothrow) tempest();
+    if (!h) return fail(nullptr, TEMPEST_ENOMEM, "tempest_create: out of host memory");
+    h->window = window;
+    h->directed = directed ? 1 : 0;
+    h->device = dev;
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (h->num_sms < 1) h->num_sms = 1;
+    e = cudaMallocHost(&h->hstat, 4096);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, TEMPEST_ENOMEM, "tempest_create: pinned host buffer: %s", cudaGetErrorString(e));
+    }
+    memset(h->hstat, 0, 4096);
+    *out = h;
+    return TEMPEST_OK;
+}
+
+int tempest_destroy(tempest_t *h)
+{
+    if (!h) return TEMPEST_OK;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    if (h->hstat) cudaFreeHost(h->hstat);
+    delete h;
+    return TEMPEST_OK;
+}
+
+int tempest_set_stream(tempest_t *h, void *stream)
+{
+    if (!h) return TEMPEST_EINVAL;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return TEMPEST_OK;
+}
+
+int tempest_set_allocator(tempest_t *h, void *(*alloc)(size_t, void *), void (*rel)(void *, void *), void *ctx,
+                          size_t hbm_budget)
+{
+    if (!h) return TEMPEST_EINVAL;
+    if (h->in_use > 0 && ((alloc != nullptr) != (h->alloc_fn != nullptr) || alloc != h->alloc_fn))
+        return fail(h, TEMPEST_EINVAL, "tempest_set_allocator: must be called before the first allocation");
+    if ((alloc == nullptr) != (rel == nullptr))
+        return fail(h, TEMPEST_EINVAL, "tempest_set_allocator: alloc and release must both be set or both NULL");
+    h->alloc_fn = alloc;
+    h->release_fn = rel;
+    h->alloc_ctx = ctx;
+    h->budget = hbm_budget;
+    return TEMPEST_OK;
+}
+
+int tempest_set_bias_params(tempest_t *h, double lambda_hop, double lambda_start)
+{
+    if (!h) return TEMPEST_EINVAL;
+    if (!(lambda_hop > 0.0) || !(lambda_start >= 0.0))
+        return fail(h, TEMPEST_EINVAL, "tempest_set_bias_params: need lambda_hop > 0 and lambda_start >= 0");
+    h->lam_hop = lambda_hop;
+    h->lam_start = lambda_start;
+    return TEMPEST_OK;
+}
+
+int tempest_set_scheduler(tempest_t *h, int mode)
+{
+    if (!h) return TEMPEST_EINVAL;
+    if (mode != TEMPEST_SCHED_FULL_WALK && mode != TEMPEST_SCHED_COOP)
+        return fail(h, TEMPEST_EINVAL, "tempest_set_scheduler: unknown mode %d", mode);
+    h->sched = mode;
+    return TEMPEST_OK;
+}
+
+int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const int64_t *ts, int64_t n,
+                   tempest_ingest_stats *stats)
+{
+    if (!h) return TEMPEST_EINVAL;
+    return ingest_batch(h, src, dst, ts, n, stats);
+}
+
+static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_len, const int32_t *len_arr,
+                        int bias, const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t *node,
+                        int64_t *ts, int32_t *len)
+{
+    int rc;
+    if (n_walks < 0) return fail(h, TEMPEST_EINVAL, "walks: n_walks < 0");
+    if (cap < 2) return fail(h, TEMPEST_EINVAL, "walks: max_len must be >= 2");
+    if (start_policy != TEMPEST_START_UNIFORM_EDGE && start_policy != TEMPEST_START_BIASED_TS)
+        return fail(h, TEMPEST_EINVAL, "walks: unknown start policy %d", start_policy);
+    if (!bias_arr && (bias < 0 || bias > 2)) return fail(h, TEMPEST_EINVAL, "walks: unknown bias %d", bias);
+    if (n_walks > 0 && (!node || !ts || !len)) return fail(h, TEMPEST_EINVAL, "walks: NULL output");
+    if (n_walks > 0 && (int64_t)cap * n_walks / n_walks != (int64_t)cap)
+        return fail(h, TEMPEST_EINVAL, "walks: output size overflows");
+    cudaStream_t st = h->stream;
+    h->last_ws = tempest_walk_stats{};
+    if (n_walks == 0) return TEMPEST_OK;
+
+    // per-walk inputs: validate on the host when they are host arrays
+    const int32_t *d_len = len_arr;
+    const uint8_t *d_bias = bias_arr;
+    const bool host_len = len_arr && !is_device_ptr(len_arr);
+    const bool host_bias = bias_arr && !is_device_ptr(bias_arr);
+    if (host_len)
+        for (int64_t i = 0; i < n_walks; i++)
+            if (len_arr[i] < 2 || len_arr[i] > cap)
+                return fail(h, TEMPEST_EINVAL, "walks_mixed: max_len_arr[%lld] = %d outside [2, %d]", (long long)i,
+                            len_arr[i], cap);
+    if (host_bias)
+        for (int64_t i = 0; i < n_walks; i++)
+            if (bias_arr[i] > 2)
+                return fail(h, TEMPEST_EINVAL, "walks_mixed: bias_arr[%lld] = %d unknown", (long long)i, bias_arr[i]);
+    if (host_len || host_bias) {
+        size_t need = 0;
+        if (host_len) need += sizeof(int32_t) * (size_t)n_walks;
+        if (host_bias) need += (size_t)n_walks + 16;
+        if ((rc = ensure(h, h->in_stage, need, true))) return rc;
+        char *p = h->in_stage.as<char>();
+        if (host_len) {
+            cudaMemcpyAsync(p, len_arr, sizeof(int32_t) * (size_t)n_walks, cudaMemcpyHostToDevice, st);
+            d_len = reinterpret_cast<const int32_t *>(p);
+            p += sizeof(int32_t) * (size_t)n_walks;
+        }
+        if (host_bias) {
+            cudaMemcpyAsync(p, bias_arr, (size_t)n_walks, cudaMemcpyHostToDevice, st);
+            d_bias = reinterpret_cast<const uint8_t *>(p);
+        }
+    }
+
+    const bool dev_node = is_device_ptr(node), dev_ts = is_device_ptr(ts), dev_len = is_device_ptr(len);
+    const size_t cells = (size_t)cap * (size_t)n_walks;
+    int32_t *d_node = node;
+    int64_t *d_ts = ts;
+    int32_t *d_lenout = len;
+    if (!dev_node || !dev_ts || !dev_len) {
+        size_t need = 0;
+        if (!dev_ts) need += sizeof(int64_t) * cells;
+        if (!dev_node) need += sizeof(int32_t) * cells;
+        if (!dev_len) need += sizeof(int32_t) * (size_t)n_walks;
+        if ((rc = ensure(h, h->out_stage, need + 64, true))) return rc;
+        char *p = h->out_stage.as<char>();
+        if (!dev_ts) {
+            d_ts = reinterpret_cast<int64_t *>(p);
+            p += sizeof(int64_t) * cells;
+        }
+        if (!dev_node) {
+            d_node = reinterpret_cast<int32_t *>(p);
+            p += sizeof(int32_t) * cells;
+        }
+        if (!dev_len) d_lenout = reinterpret_cast<int32_t *>(p);
+    }
+    WalkRequest rq{n_walks, cap, max_len, d_len, bias, d_bias, start_policy, seed, d_node, d_ts, d_lenout};
+    if ((rc = walks_run(h, rq))) return rc;
+    if (!dev_ts) cudaMemcpyAsync(ts, d_ts, sizeof(int64_t) * cells, cudaMemcpyDeviceToHost, st);
+    if (!dev_node) cudaMemcpyAsync(node, d_node, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st);
+    if (!dev_len) cudaMemcpyAsync(len, d_lenout, sizeof(int32_t) * (size_t)n_walks, cudaMemcpyDeviceToHost, st);
+    if (!dev_node || !dev_ts || !dev_len || host_len || host_bias)
+        return cuda_check(h, cudaStreamSynchronize(st), "walks (host outputs)");
+    return cuda_check(h, cudaGetLastError(), "walks");
+}
+
+int tempest_walks(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy, uint64_t seed,
+                  int32_t *node, int64_t *ts, int32_t *len)
+{
+    if (!h) return TEMPEST_EINVAL;
+    return walks_common(h, n_walks, max_len, max_len, nullptr, bias, nullptr, start_policy, seed, node, ts, len);
+}
+
+int tempest_walks_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_arr, int32_t max_len_cap,
+                        const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t *node, int64_t *ts,
+                        int32_t *len)
+{
+    if (!h) return TEMPEST_EINVAL;
+    if (n_walks > 0 && (!max_len_arr || !bias_arr))
+        return fail(h, TEMPEST_EINVAL, "tempest_walks_mixed: NULL max_len_arr or bias_arr");
+    return walks_common(h, n_walks, max_len_cap, max_len_cap, max_len_arr, 0, bias_arr, start_policy, seed, node,
+                        ts, len);
+}
+
+int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out)
+{
+    if (!h || !out) return TEMPEST_EINVAL;
+    int rc;
+    if (h->wcnt.p) {
+        WalkCounters *hc = static_cast<WalkCounters *>(h->hstat);
+        cudaMemcpyAsync(hc, h->wcnt.p, sizeof(WalkCounters), cudaMemcpyDeviceToHost, h->stream);
+        if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "walk stats"))) return rc;
+        h->last_ws.hops = (int64_t)hc->hops;
+        h->last_ws.model_bytes = (int64_t)hc->model_bytes;
+        if (hc->status) {
+            *out = h->last_ws;
+            return fail(h, TEMPEST_EINVAL, "walks_mixed: a per-walk max_len or bias was out of range "
+                                           "(those walks were clamped)");
+        }
+    }
+    *out = h->last_ws;
+    return TEMPEST_OK;
+}
+
+int tempest_get_counts(tempest_t *h, int64_t out[10])
+{
+    if (!h || !out) return TEMPEST_EINVAL;
+    out[0] = h->m;
+    out[1] = h->G;
+    out[2] = h->N;
+    out[3] = h->M;
+    out[4] = h->Gn;
+    out[5] = h->dropped;
+    out[6] = h->evicted;
+    out[7] = h->has_cutoff;
+    out[8] = h->cutoff;
+    out[9] = h->seq_next;
+    return TEMPEST_OK;
+}
+
+int tempest_export_state(tempest_t *h, int which, void *dst, int64_t cap, int64_t *n)
+{
+    if (!h) return TEMPEST_EINVAL;
+    int64_t cnt;
+    size_t esz;
+    switch (which) {
+        case TEMPEST_STATE_SRC: cnt = h->m; esz = 4; break;
+        case TEMPEST_STATE_DST: cnt = h->m; esz = 4; break;
+        case TEMPEST_STATE_TS: cnt = h->m; esz = 8; break;
+        case TEMPEST_STATE_TS_GROUP_OFF: cnt = h->G + 1; esz = 4; break;
+        case TEMPEST_STATE_NODE_OFF: cnt = h->N + 1; esz = 4; break;
+        case TEMPEST_STATE_NODE_ORDER: cnt = h->M; esz = 4; break;
+        case TEMPEST_STATE_NODE_GROUP_OFF: cnt = h->Gn + 1; esz = 4; break;
+        case TEMPEST_STATE_NODE_GIDX: cnt = h->N + 1; esz = 4; break;
+        default: return fail(h, TEMPEST_EINVAL, "tempest_export_state: unknown array %d", which);
+    }
+    if (n) *n = cnt;
+    if (!dst) return TEMPEST_OK;
+    if (cap < cnt) return fail(h, TEMPEST_EINVAL, "tempest_export_state: capacity %lld < %lld", (long long)cap,
+                               (long long)cnt);
+    if (cnt == 0) return TEMPEST_OK;
+    cudaStream_t st = h->stream;
+    const size_t bytes = esz * (size_t)cnt;
+    const bool dev = is_device_ptr(dst);
+    int rc;
+    if (!h->gidx.p) {
+        // nothing ingested yet: every remaining array is the single offset 0
+        if (dev) return cuda_check(h, cudaMemsetAsync(dst, 0, bytes, st), "export");
+        memset(dst, 0, bytes);
+        return TEMPEST_OK;
+    }
+    const void *srcp = nullptr;
+    if (which == TEMPEST_STATE_NODE_OFF || which == TEMPEST_STATE_NODE_ORDER) {
+        void *target = dst;
+        if (!dev) {
+            if ((rc = ensure(h, h->exp_stage, bytes))) return rc;
+            target = h->exp_stage.p;
+        }
+        if (which == TEMPEST_STATE_NODE_OFF) launch_node_off(h, static_cast<int32_t *>(target));
+        else launch_node_order(h, static_cast<int32_t *>(target));
+        srcp = target;
+        if (dev) return cuda_check(h, cudaGetLastError(), "export");
+    } else {
+        switch (which) {
+            case TEMPEST_STATE_SRC: srcp = h->st_src[h->cur].p; break;
+            case TEMPEST_STATE_DST: srcp = h->st_dst[h->cur].p; break;
+            case TEMPEST_STATE_TS: srcp = h->st_ts[h->cur].p; break;
+            case TEMPEST_STATE_TS_GROUP_OFF: srcp = h->ts_goff.p; break;
+            case TEMPEST_STATE_NODE_GROUP_OFF: srcp = h->ngo.p; break;
+            case TEMPEST_STATE_NODE_GIDX: srcp = h->gidx.p; break;
+        }
+    }
+    cudaMemcpyAsync(dst, srcp, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    return cuda_check(h, cudaStreamSynchronize(st), "export");
+}
+
+int tempest_sync(tempest_t *h)
+{
+    if (!h) return TEMPEST_EINVAL;
+    return cuda_check(h, cudaStreamSynchronize(h->stream), "tempest_sync");
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// engine.cuh -- the engine handle and the internal interfaces between the
+// C ABI (capi.cu), ingest (ingest.cu) and walk generation (walks.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tempest.h"
+
+namespace tw {
+
+// One entry of the node-and-timestamp-grouped view (Sec. 2.3).  The paper's
+// view is offsets over the shared store; here each entry also carries the
+// timestamp and the far endpoint of its edge, so a hop reads one 16-byte
+// aligned record instead of chasing a store position into two more arrays.
+struct __align__(16) Entry {
+    int64_t ts;
+    int32_t other;  // the endpoint a hop moves to
+    int32_t slot;   // store position (directed) or 2*position + side
+};
+
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// Small device-side record the ingest kernels fill and the host reads back.
+struct IngestScratch {
+    long long ts_min, ts_max;
+    int max_id, neg_id;
+    unsigned long long late, unsorted;
+    long long cut;          // new cut-off
+    int has_cut, pad0;
+    long long i0, j0;       // first kept store / batch element
+    long long kept_batch_min_ts;
+    long long store_last_ts;
+};
+
+// Device-side walk counters.
+struct WalkCounters {
+    unsigned long long hops;
+    unsigned long long model_bytes;
+    unsigned long long status;  // nonzero: a kernel found corrupt state
+    unsigned long long pad;
+};
+
+}  // namespace tw
+
+struct tempest {
+    // configuration
+    int64_t window = 0;
+    int directed = 1;
+    double lam_hop = 1.0;
+    double lam_start = 0.0;  // 0: 1 / G_tot
+    int sched = TEMPEST_SCHED_FULL_WALK;
+    cudaStream_t stream = nullptr;
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*release_fn)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    size_t budget = 0;
+    size_t in_use = 0;
+    int device = 0;
+    int num_sms = 1;
+
+    // host mirror of the live state's sizes and counters
+    int64_t m = 0;      // live edges
+    int64_t G = 0;      // timestamp groups
+    int64_t N = 0;      // node slots (1 + max id seen)
+    int64_t M = 0;      // node view entries
+    int64_t Gn = 0;     // node groups
+    int64_t dropped = 0, evicted = 0, seq_next = 0;
+    int has_cutoff = 0;
+    int64_t cutoff = 0;
+
+    // device state: the store (double buffered for merges) and both views
+    tw::DBuf st_src[2], st_dst[2], st_ts[2];
+    int cur = 0;
+    tw::DBuf ts_goff;  // int32 [G+1]
+    tw::DBuf ent;      // Entry [M]
+    tw::DBuf ngo;      // int32 [Gn+1] node group start offsets
+    tw::DBuf ngts;     // int64 [Gn]   node group timestamps
+    tw::DBuf gidx;     // int32 [N+1]  first group of each node
+
+    // scratch
+    tw::DBuf b_src, b_dst, b_ts;     // batch staged from host
+    tw::DBuf sb_src, sb_dst, sb_ts;  // batch sorted by timestamp
+    tw::DBuf sk64[2], sk32[2], sv[2];
+    tw::DBuf hist, partials;
+    tw::DBuf seg_node, seg_g, gcnt;
+    tw::DBuf dstat;       // IngestScratch
+    tw::DBuf wcnt;        // WalkCounters
+    tw::DBuf out_stage;   // device staging of host walk outputs
+    tw::DBuf in_stage;    // device staging of host walk inputs
+    tw::DBuf exp_stage;   // export staging
+    void *hstat = nullptr;     // pinned host mirror of IngestScratch / counters
+
+    tempest_walk_stats last_ws{};
+    int64_t pending_launches = 0;
+    std::string err;
+};
+
+namespace tw {
+
+// allocation helpers (capi.cu)
+int ensure(tempest_t *h, DBuf &b, size_t bytes, bool headroom = false);
+void release(tempest_t *h, DBuf &b);
+int fail(tempest_t *h, int code, const char *fmt, ...);
+int cuda_check(tempest_t *h, cudaError_t e, const char *what);
+bool is_device_ptr(const void *p);
+
+// ingest.cu
+int ingest_batch(tempest_t *h, const int32_t *src, const int32_t *dst, const int64_t *ts, int64_t n,
+                 tempest_ingest_stats *stats);
+// fills node_off (int32 [N+1]) from the group arrays
+void launch_node_off(tempest_t *h, int32_t *node_off);
+// fills node_order (int32 [M]) from the entries
+void launch_node_order(tempest_t *h, int32_t *node_order);
+
+// walks.cu
+struct WalkRequest {
+    int64_t n_walks;
+    int32_t cap;               // row stride
+    int32_t max_len;           // when len_arr == nullptr
+    const int32_t *len_arr;    // device, nullable
+    int bias;                  // when bias_arr == nullptr
+    const uint8_t *bias_arr;   // device, nullable
+    int start_policy;
+    uint64_t seed;
+    int32_t *node;             // device
+    int64_t *ts;               // device
+    int32_t *len;              // device
+};
+int walks_run(tempest_t *h, const WalkRequest &rq);
+
+}  // namespace tw

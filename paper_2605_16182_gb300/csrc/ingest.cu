@@ -1,0 +1,590 @@
+// ingest.cu -- streaming ingestion, window eviction and the dual index
+// (Tempest Sec. 2.3 and 2.6).
+//
+// Per batch:
+//   1. one pass over the batch: timestamp range, largest id, negative ids,
+//      late edges (older than the cut-off in force), whether it is sorted;
+//   2. a stable radix sort of the batch on timestamp (skipped when the batch
+//      arrived sorted); late edges are then a prefix and are skipped;
+//   3. the new cut-off is found without materialising the merge (a merge-path
+//      search gives the timestamp at any rank of the merged order), and the
+//      first kept element of the store and of the batch by binary search;
+//   4. the kept store suffix and the kept batch are merged into the other
+//      store buffer (two copies when the batch starts no earlier than the
+//      store ends, a merge-path merge otherwise);
+//   5. timestamp-grouped view: compaction of the run starts of equal ts;
+//   6. node view: stable radix sort of the store's (node, slot) pairs by
+//      node, one 16-byte entry per slot, then one compaction that emits the
+//      (node, ts) group starts and the node segment starts, and an exclusive
+//      scan of per-node group counts that gives each node's first group.
+#include <stdio.h>
+
+#include "engine.cuh"
+#include "prims.cuh"
+
+namespace tw {
+
+// ---------------------------------------------------------------------------
+// batch statistics
+// ---------------------------------------------------------------------------
+__global__ void k_batch_stats(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                              const int64_t *__restrict__ ts, int64_t n, int has_cut, long long cut,
+                              IngestScratch *o)
+{
+    long long tmin = LLONG_MAX, tmax = LLONG_MIN;
+    int maxid = 0, neg = 0;
+    unsigned long long late = 0, uns = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[i], b = dst[i];
+        const long long t = ts[i];
+        tmin = min(tmin, t);
+        tmax = max(tmax, t);
+        maxid = max(maxid, max(a, b));
+        neg |= (a < 0) | (b < 0);
+        late += (has_cut && t < cut) ? 1ull : 0ull;
+        if (i > 0 && ts[i - 1] > t) uns++;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, d));
+        tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, d));
+        maxid = max(maxid, __shfl_xor_sync(0xffffffffu, maxid, d));
+        neg |= __shfl_xor_sync(0xffffffffu, neg, d);
+        late += __shfl_xor_sync(0xffffffffu, late, d);
+        uns += __shfl_xor_sync(0xffffffffu, uns, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&o->ts_min, tmin);
+        atomicMax(&o->ts_max, tmax);
+        atomicMax(&o->max_id, maxid);
+        if (neg) atomicOr(&o->neg_id, 1);
+        if (late) atomicAdd(&o->late, late);
+        if (uns) atomicAdd(&o->unsorted, uns);
+    }
+}
+
+__global__ void k_init_scratch(IngestScratch *o)
+{
+    o->ts_min = LLONG_MAX;
+    o->ts_max = LLONG_MIN;
+    o->max_id = 0;
+    o->neg_id = 0;
+    o->late = 0;
+    o->unsorted = 0;
+    o->cut = 0;
+    o->has_cut = 0;
+    o->i0 = 0;
+    o->j0 = 0;
+    o->kept_batch_min_ts = 0;
+    o->store_last_ts = 0;
+}
+
+struct TsKeyLoader {
+    const int64_t *ts;
+    long long tmin;
+    __device__ __forceinline__ unsigned long long key(int64_t i) const
+    {
+        return (unsigned long long)ts[i] - (unsigned long long)tmin;
+    }
+    __device__ __forceinline__ uint32_t val(int64_t i) const { return (uint32_t)i; }
+};
+
+__global__ void k_gather_batch(const uint32_t *__restrict__ perm, const int32_t *__restrict__ src,
+                               const int32_t *__restrict__ dst, const int64_t *__restrict__ ts, int64_t n,
+                               int32_t *osrc, int32_t *odst, int64_t *ots)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = perm[i];
+        osrc[i] = src[p];
+        odst[i] = dst[p];
+        ots[i] = ts[p];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// merge-path helpers.  Merge order: a (the store) before b (the batch) on
+// equal timestamps, since every batch edge arrived after every store edge.
+// Returns the number of a-elements among the first r merged elements.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t merge_split(const int64_t *a, int64_t na, const int64_t *b, int64_t nb,
+                                               int64_t r)
+{
+    int64_t lo = r > nb ? r - nb : 0;
+    int64_t hi = r < na ? r : na;
+    while (lo < hi) {
+        const int64_t i = lo + ((hi - lo) >> 1);
+        const int64_t j = r - i;  // j >= 1 here since i < hi <= r ... when j == 0 the split is found
+        // does a[i] come after b[j-1]?
+        if (j == 0 || b[j - 1] < a[i]) hi = i;
+        else lo = i + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t lower_bound_i64(const int64_t *a, int64_t n, int64_t v)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One thread: new cut-off and the first kept element of store / batch.
+// mode: 0 none, 1 duration (param = Delta), 2 count (param = W).
+__global__ void k_window(int mode, long long param, const int64_t *old_ts, int64_t m_old,
+                         const int64_t *bts, int64_t nb, int has_old, long long cut_old, IngestScratch *o)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int has = has_old;
+    long long cut = cut_old;
+    if (mode == 1 && m_old + nb > 0) {
+        long long tmax = LLONG_MIN;
+        if (m_old > 0) tmax = old_ts[m_old - 1];
+        if (nb > 0) tmax = max(tmax, (long long)bts[nb - 1]);
+        const long long c = (tmax < LLONG_MIN + param) ? LLONG_MIN : tmax - param;
+        if (!has || c > cut) cut = c;
+        has = 1;
+    } else if (mode == 2 && m_old + nb > param) {
+        const int64_t r = m_old + nb - param;  // rank of the W-th newest element
+        const int64_t i = merge_split(old_ts, m_old, bts, nb, r);
+        const int64_t j = r - i;
+        long long c;
+        if (j >= nb || (i < m_old && old_ts[i] <= bts[j])) c = old_ts[i];
+        else c = bts[j];
+        if (!has || c > cut) cut = c;
+        has = 1;
+    }
+    int64_t i0 = 0, j0 = 0;
+    if (has) {
+        i0 = lower_bound_i64(old_ts, m_old, cut);
+        j0 = lower_bound_i64(bts, nb, cut);
+    }
+    o->cut = cut;
+    o->has_cut = has;
+    o->i0 = i0;
+    o->j0 = j0;
+    o->kept_batch_min_ts = (j0 < nb) ? bts[j0] : LLONG_MAX;
+    o->store_last_ts = (m_old > 0) ? old_ts[m_old - 1] : LLONG_MIN;
+}
+
+// General merge of two (ts)-sorted SoA runs; each thread produces MERGE_K
+// consecutive outputs.
+constexpr int MERGE_K = 8;
+__global__ void k_merge(const int32_t *__restrict__ as, const int32_t *__restrict__ ad,
+                        const int64_t *__restrict__ at, int64_t na, const int32_t *__restrict__ bs,
+                        const int32_t *__restrict__ bd, const int64_t *__restrict__ bt, int64_t nb,
+                        int32_t *os, int32_t *od, int64_t *ot)
+{
+    const int64_t n = na + nb;
+    const int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * MERGE_K;
+    if (r0 >= n) return;
+    int64_t i = merge_split(at, na, bt, nb, r0);
+    int64_t j = r0 - i;
+    const int64_t r1 = min(n, r0 + MERGE_K);
+    for (int64_t r = r0; r < r1; r++) {
+        if (j >= nb || (i < na && at[i] <= bt[j])) {
+            os[r] = as[i];
+            od[r] = ad[i];
+            ot[r] = at[i];
+            i++;
+        } else {
+            os[r] = bs[j];
+            od[r] = bd[j];
+            ot[r] = bt[j];
+            j++;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// views
+// ---------------------------------------------------------------------------
+struct TsGroupOp {
+    const int64_t *ts;
+    int32_t *goff;
+    __device__ __forceinline__ uint64_t value(int64_t i) const
+    {
+        return (i == 0 || ts[i] != ts[i - 1]) ? 1u : 0u;
+    }
+    __device__ __forceinline__ void emit(int64_t i, uint64_t v, uint64_t ex) const
+    {
+        if (v) goff[ex] = (int32_t)i;
+    }
+};
+
+struct StoreKeyLoader {
+    const int32_t *src, *dst;
+    int directed;
+    __device__ __forceinline__ uint32_t key(int64_t i) const
+    {
+        if (directed) return (uint32_t)src[i];
+        return (uint32_t)((i & 1) ? dst[i >> 1] : src[i >> 1]);
+    }
+    __device__ __forceinline__ uint32_t val(int64_t i) const { return (uint32_t)i; }
+};
+
+__global__ void k_node_entries(const uint32_t *__restrict__ slots, const int32_t *__restrict__ src,
+                               const int32_t *__restrict__ dst, const int64_t *__restrict__ ts, int directed,
+                               int64_t M, Entry *E)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t slot = slots ? slots[i] : (uint32_t)i;
+        const int64_t pos = directed ? (int64_t)slot : (int64_t)(slot >> 1);
+        const bool side = !directed && (slot & 1u);
+        Entry e;
+        e.ts = ts[pos];
+        e.other = side ? src[pos] : dst[pos];
+        e.slot = (int32_t)slot;
+        E[i] = e;
+    }
+}
+
+// Packed counter: high 32 bits count node segments, low 32 bits count
+// (node, ts) groups.
+struct NodeGroupOp {
+    const uint32_t *keys;  // sorted node keys (nullptr: every key is 0)
+    const Entry *E;
+    int32_t *ngo;
+    int64_t *ngts;
+    int32_t *seg_node;
+    int32_t *seg_g;
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return keys ? keys[i] : 0u; }
+    __device__ __forceinline__ uint64_t value(int64_t i) const
+    {
+        if (i == 0) return (1ull << 32) | 1ull;
+        const bool seg = key(i) != key(i - 1);
+        const bool grp = seg || E[i].ts != E[i - 1].ts;
+        return ((uint64_t)seg << 32) | (uint64_t)grp;
+    }
+    __device__ __forceinline__ void emit(int64_t i, uint64_t v, uint64_t ex) const
+    {
+        if (v & 1ull) {
+            const uint32_t g = (uint32_t)ex;
+            ngo[g] = (int32_t)i;
+            ngts[g] = E[i].ts;
+            if (v >> 32) {
+                const uint32_t j = (uint32_t)(ex >> 32);
+                seg_node[j] = (int32_t)key(i);
+                seg_g[j] = (int32_t)g;
+            }
+        }
+    }
+};
+
+__global__ void k_seg_counts(const int32_t *__restrict__ seg_node, const int32_t *__restrict__ seg_g,
+                             int64_t S, int64_t Gn, int32_t *gcnt)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < S;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t next = (j + 1 < S) ? seg_g[j + 1] : Gn;
+        gcnt[seg_node[j]] = (int32_t)(next - seg_g[j]);
+    }
+}
+
+struct GidxOp {
+    const int32_t *gcnt;
+    int64_t N;
+    int32_t *gidx;
+    __device__ __forceinline__ uint64_t value(int64_t v) const { return v < N ? (uint64_t)gcnt[v] : 0ull; }
+    __device__ __forceinline__ void emit(int64_t v, uint64_t, uint64_t ex) const { gidx[v] = (int32_t)ex; }
+};
+
+__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
+
+__global__ void k_node_off(const int32_t *__restrict__ gidx, const int32_t *__restrict__ ngo, int64_t N,
+                           int32_t *node_off)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= N;
+         v += (int64_t)gridDim.x * blockDim.x)
+        node_off[v] = ngo[gidx[v]];
+}
+
+__global__ void k_node_order(const Entry *__restrict__ E, int64_t M, int32_t *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = E[i].slot;
+}
+
+static unsigned grid_for(tempest_t *h, int64_t n, int threads = 256)
+{
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)h->num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+void launch_node_off(tempest_t *h, int32_t *node_off)
+{
+    k_node_off<<<grid_for(h, h->N + 1), 256, 0, h->stream>>>(h->gidx.as<int32_t>(), h->ngo.as<int32_t>(), h->N,
+                                                           node_off);
+}
+
+void launch_node_order(tempest_t *h, int32_t *node_order)
+{
+    if (h->M > 0) k_node_order<<<grid_for(h, h->M), 256, 0, h->stream>>>(h->ent.as<Entry>(), h->M, node_order);
+}
+
+static int bits_for(uint64_t maxval)
+{
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) b++;
+    return b;
+}
+
+// Rebuild both views over the store in buffer h->cur with h->m live edges.
+static int rebuild_views(tempest_t *h)
+{
+    cudaStream_t st = h->stream;
+    const int64_t m = h->m;
+    const int32_t *src = h->st_src[h->cur].as<int32_t>();
+    const int32_t *dst = h->st_dst[h->cur].as<int32_t>();
+    const int64_t *ts = h->st_ts[h->cur].as<int64_t>();
+    uint64_t *hpart = static_cast<uint64_t *>(h->hstat);
+    int rc;
+
+    // timestamp-grouped view
+    if ((rc = ensure(h, h->ts_goff, sizeof(int32_t) * (size_t)(m + 1), true))) return rc;
+    {
+        TsGroupOp op{ts, h->ts_goff.as<int32_t>()};
+        const int nb = scan_launch(op, m, h->partials.as<uint64_t>(), st);
+        cudaMemcpyAsync(hpart, h->partials.as<uint64_t>() + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+        h->pending_launches += 3;
+    }
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ts view"))) return rc;
+    h->G = (int64_t)hpart[0];
+    k_set_i32<<<1, 1, 0, st>>>(h->ts_goff.as<int32_t>() + h->G, (int32_t)m);
+    h->pending_launches++;
+
+    // node-and-timestamp-grouped view
+    const int64_t M = h->directed ? m : 2 * m;
+    const int64_t N = h->N;
+    if ((rc = ensure(h, h->ent, sizeof(Entry) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->ngo, sizeof(int32_t) * (size_t)(M + 1), true))) return rc;
+    if ((rc = ensure(h, h->ngts, sizeof(int64_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->gidx, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
+    if ((rc = ensure(h, h->gcnt, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
+    if ((rc = ensure(h, h->seg_node, sizeof(int32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->seg_g, sizeof(int32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->sk32[0], sizeof(uint32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->sk32[1], sizeof(uint32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->sv[0], sizeof(uint32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->sv[1], sizeof(uint32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+
+    const uint32_t *keys = nullptr;
+    const uint32_t *slots = nullptr;
+    if (M > 0) {
+        StoreKeyLoader ld{src, dst, h->directed};
+        uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
+        uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
+        int launches = 0;
+        const int r = radix_sort_launch<uint32_t>(ld, M, bits_for((uint64_t)(N > 0 ? N - 1 : 0)), kb, vb,
+                                                  h->hist.as<uint32_t>(), st, &launches);
+        h->pending_launches += launches;
+        if (r >= 0) {
+            keys = kb[r];
+            slots = vb[r];
+        }
+        k_node_entries<<<grid_for(h, M), 256, 0, st>>>(slots, src, dst, ts, h->directed, M, h->ent.as<Entry>());
+        h->pending_launches++;
+    }
+    {
+        NodeGroupOp op{keys, h->ent.as<Entry>(), h->ngo.as<int32_t>(), h->ngts.as<int64_t>(),
+                       h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>()};
+        const int nb = scan_launch(op, M, h->partials.as<uint64_t>(), st);
+        cudaMemcpyAsync(hpart, h->partials.as<uint64_t>() + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+        h->pending_launches += 3;
+    }
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view"))) return rc;
+    const uint64_t tot = hpart[0];
+    const int64_t Gn = M > 0 ? (int64_t)(uint32_t)tot : 0;
+    const int64_t S = M > 0 ? (int64_t)(tot >> 32) : 0;
+    h->Gn = Gn;
+    h->M = M;
+    k_set_i32<<<1, 1, 0, st>>>(h->ngo.as<int32_t>() + Gn, (int32_t)M);
+    cudaMemsetAsync(h->gcnt.as<int32_t>(), 0, sizeof(int32_t) * (size_t)(N + 1), st);
+    if (S > 0)
+        k_seg_counts<<<grid_for(h, S), 256, 0, st>>>(h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>(), S, Gn,
+                                                     h->gcnt.as<int32_t>());
+    {
+        GidxOp op{h->gcnt.as<int32_t>(), N, h->gidx.as<int32_t>()};
+        scan_launch(op, N + 1, h->partials.as<uint64_t>(), st);
+    }
+    h->pending_launches += 5;
+    return cuda_check(h, cudaGetLastError(), "rebuild views");
+}
+
+int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in, int64_t n,
+                 tempest_ingest_stats *stats)
+{
+    cudaStream_t st = h->stream;
+    int rc;
+    if (n < 0) return fail(h, TEMPEST_EINVAL, "tempest_ingest: n = %lld < 0", (long long)n);
+    if (n > 0 && (!src_in || !dst_in || !ts_in)) return fail(h, TEMPEST_EINVAL, "tempest_ingest: NULL array");
+    if (n >= (int64_t)INT32_MAX) return fail(h, TEMPEST_EINVAL, "tempest_ingest: batch of %lld edges too large",
+                                             (long long)n);
+    h->pending_launches = 0;
+    if ((rc = ensure(h, h->dstat, sizeof(IngestScratch)))) return rc;
+    if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
+    if ((rc = ensure(h, h->hist, sizeof(uint32_t) * ((size_t)RADIX * SORT_MAX_BLOCKS + 1)))) return rc;
+    IngestScratch *ds = h->dstat.as<IngestScratch>();
+    IngestScratch *hs = static_cast<IngestScratch *>(h->hstat);
+
+    // stage host inputs
+    const int32_t *src = src_in;
+    const int32_t *dst = dst_in;
+    const int64_t *ts = ts_in;
+    if (n > 0) {
+        if (!is_device_ptr(src_in)) {
+            if ((rc = ensure(h, h->b_src, sizeof(int32_t) * (size_t)n, true))) return rc;
+            cudaMemcpyAsync(h->b_src.p, src_in, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+            src = h->b_src.as<int32_t>();
+        }
+        if (!is_device_ptr(dst_in)) {
+            if ((rc = ensure(h, h->b_dst, sizeof(int32_t) * (size_t)n, true))) return rc;
+            cudaMemcpyAsync(h->b_dst.p, dst_in, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+            dst = h->b_dst.as<int32_t>();
+        }
+        if (!is_device_ptr(ts_in)) {
+            if ((rc = ensure(h, h->b_ts, sizeof(int64_t) * (size_t)n, true))) return rc;
+            cudaMemcpyAsync(h->b_ts.p, ts_in, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+            ts = h->b_ts.as<int64_t>();
+        }
+    }
+
+    // 1. batch statistics
+    k_init_scratch<<<1, 1, 0, st>>>(ds);
+    if (n > 0)
+        k_batch_stats<<<grid_for(h, n), 256, 0, st>>>(src, dst, ts, n, h->has_cutoff, h->cutoff, ds);
+    cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
+    h->pending_launches += 2;
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "batch stats"))) return rc;
+    if (hs->neg_id) return fail(h, TEMPEST_EINVAL, "tempest_ingest: negative node id");
+    const int64_t N_new = (n > 0 && (int64_t)hs->max_id + 1 > h->N) ? (int64_t)hs->max_id + 1 : h->N;
+    const int64_t late = (int64_t)hs->late;
+    const bool sorted = hs->unsorted == 0;
+    const long long bmin = hs->ts_min;
+    const uint64_t span = (n > 0) ? (uint64_t)hs->ts_max - (uint64_t)hs->ts_min : 0;
+
+    // capacity of the next state (checked before anything changes)
+    const int64_t m_max = h->m + (n - late);
+    const int64_t M_max = h->directed ? m_max : 2 * m_max;
+    if (M_max >= (int64_t)INT32_MAX - 1)
+        return fail(h, TEMPEST_ENOMEM, "tempest_ingest: %lld index entries exceed the int32 index range",
+                    (long long)M_max);
+
+    // 2. sort the batch by timestamp (stable), late edges become a prefix
+    const int32_t *bs = src;
+    const int32_t *bd = dst;
+    const int64_t *bt = ts;
+    if (n > 0 && !sorted) {
+        if ((rc = ensure(h, h->sk64[0], sizeof(uint64_t) * (size_t)n, true))) return rc;
+        if ((rc = ensure(h, h->sk64[1], sizeof(uint64_t) * (size_t)n, true))) return rc;
+        if ((rc = ensure(h, h->sv[0], sizeof(uint32_t) * (size_t)n, true))) return rc;
+        if ((rc = ensure(h, h->sv[1], sizeof(uint32_t) * (size_t)n, true))) return rc;
+        if ((rc = ensure(h, h->sb_src, sizeof(int32_t) * (size_t)n, true))) return rc;
+        if ((rc = ensure(h, h->sb_dst, sizeof(int32_t) * (size_t)n, true))) return rc;
+        if ((rc = ensure(h, h->sb_ts, sizeof(int64_t) * (size_t)n, true))) return rc;
+        TsKeyLoader ld{ts, bmin};
+        unsigned long long *kb[2] = {h->sk64[0].as<unsigned long long>(), h->sk64[1].as<unsigned long long>()};
+        uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
+        int launches = 0;
+        const int r = radix_sort_launch<unsigned long long>(ld, n, bits_for(span), kb, vb, h->hist.as<uint32_t>(),
+                                                            st, &launches);
+        h->pending_launches += launches;
+        // span > 0 whenever the batch is unsorted, so a pass ran
+        k_gather_batch<<<grid_for(h, n), 256, 0, st>>>(vb[r], src, dst, ts, n, h->sb_src.as<int32_t>(),
+                                                       h->sb_dst.as<int32_t>(), h->sb_ts.as<int64_t>());
+        h->pending_launches++;
+        bs = h->sb_src.as<int32_t>();
+        bd = h->sb_dst.as<int32_t>();
+        bt = h->sb_ts.as<int64_t>();
+    }
+    bs += late;
+    bd += late;
+    bt += late;
+    const int64_t nb = n - late;
+
+    // 3. window cut-off
+    const int mode = h->window > 0 ? 1 : (h->window < 0 ? 2 : 0);
+    const long long param = h->window > 0 ? h->window : -h->window;
+    const int64_t *old_ts = h->st_ts[h->cur].as<int64_t>();
+    k_window<<<1, 32, 0, st>>>(mode, param, old_ts, h->m, bt, nb, h->has_cutoff, h->cutoff, ds);
+    cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
+    h->pending_launches++;
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "window"))) return rc;
+    const int64_t i0 = hs->i0, j0 = hs->j0;
+    const int64_t na = h->m - i0, nbk = nb - j0;
+    const int64_t m_new = na + nbk;
+
+    // 4. merge into the other store buffer
+    const int nxt = h->cur ^ 1;
+    if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
+    if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
+    if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
+    {
+        const int32_t *as = h->st_src[h->cur].as<int32_t>() + i0;
+        const int32_t *ad = h->st_dst[h->cur].as<int32_t>() + i0;
+        const int64_t *at = h->st_ts[h->cur].as<int64_t>() + i0;
+        int32_t *os = h->st_src[nxt].as<int32_t>();
+        int32_t *od = h->st_dst[nxt].as<int32_t>();
+        int64_t *ot = h->st_ts[nxt].as<int64_t>();
+        const bool append = na == 0 || nbk == 0 || hs->store_last_ts <= hs->kept_batch_min_ts;
+        if (append) {
+            if (na > 0) {
+                cudaMemcpyAsync(os, as, sizeof(int32_t) * (size_t)na, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(od, ad, sizeof(int32_t) * (size_t)na, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(ot, at, sizeof(int64_t) * (size_t)na, cudaMemcpyDeviceToDevice, st);
+            }
+            if (nbk > 0) {
+                cudaMemcpyAsync(os + na, bs + j0, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(od + na, bd + j0, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(ot + na, bt + j0, sizeof(int64_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
+            }
+        } else {
+            const int64_t threads = (m_new + MERGE_K - 1) / MERGE_K;
+            k_merge<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(as, ad, at, na, bs + j0, bd + j0, bt + j0, nbk,
+                                                                       os, od, ot);
+            h->pending_launches++;
+        }
+    }
+    if ((rc = cuda_check(h, cudaGetLastError(), "merge"))) return rc;
+
+    // commit the new store and counters
+    h->cur = nxt;
+    h->m = m_new;
+    h->N = N_new;
+    h->seq_next += n;
+    h->dropped += late;
+    h->evicted += i0 + j0;
+    const int64_t evicted_now = i0 + j0;
+    h->has_cutoff = hs->has_cut;
+    h->cutoff = hs->cut;
+
+    // 5-6. views
+    if ((rc = rebuild_views(h))) return rc;
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ingest"))) return rc;
+
+    if (stats) {
+        stats->n_in = n;
+        stats->n_dropped_late = late;
+        stats->n_evicted = evicted_now;
+        stats->n_live = h->m;
+        stats->n_ts_groups = h->G;
+        stats->n_node_groups = h->Gn;
+        stats->n_nodes = h->N;
+        stats->cutoff = h->cutoff;
+        stats->has_cutoff = h->has_cutoff;
+        stats->sorted_input = sorted ? 1 : 0;
+    }
+    return TEMPEST_OK;
+}
+
+}  // namespace tw

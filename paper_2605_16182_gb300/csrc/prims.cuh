@@ -1,0 +1,411 @@
+// prims.cuh -- device building blocks of the engine: the counter-based RNG,
+// the closed-form samplers, a two-level scan / stream compaction driven by
+// functors, and a stable LSD radix sort of (key, u32 value) pairs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tw {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11).  Each walk owns the counter space
+// (hop, 0, walk_lo, walk_hi) under key = seed, so a draw depends only on
+// (seed, walk, hop) and never on how walks are scheduled.
+// ---------------------------------------------------------------------------
+struct Rand4 {
+    uint32_t r0, r1, r2, r3;
+};
+
+__device__ __forceinline__ Rand4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int i = 0; i < 10; i++) {
+        const uint32_t a0 = c0, a2 = c2;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, a0), lo0 = 0xD2511F53u * a0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, a2), lo1 = 0xCD9E8D57u * a2;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return Rand4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ Rand4 walk_rand(uint64_t seed, uint64_t walk, uint32_t hop)
+{
+    return philox4x32_10(hop, 0u, (uint32_t)walk, (uint32_t)(walk >> 32), (uint32_t)seed,
+                         (uint32_t)(seed >> 32));
+}
+
+// 53-bit uniform in [0, 1): exact in double.
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo)
+{
+    const uint64_t b = ((((uint64_t)hi) << 32) | lo) >> 11;
+    return __dmul_rn(__ull2double_rn(b), 1.1102230246251565404236316680908203125e-16);
+}
+
+// ---------------------------------------------------------------------------
+// Closed-form inverse-CDF samplers over an index i in [0, n) (Sec. 2.5).
+// Every step is an explicitly rounded IEEE operation so that no multiply-add
+// is contracted: the result is the same as a left-to-right double evaluation
+// on any IEEE machine, except for the last-place behaviour of exp / log.
+// ---------------------------------------------------------------------------
+enum : int { BIAS_UNIFORM = 0, BIAS_LINEAR = 1, BIAS_EXP = 2 };
+
+__device__ __forceinline__ double sampler_x(double u, int64_t n, int bias, double lambda)
+{
+    const double nd = __ll2double_rn(n);
+    if (bias == BIAS_UNIFORM) return __dmul_rn(u, nd);  // Eq. 1
+    if (bias == BIAS_LINEAR) {                          // Eq. 2, weight i+1
+        double t = __dmul_rn(4.0, u);
+        t = __dmul_rn(t, nd);
+        t = __dmul_rn(t, __dadd_rn(nd, 1.0));
+        t = __dadd_rn(1.0, t);
+        return __dmul_rn(__dadd_rn(__dsqrt_rn(t), -1.0), 0.5);
+    }
+    // weight exp(lambda*i): x = n + log(u + (1-u) exp(-lambda n)) / lambda
+    const double e = exp(__dmul_rn(-lambda, nd));
+    const double s = __dadd_rn(u, __dmul_rn(__dadd_rn(1.0, -u), e));
+    return __dadd_rn(nd, __ddiv_rn(log(s), lambda));
+}
+
+__device__ __forceinline__ int64_t sampler_index(double u, int64_t n, int bias, double lambda)
+{
+    const double x = sampler_x(u, n, bias, lambda);
+    if (!(x >= 0.0)) return 0;  // NaN, -inf, negative
+    const double f = floor(x);
+    if (f >= __ll2double_rn(n - 1)) return n - 1;
+    return (int64_t)f;
+}
+
+__device__ __forceinline__ int64_t uniform_index(double u, int64_t n)
+{
+    return sampler_index(u, n, BIAS_UNIFORM, 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// warp / block helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// Exclusive block scan; blockDim.x must be a multiple of 32 and <= 1024.
+// `sh` is caller-provided shared scratch of 33 elements.  Returns the
+// exclusive prefix of v; `total` receives the block total.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *sh, T &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const T inc = warp_incl_scan(v);
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const T t = lane < nw ? sh[lane] : T(0);
+        const T ti = warp_incl_scan(t);
+        if (lane < nw) sh[lane] = ti - t;
+        if (lane == 31) sh[32] = ti;
+    }
+    __syncthreads();
+    const T res = sh[wid] + inc - v;
+    total = sh[32];
+    __syncthreads();
+    return res;
+}
+
+// ---------------------------------------------------------------------------
+// Two-level scan / compaction.
+// Op supplies  __device__ uint64_t value(int64_t i) const
+//              __device__ void emit(int64_t i, uint64_t v, uint64_t excl) const
+// Phase 1 sums value() over each block's contiguous range, phase 2 scans the
+// block sums (one block), phase 3 rescans each range and calls emit() with
+// the exclusive prefix.  value() is evaluated twice per element.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+constexpr int SCAN_MAX_BLOCKS = 2048;
+
+template <class Op>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Op op, int64_t n, int64_t per_blk,
+                                                              uint64_t *partials)
+{
+    __shared__ uint64_t wt[32];
+    const int64_t b0 = (int64_t)blockIdx.x * per_blk;
+    const int64_t b1 = min(n, b0 + per_blk);
+    uint64_t s = 0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += op.value(i);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) wt[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += wt[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of partials[0..nb) in place (one block of 1024 threads);
+// partials[nb] receives the total.
+__global__ void k_scan_partials(uint64_t *partials, int nb);
+
+template <class Op>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_emit(Op op, int64_t n, int64_t per_blk,
+                                                            const uint64_t *partials)
+{
+    __shared__ uint64_t wt[33];
+    const int64_t b0 = (int64_t)blockIdx.x * per_blk;
+    const int64_t b1 = min(n, b0 + per_blk);
+    uint64_t carry = partials[blockIdx.x];
+    for (int64_t c = b0; c < b1; c += SCAN_CHUNK) {
+        const int64_t i0 = c + (int64_t)threadIdx.x * SCAN_ITEMS;
+        uint64_t v[SCAN_ITEMS];
+        uint64_t s = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            const int64_t i = i0 + k;
+            v[k] = (i < b1) ? op.value(i) : 0;
+            s += v[k];
+        }
+        uint64_t tot;
+        uint64_t ex = block_excl_scan<uint64_t>(s, wt, tot);
+        ex += carry;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            const int64_t i = i0 + k;
+            if (i < b1) op.emit(i, v[k], ex);
+            ex += v[k];
+        }
+        carry += tot;
+    }
+}
+
+// Host driver.  partials must hold SCAN_MAX_BLOCKS + 1 entries; the total
+// ends in partials[nb] where nb is returned.
+template <class Op>
+int scan_launch(const Op &op, int64_t n, uint64_t *partials, cudaStream_t st)
+{
+    if (n <= 0) {
+        cudaMemsetAsync(partials, 0, sizeof(uint64_t), st);
+        return 0;
+    }
+    int64_t nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (nb > SCAN_MAX_BLOCKS) nb = SCAN_MAX_BLOCKS;
+    int64_t per = (n + nb - 1) / nb;
+    per = (per + SCAN_CHUNK - 1) / SCAN_CHUNK * SCAN_CHUNK;
+    nb = (n + per - 1) / per;
+    k_scan_reduce<Op><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(op, n, per, partials);
+    k_scan_partials<<<1, 1024, 0, st>>>(partials, (int)nb);
+    k_scan_emit<Op><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(op, n, per, partials);
+    return (int)nb;
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (key, value) pairs, 8-bit digits.
+// A Loader supplies the input of the first pass:
+//   __device__ K key(int64_t i) const;  __device__ uint32_t val(int64_t i) const;
+// later passes read the previous pass's output.  Each block owns a
+// contiguous range of tiles; within a tile, warps rank their elements with
+// match_any, the block orders them by digit in shared memory and writes out
+// runs of equal digits to consecutive addresses.
+// ---------------------------------------------------------------------------
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int SORT_MAX_BLOCKS = 1024;
+
+template <typename K>
+struct ArrayLoader {
+    const K *k;
+    const uint32_t *v;
+    __device__ __forceinline__ K key(int64_t i) const { return k[i]; }
+    __device__ __forceinline__ uint32_t val(int64_t i) const { return v[i]; }
+};
+
+template <typename K, class L>
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(L ld, int64_t n, int64_t per_blk,
+                                                             int shift, uint32_t *hist, int nblk)
+{
+    __shared__ uint32_t h[SORT_WARPS][RADIX];
+    for (int i = threadIdx.x; i < SORT_WARPS * RADIX; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b0 = (int64_t)blockIdx.x * per_blk;
+    const int64_t b1 = min(n, b0 + per_blk);
+    for (int64_t base = b0; base < b1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool ok = i < b1;
+        const uint32_t d = ok ? (uint32_t)((ld.key(i) >> shift) & (RADIX - 1)) : 0xffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        if (ok && lane == leader) h[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < SORT_WARPS; k++) s += h[k][d];
+        hist[(int64_t)d * nblk + blockIdx.x] = s;
+    }
+}
+
+// exclusive scan of n u32 (one block of 1024 threads)
+__global__ void k_scan_u32_small(uint32_t *a, int64_t n);
+
+template <typename K, class L>
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(L ld, K *kout, uint32_t *vout,
+                                                                int64_t n, int64_t per_blk, int shift,
+                                                                const uint32_t *offs, int nblk)
+{
+    __shared__ uint32_t run_off[RADIX];
+    __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
+    __shared__ uint32_t dstart[RADIX];
+    __shared__ uint32_t dcnt[RADIX];
+    __shared__ K sk[SORT_TILE];
+    __shared__ uint32_t sv[SORT_TILE];
+    __shared__ uint32_t wt[33];
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t b0 = (int64_t)blockIdx.x * per_blk;
+    const int64_t b1 = min(n, b0 + per_blk);
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) run_off[d] = offs[(int64_t)d * nblk + blockIdx.x];
+
+    for (int64_t t0 = b0; t0 < b1; t0 += SORT_TILE) {
+        for (int i = threadIdx.x; i < SORT_WARPS * RADIX; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        K kk[SORT_ITEMS];
+        uint32_t vv[SORT_ITEMS];
+        uint32_t dd[SORT_ITEMS];
+        uint32_t rk[SORT_ITEMS];
+        const int64_t chunk = t0 + (int64_t)w * 32 * SORT_ITEMS;
+#pragma unroll
+        for (int r = 0; r < SORT_ITEMS; r++) {
+            const int64_t i = chunk + r * 32 + lane;
+            const bool ok = i < b1;
+            if (ok) {
+                kk[r] = ld.key(i);
+                vv[r] = ld.val(i);
+                dd[r] = (uint32_t)((kk[r] >> shift) & (RADIX - 1));
+            } else {
+                kk[r] = K(0);
+                vv[r] = 0;
+                dd[r] = 0xffffu;
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, dd[r]);
+            const uint32_t pre = ok ? wcnt[w][dd[r]] : 0u;
+            __syncwarp();
+            if (ok && (peers & lt) == 0) wcnt[w][dd[r]] = pre + __popc(peers);
+            __syncwarp();
+            rk[r] = pre + __popc(peers & lt);
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over warps and the tile count
+        for (int d = threadIdx.x; d < RADIX; d += blockDim.x) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int k = 0; k < SORT_WARPS; k++) {
+                const uint32_t c = wcnt[k][d];
+                wcnt[k][d] = s;
+                s += c;
+            }
+            dcnt[d] = s;
+        }
+        __syncthreads();
+        {
+            // exclusive scan of dcnt over digits (RADIX == blockDim)
+            uint32_t tot;
+            const uint32_t c = (threadIdx.x < RADIX) ? dcnt[threadIdx.x] : 0u;
+            const uint32_t ex = block_excl_scan<uint32_t>(c, wt, tot);
+            if (threadIdx.x < RADIX) dstart[threadIdx.x] = ex;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < SORT_ITEMS; r++) {
+            if (dd[r] != 0xffffu) {
+                const uint32_t p = dstart[dd[r]] + wcnt[w][dd[r]] + rk[r];
+                sk[p] = kk[r];
+                sv[p] = vv[r];
+            }
+        }
+        __syncthreads();
+        const int tile_n = (int)min((int64_t)SORT_TILE, b1 - t0);
+        for (int j = threadIdx.x; j < tile_n; j += blockDim.x) {
+            const K k = sk[j];
+            const uint32_t d = (uint32_t)((k >> shift) & (RADIX - 1));
+            const uint32_t g = run_off[d] + (uint32_t)j - dstart[d];
+            kout[g] = k;
+            vout[g] = sv[j];
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < RADIX; d += blockDim.x) run_off[d] += dcnt[d];
+        __syncthreads();
+    }
+}
+
+// Sorts n pairs by the low `bits` bits of the key.  The loader provides the
+// input; k[0..1], v[0..1] are double buffers of n elements (the loader may
+// read k[0]/v[0]).  hist needs RADIX * SORT_MAX_BLOCKS + 1 u32.  Returns the
+// buffer index (0 or 1) holding the result, or -1 when no pass ran (the
+// input already has all keys equal in those bits; the caller then uses the
+// loader's data as is).
+template <typename K, class L>
+int radix_sort_launch(const L &ld, int64_t n, int bits, K *k[2], uint32_t *v[2], uint32_t *hist,
+                      cudaStream_t st, int *launches)
+{
+    if (n <= 0 || bits <= 0) return -1;
+    int64_t nb = (n + SORT_TILE - 1) / SORT_TILE;
+    if (nb > SORT_MAX_BLOCKS) nb = SORT_MAX_BLOCKS;
+    int64_t per = (n + nb - 1) / nb;
+    per = (per + SORT_TILE - 1) / SORT_TILE * SORT_TILE;
+    nb = (n + per - 1) / per;
+    const int passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
+    int cur = -1;
+    for (int p = 0; p < passes; p++) {
+        const int shift = p * RADIX_BITS;
+        const int out = (cur == 0) ? 1 : 0;
+        if (p == 0) {
+            k_radix_hist<K, L><<<(unsigned)nb, SORT_THREADS, 0, st>>>(ld, n, per, shift, hist, (int)nb);
+            k_scan_u32_small<<<1, 1024, 0, st>>>(hist, (int64_t)RADIX * nb);
+            k_radix_scatter<K, L><<<(unsigned)nb, SORT_THREADS, 0, st>>>(ld, k[out], v[out], n, per, shift,
+                                                                          hist, (int)nb);
+        } else {
+            ArrayLoader<K> al{k[cur], v[cur]};
+            k_radix_hist<K, ArrayLoader<K>><<<(unsigned)nb, SORT_THREADS, 0, st>>>(al, n, per, shift, hist,
+                                                                                  (int)nb);
+            k_scan_u32_small<<<1, 1024, 0, st>>>(hist, (int64_t)RADIX * nb);
+            k_radix_scatter<K, ArrayLoader<K>><<<(unsigned)nb, SORT_THREADS, 0, st>>>(
+                al, k[out], v[out], n, per, shift, hist, (int)nb);
+        }
+        if (launches) *launches += 3;
+        cur = out;
+    }
+    return cur;
+}
+
+}  // namespace tw

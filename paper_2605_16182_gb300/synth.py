@@ -164,6 +164,7 @@ class StreamSpec:
     mean_gaps: List[int] = field(default_factory=lambda: [1000])
     switch_every: int = 0              # alternate mean gap every this many edges
     t0: int = 1_000_000_000
+    window: int = 0                    # engine window (< 0: count of newest edges kept)
 
     @property
     def n_batches(self) -> int:
@@ -229,14 +230,14 @@ def config_small(scale: float = 1.0) -> StreamSpec:
     """Directed, 10k nodes, 100k edges, Zipf 2.0, ts iid uniform in [0, 1e6), one batch."""
     e = max(1, int(100_000 * scale))
     return StreamSpec("plain-small-10k-nodes-100k-edges", 10_000, e, 2.0, 1001, e,
-                      ts_kind="uniform", ts_range=1_000_000)
+                      ts_kind="uniform", ts_range=1_000_000, window=0)
 
 
 def config_mid(scale: float = 1.0) -> StreamSpec:
     """1M nodes, 20M edges, Zipf 2.1, Poisson gaps mean 1000 ns, 20 batches of 1M."""
     b = max(1, int(1_000_000 * scale))
     return StreamSpec("biased-mid-1M-nodes-20M-edges", 1_000_000, 20 * b, 2.1, 1002, b,
-                      mean_gaps=[1000])
+                      mean_gaps=[1000], window=-5 * b)
 
 
 def config_billion(scale: float = 1.0) -> StreamSpec:
@@ -244,11 +245,11 @@ def config_billion(scale: float = 1.0) -> StreamSpec:
     every 1e7 edges), 100 batches of 10M."""
     b = max(1, int(10_000_000 * scale))
     return StreamSpec("billion-edge-stream-100M-nodes-1B-edges", 100_000_000, 100 * b, 2.0, 1003, b,
-                      mean_gaps=[1000, 100], switch_every=b)
+                      mean_gaps=[1000, 100], switch_every=b, window=-20 * b)
 
 
 def config_undirected_batched(scale: float = 1.0) -> StreamSpec:
     """Undirected, 10M nodes, 200M edges, Zipf 1.9, Poisson mean 1000 ns, one batch."""
     e = max(1, int(200_000_000 * scale))
     return StreamSpec("batched-undirected-10M-nodes-200M-edges", 10_000_000, e, 1.9, 1004, e,
-                      mean_gaps=[1000])
+                      mean_gaps=[1000], window=0)

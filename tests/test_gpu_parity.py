@@ -1,0 +1,234 @@
+"""CUDA library vs oracle, element by element, through the C ABI.
+
+Index state after every batch and uniform / linear walks must be bit-exact;
+exponential walks must agree on >= 99.99 % of hops with every divergence at
+a sampler boundary (the CUDA and libm exp / log may differ in the last place).
+"""
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2605_16182_gb300 import _lib, synth
+from parity_util import (MIN_HOP_AGREEMENT, assert_state_equal, assert_walks_bit_exact,
+                         compare_biased)
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def pair(window, directed):
+    return _lib.Engine(window=window, directed=directed, device="cuda:0"), O.Oracle(window, directed)
+
+
+def ingest_both(eng, orc, s, d, t, on_gpu=True):
+    if on_gpu:
+        st = eng.ingest(torch.as_tensor(s).cuda(), torch.as_tensor(d).cuda(), torch.as_tensor(t).cuda())
+    else:
+        st = eng.ingest(np.ascontiguousarray(s, np.int32), np.ascontiguousarray(d, np.int32),
+                        np.ascontiguousarray(t, np.int64))
+    orc.ingest(np.asarray(s), np.asarray(d), np.asarray(t))
+    return st
+
+
+def walks_both(eng, orc, n, L, bias, policy=0, seed=0, margin=False):
+    g = eng.walks(n, L, bias=bias, start_policy=policy, seed=seed)
+    torch.cuda.synchronize()
+    g = tuple(x.cpu().numpy() for x in g)
+    o = orc.walks(n, L, bias=bias, start_policy=policy, seed=seed, with_margin=margin)
+    return g, o
+
+
+def check_walks(eng, orc, n, L, policy=0, seed=0, biases=(0, 1, 2)):
+    for bias in biases:
+        g, o = walks_both(eng, orc, n, L, bias, policy, seed, margin=(bias == 2))
+        if bias == 2:
+            agree, total, div = compare_biased(g, o, o[3])
+            assert total == 0 or agree / total >= MIN_HOP_AGREEMENT, (agree, total)
+        else:
+            assert_walks_bit_exact(g, o, "bias %d" % bias)
+
+
+# ------------------------------------------------------------------ state
+def test_hand_worked_fixture_state():
+    fx = json.load(open(os.path.join(GOLDEN, "tiny_stream.json")))
+    eng, orc = pair(fx["window"], fx["directed"])
+    for b, want in zip(fx["batches"], fx["expected"]):
+        ingest_both(eng, orc, b["src"], b["dst"], b["ts"])
+        st = eng.state()
+        assert_state_equal(st, orc.state())
+        for k in ("src", "dst", "ts", "ts_group_off", "node_off", "node_order", "node_group_off", "node_gidx"):
+            assert list(st[k]) == want[k], k
+
+
+def _stream(rng, n_batches, max_batch, n_nodes, span, monotone):
+    out, t = [], 0
+    for _ in range(n_batches):
+        k = rng.randrange(0, max_batch + 1)
+        s = [rng.randrange(0, n_nodes) for _ in range(k)]
+        d = [rng.randrange(0, n_nodes) for _ in range(k)]
+        if monotone:
+            ts = []
+            for _ in range(k):
+                t += rng.choice([0, 0, 1, 3])
+                ts.append(t)
+        else:
+            ts = [t + rng.randrange(-span // 3, span) for _ in range(k)]
+            t += span // 2
+        out.append((s, d, ts))
+    return out
+
+
+@pytest.mark.parametrize("directed", [True, False])
+@pytest.mark.parametrize("window", [0, 40, -1, -25, -300])
+def test_random_streams_state_and_walks(directed, window):
+    rng = random.Random(1000 + window * 7 + directed)
+    for trial in range(6):
+        eng, orc = pair(window, directed)
+        for s, d, t in _stream(rng, rng.randrange(1, 7), rng.choice([5, 60, 700]),
+                               rng.choice([1, 3, 50, 2000]), 100, rng.random() < 0.5):
+            ingest_both(eng, orc, s, d, t, on_gpu=rng.random() < 0.5)
+            assert_state_equal(eng.state(), orc.state(), "trial %d" % trial)
+        check_walks(eng, orc, 700, rng.choice([2, 3, 9]), policy=trial % 2, seed=trial)
+
+
+def test_multi_tile_unsorted_batch_with_ragged_tail():
+    # spans several radix-sort tiles and scan chunks, not a multiple of any
+    rng = np.random.default_rng(5)
+    n = 3 * 2048 * 7 + 1234
+    s = rng.integers(0, 40_000, n).astype(np.int32)
+    d = rng.integers(0, 40_000, n).astype(np.int32)
+    t = rng.integers(-(1 << 40), 1 << 40, n).astype(np.int64)
+    t[::17] = 12345  # many ties
+    for directed in (True, False):
+        eng, orc = pair(-(n // 3), directed)
+        ingest_both(eng, orc, s, d, t)
+        ingest_both(eng, orc, s[: n // 2], d[: n // 2], t[: n // 2] + (1 << 41))
+        assert_state_equal(eng.state(), orc.state())
+        check_walks(eng, orc, 5000, 7)
+
+
+def test_late_edges_and_general_merge():
+    eng, orc = pair(50, True)
+    ingest_both(eng, orc, [0, 1, 2, 3], [1, 2, 3, 0], [100, 110, 120, 130])
+    # overlaps the store (general merge), one late edge (ts < 80)
+    st = ingest_both(eng, orc, [3, 2, 1, 0, 4], [0, 0, 0, 0, 0], [125, 79, 105, 140, 100])
+    assert st["n_dropped_late"] == 1
+    assert_state_equal(eng.state(), orc.state())
+    # whole batch late
+    st = ingest_both(eng, orc, [1, 1], [2, 2], [10, 20])
+    assert st["n_dropped_late"] == 2
+    assert_state_equal(eng.state(), orc.state())
+
+
+def test_small_config_state_and_walks():
+    spec = synth.config_small()
+    eng, orc = pair(spec.window, True)
+    for k, s, d, t in spec.batches():
+        st = ingest_both(eng, orc, s, d, t)
+        assert st["sorted_input"] == 0
+    assert_state_equal(eng.state(), orc.state())
+    for bias in (0, 1, 2):
+        g, o = walks_both(eng, orc, 10_000, 20, bias, 0, seed=0, margin=True)
+        if bias == 2:
+            agree, total, _ = compare_biased(g, o, o[3])
+            assert agree / total >= MIN_HOP_AGREEMENT
+        else:
+            assert_walks_bit_exact(g, o)
+    # the device hop counter and sector model match the oracle's accounting
+    eng.walks(10_000, 20, bias=0, seed=0)
+    ws = eng.last_walk_stats()
+    _, _, ln, _, nbytes = orc.walks(10_000, 20, bias=0, seed=0, with_bytes=True)
+    assert ws["hops"] == int(np.clip(ln - 1, 0, None).sum())
+    assert ws["model_bytes"] == int(nbytes)
+
+
+def test_mid_config_scaled_stream():
+    spec = synth.config_mid(scale=0.02)   # 20 batches of 20k, window 100k
+    eng, orc = pair(spec.window, True)
+    for k, s, d, t in spec.batches():
+        ingest_both(eng, orc, s, d, t)
+        if k % 5 == 4:
+            assert_state_equal(eng.state(), orc.state(), "batch %d" % k)
+            n = 20_000
+            bias = (np.arange(n) % 3).astype(np.uint8)
+            L = np.full(n, 40, np.int32)
+            g = eng.walks_mixed(torch.from_numpy(L).cuda(), torch.from_numpy(bias).cuda(),
+                                start_policy=_lib.START_BIASED_TS, seed=k)
+            torch.cuda.synchronize()
+            g = tuple(x.cpu().numpy() for x in g)
+            o = orc.walks(n, 40, bias_arr=bias, max_len_arr=L, start_policy=O.START_BIASED_TS, seed=k,
+                          with_margin=True)
+            agree, total, div = compare_biased(g, o, o[3])
+            assert agree / total >= MIN_HOP_AGREEMENT
+            lin_or_uni = bias != 2
+            assert (g[0][lin_or_uni] == o[0][lin_or_uni]).all()
+
+
+def test_host_and_device_outputs_agree():
+    spec = synth.config_small(scale=0.3)
+    eng, orc = pair(0, False)
+    for k, s, d, t in spec.batches():
+        ingest_both(eng, orc, s, d, t, on_gpu=False)
+    gd = eng.walks(3000, 9, bias=1, seed=11)
+    torch.cuda.synchronize()
+    node = np.zeros((3000, 9), np.int32)
+    ts = np.zeros((3000, 9), np.int64)
+    ln = np.zeros(3000, np.int32)
+    _lib.tempest_walks(eng.h, 3000, 9, 1, 0, 11, node.ctypes.data, ts.ctypes.data, ln.ctypes.data)
+    assert np.array_equal(node, gd[0].cpu().numpy()) and np.array_equal(ts, gd[1].cpu().numpy())
+    assert np.array_equal(ln, gd[2].cpu().numpy())
+    o = orc.walks(3000, 9, bias=1, seed=11)
+    assert_walks_bit_exact((node, ts, ln), o)
+
+
+# ------------------------------------------------------------------ edges
+def test_empty_and_degenerate():
+    eng, orc = pair(0, True)
+    g, o = walks_both(eng, orc, 5, 4, 0)
+    assert (g[2] == 0).all() and (g[0] == -1).all()
+    ingest_both(eng, orc, [], [], [])
+    assert_state_equal(eng.state(), orc.state())
+    # single node, self loops with equal timestamps
+    ingest_both(eng, orc, [0, 0, 0], [0, 0, 0], [7, 7, 7])
+    assert_state_equal(eng.state(), orc.state())
+    check_walks(eng, orc, 100, 5)
+    # max_len == 2, zero walks
+    check_walks(eng, orc, 50, 2)
+    eng.walks(0, 5)
+    # a large sparse id
+    ingest_both(eng, orc, [5_000_000], [3], [9])
+    assert_state_equal(eng.state(), orc.state())
+    check_walks(eng, orc, 300, 6)
+
+
+def test_invalid_input_leaves_state_unchanged():
+    eng, orc = pair(-5, True)
+    ingest_both(eng, orc, [0, 1], [1, 0], [1, 2])
+    before = eng.state()
+    with pytest.raises(_lib.TempestError) as e:
+        eng.ingest(torch.tensor([0, -3], dtype=torch.int32).cuda(), torch.tensor([1, 1], dtype=torch.int32).cuda(),
+                   torch.tensor([5, 6]).cuda())
+    assert e.value.code == _lib.TEMPEST_EINVAL
+    assert_state_equal(eng.state(), before)
+    with pytest.raises(_lib.TempestError):
+        eng.walks(3, 1)
+    with pytest.raises(_lib.TempestError):
+        eng.walks(3, 4, bias=7)
+    with pytest.raises(_lib.TempestError):
+        eng.set_bias_params(0.0)
+
+
+def test_bias_parameters():
+    spec = synth.config_small(scale=0.1)
+    eng, orc = pair(0, True)
+    for k, s, d, t in spec.batches():
+        ingest_both(eng, orc, s, d, t)
+    for lh, ls in ((0.25, 0.0), (3.0, 1e-3)):
+        eng.set_bias_params(lh, ls)
+        orc.set_bias_params(lh, ls)
+        check_walks(eng, orc, 4000, 8, policy=1, seed=4, biases=(2,))
