@@ -1,0 +1,429 @@
+"""Benchmark of the streaming temporal random-walk engine on one GB300.
+
+Workload (default): the billion-edge sliding-window stream -- 100M nodes,
+Zipf(2.0) endpoints, bursty Poisson timestamps (mean gap 1000 / 100 ns
+switching every 1e7 edges), batches of 10M edges, a count window of the 200M
+newest edges, and 10M exponential-bias walks (max_len 80, uniform start
+edge) after every 10th batch.  One step = 10 ingested batches + one walk
+call; the 100-batch stream is 10 steps (warm-up steps fill the window).
+
+Printed (rank 0, one JSON line):
+  value           walk hops per second over the walk calls (device time);
+  ingest_edges_per_s, p50 / p99 of batch and walk-call latency;
+  roofline        the walk kernel's sector-model bytes / its event time
+                  against the measured HBM copy bandwidth;
+  e2e             the same metric through the C ABI with host buffers
+                  (inputs copied in, walks copied out inside the timing);
+  cpu_baseline    the CPU oracle on a bounded sample of the workload.
+
+``--impl reference`` times the CPU oracle (the reference arm of this build).
+Under torchrun every rank holds a replica of the window and draws its own
+walks (replicas only: nothing is exchanged on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "temporal-walk hops/sec and ingest edges/sec on 1 GB300; p99 batch latency"
+BATCHES_PER_STEP = 10
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=7)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full size)")
+    p.add_argument("--walks", type=int, default=10_000_000)
+    p.add_argument("--max-len", type=int, default=80)
+    p.add_argument("--sched", default="full", choices=["full", "coop"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def percentile(xs, q):
+    if not xs:
+        return None
+    s = sorted(xs)
+    k = min(len(s) - 1, max(0, int(round(q / 100.0 * (len(s) - 1)))))
+    return s[k]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("walks.cu", "prims.cuh", "engine.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2605_16182_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(hops):
+    """DRAM bytes of the walk kernel from the committed ncu summary, scaled to
+    this launch by hops; None when the kernel changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "walk_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_hop"] * hops
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != gpu_index:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    from paper_2605_16182_gb300 import _lib, synth
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    spec = synth.config_billion(scale=args.scale)
+    n_walks = max(1, int(args.walks * args.scale)) if args.scale != 1.0 else args.walks
+    L = args.max_len
+    steps, warm = args.steps, args.warmup
+    n_batches = (steps + warm) * BATCHES_PER_STEP
+
+    # inputs resident in HBM before timing: every batch of the run
+    t_gen = time.time()
+    gen = spec.batches(device=dev, first=0, last=n_batches)
+    batches = [(s, d, t) for _, s, d, t in gen]
+    torch.cuda.synchronize()
+    t_gen = time.time() - t_gen
+
+    stream = torch.cuda.current_stream(dev)
+    eng = _lib.Engine(window=spec.window, directed=True, device=str(dev), stream=stream)
+    eng.set_scheduler(_lib.SCHED_COOP if args.sched == "coop" else _lib.SCHED_FULL_WALK)
+    node = torch.empty((n_walks, L), dtype=torch.int32, device=dev)
+    tso = torch.empty((n_walks, L), dtype=torch.int64, device=dev)
+    ln = torch.empty((n_walks,), dtype=torch.int32, device=dev)
+    seed_base = 1_000_003 * rank
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    ingest_ms, walk_ms, hops, model_bytes, launches, edges = [], [], 0, 0, 0, 0
+
+    def one_step(step, timed):
+        nonlocal hops, model_bytes, launches, edges
+        for b in range(BATCHES_PER_STEP):
+            s, d, t = batches[step * BATCHES_PER_STEP + b]
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            st = eng.ingest(s, d, t)
+            e1.record(stream)
+            if timed:
+                e1.synchronize()
+                ingest_ms.append(e0.elapsed_time(e1))
+                launches += st["launches"]
+                edges += int(s.shape[0])
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        eng.walks(n_walks, L, bias=_lib.BIAS_EXP, start_policy=_lib.START_UNIFORM_EDGE,
+                  seed=seed_base + step, out=(node, tso, ln))
+        e1.record(stream)
+        e1.synchronize()
+        ws = eng.last_walk_stats()
+        if timed:
+            walk_ms.append(e0.elapsed_time(e1))
+            hops += ws["hops"]
+            model_bytes += ws["model_bytes"]
+            launches += ws["launches"] + 1  # + the counter reset
+
+    for s in range(warm):
+        one_step(s, False)
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_all0, t_all1 = ev(), ev()
+    t_all0.record(stream)
+    for s in range(warm, warm + steps):
+        one_step(s, True)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop(dev.index or 0) if rank == 0 else None
+    total_ms = t_all0.elapsed_time(t_all1)
+
+    walk_s = sum(walk_ms) / 1e3
+    ingest_s = sum(ingest_ms) / 1e3
+    counts = eng.counts()
+    res = dict(hops=hops, walk_s=walk_s, ingest_s=ingest_s, edges=edges, total_ms=total_ms,
+               model_bytes=model_bytes, launches=launches, ingest_ms=ingest_ms, walk_ms=walk_ms,
+               live=counts["m"], clocks=clk, gen_s=t_gen, n_walks=n_walks)
+
+    # end to end through the C ABI with host buffers (one step, after the timed ones)
+    if not args.no_e2e:
+        res["e2e"] = run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream)
+    eng.close()
+    del batches
+    return res
+
+
+def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream):
+    """Continue the stream with host-resident batches: every step copies its
+    batches from pinned host memory and its walks back to pinned host memory
+    inside the timed region."""
+    import torch
+    from paper_2605_16182_gb300 import _lib
+
+    e2e_steps = 2
+    host = []
+    start = n_batches * spec.batch
+    ts_base = int(batches[-1][2][-1].item())
+    for k in range(e2e_steps * BATCHES_PER_STEP):
+        s, d, t = spec.edges(start + k * spec.batch, spec.batch, device=batches[0][0].device, ts_base=ts_base)
+        ts_base = int(t[-1].item())
+        host.append((s.cpu().pin_memory(), d.cpu().pin_memory(), t.cpu().pin_memory()))
+    hnode = torch.empty((n_walks, L), dtype=torch.int32).pin_memory()
+    hts = torch.empty((n_walks, L), dtype=torch.int64).pin_memory()
+    hln = torch.empty((n_walks,), dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    hops, walk_s, ingest_s, h2d, d2h, edges = 0, 0.0, 0.0, 0, 0, 0
+    for step in range(e2e_steps):
+        for b in range(BATCHES_PER_STEP):
+            s, d, t = host[step * BATCHES_PER_STEP + b]
+            t0 = time.perf_counter()
+            _lib.tempest_ingest(eng.h, s.data_ptr(), d.data_ptr(), t.data_ptr(), int(s.shape[0]))
+            ingest_s += time.perf_counter() - t0
+            h2d += s.numel() * 4 + d.numel() * 4 + t.numel() * 8
+            edges += int(s.shape[0])
+        t0 = time.perf_counter()
+        _lib.tempest_walks(eng.h, n_walks, L, _lib.BIAS_EXP, _lib.START_UNIFORM_EDGE, seed_base + 7777 + step,
+                           hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
+        walk_s += time.perf_counter() - t0
+        hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
+        d2h += hnode.numel() * 4 + hts.numel() * 8 + hln.numel() * 4
+    return dict(value=hops / walk_s, unit="hops/s", h2d_bytes_per_step=h2d // e2e_steps,
+                d2h_bytes_per_step=d2h // e2e_steps, ingest_edges_per_s=edges / ingest_s, steps=e2e_steps)
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference arm)
+# --------------------------------------------------------------------------
+def oracle_sample(seconds_budget=15.0, scale=0.01, n_walks=20_000, max_len=80):
+    """The oracle on the same workload scaled by `scale` (node count, batch
+    and window): it ingests the stream up to the first walk point after the
+    window is full, then draws exponential walks.  Returns rates."""
+    from oracle import oracle as O
+    from paper_2605_16182_gb300 import synth
+    spec = synth.config_billion(scale=scale)
+    spec.n_nodes = max(1000, int(spec.n_nodes * scale))
+    orc = O.Oracle(window=spec.window, directed=True)
+    edges, ing_s, lat = 0, 0.0, []
+    n_b = 3 * BATCHES_PER_STEP
+    t_begin = time.time()
+    for k, s, d, t in spec.batches(first=0, last=n_b):
+        s, d, t = s.numpy(), d.numpy(), t.numpy()
+        t0 = time.perf_counter()
+        orc.ingest(s, d, t)
+        dt = time.perf_counter() - t0
+        ing_s += dt
+        lat.append(dt)
+        edges += len(s)
+        if time.time() - t_begin > seconds_budget * 0.6:
+            break
+    t0 = time.perf_counter()
+    hops = 0
+    done = 0
+    chunk = 2000
+    while done < n_walks and time.perf_counter() - t0 < seconds_budget * 0.4:
+        ids = list(range(done, done + chunk))
+        import numpy as np
+        _, _, ln, _, _ = orc.walks(ids=np.array(ids, np.int64), max_len=max_len, bias=O.BIAS_EXP, seed=3)
+        hops += int(np.clip(ln - 1, 0, None).sum())
+        done += chunk
+    walk_s = time.perf_counter() - t0
+    c = orc.counts()
+    orc.close()
+    return dict(hops_per_s=hops / walk_s if walk_s > 0 else 0.0, edges_per_s=edges / ing_s if ing_s else 0.0,
+                walks=done, hops=hops, walk_s=walk_s, edges=edges, ingest_s=ing_s, live=c["m"],
+                sample="oracle (1 thread) on the billion-edge stream scaled by %g: %d nodes, batches of %d, "
+                       "window %d; %d batches ingested (%.1f s), then %d exponential walks of max_len %d "
+                       "(%.1f s)" % (scale, spec.n_nodes, spec.batch, -spec.window, len(lat), ing_s, done,
+                                     max_len, walk_s),
+                batch_p99_ms=1e3 * percentile(lat, 99) if lat else None)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    vals = []
+    last = None
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(seconds_budget=max(4.0, args.cpu_seconds / 2))
+        if s >= args.warmup:
+            vals.append(r["hops_per_s"])
+        last = r
+    v = statistics.median(vals) if vals else last["hops_per_s"]
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "hops/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64", "data": "synthetic",
+           "config": {"workload": "billion-edge-stream-100M-nodes-1B-edges (oracle on a 1/100 sample)"},
+           "cpu_baseline": {"value": v, "unit": "hops/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
+           "ingest_edges_per_s": last["edges_per_s"],
+           "e2e": {"value": v, "unit": "hops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    res = run_ours(args, rank, world)
+
+    # aggregate over ranks: total hops / max time
+    hops, walk_s, ingest_s, edges, total_ms = res["hops"], res["walk_s"], res["ingest_s"], res["edges"], res["total_ms"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([hops, edges], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        m = torch.tensor([walk_s, ingest_s, total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        hops, edges = int(t[0].item()), int(t[1].item())
+        walk_s, ingest_s, total_ms = (float(x) for x in m.tolist())
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    walk_kernel_s = walk_s  # one kernel (plus a 32-byte counter reset) per call
+    achieved = res["model_bytes"] / walk_kernel_s / 1e9 if walk_kernel_s > 0 else 0.0
+    traffic = recorded_traffic(res["hops"] / max(1, len(res["walk_ms"])))
+    cpu = None
+    if not args.no_cpu:
+        o = oracle_sample(seconds_budget=args.cpu_seconds)
+        cpu = {"value": o["hops_per_s"], "unit": "hops/s", "cores": 1, "kind": "oracle", "sample": o["sample"],
+               "ingest_edges_per_s": o["edges_per_s"]}
+    per_launch_bytes = res["model_bytes"] / max(1, len(res["walk_ms"]))
+    out = {
+        "metric": METRIC,
+        "value": hops / walk_s if walk_s > 0 else 0.0,
+        "unit": "hops/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "i64+f64",
+        "data": "synthetic",
+        "config": {"workload": "billion-edge-stream-100M-nodes-1B-edges" + ("" if args.scale == 1.0 else
+                                                                         " scaled %g" % args.scale),
+                   "nodes": int(100_000_000 * args.scale) if args.scale != 1.0 else 100_000_000,
+                   "batch_edges": int(10_000_000 * args.scale), "window_edges": int(200_000_000 * args.scale),
+                   "walks_per_call": res["n_walks"], "max_len": args.max_len, "bias": "exponential",
+                   "start": "uniform edge", "batches_per_step": BATCHES_PER_STEP,
+                   "scheduler": args.sched, "l2": "inputs larger than L2 (160 MB batches, GB-sized state)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "ingest_edges_per_s": edges / ingest_s if ingest_s > 0 else 0.0,
+        "stream_hops_per_s": hops / (total_ms / 1e3) if total_ms > 0 else 0.0,
+        "latency_ms": {"ingest_batch_p50": percentile(res["ingest_ms"], 50),
+                       "ingest_batch_p99": percentile(res["ingest_ms"], 99),
+                       "walk_call_p50": percentile(res["walk_ms"], 50),
+                       "walk_call_p99": percentile(res["walk_ms"], 99)},
+        "hops_per_walk": res["hops"] / max(1, res["n_walks"] * len(res["walk_ms"])),
+        "live_edges": res["live"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_walks_full" if args.sched == "full" else "coop tiers",
+                     "peak_kind": peak_kind + " hbm copy (burst)",
+                     "model_bytes_per_launch": per_launch_bytes},
+        "cpu_baseline": cpu,
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+    }
+    if "e2e" in res:
+        out["e2e"] = res["e2e"]
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

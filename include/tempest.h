@@ -81,6 +81,7 @@ typedef struct {
     int64_t cutoff;        /* window cut-off (valid when has_cutoff) */
     int32_t has_cutoff;
     int32_t sorted_input;  /* the batch arrived in timestamp order */
+    int64_t launches;      /* kernels this library launched for the batch */
 } tempest_ingest_stats;
 
 /* Per-call walk report (valid once the call's work has finished). */

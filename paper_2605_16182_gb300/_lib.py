@@ -48,7 +48,8 @@ class IngestStats(ctypes.Structure):
                 ("n_evicted", ctypes.c_int64), ("n_live", ctypes.c_int64),
                 ("n_ts_groups", ctypes.c_int64), ("n_node_groups", ctypes.c_int64),
                 ("n_nodes", ctypes.c_int64), ("cutoff", ctypes.c_int64),
-                ("has_cutoff", ctypes.c_int32), ("sorted_input", ctypes.c_int32)]
+                ("has_cutoff", ctypes.c_int32), ("sorted_input", ctypes.c_int32),
+                ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -197,13 +198,21 @@ def tempest_last_error(h) -> str:
 
 
 # ---------------------------------------------------------------- wrapper
-def _ptr(x):
+def _ptr(x, dtype: Optional[str] = None):
+    """Raw pointer of a contiguous tensor / array, checking its element type
+    (one of "int32", "int64", "uint8")."""
     if x is None:
         return None
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous()
+        if dtype is not None and str(x.dtype) != "torch." + dtype:
+            raise TypeError("expected a %s tensor, got %s" % (dtype, x.dtype))
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
         return x.data_ptr()
-    assert x.flags["C_CONTIGUOUS"]
+    if dtype is not None and x.dtype != np.dtype(dtype):
+        raise TypeError("expected a %s array, got %s" % (dtype, x.dtype))
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
     return x.ctypes.data
 
 
@@ -267,7 +276,7 @@ class Engine:
     def ingest(self, src, dst, ts) -> dict:
         n = int(src.shape[0])
         assert dst.shape[0] == n and ts.shape[0] == n
-        return tempest_ingest(self.h, _ptr(src), _ptr(dst), _ptr(ts), n).as_dict()
+        return tempest_ingest(self.h, _ptr(src, "int32"), _ptr(dst, "int32"), _ptr(ts, "int64"), n).as_dict()
 
     def walks(self, n_walks: int, max_len: int, bias: int = BIAS_UNIFORM,
               start_policy: int = START_UNIFORM_EDGE, seed: int = 0, out=None):
@@ -278,7 +287,8 @@ class Engine:
             ln = torch.empty((n_walks,), dtype=torch.int32, device=self.device)
         else:
             node, ts, ln = out
-        tempest_walks(self.h, n_walks, max_len, bias, start_policy, seed, _ptr(node), _ptr(ts), _ptr(ln))
+        tempest_walks(self.h, n_walks, max_len, bias, start_policy, seed, _ptr(node, "int32"),
+                      _ptr(ts, "int64"), _ptr(ln, "int32"))
         return node, ts, ln
 
     def walks_mixed(self, max_len_arr, bias_arr, start_policy: int = START_UNIFORM_EDGE, seed: int = 0,
@@ -292,8 +302,8 @@ class Engine:
             ln = torch.empty((n,), dtype=torch.int32, device=self.device)
         else:
             node, ts, ln = out
-        tempest_walks_mixed(self.h, n, _ptr(max_len_arr), cap, _ptr(bias_arr), start_policy, seed,
-                            _ptr(node), _ptr(ts), _ptr(ln))
+        tempest_walks_mixed(self.h, n, _ptr(max_len_arr, "int32"), cap, _ptr(bias_arr, "uint8"), start_policy,
+                            seed, _ptr(node, "int32"), _ptr(ts, "int64"), _ptr(ln, "int32"))
         return node, ts, ln
 
     def last_walk_stats(self) -> dict:

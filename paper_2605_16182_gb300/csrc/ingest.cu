@@ -583,6 +583,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
         stats->cutoff = h->cutoff;
         stats->has_cutoff = h->has_cutoff;
         stats->sorted_input = sorted ? 1 : 0;
+        stats->launches = h->pending_launches;
     }
     return TEMPEST_OK;
 }

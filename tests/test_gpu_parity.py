@@ -26,12 +26,14 @@ def pair(window, directed):
 
 
 def ingest_both(eng, orc, s, d, t, on_gpu=True):
+    s = np.ascontiguousarray(np.asarray(s), np.int32)
+    d = np.ascontiguousarray(np.asarray(d), np.int32)
+    t = np.ascontiguousarray(np.asarray(t), np.int64)
     if on_gpu:
-        st = eng.ingest(torch.as_tensor(s).cuda(), torch.as_tensor(d).cuda(), torch.as_tensor(t).cuda())
+        st = eng.ingest(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), torch.from_numpy(t).cuda())
     else:
-        st = eng.ingest(np.ascontiguousarray(s, np.int32), np.ascontiguousarray(d, np.int32),
-                        np.ascontiguousarray(t, np.int64))
-    orc.ingest(np.asarray(s), np.asarray(d), np.asarray(t))
+        st = eng.ingest(s, d, t)
+    orc.ingest(s, d, t)
     return st
 
 
@@ -212,7 +214,9 @@ def test_invalid_input_leaves_state_unchanged():
     before = eng.state()
     with pytest.raises(_lib.TempestError) as e:
         eng.ingest(torch.tensor([0, -3], dtype=torch.int32).cuda(), torch.tensor([1, 1], dtype=torch.int32).cuda(),
-                   torch.tensor([5, 6]).cuda())
+                   torch.tensor([5, 6], dtype=torch.int64).cuda())
+    with pytest.raises(TypeError):
+        eng.ingest(torch.tensor([0, 1]).cuda(), torch.tensor([1, 1]).cuda(), torch.tensor([5, 6]).cuda())
     assert e.value.code == _lib.TEMPEST_EINVAL
     assert_state_equal(eng.state(), before)
     with pytest.raises(_lib.TempestError):
