@@ -193,6 +193,29 @@ const char *tempest_last_error(tempest_t *h);
 /* Library version string. */
 const char *tempest_version(void);
 
+/* Allocation-free batch sort.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory at run time -- code
+ * under a fixed memory plan (a host framework that owns every device byte
+ * through its own pool) or a latency-critical loop that cannot afford
+ * cudaMalloc's implicit synchronisation.
+ *
+ * Sorts n edges by timestamp, keeping arrival order among equal timestamps
+ * (the batch sort that begins every ingest), and writes the sorted batch to
+ * out_src / out_dst / out_ts.  All six arrays must be device memory
+ * (int32[n], int32[n], int64[n] each); the work is queued on `stream` (a
+ * cudaStream_t, NULL for the legacy stream) and the call does not wait for it.
+ * Scratch is a static device array of TEMPEST_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits; nothing is
+ * allocated or freed.  The first call on a device looks up that array's
+ * device address, so make it before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU race.  Returns EINVAL (see
+ * tempest_last_error(NULL)) for n < 0, n > TEMPEST_NOALLOC_MAX_EDGES or a
+ * non-device array; n == 0 does nothing. */
+#define TEMPEST_NOALLOC_MAX_EDGES 262144
+#define TEMPEST_NOALLOC_SCRATCH_BYTES 6815744
+int tempest_sort_batch_noalloc(const int32_t *src, const int32_t *dst, const int64_t *ts, int64_t n,
+                               int32_t *out_src, int32_t *out_dst, int64_t *out_ts, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,9 @@ EXPORTED = (
     "tempest_set_bias_params", "tempest_ingest", "tempest_walks", "tempest_walks_mixed",
     "tempest_set_scheduler", "tempest_last_walk_stats", "tempest_get_counts",
     "tempest_export_state", "tempest_sync", "tempest_last_error", "tempest_version",
+    "tempest_sort_batch_noalloc",
 )
+NOALLOC_MAX_EDGES = 262144
 
 
 class TempestError(RuntimeError):
@@ -100,6 +102,7 @@ def load():
     L.tempest_last_error.argtypes = [vp]
     L.tempest_last_error.restype = ctypes.c_char_p
     L.tempest_version.restype = ctypes.c_char_p
+    L.tempest_sort_batch_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("tempest_last_error", "tempest_version"):
             getattr(L, name).restype = ci
@@ -195,6 +198,15 @@ def tempest_sync(h):
 def tempest_last_error(h) -> str:
     m = load().tempest_last_error(h)
     return m.decode() if m else ""
+
+
+def tempest_sort_batch_noalloc(src_ptr, dst_ptr, ts_ptr, n, out_src_ptr, out_dst_ptr, out_ts_ptr, stream_ptr):
+    """Allocation-free batch sort for callers that cannot allocate device
+    memory at run time (see include/tempest.h)."""
+    return _check(None, load().tempest_sort_batch_noalloc(
+        ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr), ctypes.c_void_p(ts_ptr), int(n),
+        ctypes.c_void_p(out_src_ptr), ctypes.c_void_p(out_dst_ptr), ctypes.c_void_p(out_ts_ptr),
+        ctypes.c_void_p(stream_ptr)))
 
 
 # ---------------------------------------------------------------- wrapper
