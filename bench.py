@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full size)")
     p.add_argument("--walks", type=int, default=10_000_000)
     p.add_argument("--max-len", type=int, default=80)
-    p.add_argument("--sched", default="full", choices=["full", "coop"])
+    p.add_argument("--sched", default="full", choices=["stream", "full", "coop"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -161,7 +161,8 @@ def run_ours(args, rank, world):
 
     stream = torch.cuda.current_stream(dev)
     eng = _lib.Engine(window=spec.window, directed=True, device=str(dev), stream=stream)
-    eng.set_scheduler(_lib.SCHED_COOP if args.sched == "coop" else _lib.SCHED_FULL_WALK)
+    eng.set_scheduler({"stream": _lib.SCHED_STREAM, "full": _lib.SCHED_FULL_WALK,
+                       "coop": _lib.SCHED_COOP}[args.sched])
     node = torch.empty((n_walks, L), dtype=torch.int32, device=dev)
     tso = torch.empty((n_walks, L), dtype=torch.int64, device=dev)
     ln = torch.empty((n_walks,), dtype=torch.int32, device=dev)
@@ -196,7 +197,7 @@ def run_ours(args, rank, world):
             walk_ms.append(e0.elapsed_time(e1))
             hops += ws["hops"]
             model_bytes += ws["model_bytes"]
-            launches += ws["launches"] + 1  # + the counter reset
+            launches += ws["launches"]
 
     for s in range(warm):
         one_step(s, False)
@@ -413,7 +414,8 @@ def main():
         "live_edges": res["live"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_walks_full" if args.sched == "full" else "coop tiers",
+                     "kernel": {"stream": "k_walks_stream", "full": "k_walks_full",
+                                "coop": "coop tiers"}[args.sched],
                      "peak_kind": peak_kind + " hbm copy (burst)",
                      "model_bytes_per_launch": per_launch_bytes},
         "cpu_baseline": cpu,

@@ -64,9 +64,14 @@ enum { TEMPEST_START_UNIFORM_EDGE = 0, TEMPEST_START_BIASED_TS = 1 };
 /* Walk execution form (Sec. 2.4).  The result is the same for every form:
  * each walk draws from its own counter-based random stream. */
 enum {
-    TEMPEST_SCHED_FULL_WALK = 0, /* one thread carries one walk (Sec. 2.4.1) */
-    TEMPEST_SCHED_COOP = 1       /* per-hop regrouping by node, thread / warp /
+    TEMPEST_SCHED_FULL_WALK = 0, /* default: one thread carries one walk (Sec. 2.4.1) */
+    TEMPEST_SCHED_COOP = 1,      /* per-hop regrouping by node, thread / warp /
                                     block tiers (Sec. 2.4.3-2.4.5, Alg. 1) */
+    TEMPEST_SCHED_STREAM = 2     /* persistent lanes that refill from a
+                                    work counter as walks end, one memory round
+                                    trip per loop iteration, interpolation
+                                    search of Gamma_t(v) (no counterpart in the
+                                    paper: a GB300 form of Sec. 2.4.1) */
 };
 
 /* Per-batch ingest report. */

@@ -217,7 +217,7 @@ int tempest_set_bias_params(tempest_t *h, double lambda_hop, double lambda_start
 int tempest_set_scheduler(tempest_t *h, int mode)
 {
     if (!h) return TEMPEST_EINVAL;
-    if (mode != TEMPEST_SCHED_FULL_WALK && mode != TEMPEST_SCHED_COOP)
+    if (mode != TEMPEST_SCHED_FULL_WALK && mode != TEMPEST_SCHED_COOP && mode != TEMPEST_SCHED_STREAM)
         return fail(h, TEMPEST_EINVAL, "tempest_set_scheduler: unknown mode %d", mode);
     h->sched = mode;
     return TEMPEST_OK;

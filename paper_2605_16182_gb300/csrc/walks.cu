@@ -160,6 +160,317 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
     }
 }
 
+// ---------------------------------------------------------------------------
+// Streaming walker.
+//
+// Each lane runs a small state machine and carries one walk at a time; every
+// loop iteration consumes the values loaded in the previous iteration,
+// computes, and issues the next (at most three independent) loads.  A lane
+// whose walk ends takes the next walk id from a warp-aggregated atomic
+// counter at once, so lanes never wait for the longest walk of their warp
+// and every iteration keeps one memory round trip in flight per lane.
+//
+// The search for c = the first group of v with ts > t uses interpolation on
+// the group timestamps (arrival times are close to uniform inside a node's
+// range, so O(log log G) probes), falling back to a bisection probe whenever
+// a probe did not halve the bracket (at most ~2 log2 G probes).  Any exact
+// search returns the same c as the plain binary search.
+// ---------------------------------------------------------------------------
+enum : int {
+    S_FETCH = 0,   // needs a walk
+    S_NEW,         // walk assigned: draw the start
+    S_SGROUP,      // start timestamp group offsets loaded
+    S_EDGE,        // start edge loaded
+    S_RANGE,       // node group range loaded
+    S_ENDS,        // first / last group timestamps loaded
+    S_SEARCH,      // one probe loaded
+    S_PICK2,       // chosen group's entry range loaded
+    S_HOP,         // chosen entry loaded
+    S_EXIT
+};
+
+struct SmLane {
+    int64_t w;
+    int64_t t;       // current time
+    int64_t vL, vR;  // bracket values: a[L] <= t < a[R]
+    double ud;       // saved uniform for the draw inside a range
+    int32_t L, R;    // bracket
+    int32_t g0, g1;  // group range of the current node
+    int32_t v;       // current node
+    int32_t len, cap_len;
+    int32_t state;
+    int32_t bias;
+    int32_t prev_w;  // bracket width before the last probe
+    uint32_t hop;
+    uint32_t orient;
+};
+
+__device__ __forceinline__ int32_t interp_probe(int32_t L, int32_t R, int64_t vL, int64_t vR, int64_t t,
+                                                bool bisect)
+{
+    // L < R - 1, vL <= t < vR.  The guess only steers the search (the
+    // comparison against t is exact), so single precision is enough.
+    if (bisect) return L + ((R - L) >> 1);
+    const float f = __fdividef((float)(t - vL), (float)(vR - vL));
+    int32_t p = L + 1 + (int32_t)(f * (float)(R - L - 1));
+    if (p <= L) p = L + 1;
+    if (p >= R) p = R - 1;
+    return p;
+}
+
+__global__ void __launch_bounds__(256) k_walks_stream(const WalkView V, const WalkOut O,
+                                                      unsigned long long *next_walk)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    SmLane s;
+    s.state = S_FETCH;
+    s.w = 0;
+    int64_t y0 = 0;           // loaded 64-bit value
+    int32_t z0 = 0, z1 = 0;   // loaded 32-bit values
+    int64_t y1 = 0;
+    unsigned long long hops = 0, bytes = 0;
+    const int64_t N = O.n_walks;
+
+    // warp-local queue of walk ids [q_next, q_end), refilled WALK_CHUNK at a
+    // time from the global counter (warp-uniform values)
+    constexpr int64_t WALK_CHUNK = 256;
+    int64_t q_next = 0, q_end = 0;
+    while (true) {
+        // lanes without a walk take the next ids from the warp's queue
+        unsigned need = __ballot_sync(0xffffffffu, s.state == S_FETCH);
+        while (need) {
+            if (q_next >= q_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(next_walk, (unsigned long long)WALK_CHUNK);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if ((int64_t)base >= N) {
+                    if (s.state == S_FETCH) s.state = S_EXIT;
+                    break;
+                }
+                q_next = (int64_t)base;
+                q_end = min(N, q_next + WALK_CHUNK);
+            }
+            const int64_t avail = q_end - q_next;
+            const int rank = __popc(need & lt);
+            const int take = (int)min((int64_t)__popc(need), avail);
+            if (s.state == S_FETCH && rank < take) {
+                s.w = q_next + rank;
+                s.state = S_NEW;
+            }
+            q_next += take;
+            need = __ballot_sync(0xffffffffu, s.state == S_FETCH);
+        }
+        if (__all_sync(0xffffffffu, s.state == S_EXIT)) break;
+
+        int32_t *nrow = O.node + s.w * (int64_t)O.cap;
+        int64_t *trow = O.ts + s.w * (int64_t)O.cap;
+        bool pick = false;   // the bracket closed this iteration: draw now
+        bool finish = false; // the walk ended this iteration
+
+        switch (s.state) {
+            case S_NEW: {
+                int32_t L = O.len_arr ? O.len_arr[s.w] : O.max_len;
+                int bias = O.bias_arr ? (int)O.bias_arr[s.w] : O.bias;
+                if (L < 2 || L > O.cap || bias < 0 || bias > 2) {
+                    atomicOr(&O.cnt->status, 1ull);
+                    L = L < 2 ? 2 : (L > O.cap ? O.cap : L);
+                    bias = (bias < 0 || bias > 2) ? BIAS_UNIFORM : bias;
+                }
+                s.cap_len = L;
+                s.bias = bias;
+                s.len = 0;
+                if (V.m == 0) {
+                    finish = true;
+                    break;
+                }
+                const Rand4 r = walk_rand(O.seed, (uint64_t)s.w, 0u);
+                const double u1 = u53(r.r0, r.r1);
+                s.ud = u53(r.r2, r.r3);
+                s.orient = (!V.directed && (r.r3 & 1u)) ? 1u : 0u;
+                if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
+                    const int64_t k = uniform_index(u1, V.m);
+                    y0 = __ldg(V.st_ts + k);
+                    z0 = __ldg(V.st_src + k);
+                    z1 = __ldg(V.st_dst + k);
+                    s.state = S_EDGE;
+                } else {
+                    const int64_t g = sampler_index(u1, V.G, bias, V.lam_start);
+                    z0 = __ldg(V.ts_goff + g);
+                    z1 = __ldg(V.ts_goff + g + 1);
+                    s.state = S_SGROUP;
+                }
+                break;
+            }
+            case S_SGROUP: {
+                const int64_t k = (int64_t)z0 + uniform_index(s.ud, (int64_t)(z1 - z0));
+                y0 = __ldg(V.st_ts + k);
+                z0 = __ldg(V.st_src + k);
+                z1 = __ldg(V.st_dst + k);
+                s.state = S_EDGE;
+                break;
+            }
+            case S_EDGE: {
+                int32_t a = z0, b = z1;
+                if (s.orient) {
+                    const int32_t x = a;
+                    a = b;
+                    b = x;
+                }
+                nrow[0] = a;
+                nrow[1] = b;
+                trow[0] = INT64_MIN;
+                trow[1] = y0;
+                s.len = 2;
+                s.hop = 1;
+                s.v = b;
+                s.t = y0;
+                hops++;
+                bytes += START_MODEL_BYTES;
+                if (s.len >= s.cap_len) {
+                    finish = true;
+                } else {
+                    z0 = __ldg(V.gidx + b);
+                    z1 = __ldg(V.gidx + b + 1);
+                    s.state = S_RANGE;
+                }
+                break;
+            }
+            case S_RANGE: {
+                s.g0 = z0;
+                s.g1 = z1;
+                if (z0 == z1) {
+                    finish = true;
+                } else {
+                    y0 = __ldg(V.ngts + z0);
+                    y1 = __ldg(V.ngts + z1 - 1);
+                    s.state = S_ENDS;
+                }
+                break;
+            }
+            case S_ENDS: {
+                if (s.t < y0) {
+                    s.R = s.g0;  // all of the node's groups are later than t
+                    pick = true;
+                } else if (s.t >= y1) {
+                    finish = true;  // Gamma_t(v) is empty
+                } else {
+                    s.L = s.g0;
+                    s.R = s.g1 - 1;
+                    s.vL = y0;
+                    s.vR = y1;
+                    if (s.R - s.L == 1) {
+                        pick = true;
+                    } else {
+                        s.prev_w = s.R - s.L;
+                        const int32_t p = interp_probe(s.L, s.R, s.vL, s.vR, s.t, false);
+                        z1 = p;
+                        y0 = __ldg(V.ngts + p);
+                        s.state = S_SEARCH;
+                    }
+                }
+                break;
+            }
+            case S_SEARCH: {
+                const int32_t p = z1;
+                if (y0 > s.t) {
+                    s.R = p;
+                    s.vR = y0;
+                } else {
+                    s.L = p;
+                    s.vL = y0;
+                }
+                const int32_t width = s.R - s.L;
+                if (width == 1) {
+                    pick = true;
+                } else {
+                    const bool bisect = 2 * width > s.prev_w;
+                    s.prev_w = width;
+                    const int32_t q = interp_probe(s.L, s.R, s.vL, s.vR, s.t, bisect);
+                    z1 = q;
+                    y0 = __ldg(V.ngts + q);
+                }
+                break;
+            }
+            case S_PICK2: {
+                const int64_t idx = (int64_t)z0 + uniform_index(s.ud, (int64_t)(z1 - z0));
+                const Entry *e = V.ent + idx;
+                y0 = __ldg(&e->ts);
+                z0 = __ldg(&e->other);
+                s.state = S_HOP;
+                break;
+            }
+            case S_HOP: {
+                nrow[s.len] = z0;
+                trow[s.len] = y0;
+                hops++;
+                bytes += hop_model_bytes((int64_t)(s.g1 - s.g0));
+                s.len++;
+                s.hop++;
+                s.v = z0;
+                s.t = y0;
+                if (s.len >= s.cap_len) {
+                    finish = true;
+                } else {
+                    const int32_t v = z0;
+                    z0 = __ldg(V.gidx + v);
+                    z1 = __ldg(V.gidx + v + 1);
+                    s.state = S_RANGE;
+                }
+                break;
+            }
+            default:
+                break;
+        }
+
+        if (pick) {
+            // c = s.R is the first group later than t; draw the next edge
+            const int32_t c = s.R;
+            const Rand4 r = walk_rand(O.seed, (uint64_t)s.w, s.hop);
+            const double u1 = u53(r.r0, r.r1);
+            if (s.bias == BIAS_UNIFORM) {
+                s.ud = u1;
+                z0 = __ldg(V.ngo + c);
+                z1 = __ldg(V.ngo + s.g1);
+            } else {
+                s.ud = u53(r.r2, r.r3);
+                const int64_t j = sampler_index(u1, (int64_t)(s.g1 - c), s.bias, V.lam_hop);
+                z0 = __ldg(V.ngo + c + j);
+                z1 = __ldg(V.ngo + c + j + 1);
+            }
+            s.state = S_PICK2;
+        }
+        if (finish) {
+            O.len[s.w] = s.len;
+            s.state = S_FETCH;
+        }
+    }
+    hops = warp_sum(hops);
+    bytes = warp_sum(bytes);
+    if (lane == 0 && hops) {
+        atomicAdd(&O.cnt->hops, hops);
+        atomicAdd(&O.cnt->model_bytes, bytes);
+    }
+}
+
+// Padding of every row after its walk: node -1, ts INT64_MIN from len to the
+// row end.  One warp per row, lanes on consecutive cells.
+__global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, const int32_t *__restrict__ len,
+                                                  int32_t *node, int64_t *ts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_walks; w += warps) {
+        const int32_t l = len[w];
+        int32_t *nr = node + w * (int64_t)cap;
+        int64_t *tr = ts + w * (int64_t)cap;
+        for (int32_t i = l + lane; i < cap; i += 32) {
+            nr[i] = -1;
+            tr[i] = INT64_MIN;
+        }
+    }
+}
+
 static WalkView make_view(tempest_t *h)
 {
     WalkView V;
@@ -201,11 +512,28 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     O.cnt = h->wcnt.as<WalkCounters>();
     int64_t launches = 0;
     if (rq.n_walks > 0) {
-        int64_t grid = (rq.n_walks + 255) / 256;
-        const int64_t cap = (int64_t)h->num_sms * 8;
-        if (grid > cap) grid = cap;
-        k_walks_full<<<(unsigned)grid, 256, 0, st>>>(V, O);
-        launches++;
+        if (h->sched == TEMPEST_SCHED_FULL_WALK) {
+            int64_t grid = (rq.n_walks + 255) / 256;
+            const int64_t cap = (int64_t)h->num_sms * 8;
+            if (grid > cap) grid = cap;
+            k_walks_full<<<(unsigned)grid, 256, 0, st>>>(V, O);
+            launches++;
+        } else {
+            static int blocks_per_sm = 0;
+            if (blocks_per_sm == 0) {
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walks_stream, 256, 0);
+                if (blocks_per_sm < 1) blocks_per_sm = 1;
+            }
+            int64_t grid = (int64_t)h->num_sms * blocks_per_sm;
+            const int64_t need = (rq.n_walks + 255) / 256;
+            if (grid > need) grid = need;
+            k_walks_stream<<<(unsigned)grid, 256, 0, st>>>(V, O, &O.cnt->pad);
+            int64_t pgrid = (rq.n_walks + 7) / 8;
+            const int64_t pcap = (int64_t)h->num_sms * 16;
+            if (pgrid > pcap) pgrid = pcap;
+            k_pad_rows<<<(unsigned)pgrid, 256, 0, st>>>(rq.n_walks, rq.cap, rq.len, rq.node, rq.ts);
+            launches += 2;
+        }
     }
     h->last_ws.n_walks = rq.n_walks;
     h->last_ws.launches = launches;

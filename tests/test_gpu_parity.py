@@ -37,6 +37,9 @@ def ingest_both(eng, orc, s, d, t, on_gpu=True):
     return st
 
 
+SCHEDULERS = (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK)
+
+
 def walks_both(eng, orc, n, L, bias, policy=0, seed=0, margin=False):
     g = eng.walks(n, L, bias=bias, start_policy=policy, seed=seed)
     torch.cuda.synchronize()
@@ -45,14 +48,18 @@ def walks_both(eng, orc, n, L, bias, policy=0, seed=0, margin=False):
     return g, o
 
 
-def check_walks(eng, orc, n, L, policy=0, seed=0, biases=(0, 1, 2)):
-    for bias in biases:
-        g, o = walks_both(eng, orc, n, L, bias, policy, seed, margin=(bias == 2))
-        if bias == 2:
-            agree, total, div = compare_biased(g, o, o[3])
-            assert total == 0 or agree / total >= MIN_HOP_AGREEMENT, (agree, total)
-        else:
-            assert_walks_bit_exact(g, o, "bias %d" % bias)
+def check_walks(eng, orc, n, L, policy=0, seed=0, biases=(0, 1, 2), scheds=SCHEDULERS):
+    """Every walk form must give the oracle's walks."""
+    for sched in scheds:
+        eng.set_scheduler(sched)
+        for bias in biases:
+            g, o = walks_both(eng, orc, n, L, bias, policy, seed, margin=(bias == 2))
+            if bias == 2:
+                agree, total, div = compare_biased(g, o, o[3])
+                assert total == 0 or agree / total >= MIN_HOP_AGREEMENT, (sched, agree, total)
+            else:
+                assert_walks_bit_exact(g, o, "sched %d bias %d" % (sched, bias))
+    eng.set_scheduler(_lib.SCHED_STREAM)
 
 
 # ------------------------------------------------------------------ state
@@ -134,19 +141,16 @@ def test_small_config_state_and_walks():
         st = ingest_both(eng, orc, s, d, t)
         assert st["sorted_input"] == 0
     assert_state_equal(eng.state(), orc.state())
-    for bias in (0, 1, 2):
-        g, o = walks_both(eng, orc, 10_000, 20, bias, 0, seed=0, margin=True)
-        if bias == 2:
-            agree, total, _ = compare_biased(g, o, o[3])
-            assert agree / total >= MIN_HOP_AGREEMENT
-        else:
-            assert_walks_bit_exact(g, o)
+    check_walks(eng, orc, 10_000, 20, policy=0, seed=0)
+    check_walks(eng, orc, 10_000, 20, policy=1, seed=1)
     # the device hop counter and sector model match the oracle's accounting
-    eng.walks(10_000, 20, bias=0, seed=0)
-    ws = eng.last_walk_stats()
     _, _, ln, _, nbytes = orc.walks(10_000, 20, bias=0, seed=0, with_bytes=True)
-    assert ws["hops"] == int(np.clip(ln - 1, 0, None).sum())
-    assert ws["model_bytes"] == int(nbytes)
+    for sched in SCHEDULERS:
+        eng.set_scheduler(sched)
+        eng.walks(10_000, 20, bias=0, seed=0)
+        ws = eng.last_walk_stats()
+        assert ws["hops"] == int(np.clip(ln - 1, 0, None).sum())
+        assert ws["model_bytes"] == int(nbytes)
 
 
 def test_mid_config_scaled_stream():
@@ -158,17 +162,20 @@ def test_mid_config_scaled_stream():
             assert_state_equal(eng.state(), orc.state(), "batch %d" % k)
             n = 20_000
             bias = (np.arange(n) % 3).astype(np.uint8)
-            L = np.full(n, 40, np.int32)
-            g = eng.walks_mixed(torch.from_numpy(L).cuda(), torch.from_numpy(bias).cuda(),
-                                start_policy=_lib.START_BIASED_TS, seed=k)
-            torch.cuda.synchronize()
-            g = tuple(x.cpu().numpy() for x in g)
+            L = (5 + np.arange(n) % 36).astype(np.int32)   # mixed lengths, cap 40
             o = orc.walks(n, 40, bias_arr=bias, max_len_arr=L, start_policy=O.START_BIASED_TS, seed=k,
                           with_margin=True)
-            agree, total, div = compare_biased(g, o, o[3])
-            assert agree / total >= MIN_HOP_AGREEMENT
-            lin_or_uni = bias != 2
-            assert (g[0][lin_or_uni] == o[0][lin_or_uni]).all()
+            for sched in SCHEDULERS:
+                eng.set_scheduler(sched)
+                g = eng.walks_mixed(torch.from_numpy(L).cuda(), torch.from_numpy(bias).cuda(),
+                                    start_policy=_lib.START_BIASED_TS, seed=k, max_len_cap=40)
+                torch.cuda.synchronize()
+                g = tuple(x.cpu().numpy() for x in g)
+                agree, total, div = compare_biased(g, o, o[3])
+                assert agree / total >= MIN_HOP_AGREEMENT
+                lin_or_uni = bias != 2
+                assert (g[0][lin_or_uni] == o[0][lin_or_uni]).all()
+                assert (g[1][lin_or_uni] == o[1][lin_or_uni]).all()
 
 
 def test_host_and_device_outputs_agree():
