@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full size)")
     p.add_argument("--walks", type=int, default=10_000_000)
     p.add_argument("--max-len", type=int, default=80)
-    p.add_argument("--sched", default="full", choices=["stream", "full", "coop"])
+    p.add_argument("--sched", default="stream", choices=["stream", "full", "coop"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)

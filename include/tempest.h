@@ -64,10 +64,10 @@ enum { TEMPEST_START_UNIFORM_EDGE = 0, TEMPEST_START_BIASED_TS = 1 };
 /* Walk execution form (Sec. 2.4).  The result is the same for every form:
  * each walk draws from its own counter-based random stream. */
 enum {
-    TEMPEST_SCHED_FULL_WALK = 0, /* default: one thread carries one walk (Sec. 2.4.1) */
+    TEMPEST_SCHED_FULL_WALK = 0, /* one thread carries one walk (Sec. 2.4.1) */
     TEMPEST_SCHED_COOP = 1,      /* per-hop regrouping by node, thread / warp /
                                     block tiers (Sec. 2.4.3-2.4.5, Alg. 1) */
-    TEMPEST_SCHED_STREAM = 2     /* persistent lanes that refill from a
+    TEMPEST_SCHED_STREAM = 2     /* default: persistent lanes that refill from a
                                     work counter as walks end, one memory round
                                     trip per loop iteration, interpolation
                                     search of Gamma_t(v) (no counterpart in the
@@ -156,6 +156,15 @@ int tempest_walks(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int 
 int tempest_walks_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_arr,
                         int32_t max_len_cap, const uint8_t *bias_arr, int start_policy,
                         uint64_t seed, int32_t *node, int64_t *ts, int32_t *len);
+
+/* The closed-form samplers on their own (Sec. 2.5, Eq. 1-3): out[i] is the
+ * index in [0, n[i]) that `bias` selects for the uniform u = u_bits[i] * 2^-53,
+ * computed exactly as walk hops compute it.  u_bits: uint64[count], each
+ * < 2^53; n: int64[count], each in [1, 2^31); out: int64[count]; all device
+ * memory.  lambda > 0 is the exponential rate.  Queued on the handle's
+ * stream.  EINVAL on a bad bias, lambda, count < 0 or non-device arrays. */
+int tempest_sample_index(tempest_t *h, const uint64_t *u_bits, const int64_t *n, int64_t count, int bias,
+                         double lambda, int64_t *out);
 
 /* Select the walk execution form (TEMPEST_SCHED_*) for later walk calls. */
 int tempest_set_scheduler(tempest_t *h, int mode);

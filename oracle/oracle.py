@@ -65,6 +65,7 @@ def lib():
         L.orc_sampler_x.argtypes = [dbl, i64, ctypes.c_int, dbl]
         L.orc_sampler_index.restype = i64
         L.orc_sampler_index.argtypes = [dbl, i64, ctypes.c_int, dbl]
+        L.orc_sampler_batch.argtypes = [vp, vp, i64, ctypes.c_int, dbl, vp, vp]
         _lib = L
     return _lib
 
@@ -91,6 +92,16 @@ def sampler_x(u, n, bias, lam=1.0):
 
 def sampler_index(u, n, bias, lam=1.0):
     return lib().orc_sampler_index(float(u), int(n), int(bias), float(lam))
+
+
+def sampler_batch(k, n, bias, lam=1.0):
+    """(index int64[count], margin float64[count]) for u = k * 2^-53."""
+    k = np.ascontiguousarray(k, dtype=np.uint64)
+    n = np.ascontiguousarray(n, dtype=np.int64)
+    out = np.zeros(k.shape[0], np.int64)
+    mg = np.zeros(k.shape[0], np.float64)
+    lib().orc_sampler_batch(_p(k), _p(n), int(k.shape[0]), int(bias), float(lam), _p(out), _p(mg))
+    return out, mg
 
 
 class Oracle:

@@ -176,6 +176,23 @@ int64_t orc_sampler_index(double u, int64_t n, int bias, double lambda)
     return (int64_t)f;
 }
 
+/* Many draws: u = k[i] * 2^-53.  out[i] = index; margin[i] (nullable) =
+ * |x - nearest integer| / max(1, n[i]). */
+void orc_sampler_batch(const uint64_t *k, const int64_t *n, int64_t count, int bias, double lambda,
+                       int64_t *out, double *margin)
+{
+    for (int64_t i = 0; i < count; i++) {
+        double u = (double)(k[i] & ((1ull << 53) - 1)) * (1.0 / 9007199254740992.0);
+        out[i] = orc_sampler_index(u, n[i], bias, lambda);
+        if (margin) {
+            double x = orc_sampler_x(u, n[i], bias, lambda);
+            double r = x - floor(x + 0.5);
+            if (r < 0) r = -r;
+            margin[i] = (x == x) ? r / (n[i] > 1 ? (double)n[i] : 1.0) : 0.0;
+        }
+    }
+}
+
 /* uniform index in [0, n) from u (Eq. 1 with the clamp) */
 static int64_t uniform_index(double u, int64_t n)
 {

@@ -34,7 +34,7 @@ EXPORTED = (
     "tempest_set_bias_params", "tempest_ingest", "tempest_walks", "tempest_walks_mixed",
     "tempest_set_scheduler", "tempest_last_walk_stats", "tempest_get_counts",
     "tempest_export_state", "tempest_sync", "tempest_last_error", "tempest_version",
-    "tempest_sort_batch_noalloc",
+    "tempest_sort_batch_noalloc", "tempest_sample_index",
 )
 NOALLOC_MAX_EDGES = 262144
 
@@ -103,6 +103,7 @@ def load():
     L.tempest_last_error.restype = ctypes.c_char_p
     L.tempest_version.restype = ctypes.c_char_p
     L.tempest_sort_batch_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+    L.tempest_sample_index.argtypes = [vp, vp, vp, i64, ci, dbl, vp]
     for name in EXPORTED:
         if name not in ("tempest_last_error", "tempest_version"):
             getattr(L, name).restype = ci
@@ -166,6 +167,11 @@ def tempest_walks_mixed(h, n_walks, max_len_ptr, max_len_cap, bias_ptr, start_po
                                                 ctypes.c_uint64(int(seed) & (2**64 - 1)),
                                                 ctypes.c_void_p(node_ptr), ctypes.c_void_p(ts_ptr),
                                                 ctypes.c_void_p(len_ptr)))
+
+
+def tempest_sample_index(h, u_bits_ptr, n_ptr, count, bias, lam, out_ptr):
+    return _check(h, load().tempest_sample_index(h, ctypes.c_void_p(u_bits_ptr), ctypes.c_void_p(n_ptr),
+                                                 int(count), int(bias), float(lam), ctypes.c_void_p(out_ptr)))
 
 
 def tempest_set_scheduler(h, mode: int):

@@ -328,6 +328,18 @@ int tempest_walks_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_ar
                         ts, len);
 }
 
+int tempest_sample_index(tempest_t *h, const uint64_t *u_bits, const int64_t *n, int64_t count, int bias,
+                         double lambda, int64_t *out)
+{
+    if (!h) return TEMPEST_EINVAL;
+    if (count < 0 || bias < 0 || bias > 2 || !(lambda > 0.0))
+        return fail(h, TEMPEST_EINVAL, "tempest_sample_index: bad count, bias or lambda");
+    if (count == 0) return TEMPEST_OK;
+    if (!is_device_ptr(u_bits) || !is_device_ptr(n) || !is_device_ptr(out))
+        return fail(h, TEMPEST_EINVAL, "tempest_sample_index: arrays must be device memory");
+    return sample_index_run(h, u_bits, n, count, bias, lambda, out);
+}
+
 int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out)
 {
     if (!h || !out) return TEMPEST_EINVAL;

@@ -56,7 +56,7 @@ struct tempest {
     int directed = 1;
     double lam_hop = 1.0;
     double lam_start = 0.0;  // 0: 1 / G_tot
-    int sched = TEMPEST_SCHED_FULL_WALK;
+    int sched = TEMPEST_SCHED_STREAM;
     cudaStream_t stream = nullptr;
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*release_fn)(void *, void *) = nullptr;
@@ -135,5 +135,7 @@ struct WalkRequest {
     int32_t *len;              // device
 };
 int walks_run(tempest_t *h, const WalkRequest &rq);
+int sample_index_run(tempest_t *h, const uint64_t *ub, const int64_t *n, int64_t count, int bias, double lambda,
+                     int64_t *out);
 
 }  // namespace tw

@@ -89,6 +89,91 @@ __device__ __forceinline__ int64_t uniform_index(double u, int64_t n)
 }
 
 // ---------------------------------------------------------------------------
+// The same samplers without FP64 on the common path.  GB300 issues FP64 at a
+// small fraction of its FP32 / integer rate, so a walk that spends ~75 FP64
+// instructions per hop is bound by the FP64 pipe.  Each function below
+// returns exactly what the double-precision formula above returns.
+// A uniform is carried as its 53-bit integer k (u = k * 2^-53).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t u53_bits(uint32_t hi, uint32_t lo)
+{
+    return ((((uint64_t)hi) << 32) | lo) >> 11;
+}
+
+// floor(fl64(u * n)) clamped to n-1, for 1 <= n < 2^31, computed with
+// integers: P = k * n is exact in 128 bits; an IEEE double product keeps the
+// top 53 bits of P rounded to nearest-even, and the floor of that value is
+// a shift of the rounded significand.
+__device__ __forceinline__ int64_t uniform_index_k(uint64_t k, int64_t n)
+{
+    const uint64_t nn = (uint64_t)n;
+    const uint64_t lo = k * nn;
+    const uint64_t hi = __umul64hi(k, nn);
+    const int b = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+    if (b <= 53) return 0;  // P < 2^53: u * n < 1, no rounding
+    const int s = b - 53;   // 1 <= s <= 31 for n < 2^31
+    uint64_t q = (lo >> s) | (hi << (64 - s));
+    const uint64_t rem = lo & ((1ull << s) - 1ull);
+    const uint64_t half = 1ull << (s - 1);
+    if (rem > half || (rem == half && (q & 1ull))) q++;
+    const int64_t f = (int64_t)(q >> (53 - s));
+    return f < n - 1 ? f : n - 1;
+}
+
+// Exponential bias (weight exp(lambda*i), i in [0, n)).  The double formula
+// x = n + log(u + (1-u) exp(-lambda n)) / lambda is first evaluated in FP32
+// with a bound e on |y32 - y| (y = x - n), derived by first-order rounding
+// analysis with rho = 2^-24: u, n, lambda and lambda*n rounded (3 rho
+// relative on t = lambda n), expf <= 2 ulp, logf <= 1 ulp, the product with a
+// rounded 1/lambda:
+//   |s32 - s| / s <= rho (3 + m (5 + 3 t)),  m = min(1, E/u), E = e^-t
+//   e32 <= rho (3 + m (5 + 3 t)) / lambda + 4 rho |y|
+// plus the error of the double evaluation itself (e64, about 1e-16 n) and a
+// 1.5x margin.  When [y32 - e, y32 + e] holds no integer, floor(x) is n +
+// floor(y32) for both the exact value and the double evaluation; otherwise
+// the double formula decides.
+struct ExpRate {
+    double lambda;
+    float lam32;   // (float)lambda
+    float inv32;   // (float)(1 / lambda)
+};
+
+__device__ __forceinline__ int64_t exp_index_k(uint64_t k, int64_t n, const ExpRate &R)
+{
+    if (k == 0) return 0;  // u = 0 draws the oldest group for every n
+    const float rho = 5.9604644775390625e-8f;  // 2^-24
+    const float u = __ull2float_rn(k) * 1.1102230246251565e-16f;  // * 2^-53 (exact scaling)
+    const float nf = (float)n;
+    const float t = R.lam32 * nf;
+    const float E = expf(-t);
+    const float s = u + (1.0f - u) * E;
+    const float L = logf(s);
+    const float y = L * R.inv32;
+    if (s > 0.0f && isfinite(y)) {
+        const float m = fminf(1.0f, __fdividef(2.0f * E, u));
+        const float ay = fabsf(y);
+        float e = rho * (3.0f + m * (5.0f + 3.0f * t)) * R.inv32 + 4.0f * rho * ay;
+        e = 1.5f * e + 5e-16f * (nf + ay) + 1e-15f * R.inv32 + 2.0f * rho * ay + 1e-37f;
+        const float flo = floorf(y - e), fhi = floorf(y + e);
+        if (flo == fhi) {
+            const int64_t i = n + (int64_t)flo;
+            return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+        }
+    }
+    const double ud = __dmul_rn(__ull2double_rn(k), 1.1102230246251565404236316680908203125e-16);
+    return sampler_index(ud, n, BIAS_EXP, R.lambda);
+}
+
+// Index of the group / edge a draw selects, for any bias.
+__device__ __forceinline__ int64_t sampler_index_k(uint64_t k, int64_t n, int bias, const ExpRate &R)
+{
+    if (bias == BIAS_UNIFORM) return uniform_index_k(k, n);
+    if (bias == BIAS_EXP) return exp_index_k(k, n, R);
+    const double ud = __dmul_rn(__ull2double_rn(k), 1.1102230246251565404236316680908203125e-16);
+    return sampler_index(ud, n, BIAS_LINEAR, R.lambda);
+}
+
+// ---------------------------------------------------------------------------
 // warp / block helpers
 // ---------------------------------------------------------------------------
 template <typename T>

@@ -27,7 +27,7 @@ struct WalkView {
     const int64_t *ngts;   // [Gn]
     const Entry *ent;      // [M]
     int directed;
-    double lam_hop, lam_start;
+    ExpRate rate_hop, rate_start;
 };
 
 struct WalkOut {
@@ -94,15 +94,15 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
         if (V.m > 0) {
             // start edge (hop 0)
             Rand4 r = walk_rand(O.seed, (uint64_t)w, 0u);
-            double u1 = u53(r.r0, r.r1);
-            double u2 = u53(r.r2, r.r3);
+            const uint64_t k1 = u53_bits(r.r0, r.r1);
+            const uint64_t k2 = u53_bits(r.r2, r.r3);
             int64_t k;
             if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
-                k = uniform_index(u1, V.m);
+                k = uniform_index_k(k1, V.m);
             } else {
-                const int64_t g = sampler_index(u1, V.G, bias, V.lam_start);
+                const int64_t g = sampler_index_k(k1, V.G, bias, V.rate_start);
                 const int64_t a = V.ts_goff[g];
-                k = a + uniform_index(u2, (int64_t)V.ts_goff[g + 1] - a);
+                k = a + uniform_index_k(k2, (int64_t)V.ts_goff[g + 1] - a);
             }
             int32_t s = V.st_src[k], d = V.st_dst[k];
             const int64_t t0 = V.st_ts[k];
@@ -125,16 +125,16 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 const int32_t c = upper_bound_ts(V.ngts, g0, g1, t);
                 if (c == g1) break;  // Gamma_t(v) is empty
                 r = walk_rand(O.seed, (uint64_t)w, h);
-                u1 = u53(r.r0, r.r1);
+                const uint64_t h1 = u53_bits(r.r0, r.r1);
                 int64_t idx;
                 if (bias == BIAS_UNIFORM) {
                     const int32_t e0 = __ldg(V.ngo + c), e1 = __ldg(V.ngo + g1);
-                    idx = e0 + uniform_index(u1, (int64_t)(e1 - e0));
+                    idx = e0 + uniform_index_k(h1, (int64_t)(e1 - e0));
                 } else {
-                    u2 = u53(r.r2, r.r3);
-                    const int64_t j = sampler_index(u1, (int64_t)(g1 - c), bias, V.lam_hop);
+                    const uint64_t h2 = u53_bits(r.r2, r.r3);
+                    const int64_t j = sampler_index_k(h1, (int64_t)(g1 - c), bias, V.rate_hop);
                     const int32_t e0 = __ldg(V.ngo + c + j), e1 = __ldg(V.ngo + c + j + 1);
-                    idx = e0 + uniform_index(u2, (int64_t)(e1 - e0));
+                    idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
                 }
                 const Entry e = V.ent[idx];
                 nrow[len] = e.other;
@@ -193,7 +193,7 @@ struct SmLane {
     int64_t w;
     int64_t t;       // current time
     int64_t vL, vR;  // bracket values: a[L] <= t < a[R]
-    double ud;       // saved uniform for the draw inside a range
+    uint64_t ud;     // saved 53-bit uniform for the draw inside a range
     int32_t L, R;    // bracket
     int32_t g0, g1;  // group range of the current node
     int32_t v;       // current node
@@ -285,17 +285,17 @@ __global__ void __launch_bounds__(256) k_walks_stream(const WalkView V, const Wa
                     break;
                 }
                 const Rand4 r = walk_rand(O.seed, (uint64_t)s.w, 0u);
-                const double u1 = u53(r.r0, r.r1);
-                s.ud = u53(r.r2, r.r3);
+                const uint64_t u1 = u53_bits(r.r0, r.r1);
+                s.ud = u53_bits(r.r2, r.r3);
                 s.orient = (!V.directed && (r.r3 & 1u)) ? 1u : 0u;
                 if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
-                    const int64_t k = uniform_index(u1, V.m);
+                    const int64_t k = uniform_index_k(u1, V.m);
                     y0 = __ldg(V.st_ts + k);
                     z0 = __ldg(V.st_src + k);
                     z1 = __ldg(V.st_dst + k);
                     s.state = S_EDGE;
                 } else {
-                    const int64_t g = sampler_index(u1, V.G, bias, V.lam_start);
+                    const int64_t g = sampler_index_k(u1, V.G, bias, V.rate_start);
                     z0 = __ldg(V.ts_goff + g);
                     z1 = __ldg(V.ts_goff + g + 1);
                     s.state = S_SGROUP;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(256) k_walks_stream(const WalkView V, const Wa
                 break;
             }
             case S_SGROUP: {
-                const int64_t k = (int64_t)z0 + uniform_index(s.ud, (int64_t)(z1 - z0));
+                const int64_t k = (int64_t)z0 + uniform_index_k(s.ud, (int64_t)(z1 - z0));
                 y0 = __ldg(V.st_ts + k);
                 z0 = __ldg(V.st_src + k);
                 z1 = __ldg(V.st_dst + k);
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(256) k_walks_stream(const WalkView V, const Wa
                 break;
             }
             case S_PICK2: {
-                const int64_t idx = (int64_t)z0 + uniform_index(s.ud, (int64_t)(z1 - z0));
+                const int64_t idx = (int64_t)z0 + uniform_index_k(s.ud, (int64_t)(z1 - z0));
                 const Entry *e = V.ent + idx;
                 y0 = __ldg(&e->ts);
                 z0 = __ldg(&e->other);
@@ -427,14 +427,14 @@ __global__ void __launch_bounds__(256) k_walks_stream(const WalkView V, const Wa
             // c = s.R is the first group later than t; draw the next edge
             const int32_t c = s.R;
             const Rand4 r = walk_rand(O.seed, (uint64_t)s.w, s.hop);
-            const double u1 = u53(r.r0, r.r1);
+            const uint64_t u1 = u53_bits(r.r0, r.r1);
             if (s.bias == BIAS_UNIFORM) {
                 s.ud = u1;
                 z0 = __ldg(V.ngo + c);
                 z1 = __ldg(V.ngo + s.g1);
             } else {
-                s.ud = u53(r.r2, r.r3);
-                const int64_t j = sampler_index(u1, (int64_t)(s.g1 - c), s.bias, V.lam_hop);
+                s.ud = u53_bits(r.r2, r.r3);
+                const int64_t j = sampler_index_k(u1, (int64_t)(s.g1 - c), s.bias, V.rate_hop);
                 z0 = __ldg(V.ngo + c + j);
                 z1 = __ldg(V.ngo + c + j + 1);
             }
@@ -471,6 +471,29 @@ __global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, 
     }
 }
 
+__global__ void k_sample_index(const uint64_t *__restrict__ ub, const int64_t *__restrict__ n, int64_t count,
+                               int bias, ExpRate R, int64_t *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ub[i] & ((1ull << 53) - 1ull);
+        const int64_t m = n[i];
+        out[i] = m >= 1 ? sampler_index_k(k, m, bias, R) : 0;
+    }
+}
+
+int sample_index_run(tempest_t *h, const uint64_t *ub, const int64_t *n, int64_t count, int bias, double lambda,
+                     int64_t *out)
+{
+    if (count <= 0) return TEMPEST_OK;
+    const ExpRate R{lambda, (float)lambda, (float)(1.0 / lambda)};
+    int64_t grid = (count + 255) / 256;
+    const int64_t cap = (int64_t)h->num_sms * 16;
+    if (grid > cap) grid = cap;
+    k_sample_index<<<(unsigned)grid, 256, 0, h->stream>>>(ub, n, count, bias, R, out);
+    return cuda_check(h, cudaGetLastError(), "sample_index");
+}
+
 static WalkView make_view(tempest_t *h)
 {
     WalkView V;
@@ -485,8 +508,9 @@ static WalkView make_view(tempest_t *h)
     V.ngts = h->ngts.as<int64_t>();
     V.ent = h->ent.as<Entry>();
     V.directed = h->directed;
-    V.lam_hop = h->lam_hop;
-    V.lam_start = h->lam_start > 0.0 ? h->lam_start : (h->G > 0 ? 1.0 / (double)h->G : 1.0);
+    const double ls = h->lam_start > 0.0 ? h->lam_start : (h->G > 0 ? 1.0 / (double)h->G : 1.0);
+    V.rate_hop = ExpRate{h->lam_hop, (float)h->lam_hop, (float)(1.0 / h->lam_hop)};
+    V.rate_start = ExpRate{ls, (float)ls, (float)(1.0 / ls)};
     return V;
 }
 
