@@ -126,8 +126,10 @@ __device__ __forceinline__ int64_t uniform_index_k(uint64_t k, int64_t n)
 // analysis with rho = 2^-24: u, n, lambda and lambda*n rounded (3 rho
 // relative on t = lambda n), expf <= 2 ulp, logf <= 1 ulp, the product with a
 // rounded 1/lambda:
-//   |s32 - s| / s <= rho (3 + m (5 + 3 t)),  m = min(1, E/u), E = e^-t
-//   e32 <= rho (3 + m (5 + 3 t)) / lambda + 4 rho |y|
+//   |s32 - s| / s <= rho (4 + m (5 + 3 t)),  m = min(1, E/u), E = e^-t
+//   e32 <= rho (4 + m (5 + 3 t)) / lambda + 4 rho |y|
+// (u is formed from two 32-bit conversions and one add: 2 rho; only 32-bit
+// integer <-> float conversions are used, 64-bit ones run on the FP64 pipe)
 // plus the error of the double evaluation itself (e64, about 1e-16 n) and a
 // 1.5x margin.  When [y32 - e, y32 + e] holds no integer, floor(x) is n +
 // floor(y32) for both the exact value and the double evaluation; otherwise
@@ -142,21 +144,23 @@ __device__ __forceinline__ int64_t exp_index_k(uint64_t k, int64_t n, const ExpR
 {
     if (k == 0) return 0;  // u = 0 draws the oldest group for every n
     const float rho = 5.9604644775390625e-8f;  // 2^-24
-    const float u = __ull2float_rn(k) * 1.1102230246251565e-16f;  // * 2^-53 (exact scaling)
-    const float nf = (float)n;
+    // u = k * 2^-53 from the high 32 and low 21 bits of k
+    const float u = __uint2float_rn((uint32_t)(k >> 21)) * 2.3283064365386963e-10f +   // 2^-32
+                    __uint2float_rn((uint32_t)(k & 0x1FFFFFu)) * 1.1102230246251565e-16f;  // 2^-53
+    const float nf = __int2float_rn((int32_t)n);
     const float t = R.lam32 * nf;
     const float E = expf(-t);
     const float s = u + (1.0f - u) * E;
     const float L = logf(s);
     const float y = L * R.inv32;
-    if (s > 0.0f && isfinite(y)) {
+    if (s > 0.0f && isfinite(y) && y > -2.0e9f) {
         const float m = fminf(1.0f, __fdividef(2.0f * E, u));
         const float ay = fabsf(y);
-        float e = rho * (3.0f + m * (5.0f + 3.0f * t)) * R.inv32 + 4.0f * rho * ay;
+        float e = rho * (4.0f + m * (5.0f + 3.0f * t)) * R.inv32 + 4.0f * rho * ay;
         e = 1.5f * e + 5e-16f * (nf + ay) + 1e-15f * R.inv32 + 2.0f * rho * ay + 1e-37f;
         const float flo = floorf(y - e), fhi = floorf(y + e);
         if (flo == fhi) {
-            const int64_t i = n + (int64_t)flo;
+            const int64_t i = n + (int64_t)__float2int_rn(flo);
             return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
         }
     }

@@ -211,7 +211,12 @@ __device__ __forceinline__ int32_t interp_probe(int32_t L, int32_t R, int64_t vL
     // L < R - 1, vL <= t < vR.  The guess only steers the search (the
     // comparison against t is exact), so single precision is enough.
     if (bisect) return L + ((R - L) >> 1);
-    const float f = __fdividef((float)(t - vL), (float)(vR - vL));
+    // scale both differences into 31 bits so that only 32-bit integer to
+    // float conversions are needed (64-bit ones issue on the FP64 pipe)
+    const uint64_t d = (uint64_t)vR - (uint64_t)vL;
+    const uint64_t a = (uint64_t)t - (uint64_t)vL;
+    const int sh = max(0, 33 - __clzll((long long)d));
+    const float f = __fdividef((float)(uint32_t)(a >> sh), (float)(uint32_t)(d >> sh));
     int32_t p = L + 1 + (int32_t)(f * (float)(R - L - 1));
     if (p <= L) p = L + 1;
     if (p >= R) p = R - 1;
