@@ -122,7 +122,8 @@ int ensure(tempest_t *h, DBuf &b, size_t bytes, bool headroom)
 static void free_all(tempest_t *h)
 {
     DBuf *bufs[] = {&h->st_src[0], &h->st_src[1], &h->st_dst[0], &h->st_dst[1], &h->st_ts[0], &h->st_ts[1],
-                    &h->ts_goff,   &h->ent,       &h->ngo,       &h->ngts,      &h->gidx,     &h->b_src,
+                    &h->ts_goff,   &h->ent[0],    &h->ent[1],    &h->enode[0],  &h->enode[1],
+                    &h->noff[0],   &h->noff[1],   &h->ev,        &h->bcnt,      &h->bstart,    &h->ngo,       &h->ngts,      &h->gidx,     &h->b_src,
                     &h->b_dst,     &h->b_ts,      &h->sb_src,    &h->sb_dst,    &h->sb_ts,    &h->sk64[0],
                     &h->sk64[1],   &h->sk32[0],   &h->sk32[1],   &h->sv[0],     &h->sv[1],    &h->hist,
                     &h->partials,  &h->seg_node,  &h->seg_g,     &h->gcnt,      &h->dstat,    &h->wcnt,

@@ -80,7 +80,10 @@ struct tempest {
     tw::DBuf st_src[2], st_dst[2], st_ts[2];
     int cur = 0;
     tw::DBuf ts_goff;  // int32 [G+1]
-    tw::DBuf ent;      // Entry [M]
+    tw::DBuf ent[2];   // Entry [M]  node view entries (double buffered)
+    tw::DBuf enode[2]; // int32 [M]  node of each entry
+    tw::DBuf noff[2];  // int32 [N+1] start of each node's segment
+    int vcur = 0;      // which ent / enode / noff buffer is live
     tw::DBuf ngo;      // int32 [Gn+1] node group start offsets
     tw::DBuf ngts;     // int64 [Gn]   node group timestamps
     tw::DBuf gidx;     // int32 [N+1]  first group of each node
@@ -91,6 +94,7 @@ struct tempest {
     tw::DBuf sk64[2], sk32[2], sv[2];
     tw::DBuf hist, partials;
     tw::DBuf seg_node, seg_g, gcnt;
+    tw::DBuf ev, bcnt, bstart;   // per-node evicted / new entry counts, batch run starts
     tw::DBuf dstat;       // IngestScratch
     tw::DBuf wcnt;        // WalkCounters
     tw::DBuf out_stage;   // device staging of host walk outputs

@@ -228,13 +228,13 @@ struct StoreKeyLoader {
     __device__ __forceinline__ uint32_t val(int64_t i) const { return (uint32_t)i; }
 };
 
-__global__ void k_node_entries(const uint32_t *__restrict__ slots, const int32_t *__restrict__ src,
-                               const int32_t *__restrict__ dst, const int64_t *__restrict__ ts, int directed,
-                               int64_t M, Entry *E)
+__global__ void k_node_entries(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ slots,
+                               const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                               const int64_t *__restrict__ ts, int directed, int64_t M, Entry *E, int32_t *enode)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t slot = slots ? slots[i] : (uint32_t)i;
+        const uint32_t slot = slots[i];
         const int64_t pos = directed ? (int64_t)slot : (int64_t)(slot >> 1);
         const bool side = !directed && (slot & 1u);
         Entry e;
@@ -242,23 +242,23 @@ __global__ void k_node_entries(const uint32_t *__restrict__ slots, const int32_t
         e.other = side ? src[pos] : dst[pos];
         e.slot = (int32_t)slot;
         E[i] = e;
+        enode[i] = (int32_t)keys[i];
     }
 }
 
 // Packed counter: high 32 bits count node segments, low 32 bits count
 // (node, ts) groups.
 struct NodeGroupOp {
-    const uint32_t *keys;  // sorted node keys (nullptr: every key is 0)
+    const int32_t *enode;  // node of each entry (entries grouped by node)
     const Entry *E;
     int32_t *ngo;
     int64_t *ngts;
     int32_t *seg_node;
     int32_t *seg_g;
-    __device__ __forceinline__ uint32_t key(int64_t i) const { return keys ? keys[i] : 0u; }
     __device__ __forceinline__ uint64_t value(int64_t i) const
     {
         if (i == 0) return (1ull << 32) | 1ull;
-        const bool seg = key(i) != key(i - 1);
+        const bool seg = enode[i] != enode[i - 1];
         const bool grp = seg || E[i].ts != E[i - 1].ts;
         return ((uint64_t)seg << 32) | (uint64_t)grp;
     }
@@ -270,7 +270,7 @@ struct NodeGroupOp {
             ngts[g] = E[i].ts;
             if (v >> 32) {
                 const uint32_t j = (uint32_t)(ex >> 32);
-                seg_node[j] = (int32_t)key(i);
+                seg_node[j] = enode[i];
                 seg_g[j] = (int32_t)g;
             }
         }
@@ -312,6 +312,115 @@ __global__ void k_node_order(const Entry *__restrict__ E, int64_t M, int32_t *ou
         out[i] = E[i].slot;
 }
 
+// ---- incremental node view (the batch starts no earlier than the store ends)
+
+// Entries of the evicted store prefix [0, i0), counted per node.  Every
+// node loses a prefix of its segment: eviction removes the oldest edges.
+__global__ void k_evict_counts(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t items,
+                               int directed, int32_t *ev)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = directed ? src[i] : ((i & 1) ? dst[i >> 1] : src[i >> 1]);
+        const unsigned am = __activemask();
+        const unsigned peers = __match_any_sync(am, v);
+        if (lane == __ffs(peers) - 1) atomicAdd(&ev[v], __popc(peers));
+    }
+}
+
+// (node, slot) pairs of the batch's entries, slots numbered in the new store
+// where the batch occupies positions [base, base + nb).
+struct BatchKeyLoader {
+    const int32_t *src, *dst;
+    int directed;
+    int64_t base;
+    __device__ __forceinline__ uint32_t key(int64_t i) const
+    {
+        if (directed) return (uint32_t)src[base + i];
+        return (uint32_t)((i & 1) ? dst[base + (i >> 1)] : src[base + (i >> 1)]);
+    }
+    __device__ __forceinline__ uint32_t val(int64_t i) const
+    {
+        return (uint32_t)(directed ? base + i : 2 * base + i);
+    }
+};
+
+// Runs of equal nodes in the sorted batch keys: bstart[v] = first index,
+// bcnt[v] = run length (bcnt starts at 0; pass 0 stores the run end, pass 1
+// subtracts the start).
+__global__ void k_batch_runs(const uint32_t *__restrict__ K, int64_t n, int pass, int32_t *bstart, int32_t *bcnt)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = K[j];
+        if (pass == 0) {
+            if (j == 0 || K[j - 1] != v) bstart[v] = (int32_t)j;
+            if (j == n - 1 || K[j + 1] != v) bcnt[v] = (int32_t)(j + 1);
+        } else if (j == 0 || K[j - 1] != v) {
+            bcnt[v] -= (int32_t)j;
+        }
+    }
+}
+
+// New segment starts: kept old entries plus new entries, per node.
+struct NoffOp {
+    const int32_t *noff_old;
+    int64_t N_old;
+    const int32_t *ev;
+    const int32_t *bcnt;
+    int64_t N;
+    int32_t *noff_new;
+    __device__ __forceinline__ uint64_t value(int64_t v) const
+    {
+        if (v >= N) return 0;
+        const int32_t old = v < N_old ? noff_old[v + 1] - noff_old[v] : 0;
+        return (uint64_t)(old - ev[v] + bcnt[v]);
+    }
+    __device__ __forceinline__ void emit(int64_t v, uint64_t, uint64_t ex) const { noff_new[v] = (int32_t)ex; }
+};
+
+// Kept old entries move by a per-node shift; their slots shift by E0 (the
+// evicted store prefix, in slots).
+__global__ void k_copy_kept(const Entry *__restrict__ E_old, const int32_t *__restrict__ enode_old, int64_t M_old,
+                            const int32_t *__restrict__ noff_old, const int32_t *__restrict__ ev,
+                            const int32_t *__restrict__ noff_new, int32_t E0, Entry *E_new, int32_t *enode_new)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M_old;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Entry e = E_old[i];
+        if (e.slot < E0) continue;  // evicted
+        const int32_t v = enode_old[i];
+        const int64_t p = (int64_t)noff_new[v] + (i - noff_old[v] - ev[v]);
+        e.slot -= E0;
+        E_new[p] = e;
+        enode_new[p] = v;
+    }
+}
+
+// New entries go after the kept ones of their node, in slot order.
+__global__ void k_scatter_batch(const uint32_t *__restrict__ K, const uint32_t *__restrict__ V, int64_t n,
+                                const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcnt,
+                                const int32_t *__restrict__ noff_new, const int32_t *__restrict__ src,
+                                const int32_t *__restrict__ dst, const int64_t *__restrict__ ts, int directed,
+                                Entry *E_new, int32_t *enode_new)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = K[j];
+        const uint32_t slot = V[j];
+        const int64_t p = (int64_t)noff_new[v + 1] - bcnt[v] + (j - bstart[v]);
+        const int64_t pos = directed ? (int64_t)slot : (int64_t)(slot >> 1);
+        const bool side = !directed && (slot & 1u);
+        Entry e;
+        e.ts = ts[pos];
+        e.other = side ? src[pos] : dst[pos];
+        e.slot = (int32_t)slot;
+        E_new[p] = e;
+        enode_new[p] = (int32_t)v;
+    }
+}
+
 static unsigned grid_for(tempest_t *h, int64_t n, int threads = 256)
 {
     int64_t g = (n + threads - 1) / threads;
@@ -323,13 +432,14 @@ static unsigned grid_for(tempest_t *h, int64_t n, int threads = 256)
 
 void launch_node_off(tempest_t *h, int32_t *node_off)
 {
-    k_node_off<<<grid_for(h, h->N + 1), 256, 0, h->stream>>>(h->gidx.as<int32_t>(), h->ngo.as<int32_t>(), h->N,
-                                                           node_off);
+    cudaMemcpyAsync(node_off, h->noff[h->vcur].p, sizeof(int32_t) * (size_t)(h->N + 1), cudaMemcpyDeviceToDevice,
+                    h->stream);
 }
 
 void launch_node_order(tempest_t *h, int32_t *node_order)
 {
-    if (h->M > 0) k_node_order<<<grid_for(h, h->M), 256, 0, h->stream>>>(h->ent.as<Entry>(), h->M, node_order);
+    if (h->M > 0)
+        k_node_order<<<grid_for(h, h->M), 256, 0, h->stream>>>(h->ent[h->vcur].as<Entry>(), h->M, node_order);
 }
 
 static int bits_for(uint64_t maxval)
@@ -339,65 +449,63 @@ static int bits_for(uint64_t maxval)
     return b;
 }
 
-// Rebuild both views over the store in buffer h->cur with h->m live edges.
-static int rebuild_views(tempest_t *h)
+// timestamp-grouped view over the store in buffer h->cur
+static int rebuild_ts_view(tempest_t *h)
 {
     cudaStream_t st = h->stream;
     const int64_t m = h->m;
-    const int32_t *src = h->st_src[h->cur].as<int32_t>();
-    const int32_t *dst = h->st_dst[h->cur].as<int32_t>();
     const int64_t *ts = h->st_ts[h->cur].as<int64_t>();
     uint64_t *hpart = static_cast<uint64_t *>(h->hstat);
     int rc;
-
-    // timestamp-grouped view
     if ((rc = ensure(h, h->ts_goff, sizeof(int32_t) * (size_t)(m + 1), true))) return rc;
-    {
-        TsGroupOp op{ts, h->ts_goff.as<int32_t>()};
-        const int nb = scan_launch(op, m, h->partials.as<uint64_t>(), st);
-        cudaMemcpyAsync(hpart, h->partials.as<uint64_t>() + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-        h->pending_launches += 3;
-    }
+    TsGroupOp op{ts, h->ts_goff.as<int32_t>()};
+    const int nb = scan_launch(op, m, h->partials.as<uint64_t>(), st);
+    cudaMemcpyAsync(hpart, h->partials.as<uint64_t>() + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    h->pending_launches += 3;
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ts view"))) return rc;
     h->G = (int64_t)hpart[0];
     k_set_i32<<<1, 1, 0, st>>>(h->ts_goff.as<int32_t>() + h->G, (int32_t)m);
     h->pending_launches++;
+    return TEMPEST_OK;
+}
 
-    // node-and-timestamp-grouped view
-    const int64_t M = h->directed ? m : 2 * m;
-    const int64_t N = h->N;
-    if ((rc = ensure(h, h->ent, sizeof(Entry) * (size_t)(M > 0 ? M : 1), true))) return rc;
+static int ensure_view_buffers(tempest_t *h, int nxt, int64_t M, int64_t N)
+{
+    int rc;
+    const size_t Mz = (size_t)(M > 0 ? M : 1);
+    if ((rc = ensure(h, h->ent[nxt], sizeof(Entry) * Mz, true))) return rc;
+    if ((rc = ensure(h, h->enode[nxt], sizeof(int32_t) * Mz, true))) return rc;
+    if ((rc = ensure(h, h->noff[nxt], sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
     if ((rc = ensure(h, h->ngo, sizeof(int32_t) * (size_t)(M + 1), true))) return rc;
-    if ((rc = ensure(h, h->ngts, sizeof(int64_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->ngts, sizeof(int64_t) * Mz, true))) return rc;
     if ((rc = ensure(h, h->gidx, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
     if ((rc = ensure(h, h->gcnt, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
-    if ((rc = ensure(h, h->seg_node, sizeof(int32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
-    if ((rc = ensure(h, h->seg_g, sizeof(int32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
-    if ((rc = ensure(h, h->sk32[0], sizeof(uint32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
-    if ((rc = ensure(h, h->sk32[1], sizeof(uint32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
-    if ((rc = ensure(h, h->sv[0], sizeof(uint32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
-    if ((rc = ensure(h, h->sv[1], sizeof(uint32_t) * (size_t)(M > 0 ? M : 1), true))) return rc;
+    if ((rc = ensure(h, h->seg_node, sizeof(int32_t) * Mz, true))) return rc;
+    if ((rc = ensure(h, h->seg_g, sizeof(int32_t) * Mz, true))) return rc;
+    return TEMPEST_OK;
+}
 
-    const uint32_t *keys = nullptr;
-    const uint32_t *slots = nullptr;
-    if (M > 0) {
-        StoreKeyLoader ld{src, dst, h->directed};
-        uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
-        uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
-        int launches = 0;
-        const int r = radix_sort_launch<uint32_t>(ld, M, bits_for((uint64_t)(N > 0 ? N - 1 : 0)), kb, vb,
-                                                  h->hist.as<uint32_t>(), st, &launches);
-        h->pending_launches += launches;
-        if (r >= 0) {
-            keys = kb[r];
-            slots = vb[r];
-        }
-        k_node_entries<<<grid_for(h, M), 256, 0, st>>>(slots, src, dst, ts, h->directed, M, h->ent.as<Entry>());
-        h->pending_launches++;
+static int ensure_sort_buffers(tempest_t *h, int64_t n)
+{
+    int rc;
+    const size_t z = (size_t)(n > 0 ? n : 1);
+    for (int b = 0; b < 2; b++) {
+        if ((rc = ensure(h, h->sk32[b], sizeof(uint32_t) * z, true))) return rc;
+        if ((rc = ensure(h, h->sv[b], sizeof(uint32_t) * z, true))) return rc;
     }
+    return TEMPEST_OK;
+}
+
+// Groups and per-node first groups over the entries in buffer nxt (common to
+// both paths); the full path also derives the segment starts from them.
+static int node_view_groups(tempest_t *h, int nxt, int64_t M, int64_t N, bool need_noff)
+{
+    cudaStream_t st = h->stream;
+    uint64_t *hpart = static_cast<uint64_t *>(h->hstat);
+    int rc;
     {
-        NodeGroupOp op{keys, h->ent.as<Entry>(), h->ngo.as<int32_t>(), h->ngts.as<int64_t>(),
-                       h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>()};
+        NodeGroupOp op{h->enode[nxt].as<int32_t>(), h->ent[nxt].as<Entry>(), h->ngo.as<int32_t>(),
+                       h->ngts.as<int64_t>(), h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>()};
         const int nb = scan_launch(op, M, h->partials.as<uint64_t>(), st);
         cudaMemcpyAsync(hpart, h->partials.as<uint64_t>() + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
         h->pending_launches += 3;
@@ -407,7 +515,6 @@ static int rebuild_views(tempest_t *h)
     const int64_t Gn = M > 0 ? (int64_t)(uint32_t)tot : 0;
     const int64_t S = M > 0 ? (int64_t)(tot >> 32) : 0;
     h->Gn = Gn;
-    h->M = M;
     k_set_i32<<<1, 1, 0, st>>>(h->ngo.as<int32_t>() + Gn, (int32_t)M);
     cudaMemsetAsync(h->gcnt.as<int32_t>(), 0, sizeof(int32_t) * (size_t)(N + 1), st);
     if (S > 0)
@@ -418,7 +525,119 @@ static int rebuild_views(tempest_t *h)
         scan_launch(op, N + 1, h->partials.as<uint64_t>(), st);
     }
     h->pending_launches += 5;
-    return cuda_check(h, cudaGetLastError(), "rebuild views");
+    if (need_noff) {
+        k_node_off<<<grid_for(h, N + 1), 256, 0, st>>>(h->gidx.as<int32_t>(), h->ngo.as<int32_t>(), N,
+                                                      h->noff[nxt].as<int32_t>());
+        h->pending_launches++;
+    }
+    return cuda_check(h, cudaGetLastError(), "node view groups");
+}
+
+// Full rebuild: stable radix sort of every (node, slot) pair by node.
+static int node_view_full(tempest_t *h)
+{
+    cudaStream_t st = h->stream;
+    const int64_t m = h->m;
+    const int32_t *src = h->st_src[h->cur].as<int32_t>();
+    const int32_t *dst = h->st_dst[h->cur].as<int32_t>();
+    const int64_t *ts = h->st_ts[h->cur].as<int64_t>();
+    const int64_t M = h->directed ? m : 2 * m;
+    const int64_t N = h->N;
+    const int nxt = h->vcur ^ 1;
+    int rc;
+    if ((rc = ensure_view_buffers(h, nxt, M, N))) return rc;
+    if ((rc = ensure_sort_buffers(h, M))) return rc;
+    if (M > 0) {
+        StoreKeyLoader ld{src, dst, h->directed};
+        uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
+        uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
+        int launches = 0;
+        int bits = bits_for((uint64_t)(N > 0 ? N - 1 : 0));
+        if (bits < 1) bits = 1;  // one pass keeps the order and materialises the pairs
+        const int r = radix_sort_launch<uint32_t>(ld, M, bits, kb, vb, h->hist.as<uint32_t>(), st, &launches);
+        h->pending_launches += launches + 1;
+        k_node_entries<<<grid_for(h, M), 256, 0, st>>>(kb[r], vb[r], src, dst, ts, h->directed, M,
+                                                       h->ent[nxt].as<Entry>(), h->enode[nxt].as<int32_t>());
+    }
+    if ((rc = node_view_groups(h, nxt, M, N, true))) return rc;
+    h->M = M;
+    h->vcur = nxt;
+    return TEMPEST_OK;
+}
+
+// Incremental update after an append: every node keeps a suffix of its old
+// segment (the evicted edges are the oldest) and gains the batch's entries
+// at the end.  Gives exactly the order of the full rebuild.
+//   i0:   evicted prefix of the old store (in the buffer before h->cur)
+//   na:   kept old edges (they are positions [0, na) of the new store)
+//   nbk:  batch edges appended at positions [na, na + nbk)
+static int node_view_append(tempest_t *h, int64_t i0, int64_t na, int64_t nbk, int64_t N_old, int64_t M_old)
+{
+    cudaStream_t st = h->stream;
+    const int old_store = h->cur ^ 1;
+    const int32_t *src = h->st_src[h->cur].as<int32_t>();
+    const int32_t *dst = h->st_dst[h->cur].as<int32_t>();
+    const int64_t *ts = h->st_ts[h->cur].as<int64_t>();
+    const int directed = h->directed;
+    const int64_t M = directed ? h->m : 2 * h->m;
+    const int64_t N = h->N;
+    const int vold = h->vcur, nxt = h->vcur ^ 1;
+    const int64_t nbe = directed ? nbk : 2 * nbk;   // new entries
+    const int64_t evi = directed ? i0 : 2 * i0;     // evicted entries
+    int rc;
+    if ((rc = ensure_view_buffers(h, nxt, M, N))) return rc;
+    if ((rc = ensure_sort_buffers(h, nbe))) return rc;
+    if ((rc = ensure(h, h->ev, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
+    if ((rc = ensure(h, h->bcnt, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
+    if ((rc = ensure(h, h->bstart, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
+    int32_t *ev = h->ev.as<int32_t>();
+    int32_t *bcnt = h->bcnt.as<int32_t>();
+    int32_t *bstart = h->bstart.as<int32_t>();
+
+    cudaMemsetAsync(ev, 0, sizeof(int32_t) * (size_t)N, st);
+    cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * (size_t)N, st);
+    if (evi > 0)
+        k_evict_counts<<<grid_for(h, evi), 256, 0, st>>>(h->st_src[old_store].as<int32_t>(),
+                                                        h->st_dst[old_store].as<int32_t>(), evi, directed, ev);
+    const uint32_t *Kb = nullptr, *Vb = nullptr;
+    if (nbe > 0) {
+        BatchKeyLoader ld{src, dst, directed, na};
+        uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
+        uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
+        int launches = 0;
+        int bits = bits_for((uint64_t)(N > 0 ? N - 1 : 0));
+        if (bits < 1) bits = 1;
+        const int r = radix_sort_launch<uint32_t>(ld, nbe, bits, kb, vb, h->hist.as<uint32_t>(), st, &launches);
+        h->pending_launches += launches;
+        Kb = kb[r];
+        Vb = vb[r];
+        k_batch_runs<<<grid_for(h, nbe), 256, 0, st>>>(Kb, nbe, 0, bstart, bcnt);
+        k_batch_runs<<<grid_for(h, nbe), 256, 0, st>>>(Kb, nbe, 1, bstart, bcnt);
+        h->pending_launches += 2;
+    }
+    {
+        NoffOp op{h->noff[vold].as<int32_t>(), N_old, ev, bcnt, N, h->noff[nxt].as<int32_t>()};
+        scan_launch(op, N + 1, h->partials.as<uint64_t>(), st);
+        h->pending_launches += 3;
+    }
+    if (M_old > 0) {
+        k_copy_kept<<<grid_for(h, M_old), 256, 0, st>>>(h->ent[vold].as<Entry>(), h->enode[vold].as<int32_t>(),
+                                                       M_old, h->noff[vold].as<int32_t>(), ev,
+                                                       h->noff[nxt].as<int32_t>(), (int32_t)evi,
+                                                       h->ent[nxt].as<Entry>(), h->enode[nxt].as<int32_t>());
+        h->pending_launches++;
+    }
+    if (nbe > 0) {
+        k_scatter_batch<<<grid_for(h, nbe), 256, 0, st>>>(Kb, Vb, nbe, bstart, bcnt, h->noff[nxt].as<int32_t>(), src,
+                                                         dst, ts, directed, h->ent[nxt].as<Entry>(),
+                                                         h->enode[nxt].as<int32_t>());
+        h->pending_launches++;
+    }
+    h->pending_launches += (evi > 0) ? 1 : 0;
+    if ((rc = node_view_groups(h, nxt, M, N, false))) return rc;
+    h->M = M;
+    h->vcur = nxt;
+    return TEMPEST_OK;
 }
 
 int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in, int64_t n,
@@ -526,6 +745,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
 
     // 4. merge into the other store buffer
     const int nxt = h->cur ^ 1;
+    const bool append = na == 0 || nbk == 0 || hs->store_last_ts <= hs->kept_batch_min_ts;
     if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
     if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
     if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
@@ -536,7 +756,6 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
         int32_t *os = h->st_src[nxt].as<int32_t>();
         int32_t *od = h->st_dst[nxt].as<int32_t>();
         int64_t *ot = h->st_ts[nxt].as<int64_t>();
-        const bool append = na == 0 || nbk == 0 || hs->store_last_ts <= hs->kept_batch_min_ts;
         if (append) {
             if (na > 0) {
                 cudaMemcpyAsync(os, as, sizeof(int32_t) * (size_t)na, cudaMemcpyDeviceToDevice, st);
@@ -558,6 +777,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     if ((rc = cuda_check(h, cudaGetLastError(), "merge"))) return rc;
 
     // commit the new store and counters
+    const int64_t N_old = h->N, M_old = h->M;
     h->cur = nxt;
     h->m = m_new;
     h->N = N_new;
@@ -568,8 +788,12 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     h->has_cutoff = hs->has_cut;
     h->cutoff = hs->cut;
 
-    // 5-6. views
-    if ((rc = rebuild_views(h))) return rc;
+    // 5-6. views: incremental node view after an append, full rebuild after
+    // a general merge (or before any view exists)
+    if ((rc = rebuild_ts_view(h))) return rc;
+    if (append && h->ent[h->vcur].p) rc = node_view_append(h, i0, na, nbk, N_old, M_old);
+    else rc = node_view_full(h);
+    if (rc) return rc;
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ingest"))) return rc;
 
     if (stats) {

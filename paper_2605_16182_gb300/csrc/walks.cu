@@ -511,7 +511,7 @@ static WalkView make_view(tempest_t *h)
     V.gidx = h->gidx.as<int32_t>();
     V.ngo = h->ngo.as<int32_t>();
     V.ngts = h->ngts.as<int64_t>();
-    V.ent = h->ent.as<Entry>();
+    V.ent = h->ent[h->vcur].as<Entry>();
     V.directed = h->directed;
     const double ls = h->lam_start > 0.0 ? h->lam_start : (h->G > 0 ? 1.0 / (double)h->G : 1.0);
     V.rate_hop = ExpRate{h->lam_hop, (float)h->lam_hop, (float)(1.0 / h->lam_hop)};
