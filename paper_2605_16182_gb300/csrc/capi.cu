@@ -26,20 +26,29 @@ __global__ void k_scan_partials(uint64_t *p, int nb)
     if (threadIdx.x == 0) p[nb] = carry;
 }
 
+// One block; every warp owns a contiguous slice and reads it 32 elements at
+// a time (coalesced): pass 1 sums the slices, pass 2 rescans them in place.
 __global__ void k_scan_u32_small(uint32_t *a, int64_t n)
 {
     __shared__ uint32_t sh[33];
-    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-    const int64_t b0 = (int64_t)threadIdx.x * per;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t per = (n + nw - 1) / nw;
+    per = (per + 31) & ~(int64_t)31;
+    const int64_t b0 = (int64_t)w * per;
     const int64_t b1 = min(n, b0 + per);
     uint32_t s = 0;
-    for (int64_t i = b0; i < b1; i++) s += a[i];
+    for (int64_t i = b0 + lane; i < b1; i += 32) s += a[i];
+    s = warp_sum(s);
+    // block scan over warp sums: lane 0 of each warp contributes
     uint32_t tot;
-    uint32_t ex = block_excl_scan<uint32_t>(s, sh, tot);
-    for (int64_t i = b0; i < b1; i++) {
-        const uint32_t v = a[i];
-        a[i] = ex;
-        ex += v;
+    uint32_t ex = block_excl_scan<uint32_t>(lane == 0 ? s : 0u, sh, tot);
+    uint32_t carry = __shfl_sync(0xffffffffu, ex, 0);
+    for (int64_t base = b0; base < b1; base += 32) {
+        const int64_t i = base + lane;
+        const uint32_t v = i < b1 ? a[i] : 0u;
+        const uint32_t inc = warp_incl_scan(v);
+        if (i < b1) a[i] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
     }
 }
 

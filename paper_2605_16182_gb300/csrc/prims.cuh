@@ -259,34 +259,55 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Op op, int64_t n, 
 // partials[nb] receives the total.
 __global__ void k_scan_partials(uint64_t *partials, int nb);
 
+// Each chunk of SCAN_CHUNK elements is read and written in striped order
+// (element c + k*THREADS + thread, so a warp touches consecutive elements) and
+// staged through shared memory, where each thread scans SCAN_ITEMS
+// consecutive values.
 template <class Op>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_emit(Op op, int64_t n, int64_t per_blk,
                                                             const uint64_t *partials)
 {
     __shared__ uint64_t wt[33];
+    __shared__ uint64_t sv[SCAN_CHUNK];   // values, then exclusive prefixes
     const int64_t b0 = (int64_t)blockIdx.x * per_blk;
     const int64_t b1 = min(n, b0 + per_blk);
     uint64_t carry = partials[blockIdx.x];
     for (int64_t c = b0; c < b1; c += SCAN_CHUNK) {
-        const int64_t i0 = c + (int64_t)threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            const int j = k * SCAN_THREADS + threadIdx.x;
+            const int64_t i = c + j;
+            sv[j] = (i < b1) ? op.value(i) : 0;
+        }
+        __syncthreads();
         uint64_t v[SCAN_ITEMS];
         uint64_t s = 0;
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; k++) {
-            const int64_t i = i0 + k;
-            v[k] = (i < b1) ? op.value(i) : 0;
+            v[k] = sv[threadIdx.x * SCAN_ITEMS + k];
             s += v[k];
         }
         uint64_t tot;
-        uint64_t ex = block_excl_scan<uint64_t>(s, wt, tot);
+        uint64_t ex = block_excl_scan<uint64_t>(s, wt, tot);  // synchronises
         ex += carry;
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; k++) {
-            const int64_t i = i0 + k;
-            if (i < b1) op.emit(i, v[k], ex);
+            sv[threadIdx.x * SCAN_ITEMS + k] = ex;
             ex += v[k];
         }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            const int j = k * SCAN_THREADS + threadIdx.x;
+            const int64_t i = c + j;
+            if (i < b1) {
+                const uint64_t e = sv[j];
+                const uint64_t nx = (j + 1 < SCAN_CHUNK) ? sv[j + 1] : carry + tot;
+                op.emit(i, nx - e, e);
+            }
+        }
         carry += tot;
+        __syncthreads();
     }
 }
 
