@@ -95,6 +95,9 @@ typedef struct {
     int64_t hops;          /* edges traversed, start edge included */
     int64_t model_bytes;   /* sum of the per-hop sector model over the hops */
     int64_t launches;      /* kernels this library launched for the call */
+    int64_t tier_launches[5]; /* TEMPEST_SCHED_COOP: terminal-kernel launches
+                                 per tier (solo, warp-smem, warp-global,
+                                 block-smem, block-global) */
 } tempest_walk_stats;
 
 /* Create an engine.  window > 0: duration Delta in timestamp units, the

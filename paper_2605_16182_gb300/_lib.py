@@ -59,10 +59,13 @@ class IngestStats(ctypes.Structure):
 
 class WalkStats(ctypes.Structure):
     _fields_ = [("n_walks", ctypes.c_int64), ("hops", ctypes.c_int64),
-                ("model_bytes", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("model_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("tier_launches", ctypes.c_int64 * 5)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["tier_launches"] = list(self.tier_launches)
+        return d
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

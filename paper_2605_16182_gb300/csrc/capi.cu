@@ -136,7 +136,9 @@ static void free_all(tempest_t *h)
                     &h->b_dst,     &h->b_ts,      &h->sb_src,    &h->sb_dst,    &h->sb_ts,    &h->sk64[0],
                     &h->sk64[1],   &h->sk32[0],   &h->sk32[1],   &h->sv[0],     &h->sv[1],    &h->hist,
                     &h->partials,  &h->seg_node,  &h->seg_g,     &h->gcnt,      &h->dstat,    &h->wcnt,
-                    &h->out_stage, &h->in_stage,  &h->exp_stage};
+                    &h->out_stage, &h->in_stage,  &h->exp_stage,
+                    &h->co_node,   &h->co_t,      &h->co_len,    &h->co_act[0], &h->co_act[1], &h->co_runs,
+                    &h->co_tasks,  &h->co_ctr};
     for (DBuf *b : bufs) release(h, *b);
 }
 

@@ -95,6 +95,11 @@ struct tempest {
     tw::DBuf hist, partials;
     tw::DBuf seg_node, seg_g, gcnt;
     tw::DBuf ev, bcnt, bstart;   // per-node evicted / new entry counts, batch run starts
+    // cooperative scheduler: walk state, active lists, runs, tier tasks, counters
+    tw::DBuf co_node, co_t, co_len, co_act[2], co_runs, co_tasks, co_ctr;
+    int coop_w_warp = 4;         // solo / warp boundary W_warp (Sec. 3.5)
+    int coop_mega = 8192;        // mega-hub split (Sec. 2.4.4)
+    int64_t coop_tier_launches[5] = {0, 0, 0, 0, 0};
     tw::DBuf dstat;       // IngestScratch
     tw::DBuf wcnt;        // WalkCounters
     tw::DBuf out_stage;   // device staging of host walk outputs

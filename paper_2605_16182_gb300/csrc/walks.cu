@@ -9,70 +9,9 @@
 // threads.
 #include "engine.cuh"
 #include "prims.cuh"
+#include "walkcore.cuh"
 
 namespace tw {
-
-struct WalkView {
-    // edge store, (ts, arrival) order
-    const int32_t *st_src;
-    const int32_t *st_dst;
-    const int64_t *st_ts;
-    int64_t m;
-    // timestamp-grouped view
-    const int32_t *ts_goff;
-    int64_t G;
-    // node view
-    const int32_t *gidx;   // [N+1]
-    const int32_t *ngo;    // [Gn+1]
-    const int64_t *ngts;   // [Gn]
-    const Entry *ent;      // [M]
-    int directed;
-    ExpRate rate_hop, rate_start;
-};
-
-struct WalkOut {
-    int64_t n_walks;
-    int32_t cap;
-    int32_t max_len;
-    const int32_t *len_arr;
-    int bias;
-    const uint8_t *bias_arr;
-    int start_policy;
-    uint64_t seed;
-    int32_t *node;
-    int64_t *ts;
-    int32_t *len;
-    WalkCounters *cnt;
-};
-
-// first index in [lo, hi) whose group timestamp is > t
-__device__ __forceinline__ int32_t upper_bound_ts(const int64_t *__restrict__ gts, int32_t lo, int32_t hi,
-                                                  int64_t t)
-{
-    while (lo < hi) {
-        const int32_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(gts + mid) > t) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int ceil_log2_plus1(int64_t G)
-{
-    // ceil(log2(G + 1)) for G >= 0
-    return 64 - __clzll((unsigned long long)G);
-}
-
-// Sector model of one hop's traffic at a node with G groups: range read,
-// binary search (last two levels share a sector), chosen entry, output write
-// (node + ts) and walk state read + write.
-__device__ __forceinline__ unsigned long long hop_model_bytes(int64_t G)
-{
-    int s = ceil_log2_plus1(G) - 2;
-    if (s < 1) s = 1;
-    return 32ull * (unsigned long long)(1 + s + 1) + 12ull + 16ull;
-}
-constexpr unsigned long long START_MODEL_BYTES = 3 * 32 + 4 + 4 + 8 + 8 + 4;
 
 __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const WalkOut O)
 {
@@ -499,7 +438,7 @@ int sample_index_run(tempest_t *h, const uint64_t *ub, const int64_t *n, int64_t
     return cuda_check(h, cudaGetLastError(), "sample_index");
 }
 
-static WalkView make_view(tempest_t *h)
+WalkView make_view(tempest_t *h)
 {
     WalkView V;
     V.st_src = h->st_src[h->cur].as<int32_t>();
@@ -540,8 +479,17 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     O.len = rq.len;
     O.cnt = h->wcnt.as<WalkCounters>();
     int64_t launches = 0;
+    for (int t = 0; t < 5; t++) h->coop_tier_launches[t] = 0;
     if (rq.n_walks > 0) {
-        if (h->sched == TEMPEST_SCHED_FULL_WALK) {
+        if (h->sched == TEMPEST_SCHED_COOP) {
+            int rc2 = coop_run(h, V, O, launches);
+            if (rc2) return rc2;
+            int64_t pgrid = (rq.n_walks + 7) / 8;
+            const int64_t pcap = (int64_t)h->num_sms * 16;
+            if (pgrid > pcap) pgrid = pcap;
+            k_pad_rows<<<(unsigned)pgrid, 256, 0, st>>>(rq.n_walks, rq.cap, rq.len, rq.node, rq.ts);
+            launches++;
+        } else if (h->sched == TEMPEST_SCHED_FULL_WALK) {
             int64_t grid = (rq.n_walks + 255) / 256;
             const int64_t cap = (int64_t)h->num_sms * 8;
             if (grid > cap) grid = cap;
@@ -566,6 +514,7 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     }
     h->last_ws.n_walks = rq.n_walks;
     h->last_ws.launches = launches;
+    for (int t = 0; t < 5; t++) h->last_ws.tier_launches[t] = h->coop_tier_launches[t];
     return cuda_check(h, cudaGetLastError(), "walk launch");
 }
 

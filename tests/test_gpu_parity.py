@@ -37,7 +37,7 @@ def ingest_both(eng, orc, s, d, t, on_gpu=True):
     return st
 
 
-SCHEDULERS = (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK)
+SCHEDULERS = (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_COOP)
 
 
 def walks_both(eng, orc, n, L, bias, policy=0, seed=0, margin=False):
@@ -243,3 +243,29 @@ def test_bias_parameters():
         eng.set_bias_params(lh, ls)
         orc.set_bias_params(lh, ls)
         check_walks(eng, orc, 4000, 8, policy=1, seed=4, biases=(2,))
+
+
+def test_cooperative_tiers_are_all_exercised():
+    """Per-hop regrouping (Alg. 1) reaches every tier of the dispatch plane on
+    a hub-heavy graph, and its walks equal the oracle's."""
+    rng = np.random.default_rng(9)
+    eng, orc = pair(0, True)
+    # a hub with many groups (block-global), a node with few groups and many
+    # walks (block-smem / warp-smem), medium nodes and a long sparse tail
+    n = 300_000
+    s = np.where(rng.random(n) < 0.5, 0, rng.integers(1, 3000, n)).astype(np.int32)
+    d = np.where(rng.random(n) < 0.5, 0, rng.integers(1, 3000, n)).astype(np.int32)
+    t = rng.integers(0, 1_000_000, n).astype(np.int64)
+    t[s == 7] = 5  # node 7: one group
+    ingest_both(eng, orc, s, d, t)
+    eng.set_scheduler(_lib.SCHED_COOP)
+    for bias in (0, 2):
+        g, o = walks_both(eng, orc, 200_000, 12, bias, 0, seed=3, margin=(bias == 2))
+        if bias == 0:
+            assert_walks_bit_exact(g, o)
+        else:
+            agree, total, _ = compare_biased(g, o, o[3])
+            assert agree / total >= MIN_HOP_AGREEMENT
+        tiers = eng.last_walk_stats()["tier_launches"]
+        assert tiers[0] > 0 and tiers[4] > 0, tiers
+    check_walks(eng, orc, 50_000, 30, policy=1, seed=8)
