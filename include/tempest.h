@@ -71,7 +71,10 @@ enum {
                                     work counter as walks end, one memory round
                                     trip per loop iteration, interpolation
                                     search of Gamma_t(v) (no counterpart in the
-                                    paper: a GB300 form of Sec. 2.4.1) */
+                                    paper: a GB300 form of Sec. 2.4.1) */,
+    TEMPEST_SCHED_GRAPH = 3      /* hop-synchronous: one kernel per hop over the
+                                    active walks, the whole hop loop captured
+                                    once as a CUDA graph and replayed */
 };
 
 /* Per-batch ingest report. */

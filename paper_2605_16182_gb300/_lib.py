@@ -24,7 +24,7 @@ TEMPEST_EBUSY = -5
 
 BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP = 0, 1, 2
 START_UNIFORM_EDGE, START_BIASED_TS = 0, 1
-SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM = 0, 1, 2
+SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH = 0, 1, 2, 3
 (STATE_SRC, STATE_DST, STATE_TS, STATE_TS_GROUP_OFF, STATE_NODE_OFF, STATE_NODE_ORDER,
  STATE_NODE_GROUP_OFF, STATE_NODE_GIDX) = range(8)
 

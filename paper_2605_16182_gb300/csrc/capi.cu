@@ -188,6 +188,7 @@ int tempest_destroy(tempest_t *h)
 {
     if (!h) return TEMPEST_OK;
     cudaStreamSynchronize(h->stream);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     free_all(h);
     if (h->hstat) cudaFreeHost(h->hstat);
     delete h;
@@ -229,7 +230,8 @@ int tempest_set_bias_params(tempest_t *h, double lambda_hop, double lambda_start
 int tempest_set_scheduler(tempest_t *h, int mode)
 {
     if (!h) return TEMPEST_EINVAL;
-    if (mode != TEMPEST_SCHED_FULL_WALK && mode != TEMPEST_SCHED_COOP && mode != TEMPEST_SCHED_STREAM)
+    if (mode != TEMPEST_SCHED_FULL_WALK && mode != TEMPEST_SCHED_COOP && mode != TEMPEST_SCHED_STREAM &&
+        mode != TEMPEST_SCHED_GRAPH)
         return fail(h, TEMPEST_EINVAL, "tempest_set_scheduler: unknown mode %d", mode);
     h->sched = mode;
     return TEMPEST_OK;

@@ -297,6 +297,128 @@ __global__ void __launch_bounds__(COOP_BLOCK) k_coop_block(const WalkView V, con
     flush_counts(O, hops, bytes);
 }
 
+// ---------------------------------------------------------------------------
+// Hop-synchronous form for graph capture: one kernel per hop over the active
+// list, whose length it reads from device memory, so the whole hop loop is a
+// fixed sequence of launches with no host decision between them.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_graph_hop(const WalkView V, const WalkOut O, CoopState S,
+                                                   const int32_t *__restrict__ active,
+                                                   const unsigned int *__restrict__ n_active)
+{
+    unsigned long long hops = 0, bytes = 0;
+    const int64_t n = *n_active;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t rounds = (n + stride - 1) / stride;
+    for (int64_t r = 0; r < rounds; r++) {
+        const int64_t i = r * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        bool push = false;
+        int32_t w = -1;
+        if (i < n) {
+            w = active[i];
+            const int32_t v = S.ws_node[w];
+            const int32_t g0 = __ldg(V.gidx + v), g1 = __ldg(V.gidx + v + 1);
+            coop_hop(V, O, S, w, v, g0, g1, nullptr, hops, bytes, push);
+        }
+        push_active(S, push, w);
+    }
+    flush_counts(O, hops, bytes);
+}
+
+// Records the hop loop of one walk call on the stream (start kernel, then
+// cap - 2 hop kernels alternating the two active lists, each preceded by a
+// reset of the list it fills).  Used under stream capture.
+static void record_graph_walk(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t grid)
+{
+    cudaStream_t st = h->stream;
+    unsigned int *ctr = h->co_ctr.as<unsigned int>();  // ctr[0], ctr[1]: active counts
+    CoopState S;
+    S.ws_node = h->co_node.as<int32_t>();
+    S.ws_t = h->co_t.as<int64_t>();
+    S.ws_len = h->co_len.as<int32_t>();
+    S.sorted_walks = nullptr;
+    S.next_active = h->co_act[0].as<int32_t>();
+    S.n_next = ctr;
+    cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), st);
+    k_coop_start<<<(unsigned)grid, 256, 0, st>>>(V, O, S);
+    for (int32_t step = 0; step + 2 < O.cap; step++) {
+        const int src = step & 1, dst = src ^ 1;
+        S.next_active = h->co_act[dst].as<int32_t>();
+        S.n_next = ctr + dst;
+        cudaMemsetAsync(ctr + dst, 0, sizeof(unsigned int), st);
+        k_graph_hop<<<(unsigned)grid, 256, 0, st>>>(V, O, S, h->co_act[src].as<int32_t>(), ctr + src);
+    }
+}
+
+int graph_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches)
+{
+    const int64_t n = O.n_walks;
+    if (n >= (int64_t)INT32_MAX) return fail(h, TEMPEST_EINVAL, "graph walks: n_walks must be < 2^31");
+    int rc;
+    const size_t nz = (size_t)(n > 0 ? n : 1);
+    if ((rc = ensure(h, h->co_node, sizeof(int32_t) * nz, true))) return rc;
+    if ((rc = ensure(h, h->co_t, sizeof(int64_t) * nz, true))) return rc;
+    if ((rc = ensure(h, h->co_len, sizeof(int32_t) * nz, true))) return rc;
+    if ((rc = ensure(h, h->co_act[0], sizeof(int32_t) * nz, true))) return rc;
+    if ((rc = ensure(h, h->co_act[1], sizeof(int32_t) * nz, true))) return rc;
+    if ((rc = ensure(h, h->co_ctr, 64 * sizeof(unsigned int)))) return rc;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_graph_hop, 256, 0);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    int64_t grid = (int64_t)h->num_sms * blocks_per_sm;
+    if (grid > (n + 255) / 256) grid = (n + 255) / 256;
+    if (grid < 1) grid = 1;
+
+    // capture the hop loop; update the cached executable graph when only the
+    // kernel arguments changed, otherwise instantiate a new one
+    cudaStream_t cap_stream = h->stream;
+    bool own_stream = false;
+    if (cap_stream == nullptr || cap_stream == cudaStreamLegacy) {
+        // the legacy stream cannot be captured: record on a private stream
+        if ((rc = cuda_check(h, cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking), "graph stream")))
+            return rc;
+        own_stream = true;
+    }
+    cudaStream_t saved = h->stream;
+    h->stream = cap_stream;
+    cudaGraph_t graph = nullptr;
+    rc = cuda_check(h, cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (!rc) {
+        record_graph_walk(h, V, O, grid);
+        rc = cuda_check(h, cudaStreamEndCapture(cap_stream, &graph), "end capture");
+    }
+    h->stream = saved;
+    if (!rc) {
+        bool updated = false;
+        if (h->graph_exec && h->graph_cap == O.cap) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(h->graph_exec, graph, &info) == cudaSuccess) updated = true;
+            else cudaGetLastError();
+        }
+        if (!updated) {
+            if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+            rc = cuda_check(h, cudaGraphInstantiate(&h->graph_exec, graph, 0), "graph instantiate");
+            h->graph_cap = O.cap;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (!rc) {
+        if (own_stream) {
+            // keep stream order with the caller's (legacy) stream
+            rc = cuda_check(h, cudaGraphLaunch(h->graph_exec, saved), "graph launch");
+        } else {
+            rc = cuda_check(h, cudaGraphLaunch(h->graph_exec, cap_stream), "graph launch");
+        }
+    }
+    if (own_stream) cudaStreamDestroy(cap_stream);
+    launches += 1 + (O.cap > 2 ? O.cap - 2 : 0);
+    h->graph_launches++;
+    return rc;
+}
+
 static int bits_for_n(int64_t N)
 {
     int b = 0;

@@ -100,6 +100,9 @@ struct tempest {
     int coop_w_warp = 4;         // solo / warp boundary W_warp (Sec. 3.5)
     int coop_mega = 8192;        // mega-hub split (Sec. 2.4.4)
     int64_t coop_tier_launches[5] = {0, 0, 0, 0, 0};
+    cudaGraphExec_t graph_exec = nullptr;  // captured hop loop (TEMPEST_SCHED_GRAPH)
+    int32_t graph_cap = 0;
+    int64_t graph_launches = 0;
     tw::DBuf dstat;       // IngestScratch
     tw::DBuf wcnt;        // WalkCounters
     tw::DBuf out_stage;   // device staging of host walk outputs

@@ -168,13 +168,53 @@ __device__ __forceinline__ int64_t exp_index_k(uint64_t k, int64_t n, const ExpR
     return sampler_index(ud, n, BIAS_EXP, R.lambda);
 }
 
+// Linear bias (weight i+1).  The exact inverse is the largest i with
+// i(i+1) <= Q, Q = u n (n+1), i.e. (2i+1)^2 <= A = 4Q + 1.  With
+// u = k 2^-53, A 2^51 = k n(n+1) + 2^51 is an integer, so i follows from
+// 128-bit integer comparisons inside a bracket found by an FP32 estimate.
+// The double formula of Eq. 2 is within (X+1) 4.4e-16 of the exact X; when
+// A is more than 64 (i+2)^2 units of 2^-51 away from both bucket edges
+// (well beyond that error) the double formula floors to the same i,
+// otherwise the double formula decides.
+__device__ __forceinline__ int64_t linear_index_k(uint64_t k, int64_t n)
+{
+    typedef unsigned __int128 u128;
+    const uint64_t nn = (uint64_t)n * (uint64_t)(n + 1);
+    const u128 A = (u128)k * nn + ((u128)1 << 51);
+    const float uf = __uint2float_rn((uint32_t)(k >> 21)) * 2.3283064365386963e-10f +
+                     __uint2float_rn((uint32_t)(k & 0x1FFFFFu)) * 1.1102230246251565e-16f;
+    const float nf = __int2float_rn((int32_t)n);
+    const float Af = 4.0f * uf * nf * (nf + 1.0f) + 1.0f;
+    const float Xf = fminf((sqrtf(Af) - 1.0f) * 0.5f, 4.0e9f);
+    const uint32_t e_lo = __float2uint_rz(Xf * (1.0f - 9.5367431640625e-07f));  // 1 - 2^-20
+    const uint32_t e_hi = __float2uint_rz(Xf * (1.0f + 9.5367431640625e-07f));
+    uint64_t lo = e_lo > 2u ? (uint64_t)e_lo - 2u : 0u;
+    uint64_t hi = (uint64_t)e_hi + 3u;
+    bool ok = (((u128)(2 * lo + 1) * (2 * lo + 1)) << 51) <= A;
+    if (ok) {
+        while (lo < hi) {  // largest m in [lo, hi] with (2m+1)^2 2^51 <= A
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if ((((u128)(2 * mid + 1) * (2 * mid + 1)) << 51) <= A) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint64_t i = lo;
+        const u128 b0 = ((u128)(2 * i + 1) * (2 * i + 1)) << 51;
+        const u128 b1 = ((u128)(2 * i + 3) * (2 * i + 3)) << 51;
+        if (b1 > A) {
+            const u128 thr = (u128)64 * (u128)((i + 2) * (i + 2));
+            if (A - b0 > thr && b1 - A > thr) return (int64_t)i < n - 1 ? (int64_t)i : n - 1;
+        }
+    }
+    const double ud = __dmul_rn(__ull2double_rn(k), 1.1102230246251565404236316680908203125e-16);
+    return sampler_index(ud, n, BIAS_LINEAR, 1.0);
+}
+
 // Index of the group / edge a draw selects, for any bias.
 __device__ __forceinline__ int64_t sampler_index_k(uint64_t k, int64_t n, int bias, const ExpRate &R)
 {
     if (bias == BIAS_UNIFORM) return uniform_index_k(k, n);
     if (bias == BIAS_EXP) return exp_index_k(k, n, R);
-    const double ud = __dmul_rn(__ull2double_rn(k), 1.1102230246251565404236316680908203125e-16);
-    return sampler_index(ud, n, BIAS_LINEAR, R.lambda);
+    return linear_index_k(k, n);
 }
 
 // ---------------------------------------------------------------------------

@@ -133,5 +133,6 @@ __device__ __forceinline__ Entry draw_entry(const WalkView &V, const WalkOut &O,
 
 WalkView make_view(tempest_t *h);
 int coop_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches);
+int graph_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches);
 
 }  // namespace tw

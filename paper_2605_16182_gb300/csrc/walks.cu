@@ -162,7 +162,7 @@ __device__ __forceinline__ int32_t interp_probe(int32_t L, int32_t R, int64_t vL
     return p;
 }
 
-__global__ void __launch_bounds__(256) k_walks_stream(const WalkView V, const WalkOut O,
+__global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const WalkOut O,
                                                       unsigned long long *next_walk)
 {
     const int lane = threadIdx.x & 31;
@@ -481,8 +481,8 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     int64_t launches = 0;
     for (int t = 0; t < 5; t++) h->coop_tier_launches[t] = 0;
     if (rq.n_walks > 0) {
-        if (h->sched == TEMPEST_SCHED_COOP) {
-            int rc2 = coop_run(h, V, O, launches);
+        if (h->sched == TEMPEST_SCHED_COOP || h->sched == TEMPEST_SCHED_GRAPH) {
+            int rc2 = h->sched == TEMPEST_SCHED_COOP ? coop_run(h, V, O, launches) : graph_run(h, V, O, launches);
             if (rc2) return rc2;
             int64_t pgrid = (rq.n_walks + 7) / 8;
             const int64_t pcap = (int64_t)h->num_sms * 16;
