@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--walks", type=int, default=10_000_000)
     p.add_argument("--max-len", type=int, default=80)
     p.add_argument("--sched", default="stream", choices=["stream", "full", "coop", "graph"])
-    p.add_argument("--workload", default="stream", choices=["stream", "batched"])
+    p.add_argument("--workload", default="stream", choices=["stream", "batched", "serve"])
+    p.add_argument("--requests", type=int, default=2000)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -414,6 +415,149 @@ def run_batched(args):
 
 
 # --------------------------------------------------------------------------
+# serving: continuous batching vs one launch per request
+# --------------------------------------------------------------------------
+def run_serve(args):
+    import math
+    import random
+    import torch
+    from paper_2605_16182_gb300 import _lib, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sc = args.scale
+    n_nodes = max(1000, int(50_000_000 * sc))
+    window = max(1000, int(100_000_000 * sc))
+    spec = synth.StreamSpec("serve-50M-nodes-100M-window", n_nodes, 10**12, 2.0, 1005, max(1, int(10_000_000 * sc)),
+                            mean_gaps=[1000], window=-window)
+    rng = random.Random(7)
+    n_req = args.requests
+
+    def loguni(lo, hi):
+        return int(math.exp(rng.uniform(math.log(lo), math.log(hi))))
+
+    reqs = []
+    for i in range(n_req):
+        if rng.random() < 0.1:
+            reqs.append(("ingest", max(1, int(loguni(1e5, 1e7) * sc))))
+        else:
+            reqs.append(("walks", max(1, int(loguni(1e3, 1e7) * sc)), rng.randint(10, 80), rng.randint(0, 2),
+                         rng.getrandbits(62)))
+    # edges for the warm-up fill and for every ingest request, resident in HBM
+    fill = window
+    need = fill + sum(r[1] for r in reqs if r[0] == "ingest")
+    src, dst, ts = spec.edges(0, need, device=dev)
+    cursor = [fill]
+
+    def fresh_engine():
+        e = _lib.Engine(window=spec.window, directed=True, device=str(dev))
+        step = spec.batch
+        for a in range(0, fill, step):
+            b = min(fill, a + step)
+            e.ingest(src[a:b], dst[a:b], ts[a:b])
+        cursor[0] = fill
+        return e
+
+    def ingest_slice(n):
+        a = cursor[0]
+        cursor[0] += n
+        return src[a:a + n], dst[a:a + n], ts[a:a + n]
+
+    max_w = max(r[1] for r in reqs if r[0] == "walks")
+    out_node = torch.empty((max_w, 80), dtype=torch.int32, device=dev)
+    out_ts = torch.empty((max_w, 80), dtype=torch.int64, device=dev)
+    out_len = torch.empty((max_w,), dtype=torch.int32, device=dev)
+
+    # plain form: one call per request, FIFO; capacity from a back-to-back run
+    def plain(arrivals):
+        eng = fresh_engine()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat = {"walks": [], "ingest": []}
+        hops = 0
+        for r, at in zip(reqs, arrivals):
+            now = time.perf_counter() - t0
+            if now < at:
+                time.sleep(at - now)
+            if r[0] == "ingest":
+                eng.ingest(*ingest_slice(r[1]))
+            else:
+                n, L, b, seed = r[1], r[2], r[3], r[4]
+                eng.walks(n, L, bias=b, seed=seed, out=(out_node.view(-1)[:n * L].view(n, L),
+                                                          out_ts.view(-1)[:n * L].view(n, L), out_len[:n]))
+                torch.cuda.synchronize()
+                hops += eng.last_walk_stats()["hops"]
+            lat[r[0]].append(time.perf_counter() - t0 - at)
+        makespan = time.perf_counter() - t0
+        eng.close()
+        return makespan, lat, hops
+
+    def served(arrivals, arena, max_wave):
+        eng = fresh_engine()
+        srv = _lib.Server(eng, arena_bytes=arena, max_wave_walks=max_wave, max_inflight=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pending = {}
+        lat = {"walks": [], "ingest": []}
+        i = 0
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arrivals[i] <= now:
+                r = reqs[i]
+                if r[0] == "ingest":
+                    tk = srv.submit_ingest(*ingest_slice(r[1]))
+                else:
+                    tk = srv.submit_walks(_lib.make_request(r[1], r[2], r[3], 0, r[4]))
+                pending[tk] = (r[0], arrivals[i])
+                i += 1
+            srv.progress()
+            for tk in list(pending):
+                st, _, _ = srv.status(tk)
+                if st >= 2 or st < 0:
+                    kind, at = pending.pop(tk)
+                    lat[kind].append(time.perf_counter() - t0 - at)
+                    srv.release(tk)
+            if i < len(reqs) and not pending:
+                time.sleep(max(0.0, min(0.001, arrivals[i] - (time.perf_counter() - t0))))
+        makespan = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        eng.close()
+        return makespan, lat, stats
+
+    def pct(xs, q):
+        return 1e3 * percentile(xs, q) if xs else None
+
+    cap_time, _, total_hops = plain([0.0] * len(reqs))
+    capacity = len(reqs) / cap_time
+    arena = int(12 * max_w * 80 * 2.5)
+    out = {"metric": METRIC, "unit": "hops/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "streaming-serving-50M-nodes-100M-window" + ("" if sc == 1.0 else " scaled %g" % sc),
+                      "requests": n_req, "ingest_fraction": 0.1, "arena_bytes": arena},
+           "plain_capacity_req_per_s": capacity, "plain_back_to_back_s": cap_time, "total_hops": total_hops,
+           "loads": []}
+    for load in (0.5, 0.7, 0.9):
+        rate = load * capacity
+        t, arr = 0.0, []
+        for _ in reqs:
+            t += rng.expovariate(rate)
+            arr.append(t)
+        pm, pl, _ = plain(arr)
+        sm, sl, sst = served(arr, arena, max_wave=max(max_w, int(16_000_000 * sc)))
+        out["loads"].append({
+            "offered_load": load,
+            "plain": {"hops_per_s": total_hops / pm, "makespan_s": pm,
+                      "walk_p50_ms": pct(pl["walks"], 50), "walk_p99_ms": pct(pl["walks"], 99),
+                      "ingest_p50_ms": pct(pl["ingest"], 50), "ingest_p99_ms": pct(pl["ingest"], 99)},
+            "served": {"hops_per_s": total_hops / sm, "makespan_s": sm,
+                       "walk_p50_ms": pct(sl["walks"], 50), "walk_p99_ms": pct(sl["walks"], 99),
+                       "ingest_p50_ms": pct(sl["ingest"], 50), "ingest_p99_ms": pct(sl["ingest"], 99),
+                       "waves": sst["waves"], "requests_per_wave": sst["wave_requests"] / max(1, sst["waves"])}})
+        print(json.dumps(out["loads"][-1]), flush=True)
+    out["value"] = out["loads"][-1]["served"]["hops_per_s"]
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -435,6 +579,10 @@ def main():
     if args.workload == "batched":
         if rank == 0:
             run_batched(args)
+        return
+    if args.workload == "serve":
+        if rank == 0:
+            run_serve(args)
         return
     res = run_ours(args, rank, world)
 

@@ -172,6 +172,70 @@ int tempest_walks_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_ar
 int tempest_sample_index(tempest_t *h, const uint64_t *u_bits, const int64_t *n, int64_t count, int bias,
                          double lambda, int64_t *out);
 
+/* One walk request of a batched launch.  All pointers are device memory.
+ * Rows have stride max_len; max_len_arr / bias_arr (nullable) give per-walk
+ * caps (each in [2, max_len]) and biases.  Walk w of the request draws from
+ * Philox(seed, w, hop) exactly as tempest_walks(n_walks, ..., seed) would, so
+ * its result does not depend on the other requests of the launch. */
+typedef struct {
+    int64_t n_walks;
+    int32_t max_len;
+    int32_t bias;
+    const int32_t *max_len_arr;
+    const uint8_t *bias_arr;
+    int32_t start_policy;
+    int32_t pad;
+    uint64_t seed;
+    int32_t *node;
+    int64_t *ts;
+    int32_t *len;
+} tempest_walk_request;
+
+/* Serve n_req walk requests in one persistent launch (continuous batching
+ * of requests; Sec. 2.4 walks, Sec. 2.5 samplers).  The requests' outputs
+ * are complete when the handle's stream reaches this point.  EINVAL on a
+ * bad request (same rules as tempest_walks_mixed) or non-device pointers. */
+int tempest_walks_batch(tempest_t *h, const tempest_walk_request *reqs, int n_req);
+
+/* ---- serving loop (continuous batching over the device-resident index) ----
+ * The paper runs one walk call per batch (Sec. 3.3); these calls serve a
+ * stream of requests instead.  A server keeps a FIFO of ingest and walk
+ * requests.  Walk requests are admitted in arrival order into a wave (one
+ * tempest_walks_batch launch) while the wave has launch slots
+ * (max_wave_walks) and their outputs fit in an output arena of arena_bytes
+ * (the HBM budget for results; requests passing NULL outputs get arena
+ * memory, which returns on tempest_server_release).  Up to max_inflight
+ * (1 or 2) waves run at once on the server's own streams, so requests that
+ * arrive while a wave runs start in the next wave and overlap it.  An ingest
+ * waits until no wave is in flight, so every walk request sees the index as
+ * of its arrival.  A wave is ordered after all work queued on the handle's
+ * stream when it launches; caller-provided arrays must be ready by then.  Ingest arrays (device memory) must stay valid until the
+ * request completes.  No call blocks except tempest_server_drain and the
+ * ingest that tempest_server_progress runs.  State: 0 queued, 1 running,
+ * 2 done, negative = failed with that TEMPEST_E* code (ENOMEM: the request's
+ * outputs can never fit the arena). */
+typedef struct tempest_server tempest_server_t;
+int tempest_server_create(tempest_t *h, size_t arena_bytes, int64_t max_wave_walks, int max_inflight,
+                          tempest_server_t **out);
+int tempest_server_destroy(tempest_server_t *s);
+int tempest_server_submit_walks(tempest_server_t *s, const tempest_walk_request *req, uint64_t *ticket);
+int tempest_server_submit_ingest(tempest_server_t *s, const int32_t *src, const int32_t *dst, const int64_t *ts,
+                                 int64_t n, uint64_t *ticket);
+/* Retire finished waves, run a ready ingest, launch new waves; *n_completed
+ * receives the number of requests that finished during the call. */
+int tempest_server_progress(tempest_server_t *s, int *n_completed);
+/* State, output pointers (device) and submit-to-completion latency in
+ * seconds (-1 while unfinished) of a request. */
+int tempest_server_status(tempest_server_t *s, uint64_t ticket, int *state, int32_t **node, int64_t **ts,
+                          int32_t **len, double *latency_s);
+/* Forget a finished request and return its arena memory. */
+int tempest_server_release(tempest_server_t *s, uint64_t ticket);
+/* Progress until the queue is empty and no wave runs. */
+int tempest_server_drain(tempest_server_t *s);
+/* out[0] waves launched, out[1] walk requests served in waves, out[2]
+ * ingests run, out[3] requests queued. */
+int tempest_server_stats(tempest_server_t *s, int64_t out[4]);
+
 /* Select the walk execution form (TEMPEST_SCHED_*) for later walk calls. */
 int tempest_set_scheduler(tempest_t *h, int mode);
 

@@ -34,7 +34,10 @@ EXPORTED = (
     "tempest_set_bias_params", "tempest_ingest", "tempest_walks", "tempest_walks_mixed",
     "tempest_set_scheduler", "tempest_last_walk_stats", "tempest_get_counts",
     "tempest_export_state", "tempest_sync", "tempest_last_error", "tempest_version",
-    "tempest_sort_batch_noalloc", "tempest_sample_index",
+    "tempest_sort_batch_noalloc", "tempest_sample_index", "tempest_walks_batch",
+    "tempest_server_create", "tempest_server_destroy", "tempest_server_submit_walks",
+    "tempest_server_submit_ingest", "tempest_server_progress", "tempest_server_status",
+    "tempest_server_release", "tempest_server_drain", "tempest_server_stats",
 )
 NOALLOC_MAX_EDGES = 262144
 
@@ -66,6 +69,13 @@ class WalkStats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["tier_launches"] = list(self.tier_launches)
         return d
+
+
+class WalkRequest(ctypes.Structure):
+    _fields_ = [("n_walks", ctypes.c_int64), ("max_len", ctypes.c_int32), ("bias", ctypes.c_int32),
+                ("max_len_arr", ctypes.c_void_p), ("bias_arr", ctypes.c_void_p),
+                ("start_policy", ctypes.c_int32), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("node", ctypes.c_void_p), ("ts", ctypes.c_void_p), ("len", ctypes.c_void_p)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -107,6 +117,17 @@ def load():
     L.tempest_version.restype = ctypes.c_char_p
     L.tempest_sort_batch_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
     L.tempest_sample_index.argtypes = [vp, vp, vp, i64, ci, dbl, vp]
+    L.tempest_walks_batch.argtypes = [vp, ctypes.POINTER(WalkRequest), ci]
+    L.tempest_server_create.argtypes = [vp, ctypes.c_size_t, i64, ci, ctypes.POINTER(vp)]
+    L.tempest_server_destroy.argtypes = [vp]
+    L.tempest_server_submit_walks.argtypes = [vp, ctypes.POINTER(WalkRequest), ctypes.POINTER(ctypes.c_uint64)]
+    L.tempest_server_submit_ingest.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
+    L.tempest_server_progress.argtypes = [vp, ctypes.POINTER(ci)]
+    L.tempest_server_status.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ci), ctypes.POINTER(vp),
+                                        ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(dbl)]
+    L.tempest_server_release.argtypes = [vp, ctypes.c_uint64]
+    L.tempest_server_drain.argtypes = [vp]
+    L.tempest_server_stats.argtypes = [vp, vp]
     for name in EXPORTED:
         if name not in ("tempest_last_error", "tempest_version"):
             getattr(L, name).restype = ci
@@ -175,6 +196,99 @@ def tempest_walks_mixed(h, n_walks, max_len_ptr, max_len_cap, bias_ptr, start_po
 def tempest_sample_index(h, u_bits_ptr, n_ptr, count, bias, lam, out_ptr):
     return _check(h, load().tempest_sample_index(h, ctypes.c_void_p(u_bits_ptr), ctypes.c_void_p(n_ptr),
                                                  int(count), int(bias), float(lam), ctypes.c_void_p(out_ptr)))
+
+
+def make_request(n_walks, max_len, bias=0, start_policy=0, seed=0, node=None, ts=None, ln=None,
+                 max_len_arr=None, bias_arr=None) -> WalkRequest:
+    """A tempest_walk_request; outputs / per-walk arrays are CUDA tensors or None."""
+    r = WalkRequest()
+    r.n_walks, r.max_len, r.bias, r.start_policy = int(n_walks), int(max_len), int(bias), int(start_policy)
+    r.seed = int(seed) & (2**64 - 1)
+    r.max_len_arr = _ptr(max_len_arr, "int32")
+    r.bias_arr = _ptr(bias_arr, "uint8")
+    r.node, r.ts, r.len = _ptr(node, "int32"), _ptr(ts, "int64"), _ptr(ln, "int32")
+    return r
+
+
+def tempest_walks_batch(h, reqs):
+    arr = (WalkRequest * len(reqs))(*reqs)
+    return _check(h, load().tempest_walks_batch(h, arr, len(reqs)))
+
+
+class Server:
+    """The serving loop of include/tempest.h (tempest_server_*)."""
+
+    QUEUED, RUNNING, DONE = 0, 1, 2
+
+    def __init__(self, engine, arena_bytes: int, max_wave_walks: int, max_inflight: int = 2):
+        self.engine = engine
+        self.s = ctypes.c_void_p()
+        _check(engine.h, load().tempest_server_create(engine.h, ctypes.c_size_t(int(arena_bytes)),
+                                                      int(max_wave_walks), int(max_inflight),
+                                                      ctypes.byref(self.s)))
+
+    def close(self):
+        if self.s:
+            load().tempest_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit_walks(self, req: WalkRequest) -> int:
+        t = ctypes.c_uint64()
+        _check(self.engine.h, load().tempest_server_submit_walks(self.s, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def submit_ingest(self, src, dst, ts) -> int:
+        t = ctypes.c_uint64()
+        _check(self.engine.h, load().tempest_server_submit_ingest(
+            self.s, _ptr(src, "int32"), _ptr(dst, "int32"), _ptr(ts, "int64"), int(src.shape[0]),
+            ctypes.byref(t)))
+        return t.value
+
+    def progress(self) -> int:
+        n = ctypes.c_int()
+        _check(self.engine.h, load().tempest_server_progress(self.s, ctypes.byref(n)))
+        return n.value
+
+    def status(self, ticket: int):
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        node, ts, ln = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(self.engine.h, load().tempest_server_status(self.s, ctypes.c_uint64(ticket), ctypes.byref(st),
+                                                           ctypes.byref(node), ctypes.byref(ts),
+                                                           ctypes.byref(ln), ctypes.byref(lat)))
+        return st.value, (node.value, ts.value, ln.value), lat.value
+
+    def result(self, ticket: int, n_walks: int, max_len: int):
+        """Copies of a finished walk request's outputs as torch tensors."""
+        import torch
+        st, (pn, pt, pl), _ = self.status(ticket)
+        assert st == self.DONE, st
+
+        class _View:
+            def __init__(self, ptr, shape, typestr):
+                self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False),
+                                                 "version": 3, "strides": None}
+
+        node = torch.as_tensor(_View(pn, (n_walks, max_len), "<i4"), device="cuda").clone()
+        ts = torch.as_tensor(_View(pt, (n_walks, max_len), "<i8"), device="cuda").clone()
+        ln = torch.as_tensor(_View(pl, (n_walks,), "<i4"), device="cuda").clone()
+        return node, ts, ln
+
+    def release(self, ticket: int):
+        _check(self.engine.h, load().tempest_server_release(self.s, ctypes.c_uint64(ticket)))
+
+    def drain(self):
+        _check(self.engine.h, load().tempest_server_drain(self.s))
+
+    def stats(self) -> dict:
+        out = (ctypes.c_int64 * 4)()
+        _check(self.engine.h, load().tempest_server_stats(self.s, out))
+        return dict(waves=out[0], wave_requests=out[1], ingests=out[2], queued=out[3])
 
 
 def tempest_set_scheduler(h, mode: int):

@@ -38,6 +38,7 @@ struct IngestScratch {
     long long i0, j0;       // first kept store / batch element
     long long kept_batch_min_ts;
     long long store_last_ts;
+    unsigned long long status;  // nonzero: an index check failed (bit per site)
 };
 
 // Device-side walk counters.

@@ -78,6 +78,7 @@ __global__ void k_init_scratch(IngestScratch *o)
     o->j0 = 0;
     o->kept_batch_min_ts = 0;
     o->store_last_ts = 0;
+    o->status = 0;
 }
 
 struct TsKeyLoader {
@@ -317,15 +318,19 @@ __global__ void k_node_order(const Entry *__restrict__ E, int64_t M, int32_t *ou
 // Entries of the evicted store prefix [0, i0), counted per node.  Every
 // node loses a prefix of its segment: eviction removes the oldest edges.
 __global__ void k_evict_counts(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t items,
-                               int directed, int32_t *ev)
+                               int directed, int64_t N, int32_t *ev, IngestScratch *chk)
 {
     const int lane = threadIdx.x & 31;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = directed ? src[i] : ((i & 1) ? dst[i >> 1] : src[i >> 1]);
+        int32_t v = directed ? src[i] : ((i & 1) ? dst[i >> 1] : src[i >> 1]);
+        if (v < 0 || v >= N) {
+            atomicOr(&chk->status, 1ull << 0);
+            v = -1;
+        }
         const unsigned am = __activemask();
         const unsigned peers = __match_any_sync(am, v);
-        if (lane == __ffs(peers) - 1) atomicAdd(&ev[v], __popc(peers));
+        if (v >= 0 && lane == __ffs(peers) - 1) atomicAdd(&ev[v], __popc(peers));
     }
 }
 
@@ -384,14 +389,23 @@ struct NoffOp {
 // evicted store prefix, in slots).
 __global__ void k_copy_kept(const Entry *__restrict__ E_old, const int32_t *__restrict__ enode_old, int64_t M_old,
                             const int32_t *__restrict__ noff_old, const int32_t *__restrict__ ev,
-                            const int32_t *__restrict__ noff_new, int32_t E0, Entry *E_new, int32_t *enode_new)
+                            const int32_t *__restrict__ noff_new, int32_t E0, int64_t N_old, int64_t M_new,
+                            Entry *E_new, int32_t *enode_new, IngestScratch *chk)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M_old;
          i += (int64_t)gridDim.x * blockDim.x) {
         Entry e = E_old[i];
         if (e.slot < E0) continue;  // evicted
         const int32_t v = enode_old[i];
+        if (v < 0 || v >= N_old) {
+            atomicOr(&chk->status, 1ull << 1);
+            continue;
+        }
         const int64_t p = (int64_t)noff_new[v] + (i - noff_old[v] - ev[v]);
+        if (p < 0 || p >= M_new) {
+            atomicOr(&chk->status, 1ull << 2);
+            continue;
+        }
         e.slot -= E0;
         E_new[p] = e;
         enode_new[p] = v;
@@ -403,13 +417,21 @@ __global__ void k_scatter_batch(const uint32_t *__restrict__ K, const uint32_t *
                                 const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcnt,
                                 const int32_t *__restrict__ noff_new, const int32_t *__restrict__ src,
                                 const int32_t *__restrict__ dst, const int64_t *__restrict__ ts, int directed,
-                                Entry *E_new, int32_t *enode_new)
+                                int64_t N, int64_t M_new, Entry *E_new, int32_t *enode_new, IngestScratch *chk)
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = K[j];
         const uint32_t slot = V[j];
+        if ((int64_t)v >= N) {
+            atomicOr(&chk->status, 1ull << 3);
+            continue;
+        }
         const int64_t p = (int64_t)noff_new[v + 1] - bcnt[v] + (j - bstart[v]);
+        if (p < 0 || p >= M_new) {
+            atomicOr(&chk->status, 1ull << 4);
+            continue;
+        }
         const int64_t pos = directed ? (int64_t)slot : (int64_t)(slot >> 1);
         const bool side = !directed && (slot & 1u);
         Entry e;
@@ -598,7 +620,8 @@ static int node_view_append(tempest_t *h, int64_t i0, int64_t na, int64_t nbk, i
     cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * (size_t)N, st);
     if (evi > 0)
         k_evict_counts<<<grid_for(h, evi), 256, 0, st>>>(h->st_src[old_store].as<int32_t>(),
-                                                        h->st_dst[old_store].as<int32_t>(), evi, directed, ev);
+                                                        h->st_dst[old_store].as<int32_t>(), evi, directed, N, ev,
+                                                        h->dstat.as<IngestScratch>());
     const uint32_t *Kb = nullptr, *Vb = nullptr;
     if (nbe > 0) {
         BatchKeyLoader ld{src, dst, directed, na};
@@ -623,14 +646,15 @@ static int node_view_append(tempest_t *h, int64_t i0, int64_t na, int64_t nbk, i
     if (M_old > 0) {
         k_copy_kept<<<grid_for(h, M_old), 256, 0, st>>>(h->ent[vold].as<Entry>(), h->enode[vold].as<int32_t>(),
                                                        M_old, h->noff[vold].as<int32_t>(), ev,
-                                                       h->noff[nxt].as<int32_t>(), (int32_t)evi,
-                                                       h->ent[nxt].as<Entry>(), h->enode[nxt].as<int32_t>());
+                                                       h->noff[nxt].as<int32_t>(), (int32_t)evi, N_old, M,
+                                                       h->ent[nxt].as<Entry>(), h->enode[nxt].as<int32_t>(),
+                                                       h->dstat.as<IngestScratch>());
         h->pending_launches++;
     }
     if (nbe > 0) {
         k_scatter_batch<<<grid_for(h, nbe), 256, 0, st>>>(Kb, Vb, nbe, bstart, bcnt, h->noff[nxt].as<int32_t>(), src,
-                                                         dst, ts, directed, h->ent[nxt].as<Entry>(),
-                                                         h->enode[nxt].as<int32_t>());
+                                                         dst, ts, directed, N, M, h->ent[nxt].as<Entry>(),
+                                                         h->enode[nxt].as<int32_t>(), h->dstat.as<IngestScratch>());
         h->pending_launches++;
     }
     h->pending_launches += (evi > 0) ? 1 : 0;
@@ -794,7 +818,11 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     if (append && h->ent[h->vcur].p) rc = node_view_append(h, i0, na, nbk, N_old, M_old);
     else rc = node_view_full(h);
     if (rc) return rc;
+    cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ingest"))) return rc;
+    if (hs->status)
+        return fail(h, TEMPEST_ECUDA, "ingest: index consistency check failed (code 0x%llx)",
+                    (unsigned long long)hs->status);
 
     if (stats) {
         stats->n_in = n;

@@ -131,7 +131,28 @@ __device__ __forceinline__ Entry draw_entry(const WalkView &V, const WalkOut &O,
     return V.ent[idx];
 }
 
+// One walk request of a multi-request launch (device copy).  offset is the
+// first global walk id of the request inside the launch.
+struct ReqDesc {
+    int64_t n_walks;
+    int64_t offset;
+    const int32_t *len_arr;
+    const uint8_t *bias_arr;
+    int32_t *node;
+    int64_t *ts;
+    int32_t *len;
+    uint64_t seed;
+    int32_t cap;
+    int32_t max_len;
+    int32_t bias;
+    int32_t start_policy;
+};
+
 WalkView make_view(tempest_t *h);
+// One persistent streaming launch (plus row padding) over n_req requests
+// whose descriptors are in device memory; counters in cnt (zeroed here).
+int walks_multi_launch(tempest_t *h, const ReqDesc *dev_reqs, int n_req, int64_t total, WalkCounters *cnt,
+                       cudaStream_t st);
 int coop_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches);
 int graph_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches);
 

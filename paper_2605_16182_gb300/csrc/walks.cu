@@ -162,19 +162,92 @@ __device__ __forceinline__ int32_t interp_probe(int32_t L, int32_t R, int64_t vL
     return p;
 }
 
-__global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const WalkOut O,
-                                                      unsigned long long *next_walk)
+// A provider maps a global walk id g in [0, total()) to a walk of some
+// request: its own walk number (which keys its Philox stream), its seed,
+// start policy, output row and length slot.
+struct OneReq {
+    WalkOut O;
+    struct Ctx {
+        int64_t w;
+    };
+    __device__ __forceinline__ int64_t total() const { return O.n_walks; }
+    __device__ __forceinline__ void open(int64_t g, Ctx &c, int32_t &L, int &bias) const
+    {
+        c.w = g;
+        walk_params(O, g, L, bias);
+    }
+    __device__ __forceinline__ uint64_t seed(const Ctx &) const { return O.seed; }
+    __device__ __forceinline__ uint64_t wid(const Ctx &c) const { return (uint64_t)c.w; }
+    __device__ __forceinline__ int policy(const Ctx &) const { return O.start_policy; }
+    __device__ __forceinline__ int32_t *nrow(const Ctx &c) const { return O.node + c.w * (int64_t)O.cap; }
+    __device__ __forceinline__ int64_t *trow(const Ctx &c) const { return O.ts + c.w * (int64_t)O.cap; }
+    __device__ __forceinline__ void finish(const Ctx &c, int32_t len) const { O.len[c.w] = len; }
+    __device__ __forceinline__ WalkCounters *cnt() const { return O.cnt; }
+};
+
+struct ManyReq {
+    const ReqDesc *reqs;  // sorted by offset, reqs[0].offset == 0
+    int n_req;
+    int64_t total_;
+    WalkCounters *counters;
+    struct Ctx {
+        int64_t w;
+        int32_t r;
+    };
+    __device__ __forceinline__ int64_t total() const { return total_; }
+    __device__ __forceinline__ void open(int64_t g, Ctx &c, int32_t &L, int &bias) const
+    {
+        int lo = 0, hi = n_req - 1;  // last request whose offset <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (reqs[mid].offset <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const ReqDesc &q = reqs[lo];
+        c.r = lo;
+        c.w = g - q.offset;
+        if (c.w < 0 || c.w >= q.n_walks) {  // corrupt request table
+            atomicOr(&counters->status, 1ull << 8);
+            c.w = 0;
+        }
+        L = q.len_arr ? q.len_arr[c.w] : q.max_len;
+        bias = q.bias_arr ? (int)q.bias_arr[c.w] : q.bias;
+        if (L < 2 || L > q.cap || bias < 0 || bias > 2) {
+            atomicOr(&counters->status, 1ull);
+            L = L < 2 ? 2 : (L > q.cap ? q.cap : L);
+            bias = (bias < 0 || bias > 2) ? BIAS_UNIFORM : bias;
+        }
+    }
+    __device__ __forceinline__ uint64_t seed(const Ctx &c) const { return reqs[c.r].seed; }
+    __device__ __forceinline__ uint64_t wid(const Ctx &c) const { return (uint64_t)c.w; }
+    __device__ __forceinline__ int policy(const Ctx &c) const { return reqs[c.r].start_policy; }
+    __device__ __forceinline__ int32_t *nrow(const Ctx &c) const
+    {
+        return reqs[c.r].node + c.w * (int64_t)reqs[c.r].cap;
+    }
+    __device__ __forceinline__ int64_t *trow(const Ctx &c) const
+    {
+        return reqs[c.r].ts + c.w * (int64_t)reqs[c.r].cap;
+    }
+    __device__ __forceinline__ void finish(const Ctx &c, int32_t len) const { reqs[c.r].len[c.w] = len; }
+    __device__ __forceinline__ WalkCounters *cnt() const { return counters; }
+};
+
+template <class P>
+__global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const P Pv,
+                                                          unsigned long long *next_walk)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     SmLane s;
+    typename P::Ctx cx;
     s.state = S_FETCH;
     s.w = 0;
     int64_t y0 = 0;           // loaded 64-bit value
     int32_t z0 = 0, z1 = 0;   // loaded 32-bit values
     int64_t y1 = 0;
     unsigned long long hops = 0, bytes = 0;
-    const int64_t N = O.n_walks;
+    const int64_t N = Pv.total();
 
     // warp-local queue of walk ids [q_next, q_end), refilled WALK_CHUNK at a
     // time from the global counter (warp-uniform values)
@@ -207,20 +280,14 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
         }
         if (__all_sync(0xffffffffu, s.state == S_EXIT)) break;
 
-        int32_t *nrow = O.node + s.w * (int64_t)O.cap;
-        int64_t *trow = O.ts + s.w * (int64_t)O.cap;
         bool pick = false;   // the bracket closed this iteration: draw now
         bool finish = false; // the walk ended this iteration
 
         switch (s.state) {
             case S_NEW: {
-                int32_t L = O.len_arr ? O.len_arr[s.w] : O.max_len;
-                int bias = O.bias_arr ? (int)O.bias_arr[s.w] : O.bias;
-                if (L < 2 || L > O.cap || bias < 0 || bias > 2) {
-                    atomicOr(&O.cnt->status, 1ull);
-                    L = L < 2 ? 2 : (L > O.cap ? O.cap : L);
-                    bias = (bias < 0 || bias > 2) ? BIAS_UNIFORM : bias;
-                }
+                int32_t L;
+                int bias;
+                Pv.open(s.w, cx, L, bias);
                 s.cap_len = L;
                 s.bias = bias;
                 s.len = 0;
@@ -228,11 +295,11 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                     finish = true;
                     break;
                 }
-                const Rand4 r = walk_rand(O.seed, (uint64_t)s.w, 0u);
+                const Rand4 r = walk_rand(Pv.seed(cx), Pv.wid(cx), 0u);
                 const uint64_t u1 = u53_bits(r.r0, r.r1);
                 s.ud = u53_bits(r.r2, r.r3);
                 s.orient = (!V.directed && (r.r3 & 1u)) ? 1u : 0u;
-                if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
+                if (Pv.policy(cx) == TEMPEST_START_UNIFORM_EDGE) {
                     const int64_t k = uniform_index_k(u1, V.m);
                     y0 = __ldg(V.st_ts + k);
                     z0 = __ldg(V.st_src + k);
@@ -261,6 +328,8 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                     a = b;
                     b = x;
                 }
+                int32_t *nrow = Pv.nrow(cx);
+                int64_t *trow = Pv.trow(cx);
                 nrow[0] = a;
                 nrow[1] = b;
                 trow[0] = INT64_MIN;
@@ -345,8 +414,8 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 break;
             }
             case S_HOP: {
-                nrow[s.len] = z0;
-                trow[s.len] = y0;
+                Pv.nrow(cx)[s.len] = z0;
+                Pv.trow(cx)[s.len] = y0;
                 hops++;
                 bytes += hop_model_bytes((int64_t)(s.g1 - s.g0));
                 s.len++;
@@ -370,7 +439,7 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
         if (pick) {
             // c = s.R is the first group later than t; draw the next edge
             const int32_t c = s.R;
-            const Rand4 r = walk_rand(O.seed, (uint64_t)s.w, s.hop);
+            const Rand4 r = walk_rand(Pv.seed(cx), Pv.wid(cx), s.hop);
             const uint64_t u1 = u53_bits(r.r0, r.r1);
             if (s.bias == BIAS_UNIFORM) {
                 s.ud = u1;
@@ -385,15 +454,15 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
             s.state = S_PICK2;
         }
         if (finish) {
-            O.len[s.w] = s.len;
+            Pv.finish(cx, s.len);
             s.state = S_FETCH;
         }
     }
     hops = warp_sum(hops);
     bytes = warp_sum(bytes);
     if (lane == 0 && hops) {
-        atomicAdd(&O.cnt->hops, hops);
-        atomicAdd(&O.cnt->model_bytes, bytes);
+        atomicAdd(&Pv.cnt()->hops, hops);
+        atomicAdd(&Pv.cnt()->model_bytes, bytes);
     }
 }
 
@@ -413,6 +482,60 @@ __global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, 
             tr[i] = INT64_MIN;
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_pad_rows_multi(const ReqDesc *__restrict__ reqs, int n_req, int64_t total,
+                                                        WalkCounters *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
+        int lo = 0, hi = n_req - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (reqs[mid].offset <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const ReqDesc &q = reqs[lo];
+        const int64_t w = g - q.offset;
+        if (w < 0 || w >= q.n_walks) {
+            if (lane == 0) atomicOr(&cnt->status, 1ull << 9);
+            continue;
+        }
+        const int32_t l = q.len[w];
+        if (l < 0 || l > q.cap) {
+            if (lane == 0) atomicOr(&cnt->status, 1ull << 10);
+            continue;
+        }
+        int32_t *nr = q.node + w * (int64_t)q.cap;
+        int64_t *tr = q.ts + w * (int64_t)q.cap;
+        for (int32_t i = l + lane; i < q.cap; i += 32) {
+            nr[i] = -1;
+            tr[i] = INT64_MIN;
+        }
+    }
+}
+
+int walks_multi_launch(tempest_t *h, const ReqDesc *dev_reqs, int n_req, int64_t total, WalkCounters *cnt,
+                       cudaStream_t st)
+{
+    cudaMemsetAsync(cnt, 0, sizeof(WalkCounters), st);
+    if (total <= 0 || n_req <= 0) return cuda_check(h, cudaGetLastError(), "walks multi");
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walks_stream<ManyReq>, 256, 0);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    int64_t grid = (int64_t)h->num_sms * blocks_per_sm;
+    const int64_t need = (total + 255) / 256;
+    if (grid > need) grid = need;
+    const WalkView V = make_view(h);
+    k_walks_stream<ManyReq><<<(unsigned)grid, 256, 0, st>>>(V, ManyReq{dev_reqs, n_req, total, cnt}, &cnt->pad);
+    int64_t pgrid = (total + 7) / 8;
+    const int64_t pcap = (int64_t)h->num_sms * 16;
+    if (pgrid > pcap) pgrid = pcap;
+    k_pad_rows_multi<<<(unsigned)pgrid, 256, 0, st>>>(dev_reqs, n_req, total, cnt);
+    return cuda_check(h, cudaGetLastError(), "walks multi");
 }
 
 __global__ void k_sample_index(const uint64_t *__restrict__ ub, const int64_t *__restrict__ n, int64_t count,
@@ -498,13 +621,13 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
         } else {
             static int blocks_per_sm = 0;
             if (blocks_per_sm == 0) {
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walks_stream, 256, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walks_stream<OneReq>, 256, 0);
                 if (blocks_per_sm < 1) blocks_per_sm = 1;
             }
             int64_t grid = (int64_t)h->num_sms * blocks_per_sm;
             const int64_t need = (rq.n_walks + 255) / 256;
             if (grid > need) grid = need;
-            k_walks_stream<<<(unsigned)grid, 256, 0, st>>>(V, O, &O.cnt->pad);
+            k_walks_stream<OneReq><<<(unsigned)grid, 256, 0, st>>>(V, OneReq{O}, &O.cnt->pad);
             int64_t pgrid = (rq.n_walks + 7) / 8;
             const int64_t pcap = (int64_t)h->num_sms * 16;
             if (pgrid > pcap) pgrid = pcap;
