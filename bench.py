@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--workload", default="stream", choices=["stream", "batched", "serve"])
     p.add_argument("--requests", type=int, default=2000)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--autotune", action="store_true", help="pick the walk form and knobs on the warm state")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -173,7 +174,7 @@ def run_ours(args, rank, world):
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    ingest_ms, walk_ms, hops, model_bytes, launches, edges = [], [], 0, 0, 0, 0
+    ingest_ms, walk_ms, walk_kernel_ms, hops, model_bytes, launches, edges = [], [], [], 0, 0, 0, 0
 
     def one_step(step, timed):
         nonlocal hops, model_bytes, launches, edges
@@ -197,12 +198,18 @@ def run_ours(args, rank, world):
         ws = eng.last_walk_stats()
         if timed:
             walk_ms.append(e0.elapsed_time(e1))
+            walk_kernel_ms.append(ws["kernel_ms"])
             hops += ws["hops"]
             model_bytes += ws["model_bytes"]
             launches += ws["launches"]
 
     for s in range(warm):
         one_step(s, False)
+    tune = None
+    if args.autotune:
+        # the autotuner times candidate settings on the warmed-up window
+        # (outside the timed region) and leaves the fastest selected
+        tune = eng.autotune(n_walks, L, bias=_lib.BIAS_EXP, seed=seed_base + 99, forms=True)
     clocks = ClockSampler()
     if rank == 0:
         clocks.start()
@@ -223,7 +230,8 @@ def run_ours(args, rank, world):
     counts = eng.counts()
     res = dict(hops=hops, walk_s=walk_s, ingest_s=ingest_s, edges=edges, total_ms=total_ms,
                model_bytes=model_bytes, launches=launches, ingest_ms=ingest_ms, walk_ms=walk_ms,
-               live=counts["m"], clocks=clk, gen_s=t_gen, n_walks=n_walks)
+               walk_kernel_ms=walk_kernel_ms, live=counts["m"], clocks=clk, gen_s=t_gen, n_walks=n_walks,
+               n_nodes=counts["n_nodes"], G_tot=counts["G_tot"], Gn=counts["Gn"], tune=tune)
 
     # end to end through the C ABI with host buffers (one step, after the timed ones)
     if not args.no_e2e:
@@ -608,8 +616,17 @@ def main():
     if rank != 0:
         return
     peak, peak_kind = measured_peaks()
-    walk_kernel_s = walk_s  # one kernel (plus a 32-byte counter reset) per call
+    # the walk kernel's own device time (events around its launch inside the
+    # library, on the launching stream); the call adds the row padding
+    walk_kernel_s = sum(res["walk_kernel_ms"]) / 1e3
     achieved = res["model_bytes"] / walk_kernel_s / 1e9 if walk_kernel_s > 0 else 0.0
+    # ingest: algorithmic bytes per batch of the linear-merge design,
+    # 16b (batch read) + 16b (store write) + 24m (node view read + write)
+    # + 8N (per-node offsets) + 4 (G_tot + Gn) (group offsets)
+    b_edges = edges / max(1, len(res["ingest_ms"]))
+    ing_bytes = 32 * b_edges + 24 * res["live"] + 8 * res["n_nodes"] + 4 * (res["G_tot"] + res["Gn"])
+    ing_s_mean = ingest_s / max(1, len(res["ingest_ms"]))
+    ing_achieved = ing_bytes / ing_s_mean / 1e9 if ing_s_mean > 0 else 0.0
     traffic = recorded_traffic(res["hops"] / max(1, len(res["walk_ms"])))
     cpu = None
     if not args.no_cpu:
@@ -617,6 +634,9 @@ def main():
         cpu = {"value": o["hops_per_s"], "unit": "hops/s", "cores": 1, "kind": "oracle", "sample": o["sample"],
                "ingest_edges_per_s": o["edges_per_s"]}
     per_launch_bytes = res["model_bytes"] / max(1, len(res["walk_ms"]))
+    sched = args.sched
+    if res.get("tune"):
+        sched = {0: "full", 1: "coop", 2: "stream", 3: "graph"}[res["tune"]["sched"]]
     out = {
         "metric": METRIC,
         "value": hops / walk_s if walk_s > 0 else 0.0,
@@ -636,7 +656,7 @@ def main():
                    "batch_edges": int(10_000_000 * args.scale), "window_edges": int(200_000_000 * args.scale),
                    "walks_per_call": res["n_walks"], "max_len": args.max_len, "bias": "exponential",
                    "start": "uniform edge", "batches_per_step": BATCHES_PER_STEP,
-                   "scheduler": args.sched, "l2": "inputs larger than L2 (160 MB batches, GB-sized state)",
+                   "scheduler": sched, "l2": "inputs larger than L2 (160 MB batches, GB-sized state)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "ingest_edges_per_s": edges / ingest_s if ingest_s > 0 else 0.0,
         "stream_hops_per_s": hops / (total_ms / 1e3) if total_ms > 0 else 0.0,
@@ -649,15 +669,25 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": {"stream": "k_walks_stream", "full": "k_walks_full",
-                                "coop": "coop tiers", "graph": "k_graph_hop"}[args.sched],
+                                "coop": "coop tiers", "graph": "k_graph_hop"}[sched],
                      "peak_kind": peak_kind + " hbm copy (burst)",
                      "model_bytes_per_launch": per_launch_bytes},
+        "ingest_roofline": {"bound": "hbm", "achieved": ing_achieved, "peak": peak, "unit": "GB/s",
+                            "frac": ing_achieved / peak, "bytes_per_batch": ing_bytes,
+                            "time": "whole tempest_ingest call (batch p50 above)"},
+        "walk_call_ms_mean": 1e3 * walk_s / max(1, len(res["walk_ms"])),
+        "walk_kernel_ms_mean": 1e3 * walk_kernel_s / max(1, len(res["walk_ms"])),
         "cpu_baseline": cpu,
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
     }
     if "e2e" in res:
         out["e2e"] = res["e2e"]
+    if res.get("tune"):
+        t = res["tune"]
+        out["autotune"] = {k: t[k] for k in ("sched", "bkt_log", "coop_w_warp", "coop_mega", "stream_ctas",
+                                             "best_ms", "start_ms")}
+        out["autotune"]["trials"] = len(t["trials"])
     print(json.dumps(out), flush=True)
 
 

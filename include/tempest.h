@@ -101,6 +101,10 @@ typedef struct {
     int64_t tier_launches[5]; /* TEMPEST_SCHED_COOP: terminal-kernel launches
                                  per tier (solo, warp-smem, warp-global,
                                  block-smem, block-global) */
+    double kernel_ms;      /* device time of the walk kernels proper (start
+                              draw and hops, without the row padding and
+                              without the index preparation), from CUDA
+                              events on the handle's stream; 0 if none ran */
 } tempest_walk_stats;
 
 /* Create an engine.  window > 0: duration Delta in timestamp units, the
@@ -238,6 +242,53 @@ int tempest_server_stats(tempest_server_t *s, int64_t out[4]);
 
 /* Select the walk execution form (TEMPEST_SCHED_*) for later walk calls. */
 int tempest_set_scheduler(tempest_t *h, int mode);
+
+/* Tuning knobs.  None of them changes a walk, only how fast it is drawn:
+ * every setting gives bit-identical outputs.  Change them between walk calls
+ * (not while a server wave is in flight). */
+enum {
+    /* log2 of the mean number of timestamp groups per time bucket of a node
+     * with >= 32 groups (the hop search index, Sec. 2.3), 0..5; default 2 */
+    TEMPEST_TUNE_BKT_LOG = 0,
+    /* TEMPEST_SCHED_COOP: largest run of walks at one node served one thread
+     * per walk (W_warp of Sec. 2.4.3), 1..256; default 4 */
+    TEMPEST_TUNE_COOP_W_WARP = 1,
+    /* TEMPEST_SCHED_COOP: walks per block sub-task of a mega-hub run
+     * (Sec. 2.4.4), 256..2^30; default 8192 */
+    TEMPEST_TUNE_COOP_MEGA = 2,
+    /* TEMPEST_SCHED_STREAM: resident 256-thread CTAs per SM of the persistent
+     * walker, 0 = as many as fit; 0..16; default 0 */
+    TEMPEST_TUNE_STREAM_CTAS = 3
+};
+/* Set / read one knob.  EINVAL on an unknown knob or a value out of range. */
+int tempest_set_tuning(tempest_t *h, int knob, int64_t value);
+int tempest_get_tuning(tempest_t *h, int knob, int64_t *value);
+
+#define TEMPEST_TUNE_MAX_TRIALS 48
+typedef struct {
+    int32_t sched, bkt_log, coop_w_warp, coop_mega, stream_ctas, pad;
+    double ms;             /* walk-call device time (start to padded rows) */
+} tempest_tune_trial;
+typedef struct {
+    int32_t sched, bkt_log, coop_w_warp, coop_mega, stream_ctas; /* chosen */
+    int32_t n_trials;
+    double best_ms;        /* call time of the chosen configuration */
+    double start_ms;       /* call time of the configuration it started from */
+    tempest_tune_trial trials[TEMPEST_TUNE_MAX_TRIALS];
+} tempest_tune_report;
+#define TEMPEST_TUNE_FORMS 1  /* flags: also choose the walk form */
+
+/* Autotuner: times walk calls of n_walks walks (max_len, bias, start_policy,
+ * seed as in tempest_walks) on the current index state for candidate
+ * settings, by coordinate descent: the walk form (with TEMPEST_TUNE_FORMS),
+ * then the bucket density, then the chosen form's own knobs (CTAs per SM for
+ * the streaming form; W_warp then the mega-hub split for the cooperative
+ * form).  Each candidate is timed with CUDA events on the handle's stream as
+ * the minimum of 3 calls after one warm-up call; outputs go to scratch
+ * memory the handle owns.  The best setting stays selected on the handle
+ * and is described in *out (nullable).  Blocking; EINVAL on bad arguments. */
+int tempest_autotune(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy, uint64_t seed,
+                     int32_t flags, tempest_tune_report *out);
 
 /* Report of the most recent walk call; waits for its work to finish. */
 int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out);

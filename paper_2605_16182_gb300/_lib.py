@@ -25,6 +25,9 @@ TEMPEST_EBUSY = -5
 BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP = 0, 1, 2
 START_UNIFORM_EDGE, START_BIASED_TS = 0, 1
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH = 0, 1, 2, 3
+TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS = 0, 1, 2, 3
+TUNE_FORMS = 1
+TUNE_MAX_TRIALS = 48
 (STATE_SRC, STATE_DST, STATE_TS, STATE_TS_GROUP_OFF, STATE_NODE_OFF, STATE_NODE_ORDER,
  STATE_NODE_GROUP_OFF, STATE_NODE_GIDX) = range(8)
 
@@ -38,6 +41,7 @@ EXPORTED = (
     "tempest_server_create", "tempest_server_destroy", "tempest_server_submit_walks",
     "tempest_server_submit_ingest", "tempest_server_progress", "tempest_server_status",
     "tempest_server_release", "tempest_server_drain", "tempest_server_stats",
+    "tempest_set_tuning", "tempest_get_tuning", "tempest_autotune",
 )
 NOALLOC_MAX_EDGES = 262144
 
@@ -63,11 +67,30 @@ class IngestStats(ctypes.Structure):
 class WalkStats(ctypes.Structure):
     _fields_ = [("n_walks", ctypes.c_int64), ("hops", ctypes.c_int64),
                 ("model_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("tier_launches", ctypes.c_int64 * 5)]
+                ("tier_launches", ctypes.c_int64 * 5), ("kernel_ms", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["tier_launches"] = list(self.tier_launches)
+        return d
+
+
+class TuneTrial(ctypes.Structure):
+    _fields_ = [("sched", ctypes.c_int32), ("bkt_log", ctypes.c_int32), ("coop_w_warp", ctypes.c_int32),
+                ("coop_mega", ctypes.c_int32), ("stream_ctas", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("sched", ctypes.c_int32), ("bkt_log", ctypes.c_int32), ("coop_w_warp", ctypes.c_int32),
+                ("coop_mega", ctypes.c_int32), ("stream_ctas", ctypes.c_int32), ("n_trials", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
+                ("trials", TuneTrial * TUNE_MAX_TRIALS)]
+
+    def as_dict(self):
+        keys = ("sched", "bkt_log", "coop_w_warp", "coop_mega", "stream_ctas")
+        d = {k: getattr(self, k) for k in keys + ("best_ms", "start_ms")}
+        d["trials"] = [dict({k: getattr(t, k) for k in keys}, ms=t.ms) for t in self.trials[:self.n_trials]]
         return d
 
 
@@ -108,6 +131,10 @@ def load():
     L.tempest_walks.argtypes = [vp, i64, i32, ci, ci, u64, vp, vp, vp]
     L.tempest_walks_mixed.argtypes = [vp, i64, vp, i32, vp, ci, u64, vp, vp, vp]
     L.tempest_set_scheduler.argtypes = [vp, ci]
+    L.tempest_set_tuning.argtypes = [vp, ci, i64]
+    L.tempest_get_tuning.argtypes = [vp, ci, ctypes.POINTER(i64)]
+    L.tempest_autotune.argtypes = [vp, i64, ctypes.c_int32, ci, ci, ctypes.c_uint64, ctypes.c_int32,
+                                   ctypes.POINTER(TuneReport)]
     L.tempest_last_walk_stats.argtypes = [vp, ctypes.POINTER(WalkStats)]
     L.tempest_get_counts.argtypes = [vp, vp]
     L.tempest_export_state.argtypes = [vp, ci, vp, i64, ctypes.POINTER(i64)]
@@ -295,6 +322,23 @@ def tempest_set_scheduler(h, mode: int):
     return _check(h, load().tempest_set_scheduler(h, int(mode)))
 
 
+def tempest_set_tuning(h, knob: int, value: int):
+    return _check(h, load().tempest_set_tuning(h, int(knob), int(value)))
+
+
+def tempest_get_tuning(h, knob: int) -> int:
+    v = ctypes.c_int64()
+    _check(h, load().tempest_get_tuning(h, int(knob), ctypes.byref(v)))
+    return v.value
+
+
+def tempest_autotune(h, n_walks, max_len, bias, start_policy, seed, flags) -> TuneReport:
+    rep = TuneReport()
+    _check(h, load().tempest_autotune(h, int(n_walks), int(max_len), int(bias), int(start_policy),
+                                      int(seed) & ((1 << 64) - 1), int(flags), ctypes.byref(rep)))
+    return rep
+
+
 def tempest_last_walk_stats(h) -> WalkStats:
     ws = WalkStats()
     _check(h, load().tempest_last_walk_stats(h, ctypes.byref(ws)))
@@ -407,6 +451,17 @@ class Engine:
 
     def set_scheduler(self, mode: int):
         tempest_set_scheduler(self.h, mode)
+
+    def set_tuning(self, knob: int, value: int):
+        tempest_set_tuning(self.h, knob, value)
+
+    def get_tuning(self, knob: int) -> int:
+        return tempest_get_tuning(self.h, knob)
+
+    def autotune(self, n_walks, max_len, bias=BIAS_EXP, start_policy=0, seed=0, forms=True) -> dict:
+        """Time candidate settings on the live index and keep the fastest."""
+        return tempest_autotune(self.h, n_walks, max_len, bias, start_policy, seed,
+                                TUNE_FORMS if forms else 0).as_dict()
 
     def ingest(self, src, dst, ts) -> dict:
         n = int(src.shape[0])

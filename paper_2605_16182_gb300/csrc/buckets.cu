@@ -1,0 +1,197 @@
+// buckets.cu -- time-bucket tables over the group timestamps of high-degree
+// nodes: an index for the first step of every hop, finding the start of
+// Gamma_t(v) among v's timestamp groups (Sec. 2.3, 2.5).
+//
+// A node with G >= BKT_MIN_G groups gets K = G >> bkt_log buckets over its
+// timestamp range and a table of K + 1 group indices (see bkt_map).  A hop at
+// such a node reads the node's first and last group timestamps, one pair of
+// adjacent table entries and then bisects the few groups of one bucket,
+// instead of bisecting all G groups with one dependent load per level.
+//
+// The tables depend only on the node view, so they are built once per index
+// state, at the first walk call after an ingest:
+//   1. a compaction over the node segments lists the big segments and
+//      places their tables back to back (prefix of K + 1);
+//   2. a scan over that list numbers their fill chunks (BKT_CHUNK groups);
+//   3. one warp per chunk reads the chunk's group timestamps (coalesced);
+//      group g owns the table entries k in (bucket(g - 1), bucket(g)] (it is
+//      the first group of those buckets) and the node's last group also
+//      owns (bucket(g), K] (value g1).  The warp writes the entries of its
+//      32 groups together: a scan of the per-lane counts gives every lane
+//      its share of consecutive entries, so a long run (a time gap that
+//      leaves many buckets empty) is written 32 entries per store
+//      instruction rather than by one lane.  Every entry is written once.
+#include "engine.cuh"
+#include "prims.cuh"
+#include "walkcore.cuh"
+
+namespace tw {
+
+namespace {
+
+struct BigSegOp {
+    const int32_t *seg_node, *seg_g;
+    int64_t S, Gn;
+    int log_b;
+    int32_t *big_seg, *big_t, *bkt_base;
+    __device__ __forceinline__ uint64_t value(int64_t j) const
+    {
+        const int64_t g1 = j + 1 < S ? seg_g[j + 1] : Gn;
+        const int64_t G = g1 - seg_g[j];
+        if (G < BKT_MIN_G) return 0;
+        return (1ull << 32) | (uint64_t)(bkt_count((int32_t)G, log_b) + 1u);
+    }
+    __device__ __forceinline__ void emit(int64_t j, uint64_t v, uint64_t ex) const
+    {
+        if (!v) return;
+        const uint32_t b = (uint32_t)(ex >> 32);
+        big_seg[b] = (int32_t)j;
+        big_t[b] = (int32_t)(uint32_t)ex;
+        bkt_base[seg_node[j]] = (int32_t)(uint32_t)ex;
+    }
+};
+
+struct ChunkOp {
+    const int32_t *big_seg, *seg_g;
+    int64_t S, Gn;
+    int32_t *big_c;
+    __device__ __forceinline__ uint64_t value(int64_t b) const
+    {
+        const int32_t j = big_seg[b];
+        const int64_t g1 = j + 1 < S ? seg_g[j + 1] : Gn;
+        return (uint64_t)((g1 - seg_g[j] + BKT_CHUNK - 1) / BKT_CHUNK);
+    }
+    __device__ __forceinline__ void emit(int64_t b, uint64_t, uint64_t ex) const { big_c[b] = (int32_t)ex; }
+};
+
+// One warp per chunk (grid-stride); totals of the compaction in tot.
+__global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ big_seg,
+                                                  const int32_t *__restrict__ big_t,
+                                                  const int32_t *__restrict__ big_c, int64_t nb,
+                                                  const uint64_t *__restrict__ tot,
+                                                  const int32_t *__restrict__ seg_node,
+                                                  const int32_t *__restrict__ seg_g, int64_t S, int64_t Gn,
+                                                  const int64_t *__restrict__ ngts, int log_b, int64_t cap,
+                                                  int32_t *bkt, WalkCounters *chk)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nch = (int64_t)*tot;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += warps) {
+        // owning big segment: last b with big_c[b] <= c
+        int64_t lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(big_c + mid) <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t b = lo;
+        const int32_t j = __ldg(big_seg + b);
+        const int32_t g0 = __ldg(seg_g + j);
+        const int32_t g1 = j + 1 < S ? __ldg(seg_g + j + 1) : (int32_t)Gn;
+        const uint32_t K = bkt_count(g1 - g0, log_b);
+        const int64_t tb = __ldg(big_t + b);
+        if (tb + K >= cap || g1 - g0 < BKT_MIN_G) {  // inconsistent lists
+            if (lane == 0) atomicOr(&chk->status, 1ull << 12);
+            continue;
+        }
+        const BktMap bm = bkt_map(__ldg(ngts + g0), __ldg(ngts + g1 - 1), K);
+        const int32_t start = g0 + (int32_t)(c - __ldg(big_c + b)) * BKT_CHUNK;
+        const int32_t end = min(g1, start + BKT_CHUNK);
+        for (int32_t base = start; base < end; base += 32) {
+            const int32_t g = base + lane;
+            const bool valid = g < end;
+            const int32_t k = valid ? (int32_t)bkt_index(bm, __ldg(ngts + g)) : 0;
+            int32_t kp = __shfl_up_sync(0xffffffffu, k, 1);
+            if (lane == 0) kp = g == g0 ? -1 : (int32_t)bkt_index(bm, __ldg(ngts + g - 1));
+            // entries (kp, k] hold g; the last group adds (k, K] holding g1
+            const bool last = valid && g == g1 - 1;
+            const int32_t lo_k = kp + 1;
+            const int32_t cnt = valid ? (last ? (int32_t)K : k) - kp : 0;
+            int32_t incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int32_t excl = incl - cnt;
+            const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int32_t r0 = 0; r0 < total; r0 += 32) {
+                const int32_t idx = r0 + lane;
+                // owner: the last lane whose share starts at or before idx
+                int32_t own = 0;
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int32_t j = own + step;
+                    if (__shfl_sync(0xffffffffu, excl, j) <= idx) own = j;
+                }
+                const int32_t o_lo = __shfl_sync(0xffffffffu, lo_k, own);
+                const int32_t o_ex = __shfl_sync(0xffffffffu, excl, own);
+                const int32_t o_g = __shfl_sync(0xffffffffu, g, own);
+                const int32_t o_k = __shfl_sync(0xffffffffu, k, own);
+                if (idx < total) {
+                    const int32_t kk = o_lo + (idx - o_ex);
+                    bkt[tb + kk] = kk <= o_k ? o_g : g1;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int prepare_walk_index(tempest_t *h)
+{
+    if (h->bkt_ver == h->state_ver) return TEMPEST_OK;
+    cudaStream_t st = h->stream;
+    const int64_t S = h->S, Gn = h->Gn, N = h->N;
+    int rc;
+    h->n_big = 0;
+    if (S > 0 && Gn >= BKT_MIN_G) {
+        const size_t Sz = (size_t)S;
+        if ((rc = ensure(h, h->bkt_base, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
+        if ((rc = ensure(h, h->big_seg, sizeof(int32_t) * Sz, true))) return rc;
+        if ((rc = ensure(h, h->big_t, sizeof(int32_t) * Sz, true))) return rc;
+        if ((rc = ensure(h, h->big_c, sizeof(int32_t) * Sz, true))) return rc;
+        if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
+        if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
+        uint64_t *part = h->partials.as<uint64_t>();
+        BigSegOp op{h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>(), S, Gn, h->bkt_log,
+                    h->big_seg.as<int32_t>(), h->big_t.as<int32_t>(), h->bkt_base.as<int32_t>()};
+        const int nblk = scan_launch(op, S, part, st);
+        uint64_t *hp = static_cast<uint64_t *>(h->hstat);
+        cudaMemcpyAsync(hp, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+        if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket lists"))) return rc;
+        const uint64_t tot = hp[0];
+        const int64_t nb = (int64_t)(tot >> 32), cap = (int64_t)(uint32_t)tot;
+        if (cap >= (int64_t)INT32_MAX)
+            return fail(h, TEMPEST_ENOMEM, "walk index: %lld bucket entries exceed the int32 range",
+                        (long long)cap);
+        if (nb > 0) {
+            if ((rc = ensure(h, h->bkt, sizeof(int32_t) * (size_t)cap, true))) return rc;
+            ChunkOp cop{h->big_seg.as<int32_t>(), h->seg_g.as<int32_t>(), S, Gn, h->big_c.as<int32_t>()};
+            const int nblk2 = scan_launch(cop, nb, part, st);
+            // the fill's consistency flag goes to the walk counters, which
+            // every walk call zeroes before its kernels: read it here
+            cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);
+            const int64_t nch_max = Gn / BKT_CHUNK + nb;  // chunks <= sum(G / CHUNK + 1)
+            int64_t grid = (nch_max + 7) / 8;
+            const int64_t gcap = (int64_t)h->num_sms * 16;
+            if (grid > gcap) grid = gcap;
+            k_bkt_fill<<<(unsigned)grid, 256, 0, st>>>(h->big_seg.as<int32_t>(), h->big_t.as<int32_t>(),
+                                                       h->big_c.as<int32_t>(), nb, part + nblk2,
+                                                       h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>(), S, Gn,
+                                                       h->ngts.as<int64_t>(), h->bkt_log, cap,
+                                                       h->bkt.as<int32_t>(), h->wcnt.as<WalkCounters>());
+            WalkCounters *hc = static_cast<WalkCounters *>(h->hstat);
+            cudaMemcpyAsync(hc, h->wcnt.p, sizeof(WalkCounters), cudaMemcpyDeviceToHost, st);
+            if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket fill"))) return rc;
+            if (hc->status)
+                return fail(h, TEMPEST_ECUDA, "walk index: bucket table check failed (code 0x%llx)",
+                            (unsigned long long)hc->status);
+        }
+        h->n_big = nb;
+    }
+    h->bkt_ver = h->state_ver;
+    return TEMPEST_OK;
+}
+
+}  // namespace tw

@@ -138,7 +138,8 @@ static void free_all(tempest_t *h)
                     &h->partials,  &h->seg_node,  &h->seg_g,     &h->gcnt,      &h->dstat,    &h->wcnt,
                     &h->out_stage, &h->in_stage,  &h->exp_stage,
                     &h->co_node,   &h->co_t,      &h->co_len,    &h->co_act[0], &h->co_act[1], &h->co_runs,
-                    &h->co_tasks,  &h->co_ctr};
+                    &h->co_tasks,  &h->co_ctr,    &h->bkt_base,  &h->bkt,       &h->big_seg,   &h->big_t,
+                    &h->big_c,     &h->tune_out};
     for (DBuf *b : bufs) release(h, *b);
 }
 
@@ -189,6 +190,8 @@ int tempest_destroy(tempest_t *h)
     if (!h) return TEMPEST_OK;
     cudaStreamSynchronize(h->stream);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    for (cudaEvent_t &e : h->kev)
+        if (e) cudaEventDestroy(e);
     free_all(h);
     if (h->hstat) cudaFreeHost(h->hstat);
     delete h;
@@ -364,6 +367,10 @@ int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out)
         if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "walk stats"))) return rc;
         h->last_ws.hops = (int64_t)hc->hops;
         h->last_ws.model_bytes = (int64_t)hc->model_bytes;
+        if (h->kev_valid) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, h->kev[0], h->kev[1]) == cudaSuccess) h->last_ws.kernel_ms = ms;
+        }
         if (hc->status) {
             *out = h->last_ws;
             return fail(h, TEMPEST_EINVAL, "walks_mixed: a per-walk max_len or bias was out of range "

@@ -170,7 +170,7 @@ __device__ __forceinline__ void coop_hop(const WalkView &V, const WalkOut &O, co
         }
         c = g0 + lo;
     } else {
-        c = upper_bound_ts(V.ngts, g0, g1, t);
+        c = first_later(V, v, g0, g1, t);
     }
     if (c == g1) {
         O.len[w] = len;  // Gamma_t(v) is empty

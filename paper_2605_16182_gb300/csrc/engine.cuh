@@ -88,6 +88,18 @@ struct tempest {
     tw::DBuf ngo;      // int32 [Gn+1] node group start offsets
     tw::DBuf ngts;     // int64 [Gn]   node group timestamps
     tw::DBuf gidx;     // int32 [N+1]  first group of each node
+    int64_t S = 0;     // node segments (nodes with at least one entry)
+    int64_t state_ver = 0;  // bumped by every ingest
+
+    // time buckets of high-degree nodes (built lazily for the walks of a
+    // state version): per node its table base, the tables, the big-segment
+    // list and its chunk prefix
+    tw::DBuf bkt_base;   // int32 [N+1]
+    tw::DBuf bkt;        // int32 tables
+    tw::DBuf big_seg, big_t, big_c;
+    int64_t bkt_ver = -1;
+    int64_t n_big = 0;
+    int bkt_log = 2;     // log2 of the mean groups per bucket
 
     // scratch
     tw::DBuf b_src, b_dst, b_ts;     // batch staged from host
@@ -100,6 +112,8 @@ struct tempest {
     tw::DBuf co_node, co_t, co_len, co_act[2], co_runs, co_tasks, co_ctr;
     int coop_w_warp = 4;         // solo / warp boundary W_warp (Sec. 3.5)
     int coop_mega = 8192;        // mega-hub split (Sec. 2.4.4)
+    int stream_ctas = 0;         // persistent walker CTAs per SM (0: occupancy limit)
+    tw::DBuf tune_out;           // autotuner walk outputs
     int64_t coop_tier_launches[5] = {0, 0, 0, 0, 0};
     cudaGraphExec_t graph_exec = nullptr;  // captured hop loop (TEMPEST_SCHED_GRAPH)
     int32_t graph_cap = 0;
@@ -112,6 +126,8 @@ struct tempest {
     void *hstat = nullptr;     // pinned host mirror of IngestScratch / counters
 
     tempest_walk_stats last_ws{};
+    cudaEvent_t kev[2] = {nullptr, nullptr};  // brackets the walk kernels of the last call
+    bool kev_valid = false;
     int64_t pending_launches = 0;
     std::string err;
 };
@@ -148,6 +164,9 @@ struct WalkRequest {
     int32_t *len;              // device
 };
 int walks_run(tempest_t *h, const WalkRequest &rq);
+// builds the time-bucket tables of the live state on the handle's stream
+// (no-op when they are current); every walk form calls it before launching
+int prepare_walk_index(tempest_t *h);
 int sample_index_run(tempest_t *h, const uint64_t *ub, const int64_t *n, int64_t count, int bias, double lambda,
                      int64_t *out);
 

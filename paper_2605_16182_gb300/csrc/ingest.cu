@@ -537,6 +537,7 @@ static int node_view_groups(tempest_t *h, int nxt, int64_t M, int64_t N, bool ne
     const int64_t Gn = M > 0 ? (int64_t)(uint32_t)tot : 0;
     const int64_t S = M > 0 ? (int64_t)(tot >> 32) : 0;
     h->Gn = Gn;
+    h->S = S;
     k_set_i32<<<1, 1, 0, st>>>(h->ngo.as<int32_t>() + Gn, (int32_t)M);
     cudaMemsetAsync(h->gcnt.as<int32_t>(), 0, sizeof(int32_t) * (size_t)(N + 1), st);
     if (S > 0)
@@ -674,6 +675,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     if (n >= (int64_t)INT32_MAX) return fail(h, TEMPEST_EINVAL, "tempest_ingest: batch of %lld edges too large",
                                              (long long)n);
     h->pending_launches = 0;
+    h->state_ver++;  // derived walk indexes are rebuilt on the next walk call
     if ((rc = ensure(h, h->dstat, sizeof(IngestScratch)))) return rc;
     if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
     if ((rc = ensure(h, h->hist, sizeof(uint32_t) * ((size_t)RADIX * SORT_MAX_BLOCKS + 1)))) return rc;

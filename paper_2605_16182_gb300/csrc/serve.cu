@@ -216,6 +216,14 @@ int launch_wave(tempest_server *s, tempest_server::Wave &wv, int &rc)
         return (int)ids.size();
     }
     const int n = compact_table(wv.stage, (int)ids.size());
+    // derived walk indexes of the current state, built on the handle's stream
+    if ((rc = prepare_walk_index(s->h))) {
+        for (uint64_t id : ids) {
+            s->reqs[id].state = rc;
+            s->reqs[id].t_done = now_s();
+        }
+        return (int)ids.size();
+    }
     // the wave runs after everything queued on the handle's stream so far
     // (for example the kernels that produced or last used its buffers)
     cudaEventRecord(s->order_ev, s->h->stream);
@@ -260,6 +268,8 @@ int tempest_walks_batch(tempest_t *h, const tempest_walk_request *reqs, int n_re
                          "batch table")))
         return rc;
     if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "batch table"))) return rc;
+    h->kev_valid = false;
+    if ((rc = prepare_walk_index(h))) return rc;
     rc = walks_multi_launch(h, h->in_stage.as<ReqDesc>(), n, total, h->wcnt.as<WalkCounters>(), h->stream);
     h->last_ws.n_walks = total;
     h->last_ws.launches = 2;

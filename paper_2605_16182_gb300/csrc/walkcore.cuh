@@ -22,6 +22,10 @@ struct WalkView {
     const int32_t *ngo;    // [Gn+1]
     const int64_t *ngts;   // [Gn]
     const Entry *ent;      // [M]
+    // time buckets of nodes with at least BKT_MIN_G groups (null: none)
+    const int32_t *bkt_base;  // [N+1], valid for those nodes
+    const int32_t *bkt;
+    int bkt_log;
     int directed;
     ExpRate rate_hop, rate_start;
 };
@@ -51,6 +55,73 @@ __device__ __forceinline__ int32_t upper_bound_ts(const int64_t *__restrict__ gt
         else lo = mid + 1;
     }
     return lo;
+}
+
+// Time buckets of a node with G >= BKT_MIN_G groups [g0, g1) and first /
+// last group timestamps tlo < thi (a node's groups have distinct
+// timestamps).  The node has K = G >> log_b buckets over [tlo, thi]; the map
+// from a time to its bucket is monotone non-decreasing and fills [0, K):
+// the offset t - tlo is normalised so that thi - tlo lands in [2^30, 2^31)
+// (32-bit values, so no 64-bit conversion is needed), converted to float
+// and scaled by K / (normalised span + 1), then truncated and clamped to
+// K - 1.  Each step is monotone (int-to-float rounding, a multiply by a
+// positive constant, truncation), and the same inline code builds and reads
+// the tables, so both sides agree bit for bit.  The node's table (K + 1
+// int32 at bkt_base[v]) holds for each k the first group whose bucket is
+// >= k, and g1 at k = K.  By monotonicity every group before table[k] is
+// earlier than any t in bucket k and every group from table[k + 1] on is
+// later, so for tlo <= t < thi the first group later than t lies in
+// [table[k], table[k + 1]], k = bucket(t).
+constexpr int32_t BKT_MIN_G = 32;
+constexpr int32_t BKT_CHUNK = 256;  // groups per table-fill task
+
+__device__ __forceinline__ uint32_t bkt_count(int32_t G, int log_b) { return (uint32_t)(G >> log_b); }
+
+struct BktMap {
+    int64_t tlo;
+    int sh;       // > 0: right shift by sh; < 0: left shift by -sh
+    float scale;  // K / (normalised span + 1)
+    uint32_t K;
+};
+
+__device__ __forceinline__ uint32_t bkt_norm(uint64_t a, int sh)
+{
+    return sh >= 0 ? (uint32_t)(a >> sh) : (uint32_t)(a << (-sh));
+}
+
+__device__ __forceinline__ BktMap bkt_map(int64_t tlo, int64_t thi, uint32_t K)
+{
+    BktMap m;
+    const uint64_t d = (uint64_t)thi - (uint64_t)tlo;  // >= 1
+    m.tlo = tlo;
+    m.sh = (64 - __clzll((long long)d)) - 31;         // bit length - 31
+    const uint32_t dn = bkt_norm(d, m.sh);             // in [2^30, 2^31)
+    m.scale = __fdividef((float)K, (float)(dn + 1u));
+    m.K = K;
+    return m;
+}
+
+__device__ __forceinline__ uint32_t bkt_index(const BktMap &m, int64_t t)
+{
+    const uint32_t an = bkt_norm((uint64_t)t - (uint64_t)m.tlo, m.sh);
+    const uint32_t k = (uint32_t)((float)an * m.scale);
+    return k < m.K ? k : m.K - 1u;
+}
+
+// First group of v in [g0, g1) whose timestamp is > t (g1 when none):
+// through the node's time buckets when it has them, else a plain bisection.
+__device__ __forceinline__ int32_t first_later(const WalkView &V, int32_t v, int32_t g0, int32_t g1, int64_t t)
+{
+    if (V.bkt && g1 - g0 >= BKT_MIN_G) {
+        const int64_t tlo = __ldg(V.ngts + g0), thi = __ldg(V.ngts + g1 - 1);
+        if (t < tlo) return g0;
+        if (t >= thi) return g1;
+        const int32_t tb = __ldg(V.bkt_base + v);
+        const uint32_t k = bkt_index(bkt_map(tlo, thi, bkt_count(g1 - g0, V.bkt_log)), t);
+        const int32_t lo = __ldg(V.bkt + tb + k), hi = __ldg(V.bkt + tb + k + 1);
+        return upper_bound_ts(V.ngts, lo, hi, t);
+    }
+    return upper_bound_ts(V.ngts, g0, g1, t);
 }
 
 __device__ __forceinline__ int ceil_log2_plus1(int64_t G)

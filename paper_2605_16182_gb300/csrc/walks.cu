@@ -7,6 +7,8 @@
 // bias and reads one 16-byte entry.  Every draw comes from Philox keyed by
 // (seed, walk, hop), so the result is independent of how walks are mapped to
 // threads.
+#include <algorithm>
+
 #include "engine.cuh"
 #include "prims.cuh"
 #include "walkcore.cuh"
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
             int64_t t = t0;
             for (uint32_t h = 1; len < L; h++) {
                 const int32_t g0 = __ldg(V.gidx + v), g1 = __ldg(V.gidx + v + 1);
-                const int32_t c = upper_bound_ts(V.ngts, g0, g1, t);
+                const int32_t c = first_later(V, v, g0, g1, t);
                 if (c == g1) break;  // Gamma_t(v) is empty
                 r = walk_rand(O.seed, (uint64_t)w, h);
                 const uint64_t h1 = u53_bits(r.r0, r.r1);
@@ -122,6 +124,7 @@ enum : int {
     S_EDGE,        // start edge loaded
     S_RANGE,       // node group range loaded
     S_ENDS,        // first / last group timestamps loaded
+    S_BKT,         // time-bucket table pair loaded (high-degree node)
     S_SEARCH,      // one probe loaded
     S_PICK2,       // chosen group's entry range loaded
     S_HOP,         // chosen entry loaded
@@ -357,6 +360,7 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 } else {
                     y0 = __ldg(V.ngts + z0);
                     y1 = __ldg(V.ngts + z1 - 1);
+                    if (V.bkt && z1 - z0 >= BKT_MIN_G) z0 = __ldg(V.bkt_base + s.v);
                     s.state = S_ENDS;
                 }
                 break;
@@ -367,6 +371,13 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                     pick = true;
                 } else if (s.t >= y1) {
                     finish = true;  // Gamma_t(v) is empty
+                } else if (V.bkt && s.g1 - s.g0 >= BKT_MIN_G) {
+                    // y0 <= t < y1: the bucket of t brackets c (z0: table base)
+                    const uint32_t k = bkt_index(bkt_map(y0, y1, bkt_count(s.g1 - s.g0, V.bkt_log)), s.t);
+                    const int32_t *tp = V.bkt + z0 + k;
+                    z0 = __ldg(tp);
+                    z1 = __ldg(tp + 1);
+                    s.state = S_BKT;
                 } else {
                     s.L = s.g0;
                     s.R = s.g1 - 1;
@@ -384,6 +395,23 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 }
                 break;
             }
+            case S_BKT: {
+                // c lies in [z0, z1]: groups before z0 are not later than t,
+                // group z1 (or g1) is later
+                if (z0 == z1) {
+                    s.R = z0;
+                    pick = true;
+                } else {
+                    s.L = z0 - 1;
+                    s.R = z1;
+                    s.prev_w = -1;  // bracket values unknown: bisect only
+                    const int32_t p = s.L + ((s.R - s.L) >> 1);
+                    z1 = p;
+                    y0 = __ldg(V.ngts + p);
+                    s.state = S_SEARCH;
+                }
+                break;
+            }
             case S_SEARCH: {
                 const int32_t p = z1;
                 if (y0 > s.t) {
@@ -397,8 +425,8 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 if (width == 1) {
                     pick = true;
                 } else {
-                    const bool bisect = 2 * width > s.prev_w;
-                    s.prev_w = width;
+                    const bool bisect = s.prev_w < 0 || 2 * width > s.prev_w;
+                    if (s.prev_w >= 0) s.prev_w = width;
                     const int32_t q = interp_probe(s.L, s.R, s.vL, s.vR, s.t, bisect);
                     z1 = q;
                     y0 = __ldg(V.ngts + q);
@@ -467,19 +495,44 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
 }
 
 // Padding of every row after its walk: node -1, ts INT64_MIN from len to the
-// row end.  One warp per row, lanes on consecutive cells.
+// row end.  A warp takes 32 consecutive rows per step: one coalesced load
+// of their lengths, then row by row with the lanes on consecutive cells,
+// as 16-byte stores when the rows are 16-byte aligned (cap % 4 == 0 and
+// aligned bases) and element stores otherwise.
 __global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, const int32_t *__restrict__ len,
                                                   int32_t *node, int64_t *ts)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_walks; w += warps) {
-        const int32_t l = len[w];
-        int32_t *nr = node + w * (int64_t)cap;
-        int64_t *tr = ts + w * (int64_t)cap;
-        for (int32_t i = l + lane; i < cap; i += 32) {
-            nr[i] = -1;
-            tr[i] = INT64_MIN;
+    const bool vec = (cap & 3) == 0 && ((uintptr_t)node & 15) == 0 && ((uintptr_t)ts & 15) == 0;
+    const int4 n4 = make_int4(-1, -1, -1, -1);
+    const longlong2 t2 = make_longlong2(INT64_MIN, INT64_MIN);
+    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < n_walks; w0 += warps * 32) {
+        const int32_t mine = w0 + lane < n_walks ? len[w0 + lane] : cap;
+        const int rows = (int)min((int64_t)32, n_walks - w0);
+        for (int r = 0; r < rows; r++) {
+            int32_t l = __shfl_sync(0xffffffffu, mine, r);
+            l = l < 0 ? 0 : (l > cap ? cap : l);
+            int32_t *nr = node + (w0 + r) * (int64_t)cap;
+            int64_t *tr = ts + (w0 + r) * (int64_t)cap;
+            if (vec) {
+                for (int32_t q = (l >> 2) + lane; q < (cap >> 2); q += 32) {
+                    if (4 * q >= l) {
+                        reinterpret_cast<int4 *>(nr)[q] = n4;
+                    } else {
+                        for (int32_t i = l; i < 4 * q + 4; i++) nr[i] = -1;
+                    }
+                }
+                for (int32_t q = (l >> 1) + lane; q < (cap >> 1); q += 32) {
+                    if (2 * q >= l) reinterpret_cast<longlong2 *>(tr)[q] = t2;
+                    else tr[l] = INT64_MIN;  // l odd: the second half of the pair
+                }
+            } else {
+                for (int32_t i = l + lane; i < cap; i += 32) {
+                    nr[i] = -1;
+                    tr[i] = INT64_MIN;
+                }
+            }
         }
     }
 }
@@ -516,6 +569,14 @@ __global__ void __launch_bounds__(256) k_pad_rows_multi(const ReqDesc *__restric
     }
 }
 
+// Events bracketing the walk kernels of a call (created on first use).
+static void kernel_mark(tempest_t *h, int which)
+{
+    if (!h->kev[which]) cudaEventCreate(&h->kev[which]);
+    cudaEventRecord(h->kev[which], h->stream);
+    if (which == 1) h->kev_valid = true;
+}
+
 int walks_multi_launch(tempest_t *h, const ReqDesc *dev_reqs, int n_req, int64_t total, WalkCounters *cnt,
                        cudaStream_t st)
 {
@@ -526,11 +587,15 @@ int walks_multi_launch(tempest_t *h, const ReqDesc *dev_reqs, int n_req, int64_t
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walks_stream<ManyReq>, 256, 0);
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
-    int64_t grid = (int64_t)h->num_sms * blocks_per_sm;
+    const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, blocks_per_sm) : blocks_per_sm;
+    int64_t grid = (int64_t)h->num_sms * bps;
     const int64_t need = (total + 255) / 256;
     if (grid > need) grid = need;
     const WalkView V = make_view(h);
+    const bool mark = st == h->stream;
+    if (mark) kernel_mark(h, 0);
     k_walks_stream<ManyReq><<<(unsigned)grid, 256, 0, st>>>(V, ManyReq{dev_reqs, n_req, total, cnt}, &cnt->pad);
+    if (mark) kernel_mark(h, 1);
     int64_t pgrid = (total + 7) / 8;
     const int64_t pcap = (int64_t)h->num_sms * 16;
     if (pgrid > pcap) pgrid = pcap;
@@ -574,6 +639,10 @@ WalkView make_view(tempest_t *h)
     V.ngo = h->ngo.as<int32_t>();
     V.ngts = h->ngts.as<int64_t>();
     V.ent = h->ent[h->vcur].as<Entry>();
+    const bool bk = h->n_big > 0 && h->bkt_ver == h->state_ver;
+    V.bkt_base = bk ? h->bkt_base.as<int32_t>() : nullptr;
+    V.bkt = bk ? h->bkt.as<int32_t>() : nullptr;
+    V.bkt_log = h->bkt_log;
     V.directed = h->directed;
     const double ls = h->lam_start > 0.0 ? h->lam_start : (h->G > 0 ? 1.0 / (double)h->G : 1.0);
     V.rate_hop = ExpRate{h->lam_hop, (float)h->lam_hop, (float)(1.0 / h->lam_hop)};
@@ -584,6 +653,8 @@ WalkView make_view(tempest_t *h)
 int walks_run(tempest_t *h, const WalkRequest &rq)
 {
     int rc;
+    h->kev_valid = false;
+    if ((rc = prepare_walk_index(h))) return rc;
     if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
     cudaStream_t st = h->stream;
     cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);
@@ -605,8 +676,10 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     for (int t = 0; t < 5; t++) h->coop_tier_launches[t] = 0;
     if (rq.n_walks > 0) {
         if (h->sched == TEMPEST_SCHED_COOP || h->sched == TEMPEST_SCHED_GRAPH) {
+            kernel_mark(h, 0);
             int rc2 = h->sched == TEMPEST_SCHED_COOP ? coop_run(h, V, O, launches) : graph_run(h, V, O, launches);
             if (rc2) return rc2;
+            kernel_mark(h, 1);
             int64_t pgrid = (rq.n_walks + 7) / 8;
             const int64_t pcap = (int64_t)h->num_sms * 16;
             if (pgrid > pcap) pgrid = pcap;
@@ -616,7 +689,9 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
             int64_t grid = (rq.n_walks + 255) / 256;
             const int64_t cap = (int64_t)h->num_sms * 8;
             if (grid > cap) grid = cap;
+            kernel_mark(h, 0);
             k_walks_full<<<(unsigned)grid, 256, 0, st>>>(V, O);
+            kernel_mark(h, 1);
             launches++;
         } else {
             static int blocks_per_sm = 0;
@@ -624,10 +699,13 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walks_stream<OneReq>, 256, 0);
                 if (blocks_per_sm < 1) blocks_per_sm = 1;
             }
-            int64_t grid = (int64_t)h->num_sms * blocks_per_sm;
+            const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, blocks_per_sm) : blocks_per_sm;
+            int64_t grid = (int64_t)h->num_sms * bps;
             const int64_t need = (rq.n_walks + 255) / 256;
             if (grid > need) grid = need;
+            kernel_mark(h, 0);
             k_walks_stream<OneReq><<<(unsigned)grid, 256, 0, st>>>(V, OneReq{O}, &O.cnt->pad);
+            kernel_mark(h, 1);
             int64_t pgrid = (rq.n_walks + 7) / 8;
             const int64_t pcap = (int64_t)h->num_sms * 16;
             if (pgrid > pcap) pgrid = pcap;

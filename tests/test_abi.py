@@ -52,3 +52,42 @@ def test_null_handle_is_rejected():
     L = _lib.load()
     assert L.tempest_set_scheduler(None, 0) == _lib.TEMPEST_EINVAL
     assert L.tempest_destroy(None) == _lib.TEMPEST_OK
+
+
+def test_null_handle_tuning_calls():
+    L = _lib.load()
+    assert L.tempest_set_tuning(None, 0, 2) == _lib.TEMPEST_EINVAL
+    assert L.tempest_get_tuning(None, 0, None) == _lib.TEMPEST_EINVAL
+    assert L.tempest_autotune(None, 10, 10, 0, 0, 0, 0, None) == _lib.TEMPEST_EINVAL
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """Sizes and field offsets of the ctypes mirrors equal what a C compiler
+    lays out from include/tempest.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    mirrors = {"tempest_ingest_stats": _lib.IngestStats, "tempest_walk_stats": _lib.WalkStats,
+               "tempest_walk_request": _lib.WalkRequest, "tempest_tune_trial": _lib.TuneTrial,
+               "tempest_tune_report": _lib.TuneReport}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tempest.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().split("\n"):
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

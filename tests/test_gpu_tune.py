@@ -1,0 +1,66 @@
+"""Tuning knobs and the autotuner.
+
+Every knob only remaps work to threads, so walks under any setting must be
+bit-identical to walks under the defaults; the autotuner must report the
+trials it timed and leave its choice selected.
+"""
+import pytest
+import torch
+
+from paper_2605_16182_gb300 import _lib, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _engine():
+    spec = synth.config_mid(scale=0.02)
+    eng = _lib.Engine(window=spec.window, directed=True, device="cuda:0")
+    for _, s, d, t in spec.batches(last=8):
+        eng.ingest(s.cuda(), d.cuda(), t.cuda())
+    return eng
+
+
+def _walks(eng, bias, seed=9):
+    return [x.clone() for x in eng.walks(20000, 30, bias=bias, seed=seed)]
+
+
+def test_knobs_validate_and_round_trip():
+    eng = _engine()
+    for knob, bad in ((_lib.TUNE_BKT_LOG, 6), (_lib.TUNE_COOP_W_WARP, 0), (_lib.TUNE_COOP_MEGA, 100),
+                      (_lib.TUNE_STREAM_CTAS, -1), (17, 0)):
+        with pytest.raises(_lib.TempestError) as e:
+            eng.set_tuning(knob, bad)
+        assert e.value.code == _lib.TEMPEST_EINVAL
+    for knob, val in ((_lib.TUNE_BKT_LOG, 4), (_lib.TUNE_COOP_W_WARP, 16), (_lib.TUNE_COOP_MEGA, 2048),
+                      (_lib.TUNE_STREAM_CTAS, 2)):
+        eng.set_tuning(knob, val)
+        assert eng.get_tuning(knob) == val
+
+
+@pytest.mark.parametrize("sched", [_lib.SCHED_STREAM, _lib.SCHED_COOP, _lib.SCHED_FULL_WALK, _lib.SCHED_GRAPH])
+def test_every_knob_setting_gives_the_same_walks(sched):
+    eng = _engine()
+    ref = {b: _walks(eng, b) for b in (0, 2)}
+    eng.set_scheduler(sched)
+    for knob, val in ((_lib.TUNE_BKT_LOG, 0), (_lib.TUNE_BKT_LOG, 5), (_lib.TUNE_COOP_W_WARP, 1),
+                      (_lib.TUNE_COOP_W_WARP, 64), (_lib.TUNE_COOP_MEGA, 256), (_lib.TUNE_STREAM_CTAS, 1)):
+        eng.set_tuning(knob, val)
+        for b in (0, 2):
+            got = eng.walks(20000, 30, bias=b, seed=9)
+            assert all(torch.equal(x, y) for x, y in zip(ref[b], got)), (sched, knob, val, b)
+
+
+def test_autotune_reports_and_keeps_its_choice():
+    eng = _engine()
+    ref = _walks(eng, 2)
+    rep = eng.autotune(50000, 30, bias=2, seed=1, forms=True)
+    assert len(rep["trials"]) >= 8
+    assert rep["best_ms"] <= rep["start_ms"] + 1e-9
+    assert rep["best_ms"] == min(t["ms"] for t in rep["trials"])
+    assert {t["sched"] for t in rep["trials"]} == {0, 1, 2, 3}
+    assert eng.get_tuning(_lib.TUNE_BKT_LOG) == rep["bkt_log"]
+    assert eng.get_tuning(_lib.TUNE_STREAM_CTAS) == rep["stream_ctas"]
+    got = eng.walks(20000, 30, bias=2, seed=9)
+    assert all(torch.equal(x, y) for x, y in zip(ref, got))
+    with pytest.raises(_lib.TempestError):
+        eng.autotune(0, 30)
