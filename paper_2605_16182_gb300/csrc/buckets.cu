@@ -10,8 +10,8 @@
 //
 // The tables depend only on the node view, so they are built once per index
 // state, at the first walk call after an ingest:
-//   1. a compaction over the node segments lists the big segments and
-//      places their tables back to back (prefix of K + 1);
+//   1. a compaction over the nodes that own index regions lists the big
+//      nodes and places their tables back to back (prefix of K + 1);
 //   2. a scan over that list numbers their fill chunks (BKT_CHUNK groups);
 //   3. one warp per chunk reads the chunk's group timestamps (coalesced);
 //      group g owns the table entries k in (bucket(g - 1), bucket(g)] (it is
@@ -29,48 +29,46 @@ namespace tw {
 
 namespace {
 
-struct BigSegOp {
-    const int32_t *seg_node, *seg_g;
-    int64_t S, Gn;
+struct BigNodeOp {
+    const int32_t *act;
+    const int2 *ngr;
     int log_b;
-    int32_t *big_seg, *big_t, *bkt_base;
+    int32_t *big_node, *big_t, *bkt_base;
     __device__ __forceinline__ uint64_t value(int64_t j) const
     {
-        const int64_t g1 = j + 1 < S ? seg_g[j + 1] : Gn;
-        const int64_t G = g1 - seg_g[j];
+        const int2 g = ngr[act[j]];
+        const int32_t G = g.y - g.x;
         if (G < BKT_MIN_G) return 0;
-        return (1ull << 32) | (uint64_t)(bkt_count((int32_t)G, log_b) + 1u);
+        return (1ull << 32) | (uint64_t)(bkt_count(G, log_b) + 1u);
     }
     __device__ __forceinline__ void emit(int64_t j, uint64_t v, uint64_t ex) const
     {
         if (!v) return;
         const uint32_t b = (uint32_t)(ex >> 32);
-        big_seg[b] = (int32_t)j;
+        const int32_t node = act[j];
+        big_node[b] = node;
         big_t[b] = (int32_t)(uint32_t)ex;
-        bkt_base[seg_node[j]] = (int32_t)(uint32_t)ex;
+        bkt_base[node] = (int32_t)(uint32_t)ex;
     }
 };
 
 struct ChunkOp {
-    const int32_t *big_seg, *seg_g;
-    int64_t S, Gn;
+    const int32_t *big_node;
+    const int2 *ngr;
     int32_t *big_c;
     __device__ __forceinline__ uint64_t value(int64_t b) const
     {
-        const int32_t j = big_seg[b];
-        const int64_t g1 = j + 1 < S ? seg_g[j + 1] : Gn;
-        return (uint64_t)((g1 - seg_g[j] + BKT_CHUNK - 1) / BKT_CHUNK);
+        const int2 g = ngr[big_node[b]];
+        return (uint64_t)((g.y - g.x + BKT_CHUNK - 1) / BKT_CHUNK);
     }
     __device__ __forceinline__ void emit(int64_t b, uint64_t, uint64_t ex) const { big_c[b] = (int32_t)ex; }
 };
 
 // One warp per chunk (grid-stride); totals of the compaction in tot.
-__global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ big_seg,
+__global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ big_node,
                                                   const int32_t *__restrict__ big_t,
                                                   const int32_t *__restrict__ big_c, int64_t nb,
-                                                  const uint64_t *__restrict__ tot,
-                                                  const int32_t *__restrict__ seg_node,
-                                                  const int32_t *__restrict__ seg_g, int64_t S, int64_t Gn,
+                                                  const uint64_t *__restrict__ tot, const int2 *__restrict__ ngr,
                                                   const int64_t *__restrict__ ngts, int log_b, int64_t cap,
                                                   int32_t *bkt, WalkCounters *chk)
 {
@@ -78,7 +76,7 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
     const int64_t nch = (int64_t)*tot;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += warps) {
-        // owning big segment: last b with big_c[b] <= c
+        // owning big node: last b with big_c[b] <= c
         int64_t lo = 0, hi = nb - 1;
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) >> 1;
@@ -86,9 +84,8 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
             else hi = mid - 1;
         }
         const int64_t b = lo;
-        const int32_t j = __ldg(big_seg + b);
-        const int32_t g0 = __ldg(seg_g + j);
-        const int32_t g1 = j + 1 < S ? __ldg(seg_g + j + 1) : (int32_t)Gn;
+        const int2 gr = __ldg(ngr + __ldg(big_node + b));
+        const int32_t g0 = gr.x, g1 = gr.y;
         const uint32_t K = bkt_count(g1 - g0, log_b);
         const int64_t tb = __ldg(big_t + b);
         if (tb + K >= cap || g1 - g0 < BKT_MIN_G) {  // inconsistent lists
@@ -142,20 +139,21 @@ int prepare_walk_index(tempest_t *h)
 {
     if (h->bkt_ver == h->state_ver) return TEMPEST_OK;
     cudaStream_t st = h->stream;
-    const int64_t S = h->S, Gn = h->Gn, N = h->N;
+    const int64_t S = h->n_act, Gn = h->Gn, N = h->N;
     int rc;
     h->n_big = 0;
     if (S > 0 && Gn >= BKT_MIN_G) {
         const size_t Sz = (size_t)S;
         if ((rc = ensure(h, h->bkt_base, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
-        if ((rc = ensure(h, h->big_seg, sizeof(int32_t) * Sz, true))) return rc;
+        if ((rc = ensure(h, h->big_node, sizeof(int32_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->big_t, sizeof(int32_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->big_c, sizeof(int32_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
         if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
         uint64_t *part = h->partials.as<uint64_t>();
-        BigSegOp op{h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>(), S, Gn, h->bkt_log,
-                    h->big_seg.as<int32_t>(), h->big_t.as<int32_t>(), h->bkt_base.as<int32_t>()};
+        const int2 *ngr = h->ngr.as<int2>();
+        BigNodeOp op{h->act.as<int32_t>(), ngr, h->bkt_log, h->big_node.as<int32_t>(), h->big_t.as<int32_t>(),
+                     h->bkt_base.as<int32_t>()};
         const int nblk = scan_launch(op, S, part, st);
         uint64_t *hp = static_cast<uint64_t *>(h->hstat);
         cudaMemcpyAsync(hp, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
@@ -167,7 +165,7 @@ int prepare_walk_index(tempest_t *h)
                         (long long)cap);
         if (nb > 0) {
             if ((rc = ensure(h, h->bkt, sizeof(int32_t) * (size_t)cap, true))) return rc;
-            ChunkOp cop{h->big_seg.as<int32_t>(), h->seg_g.as<int32_t>(), S, Gn, h->big_c.as<int32_t>()};
+            ChunkOp cop{h->big_node.as<int32_t>(), ngr, h->big_c.as<int32_t>()};
             const int nblk2 = scan_launch(cop, nb, part, st);
             // the fill's consistency flag goes to the walk counters, which
             // every walk call zeroes before its kernels: read it here
@@ -176,11 +174,10 @@ int prepare_walk_index(tempest_t *h)
             int64_t grid = (nch_max + 7) / 8;
             const int64_t gcap = (int64_t)h->num_sms * 16;
             if (grid > gcap) grid = gcap;
-            k_bkt_fill<<<(unsigned)grid, 256, 0, st>>>(h->big_seg.as<int32_t>(), h->big_t.as<int32_t>(),
-                                                       h->big_c.as<int32_t>(), nb, part + nblk2,
-                                                       h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>(), S, Gn,
-                                                       h->ngts.as<int64_t>(), h->bkt_log, cap,
-                                                       h->bkt.as<int32_t>(), h->wcnt.as<WalkCounters>());
+            k_bkt_fill<<<(unsigned)grid, 256, 0, st>>>(h->big_node.as<int32_t>(), h->big_t.as<int32_t>(),
+                                                       h->big_c.as<int32_t>(), nb, part + nblk2, ngr,
+                                                       h->ngts.as<int64_t>(), h->bkt_log, cap, h->bkt.as<int32_t>(),
+                                                       h->wcnt.as<WalkCounters>());
             WalkCounters *hc = static_cast<WalkCounters *>(h->hstat);
             cudaMemcpyAsync(hc, h->wcnt.p, sizeof(WalkCounters), cudaMemcpyDeviceToHost, st);
             if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket fill"))) return rc;

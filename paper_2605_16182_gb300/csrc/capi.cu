@@ -131,15 +131,15 @@ int ensure(tempest_t *h, DBuf &b, size_t bytes, bool headroom)
 static void free_all(tempest_t *h)
 {
     DBuf *bufs[] = {&h->st_src[0], &h->st_src[1], &h->st_dst[0], &h->st_dst[1], &h->st_ts[0], &h->st_ts[1],
-                    &h->ts_goff,   &h->ent[0],    &h->ent[1],    &h->enode[0],  &h->enode[1],
-                    &h->noff[0],   &h->noff[1],   &h->ev,        &h->bcnt,      &h->bstart,    &h->ngo,       &h->ngts,      &h->gidx,     &h->b_src,
-                    &h->b_dst,     &h->b_ts,      &h->sb_src,    &h->sb_dst,    &h->sb_ts,    &h->sk64[0],
-                    &h->sk64[1],   &h->sk32[0],   &h->sk32[1],   &h->sv[0],     &h->sv[1],    &h->hist,
-                    &h->partials,  &h->seg_node,  &h->seg_g,     &h->gcnt,      &h->dstat,    &h->wcnt,
-                    &h->out_stage, &h->in_stage,  &h->exp_stage,
-                    &h->co_node,   &h->co_t,      &h->co_len,    &h->co_act[0], &h->co_act[1], &h->co_runs,
-                    &h->co_tasks,  &h->co_ctr,    &h->bkt_base,  &h->bkt,       &h->big_seg,   &h->big_t,
-                    &h->big_c,     &h->tune_out};
+                    &h->tg,        &h->ent,       &h->ngo,       &h->ngts,      &h->ngr,       &h->nrec,
+                    &h->act,       &h->nvc,       &h->nv_tmp,    &h->run_node,  &h->run_pos,   &h->run_g,
+                    &h->run_of,    &h->fx,        &h->run_de,    &h->run_dg,    &h->ev_nodes,  &h->reloc,
+                    &h->ev,        &h->b_src,     &h->b_dst,     &h->b_ts,      &h->sb_src,    &h->sb_dst,
+                    &h->sb_ts,     &h->sk64[0],   &h->sk64[1],   &h->sk32[0],   &h->sk32[1],   &h->sv[0],
+                    &h->sv[1],     &h->hist,      &h->partials,  &h->dstat,     &h->wcnt,      &h->out_stage,
+                    &h->in_stage,  &h->exp_stage, &h->co_node,   &h->co_t,      &h->co_len,    &h->co_act[0],
+                    &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt_base,  &h->bkt,
+                    &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out};
     for (DBuf *b : bufs) release(h, *b);
 }
 
@@ -422,31 +422,29 @@ int tempest_export_state(tempest_t *h, int which, void *dst, int64_t cap, int64_
     const size_t bytes = esz * (size_t)cnt;
     const bool dev = is_device_ptr(dst);
     int rc;
-    if (!h->gidx.p) {
+    if (!h->nv_ready || !h->tg.p) {
         // nothing ingested yet: every remaining array is the single offset 0
         if (dev) return cuda_check(h, cudaMemsetAsync(dst, 0, bytes, st), "export");
         memset(dst, 0, bytes);
         return TEMPEST_OK;
     }
     const void *srcp = nullptr;
-    if (which == TEMPEST_STATE_NODE_OFF || which == TEMPEST_STATE_NODE_ORDER) {
-        void *target = dst;
-        if (!dev) {
-            if ((rc = ensure(h, h->exp_stage, bytes))) return rc;
-            target = h->exp_stage.p;
-        }
-        if (which == TEMPEST_STATE_NODE_OFF) launch_node_off(h, static_cast<int32_t *>(target));
-        else launch_node_order(h, static_cast<int32_t *>(target));
-        srcp = target;
-        if (dev) return cuda_check(h, cudaGetLastError(), "export");
-    } else {
-        switch (which) {
-            case TEMPEST_STATE_SRC: srcp = h->st_src[h->cur].p; break;
-            case TEMPEST_STATE_DST: srcp = h->st_dst[h->cur].p; break;
-            case TEMPEST_STATE_TS: srcp = h->st_ts[h->cur].p; break;
-            case TEMPEST_STATE_TS_GROUP_OFF: srcp = h->ts_goff.p; break;
-            case TEMPEST_STATE_NODE_GROUP_OFF: srcp = h->ngo.p; break;
-            case TEMPEST_STATE_NODE_GIDX: srcp = h->gidx.p; break;
+    switch (which) {
+        case TEMPEST_STATE_SRC: srcp = h->st_src[h->cur].as<int32_t>() + h->s_lo; break;
+        case TEMPEST_STATE_DST: srcp = h->st_dst[h->cur].as<int32_t>() + h->s_lo; break;
+        case TEMPEST_STATE_TS: srcp = h->st_ts[h->cur].as<int64_t>() + h->s_lo; break;
+        default: {
+            // derived arrays are written to device memory first
+            void *target = dst;
+            if (!dev) {
+                if ((rc = ensure(h, h->exp_stage, bytes))) return rc;
+                target = h->exp_stage.p;
+            }
+            rc = which == TEMPEST_STATE_TS_GROUP_OFF ? ts_export(h, static_cast<int32_t *>(target))
+                                                     : nv_export(h, which, static_cast<int32_t *>(target));
+            if (rc) return rc;
+            if (dev) return cuda_check(h, cudaStreamSynchronize(st), "export");
+            srcp = target;
         }
     }
     cudaMemcpyAsync(dst, srcp, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);

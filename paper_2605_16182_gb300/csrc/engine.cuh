@@ -38,7 +38,25 @@ struct IngestScratch {
     long long i0, j0;       // first kept store / batch element
     long long kept_batch_min_ts;
     long long store_last_ts;
+    long long tg_lo, tg_added;  // timestamp view: first live group, groups appended
     unsigned long long status;  // nonzero: an index check failed (bit per site)
+};
+
+// Device counters of the node-view update (one batch).
+struct NvCounters {
+    unsigned long long e_top, g_top;  // pool bump pointers
+    long long gn_delta;               // groups added - groups removed
+    unsigned long long n_ev_nodes;    // nodes that lost entries
+    unsigned long long n_reloc;       // regions to move
+    unsigned long long n_act;         // nodes owning regions
+    unsigned long long overflow;      // a pool could not serve a region
+    unsigned long long status;        // nonzero: a consistency check failed
+};
+
+// A region move: live entries and groups of one node to fresh regions.
+struct Reloc {
+    int32_t old_e, n_e, new_e;
+    int32_t old_g, n_g, new_g;
 };
 
 // Device-side walk counters.
@@ -77,18 +95,38 @@ struct tempest {
     int has_cutoff = 0;
     int64_t cutoff = 0;
 
-    // device state: the store (double buffered for merges) and both views
+    // edge store: SoA buffers (two, for compaction and general merges).  The
+    // live edges are buffer indices [s_lo, s_hi) of buffer cur, in (ts,
+    // arrival) order; eviction advances s_lo, an append writes at s_hi.  The
+    // absolute position of index i is s_base + i (node view slots hold it
+    // modulo 2^32, so a compaction that moves the live range to index 0 only
+    // changes s_base).
     tw::DBuf st_src[2], st_dst[2], st_ts[2];
     int cur = 0;
-    tw::DBuf ts_goff;  // int32 [G+1]
-    tw::DBuf ent[2];   // Entry [M]  node view entries (double buffered)
-    tw::DBuf enode[2]; // int32 [M]  node of each entry
-    tw::DBuf noff[2];  // int32 [N+1] start of each node's segment
-    int vcur = 0;      // which ent / enode / noff buffer is live
-    tw::DBuf ngo;      // int32 [Gn+1] node group start offsets
-    tw::DBuf ngts;     // int64 [Gn]   node group timestamps
-    tw::DBuf gidx;     // int32 [N+1]  first group of each node
-    int64_t S = 0;     // node segments (nodes with at least one entry)
+    int64_t s_lo = 0, s_hi = 0, s_cap = 0, s_base = 0;
+    // timestamp-grouped view: start index of every group, live groups
+    // [tg_lo, tg_hi) with tg[tg_hi] = s_hi; the first live group may start
+    // before s_lo (its evicted part is skipped on read)
+    tw::DBuf tg;  // int32, capacity s_cap + 1
+    int64_t tg_lo = 0, tg_hi = 0;
+    // node view in a slack layout: every node with entries owns a region of
+    // the entry pool and one of the group pools, with room to grow; the
+    // groups of node v are [ngr[v].x, ngr[v].y), group g's entries start at
+    // ngo[g] and the slot after the node's last group holds its entry end
+    tw::DBuf ent;   // Entry pool
+    tw::DBuf ngo;   // int32 group start (entry pool index)
+    tw::DBuf ngts;  // int64 group timestamp
+    tw::DBuf ngr;   // int2 [N+1]: live groups of each node
+    tw::DBuf nrec;  // int4 [N+1]: entries [x, y), entry region end z, group region end w
+    tw::DBuf act;   // int32: nodes that own regions
+    tw::DBuf nvc;   // device counters of the node view (NvCounters)
+    int64_t n_act = 0;
+    int64_t nrec_n = 0;     // node slots the per-node arrays cover
+    int64_t e_cap = 0, g_cap = 0;
+    int nv_shift = 0;       // region capacity = x + (x >> nv_shift) + 16
+    bool nv_ready = false;
+    tw::DBuf nv_tmp, run_node, run_pos, run_g, run_of, fx, run_de, run_dg, ev_nodes, reloc;
+    int64_t S = 0;     // nodes that own regions (for the bucket index)
     int64_t state_ver = 0;  // bumped by every ingest
 
     // time buckets of high-degree nodes (built lazily for the walks of a
@@ -96,7 +134,7 @@ struct tempest {
     // list and its chunk prefix
     tw::DBuf bkt_base;   // int32 [N+1]
     tw::DBuf bkt;        // int32 tables
-    tw::DBuf big_seg, big_t, big_c;
+    tw::DBuf big_node, big_t, big_c;
     int64_t bkt_ver = -1;
     int64_t n_big = 0;
     int bkt_log = 2;     // log2 of the mean groups per bucket
@@ -106,8 +144,7 @@ struct tempest {
     tw::DBuf sb_src, sb_dst, sb_ts;  // batch sorted by timestamp
     tw::DBuf sk64[2], sk32[2], sv[2];
     tw::DBuf hist, partials;
-    tw::DBuf seg_node, seg_g, gcnt;
-    tw::DBuf ev, bcnt, bstart;   // per-node evicted / new entry counts, batch run starts
+    tw::DBuf ev;                 // int32 [N+1] per-node evicted entries (zero between batches)
     // cooperative scheduler: walk state, active lists, runs, tier tasks, counters
     tw::DBuf co_node, co_t, co_len, co_act[2], co_runs, co_tasks, co_ctr;
     int coop_w_warp = 4;         // solo / warp boundary W_warp (Sec. 3.5)
@@ -144,10 +181,16 @@ bool is_device_ptr(const void *p);
 // ingest.cu
 int ingest_batch(tempest_t *h, const int32_t *src, const int32_t *dst, const int64_t *ts, int64_t n,
                  tempest_ingest_stats *stats);
-// fills node_off (int32 [N+1]) from the group arrays
-void launch_node_off(tempest_t *h, int32_t *node_off);
-// fills node_order (int32 [M]) from the entries
-void launch_node_order(tempest_t *h, int32_t *node_order);
+
+// nodeview.cu
+int nv_ensure_nodes(tempest_t *h, int64_t N);
+int nv_build(tempest_t *h);
+int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_t n_ev, int64_t new_lo, int64_t nbk,
+              int64_t N_old, bool *rebuild);
+// canonical NODE_OFF / NODE_ORDER / NODE_GROUP_OFF / NODE_GIDX into device memory
+int nv_export(tempest_t *h, int which, int32_t *out);
+// timestamp-group starts relative to the live head, plus m (G + 1 values)
+int ts_export(tempest_t *h, int32_t *out);
 
 // walks.cu
 struct WalkRequest {

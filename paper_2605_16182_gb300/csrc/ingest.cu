@@ -9,15 +9,20 @@
 //   3. the new cut-off is found without materialising the merge (a merge-path
 //      search gives the timestamp at any rank of the merged order), and the
 //      first kept element of the store and of the batch by binary search;
-//   4. the kept store suffix and the kept batch are merged into the other
-//      store buffer (two copies when the batch starts no earlier than the
-//      store ends, a merge-path merge otherwise);
-//   5. timestamp-grouped view: compaction of the run starts of equal ts;
-//   6. node view: stable radix sort of the store's (node, slot) pairs by
-//      node, one 16-byte entry per slot, then one compaction that emits the
-//      (node, ts) group starts and the node segment starts, and an exclusive
-//      scan of per-node group counts that gives each node's first group.
+//   4. when the kept batch starts no earlier than the store ends (a stream in
+//      time order), eviction only advances the store's head and the batch is
+//      appended at its tail; the live range moves to the front of the other
+//      buffer only when the tail reaches the end (amortised: the buffer holds
+//      twice the live edges).  Otherwise the kept store and batch are merged
+//      into the other buffer (merge-path merge);
+//   5. timestamp-grouped view: eviction advances its first live group (a
+//      binary search), the batch's group starts are appended (a compaction
+//      over the batch only); after a merge or a move it is rebuilt;
+//   6. node view (nodeview.cu): per-node regions updated by the batch and the
+//      evicted edges only, or rebuilt from the store after a merge.
 #include <stdio.h>
+
+#include <algorithm>
 
 #include "engine.cuh"
 #include "prims.cuh"
@@ -78,6 +83,8 @@ __global__ void k_init_scratch(IngestScratch *o)
     o->j0 = 0;
     o->kept_batch_min_ts = 0;
     o->store_last_ts = 0;
+    o->tg_lo = 0;
+    o->tg_added = 0;
     o->status = 0;
 }
 
@@ -203,244 +210,45 @@ __global__ void k_merge(const int32_t *__restrict__ as, const int32_t *__restric
 }
 
 // ---------------------------------------------------------------------------
-// views
+// timestamp-grouped view
 // ---------------------------------------------------------------------------
+// Group starts among the store indices [lo, lo + n) of ts: a group opens
+// where the timestamp differs from the previous edge's, and at index first
+// (the live head).  Starts are written densely from tg.
 struct TsGroupOp {
     const int64_t *ts;
-    int32_t *goff;
+    int64_t lo, first;
+    int32_t *tg;
     __device__ __forceinline__ uint64_t value(int64_t i) const
     {
-        return (i == 0 || ts[i] != ts[i - 1]) ? 1u : 0u;
+        const int64_t p = lo + i;
+        return (p == first || ts[p] != ts[p - 1]) ? 1u : 0u;
     }
     __device__ __forceinline__ void emit(int64_t i, uint64_t v, uint64_t ex) const
     {
-        if (v) goff[ex] = (int32_t)i;
+        if (v) tg[ex] = (int32_t)(lo + i);
     }
 };
 
-struct StoreKeyLoader {
-    const int32_t *src, *dst;
-    int directed;
-    __device__ __forceinline__ uint32_t key(int64_t i) const
-    {
-        if (directed) return (uint32_t)src[i];
-        return (uint32_t)((i & 1) ? dst[i >> 1] : src[i >> 1]);
-    }
-    __device__ __forceinline__ uint32_t val(int64_t i) const { return (uint32_t)i; }
-};
-
-__global__ void k_node_entries(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ slots,
-                               const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                               const int64_t *__restrict__ ts, int directed, int64_t M, Entry *E, int32_t *enode)
+// First live group after the head moved to s_lo: the first g in [lo, hi)
+// whose successor starts after s_lo (tg[hi] is the old tail), else hi.
+__global__ void k_ts_evict(const int32_t *__restrict__ tg, int64_t lo, int64_t hi, int64_t s_lo, IngestScratch *o)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t slot = slots[i];
-        const int64_t pos = directed ? (int64_t)slot : (int64_t)(slot >> 1);
-        const bool side = !directed && (slot & 1u);
-        Entry e;
-        e.ts = ts[pos];
-        e.other = side ? src[pos] : dst[pos];
-        e.slot = (int32_t)slot;
-        E[i] = e;
-        enode[i] = (int32_t)keys[i];
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (tg[mid + 1] > s_lo) hi = mid;
+        else lo = mid + 1;
     }
+    o->tg_lo = lo;
 }
 
-// Packed counter: high 32 bits count node segments, low 32 bits count
-// (node, ts) groups.
-struct NodeGroupOp {
-    const int32_t *enode;  // node of each entry (entries grouped by node)
-    const Entry *E;
-    int32_t *ngo;
-    int64_t *ngts;
-    int32_t *seg_node;
-    int32_t *seg_g;
-    __device__ __forceinline__ uint64_t value(int64_t i) const
-    {
-        if (i == 0) return (1ull << 32) | 1ull;
-        const bool seg = enode[i] != enode[i - 1];
-        const bool grp = seg || E[i].ts != E[i - 1].ts;
-        return ((uint64_t)seg << 32) | (uint64_t)grp;
-    }
-    __device__ __forceinline__ void emit(int64_t i, uint64_t v, uint64_t ex) const
-    {
-        if (v & 1ull) {
-            const uint32_t g = (uint32_t)ex;
-            ngo[g] = (int32_t)i;
-            ngts[g] = E[i].ts;
-            if (v >> 32) {
-                const uint32_t j = (uint32_t)(ex >> 32);
-                seg_node[j] = enode[i];
-                seg_g[j] = (int32_t)g;
-            }
-        }
-    }
-};
-
-__global__ void k_seg_counts(const int32_t *__restrict__ seg_node, const int32_t *__restrict__ seg_g,
-                             int64_t S, int64_t Gn, int32_t *gcnt)
+// After a compaction of n appended starts written from tg + base: the tail
+// entry and the count.
+__global__ void k_ts_tail(int32_t *tg, int64_t base, const uint64_t *tot, int64_t s_hi, IngestScratch *o)
 {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < S;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t next = (j + 1 < S) ? seg_g[j + 1] : Gn;
-        gcnt[seg_node[j]] = (int32_t)(next - seg_g[j]);
-    }
-}
-
-struct GidxOp {
-    const int32_t *gcnt;
-    int64_t N;
-    int32_t *gidx;
-    __device__ __forceinline__ uint64_t value(int64_t v) const { return v < N ? (uint64_t)gcnt[v] : 0ull; }
-    __device__ __forceinline__ void emit(int64_t v, uint64_t, uint64_t ex) const { gidx[v] = (int32_t)ex; }
-};
-
-__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
-
-__global__ void k_node_off(const int32_t *__restrict__ gidx, const int32_t *__restrict__ ngo, int64_t N,
-                           int32_t *node_off)
-{
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= N;
-         v += (int64_t)gridDim.x * blockDim.x)
-        node_off[v] = ngo[gidx[v]];
-}
-
-__global__ void k_node_order(const Entry *__restrict__ E, int64_t M, int32_t *out)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = E[i].slot;
-}
-
-// ---- incremental node view (the batch starts no earlier than the store ends)
-
-// Entries of the evicted store prefix [0, i0), counted per node.  Every
-// node loses a prefix of its segment: eviction removes the oldest edges.
-__global__ void k_evict_counts(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t items,
-                               int directed, int64_t N, int32_t *ev, IngestScratch *chk)
-{
-    const int lane = threadIdx.x & 31;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t v = directed ? src[i] : ((i & 1) ? dst[i >> 1] : src[i >> 1]);
-        if (v < 0 || v >= N) {
-            atomicOr(&chk->status, 1ull << 0);
-            v = -1;
-        }
-        const unsigned am = __activemask();
-        const unsigned peers = __match_any_sync(am, v);
-        if (v >= 0 && lane == __ffs(peers) - 1) atomicAdd(&ev[v], __popc(peers));
-    }
-}
-
-// (node, slot) pairs of the batch's entries, slots numbered in the new store
-// where the batch occupies positions [base, base + nb).
-struct BatchKeyLoader {
-    const int32_t *src, *dst;
-    int directed;
-    int64_t base;
-    __device__ __forceinline__ uint32_t key(int64_t i) const
-    {
-        if (directed) return (uint32_t)src[base + i];
-        return (uint32_t)((i & 1) ? dst[base + (i >> 1)] : src[base + (i >> 1)]);
-    }
-    __device__ __forceinline__ uint32_t val(int64_t i) const
-    {
-        return (uint32_t)(directed ? base + i : 2 * base + i);
-    }
-};
-
-// Runs of equal nodes in the sorted batch keys: bstart[v] = first index,
-// bcnt[v] = run length (bcnt starts at 0; pass 0 stores the run end, pass 1
-// subtracts the start).
-__global__ void k_batch_runs(const uint32_t *__restrict__ K, int64_t n, int pass, int32_t *bstart, int32_t *bcnt)
-{
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = K[j];
-        if (pass == 0) {
-            if (j == 0 || K[j - 1] != v) bstart[v] = (int32_t)j;
-            if (j == n - 1 || K[j + 1] != v) bcnt[v] = (int32_t)(j + 1);
-        } else if (j == 0 || K[j - 1] != v) {
-            bcnt[v] -= (int32_t)j;
-        }
-    }
-}
-
-// New segment starts: kept old entries plus new entries, per node.
-struct NoffOp {
-    const int32_t *noff_old;
-    int64_t N_old;
-    const int32_t *ev;
-    const int32_t *bcnt;
-    int64_t N;
-    int32_t *noff_new;
-    __device__ __forceinline__ uint64_t value(int64_t v) const
-    {
-        if (v >= N) return 0;
-        const int32_t old = v < N_old ? noff_old[v + 1] - noff_old[v] : 0;
-        return (uint64_t)(old - ev[v] + bcnt[v]);
-    }
-    __device__ __forceinline__ void emit(int64_t v, uint64_t, uint64_t ex) const { noff_new[v] = (int32_t)ex; }
-};
-
-// Kept old entries move by a per-node shift; their slots shift by E0 (the
-// evicted store prefix, in slots).
-__global__ void k_copy_kept(const Entry *__restrict__ E_old, const int32_t *__restrict__ enode_old, int64_t M_old,
-                            const int32_t *__restrict__ noff_old, const int32_t *__restrict__ ev,
-                            const int32_t *__restrict__ noff_new, int32_t E0, int64_t N_old, int64_t M_new,
-                            Entry *E_new, int32_t *enode_new, IngestScratch *chk)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M_old;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        Entry e = E_old[i];
-        if (e.slot < E0) continue;  // evicted
-        const int32_t v = enode_old[i];
-        if (v < 0 || v >= N_old) {
-            atomicOr(&chk->status, 1ull << 1);
-            continue;
-        }
-        const int64_t p = (int64_t)noff_new[v] + (i - noff_old[v] - ev[v]);
-        if (p < 0 || p >= M_new) {
-            atomicOr(&chk->status, 1ull << 2);
-            continue;
-        }
-        e.slot -= E0;
-        E_new[p] = e;
-        enode_new[p] = v;
-    }
-}
-
-// New entries go after the kept ones of their node, in slot order.
-__global__ void k_scatter_batch(const uint32_t *__restrict__ K, const uint32_t *__restrict__ V, int64_t n,
-                                const int32_t *__restrict__ bstart, const int32_t *__restrict__ bcnt,
-                                const int32_t *__restrict__ noff_new, const int32_t *__restrict__ src,
-                                const int32_t *__restrict__ dst, const int64_t *__restrict__ ts, int directed,
-                                int64_t N, int64_t M_new, Entry *E_new, int32_t *enode_new, IngestScratch *chk)
-{
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = K[j];
-        const uint32_t slot = V[j];
-        if ((int64_t)v >= N) {
-            atomicOr(&chk->status, 1ull << 3);
-            continue;
-        }
-        const int64_t p = (int64_t)noff_new[v + 1] - bcnt[v] + (j - bstart[v]);
-        if (p < 0 || p >= M_new) {
-            atomicOr(&chk->status, 1ull << 4);
-            continue;
-        }
-        const int64_t pos = directed ? (int64_t)slot : (int64_t)(slot >> 1);
-        const bool side = !directed && (slot & 1u);
-        Entry e;
-        e.ts = ts[pos];
-        e.other = side ? src[pos] : dst[pos];
-        e.slot = (int32_t)slot;
-        E_new[p] = e;
-        enode_new[p] = (int32_t)v;
-    }
+    const uint64_t n = *tot;
+    tg[base + (int64_t)n] = (int32_t)s_hi;
+    o->tg_added = (long long)n;
 }
 
 static unsigned grid_for(tempest_t *h, int64_t n, int threads = 256)
@@ -452,18 +260,6 @@ static unsigned grid_for(tempest_t *h, int64_t n, int threads = 256)
     return (unsigned)g;
 }
 
-void launch_node_off(tempest_t *h, int32_t *node_off)
-{
-    cudaMemcpyAsync(node_off, h->noff[h->vcur].p, sizeof(int32_t) * (size_t)(h->N + 1), cudaMemcpyDeviceToDevice,
-                    h->stream);
-}
-
-void launch_node_order(tempest_t *h, int32_t *node_order)
-{
-    if (h->M > 0)
-        k_node_order<<<grid_for(h, h->M), 256, 0, h->stream>>>(h->ent[h->vcur].as<Entry>(), h->M, node_order);
-}
-
 static int bits_for(uint64_t maxval)
 {
     int b = 0;
@@ -471,198 +267,34 @@ static int bits_for(uint64_t maxval)
     return b;
 }
 
-// timestamp-grouped view over the store in buffer h->cur
-static int rebuild_ts_view(tempest_t *h)
+// Timestamp view over the whole live range of buffer cur.
+static int ts_view_build(tempest_t *h)
 {
     cudaStream_t st = h->stream;
-    const int64_t m = h->m;
-    const int64_t *ts = h->st_ts[h->cur].as<int64_t>();
-    uint64_t *hpart = static_cast<uint64_t *>(h->hstat);
+    const int64_t m = h->s_hi - h->s_lo;
     int rc;
-    if ((rc = ensure(h, h->ts_goff, sizeof(int32_t) * (size_t)(m + 1), true))) return rc;
-    TsGroupOp op{ts, h->ts_goff.as<int32_t>()};
+    if ((rc = ensure(h, h->tg, sizeof(int32_t) * (size_t)(h->s_cap + 2)))) return rc;
+    IngestScratch *ds = h->dstat.as<IngestScratch>();
+    TsGroupOp op{h->st_ts[h->cur].as<int64_t>(), h->s_lo, h->s_lo, h->tg.as<int32_t>()};
     const int nb = scan_launch(op, m, h->partials.as<uint64_t>(), st);
-    cudaMemcpyAsync(hpart, h->partials.as<uint64_t>() + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-    h->pending_launches += 3;
-    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ts view"))) return rc;
-    h->G = (int64_t)hpart[0];
-    k_set_i32<<<1, 1, 0, st>>>(h->ts_goff.as<int32_t>() + h->G, (int32_t)m);
-    h->pending_launches++;
-    return TEMPEST_OK;
+    k_ts_tail<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), 0, h->partials.as<uint64_t>() + nb, h->s_hi, ds);
+    h->pending_launches += 4;
+    h->tg_lo = 0;
+    h->tg_hi = -1;  // known after the batch's final read-back (tg_added)
+    return cuda_check(h, cudaGetLastError(), "ts view");
 }
 
-static int ensure_view_buffers(tempest_t *h, int nxt, int64_t M, int64_t N)
+__global__ void k_ts_export(const int32_t *__restrict__ tg, int64_t G, int64_t s_lo, int64_t m, int32_t *out)
 {
-    int rc;
-    const size_t Mz = (size_t)(M > 0 ? M : 1);
-    if ((rc = ensure(h, h->ent[nxt], sizeof(Entry) * Mz, true))) return rc;
-    if ((rc = ensure(h, h->enode[nxt], sizeof(int32_t) * Mz, true))) return rc;
-    if ((rc = ensure(h, h->noff[nxt], sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
-    if ((rc = ensure(h, h->ngo, sizeof(int32_t) * (size_t)(M + 1), true))) return rc;
-    if ((rc = ensure(h, h->ngts, sizeof(int64_t) * Mz, true))) return rc;
-    if ((rc = ensure(h, h->gidx, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
-    if ((rc = ensure(h, h->gcnt, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
-    if ((rc = ensure(h, h->seg_node, sizeof(int32_t) * Mz, true))) return rc;
-    if ((rc = ensure(h, h->seg_g, sizeof(int32_t) * Mz, true))) return rc;
-    return TEMPEST_OK;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += (int64_t)gridDim.x * blockDim.x)
+        out[g] = g < G ? (int32_t)(max((int64_t)tg[g], s_lo) - s_lo) : (int32_t)m;
 }
 
-static int ensure_sort_buffers(tempest_t *h, int64_t n)
+int ts_export(tempest_t *h, int32_t *out)
 {
-    int rc;
-    const size_t z = (size_t)(n > 0 ? n : 1);
-    for (int b = 0; b < 2; b++) {
-        if ((rc = ensure(h, h->sk32[b], sizeof(uint32_t) * z, true))) return rc;
-        if ((rc = ensure(h, h->sv[b], sizeof(uint32_t) * z, true))) return rc;
-    }
-    return TEMPEST_OK;
-}
-
-// Groups and per-node first groups over the entries in buffer nxt (common to
-// both paths); the full path also derives the segment starts from them.
-static int node_view_groups(tempest_t *h, int nxt, int64_t M, int64_t N, bool need_noff)
-{
-    cudaStream_t st = h->stream;
-    uint64_t *hpart = static_cast<uint64_t *>(h->hstat);
-    int rc;
-    {
-        NodeGroupOp op{h->enode[nxt].as<int32_t>(), h->ent[nxt].as<Entry>(), h->ngo.as<int32_t>(),
-                       h->ngts.as<int64_t>(), h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>()};
-        const int nb = scan_launch(op, M, h->partials.as<uint64_t>(), st);
-        cudaMemcpyAsync(hpart, h->partials.as<uint64_t>() + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-        h->pending_launches += 3;
-    }
-    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view"))) return rc;
-    const uint64_t tot = hpart[0];
-    const int64_t Gn = M > 0 ? (int64_t)(uint32_t)tot : 0;
-    const int64_t S = M > 0 ? (int64_t)(tot >> 32) : 0;
-    h->Gn = Gn;
-    h->S = S;
-    k_set_i32<<<1, 1, 0, st>>>(h->ngo.as<int32_t>() + Gn, (int32_t)M);
-    cudaMemsetAsync(h->gcnt.as<int32_t>(), 0, sizeof(int32_t) * (size_t)(N + 1), st);
-    if (S > 0)
-        k_seg_counts<<<grid_for(h, S), 256, 0, st>>>(h->seg_node.as<int32_t>(), h->seg_g.as<int32_t>(), S, Gn,
-                                                     h->gcnt.as<int32_t>());
-    {
-        GidxOp op{h->gcnt.as<int32_t>(), N, h->gidx.as<int32_t>()};
-        scan_launch(op, N + 1, h->partials.as<uint64_t>(), st);
-    }
-    h->pending_launches += 5;
-    if (need_noff) {
-        k_node_off<<<grid_for(h, N + 1), 256, 0, st>>>(h->gidx.as<int32_t>(), h->ngo.as<int32_t>(), N,
-                                                      h->noff[nxt].as<int32_t>());
-        h->pending_launches++;
-    }
-    return cuda_check(h, cudaGetLastError(), "node view groups");
-}
-
-// Full rebuild: stable radix sort of every (node, slot) pair by node.
-static int node_view_full(tempest_t *h)
-{
-    cudaStream_t st = h->stream;
-    const int64_t m = h->m;
-    const int32_t *src = h->st_src[h->cur].as<int32_t>();
-    const int32_t *dst = h->st_dst[h->cur].as<int32_t>();
-    const int64_t *ts = h->st_ts[h->cur].as<int64_t>();
-    const int64_t M = h->directed ? m : 2 * m;
-    const int64_t N = h->N;
-    const int nxt = h->vcur ^ 1;
-    int rc;
-    if ((rc = ensure_view_buffers(h, nxt, M, N))) return rc;
-    if ((rc = ensure_sort_buffers(h, M))) return rc;
-    if (M > 0) {
-        StoreKeyLoader ld{src, dst, h->directed};
-        uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
-        uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
-        int launches = 0;
-        int bits = bits_for((uint64_t)(N > 0 ? N - 1 : 0));
-        if (bits < 1) bits = 1;  // one pass keeps the order and materialises the pairs
-        const int r = radix_sort_launch<uint32_t>(ld, M, bits, kb, vb, h->hist.as<uint32_t>(), st, &launches);
-        h->pending_launches += launches + 1;
-        k_node_entries<<<grid_for(h, M), 256, 0, st>>>(kb[r], vb[r], src, dst, ts, h->directed, M,
-                                                       h->ent[nxt].as<Entry>(), h->enode[nxt].as<int32_t>());
-    }
-    if ((rc = node_view_groups(h, nxt, M, N, true))) return rc;
-    h->M = M;
-    h->vcur = nxt;
-    return TEMPEST_OK;
-}
-
-// Incremental update after an append: every node keeps a suffix of its old
-// segment (the evicted edges are the oldest) and gains the batch's entries
-// at the end.  Gives exactly the order of the full rebuild.
-//   i0:   evicted prefix of the old store (in the buffer before h->cur)
-//   na:   kept old edges (they are positions [0, na) of the new store)
-//   nbk:  batch edges appended at positions [na, na + nbk)
-static int node_view_append(tempest_t *h, int64_t i0, int64_t na, int64_t nbk, int64_t N_old, int64_t M_old)
-{
-    cudaStream_t st = h->stream;
-    const int old_store = h->cur ^ 1;
-    const int32_t *src = h->st_src[h->cur].as<int32_t>();
-    const int32_t *dst = h->st_dst[h->cur].as<int32_t>();
-    const int64_t *ts = h->st_ts[h->cur].as<int64_t>();
-    const int directed = h->directed;
-    const int64_t M = directed ? h->m : 2 * h->m;
-    const int64_t N = h->N;
-    const int vold = h->vcur, nxt = h->vcur ^ 1;
-    const int64_t nbe = directed ? nbk : 2 * nbk;   // new entries
-    const int64_t evi = directed ? i0 : 2 * i0;     // evicted entries
-    int rc;
-    if ((rc = ensure_view_buffers(h, nxt, M, N))) return rc;
-    if ((rc = ensure_sort_buffers(h, nbe))) return rc;
-    if ((rc = ensure(h, h->ev, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
-    if ((rc = ensure(h, h->bcnt, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
-    if ((rc = ensure(h, h->bstart, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
-    int32_t *ev = h->ev.as<int32_t>();
-    int32_t *bcnt = h->bcnt.as<int32_t>();
-    int32_t *bstart = h->bstart.as<int32_t>();
-
-    cudaMemsetAsync(ev, 0, sizeof(int32_t) * (size_t)N, st);
-    cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * (size_t)N, st);
-    if (evi > 0)
-        k_evict_counts<<<grid_for(h, evi), 256, 0, st>>>(h->st_src[old_store].as<int32_t>(),
-                                                        h->st_dst[old_store].as<int32_t>(), evi, directed, N, ev,
-                                                        h->dstat.as<IngestScratch>());
-    const uint32_t *Kb = nullptr, *Vb = nullptr;
-    if (nbe > 0) {
-        BatchKeyLoader ld{src, dst, directed, na};
-        uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
-        uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
-        int launches = 0;
-        int bits = bits_for((uint64_t)(N > 0 ? N - 1 : 0));
-        if (bits < 1) bits = 1;
-        const int r = radix_sort_launch<uint32_t>(ld, nbe, bits, kb, vb, h->hist.as<uint32_t>(), st, &launches);
-        h->pending_launches += launches;
-        Kb = kb[r];
-        Vb = vb[r];
-        k_batch_runs<<<grid_for(h, nbe), 256, 0, st>>>(Kb, nbe, 0, bstart, bcnt);
-        k_batch_runs<<<grid_for(h, nbe), 256, 0, st>>>(Kb, nbe, 1, bstart, bcnt);
-        h->pending_launches += 2;
-    }
-    {
-        NoffOp op{h->noff[vold].as<int32_t>(), N_old, ev, bcnt, N, h->noff[nxt].as<int32_t>()};
-        scan_launch(op, N + 1, h->partials.as<uint64_t>(), st);
-        h->pending_launches += 3;
-    }
-    if (M_old > 0) {
-        k_copy_kept<<<grid_for(h, M_old), 256, 0, st>>>(h->ent[vold].as<Entry>(), h->enode[vold].as<int32_t>(),
-                                                       M_old, h->noff[vold].as<int32_t>(), ev,
-                                                       h->noff[nxt].as<int32_t>(), (int32_t)evi, N_old, M,
-                                                       h->ent[nxt].as<Entry>(), h->enode[nxt].as<int32_t>(),
-                                                       h->dstat.as<IngestScratch>());
-        h->pending_launches++;
-    }
-    if (nbe > 0) {
-        k_scatter_batch<<<grid_for(h, nbe), 256, 0, st>>>(Kb, Vb, nbe, bstart, bcnt, h->noff[nxt].as<int32_t>(), src,
-                                                         dst, ts, directed, N, M, h->ent[nxt].as<Entry>(),
-                                                         h->enode[nxt].as<int32_t>(), h->dstat.as<IngestScratch>());
-        h->pending_launches++;
-    }
-    h->pending_launches += (evi > 0) ? 1 : 0;
-    if ((rc = node_view_groups(h, nxt, M, N, false))) return rc;
-    h->M = M;
-    h->vcur = nxt;
-    return TEMPEST_OK;
+    k_ts_export<<<grid_for(h, h->G + 1), 256, 0, h->stream>>>(h->tg.as<int32_t>() + h->tg_lo, h->G, h->s_lo, h->m,
+                                                              out);
+    return cuda_check(h, cudaGetLastError(), "export");
 }
 
 int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in, int64_t n,
@@ -721,7 +353,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     // capacity of the next state (checked before anything changes)
     const int64_t m_max = h->m + (n - late);
     const int64_t M_max = h->directed ? m_max : 2 * m_max;
-    if (M_max >= (int64_t)INT32_MAX - 1)
+    if (M_max >= (int64_t)INT32_MAX / 2)
         return fail(h, TEMPEST_ENOMEM, "tempest_ingest: %lld index entries exceed the int32 index range",
                     (long long)M_max);
 
@@ -760,7 +392,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     // 3. window cut-off
     const int mode = h->window > 0 ? 1 : (h->window < 0 ? 2 : 0);
     const long long param = h->window > 0 ? h->window : -h->window;
-    const int64_t *old_ts = h->st_ts[h->cur].as<int64_t>();
+    const int64_t *old_ts = h->m > 0 ? h->st_ts[h->cur].as<int64_t>() + h->s_lo : nullptr;
     k_window<<<1, 32, 0, st>>>(mode, param, old_ts, h->m, bt, nb, h->has_cutoff, h->cutoff, ds);
     cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
     h->pending_launches++;
@@ -768,43 +400,75 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     const int64_t i0 = hs->i0, j0 = hs->j0;
     const int64_t na = h->m - i0, nbk = nb - j0;
     const int64_t m_new = na + nbk;
-
-    // 4. merge into the other store buffer
-    const int nxt = h->cur ^ 1;
     const bool append = na == 0 || nbk == 0 || hs->store_last_ts <= hs->kept_batch_min_ts;
-    if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
-    if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
-    if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)(m_new > 0 ? m_new : 1), true))) return rc;
-    {
-        const int32_t *as = h->st_src[h->cur].as<int32_t>() + i0;
-        const int32_t *ad = h->st_dst[h->cur].as<int32_t>() + i0;
-        const int64_t *at = h->st_ts[h->cur].as<int64_t>() + i0;
-        int32_t *os = h->st_src[nxt].as<int32_t>();
-        int32_t *od = h->st_dst[nxt].as<int32_t>();
-        int64_t *ot = h->st_ts[nxt].as<int64_t>();
-        if (append) {
-            if (na > 0) {
-                cudaMemcpyAsync(os, as, sizeof(int32_t) * (size_t)na, cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(od, ad, sizeof(int32_t) * (size_t)na, cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(ot, at, sizeof(int64_t) * (size_t)na, cudaMemcpyDeviceToDevice, st);
-            }
-            if (nbk > 0) {
-                cudaMemcpyAsync(os + na, bs + j0, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(od + na, bd + j0, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(ot + na, bt + j0, sizeof(int64_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
-            }
-        } else {
-            const int64_t threads = (m_new + MERGE_K - 1) / MERGE_K;
-            k_merge<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(as, ad, at, na, bs + j0, bd + j0, bt + j0, nbk,
-                                                                       os, od, ot);
-            h->pending_launches++;
-        }
-    }
-    if ((rc = cuda_check(h, cudaGetLastError(), "merge"))) return rc;
 
-    // commit the new store and counters
-    const int64_t N_old = h->N, M_old = h->M;
-    h->cur = nxt;
+    // 4. store
+    const int64_t N_old = h->N;
+    const int old_buf = h->cur;
+    const int64_t old_lo = h->s_lo;
+    bool ts_full = !append || !h->tg.p;
+    bool nv_full = !append || !h->nv_ready;
+    int64_t new_lo = 0;  // first appended index
+    if (append) {
+        if (h->s_hi + nbk > h->s_cap) {
+            // move the kept range to the front of the other buffer
+            const int nxt = h->cur ^ 1;
+            const int64_t cap = std::max<int64_t>(h->s_cap, 2 * m_new + 1024);
+            if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
+            if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
+            if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap))) return rc;
+            if (na > 0) {
+                const int64_t a = h->s_lo + i0;
+                cudaMemcpyAsync(h->st_src[nxt].p, h->st_src[h->cur].as<int32_t>() + a, sizeof(int32_t) * (size_t)na,
+                                cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(h->st_dst[nxt].p, h->st_dst[h->cur].as<int32_t>() + a, sizeof(int32_t) * (size_t)na,
+                                cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(h->st_ts[nxt].p, h->st_ts[h->cur].as<int64_t>() + a, sizeof(int64_t) * (size_t)na,
+                                cudaMemcpyDeviceToDevice, st);
+            }
+            h->s_base += h->s_lo + i0;
+            h->cur = nxt;
+            h->s_cap = std::min({(int64_t)(h->st_src[nxt].bytes / 4), (int64_t)(h->st_dst[nxt].bytes / 4),
+                                 (int64_t)(h->st_ts[nxt].bytes / 8)});
+            h->s_lo = 0;
+            h->s_hi = na;
+            ts_full = true;
+        } else {
+            h->s_lo += i0;
+        }
+        new_lo = h->s_hi;
+        if (nbk > 0) {
+            int32_t *os = h->st_src[h->cur].as<int32_t>() + h->s_hi;
+            int32_t *od = h->st_dst[h->cur].as<int32_t>() + h->s_hi;
+            int64_t *ot = h->st_ts[h->cur].as<int64_t>() + h->s_hi;
+            cudaMemcpyAsync(os, bs + j0, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(od, bd + j0, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(ot, bt + j0, sizeof(int64_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st);
+        }
+        h->s_hi += nbk;
+    } else {
+        const int nxt = h->cur ^ 1;
+        const int64_t cap = std::max<int64_t>(h->s_cap, 2 * m_new + 1024);
+        if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
+        if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
+        if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap))) return rc;
+        const int64_t a = h->s_lo + i0;
+        const int64_t threads = (m_new + MERGE_K - 1) / MERGE_K;
+        k_merge<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+            h->st_src[h->cur].as<int32_t>() + a, h->st_dst[h->cur].as<int32_t>() + a, h->st_ts[h->cur].as<int64_t>() + a,
+            na, bs + j0, bd + j0, bt + j0, nbk, h->st_src[nxt].as<int32_t>(), h->st_dst[nxt].as<int32_t>(),
+            h->st_ts[nxt].as<int64_t>());
+        h->pending_launches++;
+        h->s_base += h->s_hi;  // every slot is rebuilt below
+        h->cur = nxt;
+        h->s_cap = std::min({(int64_t)(h->st_src[nxt].bytes / 4), (int64_t)(h->st_dst[nxt].bytes / 4),
+                             (int64_t)(h->st_ts[nxt].bytes / 8)});
+        h->s_lo = 0;
+        h->s_hi = m_new;
+    }
+    if ((rc = cuda_check(h, cudaGetLastError(), "store"))) return rc;
+
+    // commit the store counters
     h->m = m_new;
     h->N = N_new;
     h->seq_next += n;
@@ -814,17 +478,41 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     h->has_cutoff = hs->has_cut;
     h->cutoff = hs->cut;
 
-    // 5-6. views: incremental node view after an append, full rebuild after
-    // a general merge (or before any view exists)
-    if ((rc = rebuild_ts_view(h))) return rc;
-    if (append && h->ent[h->vcur].p) rc = node_view_append(h, i0, na, nbk, N_old, M_old);
-    else rc = node_view_full(h);
-    if (rc) return rc;
+    // 5. timestamp view
+    if (h->tg.bytes < sizeof(int32_t) * (size_t)(h->s_cap + 2)) ts_full = true;
+    if (ts_full) {
+        if ((rc = ts_view_build(h))) return rc;
+    } else {
+        k_ts_evict<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), h->tg_lo, h->tg_hi, h->s_lo, ds);
+        TsGroupOp op{h->st_ts[h->cur].as<int64_t>(), new_lo, h->s_lo, h->tg.as<int32_t>() + h->tg_hi};
+        const int nbl = scan_launch(op, nbk, h->partials.as<uint64_t>(), st);
+        k_ts_tail<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), h->tg_hi, h->partials.as<uint64_t>() + nbl, h->s_hi, ds);
+        h->pending_launches += 5;
+    }
+
+    // 6. node view
+    if (!nv_full) {
+        bool rebuild = false;
+        rc = nv_append(h, h->st_src[old_buf].as<int32_t>() + old_lo, h->st_dst[old_buf].as<int32_t>() + old_lo, i0,
+                       new_lo, nbk, N_old, &rebuild);
+        if (rc) return rc;
+        nv_full = rebuild;
+    }
+    if (nv_full && (rc = nv_build(h))) return rc;
+
     cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ingest"))) return rc;
     if (hs->status)
         return fail(h, TEMPEST_ECUDA, "ingest: index consistency check failed (code 0x%llx)",
                     (unsigned long long)hs->status);
+    if (ts_full) {
+        h->tg_lo = 0;
+        h->tg_hi = hs->tg_added;
+    } else {
+        h->tg_lo = hs->tg_lo;
+        h->tg_hi += hs->tg_added;
+    }
+    h->G = h->tg_hi - h->tg_lo;
 
     if (stats) {
         stats->n_in = n;

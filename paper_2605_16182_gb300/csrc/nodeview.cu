@@ -1,0 +1,728 @@
+// nodeview.cu -- the node-and-timestamp-grouped view of Tempest Sec. 2.3,
+// kept up to date under the sliding window of Sec. 2.6 with work that grows
+// with the batch, not with the window.
+//
+// Layout ("slack" layout).  Every node with entries owns a region of the
+// entry pool (16-byte Entry records) and a region of the group pools (int32
+// group start, int64 group timestamp).  Its live entries are [e_lo, e_hi) in
+// (ts, arrival) order, its live groups [g_lo, g_hi); group g's entries start
+// at ngo[g] and the slot after the last live group holds e_hi, so every
+// group's range is [ngo[g], ngo[g + 1]).  Each region has room to grow
+// (capacity x + (x >> shift) + 16 for x live items).
+//
+// Per appended batch (the batch starts no earlier than the store ends):
+//   1. evicted entries are counted per node (the evicted edges are a store
+//      prefix, so every node loses a prefix of its entries); each such node
+//      advances e_lo, finds its first kept group by binary search and clamps
+//      that group's start;
+//   2. the batch's entries are sorted by node (stable radix sort; the batch
+//      is in (ts, arrival) order so each node's entries stay in that order);
+//      one compaction numbers the node runs and the new groups (a batch
+//      entry opens a group unless it has the timestamp of the entry before it
+//      in its node, or of the node's last group);
+//   3. one thread per run appends in place when the node's regions have room,
+//      otherwise takes fresh regions from the pools' bump pointers and queues
+//      a move of the node's live entries and groups;
+//   4. the moves run as chunked copies (group starts rebased), then the batch
+//      entries and new groups are scattered into place.
+// Nothing reads or writes the parts of the view the batch does not touch.  A
+// pool that runs out, a batch that merges into the middle of the store, or
+// the first batch rebuild the whole view from the store (the same compaction
+// over a radix sort of all entries), leaving every region with slack.
+#include "engine.cuh"
+#include "prims.cuh"
+
+namespace tw {
+
+namespace {
+
+constexpr int RELOC_CHUNK = 1024;
+
+__device__ __forceinline__ int64_t region_cap(int64_t x, int shift) { return x + (x >> shift) + 16; }
+
+// The entry of store item i (directed: edge i under its source; undirected:
+// item 2p under src_p, item 2p + 1 under dst_p).
+struct Items {
+    const int32_t *src, *dst;
+    const int64_t *ts;
+    int directed;
+    __device__ __forceinline__ int64_t edge(int64_t i) const { return directed ? i : (i >> 1); }
+    __device__ __forceinline__ bool side(int64_t i) const { return !directed && (i & 1); }
+    __device__ __forceinline__ uint32_t key(int64_t i) const
+    {
+        const int64_t e = edge(i);
+        return (uint32_t)(side(i) ? dst[e] : src[e]);
+    }
+    __device__ __forceinline__ uint32_t val(int64_t i) const { return (uint32_t)i; }
+    __device__ __forceinline__ Entry entry(int64_t i, uint32_t slot_base) const
+    {
+        const int64_t e = edge(i);
+        Entry x;
+        x.ts = ts[e];
+        x.other = side(i) ? src[e] : dst[e];
+        x.slot = (int32_t)(slot_base + (uint32_t)i);
+        return x;
+    }
+};
+
+// ---------------------------------------------------------------- full build
+
+__global__ void k_nv_entries(const uint32_t *__restrict__ vb, Items it, int64_t M, uint32_t slot_base, Entry *E)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M; p += (int64_t)gridDim.x * blockDim.x)
+        E[p] = it.entry(vb[p], slot_base);
+}
+
+// Node runs and groups over all entries in (node, ts, arrival) order.
+struct BuildRunOp {
+    const uint32_t *kb;
+    const Entry *E;
+    int32_t *run_of, *fx, *run_node, *run_pos, *run_g;
+    __device__ __forceinline__ uint64_t value(int64_t p) const
+    {
+        const bool nc = p == 0 || kb[p] != kb[p - 1];
+        const bool gc = nc || E[p].ts != E[p - 1].ts;
+        return ((uint64_t)nc << 32) | (uint64_t)gc;
+    }
+    __device__ __forceinline__ void emit(int64_t p, uint64_t v, uint64_t ex) const
+    {
+        const uint32_t r = (uint32_t)(ex >> 32) + (uint32_t)(v >> 32) - 1u;
+        run_of[p] = (int32_t)r;
+        fx[p] = (int32_t)(uint32_t)ex;
+        if (v >> 32) {
+            run_node[r] = (int32_t)kb[p];
+            run_pos[r] = (int32_t)p;
+            run_g[r] = (int32_t)(uint32_t)ex;
+        }
+    }
+};
+
+// Region sizes of each run: low 32 bits entries, high 32 bits groups (+1
+// for the slot after the last group).
+struct CapOp {
+    const int32_t *run_pos, *run_g;
+    int shift;
+    int32_t *run_de, *run_dg;
+    __device__ __forceinline__ uint64_t value(int64_t r) const
+    {
+        const int64_t c = run_pos[r + 1] - run_pos[r], gc = run_g[r + 1] - run_g[r];
+        return ((uint64_t)(region_cap(gc, shift) + 1) << 32) | (uint64_t)region_cap(c, shift);
+    }
+    __device__ __forceinline__ void emit(int64_t r, uint64_t, uint64_t ex) const
+    {
+        run_de[r] = (int32_t)(uint32_t)ex;
+        run_dg[r] = (int32_t)(uint32_t)(ex >> 32);
+    }
+};
+
+__global__ void k_nv_tail(int32_t *run_pos, int32_t *run_g, int32_t *fx, const uint64_t *tot, int64_t n)
+{
+    const uint64_t t = *tot;
+    const int64_t R = (int64_t)(t >> 32);
+    run_pos[R] = (int32_t)n;
+    run_g[R] = (int32_t)(uint32_t)t;
+    fx[n] = (int32_t)(uint32_t)t;
+}
+
+__global__ void k_nv_build_nodes(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
+                                 const int32_t *__restrict__ run_g, const int32_t *__restrict__ run_de,
+                                 const int32_t *__restrict__ run_dg, int64_t S, int shift, int4 *nrec, int2 *ngr,
+                                 int32_t *ngo, int32_t *act)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < S; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = run_node[r];
+        const int32_t c = run_pos[r + 1] - run_pos[r], gc = run_g[r + 1] - run_g[r];
+        const int32_t eb = run_de[r], gb = run_dg[r];
+        nrec[v] = make_int4(eb, eb + c, eb + (int32_t)region_cap(c, shift), gb + (int32_t)region_cap(gc, shift) + 1);
+        ngr[v] = make_int2(gb, gb + gc);
+        ngo[gb + gc] = eb + c;
+        act[r] = v;
+    }
+}
+
+__global__ void k_nv_build_scatter(const Entry *__restrict__ E, const int32_t *__restrict__ run_of,
+                                   const int32_t *__restrict__ fx, const int32_t *__restrict__ run_pos,
+                                   const int32_t *__restrict__ run_g, const int32_t *__restrict__ run_de,
+                                   const int32_t *__restrict__ run_dg, int64_t M, Entry *ent, int32_t *ngo,
+                                   int64_t *ngts)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = run_of[p];
+        const int32_t i = (int32_t)p - run_pos[r];
+        const Entry x = E[p];
+        const int32_t e = run_de[r] + i;
+        ent[e] = x;
+        if (fx[p + 1] != fx[p]) {
+            const int32_t g = run_dg[r] + (fx[p] - run_g[r]);
+            ngts[g] = x.ts;
+            ngo[g] = e;
+        }
+    }
+}
+
+// ----------------------------------------------------------- batch append
+
+__global__ void k_nv_evict_count(Items it, int64_t items, int64_t N, int32_t *ev, int32_t *ev_nodes,
+                                 NvCounters *c)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = (int32_t)it.key(i);
+        if (v < 0 || v >= N) {
+            atomicOr(&c->status, 1ull << 0);
+            v = -1;
+        }
+        const unsigned am = __activemask();
+        const unsigned peers = __match_any_sync(am, v);
+        if (v >= 0 && lane == __ffs(peers) - 1) {
+            const int32_t old = atomicAdd(&ev[v], __popc(peers));
+            if (old == 0) ev_nodes[atomicAdd(&c->n_ev_nodes, 1ull)] = v;
+        }
+    }
+}
+
+// Every node that lost entries drops them from the front of its region.
+__global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *ev, int4 *nrec, int2 *ngr,
+                                 int32_t *ngo, NvCounters *c)
+{
+    const int64_t n = (int64_t)c->n_ev_nodes;
+    long long removed = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = ev_nodes[j];
+        const int32_t k = ev[v];
+        ev[v] = 0;
+        int4 r = nrec[v];
+        int2 g = ngr[v];
+        int32_t e_lo = r.x + k;
+        if (k <= 0 || e_lo > r.y) {
+            atomicOr(&c->status, 1ull << 1);
+            e_lo = min(max(e_lo, r.x), r.y);
+        }
+        int32_t ng;
+        if (e_lo == r.y) {
+            ng = g.y;
+        } else {
+            // first group whose range ends after e_lo (ngo[g.y] = r.y > e_lo)
+            int32_t lo = g.x, hi = g.y - 1;
+            while (lo < hi) {
+                const int32_t mid = lo + ((hi - lo) >> 1);
+                if (ngo[mid + 1] > e_lo) hi = mid;
+                else lo = mid + 1;
+            }
+            ng = lo;
+            ngo[ng] = e_lo;  // the first kept group may have lost a prefix
+        }
+        removed += ng - g.x;
+        r.x = e_lo;
+        g.x = ng;
+        nrec[v] = r;
+        ngr[v] = g;
+    }
+    removed = warp_sum((unsigned long long)removed);
+    if ((threadIdx.x & 31) == 0 && removed) atomicAdd((unsigned long long *)&c->gn_delta, (unsigned long long)-removed);
+}
+
+// Node runs and new groups of the batch's entries in (node, ts, arrival)
+// order (kb: nodes, vb: batch items, groups as of after the eviction).
+struct AppendRunOp {
+    const uint32_t *kb, *vb;
+    Items it;
+    const int2 *ngr;
+    const int64_t *ngts;
+    int32_t *run_of, *fx, *run_node, *run_pos, *run_g;
+    __device__ __forceinline__ uint64_t value(int64_t p) const
+    {
+        const int64_t t = it.ts[it.edge(vb[p])];
+        const bool nc = p == 0 || kb[p] != kb[p - 1];
+        bool gc;
+        if (nc) {
+            const int2 g = ngr[kb[p]];
+            gc = g.x == g.y || ngts[g.y - 1] != t;
+        } else {
+            gc = it.ts[it.edge(vb[p - 1])] != t;
+        }
+        return ((uint64_t)nc << 32) | (uint64_t)gc;
+    }
+    __device__ __forceinline__ void emit(int64_t p, uint64_t v, uint64_t ex) const
+    {
+        const uint32_t r = (uint32_t)(ex >> 32) + (uint32_t)(v >> 32) - 1u;
+        run_of[p] = (int32_t)r;
+        fx[p] = (int32_t)(uint32_t)ex;
+        if (v >> 32) {
+            run_node[r] = (int32_t)kb[p];
+            run_pos[r] = (int32_t)p;
+            run_g[r] = (int32_t)(uint32_t)ex;
+        }
+    }
+};
+
+// One thread per node run: room in place, or fresh regions and a move.
+__global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
+                             const int32_t *__restrict__ run_g, const uint64_t *__restrict__ tot, int shift,
+                             int64_t e_cap, int64_t g_cap, int4 *nrec, int2 *ngr, int32_t *ngo, int32_t *act,
+                             int64_t act_cap, Reloc *reloc, int32_t *run_de, int32_t *run_dg, NvCounters *c)
+{
+    const int64_t R = (int64_t)(*tot >> 32);
+    long long added = 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = run_node[r];
+        const int32_t cnt = run_pos[r + 1] - run_pos[r], gc = run_g[r + 1] - run_g[r];
+        int4 rec = nrec[v];
+        int2 g = ngr[v];
+        const bool fresh = rec.z == 0;
+        if (fresh) {
+            const unsigned long long a = atomicAdd(&c->n_act, 1ull);
+            if ((int64_t)a < act_cap) act[a] = v;
+            else atomicOr(&c->status, 1ull << 2);
+        }
+        const int32_t live_e = rec.y - rec.x, live_g = g.y - g.x;
+        int32_t d_e, d_g;
+        if (!fresh && (int64_t)rec.y + cnt <= rec.z && (int64_t)g.y + gc + 1 <= rec.w) {
+            d_e = rec.y;
+            d_g = g.y;
+            rec.y += cnt;
+        } else {
+            const int64_t ecap = region_cap((int64_t)live_e + cnt, shift);
+            const int64_t gcap = region_cap((int64_t)live_g + gc, shift) + 1;
+            const unsigned long long eb = atomicAdd(&c->e_top, (unsigned long long)ecap);
+            const unsigned long long gb = atomicAdd(&c->g_top, (unsigned long long)gcap);
+            if ((int64_t)eb + ecap > e_cap || (int64_t)gb + gcap > g_cap) {
+                atomicOr(&c->overflow, 1ull);
+                run_de[r] = -1;
+                continue;
+            }
+            if (live_e > 0 || live_g > 0) {
+                const unsigned long long t = atomicAdd(&c->n_reloc, 1ull);
+                reloc[t] = Reloc{rec.x, live_e, (int32_t)eb, g.x, live_g, (int32_t)gb};
+            }
+            d_e = (int32_t)eb + live_e;
+            d_g = (int32_t)gb + live_g;
+            rec = make_int4((int32_t)eb, d_e + cnt, (int32_t)(eb + ecap), (int32_t)(gb + gcap));
+            g.x = (int32_t)gb;
+        }
+        g.y = d_g + gc;
+        nrec[v] = rec;
+        ngr[v] = g;
+        ngo[g.y] = rec.y;
+        run_de[r] = d_e;
+        run_dg[r] = d_g;
+        added += gc;
+    }
+    added = warp_sum((unsigned long long)added);
+    if ((threadIdx.x & 31) == 0 && added) atomicAdd((unsigned long long *)&c->gn_delta, (unsigned long long)added);
+}
+
+struct RelocChunkOp {
+    const Reloc *reloc;
+    int32_t *cbase;
+    __device__ __forceinline__ uint64_t value(int64_t t) const
+    {
+        const Reloc x = reloc[t];
+        return (uint64_t)((max(x.n_e, x.n_g) + RELOC_CHUNK - 1) / RELOC_CHUNK);
+    }
+    __device__ __forceinline__ void emit(int64_t t, uint64_t, uint64_t ex) const { cbase[t] = (int32_t)ex; }
+};
+
+// One warp per chunk of a move: entries copied, group timestamps copied,
+// group starts rebased to the new entry region.
+__global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__restrict__ cbase, int64_t n_reloc,
+                           const uint64_t *__restrict__ tot, Entry *ent, int32_t *ngo, int64_t *ngts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nch = (int64_t)*tot;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += warps) {
+        int64_t lo = 0, hi = n_reloc - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (cbase[mid] <= ch) lo = mid;
+            else hi = mid - 1;
+        }
+        const Reloc x = reloc[lo];
+        const int32_t off = (int32_t)(ch - cbase[lo]) * RELOC_CHUNK;
+        const int32_t e_end = min(x.n_e, off + RELOC_CHUNK);
+        for (int32_t i = off + lane; i < e_end; i += 32) ent[x.new_e + i] = ent[x.old_e + i];
+        const int32_t g_end = min(x.n_g, off + RELOC_CHUNK);
+        for (int32_t i = off + lane; i < g_end; i += 32) {
+            ngts[x.new_g + i] = ngts[x.old_g + i];
+            ngo[x.new_g + i] = ngo[x.old_g + i] - x.old_e + x.new_e;
+        }
+    }
+}
+
+__global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t slot_base, int64_t nbe,
+                             const int32_t *__restrict__ run_of, const int32_t *__restrict__ fx,
+                             const int32_t *__restrict__ run_pos, const int32_t *__restrict__ run_g,
+                             const int32_t *__restrict__ run_de, const int32_t *__restrict__ run_dg, int64_t e_cap,
+                             int64_t g_cap, Entry *ent, int32_t *ngo, int64_t *ngts, NvCounters *c)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nbe; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = run_of[p];
+        const int32_t de = run_de[r];
+        const int32_t i = (int32_t)p - run_pos[r];
+        const int64_t e = (int64_t)de + i;
+        if (de < 0 || e >= e_cap) {
+            atomicOr(&c->status, 1ull << 3);
+            continue;
+        }
+        const Entry x = it.entry(vb[p], slot_base);
+        ent[e] = x;
+        if (fx[p + 1] != fx[p]) {
+            const int64_t g = (int64_t)run_dg[r] + (fx[p] - run_g[r]);
+            if (g < 0 || g >= g_cap) {
+                atomicOr(&c->status, 1ull << 4);
+                continue;
+            }
+            ngts[g] = x.ts;
+            ngo[g] = (int32_t)e;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ exports
+
+struct CountOp {
+    const int4 *nrec;
+    const int2 *ngr;
+    int64_t N;
+    int groups;
+    int32_t *out;
+    __device__ __forceinline__ uint64_t value(int64_t v) const
+    {
+        if (v >= N) return 0;
+        return groups ? (uint64_t)(ngr[v].y - ngr[v].x) : (uint64_t)(nrec[v].y - nrec[v].x);
+    }
+    __device__ __forceinline__ void emit(int64_t v, uint64_t, uint64_t ex) const { out[v] = (int32_t)ex; }
+};
+
+// One warp per node: its entries' store positions (node order) or its group
+// starts (canonical offsets), at the node's canonical place.
+__global__ void k_nv_export(const int4 *__restrict__ nrec, const int2 *__restrict__ ngr,
+                            const int32_t *__restrict__ off, const int32_t *__restrict__ gidx,
+                            const Entry *__restrict__ ent, const int32_t *__restrict__ ngo, int64_t N,
+                            uint32_t slot_base, int groups, int32_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < N; v += warps) {
+        const int4 r = nrec[v];
+        if (!groups) {
+            for (int32_t i = lane; i < r.y - r.x; i += 32)
+                out[off[v] + i] = (int32_t)((uint32_t)ent[r.x + i].slot - slot_base);
+        } else {
+            const int2 g = ngr[v];
+            for (int32_t i = lane; i < g.y - g.x; i += 32) out[gidx[v] + i] = off[v] + (ngo[g.x + i] - r.x);
+        }
+    }
+}
+
+unsigned grid_for(tempest_t *h, int64_t n, int threads = 256)
+{
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)h->num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+int bits_for(uint64_t maxval)
+{
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) b++;
+    return b < 1 ? 1 : b;
+}
+
+uint32_t slot_base(const tempest_t *h, int64_t idx)
+{
+    const uint64_t p = (uint64_t)(h->s_base + idx);
+    return (uint32_t)(h->directed ? p : 2 * p);
+}
+
+Items items_at(const tempest_t *h, int buf, int64_t idx)
+{
+    return Items{h->st_src[buf].as<int32_t>() + idx, h->st_dst[buf].as<int32_t>() + idx,
+                 h->st_ts[buf].as<int64_t>() + idx, h->directed};
+}
+
+int ensure_runs(tempest_t *h, int64_t items, int64_t runs)
+{
+    int rc;
+    const size_t iz = (size_t)(items + 1), rz = (size_t)(runs + 1);
+    if ((rc = ensure(h, h->run_of, sizeof(int32_t) * iz, true))) return rc;
+    if ((rc = ensure(h, h->fx, sizeof(int32_t) * iz, true))) return rc;
+    if ((rc = ensure(h, h->run_node, sizeof(int32_t) * rz, true))) return rc;
+    if ((rc = ensure(h, h->run_pos, sizeof(int32_t) * rz, true))) return rc;
+    if ((rc = ensure(h, h->run_g, sizeof(int32_t) * rz, true))) return rc;
+    if ((rc = ensure(h, h->run_de, sizeof(int32_t) * rz, true))) return rc;
+    if ((rc = ensure(h, h->run_dg, sizeof(int32_t) * rz, true))) return rc;
+    for (int b = 0; b < 2; b++) {
+        if ((rc = ensure(h, h->sk32[b], sizeof(uint32_t) * iz, true))) return rc;
+        if ((rc = ensure(h, h->sv[b], sizeof(uint32_t) * iz, true))) return rc;
+    }
+    return TEMPEST_OK;
+}
+
+// Grows an array that must keep its contents (zero-filled tail).
+int grow_keep(tempest_t *h, DBuf &b, size_t used, size_t bytes)
+{
+    if (b.p && b.bytes >= bytes) return TEMPEST_OK;
+    DBuf nb;
+    std::swap(nb, b);  // b empty: ensure allocates fresh
+    int rc = ensure(h, b, bytes + bytes / 4);
+    if (rc) {
+        std::swap(nb, b);
+        return rc;
+    }
+    if (used && nb.p) cudaMemcpyAsync(b.p, nb.p, used, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemsetAsync(static_cast<char *>(b.p) + used, 0, b.bytes - used, h->stream);
+    release(h, nb);
+    return TEMPEST_OK;
+}
+
+}  // namespace
+
+// Per-node arrays cover node slots [0, N]: existing records kept, new ones
+// empty, the per-node eviction counters zero.
+int nv_ensure_nodes(tempest_t *h, int64_t N)
+{
+    const int64_t need = N + 1;
+    if (need <= h->nrec_n && h->ngr.p && h->nrec.p && h->ev.p && h->act.p) return TEMPEST_OK;
+    int rc;
+    const size_t used = (size_t)h->nrec_n;
+    if ((rc = grow_keep(h, h->nrec, sizeof(int4) * used, sizeof(int4) * (size_t)need))) return rc;
+    if ((rc = grow_keep(h, h->ngr, sizeof(int2) * used, sizeof(int2) * (size_t)need))) return rc;
+    if ((rc = grow_keep(h, h->ev, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
+    if ((rc = grow_keep(h, h->act, sizeof(int32_t) * (size_t)h->n_act, sizeof(int32_t) * (size_t)need))) return rc;
+    int64_t cover = (int64_t)(h->nrec.bytes / sizeof(int4));
+    cover = std::min(cover, (int64_t)(h->ngr.bytes / sizeof(int2)));
+    cover = std::min(cover, (int64_t)(h->ev.bytes / sizeof(int32_t)));
+    cover = std::min(cover, (int64_t)(h->act.bytes / sizeof(int32_t)));
+    h->nrec_n = cover;
+    return TEMPEST_OK;
+}
+
+// Whole view from the live store.
+int nv_build(tempest_t *h)
+{
+    cudaStream_t st = h->stream;
+    const int64_t m = h->s_hi - h->s_lo;
+    const int64_t M = h->directed ? m : 2 * m;
+    const int64_t N = h->N;
+    int rc;
+    if ((rc = nv_ensure_nodes(h, N))) return rc;
+    if ((rc = ensure(h, h->nvc, sizeof(NvCounters)))) return rc;
+    cudaMemsetAsync(h->nrec.p, 0, h->nrec.bytes, st);
+    cudaMemsetAsync(h->ngr.p, 0, h->ngr.bytes, st);
+    cudaMemsetAsync(h->nvc.p, 0, sizeof(NvCounters), st);
+    h->n_act = 0;
+    h->Gn = 0;
+    h->M = M;
+    h->pending_launches += 4;
+    if (M == 0) {
+        h->nv_ready = true;
+        return cuda_check(h, cudaGetLastError(), "node view");
+    }
+    const int64_t runs_max = std::min(M, N);
+    if ((rc = ensure_runs(h, M, runs_max))) return rc;
+    if ((rc = ensure(h, h->nv_tmp, sizeof(Entry) * (size_t)M, true))) return rc;
+    const Items it = items_at(h, h->cur, h->s_lo);
+    uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
+    uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
+    int launches = 0;
+    const int r = radix_sort_launch<uint32_t>(it, M, bits_for((uint64_t)(N > 0 ? N - 1 : 0)), kb, vb,
+                                              h->hist.as<uint32_t>(), st, &launches);
+    Entry *E = h->nv_tmp.as<Entry>();
+    k_nv_entries<<<grid_for(h, M), 256, 0, st>>>(vb[r], it, M, slot_base(h, h->s_lo), E);
+    uint64_t *part = h->partials.as<uint64_t>();
+    BuildRunOp op{kb[r], E, h->run_of.as<int32_t>(), h->fx.as<int32_t>(), h->run_node.as<int32_t>(),
+                  h->run_pos.as<int32_t>(), h->run_g.as<int32_t>()};
+    int nb = scan_launch(op, M, part, st);
+    k_nv_tail<<<1, 1, 0, st>>>(h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), h->fx.as<int32_t>(), part + nb, M);
+    uint64_t *hp = static_cast<uint64_t *>(h->hstat);
+    cudaMemcpyAsync(hp, part + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    h->pending_launches += launches + 5;
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view runs"))) return rc;
+    const int64_t S = (int64_t)(hp[0] >> 32), Gn = (int64_t)(uint32_t)hp[0];
+    // region slack: halve it until the pools fit the int32 index range
+    int shift = 0;
+    while (shift < 4 && (M + (M >> shift) + 16 * S + 1 >= (int64_t)INT32_MAX / 2 ||
+                         Gn + (Gn >> shift) + 17 * S + 1 >= (int64_t)INT32_MAX / 2))
+        shift++;
+    h->nv_shift = shift;
+    CapOp cop{h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), shift, h->run_de.as<int32_t>(),
+              h->run_dg.as<int32_t>()};
+    nb = scan_launch(cop, S, part, st);
+    cudaMemcpyAsync(hp, part + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view regions"))) return rc;
+    const int64_t e_need = (int64_t)(uint32_t)hp[0], g_need = (int64_t)(hp[0] >> 32);
+    // pools: the regions plus as much again for regions that move
+    const int64_t e_cap = std::min((int64_t)INT32_MAX - 1, 2 * e_need + 4096);
+    const int64_t g_cap = std::min((int64_t)INT32_MAX - 1, 2 * g_need + 4096);
+    if (e_need >= e_cap || g_need >= g_cap)
+        return fail(h, TEMPEST_ENOMEM, "node view: %lld entries exceed the int32 index range", (long long)M);
+    if ((rc = ensure(h, h->ent, sizeof(Entry) * (size_t)e_cap))) return rc;
+    if ((rc = ensure(h, h->ngo, sizeof(int32_t) * (size_t)g_cap))) return rc;
+    if ((rc = ensure(h, h->ngts, sizeof(int64_t) * (size_t)g_cap))) return rc;
+    h->e_cap = (int64_t)(h->ent.bytes / sizeof(Entry));
+    h->g_cap = std::min((int64_t)(h->ngo.bytes / sizeof(int32_t)), (int64_t)(h->ngts.bytes / sizeof(int64_t)));
+    h->e_cap = std::min(h->e_cap, (int64_t)INT32_MAX - 1);
+    h->g_cap = std::min(h->g_cap, (int64_t)INT32_MAX - 1);
+    k_nv_build_nodes<<<grid_for(h, S), 256, 0, st>>>(h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
+                                                     h->run_g.as<int32_t>(), h->run_de.as<int32_t>(),
+                                                     h->run_dg.as<int32_t>(), S, shift, h->nrec.as<int4>(),
+                                                     h->ngr.as<int2>(), h->ngo.as<int32_t>(), h->act.as<int32_t>());
+    k_nv_build_scatter<<<grid_for(h, M), 256, 0, st>>>(E, h->run_of.as<int32_t>(), h->fx.as<int32_t>(),
+                                                       h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(),
+                                                       h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(), M,
+                                                       h->ent.as<Entry>(), h->ngo.as<int32_t>(),
+                                                       h->ngts.as<int64_t>());
+    NvCounters c0{};
+    c0.e_top = (unsigned long long)e_need;
+    c0.g_top = (unsigned long long)g_need;
+    c0.n_act = (unsigned long long)S;
+    cudaMemcpyAsync(h->nvc.p, &c0, sizeof(NvCounters), cudaMemcpyHostToDevice, st);
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view build"))) return rc;
+    h->pending_launches += 7;
+    h->n_act = S;
+    h->S = S;
+    h->Gn = Gn;
+    h->nv_ready = true;
+    return TEMPEST_OK;
+}
+
+// Appends the store items of the edges [new_lo, new_lo + nbk) of the current
+// buffer after evicting the n_ev oldest edges, whose endpoints are ev_src /
+// ev_dst.  Returns TEMPEST_OK with *rebuild set when a pool ran out (the
+// caller then rebuilds the whole view).
+int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_t n_ev, int64_t new_lo, int64_t nbk,
+              int64_t N_old, bool *rebuild)
+{
+    cudaStream_t st = h->stream;
+    const int directed = h->directed;
+    const int64_t N = h->N;
+    const int64_t ne = directed ? n_ev : 2 * n_ev, nbe = directed ? nbk : 2 * nbk;
+    int rc;
+    *rebuild = false;
+    if ((rc = nv_ensure_nodes(h, N))) return rc;
+    if ((rc = ensure(h, h->nvc, sizeof(NvCounters)))) return rc;
+    NvCounters *dc = h->nvc.as<NvCounters>();
+    // keep the pool pointers and region count, reset the per-batch counters
+    cudaMemsetAsync(&dc->gn_delta, 0, sizeof(NvCounters) - offsetof(NvCounters, gn_delta), st);
+    cudaMemcpyAsync(&dc->n_act, &h->n_act, sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (ne > 0) {
+        if ((rc = ensure(h, h->ev_nodes, sizeof(int32_t) * (size_t)std::min(ne, N_old + 1), true))) return rc;
+        const Items ei{ev_src, ev_dst, nullptr, directed};
+        k_nv_evict_count<<<grid_for(h, ne), 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
+                                                          h->ev_nodes.as<int32_t>(), dc);
+        k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
+            h->ev_nodes.as<int32_t>(), h->ev.as<int32_t>(), h->nrec.as<int4>(), h->ngr.as<int2>(),
+            h->ngo.as<int32_t>(), dc);
+        h->pending_launches += 2;
+    }
+    if (nbe > 0) {
+        const int64_t runs_max = std::min(nbe, N);
+        if ((rc = ensure_runs(h, nbe, runs_max))) return rc;
+        if ((rc = ensure(h, h->reloc, sizeof(Reloc) * (size_t)(runs_max + 1), true))) return rc;
+        if ((rc = ensure(h, h->nv_tmp, sizeof(int32_t) * (size_t)(runs_max + 1), true))) return rc;
+        const Items it = items_at(h, h->cur, new_lo);
+        uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
+        uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
+        int launches = 0;
+        const int r = radix_sort_launch<uint32_t>(it, nbe, bits_for((uint64_t)(N > 0 ? N - 1 : 0)), kb, vb,
+                                                  h->hist.as<uint32_t>(), st, &launches);
+        uint64_t *part = h->partials.as<uint64_t>();
+        AppendRunOp op{kb[r], vb[r], it, h->ngr.as<int2>(), h->ngts.as<int64_t>(), h->run_of.as<int32_t>(),
+                       h->fx.as<int32_t>(), h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
+                       h->run_g.as<int32_t>()};
+        const int nb = scan_launch(op, nbe, part, st);
+        // keep the run totals apart: the next scans reuse the partials
+        uint64_t *tot = part + SCAN_MAX_BLOCKS + 1;
+        cudaMemcpyAsync(tot, part + nb, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+        k_nv_tail<<<1, 1, 0, st>>>(h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), h->fx.as<int32_t>(), tot, nbe);
+        k_nv_reserve<<<grid_for(h, runs_max), 256, 0, st>>>(
+            h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), tot, h->nv_shift, h->e_cap,
+            h->g_cap, h->nrec.as<int4>(), h->ngr.as<int2>(), h->ngo.as<int32_t>(), h->act.as<int32_t>(),
+            h->nrec_n, h->reloc.as<Reloc>(), h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(), dc);
+        NvCounters *hc = static_cast<NvCounters *>(h->hstat);
+        cudaMemcpyAsync(hc, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
+        h->pending_launches += launches + 5;
+        if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view reserve"))) return rc;
+        if (hc->overflow) {
+            *rebuild = true;
+            return TEMPEST_OK;
+        }
+        const int64_t n_reloc = (int64_t)hc->n_reloc;
+        if (n_reloc > 0) {
+            RelocChunkOp rop{h->reloc.as<Reloc>(), h->nv_tmp.as<int32_t>()};
+            const int nb2 = scan_launch(rop, n_reloc, part, st);
+            const int64_t nch_max = (2 * h->e_cap) / RELOC_CHUNK + n_reloc;  // bound for the grid only
+            int64_t grid = (nch_max + 7) / 8;
+            const int64_t gcap = (int64_t)h->num_sms * 16;
+            if (grid > gcap) grid = gcap;
+            k_nv_reloc<<<(unsigned)grid, 256, 0, st>>>(h->reloc.as<Reloc>(), h->nv_tmp.as<int32_t>(), n_reloc,
+                                                       part + nb2, h->ent.as<Entry>(), h->ngo.as<int32_t>(),
+                                                       h->ngts.as<int64_t>());
+            h->pending_launches += 4;
+        }
+        k_nv_scatter<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], it, slot_base(h, new_lo), nbe, h->run_of.as<int32_t>(),
+                                                       h->fx.as<int32_t>(), h->run_pos.as<int32_t>(),
+                                                       h->run_g.as<int32_t>(), h->run_de.as<int32_t>(),
+                                                       h->run_dg.as<int32_t>(), h->e_cap, h->g_cap,
+                                                       h->ent.as<Entry>(), h->ngo.as<int32_t>(),
+                                                       h->ngts.as<int64_t>(), dc);
+        h->pending_launches++;
+    }
+    NvCounters *hc = static_cast<NvCounters *>(h->hstat);
+    cudaMemcpyAsync(hc, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view append"))) return rc;
+    if (hc->status)
+        return fail(h, TEMPEST_ECUDA, "node view: consistency check failed (code 0x%llx)",
+                    (unsigned long long)hc->status);
+    h->Gn += (int64_t)hc->gn_delta;
+    h->n_act = (int64_t)hc->n_act;
+    h->S = h->n_act;
+    h->M = directed ? (h->s_hi - h->s_lo) : 2 * (h->s_hi - h->s_lo);
+    return TEMPEST_OK;
+}
+
+// Canonical arrays of the view (device destination): node segment starts
+// (NODE_OFF, N + 1), node order as store positions (M), group starts as
+// canonical offsets (Gn + 1), per-node first group (N + 1).
+int nv_export(tempest_t *h, int which, int32_t *out)
+{
+    cudaStream_t st = h->stream;
+    const int64_t N = h->N;
+    int rc;
+    if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
+    uint64_t *part = h->partials.as<uint64_t>();
+    const int4 *nrec = h->nrec.as<int4>();
+    const int2 *ngr = h->ngr.as<int2>();
+    if (which == TEMPEST_STATE_NODE_OFF || which == TEMPEST_STATE_NODE_GIDX) {
+        CountOp op{nrec, ngr, N, which == TEMPEST_STATE_NODE_GIDX, out};
+        scan_launch(op, N + 1, part, st);
+        return cuda_check(h, cudaGetLastError(), "export");
+    }
+    // temporaries: canonical segment starts and first groups
+    if ((rc = ensure(h, h->nv_tmp, sizeof(int32_t) * 2 * (size_t)(N + 1), true))) return rc;
+    int32_t *off = h->nv_tmp.as<int32_t>();
+    int32_t *gidx = off + (N + 1);
+    CountOp o1{nrec, ngr, N, 0, off};
+    scan_launch(o1, N + 1, part, st);
+    const int groups = which == TEMPEST_STATE_NODE_GROUP_OFF;
+    if (groups) {
+        CountOp o2{nrec, ngr, N, 1, gidx};
+        scan_launch(o2, N + 1, part, st);
+    }
+    if (N > 0)
+        k_nv_export<<<grid_for(h, 32 * N), 256, 0, st>>>(nrec, ngr, off, gidx, h->ent.as<Entry>(),
+                                                         h->ngo.as<int32_t>(), N, slot_base(h, h->s_lo), groups,
+                                                         out);
+    if (groups) {
+        const int32_t Mv = (int32_t)h->M;
+        cudaMemcpyAsync(out + h->Gn, &Mv, sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    }
+    return cuda_check(h, cudaStreamSynchronize(st), "export");
+}
+
+}  // namespace tw

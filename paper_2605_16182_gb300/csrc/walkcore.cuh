@@ -9,19 +9,24 @@
 namespace tw {
 
 struct WalkView {
-    // edge store, (ts, arrival) order
+    // edge store, (ts, arrival) order: the live edges are [0, m) from these
+    // pointers
     const int32_t *st_src;
     const int32_t *st_dst;
     const int64_t *st_ts;
     int64_t m;
-    // timestamp-grouped view
-    const int32_t *ts_goff;
+    // timestamp-grouped view: group g's edges are [max(tg[g], s_lo) - s_lo,
+    // tg[g + 1] - s_lo) (store buffer indices; the head group may have lost a
+    // prefix to eviction)
+    const int32_t *tg;
+    int64_t s_lo;
     int64_t G;
-    // node view
-    const int32_t *gidx;   // [N+1]
-    const int32_t *ngo;    // [Gn+1]
-    const int64_t *ngts;   // [Gn]
-    const Entry *ent;      // [M]
+    // node view: groups [ngr[v].x, ngr[v].y) of node v; group g's entries
+    // [ngo[g], ngo[g + 1]) in the entry pool
+    const int2 *ngr;
+    const int32_t *ngo;
+    const int64_t *ngts;
+    const Entry *ent;
     // time buckets of nodes with at least BKT_MIN_G groups (null: none)
     const int32_t *bkt_base;  // [N+1], valid for those nodes
     const int32_t *bkt;
@@ -29,6 +34,14 @@ struct WalkView {
     int directed;
     ExpRate rate_hop, rate_start;
 };
+
+// Store range [a, b) of timestamp group g (g < G).
+__device__ __forceinline__ void ts_group_range(const WalkView &V, int64_t g, int64_t &a, int64_t &b)
+{
+    const int64_t x = __ldg(V.tg + g);
+    a = (x > V.s_lo ? x : V.s_lo) - V.s_lo;
+    b = (int64_t)__ldg(V.tg + g + 1) - V.s_lo;
+}
 
 struct WalkOut {
     int64_t n_walks;
@@ -168,8 +181,9 @@ __device__ __forceinline__ void start_edge(const WalkView &V, const WalkOut &O, 
         k = uniform_index_k(k1, V.m);
     } else {
         const int64_t g = sampler_index_k(k1, V.G, bias, V.rate_start);
-        const int64_t a = V.ts_goff[g];
-        k = a + uniform_index_k(k2, (int64_t)V.ts_goff[g + 1] - a);
+        int64_t a, b;
+        ts_group_range(V, g, a, b);
+        k = a + uniform_index_k(k2, b - a);
     }
     s = V.st_src[k];
     d = V.st_dst[k];

@@ -42,8 +42,9 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 k = uniform_index_k(k1, V.m);
             } else {
                 const int64_t g = sampler_index_k(k1, V.G, bias, V.rate_start);
-                const int64_t a = V.ts_goff[g];
-                k = a + uniform_index_k(k2, (int64_t)V.ts_goff[g + 1] - a);
+                int64_t a, b;
+                ts_group_range(V, g, a, b);
+                k = a + uniform_index_k(k2, b - a);
             }
             int32_t s = V.st_src[k], d = V.st_dst[k];
             const int64_t t0 = V.st_ts[k];
@@ -62,7 +63,8 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
             int32_t v = d;
             int64_t t = t0;
             for (uint32_t h = 1; len < L; h++) {
-                const int32_t g0 = __ldg(V.gidx + v), g1 = __ldg(V.gidx + v + 1);
+                const int2 gr = __ldg(V.ngr + v);
+                const int32_t g0 = gr.x, g1 = gr.y;
                 const int32_t c = first_later(V, v, g0, g1, t);
                 if (c == g1) break;  // Gamma_t(v) is empty
                 r = walk_rand(O.seed, (uint64_t)w, h);
@@ -310,14 +312,15 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                     s.state = S_EDGE;
                 } else {
                     const int64_t g = sampler_index_k(u1, V.G, bias, V.rate_start);
-                    z0 = __ldg(V.ts_goff + g);
-                    z1 = __ldg(V.ts_goff + g + 1);
+                    z0 = __ldg(V.tg + g);
+                    z1 = __ldg(V.tg + g + 1);
                     s.state = S_SGROUP;
                 }
                 break;
             }
             case S_SGROUP: {
-                const int64_t k = (int64_t)z0 + uniform_index_k(s.ud, (int64_t)(z1 - z0));
+                const int64_t a = ((int64_t)z0 > V.s_lo ? (int64_t)z0 : V.s_lo) - V.s_lo;
+                const int64_t k = a + uniform_index_k(s.ud, (int64_t)z1 - V.s_lo - a);
                 y0 = __ldg(V.st_ts + k);
                 z0 = __ldg(V.st_src + k);
                 z1 = __ldg(V.st_dst + k);
@@ -346,8 +349,9 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 if (s.len >= s.cap_len) {
                     finish = true;
                 } else {
-                    z0 = __ldg(V.gidx + b);
-                    z1 = __ldg(V.gidx + b + 1);
+                    const int2 gr = __ldg(V.ngr + b);
+                    z0 = gr.x;
+                    z1 = gr.y;
                     s.state = S_RANGE;
                 }
                 break;
@@ -453,9 +457,9 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 if (s.len >= s.cap_len) {
                     finish = true;
                 } else {
-                    const int32_t v = z0;
-                    z0 = __ldg(V.gidx + v);
-                    z1 = __ldg(V.gidx + v + 1);
+                    const int2 gr = __ldg(V.ngr + z0);
+                    z0 = gr.x;
+                    z1 = gr.y;
                     s.state = S_RANGE;
                 }
                 break;
@@ -629,16 +633,17 @@ int sample_index_run(tempest_t *h, const uint64_t *ub, const int64_t *n, int64_t
 WalkView make_view(tempest_t *h)
 {
     WalkView V;
-    V.st_src = h->st_src[h->cur].as<int32_t>();
-    V.st_dst = h->st_dst[h->cur].as<int32_t>();
-    V.st_ts = h->st_ts[h->cur].as<int64_t>();
+    V.st_src = h->st_src[h->cur].as<int32_t>() + h->s_lo;
+    V.st_dst = h->st_dst[h->cur].as<int32_t>() + h->s_lo;
+    V.st_ts = h->st_ts[h->cur].as<int64_t>() + h->s_lo;
     V.m = h->m;
-    V.ts_goff = h->ts_goff.as<int32_t>();
+    V.tg = h->tg.as<int32_t>() + h->tg_lo;
+    V.s_lo = h->s_lo;
     V.G = h->G;
-    V.gidx = h->gidx.as<int32_t>();
+    V.ngr = h->ngr.as<int2>();
     V.ngo = h->ngo.as<int32_t>();
     V.ngts = h->ngts.as<int64_t>();
-    V.ent = h->ent[h->vcur].as<Entry>();
+    V.ent = h->ent.as<Entry>();
     const bool bk = h->n_big > 0 && h->bkt_ver == h->state_ver;
     V.bkt_base = bk ? h->bkt_base.as<int32_t>() : nullptr;
     V.bkt = bk ? h->bkt.as<int32_t>() : nullptr;

@@ -269,3 +269,43 @@ def test_cooperative_tiers_are_all_exercised():
         tiers = eng.last_walk_stats()["tier_launches"]
         assert tiers[0] > 0 and tiers[4] > 0, tiers
     check_walks(eng, orc, 50_000, 30, policy=1, seed=8)
+
+
+# ------------------------------------------------- index regions under growth
+def test_growing_hub_moves_regions_and_rebuilds():
+    """Without a window one node keeps growing: its regions move to larger
+    ones every few batches and the pools run out (a full rebuild); every
+    state array and the walks must stay the oracle's after every batch."""
+    eng, orc = pair(0, 1)
+    rng = np.random.default_rng(3)
+    t = 0
+    for b in range(14):
+        n = 10 if b == 0 else int(rng.integers(200, 3000))
+        s = np.where(rng.random(n) < 0.8, 0, rng.integers(1, 50 + 40 * b, n)).astype(np.int32)
+        d = rng.integers(0, 60 + 40 * b, n).astype(np.int32)
+        ts = (t + np.sort(rng.integers(0, 5 * n, n))).astype(np.int64)
+        t = int(ts[-1])  # the next batch may start on the same timestamp
+        ingest_both(eng, orc, s, d, ts)
+        assert_state_equal(eng.state(), orc.state())
+        if b % 4 == 3:
+            check_walks(eng, orc, 2000, 12, seed=b, biases=(0, 1), scheds=(_lib.SCHED_STREAM,))
+
+
+@pytest.mark.parametrize("directed", [1, 0])
+def test_sliding_window_moves_store_and_regions(directed):
+    """A count window over many small batches: the store's live range walks
+    through its buffer and moves to the front of the other buffer, and node
+    regions move as nodes drift; the state stays the oracle's throughout."""
+    eng, orc = pair(-700, directed)
+    rng = np.random.default_rng(5 + directed)
+    t = 0
+    for b in range(40):
+        n = int(rng.integers(0, 400))
+        s = rng.integers(0, 30 + b, n).astype(np.int32)
+        d = rng.integers(0, 30 + b, n).astype(np.int32)
+        ts = (t + np.sort(rng.integers(0, 3 * n + 1, n))).astype(np.int64)
+        if n:
+            t = int(ts[-1])
+        ingest_both(eng, orc, s, d, ts)
+        assert_state_equal(eng.state(), orc.state())
+    check_walks(eng, orc, 3000, 16, seed=1, biases=(0, 2))
