@@ -29,6 +29,8 @@ namespace tw {
 
 namespace {
 
+constexpr int BKT_UNROLL = 4;  // 32-group steps whose loads are issued together
+
 struct BigNodeOp {
     const int32_t *act;
     const int2 *ngr;
@@ -95,38 +97,52 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
         const BktMap bm = bkt_map(__ldg(ngts + g0), __ldg(ngts + g1 - 1), K);
         const int32_t start = g0 + (int32_t)(c - __ldg(big_c + b)) * BKT_CHUNK;
         const int32_t end = min(g1, start + BKT_CHUNK);
-        for (int32_t base = start; base < end; base += 32) {
-            const int32_t g = base + lane;
-            const bool valid = g < end;
-            const int32_t k = valid ? (int32_t)bkt_index(bm, __ldg(ngts + g)) : 0;
-            int32_t kp = __shfl_up_sync(0xffffffffu, k, 1);
-            if (lane == 0) kp = g == g0 ? -1 : (int32_t)bkt_index(bm, __ldg(ngts + g - 1));
-            // entries (kp, k] hold g; the last group adds (k, K] holding g1
-            const bool last = valid && g == g1 - 1;
-            const int32_t lo_k = kp + 1;
-            const int32_t cnt = valid ? (last ? (int32_t)K : k) - kp : 0;
-            int32_t incl = cnt;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+        // bucket of the group before the chunk (-1 at the node's first group)
+        int32_t k_prev = start == g0 ? -1 : (int32_t)bkt_index(bm, __ldg(ngts + start - 1));
+        for (int32_t base = start; base < end; base += 32 * BKT_UNROLL) {
+            // BKT_UNROLL coalesced loads in flight, then the groups in order
+            int64_t tv[BKT_UNROLL];
+#pragma unroll
+            for (int q = 0; q < BKT_UNROLL; q++) {
+                const int32_t g = base + 32 * q + lane;
+                tv[q] = g < end ? __ldg(ngts + g) : 0;
             }
-            const int32_t excl = incl - cnt;
-            const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            for (int32_t r0 = 0; r0 < total; r0 += 32) {
-                const int32_t idx = r0 + lane;
-                // owner: the last lane whose share starts at or before idx
-                int32_t own = 0;
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int32_t j = own + step;
-                    if (__shfl_sync(0xffffffffu, excl, j) <= idx) own = j;
+#pragma unroll
+            for (int q = 0; q < BKT_UNROLL; q++) {
+                const int32_t g = base + 32 * q + lane;
+                if (base + 32 * q >= end) break;  // warp-uniform
+                const bool valid = g < end;
+                const int32_t k = valid ? (int32_t)bkt_index(bm, tv[q]) : (int32_t)K;
+                int32_t kp = __shfl_up_sync(0xffffffffu, k, 1);
+                if (lane == 0) kp = k_prev;
+                k_prev = __shfl_sync(0xffffffffu, k, 31);
+                // entries (kp, k] hold g; the last group adds (k, K] holding g1
+                const bool last = valid && g == g1 - 1;
+                const int32_t lo_k = kp + 1;
+                const int32_t cnt = valid ? (last ? (int32_t)K : k) - kp : 0;
+                int32_t incl = cnt;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
                 }
-                const int32_t o_lo = __shfl_sync(0xffffffffu, lo_k, own);
-                const int32_t o_ex = __shfl_sync(0xffffffffu, excl, own);
-                const int32_t o_g = __shfl_sync(0xffffffffu, g, own);
-                const int32_t o_k = __shfl_sync(0xffffffffu, k, own);
-                if (idx < total) {
-                    const int32_t kk = o_lo + (idx - o_ex);
-                    bkt[tb + kk] = kk <= o_k ? o_g : g1;
+                const int32_t excl = incl - cnt;
+                const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                for (int32_t r0 = 0; r0 < total; r0 += 32) {
+                    const int32_t idx = r0 + lane;
+                    // owner: the last lane whose share starts at or before idx
+                    int32_t own = 0;
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int32_t j = own + step;
+                        if (__shfl_sync(0xffffffffu, excl, j) <= idx) own = j;
+                    }
+                    const int32_t o_lo = __shfl_sync(0xffffffffu, lo_k, own);
+                    const int32_t o_ex = __shfl_sync(0xffffffffu, excl, own);
+                    const int32_t o_g = __shfl_sync(0xffffffffu, g, own);
+                    const int32_t o_k = __shfl_sync(0xffffffffu, k, own);
+                    if (idx < total) {
+                        const int32_t kk = o_lo + (idx - o_ex);
+                        bkt[tb + kk] = kk <= o_k ? o_g : g1;
+                    }
                 }
             }
         }

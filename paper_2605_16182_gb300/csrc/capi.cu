@@ -26,32 +26,6 @@ __global__ void k_scan_partials(uint64_t *p, int nb)
     if (threadIdx.x == 0) p[nb] = carry;
 }
 
-// One block; every warp owns a contiguous slice and reads it 32 elements at
-// a time (coalesced): pass 1 sums the slices, pass 2 rescans them in place.
-__global__ void k_scan_u32_small(uint32_t *a, int64_t n)
-{
-    __shared__ uint32_t sh[33];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int64_t per = (n + nw - 1) / nw;
-    per = (per + 31) & ~(int64_t)31;
-    const int64_t b0 = (int64_t)w * per;
-    const int64_t b1 = min(n, b0 + per);
-    uint32_t s = 0;
-    for (int64_t i = b0 + lane; i < b1; i += 32) s += a[i];
-    s = warp_sum(s);
-    // block scan over warp sums: lane 0 of each warp contributes
-    uint32_t tot;
-    uint32_t ex = block_excl_scan<uint32_t>(lane == 0 ? s : 0u, sh, tot);
-    uint32_t carry = __shfl_sync(0xffffffffu, ex, 0);
-    for (int64_t base = b0; base < b1; base += 32) {
-        const int64_t i = base + lane;
-        const uint32_t v = i < b1 ? a[i] : 0u;
-        const uint32_t inc = warp_incl_scan(v);
-        if (i < b1) a[i] = carry + inc - v;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-    }
-}
-
 static thread_local std::string g_create_err;
 
 int fail(tempest_t *h, int code, const char *fmt, ...)
@@ -139,7 +113,7 @@ static void free_all(tempest_t *h)
                     &h->sv[1],     &h->hist,      &h->partials,  &h->dstat,     &h->wcnt,      &h->out_stage,
                     &h->in_stage,  &h->exp_stage, &h->co_node,   &h->co_t,      &h->co_len,    &h->co_act[0],
                     &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt_base,  &h->bkt,
-                    &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out};
+                    &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched};
     for (DBuf *b : bufs) release(h, *b);
 }
 

@@ -452,7 +452,7 @@ int coop_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launche
         if ((rc = ensure(h, h->sv[b], sizeof(uint32_t) * nz, true))) return rc;
     }
     if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
-    if ((rc = ensure(h, h->hist, sizeof(uint32_t) * ((size_t)RADIX * SORT_MAX_BLOCKS + 1)))) return rc;
+    if ((rc = ensure(h, h->hist, sizeof(uint32_t) * (size_t)SORT_HIST_WORDS))) return rc;
 
     unsigned int *ctr = h->co_ctr.as<unsigned int>();  // [0..4] tier counts, [8] next active count
     unsigned int *hc = static_cast<unsigned int *>(h->hstat);

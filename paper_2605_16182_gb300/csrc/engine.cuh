@@ -51,6 +51,7 @@ struct NvCounters {
     unsigned long long n_act;         // nodes owning regions
     unsigned long long overflow;      // a pool could not serve a region
     unsigned long long status;        // nonzero: a consistency check failed
+    unsigned long long n_dense;       // batch-local node ids handed out
 };
 
 // A region move: live entries and groups of one node to fresh regions.
@@ -126,6 +127,8 @@ struct tempest {
     int nv_shift = 0;       // region capacity = x + (x >> nv_shift) + 16
     bool nv_ready = false;
     tw::DBuf nv_tmp, run_node, run_pos, run_g, run_of, fx, run_de, run_dg, ev_nodes, reloc;
+    tw::DBuf dense;    // int32 [N+1]: 1 + a batch-local id of each node the batch touches (0 between batches)
+    tw::DBuf touched;  // int32: node of each batch-local id
     int64_t S = 0;     // nodes that own regions (for the bucket index)
     int64_t state_ver = 0;  // bumped by every ingest
 

@@ -310,7 +310,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     h->state_ver++;  // derived walk indexes are rebuilt on the next walk call
     if ((rc = ensure(h, h->dstat, sizeof(IngestScratch)))) return rc;
     if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
-    if ((rc = ensure(h, h->hist, sizeof(uint32_t) * ((size_t)RADIX * SORT_MAX_BLOCKS + 1)))) return rc;
+    if ((rc = ensure(h, h->hist, sizeof(uint32_t) * (size_t)SORT_HIST_WORDS))) return rc;
     IngestScratch *ds = h->dstat.as<IngestScratch>();
     IngestScratch *hs = static_cast<IngestScratch *>(h->hstat);
 

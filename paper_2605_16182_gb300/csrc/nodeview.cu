@@ -223,10 +223,65 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
     if ((threadIdx.x & 31) == 0 && removed) atomicAdd((unsigned long long *)&c->gn_delta, (unsigned long long)-removed);
 }
 
+// Batch-local node ids, so that the batch's node sort needs only as many
+// key bits as the batch has distinct nodes.  The first warp leader to see a
+// node claims an id with a compare-and-swap; a leader that loses the race
+// adopts the winner's id (its own candidate id stays unused: touched[] keeps
+// -1 there).  Ids are in arbitrary order; only grouping matters downstream.
+__global__ void k_nv_dense(Items it, int64_t nbe, int32_t *dense, int32_t *touched, uint32_t *keys, NvCounters *c)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nbe; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)it.key(j);
+        const unsigned am = __activemask();
+        const unsigned peers = __match_any_sync(am, v);
+        const int leader = __ffs(peers) - 1;
+        int32_t id = 0;
+        if (lane == leader) {
+            id = dense[v];
+            if (id == 0) {
+                const int32_t cand = (int32_t)atomicAdd(&c->n_dense, 1ull) + 1;
+                const int32_t prev = atomicCAS(&dense[v], 0, cand);
+                if (prev == 0) {
+                    id = cand;
+                    touched[cand - 1] = v;
+                } else {
+                    id = prev;
+                }
+            }
+        }
+        id = __shfl_sync(am, id, leader);
+        keys[j] = (uint32_t)(id - 1);
+    }
+}
+
+__global__ void k_iota(uint32_t *v, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (uint32_t)i;
+}
+
+__global__ void k_nv_dense_reset(const int32_t *__restrict__ touched, const NvCounters *c, int32_t *dense)
+{
+    const int64_t n = (int64_t)c->n_dense;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = touched[i];
+        if (v >= 0) dense[v] = 0;
+    }
+}
+
+struct DenseLoader {
+    const uint32_t *keys;
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return keys[i]; }
+    __device__ __forceinline__ uint32_t val(int64_t i) const { return (uint32_t)i; }
+};
+
 // Node runs and new groups of the batch's entries in (node, ts, arrival)
-// order (kb: nodes, vb: batch items, groups as of after the eviction).
+// order (kb: batch-local node ids, vb: batch items, groups as of after the
+// eviction).
 struct AppendRunOp {
     const uint32_t *kb, *vb;
+    const int32_t *touched;
     Items it;
     const int2 *ngr;
     const int64_t *ngts;
@@ -237,7 +292,7 @@ struct AppendRunOp {
         const bool nc = p == 0 || kb[p] != kb[p - 1];
         bool gc;
         if (nc) {
-            const int2 g = ngr[kb[p]];
+            const int2 g = ngr[touched[kb[p]]];
             gc = g.x == g.y || ngts[g.y - 1] != t;
         } else {
             gc = it.ts[it.edge(vb[p - 1])] != t;
@@ -250,7 +305,7 @@ struct AppendRunOp {
         run_of[p] = (int32_t)r;
         fx[p] = (int32_t)(uint32_t)ex;
         if (v >> 32) {
-            run_node[r] = (int32_t)kb[p];
+            run_node[r] = touched[kb[p]];
             run_pos[r] = (int32_t)p;
             run_g[r] = (int32_t)(uint32_t)ex;
         }
@@ -487,14 +542,16 @@ int grow_keep(tempest_t *h, DBuf &b, size_t used, size_t bytes)
 int nv_ensure_nodes(tempest_t *h, int64_t N)
 {
     const int64_t need = N + 1;
-    if (need <= h->nrec_n && h->ngr.p && h->nrec.p && h->ev.p && h->act.p) return TEMPEST_OK;
+    if (need <= h->nrec_n && h->ngr.p && h->nrec.p && h->ev.p && h->act.p && h->dense.p) return TEMPEST_OK;
     int rc;
     const size_t used = (size_t)h->nrec_n;
     if ((rc = grow_keep(h, h->nrec, sizeof(int4) * used, sizeof(int4) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->ngr, sizeof(int2) * used, sizeof(int2) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->ev, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->act, sizeof(int32_t) * (size_t)h->n_act, sizeof(int32_t) * (size_t)need))) return rc;
+    if ((rc = grow_keep(h, h->dense, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
     int64_t cover = (int64_t)(h->nrec.bytes / sizeof(int4));
+    cover = std::min(cover, (int64_t)(h->dense.bytes / sizeof(int32_t)));
     cover = std::min(cover, (int64_t)(h->ngr.bytes / sizeof(int2)));
     cover = std::min(cover, (int64_t)(h->ev.bytes / sizeof(int32_t)));
     cover = std::min(cover, (int64_t)(h->act.bytes / sizeof(int32_t)));
@@ -626,13 +683,33 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         if ((rc = ensure(h, h->reloc, sizeof(Reloc) * (size_t)(runs_max + 1), true))) return rc;
         if ((rc = ensure(h, h->nv_tmp, sizeof(int32_t) * (size_t)(runs_max + 1), true))) return rc;
         const Items it = items_at(h, h->cur, new_lo);
+        // batch-local node ids (keys in run_of, which the run scan rewrites later)
+        if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
+        cudaMemsetAsync(h->touched.p, 0xff, sizeof(int32_t) * (size_t)nbe, st);
+        uint32_t *dkeys = reinterpret_cast<uint32_t *>(h->run_of.as<int32_t>());
+        k_nv_dense<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), h->touched.as<int32_t>(),
+                                                     dkeys, dc);
+        NvCounters *hd = static_cast<NvCounters *>(h->hstat);
+        cudaMemcpyAsync(hd, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
+        if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view ids"))) return rc;
+        const int64_t n_ids = (int64_t)hd->n_dense;
+        // the ids live in keys and touched[] from here on: clear dense[] now,
+        // so no later exit of this call can leave ids behind
+        k_nv_dense_reset<<<grid_for(h, n_ids), 256, 0, st>>>(h->touched.as<int32_t>(), dc, h->dense.as<int32_t>());
         uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
         uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
         int launches = 0;
-        const int r = radix_sort_launch<uint32_t>(it, nbe, bits_for((uint64_t)(N > 0 ? N - 1 : 0)), kb, vb,
-                                                  h->hist.as<uint32_t>(), st, &launches);
+        const DenseLoader dl{dkeys};
+        int r = radix_sort_launch<uint32_t>(dl, nbe, bits_for((uint64_t)(n_ids > 0 ? n_ids - 1 : 0)), kb, vb,
+                                            h->hist.as<uint32_t>(), st, &launches);
+        if (r < 0) {  // a single distinct node: the batch order is already grouped
+            cudaMemcpyAsync(kb[0], dkeys, sizeof(uint32_t) * (size_t)nbe, cudaMemcpyDeviceToDevice, st);
+            k_iota<<<grid_for(h, nbe), 256, 0, st>>>(vb[0], nbe);
+            r = 0;
+        }
         uint64_t *part = h->partials.as<uint64_t>();
-        AppendRunOp op{kb[r], vb[r], it, h->ngr.as<int2>(), h->ngts.as<int64_t>(), h->run_of.as<int32_t>(),
+        AppendRunOp op{kb[r], vb[r], h->touched.as<int32_t>(), it, h->ngr.as<int2>(), h->ngts.as<int64_t>(),
+                       h->run_of.as<int32_t>(),
                        h->fx.as<int32_t>(), h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
                        h->run_g.as<int32_t>()};
         const int nb = scan_launch(op, nbe, part, st);

@@ -424,13 +424,49 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(L ld, int64_t n, in
     }
 }
 
-// exclusive scan of n u32 (one block of 1024 threads)
-__global__ void k_scan_u32_small(uint32_t *a, int64_t n);
+// Exclusive scan of the digit histogram, in two kernels: every 1024-thread
+// block scans a chunk of HSCAN_CHUNK counts in place and leaves the chunk
+// total in part[]; one block then scans part[].  The scatter adds part[] of
+// the chunk to each offset it reads.  part[] follows the histogram (the
+// histogram buffer holds SORT_HIST_WORDS u32).
+constexpr int HSCAN_CHUNK = 4096;
+constexpr int64_t SORT_HIST_WORDS = (int64_t)RADIX * SORT_MAX_BLOCKS + 1 + 2 * 128;
+
+static __global__ void __launch_bounds__(1024) k_hscan_local(uint32_t *a, int64_t n, uint32_t *part)
+{
+    __shared__ uint32_t sh[33];
+    const int64_t c0 = (int64_t)blockIdx.x * HSCAN_CHUNK + (int64_t)threadIdx.x * 4;
+    uint32_t v[4];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        v[k] = c0 + k < n ? a[c0 + k] : 0u;
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan<uint32_t>(s, sh, tot);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (c0 + k < n) a[c0 + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+static __global__ void __launch_bounds__(1024) k_hscan_part(uint32_t *part, int nb)
+{
+    __shared__ uint32_t sh[33];
+    const uint32_t v = (int)threadIdx.x < nb ? part[threadIdx.x] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan<uint32_t>(v, sh, tot);
+    if ((int)threadIdx.x < nb) part[threadIdx.x] = ex;
+}
 
 template <typename K, class L>
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(L ld, K *kout, uint32_t *vout,
                                                                 int64_t n, int64_t per_blk, int shift,
-                                                                const uint32_t *offs, int nblk)
+                                                                const uint32_t *offs, const uint32_t *part,
+                                                                int nblk)
 {
     __shared__ uint32_t run_off[RADIX];
     __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
@@ -444,7 +480,10 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(L ld, K *kout, u
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t b0 = (int64_t)blockIdx.x * per_blk;
     const int64_t b1 = min(n, b0 + per_blk);
-    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) run_off[d] = offs[(int64_t)d * nblk + blockIdx.x];
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) {
+        const int64_t x = (int64_t)d * nblk + blockIdx.x;
+        run_off[d] = offs[x] + part[x / HSCAN_CHUNK];
+    }
 
     for (int64_t t0 = b0; t0 < b1; t0 += SORT_TILE) {
         for (int i = threadIdx.x; i < SORT_WARPS * RADIX; i += blockDim.x) (&wcnt[0][0])[i] = 0;
@@ -519,11 +558,12 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(L ld, K *kout, u
 }
 
 // Sorts n pairs by the low `bits` bits of the key.  The loader provides the
-// input; k[0..1], v[0..1] are double buffers of n elements (the loader may
-// read k[0]/v[0]).  hist needs RADIX * SORT_MAX_BLOCKS + 1 u32.  Returns the
+// input (it must not read k[0] / v[0], which the first pass writes);
+// k[0..1], v[0..1] are double buffers of n elements.  Returns the
 // buffer index (0 or 1) holding the result, or -1 when no pass ran (the
 // input already has all keys equal in those bits; the caller then uses the
-// loader's data as is).
+// loader's data as is).  hist needs RADIX * nblocks + 1 + 2 * 128 u32 (at most
+// SORT_HIST_WORDS).
 template <typename K, class L>
 int radix_sort_launch(const L &ld, int64_t n, int bits, K *k[2], uint32_t *v[2], uint32_t *hist,
                       cudaStream_t st, int *launches)
@@ -535,24 +575,29 @@ int radix_sort_launch(const L &ld, int64_t n, int bits, K *k[2], uint32_t *v[2],
     per = (per + SORT_TILE - 1) / SORT_TILE * SORT_TILE;
     nb = (n + per - 1) / per;
     const int passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
+    const int64_t hn = (int64_t)RADIX * nb;
+    const int hchunks = (int)((hn + HSCAN_CHUNK - 1) / HSCAN_CHUNK);
+    uint32_t *part = hist + hn + 1;
     int cur = -1;
     for (int p = 0; p < passes; p++) {
         const int shift = p * RADIX_BITS;
         const int out = (cur == 0) ? 1 : 0;
         if (p == 0) {
             k_radix_hist<K, L><<<(unsigned)nb, SORT_THREADS, 0, st>>>(ld, n, per, shift, hist, (int)nb);
-            k_scan_u32_small<<<1, 1024, 0, st>>>(hist, (int64_t)RADIX * nb);
+            k_hscan_local<<<hchunks, 1024, 0, st>>>(hist, hn, part);
+            k_hscan_part<<<1, 1024, 0, st>>>(part, hchunks);
             k_radix_scatter<K, L><<<(unsigned)nb, SORT_THREADS, 0, st>>>(ld, k[out], v[out], n, per, shift,
-                                                                          hist, (int)nb);
+                                                                          hist, part, (int)nb);
         } else {
             ArrayLoader<K> al{k[cur], v[cur]};
             k_radix_hist<K, ArrayLoader<K>><<<(unsigned)nb, SORT_THREADS, 0, st>>>(al, n, per, shift, hist,
                                                                                   (int)nb);
-            k_scan_u32_small<<<1, 1024, 0, st>>>(hist, (int64_t)RADIX * nb);
+            k_hscan_local<<<hchunks, 1024, 0, st>>>(hist, hn, part);
+            k_hscan_part<<<1, 1024, 0, st>>>(part, hchunks);
             k_radix_scatter<K, ArrayLoader<K>><<<(unsigned)nb, SORT_THREADS, 0, st>>>(
-                al, k[out], v[out], n, per, shift, hist, (int)nb);
+                al, k[out], v[out], n, per, shift, hist, part, (int)nb);
         }
-        if (launches) *launches += 3;
+        if (launches) *launches += 4;
         cur = out;
     }
     return cur;

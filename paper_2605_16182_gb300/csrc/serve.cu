@@ -272,7 +272,7 @@ int tempest_walks_batch(tempest_t *h, const tempest_walk_request *reqs, int n_re
     if ((rc = prepare_walk_index(h))) return rc;
     rc = walks_multi_launch(h, h->in_stage.as<ReqDesc>(), n, total, h->wcnt.as<WalkCounters>(), h->stream);
     h->last_ws.n_walks = total;
-    h->last_ws.launches = 2;
+    h->last_ws.launches = 1;
     return rc;
 }
 

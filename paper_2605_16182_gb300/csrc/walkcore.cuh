@@ -86,7 +86,7 @@ __device__ __forceinline__ int32_t upper_bound_ts(const int64_t *__restrict__ gt
 // later, so for tlo <= t < thi the first group later than t lies in
 // [table[k], table[k + 1]], k = bucket(t).
 constexpr int32_t BKT_MIN_G = 32;
-constexpr int32_t BKT_CHUNK = 256;  // groups per table-fill task
+constexpr int32_t BKT_CHUNK = 1024;  // groups per table-fill task
 
 __device__ __forceinline__ uint32_t bkt_count(int32_t G, int log_b) { return (uint32_t)(G >> log_b); }
 

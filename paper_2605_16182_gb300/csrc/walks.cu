@@ -187,6 +187,7 @@ struct OneReq {
     __device__ __forceinline__ int32_t *nrow(const Ctx &c) const { return O.node + c.w * (int64_t)O.cap; }
     __device__ __forceinline__ int64_t *trow(const Ctx &c) const { return O.ts + c.w * (int64_t)O.cap; }
     __device__ __forceinline__ void finish(const Ctx &c, int32_t len) const { O.len[c.w] = len; }
+    __device__ __forceinline__ int32_t cap(const Ctx &) const { return O.cap; }
     __device__ __forceinline__ WalkCounters *cnt() const { return O.cnt; }
 };
 
@@ -235,6 +236,7 @@ struct ManyReq {
         return reqs[c.r].ts + c.w * (int64_t)reqs[c.r].cap;
     }
     __device__ __forceinline__ void finish(const Ctx &c, int32_t len) const { reqs[c.r].len[c.w] = len; }
+    __device__ __forceinline__ int32_t cap(const Ctx &c) const { return reqs[c.r].cap; }
     __device__ __forceinline__ WalkCounters *cnt() const { return counters; }
 };
 
@@ -485,9 +487,33 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
             }
             s.state = S_PICK2;
         }
-        if (finish) {
-            Pv.finish(cx, s.len);
-            s.state = S_FETCH;
+        // rows of the walks that ended here: the whole warp writes their
+        // padding (node -1, ts INT64_MIN up to the row end), 32 consecutive
+        // cells per store, while the row's head is still in L2
+        unsigned fin = __ballot_sync(0xffffffffu, finish);
+        if (fin) {
+            unsigned long long my_n = 0, my_t = 0;
+            int32_t my_len = 0, my_cap = 0;
+            if (finish) {
+                Pv.finish(cx, s.len);
+                my_n = (unsigned long long)Pv.nrow(cx);
+                my_t = (unsigned long long)Pv.trow(cx);
+                my_len = s.len;
+                my_cap = Pv.cap(cx);
+                s.state = S_FETCH;
+            }
+            while (fin) {
+                const int src = __ffs(fin) - 1;
+                fin &= fin - 1;
+                int32_t *nr = reinterpret_cast<int32_t *>(__shfl_sync(0xffffffffu, my_n, src));
+                int64_t *tr = reinterpret_cast<int64_t *>(__shfl_sync(0xffffffffu, my_t, src));
+                const int32_t l = __shfl_sync(0xffffffffu, my_len, src);
+                const int32_t cp = __shfl_sync(0xffffffffu, my_cap, src);
+                for (int32_t i = l + lane; i < cp; i += 32) {
+                    nr[i] = -1;
+                    tr[i] = INT64_MIN;
+                }
+            }
         }
     }
     hops = warp_sum(hops);
@@ -541,38 +567,6 @@ __global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_pad_rows_multi(const ReqDesc *__restrict__ reqs, int n_req, int64_t total,
-                                                        WalkCounters *cnt)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
-        int lo = 0, hi = n_req - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (reqs[mid].offset <= g) lo = mid;
-            else hi = mid - 1;
-        }
-        const ReqDesc &q = reqs[lo];
-        const int64_t w = g - q.offset;
-        if (w < 0 || w >= q.n_walks) {
-            if (lane == 0) atomicOr(&cnt->status, 1ull << 9);
-            continue;
-        }
-        const int32_t l = q.len[w];
-        if (l < 0 || l > q.cap) {
-            if (lane == 0) atomicOr(&cnt->status, 1ull << 10);
-            continue;
-        }
-        int32_t *nr = q.node + w * (int64_t)q.cap;
-        int64_t *tr = q.ts + w * (int64_t)q.cap;
-        for (int32_t i = l + lane; i < q.cap; i += 32) {
-            nr[i] = -1;
-            tr[i] = INT64_MIN;
-        }
-    }
-}
-
 // Events bracketing the walk kernels of a call (created on first use).
 static void kernel_mark(tempest_t *h, int which)
 {
@@ -600,10 +594,6 @@ int walks_multi_launch(tempest_t *h, const ReqDesc *dev_reqs, int n_req, int64_t
     if (mark) kernel_mark(h, 0);
     k_walks_stream<ManyReq><<<(unsigned)grid, 256, 0, st>>>(V, ManyReq{dev_reqs, n_req, total, cnt}, &cnt->pad);
     if (mark) kernel_mark(h, 1);
-    int64_t pgrid = (total + 7) / 8;
-    const int64_t pcap = (int64_t)h->num_sms * 16;
-    if (pgrid > pcap) pgrid = pcap;
-    k_pad_rows_multi<<<(unsigned)pgrid, 256, 0, st>>>(dev_reqs, n_req, total, cnt);
     return cuda_check(h, cudaGetLastError(), "walks multi");
 }
 
@@ -711,11 +701,7 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
             kernel_mark(h, 0);
             k_walks_stream<OneReq><<<(unsigned)grid, 256, 0, st>>>(V, OneReq{O}, &O.cnt->pad);
             kernel_mark(h, 1);
-            int64_t pgrid = (rq.n_walks + 7) / 8;
-            const int64_t pcap = (int64_t)h->num_sms * 16;
-            if (pgrid > pcap) pgrid = pcap;
-            k_pad_rows<<<(unsigned)pgrid, 256, 0, st>>>(rq.n_walks, rq.cap, rq.len, rq.node, rq.ts);
-            launches += 2;
+            launches += 1;  // the walker pads its rows itself
         }
     }
     h->last_ws.n_walks = rq.n_walks;
