@@ -105,10 +105,11 @@ struct tempest {
     tw::DBuf st_src[2], st_dst[2], st_ts[2];
     int cur = 0;
     int64_t s_lo = 0, s_hi = 0, s_cap = 0, s_base = 0;
-    // timestamp-grouped view: start index of every group, live groups
-    // [tg_lo, tg_hi) with tg[tg_hi] = s_hi; the first live group may start
-    // before s_lo (its evicted part is skipped on read)
-    tw::DBuf tg;  // int32, capacity s_cap + 1
+    // timestamp-grouped view: absolute store position (modulo 2^32) of the
+    // start of every group, live groups [tg_lo, tg_hi) with tg[tg_hi] the
+    // absolute end; the first live group may start before the head (its
+    // evicted part is skipped on read)
+    tw::DBuf tg, tg2;  // int32; tg2 receives tg when it moves to a larger buffer
     int64_t tg_lo = 0, tg_hi = 0;
     // node view in a slack layout: every node with entries owns a region of
     // the entry pool and one of the group pools, with room to grow; the
@@ -119,6 +120,7 @@ struct tempest {
     tw::DBuf ngts;  // int64 group timestamp
     tw::DBuf ngr;   // int2 [N+1]: live groups of each node
     tw::DBuf nrec;  // int4 [N+1]: entries [x, y), entry region end z, group region end w
+    tw::DBuf nbeg;  // int2 [N+1]: entry region begin x, group region begin y
     tw::DBuf act;   // int32: nodes that own regions
     tw::DBuf nvc;   // device counters of the node view (NvCounters)
     int64_t n_act = 0;

@@ -214,10 +214,13 @@ __global__ void k_merge(const int32_t *__restrict__ as, const int32_t *__restric
 // ---------------------------------------------------------------------------
 // Group starts among the store indices [lo, lo + n) of ts: a group opens
 // where the timestamp differs from the previous edge's, and at index first
-// (the live head).  Starts are written densely from tg.
+// (the live head).  Starts are written densely from tg as absolute store
+// positions modulo 2^32 (abs0 is the absolute position of index 0), so a
+// move of the store's live range does not change them.
 struct TsGroupOp {
     const int64_t *ts;
     int64_t lo, first;
+    uint32_t abs0;
     int32_t *tg;
     __device__ __forceinline__ uint64_t value(int64_t i) const
     {
@@ -226,25 +229,26 @@ struct TsGroupOp {
     }
     __device__ __forceinline__ void emit(int64_t i, uint64_t v, uint64_t ex) const
     {
-        if (v) tg[ex] = (int32_t)(lo + i);
+        if (v) tg[ex] = (int32_t)(abs0 + (uint32_t)(lo + i));
     }
 };
 
-// First live group after the head moved to s_lo: the first g in [lo, hi)
-// whose successor starts after s_lo (tg[hi] is the old tail), else hi.
-__global__ void k_ts_evict(const int32_t *__restrict__ tg, int64_t lo, int64_t hi, int64_t s_lo, IngestScratch *o)
+// First live group after the head moved to absolute position s_lo: the first
+// g in [lo, hi) whose successor starts after s_lo (tg[hi] is the old tail),
+// else hi.  Positions compare modulo 2^32 (the live span is below 2^31).
+__global__ void k_ts_evict(const int32_t *__restrict__ tg, int64_t lo, int64_t hi, uint32_t s_lo, IngestScratch *o)
 {
     while (lo < hi) {
         const int64_t mid = lo + ((hi - lo) >> 1);
-        if (tg[mid + 1] > s_lo) hi = mid;
+        if ((int32_t)((uint32_t)tg[mid + 1] - s_lo) > 0) hi = mid;
         else lo = mid + 1;
     }
     o->tg_lo = lo;
 }
 
 // After a compaction of n appended starts written from tg + base: the tail
-// entry and the count.
-__global__ void k_ts_tail(int32_t *tg, int64_t base, const uint64_t *tot, int64_t s_hi, IngestScratch *o)
+// entry (absolute end of the store) and the count.
+__global__ void k_ts_tail(int32_t *tg, int64_t base, const uint64_t *tot, uint32_t s_hi, IngestScratch *o)
 {
     const uint64_t n = *tot;
     tg[base + (int64_t)n] = (int32_t)s_hi;
@@ -267,33 +271,35 @@ static int bits_for(uint64_t maxval)
     return b;
 }
 
+static uint32_t abs32(const tempest_t *h, int64_t idx) { return (uint32_t)(uint64_t)(h->s_base + idx); }
+
 // Timestamp view over the whole live range of buffer cur.
 static int ts_view_build(tempest_t *h)
 {
     cudaStream_t st = h->stream;
     const int64_t m = h->s_hi - h->s_lo;
     int rc;
-    if ((rc = ensure(h, h->tg, sizeof(int32_t) * (size_t)(h->s_cap + 2)))) return rc;
+    if ((rc = ensure(h, h->tg, sizeof(int32_t) * (size_t)(2 * m + 1024), true))) return rc;
     IngestScratch *ds = h->dstat.as<IngestScratch>();
-    TsGroupOp op{h->st_ts[h->cur].as<int64_t>(), h->s_lo, h->s_lo, h->tg.as<int32_t>()};
+    TsGroupOp op{h->st_ts[h->cur].as<int64_t>(), h->s_lo, h->s_lo, abs32(h, 0), h->tg.as<int32_t>()};
     const int nb = scan_launch(op, m, h->partials.as<uint64_t>(), st);
-    k_ts_tail<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), 0, h->partials.as<uint64_t>() + nb, h->s_hi, ds);
+    k_ts_tail<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), 0, h->partials.as<uint64_t>() + nb, abs32(h, h->s_hi), ds);
     h->pending_launches += 4;
     h->tg_lo = 0;
     h->tg_hi = -1;  // known after the batch's final read-back (tg_added)
     return cuda_check(h, cudaGetLastError(), "ts view");
 }
 
-__global__ void k_ts_export(const int32_t *__restrict__ tg, int64_t G, int64_t s_lo, int64_t m, int32_t *out)
+__global__ void k_ts_export(const int32_t *__restrict__ tg, int64_t G, uint32_t s_lo, int64_t m, int32_t *out)
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += (int64_t)gridDim.x * blockDim.x)
-        out[g] = g < G ? (int32_t)(max((int64_t)tg[g], s_lo) - s_lo) : (int32_t)m;
+        out[g] = g < G ? max((int32_t)((uint32_t)tg[g] - s_lo), 0) : (int32_t)m;
 }
 
 int ts_export(tempest_t *h, int32_t *out)
 {
-    k_ts_export<<<grid_for(h, h->G + 1), 256, 0, h->stream>>>(h->tg.as<int32_t>() + h->tg_lo, h->G, h->s_lo, h->m,
-                                                              out);
+    k_ts_export<<<grid_for(h, h->G + 1), 256, 0, h->stream>>>(h->tg.as<int32_t>() + h->tg_lo, h->G,
+                                                              abs32(h, h->s_lo), h->m, out);
     return cuda_check(h, cudaGetLastError(), "export");
 }
 
@@ -413,10 +419,10 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
         if (h->s_hi + nbk > h->s_cap) {
             // move the kept range to the front of the other buffer
             const int nxt = h->cur ^ 1;
-            const int64_t cap = std::max<int64_t>(h->s_cap, 2 * m_new + 1024);
-            if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
-            if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
-            if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap))) return rc;
+            const int64_t cap = std::max<int64_t>(h->s_cap, 2 * m_new + m_new / 2 + nbk + 1024);
+            if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
+            if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
+            if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap, true))) return rc;
             if (na > 0) {
                 const int64_t a = h->s_lo + i0;
                 cudaMemcpyAsync(h->st_src[nxt].p, h->st_src[h->cur].as<int32_t>() + a, sizeof(int32_t) * (size_t)na,
@@ -432,7 +438,6 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
                                  (int64_t)(h->st_ts[nxt].bytes / 8)});
             h->s_lo = 0;
             h->s_hi = na;
-            ts_full = true;
         } else {
             h->s_lo += i0;
         }
@@ -479,14 +484,24 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     h->cutoff = hs->cut;
 
     // 5. timestamp view
-    if (h->tg.bytes < sizeof(int32_t) * (size_t)(h->s_cap + 2)) ts_full = true;
+    if (!ts_full && (int64_t)(h->tg.bytes / sizeof(int32_t)) < h->tg_hi + nbk + 2) {
+        // move the live starts [tg_lo, tg_hi] to the front of a larger buffer
+        const int64_t live = h->tg_hi - h->tg_lo + 1;
+        if ((rc = ensure(h, h->tg2, sizeof(int32_t) * (size_t)(2 * (live + nbk) + 1024), true))) return rc;
+        cudaMemcpyAsync(h->tg2.p, h->tg.as<int32_t>() + h->tg_lo, sizeof(int32_t) * (size_t)live,
+                        cudaMemcpyDeviceToDevice, st);
+        std::swap(h->tg, h->tg2);
+        h->tg_hi -= h->tg_lo;
+        h->tg_lo = 0;
+    }
     if (ts_full) {
         if ((rc = ts_view_build(h))) return rc;
     } else {
-        k_ts_evict<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), h->tg_lo, h->tg_hi, h->s_lo, ds);
-        TsGroupOp op{h->st_ts[h->cur].as<int64_t>(), new_lo, h->s_lo, h->tg.as<int32_t>() + h->tg_hi};
+        k_ts_evict<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), h->tg_lo, h->tg_hi, abs32(h, h->s_lo), ds);
+        TsGroupOp op{h->st_ts[h->cur].as<int64_t>(), new_lo, h->s_lo, abs32(h, 0), h->tg.as<int32_t>() + h->tg_hi};
         const int nbl = scan_launch(op, nbk, h->partials.as<uint64_t>(), st);
-        k_ts_tail<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), h->tg_hi, h->partials.as<uint64_t>() + nbl, h->s_hi, ds);
+        k_ts_tail<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), h->tg_hi, h->partials.as<uint64_t>() + nbl,
+                                   abs32(h, h->s_hi), ds);
         h->pending_launches += 5;
     }
 

@@ -24,7 +24,11 @@
 //      otherwise takes fresh regions from the pools' bump pointers and queues
 //      a move of the node's live entries and groups;
 //   4. the moves run as chunked copies (group starts rebased), then the batch
-//      entries and new groups are scattered into place.
+//      entries, new groups and each node's closing group slot are scattered
+//      into place.  A node whose regions have no room at the end but whose
+//      evicted front can hold its live items moves back to the front of its
+//      own regions (a sliding window's steady state), otherwise it takes fresh
+//      regions from the pools.
 // Nothing reads or writes the parts of the view the batch does not touch.  A
 // pool that runs out, a batch that merges into the middle of the store, or
 // the first batch rebuild the whole view from the store (the same compaction
@@ -127,7 +131,7 @@ __global__ void k_nv_tail(int32_t *run_pos, int32_t *run_g, int32_t *fx, const u
 __global__ void k_nv_build_nodes(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
                                  const int32_t *__restrict__ run_g, const int32_t *__restrict__ run_de,
                                  const int32_t *__restrict__ run_dg, int64_t S, int shift, int4 *nrec, int2 *ngr,
-                                 int32_t *ngo, int32_t *act)
+                                 int2 *nbeg, int32_t *ngo, int32_t *act)
 {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < S; r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = run_node[r];
@@ -135,6 +139,7 @@ __global__ void k_nv_build_nodes(const int32_t *__restrict__ run_node, const int
         const int32_t eb = run_de[r], gb = run_dg[r];
         nrec[v] = make_int4(eb, eb + c, eb + (int32_t)region_cap(c, shift), gb + (int32_t)region_cap(gc, shift) + 1);
         ngr[v] = make_int2(gb, gb + gc);
+        nbeg[v] = make_int2(eb, gb);
         ngo[gb + gc] = eb + c;
         act[r] = v;
     }
@@ -312,11 +317,15 @@ struct AppendRunOp {
     }
 };
 
-// One thread per node run: room in place, or fresh regions and a move.
+// One thread per node run: room in place; else, when the evicted front of
+// the node's own regions can take its live items without overlapping them, a
+// move back to the regions' start (a sliding window's steady state: no pool
+// space is used); else fresh regions from the pools and a move.
 __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
                              const int32_t *__restrict__ run_g, const uint64_t *__restrict__ tot, int shift,
-                             int64_t e_cap, int64_t g_cap, int4 *nrec, int2 *ngr, int32_t *ngo, int32_t *act,
-                             int64_t act_cap, Reloc *reloc, int32_t *run_de, int32_t *run_dg, NvCounters *c)
+                             int64_t e_cap, int64_t g_cap, int4 *nrec, int2 *ngr, int2 *nbeg, int32_t *ngo,
+                             int32_t *act, int64_t act_cap, Reloc *reloc, int32_t *run_de, int32_t *run_dg,
+                             NvCounters *c)
 {
     const int64_t R = (int64_t)(*tot >> 32);
     long long added = 0;
@@ -338,14 +347,27 @@ __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t
             d_g = g.y;
             rec.y += cnt;
         } else {
-            const int64_t ecap = region_cap((int64_t)live_e + cnt, shift);
-            const int64_t gcap = region_cap((int64_t)live_g + gc, shift) + 1;
-            const unsigned long long eb = atomicAdd(&c->e_top, (unsigned long long)ecap);
-            const unsigned long long gb = atomicAdd(&c->g_top, (unsigned long long)gcap);
-            if ((int64_t)eb + ecap > e_cap || (int64_t)gb + gcap > g_cap) {
-                atomicOr(&c->overflow, 1ull);
-                run_de[r] = -1;
-                continue;
+            const int2 beg = fresh ? make_int2(0, 0) : nbeg[v];
+            const bool slide = !fresh && rec.x - beg.x >= live_e && g.x - beg.y >= live_g &&
+                               (int64_t)live_e + cnt <= rec.z - beg.x && (int64_t)live_g + gc + 1 <= rec.w - beg.y;
+            int64_t ecap, gcap;
+            unsigned long long eb, gb;
+            if (slide) {
+                eb = (unsigned long long)beg.x;
+                gb = (unsigned long long)beg.y;
+                ecap = rec.z - beg.x;
+                gcap = rec.w - beg.y;
+            } else {
+                ecap = region_cap((int64_t)live_e + cnt, shift);
+                gcap = region_cap((int64_t)live_g + gc, shift) + 1;
+                eb = atomicAdd(&c->e_top, (unsigned long long)ecap);
+                gb = atomicAdd(&c->g_top, (unsigned long long)gcap);
+                if ((int64_t)eb + ecap > e_cap || (int64_t)gb + gcap > g_cap) {
+                    atomicOr(&c->overflow, 1ull);
+                    run_de[r] = -1;
+                    continue;
+                }
+                nbeg[v] = make_int2((int32_t)eb, (int32_t)gb);
             }
             if (live_e > 0 || live_g > 0) {
                 const unsigned long long t = atomicAdd(&c->n_reloc, 1ull);
@@ -359,7 +381,8 @@ __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t
         g.y = d_g + gc;
         nrec[v] = rec;
         ngr[v] = g;
-        ngo[g.y] = rec.y;
+        // the slot after the last group (= rec.y) is written with the batch's
+        // groups, after any move has read the old groups
         run_de[r] = d_e;
         run_dg[r] = d_g;
         added += gc;
@@ -431,6 +454,14 @@ __global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t
             }
             ngts[g] = x.ts;
             ngo[g] = (int32_t)e;
+        }
+        if (p + 1 == run_pos[r + 1]) {  // the node's new end after its last group
+            const int64_t gs = (int64_t)run_dg[r] + (run_g[r + 1] - run_g[r]);
+            if (gs < 0 || gs >= g_cap) {
+                atomicOr(&c->status, 1ull << 5);
+                continue;
+            }
+            ngo[gs] = (int32_t)(e + 1);
         }
     }
 }
@@ -542,7 +573,8 @@ int grow_keep(tempest_t *h, DBuf &b, size_t used, size_t bytes)
 int nv_ensure_nodes(tempest_t *h, int64_t N)
 {
     const int64_t need = N + 1;
-    if (need <= h->nrec_n && h->ngr.p && h->nrec.p && h->ev.p && h->act.p && h->dense.p) return TEMPEST_OK;
+    if (need <= h->nrec_n && h->ngr.p && h->nrec.p && h->ev.p && h->act.p && h->dense.p && h->nbeg.p)
+        return TEMPEST_OK;
     int rc;
     const size_t used = (size_t)h->nrec_n;
     if ((rc = grow_keep(h, h->nrec, sizeof(int4) * used, sizeof(int4) * (size_t)need))) return rc;
@@ -550,7 +582,9 @@ int nv_ensure_nodes(tempest_t *h, int64_t N)
     if ((rc = grow_keep(h, h->ev, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->act, sizeof(int32_t) * (size_t)h->n_act, sizeof(int32_t) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->dense, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
+    if ((rc = grow_keep(h, h->nbeg, sizeof(int2) * used, sizeof(int2) * (size_t)need))) return rc;
     int64_t cover = (int64_t)(h->nrec.bytes / sizeof(int4));
+    cover = std::min(cover, (int64_t)(h->nbeg.bytes / sizeof(int2)));
     cover = std::min(cover, (int64_t)(h->dense.bytes / sizeof(int32_t)));
     cover = std::min(cover, (int64_t)(h->ngr.bytes / sizeof(int2)));
     cover = std::min(cover, (int64_t)(h->ev.bytes / sizeof(int32_t)));
@@ -628,7 +662,8 @@ int nv_build(tempest_t *h)
     k_nv_build_nodes<<<grid_for(h, S), 256, 0, st>>>(h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
                                                      h->run_g.as<int32_t>(), h->run_de.as<int32_t>(),
                                                      h->run_dg.as<int32_t>(), S, shift, h->nrec.as<int4>(),
-                                                     h->ngr.as<int2>(), h->ngo.as<int32_t>(), h->act.as<int32_t>());
+                                                     h->ngr.as<int2>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
+                                                     h->act.as<int32_t>());
     k_nv_build_scatter<<<grid_for(h, M), 256, 0, st>>>(E, h->run_of.as<int32_t>(), h->fx.as<int32_t>(),
                                                        h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(),
                                                        h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(), M,
@@ -719,8 +754,9 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         k_nv_tail<<<1, 1, 0, st>>>(h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), h->fx.as<int32_t>(), tot, nbe);
         k_nv_reserve<<<grid_for(h, runs_max), 256, 0, st>>>(
             h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), tot, h->nv_shift, h->e_cap,
-            h->g_cap, h->nrec.as<int4>(), h->ngr.as<int2>(), h->ngo.as<int32_t>(), h->act.as<int32_t>(),
-            h->nrec_n, h->reloc.as<Reloc>(), h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(), dc);
+            h->g_cap, h->nrec.as<int4>(), h->ngr.as<int2>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
+            h->act.as<int32_t>(), h->nrec_n, h->reloc.as<Reloc>(), h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(),
+            dc);
         NvCounters *hc = static_cast<NvCounters *>(h->hstat);
         cudaMemcpyAsync(hc, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
         h->pending_launches += launches + 5;

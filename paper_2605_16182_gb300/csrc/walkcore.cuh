@@ -15,11 +15,12 @@ struct WalkView {
     const int32_t *st_dst;
     const int64_t *st_ts;
     int64_t m;
-    // timestamp-grouped view: group g's edges are [max(tg[g], s_lo) - s_lo,
-    // tg[g + 1] - s_lo) (store buffer indices; the head group may have lost a
-    // prefix to eviction)
+    // timestamp-grouped view: group g starts at absolute store position tg[g]
+    // (modulo 2^32) and ends where g + 1 starts; its live edges are store
+    // offsets [max(tg[g] - s_lo, 0), tg[g + 1] - s_lo) with s_lo the absolute
+    // position of the head (the head group may have lost a prefix)
     const int32_t *tg;
-    int64_t s_lo;
+    uint32_t s_lo;
     int64_t G;
     // node view: groups [ngr[v].x, ngr[v].y) of node v; group g's entries
     // [ngo[g], ngo[g + 1]) in the entry pool
@@ -38,9 +39,9 @@ struct WalkView {
 // Store range [a, b) of timestamp group g (g < G).
 __device__ __forceinline__ void ts_group_range(const WalkView &V, int64_t g, int64_t &a, int64_t &b)
 {
-    const int64_t x = __ldg(V.tg + g);
-    a = (x > V.s_lo ? x : V.s_lo) - V.s_lo;
-    b = (int64_t)__ldg(V.tg + g + 1) - V.s_lo;
+    const int32_t x = (int32_t)((uint32_t)__ldg(V.tg + g) - V.s_lo);
+    a = x > 0 ? x : 0;
+    b = (int32_t)((uint32_t)__ldg(V.tg + g + 1) - V.s_lo);
 }
 
 struct WalkOut {

@@ -321,8 +321,9 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 break;
             }
             case S_SGROUP: {
-                const int64_t a = ((int64_t)z0 > V.s_lo ? (int64_t)z0 : V.s_lo) - V.s_lo;
-                const int64_t k = a + uniform_index_k(s.ud, (int64_t)z1 - V.s_lo - a);
+                const int32_t x = (int32_t)((uint32_t)z0 - V.s_lo);
+                const int64_t a = x > 0 ? x : 0;
+                const int64_t k = a + uniform_index_k(s.ud, (int64_t)(int32_t)((uint32_t)z1 - V.s_lo) - a);
                 y0 = __ldg(V.st_ts + k);
                 z0 = __ldg(V.st_src + k);
                 z1 = __ldg(V.st_dst + k);
@@ -628,7 +629,7 @@ WalkView make_view(tempest_t *h)
     V.st_ts = h->st_ts[h->cur].as<int64_t>() + h->s_lo;
     V.m = h->m;
     V.tg = h->tg.as<int32_t>() + h->tg_lo;
-    V.s_lo = h->s_lo;
+    V.s_lo = (uint32_t)(uint64_t)(h->s_base + h->s_lo);
     V.G = h->G;
     V.ngr = h->ngr.as<int2>();
     V.ngo = h->ngo.as<int32_t>();
