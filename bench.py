@@ -396,7 +396,19 @@ def run_batched(args):
         ws = eng.last_walk_stats()
         results[name] = {"ms_per_call": ms, "hops": ws["hops"], "launches_per_call": ws["launches"],
                          "hops_per_s": ws["hops"] / (ms / 1e3)}
+    # autotuned: the tuner times candidate forms and knobs on a tenth of the
+    # workload (outside the timing), then the whole call runs with its choice
+    nt = max(1000, n_walks // 10)
+    tune = eng.autotune_mixed(L[:nt], bias[:nt], max_len_cap=cap, seed=99, forms=True)
+    ms = timed(lambda k: eng.walks_mixed(L, bias, seed=k, max_len_cap=cap, out=(node, tso, ln)))
+    ws = eng.last_walk_stats()
+    results["autotuned"] = {"ms_per_call": ms, "hops": ws["hops"], "launches_per_call": ws["launches"],
+                            "hops_per_s": ws["hops"] / (ms / 1e3),
+                            "choice": {k: tune[k] for k in ("sched", "bkt_log", "coop_w_warp", "coop_mega",
+                                                             "stream_ctas")}}
     eng.set_scheduler(_lib.SCHED_STREAM)
+    eng.set_tuning(_lib.TUNE_BKT_LOG, 2)
+    eng.set_tuning(_lib.TUNE_STREAM_CTAS, 0)
 
     def per_batch(k):
         for b0 in range(0, n_walks, batch):
@@ -406,7 +418,7 @@ def run_batched(args):
     ms = timed(per_batch)
     hops = int((ln.to(torch.int64) - 1).clamp(min=0).sum().item())
     results["per_batch_stream"] = {"ms_per_call": ms, "hops": hops,
-                                   "launches_per_call": 2 * ((n_walks + batch - 1) // batch),
+                                   "launches_per_call": (n_walks + batch - 1) // batch,
                                    "hops_per_s": hops / (ms / 1e3), "batch_walks": batch}
     best = max(results, key=lambda k: results[k]["hops_per_s"])
     out = {"metric": METRIC, "value": results["stream"]["hops_per_s"], "unit": "hops/s", "n_gpus": 1,

@@ -290,6 +290,13 @@ typedef struct {
 int tempest_autotune(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy, uint64_t seed,
                      int32_t flags, tempest_tune_report *out);
 
+/* The same, timing tempest_walks_mixed calls on the caller's own per-walk
+ * lengths and biases (device arrays of n_walks, as in tempest_walks_mixed),
+ * so a mixed workload is tuned on its own mix. */
+int tempest_autotune_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_arr, int32_t max_len_cap,
+                           const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t flags,
+                           tempest_tune_report *out);
+
 /* Report of the most recent walk call; waits for its work to finish. */
 int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out);
 

@@ -41,7 +41,7 @@ EXPORTED = (
     "tempest_server_create", "tempest_server_destroy", "tempest_server_submit_walks",
     "tempest_server_submit_ingest", "tempest_server_progress", "tempest_server_status",
     "tempest_server_release", "tempest_server_drain", "tempest_server_stats",
-    "tempest_set_tuning", "tempest_get_tuning", "tempest_autotune",
+    "tempest_set_tuning", "tempest_get_tuning", "tempest_autotune", "tempest_autotune_mixed",
 )
 NOALLOC_MAX_EDGES = 262144
 
@@ -135,6 +135,8 @@ def load():
     L.tempest_get_tuning.argtypes = [vp, ci, ctypes.POINTER(i64)]
     L.tempest_autotune.argtypes = [vp, i64, ctypes.c_int32, ci, ci, ctypes.c_uint64, ctypes.c_int32,
                                    ctypes.POINTER(TuneReport)]
+    L.tempest_autotune_mixed.argtypes = [vp, i64, vp, ctypes.c_int32, vp, ci, ctypes.c_uint64, ctypes.c_int32,
+                                         ctypes.POINTER(TuneReport)]
     L.tempest_last_walk_stats.argtypes = [vp, ctypes.POINTER(WalkStats)]
     L.tempest_get_counts.argtypes = [vp, vp]
     L.tempest_export_state.argtypes = [vp, ci, vp, i64, ctypes.POINTER(i64)]
@@ -332,6 +334,14 @@ def tempest_get_tuning(h, knob: int) -> int:
     return v.value
 
 
+def tempest_autotune_mixed(h, n_walks, max_len_arr, max_len_cap, bias_arr, start_policy, seed, flags) -> TuneReport:
+    rep = TuneReport()
+    _check(h, load().tempest_autotune_mixed(h, int(n_walks), max_len_arr, int(max_len_cap), bias_arr,
+                                            int(start_policy), int(seed) & ((1 << 64) - 1), int(flags),
+                                            ctypes.byref(rep)))
+    return rep
+
+
 def tempest_autotune(h, n_walks, max_len, bias, start_policy, seed, flags) -> TuneReport:
     rep = TuneReport()
     _check(h, load().tempest_autotune(h, int(n_walks), int(max_len), int(bias), int(start_policy),
@@ -462,6 +472,14 @@ class Engine:
         """Time candidate settings on the live index and keep the fastest."""
         return tempest_autotune(self.h, n_walks, max_len, bias, start_policy, seed,
                                 TUNE_FORMS if forms else 0).as_dict()
+
+    def autotune_mixed(self, max_len_arr, bias_arr, max_len_cap=None, start_policy=0, seed=0, forms=True) -> dict:
+        """Autotune on a mixed request's own per-walk lengths and biases."""
+        n = int(max_len_arr.shape[0])
+        assert bias_arr.shape[0] == n
+        cap = int(max_len_cap) if max_len_cap is not None else int(max_len_arr.max().item())
+        return tempest_autotune_mixed(self.h, n, _ptr(max_len_arr, "int32"), cap, _ptr(bias_arr, "uint8"),
+                                      start_policy, seed, TUNE_FORMS if forms else 0).as_dict()
 
     def ingest(self, src, dst, ts) -> dict:
         n = int(src.shape[0])

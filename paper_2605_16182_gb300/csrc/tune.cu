@@ -137,13 +137,37 @@ int tempest_get_tuning(tempest_t *h, int knob, int64_t *value)
     }
 }
 
+static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const int32_t *len_arr, int bias,
+                         const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t flags,
+                         tempest_tune_report *out);
+
 int tempest_autotune(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy, uint64_t seed,
                      int32_t flags, tempest_tune_report *out)
 {
     if (!h) return TEMPEST_EINVAL;
-    if (n_walks < 1 || max_len < 2 || bias < 0 || bias > 2 ||
+    if (bias < 0 || bias > 2) return fail(h, TEMPEST_EINVAL, "tempest_autotune: unknown bias %d", bias);
+    return autotune_impl(h, n_walks, max_len, nullptr, bias, nullptr, start_policy, seed, flags, out);
+}
+
+int tempest_autotune_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_arr, int32_t max_len_cap,
+                           const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t flags,
+                           tempest_tune_report *out)
+{
+    if (!h) return TEMPEST_EINVAL;
+    if (!max_len_arr || !bias_arr || !is_device_ptr(max_len_arr) || !is_device_ptr(bias_arr))
+        return fail(h, TEMPEST_EINVAL, "tempest_autotune_mixed: per-walk arrays must be device memory");
+    return autotune_impl(h, n_walks, max_len_cap, max_len_arr, 0, bias_arr, start_policy, seed, flags, out);
+}
+
+}  // extern "C"
+
+static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const int32_t *len_arr, int bias,
+                         const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t flags,
+                         tempest_tune_report *out)
+{
+    if (n_walks < 1 || max_len < 2 ||
         (start_policy != TEMPEST_START_UNIFORM_EDGE && start_policy != TEMPEST_START_BIASED_TS))
-        return fail(h, TEMPEST_EINVAL, "tempest_autotune: bad n_walks, max_len, bias or start policy");
+        return fail(h, TEMPEST_EINVAL, "tempest_autotune: bad n_walks, max_len or start policy");
     if ((flags & ~TEMPEST_TUNE_FORMS) != 0) return fail(h, TEMPEST_EINVAL, "tempest_autotune: unknown flags");
     if (n_walks > (int64_t)INT32_MAX / 2) return fail(h, TEMPEST_EINVAL, "tempest_autotune: n_walks too large");
     int rc;
@@ -157,9 +181,9 @@ int tempest_autotune(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, i
     T.rq.n_walks = n_walks;
     T.rq.cap = max_len;
     T.rq.max_len = max_len;
-    T.rq.len_arr = nullptr;
+    T.rq.len_arr = len_arr;
     T.rq.bias = bias;
-    T.rq.bias_arr = nullptr;
+    T.rq.bias_arr = bias_arr;
     T.rq.start_policy = start_policy;
     T.rq.seed = seed;
     T.rq.ts = reinterpret_cast<int64_t *>(base);
@@ -208,5 +232,3 @@ int tempest_autotune(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, i
     }
     return TEMPEST_OK;
 }
-
-}  // extern "C"

@@ -64,3 +64,18 @@ def test_autotune_reports_and_keeps_its_choice():
     assert all(torch.equal(x, y) for x, y in zip(ref, got))
     with pytest.raises(_lib.TempestError):
         eng.autotune(0, 30)
+
+
+def test_autotune_on_a_mixed_request():
+    eng = _engine()
+    g = torch.Generator().manual_seed(3)
+    n = 30000
+    lens = torch.randint(2, 41, (n,), generator=g, dtype=torch.int32).cuda()
+    bias = torch.randint(0, 3, (n,), generator=g, dtype=torch.int32).to(torch.uint8).cuda()
+    ref = [x.clone() for x in eng.walks_mixed(lens, bias, seed=8, max_len_cap=40)]
+    rep = eng.autotune_mixed(lens, bias, max_len_cap=40, seed=2)
+    assert len(rep["trials"]) >= 8 and rep["best_ms"] == min(t["ms"] for t in rep["trials"])
+    got = eng.walks_mixed(lens, bias, seed=8, max_len_cap=40)
+    assert all(torch.equal(x, y) for x, y in zip(ref, got))
+    with pytest.raises(_lib.TempestError):
+        eng.autotune_mixed(lens.cpu(), bias.cpu(), max_len_cap=40)
