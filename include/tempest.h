@@ -257,7 +257,9 @@ enum {
      * (Sec. 2.4.4), 256..2^30; default 8192 */
     TEMPEST_TUNE_COOP_MEGA = 2,
     /* TEMPEST_SCHED_STREAM: resident 256-thread CTAs per SM of the persistent
-     * walker, 0 = as many as fit; 0..16; default 0 */
+     * walker, 0 = as many as fit; values above 4 select a build with a
+     * smaller register budget (more warps in flight, a few spills); 0..16;
+     * default 0 */
     TEMPEST_TUNE_STREAM_CTAS = 3
 };
 /* Set / read one knob.  EINVAL on an unknown knob or a value out of range. */

@@ -33,13 +33,13 @@ constexpr int BKT_UNROLL = 4;  // 32-group steps whose loads are issued together
 
 struct BigNodeOp {
     const int32_t *act;
-    const int2 *ngr;
+    NodeRange *ngr;
     int log_b;
-    int32_t *big_node, *big_t, *bkt_base;
+    int32_t *big_node, *big_t;
     __device__ __forceinline__ uint64_t value(int64_t j) const
     {
-        const int2 g = ngr[act[j]];
-        const int32_t G = g.y - g.x;
+        const NodeRange &r = ngr[act[j]];
+        const int32_t G = r.g_hi - r.g_lo;
         if (G < BKT_MIN_G) return 0;
         return (1ull << 32) | (uint64_t)(bkt_count(G, log_b) + 1u);
     }
@@ -50,18 +50,18 @@ struct BigNodeOp {
         const int32_t node = act[j];
         big_node[b] = node;
         big_t[b] = (int32_t)(uint32_t)ex;
-        bkt_base[node] = (int32_t)(uint32_t)ex;
+        ngr[node].tb = (int32_t)(uint32_t)ex;
     }
 };
 
 struct ChunkOp {
     const int32_t *big_node;
-    const int2 *ngr;
+    const NodeRange *ngr;
     int32_t *big_c;
     __device__ __forceinline__ uint64_t value(int64_t b) const
     {
-        const int2 g = ngr[big_node[b]];
-        return (uint64_t)((g.y - g.x + BKT_CHUNK - 1) / BKT_CHUNK);
+        const NodeRange &r = ngr[big_node[b]];
+        return (uint64_t)((r.g_hi - r.g_lo + BKT_CHUNK - 1) / BKT_CHUNK);
     }
     __device__ __forceinline__ void emit(int64_t b, uint64_t, uint64_t ex) const { big_c[b] = (int32_t)ex; }
 };
@@ -70,7 +70,8 @@ struct ChunkOp {
 __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ big_node,
                                                   const int32_t *__restrict__ big_t,
                                                   const int32_t *__restrict__ big_c, int64_t nb,
-                                                  const uint64_t *__restrict__ tot, const int2 *__restrict__ ngr,
+                                                  const uint64_t *__restrict__ tot,
+                                                  const NodeRange *__restrict__ ngr,
                                                   const int64_t *__restrict__ ngts, int log_b, int64_t cap,
                                                   int32_t *bkt, WalkCounters *chk)
 {
@@ -86,8 +87,8 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
             else hi = mid - 1;
         }
         const int64_t b = lo;
-        const int2 gr = __ldg(ngr + __ldg(big_node + b));
-        const int32_t g0 = gr.x, g1 = gr.y;
+        const int32_t node = __ldg(big_node + b);
+        const int32_t g0 = ngr[node].g_lo, g1 = ngr[node].g_hi;
         const uint32_t K = bkt_count(g1 - g0, log_b);
         const int64_t tb = __ldg(big_t + b);
         if (tb + K >= cap || g1 - g0 < BKT_MIN_G) {  // inconsistent lists
@@ -155,21 +156,19 @@ int prepare_walk_index(tempest_t *h)
 {
     if (h->bkt_ver == h->state_ver) return TEMPEST_OK;
     cudaStream_t st = h->stream;
-    const int64_t S = h->n_act, Gn = h->Gn, N = h->N;
+    const int64_t S = h->n_act, Gn = h->Gn;
     int rc;
     h->n_big = 0;
     if (S > 0 && Gn >= BKT_MIN_G) {
         const size_t Sz = (size_t)S;
-        if ((rc = ensure(h, h->bkt_base, sizeof(int32_t) * (size_t)(N + 1), true))) return rc;
         if ((rc = ensure(h, h->big_node, sizeof(int32_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->big_t, sizeof(int32_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->big_c, sizeof(int32_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
         if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
         uint64_t *part = h->partials.as<uint64_t>();
-        const int2 *ngr = h->ngr.as<int2>();
-        BigNodeOp op{h->act.as<int32_t>(), ngr, h->bkt_log, h->big_node.as<int32_t>(), h->big_t.as<int32_t>(),
-                     h->bkt_base.as<int32_t>()};
+        NodeRange *ngr = h->ngr.as<NodeRange>();
+        BigNodeOp op{h->act.as<int32_t>(), ngr, h->bkt_log, h->big_node.as<int32_t>(), h->big_t.as<int32_t>()};
         const int nblk = scan_launch(op, S, part, st);
         uint64_t *hp = static_cast<uint64_t *>(h->hstat);
         cudaMemcpyAsync(hp, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);

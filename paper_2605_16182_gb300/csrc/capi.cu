@@ -112,7 +112,7 @@ static void free_all(tempest_t *h)
                     &h->sb_ts,     &h->sk64[0],   &h->sk64[1],   &h->sk32[0],   &h->sk32[1],   &h->sv[0],
                     &h->sv[1],     &h->hist,      &h->partials,  &h->dstat,     &h->wcnt,      &h->out_stage,
                     &h->in_stage,  &h->exp_stage, &h->co_node,   &h->co_t,      &h->co_len,    &h->co_act[0],
-                    &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt_base,  &h->bkt,
+                    &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt,
                     &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched,   &h->tg2,       &h->nbeg};
     for (DBuf *b : bufs) release(h, *b);
 }

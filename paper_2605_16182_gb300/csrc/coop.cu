@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_coop_start(const WalkView V, const Walk
 
 __global__ void k_coop_classify(const int32_t *__restrict__ run_pos, const int32_t *__restrict__ run_node,
                                 const uint64_t *__restrict__ n_runs_ptr, int64_t n_active,
-                                const int2 *__restrict__ ngr, int w_warp, int mega, Task *tasks,
+                                const NodeRange *__restrict__ ngr, int w_warp, int mega, Task *tasks,
                                 int64_t tier_stride, unsigned int *counts)
 {
     const int64_t R = (int64_t)*n_runs_ptr;
@@ -129,8 +129,7 @@ __global__ void k_coop_classify(const int32_t *__restrict__ run_pos, const int32
         const int32_t end = (r + 1 < R) ? run_pos[r + 1] : (int32_t)n_active;
         const int32_t W = end - start;
         const int32_t v = run_node[r];
-        const int2 gr = ngr[v];
-        const int32_t G = gr.y - gr.x;
+        const int32_t G = ngr[v].g_hi - ngr[v].g_lo;
         int tier;
         if (W <= w_warp) tier = T_SOLO;
         else if (W <= COOP_BLOCK) tier = (G <= WARP_G_CAP) ? T_WARP_SMEM : T_WARP_GLOBAL;
@@ -224,8 +223,8 @@ __global__ void __launch_bounds__(256) k_coop_solo(const WalkView V, const WalkO
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const Task tk = tasks[i];
-        const int2 gr = __ldg(V.ngr + tk.node);
-        const int32_t g0 = gr.x, g1 = gr.y;
+        int32_t g0, g1;
+        node_groups(V, tk.node, g0, g1);
         for (int32_t k = 0; k < tk.count; k++) {
             const int32_t w = (int32_t)S.sorted_walks[tk.start + k];
             bool push;
@@ -251,8 +250,8 @@ __global__ void __launch_bounds__(COOP_BLOCK) k_coop_warp(const WalkView V, cons
     const unsigned ti = blockIdx.x * COOP_WARPS + wid;
     if (ti < n) {
         const Task tk = tasks[ti];
-        const int2 gr = __ldg(V.ngr + tk.node);
-        const int32_t g0 = gr.x, g1 = gr.y;
+        int32_t g0, g1;
+        node_groups(V, tk.node, g0, g1);
         int64_t *mine = SMEM ? sts + wid * WARP_G_CAP : nullptr;
         if (SMEM) {
             for (int32_t g = lane; g < g1 - g0; g += 32) mine[g] = __ldg(V.ngts + g0 + g);
@@ -281,8 +280,8 @@ __global__ void __launch_bounds__(COOP_BLOCK) k_coop_block(const WalkView V, con
     __shared__ int64_t sts[SMEM ? BLOCK_G_CAP : 1];
     unsigned long long hops = 0, bytes = 0;
     const Task tk = tasks[blockIdx.x];
-    const int2 gr = __ldg(V.ngr + tk.node);
-        const int32_t g0 = gr.x, g1 = gr.y;
+    int32_t g0, g1;
+        node_groups(V, tk.node, g0, g1);
     if (SMEM) {
         for (int32_t g = threadIdx.x; g < g1 - g0; g += blockDim.x) sts[g] = __ldg(V.ngts + g0 + g);
         __syncthreads();
@@ -321,8 +320,8 @@ __global__ void __launch_bounds__(256) k_graph_hop(const WalkView V, const WalkO
         if (i < n) {
             w = active[i];
             const int32_t v = S.ws_node[w];
-            const int2 gr = __ldg(V.ngr + v);
-            const int32_t g0 = gr.x, g1 = gr.y;
+            int32_t g0, g1;
+            node_groups(V, v, g0, g1);
             coop_hop(V, O, S, w, v, g0, g1, nullptr, hops, bytes, push);
         }
         push_active(S, push, w);

@@ -42,6 +42,17 @@ struct IngestScratch {
     unsigned long long status;  // nonzero: an index check failed (bit per site)
 };
 
+// The per-node record a hop reads first: the node's live groups [g_lo,
+// g_hi), the base of its time-bucket table (nodes with enough groups; set
+// when the tables are built), and the timestamps of its first and last live
+// groups.  32 bytes, one sector: a hop gets everything it needs before the
+// search in one round trip.
+struct __align__(32) NodeRange {
+    int32_t g_lo, g_hi;
+    int32_t tb, pad;
+    int64_t t_first, t_last;
+};
+
 // Device counters of the node-view update (one batch).
 struct NvCounters {
     unsigned long long e_top, g_top;  // pool bump pointers
@@ -118,7 +129,7 @@ struct tempest {
     tw::DBuf ent;   // Entry pool
     tw::DBuf ngo;   // int32 group start (entry pool index)
     tw::DBuf ngts;  // int64 group timestamp
-    tw::DBuf ngr;   // int2 [N+1]: live groups of each node
+    tw::DBuf ngr;   // NodeRange [N+1]
     tw::DBuf nrec;  // int4 [N+1]: entries [x, y), entry region end z, group region end w
     tw::DBuf nbeg;  // int2 [N+1]: entry region begin x, group region begin y
     tw::DBuf act;   // int32: nodes that own regions
@@ -137,8 +148,7 @@ struct tempest {
     // time buckets of high-degree nodes (built lazily for the walks of a
     // state version): per node its table base, the tables, the big-segment
     // list and its chunk prefix
-    tw::DBuf bkt_base;   // int32 [N+1]
-    tw::DBuf bkt;        // int32 tables
+    tw::DBuf bkt;        // int32 tables (each big node's base is in its NodeRange)
     tw::DBuf big_node, big_t, big_c;
     int64_t bkt_ver = -1;
     int64_t n_big = 0;

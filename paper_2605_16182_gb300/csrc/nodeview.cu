@@ -130,15 +130,22 @@ __global__ void k_nv_tail(int32_t *run_pos, int32_t *run_g, int32_t *fx, const u
 
 __global__ void k_nv_build_nodes(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
                                  const int32_t *__restrict__ run_g, const int32_t *__restrict__ run_de,
-                                 const int32_t *__restrict__ run_dg, int64_t S, int shift, int4 *nrec, int2 *ngr,
-                                 int2 *nbeg, int32_t *ngo, int32_t *act)
+                                 const int32_t *__restrict__ run_dg, const Entry *__restrict__ E, int64_t S,
+                                 int shift, int4 *nrec, NodeRange *ngr, int2 *nbeg, int32_t *ngo, int32_t *act)
 {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < S; r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = run_node[r];
         const int32_t c = run_pos[r + 1] - run_pos[r], gc = run_g[r + 1] - run_g[r];
         const int32_t eb = run_de[r], gb = run_dg[r];
         nrec[v] = make_int4(eb, eb + c, eb + (int32_t)region_cap(c, shift), gb + (int32_t)region_cap(gc, shift) + 1);
-        ngr[v] = make_int2(gb, gb + gc);
+        NodeRange x;
+        x.g_lo = gb;
+        x.g_hi = gb + gc;
+        x.tb = 0;
+        x.pad = 0;
+        x.t_first = E[run_pos[r]].ts;
+        x.t_last = E[run_pos[r + 1] - 1].ts;
+        ngr[v] = x;
         nbeg[v] = make_int2(eb, gb);
         ngo[gb + gc] = eb + c;
         act[r] = v;
@@ -188,8 +195,8 @@ __global__ void k_nv_evict_count(Items it, int64_t items, int64_t N, int32_t *ev
 }
 
 // Every node that lost entries drops them from the front of its region.
-__global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *ev, int4 *nrec, int2 *ngr,
-                                 int32_t *ngo, NvCounters *c)
+__global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *ev, int4 *nrec, NodeRange *ngr,
+                                 int32_t *ngo, const int64_t *__restrict__ ngts, NvCounters *c)
 {
     const int64_t n = (int64_t)c->n_ev_nodes;
     long long removed = 0;
@@ -198,7 +205,7 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
         const int32_t k = ev[v];
         ev[v] = 0;
         int4 r = nrec[v];
-        int2 g = ngr[v];
+        const int32_t gx = ngr[v].g_lo, gy = ngr[v].g_hi;
         int32_t e_lo = r.x + k;
         if (k <= 0 || e_lo > r.y) {
             atomicOr(&c->status, 1ull << 1);
@@ -206,10 +213,10 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
         }
         int32_t ng;
         if (e_lo == r.y) {
-            ng = g.y;
+            ng = gy;
         } else {
-            // first group whose range ends after e_lo (ngo[g.y] = r.y > e_lo)
-            int32_t lo = g.x, hi = g.y - 1;
+            // first group whose range ends after e_lo (ngo[gy] = r.y > e_lo)
+            int32_t lo = gx, hi = gy - 1;
             while (lo < hi) {
                 const int32_t mid = lo + ((hi - lo) >> 1);
                 if (ngo[mid + 1] > e_lo) hi = mid;
@@ -217,12 +224,12 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
             }
             ng = lo;
             ngo[ng] = e_lo;  // the first kept group may have lost a prefix
+            ngr[v].t_first = ngts[ng];
         }
-        removed += ng - g.x;
+        removed += ng - gx;
         r.x = e_lo;
-        g.x = ng;
         nrec[v] = r;
-        ngr[v] = g;
+        ngr[v].g_lo = ng;
     }
     removed = warp_sum((unsigned long long)removed);
     if ((threadIdx.x & 31) == 0 && removed) atomicAdd((unsigned long long *)&c->gn_delta, (unsigned long long)-removed);
@@ -288,8 +295,7 @@ struct AppendRunOp {
     const uint32_t *kb, *vb;
     const int32_t *touched;
     Items it;
-    const int2 *ngr;
-    const int64_t *ngts;
+    const NodeRange *ngr;
     int32_t *run_of, *fx, *run_node, *run_pos, *run_g;
     __device__ __forceinline__ uint64_t value(int64_t p) const
     {
@@ -297,8 +303,8 @@ struct AppendRunOp {
         const bool nc = p == 0 || kb[p] != kb[p - 1];
         bool gc;
         if (nc) {
-            const int2 g = ngr[touched[kb[p]]];
-            gc = g.x == g.y || ngts[g.y - 1] != t;
+            const NodeRange &g = ngr[touched[kb[p]]];
+            gc = g.g_lo == g.g_hi || g.t_last != t;
         } else {
             gc = it.ts[it.edge(vb[p - 1])] != t;
         }
@@ -323,7 +329,7 @@ struct AppendRunOp {
 // space is used); else fresh regions from the pools and a move.
 __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
                              const int32_t *__restrict__ run_g, const uint64_t *__restrict__ tot, int shift,
-                             int64_t e_cap, int64_t g_cap, int4 *nrec, int2 *ngr, int2 *nbeg, int32_t *ngo,
+                             int64_t e_cap, int64_t g_cap, int4 *nrec, NodeRange *ngr, int2 *nbeg, int32_t *ngo,
                              int32_t *act, int64_t act_cap, Reloc *reloc, int32_t *run_de, int32_t *run_dg,
                              NvCounters *c)
 {
@@ -333,7 +339,7 @@ __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t
         const int32_t v = run_node[r];
         const int32_t cnt = run_pos[r + 1] - run_pos[r], gc = run_g[r + 1] - run_g[r];
         int4 rec = nrec[v];
-        int2 g = ngr[v];
+        int2 g = make_int2(ngr[v].g_lo, ngr[v].g_hi);
         const bool fresh = rec.z == 0;
         if (fresh) {
             const unsigned long long a = atomicAdd(&c->n_act, 1ull);
@@ -380,7 +386,8 @@ __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t
         }
         g.y = d_g + gc;
         nrec[v] = rec;
-        ngr[v] = g;
+        ngr[v].g_lo = g.x;
+        ngr[v].g_hi = g.y;
         // the slot after the last group (= rec.y) is written with the batch's
         // groups, after any move has read the old groups
         run_de[r] = d_e;
@@ -432,8 +439,9 @@ __global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__res
 __global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t slot_base, int64_t nbe,
                              const int32_t *__restrict__ run_of, const int32_t *__restrict__ fx,
                              const int32_t *__restrict__ run_pos, const int32_t *__restrict__ run_g,
-                             const int32_t *__restrict__ run_de, const int32_t *__restrict__ run_dg, int64_t e_cap,
-                             int64_t g_cap, Entry *ent, int32_t *ngo, int64_t *ngts, NvCounters *c)
+                             const int32_t *__restrict__ run_de, const int32_t *__restrict__ run_dg,
+                             const int32_t *__restrict__ run_node, int64_t e_cap, int64_t g_cap, Entry *ent,
+                             int32_t *ngo, int64_t *ngts, NodeRange *ngr, NvCounters *c)
 {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nbe; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = run_of[p];
@@ -446,6 +454,12 @@ __global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t
         }
         const Entry x = it.entry(vb[p], slot_base);
         ent[e] = x;
+        // the node record's first / last group timestamps
+        if (p == run_pos[r]) {
+            const int32_t v = run_node[r];
+            if (ngr[v].g_lo == run_dg[r]) ngr[v].t_first = x.ts;  // no live group before the batch
+        }
+        if (p + 1 == run_pos[r + 1]) ngr[run_node[r]].t_last = x.ts;
         if (fx[p + 1] != fx[p]) {
             const int64_t g = (int64_t)run_dg[r] + (fx[p] - run_g[r]);
             if (g < 0 || g >= g_cap) {
@@ -470,21 +484,21 @@ __global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t
 
 struct CountOp {
     const int4 *nrec;
-    const int2 *ngr;
+    const NodeRange *ngr;
     int64_t N;
     int groups;
     int32_t *out;
     __device__ __forceinline__ uint64_t value(int64_t v) const
     {
         if (v >= N) return 0;
-        return groups ? (uint64_t)(ngr[v].y - ngr[v].x) : (uint64_t)(nrec[v].y - nrec[v].x);
+        return groups ? (uint64_t)(ngr[v].g_hi - ngr[v].g_lo) : (uint64_t)(nrec[v].y - nrec[v].x);
     }
     __device__ __forceinline__ void emit(int64_t v, uint64_t, uint64_t ex) const { out[v] = (int32_t)ex; }
 };
 
 // One warp per node: its entries' store positions (node order) or its group
 // starts (canonical offsets), at the node's canonical place.
-__global__ void k_nv_export(const int4 *__restrict__ nrec, const int2 *__restrict__ ngr,
+__global__ void k_nv_export(const int4 *__restrict__ nrec, const NodeRange *__restrict__ ngr,
                             const int32_t *__restrict__ off, const int32_t *__restrict__ gidx,
                             const Entry *__restrict__ ent, const int32_t *__restrict__ ngo, int64_t N,
                             uint32_t slot_base, int groups, int32_t *out)
@@ -497,8 +511,8 @@ __global__ void k_nv_export(const int4 *__restrict__ nrec, const int2 *__restric
             for (int32_t i = lane; i < r.y - r.x; i += 32)
                 out[off[v] + i] = (int32_t)((uint32_t)ent[r.x + i].slot - slot_base);
         } else {
-            const int2 g = ngr[v];
-            for (int32_t i = lane; i < g.y - g.x; i += 32) out[gidx[v] + i] = off[v] + (ngo[g.x + i] - r.x);
+            const int32_t gx = ngr[v].g_lo, gy = ngr[v].g_hi;
+            for (int32_t i = lane; i < gy - gx; i += 32) out[gidx[v] + i] = off[v] + (ngo[gx + i] - r.x);
         }
     }
 }
@@ -578,7 +592,7 @@ int nv_ensure_nodes(tempest_t *h, int64_t N)
     int rc;
     const size_t used = (size_t)h->nrec_n;
     if ((rc = grow_keep(h, h->nrec, sizeof(int4) * used, sizeof(int4) * (size_t)need))) return rc;
-    if ((rc = grow_keep(h, h->ngr, sizeof(int2) * used, sizeof(int2) * (size_t)need))) return rc;
+    if ((rc = grow_keep(h, h->ngr, sizeof(NodeRange) * used, sizeof(NodeRange) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->ev, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->act, sizeof(int32_t) * (size_t)h->n_act, sizeof(int32_t) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->dense, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
@@ -586,7 +600,7 @@ int nv_ensure_nodes(tempest_t *h, int64_t N)
     int64_t cover = (int64_t)(h->nrec.bytes / sizeof(int4));
     cover = std::min(cover, (int64_t)(h->nbeg.bytes / sizeof(int2)));
     cover = std::min(cover, (int64_t)(h->dense.bytes / sizeof(int32_t)));
-    cover = std::min(cover, (int64_t)(h->ngr.bytes / sizeof(int2)));
+    cover = std::min(cover, (int64_t)(h->ngr.bytes / sizeof(NodeRange)));
     cover = std::min(cover, (int64_t)(h->ev.bytes / sizeof(int32_t)));
     cover = std::min(cover, (int64_t)(h->act.bytes / sizeof(int32_t)));
     h->nrec_n = cover;
@@ -661,8 +675,8 @@ int nv_build(tempest_t *h)
     h->g_cap = std::min(h->g_cap, (int64_t)INT32_MAX - 1);
     k_nv_build_nodes<<<grid_for(h, S), 256, 0, st>>>(h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
                                                      h->run_g.as<int32_t>(), h->run_de.as<int32_t>(),
-                                                     h->run_dg.as<int32_t>(), S, shift, h->nrec.as<int4>(),
-                                                     h->ngr.as<int2>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
+                                                     h->run_dg.as<int32_t>(), E, S, shift, h->nrec.as<int4>(),
+                                                     h->ngr.as<NodeRange>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
                                                      h->act.as<int32_t>());
     k_nv_build_scatter<<<grid_for(h, M), 256, 0, st>>>(E, h->run_of.as<int32_t>(), h->fx.as<int32_t>(),
                                                        h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(),
@@ -708,8 +722,8 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         k_nv_evict_count<<<grid_for(h, ne), 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
                                                           h->ev_nodes.as<int32_t>(), dc);
         k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
-            h->ev_nodes.as<int32_t>(), h->ev.as<int32_t>(), h->nrec.as<int4>(), h->ngr.as<int2>(),
-            h->ngo.as<int32_t>(), dc);
+            h->ev_nodes.as<int32_t>(), h->ev.as<int32_t>(), h->nrec.as<int4>(), h->ngr.as<NodeRange>(),
+            h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), dc);
         h->pending_launches += 2;
     }
     if (nbe > 0) {
@@ -743,7 +757,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
             r = 0;
         }
         uint64_t *part = h->partials.as<uint64_t>();
-        AppendRunOp op{kb[r], vb[r], h->touched.as<int32_t>(), it, h->ngr.as<int2>(), h->ngts.as<int64_t>(),
+        AppendRunOp op{kb[r], vb[r], h->touched.as<int32_t>(), it, h->ngr.as<NodeRange>(),
                        h->run_of.as<int32_t>(),
                        h->fx.as<int32_t>(), h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
                        h->run_g.as<int32_t>()};
@@ -754,7 +768,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         k_nv_tail<<<1, 1, 0, st>>>(h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), h->fx.as<int32_t>(), tot, nbe);
         k_nv_reserve<<<grid_for(h, runs_max), 256, 0, st>>>(
             h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), tot, h->nv_shift, h->e_cap,
-            h->g_cap, h->nrec.as<int4>(), h->ngr.as<int2>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
+            h->g_cap, h->nrec.as<int4>(), h->ngr.as<NodeRange>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
             h->act.as<int32_t>(), h->nrec_n, h->reloc.as<Reloc>(), h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(),
             dc);
         NvCounters *hc = static_cast<NvCounters *>(h->hstat);
@@ -781,9 +795,9 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         k_nv_scatter<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], it, slot_base(h, new_lo), nbe, h->run_of.as<int32_t>(),
                                                        h->fx.as<int32_t>(), h->run_pos.as<int32_t>(),
                                                        h->run_g.as<int32_t>(), h->run_de.as<int32_t>(),
-                                                       h->run_dg.as<int32_t>(), h->e_cap, h->g_cap,
-                                                       h->ent.as<Entry>(), h->ngo.as<int32_t>(),
-                                                       h->ngts.as<int64_t>(), dc);
+                                                       h->run_dg.as<int32_t>(), h->run_node.as<int32_t>(), h->e_cap,
+                                                       h->g_cap, h->ent.as<Entry>(), h->ngo.as<int32_t>(),
+                                                       h->ngts.as<int64_t>(), h->ngr.as<NodeRange>(), dc);
         h->pending_launches++;
     }
     NvCounters *hc = static_cast<NvCounters *>(h->hstat);
@@ -810,7 +824,7 @@ int nv_export(tempest_t *h, int which, int32_t *out)
     if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
     uint64_t *part = h->partials.as<uint64_t>();
     const int4 *nrec = h->nrec.as<int4>();
-    const int2 *ngr = h->ngr.as<int2>();
+    const NodeRange *ngr = h->ngr.as<NodeRange>();
     if (which == TEMPEST_STATE_NODE_OFF || which == TEMPEST_STATE_NODE_GIDX) {
         CountOp op{nrec, ngr, N, which == TEMPEST_STATE_NODE_GIDX, out};
         scan_launch(op, N + 1, part, st);

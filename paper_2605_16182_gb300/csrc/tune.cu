@@ -206,7 +206,7 @@ static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const i
         rc = T.sweep(best, best_ms, logs, 5, [](Cfg &c, int v) { c.bkt_log = v; });
     }
     if (!rc && best.sched == TEMPEST_SCHED_STREAM) {
-        const int ctas[] = {1, 2, 3, 4};
+        const int ctas[] = {2, 3, 4, 5};
         rc = T.sweep(best, best_ms, ctas, 4, [](Cfg &c, int v) { c.ctas = v; });
     }
     if (!rc && best.sched == TEMPEST_SCHED_COOP) {

@@ -22,14 +22,13 @@ struct WalkView {
     const int32_t *tg;
     uint32_t s_lo;
     int64_t G;
-    // node view: groups [ngr[v].x, ngr[v].y) of node v; group g's entries
-    // [ngo[g], ngo[g + 1]) in the entry pool
-    const int2 *ngr;
+    // node view: record of node v (its groups, bucket base, first / last
+    // group timestamps); group g's entries [ngo[g], ngo[g + 1]) in the pool
+    const NodeRange *ngr;
     const int32_t *ngo;
     const int64_t *ngts;
     const Entry *ent;
     // time buckets of nodes with at least BKT_MIN_G groups (null: none)
-    const int32_t *bkt_base;  // [N+1], valid for those nodes
     const int32_t *bkt;
     int bkt_log;
     int directed;
@@ -122,15 +121,37 @@ __device__ __forceinline__ uint32_t bkt_index(const BktMap &m, int64_t t)
     return k < m.K ? k : m.K - 1u;
 }
 
+// The node record of v (two 16-byte loads of one sector).
+__device__ __forceinline__ void load_range(const NodeRange *r, int32_t &g_lo, int32_t &g_hi, int32_t &tb,
+                                           int64_t &t_first, int64_t &t_last)
+{
+    const int4 a = __ldg(reinterpret_cast<const int4 *>(r));
+    const longlong2 b = __ldg(reinterpret_cast<const longlong2 *>(r) + 1);
+    g_lo = a.x;
+    g_hi = a.y;
+    tb = a.z;
+    t_first = b.x;
+    t_last = b.y;
+}
+
+// Live groups [g0, g1) of v (the first 8 bytes of its record).
+__device__ __forceinline__ void node_groups(const WalkView &V, int32_t v, int32_t &g0, int32_t &g1)
+{
+    const int2 a = __ldg(reinterpret_cast<const int2 *>(V.ngr + v));
+    g0 = a.x;
+    g1 = a.y;
+}
+
 // First group of v in [g0, g1) whose timestamp is > t (g1 when none):
 // through the node's time buckets when it has them, else a plain bisection.
 __device__ __forceinline__ int32_t first_later(const WalkView &V, int32_t v, int32_t g0, int32_t g1, int64_t t)
 {
     if (V.bkt && g1 - g0 >= BKT_MIN_G) {
-        const int64_t tlo = __ldg(V.ngts + g0), thi = __ldg(V.ngts + g1 - 1);
+        int32_t a, b, tb;
+        int64_t tlo, thi;
+        load_range(V.ngr + v, a, b, tb, tlo, thi);
         if (t < tlo) return g0;
         if (t >= thi) return g1;
-        const int32_t tb = __ldg(V.bkt_base + v);
         const uint32_t k = bkt_index(bkt_map(tlo, thi, bkt_count(g1 - g0, V.bkt_log)), t);
         const int32_t lo = __ldg(V.bkt + tb + k), hi = __ldg(V.bkt + tb + k + 1);
         return upper_bound_ts(V.ngts, lo, hi, t);

@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
             int32_t v = d;
             int64_t t = t0;
             for (uint32_t h = 1; len < L; h++) {
-                const int2 gr = __ldg(V.ngr + v);
-                const int32_t g0 = gr.x, g1 = gr.y;
+                int32_t g0, g1;
+                node_groups(V, v, g0, g1);
                 const int32_t c = first_later(V, v, g0, g1, t);
                 if (c == g1) break;  // Gamma_t(v) is empty
                 r = walk_rand(O.seed, (uint64_t)w, h);
@@ -124,8 +124,7 @@ enum : int {
     S_NEW,         // walk assigned: draw the start
     S_SGROUP,      // start timestamp group offsets loaded
     S_EDGE,        // start edge loaded
-    S_RANGE,       // node group range loaded
-    S_ENDS,        // first / last group timestamps loaded
+    S_RANGE,       // node record loaded (groups, bucket base, first / last ts)
     S_BKT,         // time-bucket table pair loaded (high-degree node)
     S_SEARCH,      // one probe loaded
     S_PICK2,       // chosen group's entry range loaded
@@ -240,9 +239,11 @@ struct ManyReq {
     __device__ __forceinline__ WalkCounters *cnt() const { return counters; }
 };
 
-template <class P>
-__global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const P Pv,
-                                                          unsigned long long *next_walk)
+// MINB: resident CTAs per SM the register budget is cut for (4: 64
+// registers; 5: 48 registers with a few spills, for more warps in flight).
+template <class P, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, const P Pv,
+                                                             unsigned long long *next_walk)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
     s.w = 0;
     int64_t y0 = 0;           // loaded 64-bit value
     int32_t z0 = 0, z1 = 0;   // loaded 32-bit values
+    int32_t z2 = 0;
     int64_t y1 = 0;
     unsigned long long hops = 0, bytes = 0;
     const int64_t N = Pv.total();
@@ -352,36 +354,26 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 if (s.len >= s.cap_len) {
                     finish = true;
                 } else {
-                    const int2 gr = __ldg(V.ngr + b);
-                    z0 = gr.x;
-                    z1 = gr.y;
+                    load_range(V.ngr + b, z0, z1, z2, y0, y1);
                     s.state = S_RANGE;
                 }
                 break;
             }
             case S_RANGE: {
+                // z0, z1: groups; z2: bucket base; y0, y1: first / last ts
                 s.g0 = z0;
                 s.g1 = z1;
                 if (z0 == z1) {
                     finish = true;
-                } else {
-                    y0 = __ldg(V.ngts + z0);
-                    y1 = __ldg(V.ngts + z1 - 1);
-                    if (V.bkt && z1 - z0 >= BKT_MIN_G) z0 = __ldg(V.bkt_base + s.v);
-                    s.state = S_ENDS;
-                }
-                break;
-            }
-            case S_ENDS: {
-                if (s.t < y0) {
+                } else if (s.t < y0) {
                     s.R = s.g0;  // all of the node's groups are later than t
                     pick = true;
                 } else if (s.t >= y1) {
                     finish = true;  // Gamma_t(v) is empty
                 } else if (V.bkt && s.g1 - s.g0 >= BKT_MIN_G) {
-                    // y0 <= t < y1: the bucket of t brackets c (z0: table base)
+                    // y0 <= t < y1: the bucket of t brackets c
                     const uint32_t k = bkt_index(bkt_map(y0, y1, bkt_count(s.g1 - s.g0, V.bkt_log)), s.t);
-                    const int32_t *tp = V.bkt + z0 + k;
+                    const int32_t *tp = V.bkt + z2 + k;
                     z0 = __ldg(tp);
                     z1 = __ldg(tp + 1);
                     s.state = S_BKT;
@@ -460,9 +452,7 @@ __global__ void __launch_bounds__(256, 4) k_walks_stream(const WalkView V, const
                 if (s.len >= s.cap_len) {
                     finish = true;
                 } else {
-                    const int2 gr = __ldg(V.ngr + z0);
-                    z0 = gr.x;
-                    z1 = gr.y;
+                    load_range(V.ngr + z0, z0, z1, z2, y0, y1);
                     s.state = S_RANGE;
                 }
                 break;
@@ -568,6 +558,29 @@ __global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, 
     }
 }
 
+// Launches the streaming walker with the register budget the CTAs-per-SM
+// knob asks for (0: the 64-register build at its occupancy limit).
+template <class P>
+static void launch_stream(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
+                          cudaStream_t st)
+{
+    static int occ4 = 0, occ5 = 0;
+    if (occ4 == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ4, k_walks_stream<P, 4>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_stream<P, 5>, 256, 0);
+        if (occ4 < 1) occ4 = 1;
+        if (occ5 < 1) occ5 = 1;
+    }
+    const bool wide = h->stream_ctas > 4;
+    const int occ = wide ? occ5 : occ4;
+    const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, occ) : occ;
+    int64_t grid = (int64_t)h->num_sms * bps;
+    const int64_t need = (total + 255) / 256;
+    if (grid > need) grid = need;
+    if (wide) k_walks_stream<P, 5><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else k_walks_stream<P, 4><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+}
+
 // Events bracketing the walk kernels of a call (created on first use).
 static void kernel_mark(tempest_t *h, int which)
 {
@@ -581,19 +594,10 @@ int walks_multi_launch(tempest_t *h, const ReqDesc *dev_reqs, int n_req, int64_t
 {
     cudaMemsetAsync(cnt, 0, sizeof(WalkCounters), st);
     if (total <= 0 || n_req <= 0) return cuda_check(h, cudaGetLastError(), "walks multi");
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walks_stream<ManyReq>, 256, 0);
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
-    const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, blocks_per_sm) : blocks_per_sm;
-    int64_t grid = (int64_t)h->num_sms * bps;
-    const int64_t need = (total + 255) / 256;
-    if (grid > need) grid = need;
     const WalkView V = make_view(h);
     const bool mark = st == h->stream;
     if (mark) kernel_mark(h, 0);
-    k_walks_stream<ManyReq><<<(unsigned)grid, 256, 0, st>>>(V, ManyReq{dev_reqs, n_req, total, cnt}, &cnt->pad);
+    launch_stream(h, V, ManyReq{dev_reqs, n_req, total, cnt}, &cnt->pad, total, st);
     if (mark) kernel_mark(h, 1);
     return cuda_check(h, cudaGetLastError(), "walks multi");
 }
@@ -631,12 +635,11 @@ WalkView make_view(tempest_t *h)
     V.tg = h->tg.as<int32_t>() + h->tg_lo;
     V.s_lo = (uint32_t)(uint64_t)(h->s_base + h->s_lo);
     V.G = h->G;
-    V.ngr = h->ngr.as<int2>();
+    V.ngr = h->ngr.as<NodeRange>();
     V.ngo = h->ngo.as<int32_t>();
     V.ngts = h->ngts.as<int64_t>();
     V.ent = h->ent.as<Entry>();
     const bool bk = h->n_big > 0 && h->bkt_ver == h->state_ver;
-    V.bkt_base = bk ? h->bkt_base.as<int32_t>() : nullptr;
     V.bkt = bk ? h->bkt.as<int32_t>() : nullptr;
     V.bkt_log = h->bkt_log;
     V.directed = h->directed;
@@ -690,17 +693,8 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
             kernel_mark(h, 1);
             launches++;
         } else {
-            static int blocks_per_sm = 0;
-            if (blocks_per_sm == 0) {
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walks_stream<OneReq>, 256, 0);
-                if (blocks_per_sm < 1) blocks_per_sm = 1;
-            }
-            const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, blocks_per_sm) : blocks_per_sm;
-            int64_t grid = (int64_t)h->num_sms * bps;
-            const int64_t need = (rq.n_walks + 255) / 256;
-            if (grid > need) grid = need;
             kernel_mark(h, 0);
-            k_walks_stream<OneReq><<<(unsigned)grid, 256, 0, st>>>(V, OneReq{O}, &O.cnt->pad);
+            launch_stream(h, V, OneReq{O}, &O.cnt->pad, rq.n_walks, st);
             kernel_mark(h, 1);
             launches += 1;  // the walker pads its rows itself
         }

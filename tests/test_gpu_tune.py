@@ -43,7 +43,8 @@ def test_every_knob_setting_gives_the_same_walks(sched):
     ref = {b: _walks(eng, b) for b in (0, 2)}
     eng.set_scheduler(sched)
     for knob, val in ((_lib.TUNE_BKT_LOG, 0), (_lib.TUNE_BKT_LOG, 5), (_lib.TUNE_COOP_W_WARP, 1),
-                      (_lib.TUNE_COOP_W_WARP, 64), (_lib.TUNE_COOP_MEGA, 256), (_lib.TUNE_STREAM_CTAS, 1)):
+                      (_lib.TUNE_COOP_W_WARP, 64), (_lib.TUNE_COOP_MEGA, 256), (_lib.TUNE_STREAM_CTAS, 1),
+                      (_lib.TUNE_STREAM_CTAS, 5)):
         eng.set_tuning(knob, val)
         for b in (0, 2):
             got = eng.walks(20000, 30, bias=b, seed=9)
