@@ -22,7 +22,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
 
 BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP = 0, 1, 2
-START_UNIFORM_EDGE, START_BIASED_TS = 0, 1
+START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -52,9 +52,11 @@ def lib():
         L.orc_destroy.argtypes = [vp]
         L.orc_set_bias_params.argtypes = [vp, dbl, dbl]
         L.orc_ingest.argtypes = [vp, vp, vp, vp, i64]
-        L.orc_walks.argtypes = [vp, i64, vp, i32, vp, i32, vp, ctypes.c_int, ctypes.c_int, u64,
+        L.orc_walks.argtypes = [vp, i64, vp, i32, vp, i32, vp, ctypes.c_int, ctypes.c_int, i64, u64,
                                 vp, vp, vp, vp, vp]
         L.orc_counts.argtypes = [vp, vp]
+        L.orc_active_nodes.argtypes = [vp, vp]
+        L.orc_active_nodes.restype = i64
         L.orc_export_live.argtypes = [vp, vp, vp, vp]
         L.orc_export_ts_groups.argtypes = [vp, vp]
         L.orc_export_node_view.argtypes = [vp, vp, vp, vp, vp]
@@ -163,15 +165,32 @@ class Oracle:
         return dict(counts=c, src=src, dst=dst, ts=ts, ts_group_off=tgo, node_off=node_off,
                     node_order=node_order[:M], node_group_off=ngo, node_gidx=gidx)
 
+    def active_nodes(self):
+        """Nodes with at least one live entry in the node view, in id order."""
+        n = int(lib().orc_active_nodes(self._h, None))
+        out = np.zeros(max(n, 1), np.int32)
+        lib().orc_active_nodes(self._h, _p(out))
+        return out[:n]
+
     def walks(self, n_walks=None, max_len=2, bias=BIAS_UNIFORM, start_policy=START_UNIFORM_EDGE,
               seed=0, ids=None, max_len_arr=None, bias_arr=None, with_margin=False,
-              with_bytes=False):
-        """Returns (node [n, cap], ts [n, cap], len [n], margin or None, bytes or None)."""
+              with_bytes=False, walks_per_node=None):
+        """Returns (node [n, cap], ts [n, cap], len [n], margin or None, bytes or None).
+        With START_PER_NODE, walk w starts at active node w // walks_per_node
+        (by default n_walks divided by the number of active nodes)."""
         if ids is not None:
             ids = np.ascontiguousarray(ids, dtype=np.int64)
             n = ids.shape[0]
         else:
             n = int(n_walks)
+        k = 0
+        if start_policy == START_PER_NODE:
+            if walks_per_node is None:
+                na = len(self.active_nodes())
+                if na == 0 or n % na:
+                    raise ValueError("per-node walks: %d walks for %d active nodes" % (n, na))
+                walks_per_node = n // na
+            k = int(walks_per_node)
         cap = int(max_len)
         if max_len_arr is not None:
             max_len_arr = np.ascontiguousarray(max_len_arr, dtype=np.int32)
@@ -184,7 +203,7 @@ class Oracle:
         margin = np.zeros((n, cap), np.float64) if with_margin else None
         nbytes = np.zeros(1, np.float64) if with_bytes else None
         rc = lib().orc_walks(self._h, n, _p(ids), cap, _p(max_len_arr), int(max_len), _p(bias_arr),
-                             int(bias), int(start_policy), ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                             int(bias), int(start_policy), k, ctypes.c_uint64(int(seed) & (2**64 - 1)),
                              _p(node), _p(ts), _p(ln), _p(margin), _p(nbytes))
         if rc != 0:
             raise ValueError("orc_walks rc=%d" % rc)

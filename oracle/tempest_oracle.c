@@ -61,6 +61,7 @@
 
 #define START_UNIFORM_EDGE 0
 #define START_BIASED_TS 1
+#define START_PER_NODE 2
 
 typedef struct {
     int32_t src, dst;
@@ -339,7 +340,7 @@ int orc_ingest(orc *o, const int32_t *src, const int32_t *dst, const int64_t *ts
     if (n < 0) return ORC_EINVAL;
     if (n > 0 && (!src || !dst || !ts)) return ORC_EINVAL;
     for (int64_t i = 0; i < n; i++)
-        if (src[i] < 0 || dst[i] < 0) return ORC_EINVAL;
+        if (src[i] < 0 || dst[i] < 0 || ts[i] == INT64_MIN) return ORC_EINVAL;
 
     /* 1. arrival index for every edge; drop late edges */
     orc_edge *batch = (orc_edge *)malloc(sizeof(orc_edge) * (size_t)(n > 0 ? n : 1));
@@ -437,13 +438,17 @@ static double rel_margin(double x, int64_t n)
 /*
  * One walk.  Writes up to max_len nodes and timestamps (the first timestamp
  * is INT64_MIN: the start node is reached at no time), returns the length.
+ * With START_PER_NODE the walk starts at node `start_node` and its first hop
+ * draws from all of that node's live edges (every timestamp is above
+ * INT64_MIN); the other policies draw a start edge, which gives two nodes.
+ * The hop that appends the node at position p uses Philox counter p - 1.
  * margin (nullable, max_len entries) receives, for each position drawn by a
  * linear or exponential sampler, |x - nearest integer| / max(1, n); other
  * positions receive +inf.  bytes (nullable) accumulates the per-hop sector
  * model of the walk's memory traffic.
  */
 static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int start_policy,
-                        uint64_t seed, int32_t *node, int64_t *tsout, double *margin,
+                        int64_t start_node, uint64_t seed, int32_t *node, int64_t *tsout, double *margin,
                         double lambda_start, double *bytes)
 {
     for (int32_t i = 0; i < max_len; i++) {
@@ -454,32 +459,43 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
     if (o->m == 0) return 0;
 
     uint32_t r[4];
-    walk_block(seed, w, 0, r);
-    double u1 = orc_u53(r[0], r[1]);
-    double u2 = orc_u53(r[2], r[3]);
-
-    int64_t k;
-    if (start_policy == START_UNIFORM_EDGE) {
-        k = uniform_index(u1, o->m);
+    double u1, u2;
+    int32_t len;
+    int64_t v, t;
+    if (start_policy == START_PER_NODE) {
+        node[0] = (int32_t)start_node;
+        len = 1;
+        v = start_node;
+        t = INT64_MIN;
     } else {
-        double x = orc_sampler_x(u1, o->G_tot, bias, lambda_start);
-        int64_t g = orc_sampler_index(u1, o->G_tot, bias, lambda_start);
-        if (margin && bias != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
-        int64_t a = o->ts_group_off[g], size = o->ts_group_off[g + 1] - a;
-        k = a + uniform_index(u2, size);
+        walk_block(seed, w, 0, r);
+        u1 = orc_u53(r[0], r[1]);
+        u2 = orc_u53(r[2], r[3]);
+        int64_t k;
+        if (start_policy == START_UNIFORM_EDGE) {
+            k = uniform_index(u1, o->m);
+        } else {
+            double x = orc_sampler_x(u1, o->G_tot, bias, lambda_start);
+            int64_t g = orc_sampler_index(u1, o->G_tot, bias, lambda_start);
+            if (margin && bias != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
+            int64_t a = o->ts_group_off[g], size = o->ts_group_off[g + 1] - a;
+            k = a + uniform_index(u2, size);
+        }
+        int32_t s = o->live[k].src, d = o->live[k].dst;
+        if (!o->directed && (r[3] & 1u)) {
+            int32_t tmp = s; s = d; d = tmp;
+        }
+        node[0] = s;
+        node[1] = d;
+        tsout[1] = o->live[k].ts;
+        len = 2;
+        if (bytes) *bytes += 3 * 32.0 + 4 + 4 + 8 + 8 + 4;
+        v = d;
+        t = o->live[k].ts;
     }
-    int32_t s = o->live[k].src, d = o->live[k].dst;
-    if (!o->directed && (r[3] & 1u)) {
-        int32_t tmp = s; s = d; d = tmp;
-    }
-    node[0] = s;
-    node[1] = d;
-    tsout[1] = o->live[k].ts;
-    int32_t len = 2;
-    if (bytes) *bytes += 3 * 32.0 + 4 + 4 + 8 + 8 + 4;
 
-    int64_t v = d, t = o->live[k].ts;
-    for (uint32_t h = 1; len < max_len; h++) {
+    while (len < max_len) {
+        const uint32_t h = (uint32_t)(len - 1);
         int64_t g0 = o->node_gidx[v], g1 = o->node_gidx[v + 1];
         int64_t c = first_group_after(o, g0, g1, t);
         if (c == g1) break; /* Gamma_t(v) is empty */
@@ -515,6 +531,18 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
     return len;
 }
 
+/* Nodes with at least one live entry in the node view, in id order. */
+int64_t orc_active_nodes(const orc *o, int32_t *out)
+{
+    int64_t n = 0;
+    for (int64_t v = 0; v < o->n_nodes; v++)
+        if (o->node_gidx[v + 1] > o->node_gidx[v]) {
+            if (out) out[n] = (int32_t)v;
+            n++;
+        }
+    return n;
+}
+
 static double eff_lambda_start(const orc *o)
 {
     if (o->lambda_start > 0.0) return o->lambda_start;
@@ -528,18 +556,40 @@ static double eff_lambda_start(const orc *o)
  */
 int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
               const int32_t *max_len_arr, int32_t max_len, const uint8_t *bias_arr, int bias,
-              int start_policy, uint64_t seed, int32_t *node, int64_t *ts, int32_t *len,
-              double *margin, double *bytes)
+              int start_policy, int64_t walks_per_node, uint64_t seed, int32_t *node, int64_t *ts,
+              int32_t *len, double *margin, double *bytes)
 {
     if (n < 0 || max_len_cap < 2) return ORC_EINVAL;
-    if (start_policy != START_UNIFORM_EDGE && start_policy != START_BIASED_TS) return ORC_EINVAL;
+    if (start_policy != START_UNIFORM_EDGE && start_policy != START_BIASED_TS && start_policy != START_PER_NODE)
+        return ORC_EINVAL;
+    int32_t *active = NULL;
+    int64_t n_active = 0;
+    if (start_policy == START_PER_NODE && o->m > 0) {
+        if (walks_per_node < 1) return ORC_EINVAL;
+        n_active = orc_active_nodes(o, NULL);
+        active = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_active > 0 ? n_active : 1));
+        if (!active) return ORC_ENOMEM;
+        orc_active_nodes(o, active);
+    }
     double ls = eff_lambda_start(o);
     if (bytes) *bytes = 0.0;
     for (int64_t i = 0; i < n; i++) {
         uint64_t w = ids ? (uint64_t)ids[i] : (uint64_t)i;
         int32_t L = max_len_arr ? max_len_arr[i] : max_len;
         int b = bias_arr ? (int)bias_arr[i] : bias;
-        if (L < 2 || L > max_len_cap || b < 0 || b > 2) return ORC_EINVAL;
+        if (L < 2 || L > max_len_cap || b < 0 || b > 2) {
+            free(active);
+            return ORC_EINVAL;
+        }
+        int64_t start_node = -1;
+        if (active) {
+            const int64_t a = (int64_t)(w / (uint64_t)walks_per_node);
+            if (a >= n_active) {
+                free(active);
+                return ORC_EINVAL;
+            }
+            start_node = active[a];
+        }
         int32_t *nr = node + i * (int64_t)max_len_cap;
         int64_t *tr = ts + i * (int64_t)max_len_cap;
         double *mr = margin ? margin + i * (int64_t)max_len_cap : NULL;
@@ -548,8 +598,9 @@ int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
             tr[j] = INT64_MIN;
             if (mr) mr[j] = INFINITY;
         }
-        len[i] = one_walk(o, w, L, b, start_policy, seed, nr, tr, mr, ls, bytes);
+        len[i] = one_walk(o, w, L, b, start_policy, start_node, seed, nr, tr, mr, ls, bytes);
     }
+    free(active);
     return ORC_OK;
 }
 

@@ -152,12 +152,16 @@ def start_distribution(live, directed, policy, bias, lam_start):
     return dist
 
 
-def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start):
-    """Exact probability of every complete walk (tuple of (node, ts) pairs)."""
+def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start, start_node=None):
+    """Exact probability of every complete walk (tuple of (node, ts) pairs).
+    With start_node the walk starts at that node and its first hop may take
+    any of the node's live edges (the per-node start policy)."""
     out = {}
 
     def rec(path, p):
         v, t = path[-1]
+        if t is None:
+            t = float("-inf")
         if len(path) >= max_len:
             out[tuple(path)] = out.get(tuple(path), 0.0) + p
             return
@@ -168,6 +172,9 @@ def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start)
         for (w, ts), q in d.items():
             rec(path + [(w, ts)], p * q)
 
+    if start_node is not None:
+        rec([(start_node, None)], 1.0)
+        return out
     for (a, b, ts), p in start_distribution(live, directed, policy, bias, lam_start).items():
         rec([(a, None), (b, ts)], p)
     return out

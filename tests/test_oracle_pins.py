@@ -295,6 +295,60 @@ def test_walk_distribution_matches_enumeration(directed, bias, policy):
     assert p > 1e-3, p
 
 
+@pytest.mark.parametrize("directed,bias", [(True, 0), (True, 1), (True, 2), (False, 2)])
+def test_per_node_walks_match_enumeration(directed, bias):
+    """K walks start at every node with a live edge, in id order; each start
+    node's walks follow the exact walk distribution from that node, whose
+    first hop may take any live edge of the node."""
+    from scipy.stats import chisquare
+    src = [0, 0, 0, 1, 1, 2, 2, 3, 0, 2, 5]
+    dst = [1, 2, 1, 2, 0, 0, 3, 0, 0, 2, 1]
+    ts = [1, 2, 2, 3, 4, 5, 5, 6, 7, 6, 3]
+    lam_hop = 0.7
+    max_len = 4
+    o = O.Oracle(window=0, directed=directed)
+    o.ingest(src, dst, ts)
+    o.set_bias_params(lam_hop, 0.4)
+    act = list(o.active_nodes())
+    want = sorted(set(src) | (set() if directed else set(dst)))
+    assert act == want  # node 4 has no edge; 5 only an out-edge
+    live = brute.window_state([(src, dst, ts)], 0, directed)[-1]["live"]
+    K = 12_000
+    node, tsa, ln, _, _ = o.walks(K * len(act), max_len, bias=bias, start_policy=O.START_PER_NODE, seed=5)
+    assert (ln >= 2).all()  # an active node always has a first hop
+    for a, v in enumerate(act):
+        dist = brute.walk_distribution(live, directed, max_len, bias, 0, lam_hop, 0.4, start_node=v)
+        assert abs(sum(dist.values()) - 1.0) < 1e-9
+        counts = {}
+        for i in range(a * K, (a + 1) * K):
+            assert node[i][0] == v and tsa[i][0] == np.iinfo(np.int64).min
+            k = _walk_key(node[i], tsa[i], ln[i])
+            assert k in dist, k
+            counts[k] = counts.get(k, 0) + 1
+        keys = [k for k in dist if dist[k] * K > 5]
+        if len(keys) < 2:
+            continue
+        obs = np.array([counts.get(k, 0) for k in keys], np.float64)
+        exp = np.array([dist[k] * K for k in keys], np.float64)
+        exp *= obs.sum() / exp.sum()
+        assert chisquare(obs, exp)[1] > 1e-3, v
+
+
+def test_per_node_walks_need_a_whole_number_per_node():
+    o = O.Oracle(window=0, directed=True)
+    o.ingest([0, 1, 2], [1, 2, 0], [1, 2, 3])
+    with pytest.raises(ValueError):
+        o.walks(7, 4, start_policy=O.START_PER_NODE)  # 3 active nodes
+    node, _, ln, _, _ = o.walks(6, 4, start_policy=O.START_PER_NODE)
+    assert list(node[:, 0]) == [0, 0, 1, 1, 2, 2]
+
+
+def test_int64_min_timestamps_are_rejected():
+    o = O.Oracle(window=0, directed=True)
+    with pytest.raises(Exception):
+        o.ingest([0], [1], [np.iinfo(np.int64).min])
+
+
 def _check_walk_invariants(st, directed, node, tsa, ln, max_len):
     live = {}
     for a, b, t in zip(st["src"], st["dst"], st["ts"]):
