@@ -55,11 +55,15 @@ enum {
  * Sec. 2.1). */
 enum { TEMPEST_BIAS_UNIFORM = 0, TEMPEST_BIAS_LINEAR = 1, TEMPEST_BIAS_EXP = 2 };
 
-/* Start-edge selection (Sec. 2.3, timestamp-grouped view).
+/* Start selection (Sec. 2.3, timestamp-grouped view; Sec. 3 workloads).
  * UNIFORM_EDGE: a live edge uniformly.  BIASED_TS: a timestamp group of the
  * whole window under the walk's own bias (EXP uses the start rate), then an
- * edge uniformly inside the group. */
-enum { TEMPEST_START_UNIFORM_EDGE = 0, TEMPEST_START_BIASED_TS = 1 };
+ * edge uniformly inside the group.  PER_NODE: K walks from every active node
+ * (a node with at least one live entry in the node view), in increasing id
+ * order: walk w starts at active node w / K, K = n_walks / (active nodes),
+ * which must divide; its first hop may take any of the node's live edges
+ * (as from a time before every live edge) and uses Philox counter 0. */
+enum { TEMPEST_START_UNIFORM_EDGE = 0, TEMPEST_START_BIASED_TS = 1, TEMPEST_START_PER_NODE = 2 };
 
 /* Walk execution form (Sec. 2.4).  The result is the same for every form:
  * each walk draws from its own counter-based random stream. */
@@ -139,14 +143,18 @@ int tempest_set_bias_params(tempest_t *h, double lambda_hop, double lambda_start
  * rest are sorted by timestamp (arrival order among ties) and merged into
  * the edge store; the cut-off advances and the edges before it are evicted;
  * both views are rebuilt (Sec. 2.3).  src, dst: int32[n] node ids >= 0;
- * ts: int64[n].  stats may be NULL.  EINVAL (state unchanged) on n < 0, NULL
- * arrays with n > 0, or a negative id.  Synchronises the stream. */
+ * ts: int64[n], each > INT64_MIN (the time before every edge, which walk
+ * outputs give their first node).  stats may be NULL.  EINVAL (state
+ * unchanged) on n < 0, NULL arrays with n > 0, a negative id or an INT64_MIN
+ * timestamp.  Synchronises the stream. */
 int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const int64_t *ts,
                    int64_t n, tempest_ingest_stats *stats);
 
 /* Draw n_walks walks (Sec. 2.1, 2.4, 2.5).  Walk w uses Philox4x32-10
  * (Salmon et al., SC'11) with key = seed and counter (hop, 0, w_lo, w_hi);
- * hop 0 selects the start edge, hop h >= 1 the h-th continuation.  From each
+ * the draw that appends the node at row position p uses hop = p - 1 (hop 0
+ * selects the start edge, which gives positions 0 and 1; under PER_NODE it
+ * is the first hop from the start node).  From each
  * block, u1 = (r0:r1 >> 11) * 2^-53 picks the edge or group and
  * u2 = (r2:r3 >> 11) * 2^-53 the edge inside a group; bit 0 of r3 orients an
  * undirected start edge.  At node v and time t the next edge comes from
@@ -298,6 +306,10 @@ int tempest_autotune(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, i
 int tempest_autotune_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_arr, int32_t max_len_cap,
                            const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t flags,
                            tempest_tune_report *out);
+
+/* Number of active nodes (nodes with at least one live entry in the node
+ * view) of the current state: the divisor of PER_NODE walk counts. */
+int tempest_active_nodes(tempest_t *h, int64_t *n);
 
 /* Report of the most recent walk call; waits for its work to finish. */
 int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out);

@@ -23,7 +23,7 @@ TEMPEST_ETIMEDOUT = -4
 TEMPEST_EBUSY = -5
 
 BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP = 0, 1, 2
-START_UNIFORM_EDGE, START_BIASED_TS = 0, 1
+START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH = 0, 1, 2, 3
 TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS = 0, 1, 2, 3
 TUNE_FORMS = 1
@@ -42,6 +42,7 @@ EXPORTED = (
     "tempest_server_submit_ingest", "tempest_server_progress", "tempest_server_status",
     "tempest_server_release", "tempest_server_drain", "tempest_server_stats",
     "tempest_set_tuning", "tempest_get_tuning", "tempest_autotune", "tempest_autotune_mixed",
+    "tempest_active_nodes",
 )
 NOALLOC_MAX_EDGES = 262144
 
@@ -135,6 +136,7 @@ def load():
     L.tempest_get_tuning.argtypes = [vp, ci, ctypes.POINTER(i64)]
     L.tempest_autotune.argtypes = [vp, i64, ctypes.c_int32, ci, ci, ctypes.c_uint64, ctypes.c_int32,
                                    ctypes.POINTER(TuneReport)]
+    L.tempest_active_nodes.argtypes = [vp, ctypes.POINTER(i64)]
     L.tempest_autotune_mixed.argtypes = [vp, i64, vp, ctypes.c_int32, vp, ci, ctypes.c_uint64, ctypes.c_int32,
                                          ctypes.POINTER(TuneReport)]
     L.tempest_last_walk_stats.argtypes = [vp, ctypes.POINTER(WalkStats)]
@@ -334,6 +336,12 @@ def tempest_get_tuning(h, knob: int) -> int:
     return v.value
 
 
+def tempest_active_nodes(h) -> int:
+    n = ctypes.c_int64()
+    _check(h, load().tempest_active_nodes(h, ctypes.byref(n)))
+    return n.value
+
+
 def tempest_autotune_mixed(h, n_walks, max_len_arr, max_len_cap, bias_arr, start_policy, seed, flags) -> TuneReport:
     rep = TuneReport()
     _check(h, load().tempest_autotune_mixed(h, int(n_walks), max_len_arr, int(max_len_cap), bias_arr,
@@ -467,6 +475,10 @@ class Engine:
 
     def get_tuning(self, knob: int) -> int:
         return tempest_get_tuning(self.h, knob)
+
+    def active_nodes(self) -> int:
+        """Number of nodes with a live entry: PER_NODE walk counts are multiples of it."""
+        return tempest_active_nodes(self.h)
 
     def autotune(self, n_walks, max_len, bias=BIAS_EXP, start_policy=0, seed=0, forms=True) -> dict:
         """Time candidate settings on the live index and keep the fastest."""

@@ -150,7 +150,42 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
     }
 }
 
+// Active nodes (at least one live group) in id order.
+struct ActiveOp {
+    const NodeRange *ngr;
+    int64_t N;
+    int32_t *out;
+    __device__ __forceinline__ uint64_t value(int64_t v) const
+    {
+        return v < N && ngr[v].g_hi > ngr[v].g_lo ? 1u : 0u;
+    }
+    __device__ __forceinline__ void emit(int64_t v, uint64_t x, uint64_t ex) const
+    {
+        if (x) out[ex] = (int32_t)v;
+    }
+};
+
 }  // namespace
+
+int prepare_active_nodes(tempest_t *h)
+{
+    if (h->pn_ver == h->state_ver) return TEMPEST_OK;
+    const int64_t N = h->N;
+    int rc;
+    h->n_pn = 0;
+    if (N > 0 && h->nv_ready && h->M > 0) {
+        if ((rc = ensure(h, h->pn_nodes, sizeof(int32_t) * (size_t)N, true))) return rc;
+        if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
+        ActiveOp op{h->ngr.as<NodeRange>(), N, h->pn_nodes.as<int32_t>()};
+        const int nb = scan_launch(op, N, h->partials.as<uint64_t>(), h->stream);
+        uint64_t *hp = static_cast<uint64_t *>(h->hstat);
+        cudaMemcpyAsync(hp, h->partials.as<uint64_t>() + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream);
+        if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "active nodes"))) return rc;
+        h->n_pn = (int64_t)hp[0];
+    }
+    h->pn_ver = h->state_ver;
+    return TEMPEST_OK;
+}
 
 int prepare_walk_index(tempest_t *h)
 {

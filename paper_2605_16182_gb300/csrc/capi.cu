@@ -113,8 +113,28 @@ static void free_all(tempest_t *h)
                     &h->sv[1],     &h->hist,      &h->partials,  &h->dstat,     &h->wcnt,      &h->out_stage,
                     &h->in_stage,  &h->exp_stage, &h->co_node,   &h->co_t,      &h->co_len,    &h->co_act[0],
                     &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt,
-                    &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched,   &h->tg2,       &h->nbeg};
+                    &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched,   &h->tg2,       &h->nbeg,
+                    &h->pn_nodes};
     for (DBuf *b : bufs) release(h, *b);
+}
+
+// Walks per active node of a PER_NODE request (0 for other policies);
+// EINVAL when the active nodes do not divide n_walks.
+int per_node_k(tempest_t *h, int start_policy, int64_t n_walks, int64_t &k, const char *who)
+{
+    k = 0;
+    if (start_policy != TEMPEST_START_PER_NODE || n_walks == 0) return TEMPEST_OK;
+    int rc;
+    if ((rc = prepare_active_nodes(h))) return rc;
+    if (h->n_pn == 0) {
+        k = 1;  // empty window: every walk has length 0
+        return TEMPEST_OK;
+    }
+    if (n_walks % h->n_pn != 0)
+        return fail(h, TEMPEST_EINVAL, "%s: PER_NODE needs a multiple of the %lld active nodes, got %lld walks", who,
+                    (long long)h->n_pn, (long long)n_walks);
+    k = n_walks / h->n_pn;
+    return TEMPEST_OK;
 }
 
 }  // namespace tw
@@ -221,6 +241,15 @@ int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const i
     return ingest_batch(h, src, dst, ts, n, stats);
 }
 
+int tempest_active_nodes(tempest_t *h, int64_t *n)
+{
+    if (!h || !n) return TEMPEST_EINVAL;
+    int rc;
+    if ((rc = prepare_active_nodes(h))) return rc;
+    *n = h->n_pn;
+    return TEMPEST_OK;
+}
+
 static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_len, const int32_t *len_arr,
                         int bias, const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t *node,
                         int64_t *ts, int32_t *len)
@@ -228,12 +257,14 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
     int rc;
     if (n_walks < 0) return fail(h, TEMPEST_EINVAL, "walks: n_walks < 0");
     if (cap < 2) return fail(h, TEMPEST_EINVAL, "walks: max_len must be >= 2");
-    if (start_policy != TEMPEST_START_UNIFORM_EDGE && start_policy != TEMPEST_START_BIASED_TS)
+    if (start_policy < TEMPEST_START_UNIFORM_EDGE || start_policy > TEMPEST_START_PER_NODE)
         return fail(h, TEMPEST_EINVAL, "walks: unknown start policy %d", start_policy);
     if (!bias_arr && (bias < 0 || bias > 2)) return fail(h, TEMPEST_EINVAL, "walks: unknown bias %d", bias);
     if (n_walks > 0 && (!node || !ts || !len)) return fail(h, TEMPEST_EINVAL, "walks: NULL output");
     if (n_walks > 0 && (int64_t)cap * n_walks / n_walks != (int64_t)cap)
         return fail(h, TEMPEST_EINVAL, "walks: output size overflows");
+    int64_t pn_k = 0;
+    if ((rc = per_node_k(h, start_policy, n_walks, pn_k, "walks"))) return rc;
     cudaStream_t st = h->stream;
     h->last_ws = tempest_walk_stats{};
     if (n_walks == 0) return TEMPEST_OK;
@@ -291,7 +322,7 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
         }
         if (!dev_len) d_lenout = reinterpret_cast<int32_t *>(p);
     }
-    WalkRequest rq{n_walks, cap, max_len, d_len, bias, d_bias, start_policy, seed, d_node, d_ts, d_lenout};
+    WalkRequest rq{n_walks, cap, max_len, d_len, bias, d_bias, start_policy, pn_k, seed, d_node, d_ts, d_lenout};
     if ((rc = walks_run(h, rq))) return rc;
     if (!dev_ts) cudaMemcpyAsync(ts, d_ts, sizeof(int64_t) * cells, cudaMemcpyDeviceToHost, st);
     if (!dev_node) cudaMemcpyAsync(node, d_node, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st);

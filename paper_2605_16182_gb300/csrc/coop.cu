@@ -85,21 +85,31 @@ __global__ void __launch_bounds__(256) k_coop_start(const WalkView V, const Walk
             O.len[w] = 0;
             continue;
         }
-        int32_t s, d;
+        int32_t s, d, len0;
         int64_t t0;
-        start_edge(V, O, w, bias, s, d, t0);
-        nrow[0] = s;
-        nrow[1] = d;
-        trow[0] = INT64_MIN;
-        trow[1] = t0;
-        hops++;
-        bytes += START_MODEL_BYTES;
-        if (L <= 2) {
-            O.len[w] = 2;
+        if (O.start_policy == TEMPEST_START_PER_NODE) {
+            // the walk starts at an active node before every live edge
+            d = __ldg(V.pn_nodes + w / O.pn_k);
+            t0 = INT64_MIN;
+            nrow[0] = d;
+            trow[0] = INT64_MIN;
+            len0 = 1;
+        } else {
+            start_edge(V, O, w, bias, s, d, t0);
+            nrow[0] = s;
+            nrow[1] = d;
+            trow[0] = INT64_MIN;
+            trow[1] = t0;
+            hops++;
+            bytes += START_MODEL_BYTES;
+            len0 = 2;
+        }
+        if (L <= len0) {
+            O.len[w] = len0;
         } else {
             S.ws_node[w] = d;
             S.ws_t[w] = t0;
-            S.ws_len[w] = 2;
+            S.ws_len[w] = len0;
             const unsigned am = __activemask();
             const int lane = threadIdx.x & 31;
             const int leader = __ffs(am) - 1;
@@ -330,7 +340,7 @@ __global__ void __launch_bounds__(256) k_graph_hop(const WalkView V, const WalkO
 }
 
 // Records the hop loop of one walk call on the stream (start kernel, then
-// cap - 2 hop kernels alternating the two active lists, each preceded by a
+// cap - 1 hop kernels alternating the two active lists, each preceded by a
 // reset of the list it fills).  Used under stream capture.
 static void record_graph_walk(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t grid)
 {
@@ -345,7 +355,10 @@ static void record_graph_walk(tempest_t *h, const WalkView &V, const WalkOut &O,
     S.n_next = ctr;
     cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), st);
     k_coop_start<<<(unsigned)grid, 256, 0, st>>>(V, O, S);
-    for (int32_t step = 0; step + 2 < O.cap; step++) {
+    // cap - 1 hop kernels: a walk gains at most one node per kernel and a
+    // PER_NODE walk starts with one (edge starts begin with two; their last
+    // kernel then finds an empty list)
+    for (int32_t step = 0; step + 1 < O.cap; step++) {
         const int src = step & 1, dst = src ^ 1;
         S.next_active = h->co_act[dst].as<int32_t>();
         S.n_next = ctr + dst;
@@ -418,7 +431,7 @@ int graph_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launch
         }
     }
     if (own_stream) cudaStreamDestroy(cap_stream);
-    launches += 1 + (O.cap > 2 ? O.cap - 2 : 0);
+    launches += 1 + (O.cap > 1 ? O.cap - 1 : 0);
     h->graph_launches++;
     return rc;
 }

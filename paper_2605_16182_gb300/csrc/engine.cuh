@@ -31,7 +31,7 @@ struct DBuf {
 // Small device-side record the ingest kernels fill and the host reads back.
 struct IngestScratch {
     long long ts_min, ts_max;
-    int max_id, neg_id;
+    int max_id, neg_id;  // neg_id: bit 0 a negative id, bit 1 an INT64_MIN timestamp
     unsigned long long late, unsorted;
     long long cut;          // new cut-off
     int has_cut, pad0;
@@ -151,6 +151,10 @@ struct tempest {
     tw::DBuf bkt;        // int32 tables (each big node's base is in its NodeRange)
     tw::DBuf big_node, big_t, big_c;
     int64_t bkt_ver = -1;
+    // active nodes in id order, for PER_NODE starts (built lazily per state)
+    tw::DBuf pn_nodes;
+    int64_t n_pn = 0;
+    int64_t pn_ver = -1;
     int64_t n_big = 0;
     int bkt_log = 2;     // log2 of the mean groups per bucket
 
@@ -216,6 +220,7 @@ struct WalkRequest {
     int bias;                  // when bias_arr == nullptr
     const uint8_t *bias_arr;   // device, nullable
     int start_policy;
+    int64_t pn_k;              // PER_NODE: walks per active node
     uint64_t seed;
     int32_t *node;             // device
     int64_t *ts;               // device
@@ -225,6 +230,10 @@ int walks_run(tempest_t *h, const WalkRequest &rq);
 // builds the time-bucket tables of the live state on the handle's stream
 // (no-op when they are current); every walk form calls it before launching
 int prepare_walk_index(tempest_t *h);
+// lists the active nodes of the live state in id order (no-op when current)
+int prepare_active_nodes(tempest_t *h);
+// walks per active node of a PER_NODE request (capi.cu)
+int per_node_k(tempest_t *h, int start_policy, int64_t n_walks, int64_t &k, const char *who);
 int sample_index_run(tempest_t *h, const uint64_t *ub, const int64_t *n, int64_t count, int bias, double lambda,
                      int64_t *out);
 

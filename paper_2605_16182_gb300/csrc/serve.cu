@@ -36,7 +36,7 @@ static int build_table(tempest_t *h, const tempest_walk_request *reqs, int n, Re
     total = 0;
     for (int i = 0; i < n; i++) {
         const tempest_walk_request &q = reqs[i];
-        if (q.n_walks < 0 || q.max_len < 2 || q.start_policy < 0 || q.start_policy > 1 ||
+        if (q.n_walks < 0 || q.max_len < 2 || q.start_policy < 0 || q.start_policy > TEMPEST_START_PER_NODE ||
             (!q.bias_arr && (q.bias < 0 || q.bias > 2)))
             return fail(h, TEMPEST_EINVAL, "walk request %d: bad n_walks, max_len, bias or start policy", i);
         if (q.n_walks > 0 && (!is_device_ptr(q.node) || !is_device_ptr(q.ts) || !is_device_ptr(q.len)))
@@ -44,6 +44,8 @@ static int build_table(tempest_t *h, const tempest_walk_request *reqs, int n, Re
         if ((q.max_len_arr && !is_device_ptr(q.max_len_arr)) || (q.bias_arr && !is_device_ptr(q.bias_arr)))
             return fail(h, TEMPEST_EINVAL, "walk request %d: per-walk arrays must be device memory", i);
         ReqDesc &d = out[i];
+        int rc = per_node_k(h, q.start_policy, q.n_walks, d.pn_k, "walk request");
+        if (rc) return rc;
         d.n_walks = q.n_walks;
         d.offset = total;
         d.len_arr = q.max_len_arr;

@@ -30,6 +30,8 @@ struct WalkView {
     const Entry *ent;
     // time buckets of nodes with at least BKT_MIN_G groups (null: none)
     const int32_t *bkt;
+    // active nodes in id order (PER_NODE starts; null when not built)
+    const int32_t *pn_nodes;
     int bkt_log;
     int directed;
     ExpRate rate_hop, rate_start;
@@ -51,6 +53,7 @@ struct WalkOut {
     int bias;
     const uint8_t *bias_arr;
     int start_policy;
+    int64_t pn_k;  // PER_NODE: walks per active node
     uint64_t seed;
     int32_t *node;
     int64_t *ts;
@@ -253,6 +256,7 @@ struct ReqDesc {
     int32_t max_len;
     int32_t bias;
     int32_t start_policy;
+    int64_t pn_k;  // PER_NODE: walks per active node
 };
 
 WalkView make_view(tempest_t *h);

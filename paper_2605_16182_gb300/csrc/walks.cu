@@ -33,36 +33,49 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
         int64_t *trow = O.ts + w * (int64_t)O.cap;
         int32_t len = 0;
         if (V.m > 0) {
-            // start edge (hop 0)
-            Rand4 r = walk_rand(O.seed, (uint64_t)w, 0u);
-            const uint64_t k1 = u53_bits(r.r0, r.r1);
-            const uint64_t k2 = u53_bits(r.r2, r.r3);
-            int64_t k;
-            if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
-                k = uniform_index_k(k1, V.m);
+            int32_t v;
+            int64_t t;
+            Rand4 r;
+            if (O.start_policy == TEMPEST_START_PER_NODE) {
+                // the walk starts at an active node before every live edge
+                v = __ldg(V.pn_nodes + w / O.pn_k);
+                t = INT64_MIN;
+                nrow[0] = v;
+                trow[0] = INT64_MIN;
+                len = 1;
             } else {
-                const int64_t g = sampler_index_k(k1, V.G, bias, V.rate_start);
-                int64_t a, b;
-                ts_group_range(V, g, a, b);
-                k = a + uniform_index_k(k2, b - a);
+                // start edge (hop 0)
+                r = walk_rand(O.seed, (uint64_t)w, 0u);
+                const uint64_t k1 = u53_bits(r.r0, r.r1);
+                const uint64_t k2 = u53_bits(r.r2, r.r3);
+                int64_t k;
+                if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
+                    k = uniform_index_k(k1, V.m);
+                } else {
+                    const int64_t g = sampler_index_k(k1, V.G, bias, V.rate_start);
+                    int64_t a, b;
+                    ts_group_range(V, g, a, b);
+                    k = a + uniform_index_k(k2, b - a);
+                }
+                int32_t s = V.st_src[k], d = V.st_dst[k];
+                const int64_t t0 = V.st_ts[k];
+                if (!V.directed && (r.r3 & 1u)) {
+                    const int32_t x = s;
+                    s = d;
+                    d = x;
+                }
+                nrow[0] = s;
+                nrow[1] = d;
+                trow[0] = INT64_MIN;
+                trow[1] = t0;
+                len = 2;
+                hops++;
+                bytes += START_MODEL_BYTES;
+                v = d;
+                t = t0;
             }
-            int32_t s = V.st_src[k], d = V.st_dst[k];
-            const int64_t t0 = V.st_ts[k];
-            if (!V.directed && (r.r3 & 1u)) {
-                const int32_t x = s;
-                s = d;
-                d = x;
-            }
-            nrow[0] = s;
-            nrow[1] = d;
-            trow[0] = INT64_MIN;
-            trow[1] = t0;
-            len = 2;
-            hops++;
-            bytes += START_MODEL_BYTES;
-            int32_t v = d;
-            int64_t t = t0;
-            for (uint32_t h = 1; len < L; h++) {
+            while (len < L) {
+                const uint32_t h = (uint32_t)(len - 1);  // counter of the draw for position len
                 int32_t g0, g1;
                 node_groups(V, v, g0, g1);
                 const int32_t c = first_later(V, v, g0, g1, t);
@@ -122,6 +135,7 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
 enum : int {
     S_FETCH = 0,   // needs a walk
     S_NEW,         // walk assigned: draw the start
+    S_PNODE,       // PER_NODE: start node loaded
     S_SGROUP,      // start timestamp group offsets loaded
     S_EDGE,        // start edge loaded
     S_RANGE,       // node record loaded (groups, bucket base, first / last ts)
@@ -187,6 +201,7 @@ struct OneReq {
     __device__ __forceinline__ int64_t *trow(const Ctx &c) const { return O.ts + c.w * (int64_t)O.cap; }
     __device__ __forceinline__ void finish(const Ctx &c, int32_t len) const { O.len[c.w] = len; }
     __device__ __forceinline__ int32_t cap(const Ctx &) const { return O.cap; }
+    __device__ __forceinline__ int64_t pn_k(const Ctx &) const { return O.pn_k; }
     __device__ __forceinline__ WalkCounters *cnt() const { return O.cnt; }
 };
 
@@ -236,6 +251,7 @@ struct ManyReq {
     }
     __device__ __forceinline__ void finish(const Ctx &c, int32_t len) const { reqs[c.r].len[c.w] = len; }
     __device__ __forceinline__ int32_t cap(const Ctx &c) const { return reqs[c.r].cap; }
+    __device__ __forceinline__ int64_t pn_k(const Ctx &c) const { return reqs[c.r].pn_k; }
     __device__ __forceinline__ WalkCounters *cnt() const { return counters; }
 };
 
@@ -304,6 +320,11 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                     finish = true;
                     break;
                 }
+                if (Pv.policy(cx) == TEMPEST_START_PER_NODE) {
+                    z0 = __ldg(V.pn_nodes + (int64_t)(Pv.wid(cx) / (uint64_t)Pv.pn_k(cx)));
+                    s.state = S_PNODE;
+                    break;
+                }
                 const Rand4 r = walk_rand(Pv.seed(cx), Pv.wid(cx), 0u);
                 const uint64_t u1 = u53_bits(r.r0, r.r1);
                 s.ud = u53_bits(r.r2, r.r3);
@@ -320,6 +341,19 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                     z1 = __ldg(V.tg + g + 1);
                     s.state = S_SGROUP;
                 }
+                break;
+            }
+            case S_PNODE: {
+                // the walk starts at node z0 before every live edge; its
+                // first hop (Philox counter 0) may take any of them
+                Pv.nrow(cx)[0] = z0;
+                Pv.trow(cx)[0] = INT64_MIN;
+                s.len = 1;
+                s.hop = 0;
+                s.v = z0;
+                s.t = INT64_MIN;
+                load_range(V.ngr + z0, z0, z1, z2, y0, y1);
+                s.state = S_RANGE;
                 break;
             }
             case S_SGROUP: {
@@ -641,6 +675,7 @@ WalkView make_view(tempest_t *h)
     V.ent = h->ent.as<Entry>();
     const bool bk = h->n_big > 0 && h->bkt_ver == h->state_ver;
     V.bkt = bk ? h->bkt.as<int32_t>() : nullptr;
+    V.pn_nodes = h->pn_ver == h->state_ver ? h->pn_nodes.as<int32_t>() : nullptr;
     V.bkt_log = h->bkt_log;
     V.directed = h->directed;
     const double ls = h->lam_start > 0.0 ? h->lam_start : (h->G > 0 ? 1.0 / (double)h->G : 1.0);
@@ -666,6 +701,7 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     O.bias = rq.bias;
     O.bias_arr = rq.bias_arr;
     O.start_policy = rq.start_policy;
+    O.pn_k = rq.pn_k;
     O.seed = rq.seed;
     O.node = rq.node;
     O.ts = rq.ts;

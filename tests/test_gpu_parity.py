@@ -309,3 +309,50 @@ def test_sliding_window_moves_store_and_regions(directed):
         ingest_both(eng, orc, s, d, ts)
         assert_state_equal(eng.state(), orc.state())
     check_walks(eng, orc, 3000, 16, seed=1, biases=(0, 2))
+
+
+# ------------------------------------------------------------ PER_NODE starts
+@pytest.mark.parametrize("directed", [1, 0])
+def test_per_node_walks_all_forms(directed):
+    """K walks from every active node, in id order; bit-exact with the
+    oracle for uniform and linear bias, the boundary rule for exponential,
+    in every walk form, after streaming ingest with eviction."""
+    spec = synth.config_mid(scale=0.005)
+    eng, orc = pair(spec.window, directed)
+    for i, (_, s, d, t) in enumerate(spec.batches(last=6)):
+        ingest_both(eng, orc, s.numpy(), d.numpy(), t.numpy())
+    na = eng.active_nodes()
+    assert na == len(orc.active_nodes()) > 0
+    for K in (1, 3):
+        check_walks(eng, orc, K * na, 12, policy=_lib.START_PER_NODE, seed=K)
+    with pytest.raises(_lib.TempestError) as e:
+        eng.walks(na + 1, 8, start_policy=_lib.START_PER_NODE)
+    assert e.value.code == _lib.TEMPEST_EINVAL
+
+
+def test_per_node_walks_in_a_batched_launch():
+    spec = synth.config_mid(scale=0.005)
+    eng, orc = pair(spec.window, 1)
+    for _, s, d, t in spec.batches(last=3):
+        ingest_both(eng, orc, s.numpy(), d.numpy(), t.numpy())
+    na = eng.active_nodes()
+    alone = [x.clone() for x in eng.walks(2 * na, 10, bias=2, start_policy=_lib.START_PER_NODE, seed=4)]
+    outs = (torch.empty((2 * na, 10), dtype=torch.int32, device="cuda"),
+            torch.empty((2 * na, 10), dtype=torch.int64, device="cuda"),
+            torch.empty((2 * na,), dtype=torch.int32, device="cuda"))
+    outs2 = (torch.empty((500, 10), dtype=torch.int32, device="cuda"),
+             torch.empty((500, 10), dtype=torch.int64, device="cuda"),
+             torch.empty((500,), dtype=torch.int32, device="cuda"))
+    other = _lib.make_request(500, 10, 0, 0, 7, *outs2)
+    r = _lib.make_request(2 * na, 10, 2, _lib.START_PER_NODE, 4, *outs)
+    _lib.tempest_walks_batch(eng.h, [other, r])
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(alone, outs))
+
+
+def test_int64_min_timestamp_is_rejected():
+    eng, _ = pair(0, 1)
+    with pytest.raises(_lib.TempestError) as e:
+        eng.ingest(torch.tensor([0], dtype=torch.int32).cuda(), torch.tensor([1], dtype=torch.int32).cuda(),
+                   torch.tensor([np.iinfo(np.int64).min], dtype=torch.int64).cuda())
+    assert e.value.code == _lib.TEMPEST_EINVAL
