@@ -16,6 +16,9 @@ Printed (rank 0, one JSON line):
                   (inputs copied in, walks copied out inside the timing);
   cpu_baseline    the CPU oracle on a bounded sample of the workload.
 
+Before the timed steps the autotuner picks the walk form and its knobs on the
+warmed-up window (outside the timing; --no-autotune keeps --sched).
+
 ``--impl reference`` times the CPU oracle (the reference arm of this build).
 Under torchrun every rank holds a replica of the window and draws its own
 walks (replicas only: nothing is exchanged on the data path).
@@ -52,7 +55,8 @@ def parse():
     p.add_argument("--workload", default="stream", choices=["stream", "batched", "serve"])
     p.add_argument("--requests", type=int, default=2000)
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--autotune", action="store_true", help="pick the walk form and knobs on the warm state")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="keep --sched instead of letting the autotuner pick the walk form and knobs")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
