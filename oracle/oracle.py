@@ -21,7 +21,7 @@ SRC = os.path.join(HERE, "tempest_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
 
-BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP = 0, 1, 2
+BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP, BIAS_EXP_WEIGHT = 0, 1, 2, 3
 START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 
 
@@ -55,6 +55,9 @@ def lib():
         L.orc_walks.argtypes = [vp, i64, vp, i32, vp, i32, vp, ctypes.c_int, ctypes.c_int, i64, u64,
                                 vp, vp, vp, vp, vp]
         L.orc_counts.argtypes = [vp, vp]
+        L.orc_set_weight_rate.argtypes = [vp, dbl]
+        L.orc_weight_pick.argtypes = [vp, vp, i64, dbl, dbl, vp]
+        L.orc_weight_pick.restype = i64
         L.orc_active_nodes.argtypes = [vp, vp]
         L.orc_active_nodes.restype = i64
         L.orc_export_live.argtypes = [vp, vp, vp, vp]
@@ -165,6 +168,10 @@ class Oracle:
         return dict(counts=c, src=src, dst=dst, ts=ts, ts_group_off=tgo, node_off=node_off,
                     node_order=node_order[:M], node_group_off=ngo, node_gidx=gidx)
 
+    def set_weight_rate(self, lambda_w):
+        if lib().orc_set_weight_rate(self._h, float(lambda_w)) != 0:
+            raise ValueError("bad weight rate")
+
     def active_nodes(self):
         """Nodes with at least one live entry in the node view, in id order."""
         n = int(lib().orc_active_nodes(self._h, None))
@@ -208,3 +215,13 @@ class Oracle:
         if rc != 0:
             raise ValueError("orc_walks rc=%d" % rc)
         return node, ts, ln, margin, (float(nbytes[0]) if with_bytes else None)
+
+
+def weight_pick(ts, size, lam, u):
+    """The weight-based sampler over groups with timestamps ts and sizes size
+    (ascending): (group index, relative margin of the draw)."""
+    ts = np.ascontiguousarray(ts, dtype=np.int64)
+    size = np.ascontiguousarray(size, dtype=np.int64)
+    mg = np.zeros(1, np.float64)
+    j = int(lib().orc_weight_pick(_p(ts), _p(size), int(ts.shape[0]), float(lam), float(u), _p(mg)))
+    return j, float(mg[0])

@@ -58,6 +58,7 @@
 #define BIAS_UNIFORM 0
 #define BIAS_LINEAR 1
 #define BIAS_EXP 2
+#define BIAS_EXP_WEIGHT 3
 
 #define START_UNIFORM_EDGE 0
 #define START_BIASED_TS 1
@@ -79,6 +80,7 @@ typedef struct orc {
     int directed;
     double lambda_hop;   /* exponential rate per timestamp group for hops */
     double lambda_start; /* > 0: fixed rate for start selection; 0: 1/G_tot */
+    double lambda_w;     /* weight-based sampler: rate per timestamp unit */
 
     orc_edge *live; /* live edges in (ts, seq) order */
     int64_t m;
@@ -211,6 +213,7 @@ orc *orc_create(int64_t window, int directed)
     o->directed = directed ? 1 : 0;
     o->lambda_hop = 1.0;
     o->lambda_start = 0.0;
+    o->lambda_w = 1e-9;
     o->ts_group_off = (int64_t *)calloc(1, sizeof(int64_t));
     o->node_off = (int64_t *)calloc(1, sizeof(int64_t));
     o->node_gidx = (int64_t *)calloc(1, sizeof(int64_t));
@@ -228,6 +231,45 @@ void orc_destroy(orc *o)
     free(o->node_group_off);
     free(o->node_gidx);
     free(o);
+}
+
+int orc_set_weight_rate(orc *o, double lambda_w)
+{
+    if (!(lambda_w > 0.0)) return ORC_EINVAL;
+    o->lambda_w = lambda_w;
+    return ORC_OK;
+}
+
+/*
+ * The weight-based exponential sampler of Sec. 2.5 over n timestamp groups
+ * (ascending timestamps ts[0..n), sizes size[0..n)): every edge weighs
+ * exp(lambda (t_e - t_min)) with t_min = ts[0], the earliest timestamp of
+ * the neighbourhood; r = u * (total weight); the result is the group holding
+ * the first edge whose running sum reaches r (edges of one group weigh the
+ * same, so the group follows from the group sums).  margin (nullable)
+ * receives the distance of r to the nearer boundary of that group's
+ * interval, relative to the total.
+ */
+int64_t orc_weight_pick(const int64_t *ts, const int64_t *size, int64_t n, double lambda, double u, double *margin)
+{
+    double total = 0.0;
+    for (int64_t g = 0; g < n; g++) total += (double)size[g] * exp(lambda * (double)(ts[g] - ts[0]));
+    const double r = u * total;
+    double run = 0.0;
+    for (int64_t g = 0; g < n; g++) {
+        const double before = run;
+        run += (double)size[g] * exp(lambda * (double)(ts[g] - ts[0]));
+        if (run >= r || g == n - 1) {
+            if (margin) {
+                double a = r - before, b = run - r;
+                if (a < 0) a = -a;
+                if (b < 0) b = -b;
+                *margin = (a < b ? a : b) / total;
+            }
+            return g;
+        }
+    }
+    return n - 1;
 }
 
 int orc_set_bias_params(orc *o, double lambda_hop, double lambda_start)
@@ -475,9 +517,11 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
         if (start_policy == START_UNIFORM_EDGE) {
             k = uniform_index(u1, o->m);
         } else {
-            double x = orc_sampler_x(u1, o->G_tot, bias, lambda_start);
-            int64_t g = orc_sampler_index(u1, o->G_tot, bias, lambda_start);
-            if (margin && bias != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
+            /* the weight-based bias starts like the index-based exponential */
+            const int sb = bias == BIAS_EXP_WEIGHT ? BIAS_EXP : bias;
+            double x = orc_sampler_x(u1, o->G_tot, sb, lambda_start);
+            int64_t g = orc_sampler_index(u1, o->G_tot, sb, lambda_start);
+            if (margin && sb != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
             int64_t a = o->ts_group_off[g], size = o->ts_group_off[g + 1] - a;
             k = a + uniform_index(u2, size);
         }
@@ -506,6 +550,27 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
         if (bias == BIAS_UNIFORM) {
             int64_t e0 = o->node_group_off[c], e1 = o->node_off[v + 1];
             idx = e0 + uniform_index(u1, e1 - e0);
+        } else if (bias == BIAS_EXP_WEIGHT) {
+            const int64_t n = g1 - c;
+            int64_t *gts = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+            int64_t *gsz = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+            if (!gts || !gsz) {
+                free(gts);
+                free(gsz);
+                break;
+            }
+            for (int64_t g = 0; g < n; g++) {
+                const int64_t a = o->node_group_off[c + g], b = o->node_group_off[c + g + 1];
+                gts[g] = slot_ts(o, o->node_order[a]);
+                gsz[g] = b - a;
+            }
+            double mg = INFINITY;
+            const int64_t j = orc_weight_pick(gts, gsz, n, o->lambda_w, u1, &mg);
+            free(gts);
+            free(gsz);
+            if (margin) margin[len] = mg;
+            int64_t e0 = o->node_group_off[c + j], e1 = o->node_group_off[c + j + 1];
+            idx = e0 + uniform_index(u2, e1 - e0);
         } else {
             int64_t n = g1 - c;
             double x = orc_sampler_x(u1, n, bias, o->lambda_hop);
@@ -577,7 +642,7 @@ int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
         uint64_t w = ids ? (uint64_t)ids[i] : (uint64_t)i;
         int32_t L = max_len_arr ? max_len_arr[i] : max_len;
         int b = bias_arr ? (int)bias_arr[i] : bias;
-        if (L < 2 || L > max_len_cap || b < 0 || b > 2) {
+        if (L < 2 || L > max_len_cap || b < 0 || b > 3) {
             free(active);
             return ORC_EINVAL;
         }

@@ -105,12 +105,20 @@ def gamma(live, directed, v, t):
     return [(e[3], e[0]) for e in g]
 
 
-def hop_distribution(live, directed, v, t, bias, lam):
-    """{(other, ts): probability} of the next hop, or {} when Gamma is empty."""
+def hop_distribution(live, directed, v, t, bias, lam, lam_w=None):
+    """{(other, ts): probability} of the next hop, or {} when Gamma is empty.
+    Bias 3 (weight-based): every edge of Gamma weighs exp(lam_w (ts - t_min))."""
     g = gamma(live, directed, v, t)
     if not g:
         return {}
     dist = {}
+    if bias == 3:
+        t_min = min(ts for _, ts in g)
+        w = [math.exp(lam_w * (ts - t_min)) for _, ts in g]
+        tot = sum(w)
+        for e, x in zip(g, w):
+            dist[e] = dist.get(e, 0.0) + x / tot
+        return dist
     if bias == 0:
         for e in g:
             dist[e] = dist.get(e, 0.0) + 1.0 / len(g)
@@ -152,7 +160,7 @@ def start_distribution(live, directed, policy, bias, lam_start):
     return dist
 
 
-def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start, start_node=None):
+def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start, start_node=None, lam_w=None):
     """Exact probability of every complete walk (tuple of (node, ts) pairs).
     With start_node the walk starts at that node and its first hop may take
     any of the node's live edges (the per-node start policy)."""
@@ -165,7 +173,7 @@ def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start,
         if len(path) >= max_len:
             out[tuple(path)] = out.get(tuple(path), 0.0) + p
             return
-        d = hop_distribution(live, directed, v, t, bias, lam_hop)
+        d = hop_distribution(live, directed, v, t, bias, lam_hop, lam_w)
         if not d:
             out[tuple(path)] = out.get(tuple(path), 0.0) + p
             return
@@ -175,7 +183,8 @@ def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start,
     if start_node is not None:
         rec([(start_node, None)], 1.0)
         return out
-    for (a, b, ts), p in start_distribution(live, directed, policy, bias, lam_start).items():
+    sb = 2 if bias == 3 else bias  # the weight-based bias starts like the index-based exponential
+    for (a, b, ts), p in start_distribution(live, directed, policy, sb, lam_start).items():
         rec([(a, None), (b, ts)], p)
     return out
 

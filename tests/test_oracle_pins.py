@@ -264,7 +264,7 @@ def _walk_key(node_row, ts_row, ln):
 
 @pytest.mark.parametrize("directed,bias,policy", [
     (True, 0, 0), (True, 1, 0), (True, 2, 0), (True, 1, 1), (True, 2, 1), (True, 0, 1),
-    (False, 0, 0), (False, 2, 1),
+    (False, 0, 0), (False, 2, 1), (True, 3, 0), (False, 3, 1),
 ])
 def test_walk_distribution_matches_enumeration(directed, bias, policy):
     from scipy.stats import chisquare
@@ -274,11 +274,13 @@ def test_walk_distribution_matches_enumeration(directed, bias, policy):
     ts = [1, 2, 2, 3, 4, 5, 5, 6, 7, 6]
     lam_hop, lam_start = 0.7, 0.4
     max_len = 4
+    lam_w = 0.45
     o = O.Oracle(window=0, directed=directed)
     o.ingest(src, dst, ts)
     o.set_bias_params(lam_hop, lam_start)
+    o.set_weight_rate(lam_w)
     live = brute.window_state([(src, dst, ts)], 0, directed)[-1]["live"]
-    dist = brute.walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start)
+    dist = brute.walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start, lam_w=lam_w)
     assert abs(sum(dist.values()) - 1.0) < 1e-9
     n = 60_000
     node, tsa, ln, _, _ = o.walks(n, max_len, bias=bias, start_policy=policy, seed=99)
@@ -332,6 +334,47 @@ def test_per_node_walks_match_enumeration(directed, bias):
         exp = np.array([dist[k] * K for k in keys], np.float64)
         exp *= obs.sum() / exp.sum()
         assert chisquare(obs, exp)[1] > 1e-3, v
+
+
+# ------------------------------------------------- weight-based sampler (Sec. 2.5)
+@pytest.mark.parametrize("lam", [1.0, 0.3, 2.5])
+def test_weight_sampler_worked_example(lam):
+    """Node with live edges at ts {1, 2, 2, 5}, t = 1: Gamma holds the two
+    edges at 2 and the one at 5; weights exp(lam (ts - 2)) give group 0 the
+    probability 2 / (2 + e^{3 lam}), so u below that picks group 0."""
+    b = 2.0 / (2.0 + math.exp(3.0 * lam))
+    for u, want in ((0.0, 0), (b * (1 - 1e-9), 0), (b * (1 + 1e-9), 1), (0.999999, 1), (b / 2, 0)):
+        j, mg = O.weight_pick([2, 5], [2, 1], lam, u)
+        assert j == want, (u, j)
+    # the margin measures the distance to the boundary
+    assert O.weight_pick([2, 5], [2, 1], lam, b * (1 + 1e-9))[1] < 1e-8
+
+
+def test_weight_sampler_frequencies_and_invariances():
+    from scipy.stats import chisquare
+    rng = np.random.default_rng(4)
+    for trial in range(6):
+        n = int(rng.integers(2, 12))
+        ts = np.cumsum(rng.integers(1, 50, n)).astype(np.int64)
+        size = rng.integers(1, 4, n).astype(np.int64)
+        lam = float(rng.choice([0.001, 0.02, 0.1]))
+        w = size * np.exp(lam * (ts - ts[0]).astype(np.float64))
+        p = w / w.sum()
+        us = rng.random(20000)
+        picks = np.array([O.weight_pick(ts, size, lam, u)[0] for u in us])
+        obs = np.bincount(picks, minlength=n).astype(np.float64)
+        keep = p * len(us) > 5
+        exp = p * len(us)
+        assert chisquare(obs[keep], exp[keep] * obs[keep].sum() / exp[keep].sum())[1] > 1e-3
+        # shifting every timestamp changes nothing; the pick is the inverse CDF
+        for u in us[:200]:
+            j = O.weight_pick(ts, size, lam, u)[0]
+            assert O.weight_pick(ts + 10**12, size, lam, u)[0] == j
+            cdf = np.cumsum(p)
+            assert j == int(np.searchsorted(cdf, u * (1 - 1e-12), "left")) or abs(cdf[j - 1] - u) < 1e-9
+    # a vanishing rate weighs every edge the same
+    j = [O.weight_pick([0, 7, 9], [1, 2, 1], 1e-15, u)[0] for u in (0.2, 0.3, 0.7, 0.8)]
+    assert j == [0, 1, 1, 2]
 
 
 def test_per_node_walks_need_a_whole_number_per_node():
