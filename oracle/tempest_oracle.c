@@ -246,19 +246,23 @@ int orc_set_weight_rate(orc *o, double lambda_w)
  * exp(lambda (t_e - t_min)) with t_min = ts[0], the earliest timestamp of
  * the neighbourhood; r = u * (total weight); the result is the group holding
  * the first edge whose running sum reaches r (edges of one group weigh the
- * same, so the group follows from the group sums).  margin (nullable)
- * receives the distance of r to the nearer boundary of that group's
- * interval, relative to the total.
+ * same, so the group follows from the group sums).  Every weight is
+ * multiplied by exp(-lambda (t_max - t_min)), a common factor that cancels
+ * from r and the running sum: the weights become exp(lambda (t_e - t_max))
+ * <= 1, which stays finite where the raw form overflows (lambda (t_max -
+ * t_min) > 709).  margin (nullable) receives the distance of r to the
+ * nearer boundary of that group's interval, relative to the total.
  */
 int64_t orc_weight_pick(const int64_t *ts, const int64_t *size, int64_t n, double lambda, double u, double *margin)
 {
+    const int64_t tmax = ts[n - 1];
     double total = 0.0;
-    for (int64_t g = 0; g < n; g++) total += (double)size[g] * exp(lambda * (double)(ts[g] - ts[0]));
+    for (int64_t g = 0; g < n; g++) total += (double)size[g] * exp(lambda * (double)(ts[g] - tmax));
     const double r = u * total;
     double run = 0.0;
     for (int64_t g = 0; g < n; g++) {
         const double before = run;
-        run += (double)size[g] * exp(lambda * (double)(ts[g] - ts[0]));
+        run += (double)size[g] * exp(lambda * (double)(ts[g] - tmax));
         if (run >= r || g == n - 1) {
             if (margin) {
                 double a = r - before, b = run - r;

@@ -372,6 +372,10 @@ def test_weight_sampler_frequencies_and_invariances():
             assert O.weight_pick(ts + 10**12, size, lam, u)[0] == j
             cdf = np.cumsum(p)
             assert j == int(np.searchsorted(cdf, u * (1 - 1e-12), "left")) or abs(cdf[j - 1] - u) < 1e-9
+    # a rate whose raw weights overflow exp (lambda (t_max - t_min) = 3000)
+    # still gives the limit: all mass on the newest group, a finite margin
+    j, mg = O.weight_pick([0, 10, 30000], [5, 5, 1], 0.1, 0.999)
+    assert j == 2 and math.isfinite(mg)
     # a vanishing rate weighs every edge the same
     j = [O.weight_pick([0, 7, 9], [1, 2, 1], 1e-15, u)[0] for u in (0.2, 0.3, 0.7, 0.8)]
     assert j == [0, 1, 1, 2]
