@@ -53,7 +53,13 @@ enum {
  * approximation cannot return the newest group).  For LINEAR and EXP an edge
  * is then drawn uniformly inside the chosen group (ties broken uniformly,
  * Sec. 2.1). */
-enum { TEMPEST_BIAS_UNIFORM = 0, TEMPEST_BIAS_LINEAR = 1, TEMPEST_BIAS_EXP = 2 };
+enum { TEMPEST_BIAS_UNIFORM = 0, TEMPEST_BIAS_LINEAR = 1, TEMPEST_BIAS_EXP = 2,
+       /* weight-based exponential (Sec. 2.5, the paper's default sampler):
+        * every edge of Gamma_t(v) weighs exp(lambda_w (t_e - t_min)); an
+        * inverse-CDF draw on the running weight (u1) picks the timestamp
+        * group, an edge of it is uniform (u2).  A BIASED_TS start draws as
+        * TEMPEST_BIAS_EXP does.  See tempest_set_weight_rate. */
+       TEMPEST_BIAS_EXP_WEIGHT = 3 };
 
 /* Start selection (Sec. 2.3, timestamp-grouped view; Sec. 3 workloads).
  * UNIFORM_EDGE: a live edge uniformly.  BIASED_TS: a timestamp group of the
@@ -121,6 +127,14 @@ int tempest_create(int64_t window, int directed, tempest_t **out);
 
 /* Free the handle and all device memory it owns.  NULL is accepted. */
 int tempest_destroy(tempest_t *h);
+
+/* Rate lambda_w > 0 (per timestamp unit) of the weight-based sampler
+ * (TEMPEST_BIAS_EXP_WEIGHT; default 1e-9, i.e. per second for nanosecond
+ * timestamps).  Group weights are kept in the index from the first call of
+ * this function or the first weight-based walk on, at a cost per ingested
+ * group; the first walk call after a change recomputes all of them.  EINVAL
+ * on lambda_w <= 0 or not finite. */
+int tempest_set_weight_rate(tempest_t *h, double lambda_w);
 
 /* Queue all further device work of the handle on stream (a cudaStream_t). */
 int tempest_set_stream(tempest_t *h, void *stream);

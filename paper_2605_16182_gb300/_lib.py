@@ -22,7 +22,7 @@ TEMPEST_ECUDA = -3
 TEMPEST_ETIMEDOUT = -4
 TEMPEST_EBUSY = -5
 
-BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP = 0, 1, 2
+BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP, BIAS_EXP_WEIGHT = 0, 1, 2, 3
 START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH = 0, 1, 2, 3
 TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS = 0, 1, 2, 3
@@ -42,7 +42,7 @@ EXPORTED = (
     "tempest_server_submit_ingest", "tempest_server_progress", "tempest_server_status",
     "tempest_server_release", "tempest_server_drain", "tempest_server_stats",
     "tempest_set_tuning", "tempest_get_tuning", "tempest_autotune", "tempest_autotune_mixed",
-    "tempest_active_nodes",
+    "tempest_active_nodes", "tempest_set_weight_rate",
 )
 NOALLOC_MAX_EDGES = 262144
 
@@ -137,6 +137,7 @@ def load():
     L.tempest_autotune.argtypes = [vp, i64, ctypes.c_int32, ci, ci, ctypes.c_uint64, ctypes.c_int32,
                                    ctypes.POINTER(TuneReport)]
     L.tempest_active_nodes.argtypes = [vp, ctypes.POINTER(i64)]
+    L.tempest_set_weight_rate.argtypes = [vp, dbl]
     L.tempest_autotune_mixed.argtypes = [vp, i64, vp, ctypes.c_int32, vp, ci, ctypes.c_uint64, ctypes.c_int32,
                                          ctypes.POINTER(TuneReport)]
     L.tempest_last_walk_stats.argtypes = [vp, ctypes.POINTER(WalkStats)]
@@ -475,6 +476,10 @@ class Engine:
 
     def get_tuning(self, knob: int) -> int:
         return tempest_get_tuning(self.h, knob)
+
+    def set_weight_rate(self, lambda_w: float):
+        """Rate of the weight-based sampler (TEMPEST_BIAS_EXP_WEIGHT); keeps group weights from now on."""
+        _check(self.h, load().tempest_set_weight_rate(self.h, float(lambda_w)))
 
     def active_nodes(self) -> int:
         """Number of nodes with a live entry: PER_NODE walk counts are multiples of it."""

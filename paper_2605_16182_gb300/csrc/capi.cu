@@ -114,7 +114,8 @@ static void free_all(tempest_t *h)
                     &h->in_stage,  &h->exp_stage, &h->co_node,   &h->co_t,      &h->co_len,    &h->co_act[0],
                     &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt,
                     &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched,   &h->tg2,       &h->nbeg,
-                    &h->pn_nodes};
+                    &h->pn_nodes,  &h->gw,        &h->gs,        &h->wref,      &h->w_cbase,   &h->w_ctot,
+                    &h->w_coff};
     for (DBuf *b : bufs) release(h, *b);
 }
 
@@ -259,7 +260,7 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
     if (cap < 2) return fail(h, TEMPEST_EINVAL, "walks: max_len must be >= 2");
     if (start_policy < TEMPEST_START_UNIFORM_EDGE || start_policy > TEMPEST_START_PER_NODE)
         return fail(h, TEMPEST_EINVAL, "walks: unknown start policy %d", start_policy);
-    if (!bias_arr && (bias < 0 || bias > 2)) return fail(h, TEMPEST_EINVAL, "walks: unknown bias %d", bias);
+    if (!bias_arr && (bias < 0 || bias > 3)) return fail(h, TEMPEST_EINVAL, "walks: unknown bias %d", bias);
     if (n_walks > 0 && (!node || !ts || !len)) return fail(h, TEMPEST_EINVAL, "walks: NULL output");
     if (n_walks > 0 && (int64_t)cap * n_walks / n_walks != (int64_t)cap)
         return fail(h, TEMPEST_EINVAL, "walks: output size overflows");
@@ -281,7 +282,7 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
                             len_arr[i], cap);
     if (host_bias)
         for (int64_t i = 0; i < n_walks; i++)
-            if (bias_arr[i] > 2)
+            if (bias_arr[i] > 3)
                 return fail(h, TEMPEST_EINVAL, "walks_mixed: bias_arr[%lld] = %d unknown", (long long)i, bias_arr[i]);
     if (host_len || host_bias) {
         size_t need = 0;
@@ -323,6 +324,8 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
         if (!dev_len) d_lenout = reinterpret_cast<int32_t *>(p);
     }
     WalkRequest rq{n_walks, cap, max_len, d_len, bias, d_bias, start_policy, pn_k, seed, d_node, d_ts, d_lenout};
+    if (host_bias)
+        for (int64_t i = 0; i < n_walks && !rq.want_w; i++) rq.want_w = bias_arr[i] == TEMPEST_BIAS_EXP_WEIGHT;
     if ((rc = walks_run(h, rq))) return rc;
     if (!dev_ts) cudaMemcpyAsync(ts, d_ts, sizeof(int64_t) * cells, cudaMemcpyDeviceToHost, st);
     if (!dev_node) cudaMemcpyAsync(node, d_node, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st);

@@ -63,6 +63,7 @@ struct NvCounters {
     unsigned long long overflow;      // a pool could not serve a region
     unsigned long long status;        // nonzero: a consistency check failed
     unsigned long long n_dense;       // batch-local node ids handed out
+    unsigned long long w_rebase;      // a group weight's exponent grew too large
 };
 
 // A region move: live entries and groups of one node to fresh regions.
@@ -87,6 +88,7 @@ struct tempest {
     int directed = 1;
     double lam_hop = 1.0;
     double lam_start = 0.0;  // 0: 1 / G_tot
+    double lam_w = 1e-9;     // weight-based sampler rate per timestamp unit
     int sched = TEMPEST_SCHED_STREAM;
     cudaStream_t stream = nullptr;
     void *(*alloc_fn)(size_t, void *) = nullptr;
@@ -141,6 +143,15 @@ struct tempest {
     bool nv_ready = false;
     tw::DBuf nv_tmp, run_node, run_pos, run_g, run_of, fx, run_de, run_dg, ev_nodes, reloc;
     tw::DBuf dense;    // int32 [N+1]: 1 + a batch-local id of each node the batch touches (0 between batches)
+    // weight-based sampler: per-group weights (group size * exp(lam_w (t_g -
+    // wref[v]))) kept by ingest once enabled, and per-node suffix sums of them
+    // built for the walks of a state version
+    tw::DBuf gw, gs;   // double, group pool indexing
+    tw::DBuf wref;     // int64 [N+1] per-node reference time
+    tw::DBuf w_cbase, w_ctot, w_coff;  // suffix-sum chunk lists
+    bool w_on = false;     // weights are maintained
+    bool w_valid = false;  // every live group's weight is current
+    int64_t w_ver = -1;    // state version of the suffix sums
     tw::DBuf touched;  // int32: node of each batch-local id
     int64_t S = 0;     // nodes that own regions (for the bucket index)
     int64_t state_ver = 0;  // bumped by every ingest
@@ -225,6 +236,7 @@ struct WalkRequest {
     int32_t *node;             // device
     int64_t *ts;               // device
     int32_t *len;              // device
+    int want_w = 0;            // per-walk biases known to include the weight-based one
 };
 int walks_run(tempest_t *h, const WalkRequest &rq);
 // builds the time-bucket tables of the live state on the handle's stream
@@ -232,6 +244,11 @@ int walks_run(tempest_t *h, const WalkRequest &rq);
 int prepare_walk_index(tempest_t *h);
 // lists the active nodes of the live state in id order (no-op when current)
 int prepare_active_nodes(tempest_t *h);
+// group weights and their suffix sums for weight-based walks (weights.cu)
+int prepare_weights(tempest_t *h);
+// weights of the groups an append created or grew (weights.cu); runs after
+// the node view scatter of the batch
+int nv_append_weights(tempest_t *h, int64_t nbe);
 // walks per active node of a PER_NODE request (capi.cu)
 int per_node_k(tempest_t *h, int start_policy, int64_t n_walks, int64_t &k, const char *who);
 int sample_index_run(tempest_t *h, const uint64_t *ub, const int64_t *n, int64_t count, int bias, double lambda,

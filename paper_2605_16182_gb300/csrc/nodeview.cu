@@ -412,7 +412,7 @@ struct RelocChunkOp {
 // One warp per chunk of a move: entries copied, group timestamps copied,
 // group starts rebased to the new entry region.
 __global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__restrict__ cbase, int64_t n_reloc,
-                           const uint64_t *__restrict__ tot, Entry *ent, int32_t *ngo, int64_t *ngts)
+                           const uint64_t *__restrict__ tot, Entry *ent, int32_t *ngo, int64_t *ngts, double *gw)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nch = (int64_t)*tot;
@@ -432,6 +432,7 @@ __global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__res
         for (int32_t i = off + lane; i < g_end; i += 32) {
             ngts[x.new_g + i] = ngts[x.old_g + i];
             ngo[x.new_g + i] = ngo[x.old_g + i] - x.old_e + x.new_e;
+            if (gw) gw[x.new_g + i] = gw[x.old_g + i];  // group weights move with their groups
         }
     }
 }
@@ -694,6 +695,7 @@ int nv_build(tempest_t *h)
     h->S = S;
     h->Gn = Gn;
     h->nv_ready = true;
+    h->w_valid = false;  // new regions: the weights are recomputed for the next walks
     return TEMPEST_OK;
 }
 
@@ -789,7 +791,8 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
             if (grid > gcap) grid = gcap;
             k_nv_reloc<<<(unsigned)grid, 256, 0, st>>>(h->reloc.as<Reloc>(), h->nv_tmp.as<int32_t>(), n_reloc,
                                                        part + nb2, h->ent.as<Entry>(), h->ngo.as<int32_t>(),
-                                                       h->ngts.as<int64_t>());
+                                                       h->ngts.as<int64_t>(),
+                                                       h->w_on && h->w_valid && h->gw.p ? h->gw.as<double>() : nullptr);
             h->pending_launches += 4;
         }
         k_nv_scatter<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], it, slot_base(h, new_lo), nbe, h->run_of.as<int32_t>(),
@@ -799,6 +802,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
                                                        h->g_cap, h->ent.as<Entry>(), h->ngo.as<int32_t>(),
                                                        h->ngts.as<int64_t>(), h->ngr.as<NodeRange>(), dc);
         h->pending_launches++;
+        if ((rc = nv_append_weights(h, nbe))) return rc;
     }
     NvCounters *hc = static_cast<NvCounters *>(h->hstat);
     cudaMemcpyAsync(hc, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
@@ -807,6 +811,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         return fail(h, TEMPEST_ECUDA, "node view: consistency check failed (code 0x%llx)",
                     (unsigned long long)hc->status);
     h->Gn += (int64_t)hc->gn_delta;
+    if (hc->w_rebase) h->w_valid = false;  // a weight exponent grew large: move every reference
     h->n_act = (int64_t)hc->n_act;
     h->S = h->n_act;
     h->M = directed ? (h->s_hi - h->s_lo) : 2 * (h->s_hi - h->s_lo);

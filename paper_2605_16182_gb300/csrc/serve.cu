@@ -37,7 +37,7 @@ static int build_table(tempest_t *h, const tempest_walk_request *reqs, int n, Re
     for (int i = 0; i < n; i++) {
         const tempest_walk_request &q = reqs[i];
         if (q.n_walks < 0 || q.max_len < 2 || q.start_policy < 0 || q.start_policy > TEMPEST_START_PER_NODE ||
-            (!q.bias_arr && (q.bias < 0 || q.bias > 2)))
+            (!q.bias_arr && (q.bias < 0 || q.bias > 3)))
             return fail(h, TEMPEST_EINVAL, "walk request %d: bad n_walks, max_len, bias or start policy", i);
         if (q.n_walks > 0 && (!is_device_ptr(q.node) || !is_device_ptr(q.ts) || !is_device_ptr(q.len)))
             return fail(h, TEMPEST_EINVAL, "walk request %d: outputs must be device memory", i);
@@ -60,6 +60,16 @@ static int build_table(tempest_t *h, const tempest_walk_request *reqs, int n, Re
         d.start_policy = q.start_policy;
         total += q.n_walks;
     }
+    return TEMPEST_OK;
+}
+
+// Weight sums are needed when a request asks for the weight-based bias, or
+// may (device per-walk biases) once weights are kept.
+static int prepare_for(tempest_t *h, const ReqDesc *t, int n)
+{
+    for (int i = 0; i < n; i++)
+        if ((!t[i].bias_arr && t[i].bias == TEMPEST_BIAS_EXP_WEIGHT) || (t[i].bias_arr && h->w_on))
+            return prepare_weights(h);
     return TEMPEST_OK;
 }
 
@@ -219,7 +229,7 @@ int launch_wave(tempest_server *s, tempest_server::Wave &wv, int &rc)
     }
     const int n = compact_table(wv.stage, (int)ids.size());
     // derived walk indexes of the current state, built on the handle's stream
-    if ((rc = prepare_walk_index(s->h))) {
+    if ((rc = prepare_walk_index(s->h)) || (rc = prepare_for(s->h, wv.stage, n))) {
         for (uint64_t id : ids) {
             s->reqs[id].state = rc;
             s->reqs[id].t_done = now_s();
@@ -272,6 +282,7 @@ int tempest_walks_batch(tempest_t *h, const tempest_walk_request *reqs, int n_re
     if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "batch table"))) return rc;
     h->kev_valid = false;
     if ((rc = prepare_walk_index(h))) return rc;
+    if ((rc = prepare_for(h, tab.data(), n))) return rc;
     rc = walks_multi_launch(h, h->in_stage.as<ReqDesc>(), n, total, h->wcnt.as<WalkCounters>(), h->stream);
     h->last_ws.n_walks = total;
     h->last_ws.launches = 1;

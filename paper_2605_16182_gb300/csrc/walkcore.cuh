@@ -32,6 +32,9 @@ struct WalkView {
     const int32_t *bkt;
     // active nodes in id order (PER_NODE starts; null when not built)
     const int32_t *pn_nodes;
+    // per-node suffix sums of the group weights (weight-based bias; null when
+    // not built)
+    const double *gs;
     int bkt_log;
     int directed;
     ExpRate rate_hop, rate_start;
@@ -187,11 +190,42 @@ __device__ __forceinline__ void walk_params(const WalkOut &O, int64_t w, int32_t
 {
     L = O.len_arr ? O.len_arr[w] : O.max_len;
     bias = O.bias_arr ? (int)O.bias_arr[w] : O.bias;
-    if (L < 2 || L > O.cap || bias < 0 || bias > 2) {
+    if (L < 2 || L > O.cap || bias < 0 || bias > 3) {
         atomicOr(&O.cnt->status, 1ull);
         L = L < 2 ? 2 : (L > O.cap ? O.cap : L);
-        bias = (bias < 0 || bias > 2) ? BIAS_UNIFORM : bias;
+        bias = (bias < 0 || bias > 3) ? BIAS_UNIFORM : bias;
     }
+}
+
+// Start draws and index-based hops treat the weight-based bias as the
+// index-based exponential; a weight-based walk without weight sums (device
+// bias arrays before the weights were enabled) reports EINVAL and walks as
+// the index-based exponential.
+constexpr int BIAS_EXP_WEIGHT = 3;
+__device__ __forceinline__ int start_bias(int bias) { return bias == BIAS_EXP_WEIGHT ? BIAS_EXP : bias; }
+
+__device__ __forceinline__ int hop_bias(const WalkView &V, int bias, WalkCounters *cnt)
+{
+    if (bias == BIAS_EXP_WEIGHT && !V.gs) {
+        atomicOr(&cnt->status, 1ull);
+        return BIAS_EXP;
+    }
+    return bias;
+}
+
+// Weight-based draw over the groups [c, g1) (Sec. 2.5): the smallest k with
+// gs[k + 1] <= gs[c] (1 - u), i.e. the group whose running weight from c first
+// reaches u gs[c] (k1: the 53-bit integer of u).
+__device__ __forceinline__ int32_t weight_group(const WalkView &V, int32_t c, int32_t g1, uint64_t k1)
+{
+    const double R = __ldg(V.gs + c) * (1.0 - (double)k1 * 0x1.0p-53);
+    int32_t lo = c, hi = g1 - 1;
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(V.gs + mid + 1) <= R) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
 }
 
 // Hop 0: the start edge (s -> d at t0), oriented for undirected graphs.
@@ -205,7 +239,7 @@ __device__ __forceinline__ void start_edge(const WalkView &V, const WalkOut &O, 
     if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
         k = uniform_index_k(k1, V.m);
     } else {
-        const int64_t g = sampler_index_k(k1, V.G, bias, V.rate_start);
+        const int64_t g = sampler_index_k(k1, V.G, start_bias(bias), V.rate_start);
         int64_t a, b;
         ts_group_range(V, g, a, b);
         k = a + uniform_index_k(k2, b - a);
@@ -229,9 +263,15 @@ __device__ __forceinline__ Entry draw_entry(const WalkView &V, const WalkOut &O,
     const Rand4 r = walk_rand(O.seed, (uint64_t)w, hop);
     const uint64_t h1 = u53_bits(r.r0, r.r1);
     int64_t idx;
+    bias = hop_bias(V, bias, O.cnt);
     if (bias == BIAS_UNIFORM) {
         const int32_t e0 = __ldg(V.ngo + c), e1 = __ldg(V.ngo + g1);
         idx = e0 + uniform_index_k(h1, (int64_t)(e1 - e0));
+    } else if (bias == BIAS_EXP_WEIGHT) {
+        const uint64_t h2 = u53_bits(r.r2, r.r3);
+        const int32_t k = weight_group(V, c, g1, h1);
+        const int32_t e0 = __ldg(V.ngo + k), e1 = __ldg(V.ngo + k + 1);
+        idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
     } else {
         const uint64_t h2 = u53_bits(r.r2, r.r3);
         const int64_t j = sampler_index_k(h1, (int64_t)(g1 - c), bias, V.rate_hop);

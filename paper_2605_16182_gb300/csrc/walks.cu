@@ -22,12 +22,12 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
          w += (int64_t)gridDim.x * blockDim.x) {
         int32_t L = O.len_arr ? O.len_arr[w] : O.max_len;
         int bias = O.bias_arr ? (int)O.bias_arr[w] : O.bias;
-        if (L < 2 || L > O.cap || bias < 0 || bias > 2) {
+        if (L < 2 || L > O.cap || bias < 0 || bias > 3) {
             // per-walk arrays that live on the device are checked here: the
             // walk is clamped into its row and the call reports EINVAL
             atomicOr(&O.cnt->status, 1ull);
             L = L < 2 ? 2 : (L > O.cap ? O.cap : L);
-            bias = (bias < 0 || bias > 2) ? BIAS_UNIFORM : bias;
+            bias = (bias < 0 || bias > 3) ? BIAS_UNIFORM : bias;
         }
         int32_t *nrow = O.node + w * (int64_t)O.cap;
         int64_t *trow = O.ts + w * (int64_t)O.cap;
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
                     k = uniform_index_k(k1, V.m);
                 } else {
-                    const int64_t g = sampler_index_k(k1, V.G, bias, V.rate_start);
+                    const int64_t g = sampler_index_k(k1, V.G, start_bias(bias), V.rate_start);
                     int64_t a, b;
                     ts_group_range(V, g, a, b);
                     k = a + uniform_index_k(k2, b - a);
@@ -83,9 +83,15 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 r = walk_rand(O.seed, (uint64_t)w, h);
                 const uint64_t h1 = u53_bits(r.r0, r.r1);
                 int64_t idx;
-                if (bias == BIAS_UNIFORM) {
+                const int hb = hop_bias(V, bias, O.cnt);
+                if (hb == BIAS_UNIFORM) {
                     const int32_t e0 = __ldg(V.ngo + c), e1 = __ldg(V.ngo + g1);
                     idx = e0 + uniform_index_k(h1, (int64_t)(e1 - e0));
+                } else if (hb == BIAS_EXP_WEIGHT) {
+                    const uint64_t h2 = u53_bits(r.r2, r.r3);
+                    const int32_t kg = weight_group(V, c, g1, h1);
+                    const int32_t e0 = __ldg(V.ngo + kg), e1 = __ldg(V.ngo + kg + 1);
+                    idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
                 } else {
                     const uint64_t h2 = u53_bits(r.r2, r.r3);
                     const int64_t j = sampler_index_k(h1, (int64_t)(g1 - c), bias, V.rate_hop);
@@ -141,6 +147,8 @@ enum : int {
     S_RANGE,       // node record loaded (groups, bucket base, first / last ts)
     S_BKT,         // time-bucket table pair loaded (high-degree node)
     S_SEARCH,      // one probe loaded
+    S_WTOT,        // weight of Gamma loaded (weight-based bias)
+    S_WSEARCH,     // one suffix sum loaded (weight-based bias)
     S_PICK2,       // chosen group's entry range loaded
     S_HOP,         // chosen entry loaded
     S_EXIT
@@ -232,10 +240,10 @@ struct ManyReq {
         }
         L = q.len_arr ? q.len_arr[c.w] : q.max_len;
         bias = q.bias_arr ? (int)q.bias_arr[c.w] : q.bias;
-        if (L < 2 || L > q.cap || bias < 0 || bias > 2) {
+        if (L < 2 || L > q.cap || bias < 0 || bias > 3) {
             atomicOr(&counters->status, 1ull);
             L = L < 2 ? 2 : (L > q.cap ? q.cap : L);
-            bias = (bias < 0 || bias > 2) ? BIAS_UNIFORM : bias;
+            bias = (bias < 0 || bias > 3) ? BIAS_UNIFORM : bias;
         }
     }
     __device__ __forceinline__ uint64_t seed(const Ctx &c) const { return reqs[c.r].seed; }
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                     z1 = __ldg(V.st_dst + k);
                     s.state = S_EDGE;
                 } else {
-                    const int64_t g = sampler_index_k(u1, V.G, bias, V.rate_start);
+                    const int64_t g = sampler_index_k(u1, V.G, start_bias(bias), V.rate_start);
                     z0 = __ldg(V.tg + g);
                     z1 = __ldg(V.tg + g + 1);
                     s.state = S_SGROUP;
@@ -466,6 +474,29 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 }
                 break;
             }
+            case S_WTOT:
+            case S_WSEARCH: {
+                // weight-based draw: smallest k in [L, R] with gs[k + 1] <= R_w,
+                // R_w = gs[c] (1 - u) (vR); y0 holds the last loaded sum
+                if (s.state == S_WTOT) {
+                    s.vR = __double_as_longlong(__longlong_as_double(y0) * (1.0 - (double)s.vL * 0x1.0p-53));
+                } else if (__longlong_as_double(y0) <= __longlong_as_double(s.vR)) {
+                    s.R = z1;
+                } else {
+                    s.L = z1 + 1;
+                }
+                if (s.L == s.R) {
+                    z0 = __ldg(V.ngo + s.L);
+                    z1 = __ldg(V.ngo + s.L + 1);
+                    s.state = S_PICK2;
+                } else {
+                    const int32_t mid = s.L + ((s.R - s.L) >> 1);
+                    z1 = mid;
+                    y0 = __double_as_longlong(__ldg(V.gs + mid + 1));
+                    s.state = S_WSEARCH;
+                }
+                break;
+            }
             case S_PICK2: {
                 const int64_t idx = (int64_t)z0 + uniform_index_k(s.ud, (int64_t)(z1 - z0));
                 const Entry *e = V.ent + idx;
@@ -500,17 +531,26 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             const int32_t c = s.R;
             const Rand4 r = walk_rand(Pv.seed(cx), Pv.wid(cx), s.hop);
             const uint64_t u1 = u53_bits(r.r0, r.r1);
-            if (s.bias == BIAS_UNIFORM) {
+            const int hb = hop_bias(V, s.bias, Pv.cnt());
+            s.state = S_PICK2;
+            if (hb == BIAS_UNIFORM) {
                 s.ud = u1;
                 z0 = __ldg(V.ngo + c);
                 z1 = __ldg(V.ngo + s.g1);
+            } else if (hb == BIAS_EXP_WEIGHT) {
+                // weight of Gamma first, then a bisection on the suffix sums
+                s.ud = u53_bits(r.r2, r.r3);
+                s.vL = (int64_t)u1;
+                s.L = c;
+                s.R = s.g1 - 1;
+                y0 = __double_as_longlong(__ldg(V.gs + c));
+                s.state = S_WTOT;
             } else {
                 s.ud = u53_bits(r.r2, r.r3);
                 const int64_t j = sampler_index_k(u1, (int64_t)(s.g1 - c), s.bias, V.rate_hop);
                 z0 = __ldg(V.ngo + c + j);
                 z1 = __ldg(V.ngo + c + j + 1);
             }
-            s.state = S_PICK2;
         }
         // rows of the walks that ended here: the whole warp writes their
         // padding (node -1, ts INT64_MIN up to the row end), 32 consecutive
@@ -676,6 +716,7 @@ WalkView make_view(tempest_t *h)
     const bool bk = h->n_big > 0 && h->bkt_ver == h->state_ver;
     V.bkt = bk ? h->bkt.as<int32_t>() : nullptr;
     V.pn_nodes = h->pn_ver == h->state_ver ? h->pn_nodes.as<int32_t>() : nullptr;
+    V.gs = h->w_on && h->w_valid && h->w_ver == h->state_ver ? h->gs.as<double>() : nullptr;
     V.bkt_log = h->bkt_log;
     V.directed = h->directed;
     const double ls = h->lam_start > 0.0 ? h->lam_start : (h->G > 0 ? 1.0 / (double)h->G : 1.0);
@@ -689,6 +730,8 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     int rc;
     h->kev_valid = false;
     if ((rc = prepare_walk_index(h))) return rc;
+    if ((!rq.bias_arr && rq.bias == TEMPEST_BIAS_EXP_WEIGHT) || rq.want_w || (rq.bias_arr && h->w_on))
+        if ((rc = prepare_weights(h))) return rc;
     if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
     cudaStream_t st = h->stream;
     cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);

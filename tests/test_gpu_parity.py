@@ -53,8 +53,8 @@ def check_walks(eng, orc, n, L, policy=0, seed=0, biases=(0, 1, 2), scheds=SCHED
     for sched in scheds:
         eng.set_scheduler(sched)
         for bias in biases:
-            g, o = walks_both(eng, orc, n, L, bias, policy, seed, margin=(bias == 2))
-            if bias == 2:
+            g, o = walks_both(eng, orc, n, L, bias, policy, seed, margin=(bias >= 2))
+            if bias >= 2:
                 agree, total, div = compare_biased(g, o, o[3])
                 assert total == 0 or agree / total >= MIN_HOP_AGREEMENT, (sched, agree, total)
             else:
@@ -356,3 +356,73 @@ def test_int64_min_timestamp_is_rejected():
         eng.ingest(torch.tensor([0], dtype=torch.int32).cuda(), torch.tensor([1], dtype=torch.int32).cuda(),
                    torch.tensor([np.iinfo(np.int64).min], dtype=torch.int64).cuda())
     assert e.value.code == _lib.TEMPEST_EINVAL
+
+
+
+# ------------------------------------------------- weight-based sampler (Sec. 2.5)
+def _weight_pair(window, directed, lam):
+    eng, orc = pair(window, directed)
+    eng.set_weight_rate(lam)
+    orc.set_weight_rate(lam)
+    return eng, orc
+
+
+@pytest.mark.parametrize("directed", [1, 0])
+def test_weight_based_walks_all_forms(directed):
+    """Weight-based exponential walks (per-edge weights exp(lambda (t - t_min)))
+    agree with the oracle in every walk form, under the boundary rule, on a
+    stream with hubs, ties and eviction; the rate makes weights span e^0..e^30
+    across a hub's window."""
+    spec = synth.config_mid(scale=0.005)
+    eng, orc = _weight_pair(spec.window, directed, 3e-6)
+    for i, (_, s, d, t) in enumerate(spec.batches(last=7)):
+        ingest_both(eng, orc, s.numpy(), d.numpy(), t.numpy())
+        if i in (0, 3, 6):
+            check_walks(eng, orc, 4000, 14, seed=20 + i, biases=(3,))
+    check_walks(eng, orc, 3000, 10, policy=_lib.START_BIASED_TS, seed=9, biases=(3,),
+                scheds=(_lib.SCHED_STREAM,))
+
+
+def test_weight_based_walks_after_reference_moves():
+    """A rate so large that every batch pushes new groups' exponents past the
+    rebase threshold: each node's reference moves and all weights are
+    recomputed; walks stay the oracle's."""
+    eng, orc = _weight_pair(-3000, 1, 0.05)
+    rng = np.random.default_rng(8)
+    t = 0
+    for b in range(8):
+        n = 1500
+        s = np.where(rng.random(n) < 0.6, 0, rng.integers(1, 30, n)).astype(np.int32)
+        d = np.where(rng.random(n) < 0.6, 0, rng.integers(1, 30, n)).astype(np.int32)
+        ts = (t + np.sort(rng.integers(0, 20000, n))).astype(np.int64)
+        t = int(ts[-1])
+        ingest_both(eng, orc, s, d, ts)
+        check_walks(eng, orc, 2000, 12, seed=b, biases=(3,), scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK))
+
+
+def test_weight_bias_in_mixed_and_batched_requests():
+    spec = synth.config_mid(scale=0.005)
+    eng, orc = pair(spec.window, 1)
+    for _, s, d, t in spec.batches(last=3):
+        ingest_both(eng, orc, s.numpy(), d.numpy(), t.numpy())
+    n = 3000
+    lens = torch.full((n,), 10, dtype=torch.int32).cuda()
+    bias = torch.tensor([3, 2, 0] * (n // 3), dtype=torch.uint8).cuda()
+    # device per-walk biases before the weights are kept: EINVAL, walks clamped
+    eng.walks_mixed(lens, bias, seed=1, max_len_cap=10)
+    with pytest.raises(_lib.TempestError) as e:
+        eng.last_walk_stats()
+    assert e.value.code == _lib.TEMPEST_EINVAL
+    eng.set_weight_rate(1e-9)
+    g = [x.cpu().numpy() for x in eng.walks_mixed(lens, bias, seed=1, max_len_cap=10)]
+    eng.last_walk_stats()
+    o = orc.walks(n, 10, max_len_arr=lens.cpu().numpy(), bias_arr=bias.cpu().numpy(), seed=1, with_margin=True)
+    agree, total, _ = compare_biased(g, o, o[3])
+    assert total == 0 or agree / total >= MIN_HOP_AGREEMENT
+    # the same walks from a batched launch
+    outs = (torch.empty((n, 10), dtype=torch.int32, device="cuda"),
+            torch.empty((n, 10), dtype=torch.int64, device="cuda"),
+            torch.empty((n,), dtype=torch.int32, device="cuda"))
+    _lib.tempest_walks_batch(eng.h, [_lib.make_request(n, 10, 0, 0, 1, *outs, max_len_arr=lens, bias_arr=bias)])
+    torch.cuda.synchronize()
+    assert all(np.array_equal(a, b.cpu().numpy()) for a, b in zip(g, outs))
