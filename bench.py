@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--walks", type=int, default=10_000_000)
     p.add_argument("--max-len", type=int, default=80)
     p.add_argument("--sched", default="stream", choices=["stream", "full", "coop", "graph"])
+    p.add_argument("--bias", default="exp", choices=["uniform", "linear", "exp", "weight"],
+                   help="hop bias of the stream workload (weight: the weight-based sampler, rate 1/window span)")
     p.add_argument("--workload", default="stream", choices=["stream", "batched", "serve"])
     p.add_argument("--requests", type=int, default=2000)
     p.add_argument("--no-e2e", action="store_true")
@@ -168,6 +170,12 @@ def run_ours(args, rank, world):
 
     stream = torch.cuda.current_stream(dev)
     eng = _lib.Engine(window=spec.window, directed=True, device=str(dev), stream=stream)
+    bias_id = {"uniform": _lib.BIAS_UNIFORM, "linear": _lib.BIAS_LINEAR, "exp": _lib.BIAS_EXP,
+               "weight": _lib.BIAS_EXP_WEIGHT}[args.bias]
+    if bias_id == _lib.BIAS_EXP_WEIGHT:
+        # one e-fold per window span: the window holds -window edges at the
+        # stream's mean gap of 550 ns
+        eng.set_weight_rate(1.0 / (550.0 * (-spec.window)))
     eng.set_scheduler({"stream": _lib.SCHED_STREAM, "full": _lib.SCHED_FULL_WALK,
                        "coop": _lib.SCHED_COOP, "graph": _lib.SCHED_GRAPH}[args.sched])
     node = torch.empty((n_walks, L), dtype=torch.int32, device=dev)
@@ -195,7 +203,7 @@ def run_ours(args, rank, world):
                 edges += int(s.shape[0])
         e0, e1 = ev(), ev()
         e0.record(stream)
-        eng.walks(n_walks, L, bias=_lib.BIAS_EXP, start_policy=_lib.START_UNIFORM_EDGE,
+        eng.walks(n_walks, L, bias=bias_id, start_policy=_lib.START_UNIFORM_EDGE,
                   seed=seed_base + step, out=(node, tso, ln))
         e1.record(stream)
         e1.synchronize()
@@ -213,7 +221,7 @@ def run_ours(args, rank, world):
     if args.autotune:
         # the autotuner times candidate settings on the warmed-up window
         # (outside the timed region) and leaves the fastest selected
-        tune = eng.autotune(n_walks, L, bias=_lib.BIAS_EXP, seed=seed_base + 99, forms=True)
+        tune = eng.autotune(n_walks, L, bias=bias_id, seed=seed_base + 99, forms=True)
     clocks = ClockSampler()
     if rank == 0:
         clocks.start()
@@ -239,13 +247,13 @@ def run_ours(args, rank, world):
 
     # end to end through the C ABI with host buffers (one step, after the timed ones)
     if not args.no_e2e:
-        res["e2e"] = run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream)
+        res["e2e"] = run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id)
     eng.close()
     del batches
     return res
 
 
-def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream):
+def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id):
     """Continue the stream with host-resident batches: every step copies its
     batches from pinned host memory and its walks back to pinned host memory
     inside the timed region."""
@@ -274,7 +282,7 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream):
             h2d += s.numel() * 4 + d.numel() * 4 + t.numel() * 8
             edges += int(s.shape[0])
         t0 = time.perf_counter()
-        _lib.tempest_walks(eng.h, n_walks, L, _lib.BIAS_EXP, _lib.START_UNIFORM_EDGE, seed_base + 7777 + step,
+        _lib.tempest_walks(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7777 + step,
                            hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
         walk_s += time.perf_counter() - t0
         hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
@@ -670,7 +678,8 @@ def main():
                                                                          " scaled %g" % args.scale),
                    "nodes": int(100_000_000 * args.scale) if args.scale != 1.0 else 100_000_000,
                    "batch_edges": int(10_000_000 * args.scale), "window_edges": int(200_000_000 * args.scale),
-                   "walks_per_call": res["n_walks"], "max_len": args.max_len, "bias": "exponential",
+                   "walks_per_call": res["n_walks"], "max_len": args.max_len,
+                   "bias": {"exp": "exponential", "weight": "weight-based exponential"}.get(args.bias, args.bias),
                    "start": "uniform edge", "batches_per_step": BATCHES_PER_STEP,
                    "scheduler": sched, "l2": "inputs larger than L2 (160 MB batches, GB-sized state)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
