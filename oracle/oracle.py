@@ -52,7 +52,7 @@ def lib():
         L.orc_destroy.argtypes = [vp]
         L.orc_set_bias_params.argtypes = [vp, dbl, dbl]
         L.orc_ingest.argtypes = [vp, vp, vp, vp, i64]
-        L.orc_walks.argtypes = [vp, i64, vp, i32, vp, i32, vp, ctypes.c_int, ctypes.c_int, i64, u64,
+        L.orc_walks.argtypes = [vp, i64, vp, i32, vp, i32, vp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, u64,
                                 vp, vp, vp, vp, vp]
         L.orc_counts.argtypes = [vp, vp]
         L.orc_set_weight_rate.argtypes = [vp, dbl]
@@ -172,8 +172,14 @@ class Oracle:
         if lib().orc_set_weight_rate(self._h, float(lambda_w)) != 0:
             raise ValueError("bad weight rate")
 
-    def active_nodes(self):
-        """Nodes with at least one live entry in the node view, in id order."""
+    def active_nodes(self, direction=0):
+        """Nodes with at least one live entry in the node view (the in-view for
+        direction 1: a live in-edge), in id order."""
+        if direction == 1:
+            st = self.state()
+            src, dst = np.asarray(st["src"]), np.asarray(st["dst"])
+            nodes = dst if self.directed else np.concatenate([src, dst])
+            return np.unique(nodes).astype(np.int32)
         n = int(lib().orc_active_nodes(self._h, None))
         out = np.zeros(max(n, 1), np.int32)
         lib().orc_active_nodes(self._h, _p(out))
@@ -181,7 +187,7 @@ class Oracle:
 
     def walks(self, n_walks=None, max_len=2, bias=BIAS_UNIFORM, start_policy=START_UNIFORM_EDGE,
               seed=0, ids=None, max_len_arr=None, bias_arr=None, with_margin=False,
-              with_bytes=False, walks_per_node=None):
+              with_bytes=False, walks_per_node=None, direction=0):
         """Returns (node [n, cap], ts [n, cap], len [n], margin or None, bytes or None).
         With START_PER_NODE, walk w starts at active node w // walks_per_node
         (by default n_walks divided by the number of active nodes)."""
@@ -193,7 +199,7 @@ class Oracle:
         k = 0
         if start_policy == START_PER_NODE:
             if walks_per_node is None:
-                na = len(self.active_nodes())
+                na = len(self.active_nodes(direction))
                 if na == 0 or n % na:
                     raise ValueError("per-node walks: %d walks for %d active nodes" % (n, na))
                 walks_per_node = n // na
@@ -210,7 +216,7 @@ class Oracle:
         margin = np.zeros((n, cap), np.float64) if with_margin else None
         nbytes = np.zeros(1, np.float64) if with_bytes else None
         rc = lib().orc_walks(self._h, n, _p(ids), cap, _p(max_len_arr), int(max_len), _p(bias_arr),
-                             int(bias), int(start_policy), k, ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                             int(bias), int(start_policy), k, int(direction), ctypes.c_uint64(int(seed) & (2**64 - 1)),
                              _p(node), _p(ts), _p(ln), _p(margin), _p(nbytes))
         if rc != 0:
             raise ValueError("orc_walks rc=%d" % rc)

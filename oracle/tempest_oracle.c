@@ -386,7 +386,7 @@ int orc_ingest(orc *o, const int32_t *src, const int32_t *dst, const int64_t *ts
     if (n < 0) return ORC_EINVAL;
     if (n > 0 && (!src || !dst || !ts)) return ORC_EINVAL;
     for (int64_t i = 0; i < n; i++)
-        if (src[i] < 0 || dst[i] < 0 || ts[i] == INT64_MIN) return ORC_EINVAL;
+        if (src[i] < 0 || dst[i] < 0 || ts[i] == INT64_MIN || ts[i] == INT64_MAX) return ORC_EINVAL;
 
     /* 1. arrival index for every edge; drop late edges */
     orc_edge *batch = (orc_edge *)malloc(sizeof(orc_edge) * (size_t)(n > 0 ? n : 1));
@@ -612,6 +612,169 @@ int64_t orc_active_nodes(const orc *o, int32_t *out)
     return n;
 }
 
+/* ------------------------------------------------------------------ */
+/* Backward walks (Sec. 2.1: "the backward case defined analogously").  */
+/* ------------------------------------------------------------------ */
+/*
+ * Reading: a backward walk on G is a forward walk on the time-reversed graph
+ * that holds every live edge (u, v, t) as (v, u, -t), in mirrored arrival
+ * order.  So from node v at time t it draws from the in-edges of v earlier
+ * than t, Gamma^-_t(v) = {(u, v, t') : t' < t}, taken in the mirrored order
+ * (descending timestamp, descending arrival): the samplers' index 0 is the
+ * latest such edge or group, and a draw at mirrored position q of a range is
+ * the range's element last - q.  Start edges are mirrored the same way
+ * (store position m - 1 - k, timestamp group G - 1 - g), and the walk takes
+ * the start edge from its destination to its source.
+ */
+typedef struct {
+    int64_t *off, *order, *group_off, *gidx;
+    int64_t Gn;
+} orc_inview;
+
+static void free_inview(orc_inview *iv)
+{
+    free(iv->off);
+    free(iv->order);
+    free(iv->group_off);
+    free(iv->gidx);
+}
+
+/* Entries keyed by destination (directed graphs), in (node, slot) order,
+ * with timestamp groups inside each node's segment. */
+static int build_inview(const orc *o, orc_inview *iv)
+{
+    int64_t m = o->m, N = o->n_nodes;
+    memset(iv, 0, sizeof(*iv));
+    orc_entry *ent = (orc_entry *)malloc(sizeof(orc_entry) * (size_t)(m > 0 ? m : 1));
+    iv->order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    iv->off = (int64_t *)calloc((size_t)(N + 1), sizeof(int64_t));
+    iv->group_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    iv->gidx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    if (!ent || !iv->order || !iv->off || !iv->group_off || !iv->gidx) {
+        free(ent);
+        free_inview(iv);
+        return ORC_ENOMEM;
+    }
+    for (int64_t p = 0; p < m; p++) {
+        ent[p].node = o->live[p].dst;
+        ent[p].slot = p;
+    }
+    qsort(ent, (size_t)m, sizeof(orc_entry), cmp_entry);
+    for (int64_t i = 0; i < m; i++) {
+        iv->order[i] = ent[i].slot;
+        iv->off[ent[i].node + 1] += 1;
+    }
+    for (int64_t v = 0; v < N; v++) iv->off[v + 1] += iv->off[v];
+    int64_t Gn = 0;
+    for (int64_t v = 0; v < N; v++) {
+        iv->gidx[v] = Gn;
+        for (int64_t i = iv->off[v]; i < iv->off[v + 1]; i++)
+            if (i == iv->off[v] || o->live[iv->order[i]].ts != o->live[iv->order[i - 1]].ts)
+                iv->group_off[Gn++] = i;
+    }
+    iv->gidx[N] = Gn;
+    iv->group_off[Gn] = m;
+    iv->Gn = Gn;
+    free(ent);
+    return ORC_OK;
+}
+
+/* the far endpoint and timestamp of in-view entry slot */
+static int64_t back_other(const orc *o, int64_t slot)
+{
+    return o->directed ? o->live[slot].src : slot_other(o, slot);
+}
+
+static int32_t one_walk_back(const orc *o, const orc_inview *iv, uint64_t w, int32_t max_len, int bias,
+                             int start_policy, int64_t start_node, uint64_t seed, int32_t *node, int64_t *tsout,
+                             double *margin, double lambda_start, double *bytes)
+{
+    for (int32_t i = 0; i < max_len; i++) {
+        node[i] = -1;
+        tsout[i] = INT64_MIN;
+        if (margin) margin[i] = INFINITY;
+    }
+    if (o->m == 0) return 0;
+    uint32_t r[4];
+    double u1, u2;
+    int32_t len;
+    int64_t v, t;
+    if (start_policy == START_PER_NODE) {
+        node[0] = (int32_t)start_node;
+        len = 1;
+        v = start_node;
+        t = INT64_MAX;
+    } else {
+        walk_block(seed, w, 0, r);
+        u1 = orc_u53(r[0], r[1]);
+        u2 = orc_u53(r[2], r[3]);
+        int64_t k;
+        if (start_policy == START_UNIFORM_EDGE) {
+            k = o->m - 1 - uniform_index(u1, o->m);
+        } else {
+            double x = orc_sampler_x(u1, o->G_tot, bias, lambda_start);
+            int64_t g = o->G_tot - 1 - orc_sampler_index(u1, o->G_tot, bias, lambda_start);
+            if (margin && bias != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
+            int64_t a = o->ts_group_off[g], size = o->ts_group_off[g + 1] - a;
+            k = a + size - 1 - uniform_index(u2, size);
+        }
+        int32_t a = o->live[k].dst, b = o->live[k].src;
+        if (!o->directed && (r[3] & 1u)) {
+            int32_t tmp = a; a = b; b = tmp;
+        }
+        node[0] = a;
+        node[1] = b;
+        tsout[1] = o->live[k].ts;
+        len = 2;
+        if (bytes) *bytes += 3 * 32.0 + 4 + 4 + 8 + 8 + 4;
+        v = b;
+        t = o->live[k].ts;
+    }
+    while (len < max_len) {
+        const uint32_t h = (uint32_t)(len - 1);
+        const int64_t g0 = iv->gidx[v], g1 = iv->gidx[v + 1];
+        /* c: first group at or after t; Gamma^- = groups [g0, c) */
+        int64_t lo = g0, hi = g1;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (slot_ts(o, iv->order[iv->group_off[mid]]) >= t) hi = mid;
+            else lo = mid + 1;
+        }
+        const int64_t c = lo;
+        if (c == g0) break; /* Gamma^-_t(v) is empty */
+        walk_block(seed, w, h, r);
+        u1 = orc_u53(r[0], r[1]);
+        u2 = orc_u53(r[2], r[3]);
+        int64_t idx;
+        if (bias == BIAS_UNIFORM) {
+            int64_t e0 = iv->group_off[g0], e1 = iv->group_off[c];
+            idx = e1 - 1 - uniform_index(u1, e1 - e0);
+        } else {
+            int64_t n = c - g0;
+            double x = orc_sampler_x(u1, n, bias, o->lambda_hop);
+            int64_t j = orc_sampler_index(u1, n, bias, o->lambda_hop);
+            if (margin) margin[len] = rel_margin(x, n);
+            int64_t gg = c - 1 - j;
+            int64_t e0 = iv->group_off[gg], e1 = iv->group_off[gg + 1];
+            idx = e1 - 1 - uniform_index(u2, e1 - e0);
+        }
+        int64_t slot = iv->order[idx];
+        node[len] = (int32_t)back_other(o, slot);
+        tsout[len] = slot_ts(o, slot);
+        if (bytes) {
+            int64_t G = g1 - g0;
+            int lg = 0;
+            while (((int64_t)1 << lg) < G + 1) lg++;
+            int search = lg - 2 > 1 ? lg - 2 : 1;
+            *bytes += 32.0 * (1 + search + 1) + 12 + 16;
+        }
+        v = node[len];
+        t = tsout[len];
+        len++;
+    }
+    return len;
+}
+
 static double eff_lambda_start(const orc *o)
 {
     if (o->lambda_start > 0.0) return o->lambda_start;
@@ -625,20 +788,40 @@ static double eff_lambda_start(const orc *o)
  */
 int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
               const int32_t *max_len_arr, int32_t max_len, const uint8_t *bias_arr, int bias,
-              int start_policy, int64_t walks_per_node, uint64_t seed, int32_t *node, int64_t *ts,
+              int start_policy, int64_t walks_per_node, int direction, uint64_t seed, int32_t *node, int64_t *ts,
               int32_t *len, double *margin, double *bytes)
 {
-    if (n < 0 || max_len_cap < 2) return ORC_EINVAL;
+    if (n < 0 || max_len_cap < 2 || direction < 0 || direction > 1) return ORC_EINVAL;
+    /* backward walks: the in-view (the out-view itself for undirected graphs) */
+    orc_inview iv;
+    int have_iv = 0;
+    if (direction == 1) {
+        if (o->directed) {
+            int rc = build_inview(o, &iv);
+            if (rc) return rc;
+            have_iv = 1;
+        } else {
+            iv.off = o->node_off;
+            iv.order = o->node_order;
+            iv.group_off = o->node_group_off;
+            iv.gidx = o->node_gidx;
+            iv.Gn = o->Gn;
+        }
+    }
+#define ORC_WALKS_FAIL(code) do { if (have_iv) free_inview(&iv); return (code); } while (0)
     if (start_policy != START_UNIFORM_EDGE && start_policy != START_BIASED_TS && start_policy != START_PER_NODE)
-        return ORC_EINVAL;
+        ORC_WALKS_FAIL(ORC_EINVAL);
     int32_t *active = NULL;
     int64_t n_active = 0;
     if (start_policy == START_PER_NODE && o->m > 0) {
-        if (walks_per_node < 1) return ORC_EINVAL;
-        n_active = orc_active_nodes(o, NULL);
+        if (walks_per_node < 1) ORC_WALKS_FAIL(ORC_EINVAL);
+        const int64_t *gx = direction == 1 ? iv.gidx : o->node_gidx;
+        for (int64_t v = 0; v < o->n_nodes; v++) n_active += gx[v + 1] > gx[v];
         active = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_active > 0 ? n_active : 1));
-        if (!active) return ORC_ENOMEM;
-        orc_active_nodes(o, active);
+        if (!active) ORC_WALKS_FAIL(ORC_ENOMEM);
+        n_active = 0;
+        for (int64_t v = 0; v < o->n_nodes; v++)
+            if (gx[v + 1] > gx[v]) active[n_active++] = (int32_t)v;
     }
     double ls = eff_lambda_start(o);
     if (bytes) *bytes = 0.0;
@@ -646,16 +829,16 @@ int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
         uint64_t w = ids ? (uint64_t)ids[i] : (uint64_t)i;
         int32_t L = max_len_arr ? max_len_arr[i] : max_len;
         int b = bias_arr ? (int)bias_arr[i] : bias;
-        if (L < 2 || L > max_len_cap || b < 0 || b > 3) {
+        if (L < 2 || L > max_len_cap || b < 0 || b > 3 || (direction == 1 && b == BIAS_EXP_WEIGHT)) {
             free(active);
-            return ORC_EINVAL;
+            ORC_WALKS_FAIL(ORC_EINVAL);
         }
         int64_t start_node = -1;
         if (active) {
             const int64_t a = (int64_t)(w / (uint64_t)walks_per_node);
             if (a >= n_active) {
                 free(active);
-                return ORC_EINVAL;
+                ORC_WALKS_FAIL(ORC_EINVAL);
             }
             start_node = active[a];
         }
@@ -667,9 +850,14 @@ int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
             tr[j] = INT64_MIN;
             if (mr) mr[j] = INFINITY;
         }
-        len[i] = one_walk(o, w, L, b, start_policy, start_node, seed, nr, tr, mr, ls, bytes);
+        if (direction == 1)
+            len[i] = one_walk_back(o, &iv, w, L, b, start_policy, start_node, seed, nr, tr, mr, ls, bytes);
+        else
+            len[i] = one_walk(o, w, L, b, start_policy, start_node, seed, nr, tr, mr, ls, bytes);
     }
     free(active);
+    if (have_iv) free_inview(&iv);
+#undef ORC_WALKS_FAIL
     return ORC_OK;
 }
 

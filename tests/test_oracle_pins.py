@@ -452,3 +452,59 @@ def test_walks_on_empty_graph():
     o = O.Oracle(window=0)
     node, tsa, ln, _, _ = o.walks(4, 5, seed=1)
     assert (ln == 0).all() and (node == -1).all()
+
+
+# ---------------------------------------------------------------- backward walks
+def _reversed(src, dst, ts):
+    """The time-reversed graph: every edge (u, v, t) as (v, u, -t), arriving
+    in mirrored order (one batch)."""
+    return list(dst[::-1]), list(src[::-1]), [-x for x in ts[::-1]]
+
+
+@pytest.mark.parametrize("directed", [True, False])
+@pytest.mark.parametrize("policy", [0, 1, 2])
+def test_backward_walks_are_forward_walks_of_the_reversed_graph(directed, policy):
+    """Backward walks on G equal forward walks on the time-reversed graph,
+    position by position, for every bias and start policy: the two run
+    through different code (in-view search for the last earlier group vs the
+    forward search) over mirrored data."""
+    rng = np.random.default_rng(12 + directed)
+    n = 400
+    src = list(rng.integers(0, 25, n))
+    dst = list(rng.integers(0, 25, n))
+    ts = list(rng.integers(1, 60, n))  # many ties
+    a = O.Oracle(window=0, directed=directed)
+    a.ingest(src, dst, ts)
+    b = O.Oracle(window=0, directed=directed)
+    b.ingest(*_reversed(src, dst, ts))
+    na = len(a.active_nodes(1))
+    assert na == len(b.active_nodes())
+    for bias in (0, 1, 2):
+        nw = 5 * na if policy == 2 else 3000
+        g = a.walks(nw, 9, bias=bias, start_policy=policy, seed=bias + 7, direction=1)
+        f = b.walks(nw, 9, bias=bias, start_policy=policy, seed=bias + 7)
+        assert np.array_equal(g[2], f[2]), (bias, policy)
+        assert np.array_equal(g[0], f[0])
+        imin = np.iinfo(np.int64).min
+        real = g[1] != imin
+        assert np.array_equal(g[1] != imin, f[1] != imin)
+        assert np.array_equal(g[1][real], -f[1][real])
+
+
+def test_backward_walks_follow_in_edges_back_in_time():
+    rng = np.random.default_rng(3)
+    src = list(rng.integers(0, 15, 300))
+    dst = list(rng.integers(0, 15, 300))
+    ts = list(rng.integers(1, 40, 300))
+    o = O.Oracle(window=0, directed=True)
+    o.ingest(src, dst, ts)
+    edges = set(zip(src, dst, ts))
+    node, tsa, ln, _, _ = o.walks(2000, 10, bias=2, seed=4, direction=1)
+    for i in range(2000):
+        for p in range(1, ln[i]):
+            # position p was reached over the edge (node[p], node[p-1], ts[p])
+            assert (int(node[i][p]), int(node[i][p - 1]), int(tsa[i][p])) in edges
+            if p >= 2:
+                assert tsa[i][p] < tsa[i][p - 1]
+    with pytest.raises(ValueError):
+        o.walks(10, 5, bias=3, direction=1)  # the weight-based bias runs forward only
