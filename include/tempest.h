@@ -182,6 +182,15 @@ int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const i
 int tempest_walks(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy,
                   uint64_t seed, int32_t *node, int64_t *ts, int32_t *len);
 
+/* Backward walks (the walk form of tempest_enable_backward): arguments,
+ * outputs and draw counters as in tempest_walks; node 0 -> node 1 is a start
+ * edge walked from its destination to its source, and each later position
+ * is an in-edge of the current node earlier than the current time.  Biases
+ * 0-2.  EINVAL as tempest_walks, on bias 3, or on a directed graph without
+ * tempest_enable_backward. */
+int tempest_walks_backward(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy,
+                           uint64_t seed, int32_t *node, int64_t *ts, int32_t *len);
+
 /* Like tempest_walks with a per-walk length cap and bias, all in one launch:
  * max_len_arr int32[n_walks] (each in [2, max_len_cap]), bias_arr
  * uint8[n_walks] (each a TEMPEST_BIAS_*).  Rows have stride max_len_cap. */
@@ -210,12 +219,26 @@ typedef struct {
     const int32_t *max_len_arr;
     const uint8_t *bias_arr;
     int32_t start_policy;
-    int32_t pad;
+    int32_t direction;  /* 0: forward; 1: backward (see tempest_enable_backward) */
     uint64_t seed;
     int32_t *node;
     int64_t *ts;
     int32_t *len;
 } tempest_walk_request;
+
+/* Backward walks (Sec. 2.1, "the backward case defined analogously"): a
+ * request with direction 1 walks the time-reversed graph, in which every
+ * live edge (u, v, t) reads as (v, u, -t) in mirrored arrival order.  From
+ * node v at time t it draws from the in-edges of v earlier than t,
+ * {(u, v, t') : t' < t}, taken latest first (the samplers' index 0 is the
+ * latest edge or group; the bias favours older ones as the forward bias
+ * favours newer ones); a start edge (u, v, t) is walked from v to u, and a
+ * PER_NODE start begins after every live edge.  Biases 0-2 only.  Directed
+ * graphs need this call first: from it on every ingest also keeps an index
+ * of the in-edges (a second store and view, built now from the live edges).
+ * Undirected graphs walk backward on their one view.  ENOMEM when the
+ * second index does not fit. */
+int tempest_enable_backward(tempest_t *h);
 
 /* Serve n_req walk requests in one persistent launch (continuous batching
  * of requests; Sec. 2.4 walks, Sec. 2.5 samplers).  The requests' outputs
@@ -324,6 +347,11 @@ int tempest_autotune_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len
 /* Number of active nodes (nodes with at least one live entry in the node
  * view) of the current state: the divisor of PER_NODE walk counts. */
 int tempest_active_nodes(tempest_t *h, int64_t *n);
+
+/* The same for backward walks: nodes with at least one live in-edge (any
+ * live edge, for undirected graphs).  EINVAL on a directed graph without
+ * tempest_enable_backward. */
+int tempest_active_nodes_backward(tempest_t *h, int64_t *n);
 
 /* Report of the most recent walk call; waits for its work to finish. */
 int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out);

@@ -42,7 +42,8 @@ EXPORTED = (
     "tempest_server_submit_ingest", "tempest_server_progress", "tempest_server_status",
     "tempest_server_release", "tempest_server_drain", "tempest_server_stats",
     "tempest_set_tuning", "tempest_get_tuning", "tempest_autotune", "tempest_autotune_mixed",
-    "tempest_active_nodes", "tempest_set_weight_rate",
+    "tempest_active_nodes", "tempest_set_weight_rate", "tempest_enable_backward", "tempest_walks_backward",
+    "tempest_active_nodes_backward",
 )
 NOALLOC_MAX_EDGES = 262144
 
@@ -98,7 +99,7 @@ class TuneReport(ctypes.Structure):
 class WalkRequest(ctypes.Structure):
     _fields_ = [("n_walks", ctypes.c_int64), ("max_len", ctypes.c_int32), ("bias", ctypes.c_int32),
                 ("max_len_arr", ctypes.c_void_p), ("bias_arr", ctypes.c_void_p),
-                ("start_policy", ctypes.c_int32), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("start_policy", ctypes.c_int32), ("direction", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("node", ctypes.c_void_p), ("ts", ctypes.c_void_p), ("len", ctypes.c_void_p)]
 
 
@@ -138,6 +139,9 @@ def load():
                                    ctypes.POINTER(TuneReport)]
     L.tempest_active_nodes.argtypes = [vp, ctypes.POINTER(i64)]
     L.tempest_set_weight_rate.argtypes = [vp, dbl]
+    L.tempest_enable_backward.argtypes = [vp]
+    L.tempest_walks_backward.argtypes = [vp, i64, i32, ci, ci, u64, vp, vp, vp]
+    L.tempest_active_nodes_backward.argtypes = [vp, ctypes.POINTER(i64)]
     L.tempest_autotune_mixed.argtypes = [vp, i64, vp, ctypes.c_int32, vp, ci, ctypes.c_uint64, ctypes.c_int32,
                                          ctypes.POINTER(TuneReport)]
     L.tempest_last_walk_stats.argtypes = [vp, ctypes.POINTER(WalkStats)]
@@ -215,6 +219,13 @@ def tempest_walks(h, n_walks, max_len, bias, start_policy, seed, node_ptr, ts_pt
                                           ctypes.c_void_p(len_ptr)))
 
 
+def tempest_walks_backward(h, n_walks, max_len, bias, start_policy, seed, node_ptr, ts_ptr, len_ptr):
+    return _check(h, load().tempest_walks_backward(h, int(n_walks), int(max_len), int(bias), int(start_policy),
+                                                   ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                                   ctypes.c_void_p(node_ptr), ctypes.c_void_p(ts_ptr),
+                                                   ctypes.c_void_p(len_ptr)))
+
+
 def tempest_walks_mixed(h, n_walks, max_len_ptr, max_len_cap, bias_ptr, start_policy, seed, node_ptr,
                         ts_ptr, len_ptr):
     return _check(h, load().tempest_walks_mixed(h, int(n_walks), ctypes.c_void_p(max_len_ptr),
@@ -231,9 +242,10 @@ def tempest_sample_index(h, u_bits_ptr, n_ptr, count, bias, lam, out_ptr):
 
 
 def make_request(n_walks, max_len, bias=0, start_policy=0, seed=0, node=None, ts=None, ln=None,
-                 max_len_arr=None, bias_arr=None) -> WalkRequest:
+                 max_len_arr=None, bias_arr=None, direction=0) -> WalkRequest:
     """A tempest_walk_request; outputs / per-walk arrays are CUDA tensors or None."""
     r = WalkRequest()
+    r.direction = int(direction)
     r.n_walks, r.max_len, r.bias, r.start_policy = int(n_walks), int(max_len), int(bias), int(start_policy)
     r.seed = int(seed) & (2**64 - 1)
     r.max_len_arr = _ptr(max_len_arr, "int32")
@@ -337,10 +349,15 @@ def tempest_get_tuning(h, knob: int) -> int:
     return v.value
 
 
-def tempest_active_nodes(h) -> int:
+def tempest_active_nodes(h, direction=0) -> int:
     n = ctypes.c_int64()
-    _check(h, load().tempest_active_nodes(h, ctypes.byref(n)))
+    fn = load().tempest_active_nodes_backward if direction else load().tempest_active_nodes
+    _check(h, fn(h, ctypes.byref(n)))
     return n.value
+
+
+def tempest_enable_backward(h):
+    return _check(h, load().tempest_enable_backward(h))
 
 
 def tempest_autotune_mixed(h, n_walks, max_len_arr, max_len_cap, bias_arr, start_policy, seed, flags) -> TuneReport:
@@ -481,9 +498,14 @@ class Engine:
         """Rate of the weight-based sampler (TEMPEST_BIAS_EXP_WEIGHT); keeps group weights from now on."""
         _check(self.h, load().tempest_set_weight_rate(self.h, float(lambda_w)))
 
-    def active_nodes(self) -> int:
-        """Number of nodes with a live entry: PER_NODE walk counts are multiples of it."""
-        return tempest_active_nodes(self.h)
+    def active_nodes(self, direction: int = 0) -> int:
+        """Number of nodes with a live entry (in-entry when direction is 1): PER_NODE walk counts are
+        multiples of it."""
+        return tempest_active_nodes(self.h, direction)
+
+    def enable_backward(self):
+        """Keep the in-edge index that backward walks of a directed graph read."""
+        tempest_enable_backward(self.h)
 
     def autotune(self, n_walks, max_len, bias=BIAS_EXP, start_policy=0, seed=0, forms=True) -> dict:
         """Time candidate settings on the live index and keep the fastest."""
@@ -504,7 +526,7 @@ class Engine:
         return tempest_ingest(self.h, _ptr(src, "int32"), _ptr(dst, "int32"), _ptr(ts, "int64"), n).as_dict()
 
     def walks(self, n_walks: int, max_len: int, bias: int = BIAS_UNIFORM,
-              start_policy: int = START_UNIFORM_EDGE, seed: int = 0, out=None):
+              start_policy: int = START_UNIFORM_EDGE, seed: int = 0, out=None, direction: int = 0):
         torch = self.torch
         if out is None:
             node = torch.empty((n_walks, max_len), dtype=torch.int32, device=self.device)
@@ -512,8 +534,9 @@ class Engine:
             ln = torch.empty((n_walks,), dtype=torch.int32, device=self.device)
         else:
             node, ts, ln = out
-        tempest_walks(self.h, n_walks, max_len, bias, start_policy, seed, _ptr(node, "int32"),
-                      _ptr(ts, "int64"), _ptr(ln, "int32"))
+        fn = tempest_walks_backward if direction else tempest_walks
+        fn(self.h, n_walks, max_len, bias, start_policy, seed, _ptr(node, "int32"), _ptr(ts, "int64"),
+           _ptr(ln, "int32"))
         return node, ts, ln
 
     def walks_mixed(self, max_len_arr, bias_arr, start_policy: int = START_UNIFORM_EDGE, seed: int = 0,

@@ -184,6 +184,8 @@ int tempest_destroy(tempest_t *h)
 {
     if (!h) return TEMPEST_OK;
     cudaStreamSynchronize(h->stream);
+    if (h->rev) tempest_destroy(h->rev);
+    h->rev = nullptr;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     for (cudaEvent_t &e : h->kev)
         if (e) cudaEventDestroy(e);
@@ -239,23 +241,84 @@ int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const i
                    tempest_ingest_stats *stats)
 {
     if (!h) return TEMPEST_EINVAL;
-    return ingest_batch(h, src, dst, ts, n, stats);
+    int rc = ingest_batch(h, src, dst, ts, n, stats);
+    if (rc || !h->rev) return rc;
+    // the reversed index takes the same batch with the endpoints swapped; it
+    // sees the same timestamps in the same order, so its window evicts the
+    // same edges and its store stays position-aligned with the main one
+    h->rev->stream = h->stream;
+    rc = ingest_batch(h->rev, dst, src, ts, n, nullptr);
+    if (rc) {
+        fail(h, rc, "tempest_ingest: the in-edge index failed (%s); backward walks are off until "
+                    "tempest_enable_backward", h->rev->err.c_str());
+        cudaStreamSynchronize(h->stream);
+        tempest_destroy(h->rev);
+        h->rev = nullptr;
+    }
+    return rc;
 }
 
-int tempest_active_nodes(tempest_t *h, int64_t *n)
+int tempest_enable_backward(tempest_t *h)
 {
-    if (!h || !n) return TEMPEST_EINVAL;
-    int rc;
-    if ((rc = prepare_active_nodes(h))) return rc;
-    *n = h->n_pn;
+    if (!h) return TEMPEST_EINVAL;
+    if (!h->directed || h->rev) return TEMPEST_OK;  // undirected graphs use their one view
+    tempest_t *r = nullptr;
+    int rc = tempest_create(h->window, 1, &r);
+    if (rc) return fail(h, rc, "tempest_enable_backward: %s", tempest_last_error(nullptr));
+    r->alloc_fn = h->alloc_fn;
+    r->release_fn = h->release_fn;
+    r->alloc_ctx = h->alloc_ctx;
+    r->budget = h->budget;
+    r->stream = h->stream;
+    r->bkt_log = h->bkt_log;
+    if (h->m > 0) {
+        // the live edges, reversed, as one batch: they are in (ts, arrival)
+        // order and inside the window, so the new index holds all of them in
+        // the same order
+        const int32_t *ss = h->st_src[h->cur].as<int32_t>() + h->s_lo;
+        const int32_t *sd = h->st_dst[h->cur].as<int32_t>() + h->s_lo;
+        const int64_t *st = h->st_ts[h->cur].as<int64_t>() + h->s_lo;
+        rc = ingest_batch(r, sd, ss, st, h->m, nullptr);
+        if (!rc && r->m != h->m) rc = fail(r, TEMPEST_ECUDA, "replay kept %lld of %lld edges", (long long)r->m,
+                                           (long long)h->m);
+        if (rc) {
+            fail(h, rc, "tempest_enable_backward: %s", r->err.c_str());
+            cudaStreamSynchronize(h->stream);
+            tempest_destroy(r);
+            return rc;
+        }
+    }
+    // later batches meet the same late-arrival cutoff as the main index
+    r->has_cutoff = h->has_cutoff;
+    r->cutoff = h->cutoff;
+    h->rev = r;
     return TEMPEST_OK;
 }
 
+static int active_nodes_dir(tempest_t *h, int direction, int64_t *n)
+{
+    if (!h || !n) return TEMPEST_EINVAL;
+    tempest_t *vh = view_handle(h, direction);
+    if (!vh) return fail(h, TEMPEST_EINVAL, "backward walks of a directed graph need tempest_enable_backward");
+    int rc;
+    if ((rc = prepare_active_nodes(vh))) return vh == h ? rc : fail(h, rc, "%s", vh->err.c_str());
+    *n = vh->n_pn;
+    return TEMPEST_OK;
+}
+
+int tempest_active_nodes(tempest_t *h, int64_t *n) { return active_nodes_dir(h, 0, n); }
+
+int tempest_active_nodes_backward(tempest_t *h, int64_t *n) { return active_nodes_dir(h, 1, n); }
+
 static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_len, const int32_t *len_arr,
                         int bias, const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t *node,
-                        int64_t *ts, int32_t *len)
+                        int64_t *ts, int32_t *len, int direction = 0)
 {
     int rc;
+    tempest_t *vh = view_handle(h, direction);
+    if (!vh) return fail(h, TEMPEST_EINVAL, "backward walks of a directed graph need tempest_enable_backward");
+    if (direction && !bias_arr && bias == TEMPEST_BIAS_EXP_WEIGHT)
+        return fail(h, TEMPEST_EINVAL, "walks: backward walks take biases 0-2");
     if (n_walks < 0) return fail(h, TEMPEST_EINVAL, "walks: n_walks < 0");
     if (cap < 2) return fail(h, TEMPEST_EINVAL, "walks: max_len must be >= 2");
     if (start_policy < TEMPEST_START_UNIFORM_EDGE || start_policy > TEMPEST_START_PER_NODE)
@@ -265,7 +328,8 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
     if (n_walks > 0 && (int64_t)cap * n_walks / n_walks != (int64_t)cap)
         return fail(h, TEMPEST_EINVAL, "walks: output size overflows");
     int64_t pn_k = 0;
-    if ((rc = per_node_k(h, start_policy, n_walks, pn_k, "walks"))) return rc;
+    if ((rc = per_node_k(vh, start_policy, n_walks, pn_k, "walks")))
+        return vh == h ? rc : fail(h, rc, "%s", vh->err.c_str());
     cudaStream_t st = h->stream;
     h->last_ws = tempest_walk_stats{};
     if (n_walks == 0) return TEMPEST_OK;
@@ -282,8 +346,9 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
                             len_arr[i], cap);
     if (host_bias)
         for (int64_t i = 0; i < n_walks; i++)
-            if (bias_arr[i] > 3)
-                return fail(h, TEMPEST_EINVAL, "walks_mixed: bias_arr[%lld] = %d unknown", (long long)i, bias_arr[i]);
+            if (bias_arr[i] > (direction ? 2 : 3))
+                return fail(h, TEMPEST_EINVAL, "walks_mixed: bias_arr[%lld] = %d unknown%s", (long long)i,
+                            bias_arr[i], direction ? " for backward walks" : "");
     if (host_len || host_bias) {
         size_t need = 0;
         if (host_len) need += sizeof(int32_t) * (size_t)n_walks;
@@ -324,6 +389,7 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
         if (!dev_len) d_lenout = reinterpret_cast<int32_t *>(p);
     }
     WalkRequest rq{n_walks, cap, max_len, d_len, bias, d_bias, start_policy, pn_k, seed, d_node, d_ts, d_lenout};
+    rq.direction = direction;
     if (host_bias)
         for (int64_t i = 0; i < n_walks && !rq.want_w; i++) rq.want_w = bias_arr[i] == TEMPEST_BIAS_EXP_WEIGHT;
     if ((rc = walks_run(h, rq))) return rc;
@@ -340,6 +406,13 @@ int tempest_walks(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int 
 {
     if (!h) return TEMPEST_EINVAL;
     return walks_common(h, n_walks, max_len, max_len, nullptr, bias, nullptr, start_policy, seed, node, ts, len);
+}
+
+int tempest_walks_backward(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy,
+                           uint64_t seed, int32_t *node, int64_t *ts, int32_t *len)
+{
+    if (!h) return TEMPEST_EINVAL;
+    return walks_common(h, n_walks, max_len, max_len, nullptr, bias, nullptr, start_policy, seed, node, ts, len, 1);
 }
 
 int tempest_walks_mixed(tempest_t *h, int64_t n_walks, const int32_t *max_len_arr, int32_t max_len_cap,

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) k_coop_start(const WalkView V, const Walk
         if (O.start_policy == TEMPEST_START_PER_NODE) {
             // the walk starts at an active node before every live edge
             d = __ldg(V.pn_nodes + w / O.pn_k);
-            t0 = INT64_MIN;
+            t0 = pernode_time(V);
             nrow[0] = d;
             trow[0] = INT64_MIN;
             len0 = 1;
@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(256) k_coop_start(const WalkView V, const Walk
             nrow[1] = d;
             trow[0] = INT64_MIN;
             trow[1] = t0;
+            t0 = search_time(V, t0);
             hops++;
             bytes += START_MODEL_BYTES;
             len0 = 2;
@@ -182,11 +183,12 @@ __device__ __forceinline__ void coop_hop(const WalkView &V, const WalkOut &O, co
     } else {
         c = first_later(V, v, g0, g1, t);
     }
-    if (c == g1) {
+    if (V.back ? c == g0 : c == g1) {
         O.len[w] = len;  // Gamma_t(v) is empty
         return;
     }
-    const Entry e = draw_entry(V, O, w, (uint32_t)(len - 1), bias, c, g1);
+    const Entry e = V.back ? draw_entry_back(V, O, w, (uint32_t)(len - 1), bias, g0, c)
+                           : draw_entry(V, O, w, (uint32_t)(len - 1), bias, c, g1);
     O.node[w * (int64_t)O.cap + len] = e.other;
     O.ts[w * (int64_t)O.cap + len] = e.ts;
     hops++;
@@ -197,7 +199,7 @@ __device__ __forceinline__ void coop_hop(const WalkView &V, const WalkOut &O, co
         return;
     }
     S.ws_node[w] = e.other;
-    S.ws_t[w] = e.ts;
+    S.ws_t[w] = search_time(V, e.ts);
     S.ws_len[w] = len;
     push = true;
 }

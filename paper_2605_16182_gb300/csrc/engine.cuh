@@ -192,6 +192,9 @@ struct tempest {
     tw::DBuf exp_stage;   // export staging
     void *hstat = nullptr;     // pinned host mirror of IngestScratch / counters
 
+    // backward walks of directed graphs: a handle over the reversed edges
+    // (dst, src, ts), fed every batch; its node view is the in-view
+    tempest *rev = nullptr;
     tempest_walk_stats last_ws{};
     cudaEvent_t kev[2] = {nullptr, nullptr};  // brackets the walk kernels of the last call
     bool kev_valid = false;
@@ -223,6 +226,10 @@ int nv_export(tempest_t *h, int which, int32_t *out);
 int ts_export(tempest_t *h, int32_t *out);
 
 // walks.cu
+struct WalkRequest;
+// the handle whose index a walk of the given direction reads (h itself for
+// forward walks and undirected graphs); null when backward walks are off
+tempest_t *view_handle(tempest_t *h, int direction);
 struct WalkRequest {
     int64_t n_walks;
     int32_t cap;               // row stride
@@ -237,6 +244,7 @@ struct WalkRequest {
     int64_t *ts;               // device
     int32_t *len;              // device
     int want_w = 0;            // per-walk biases known to include the weight-based one
+    int direction = 0;         // 1: backward walks
 };
 int walks_run(tempest_t *h, const WalkRequest &rq);
 // builds the time-bucket tables of the live state on the handle's stream

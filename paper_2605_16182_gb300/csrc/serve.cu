@@ -43,8 +43,17 @@ static int build_table(tempest_t *h, const tempest_walk_request *reqs, int n, Re
             return fail(h, TEMPEST_EINVAL, "walk request %d: outputs must be device memory", i);
         if ((q.max_len_arr && !is_device_ptr(q.max_len_arr)) || (q.bias_arr && !is_device_ptr(q.bias_arr)))
             return fail(h, TEMPEST_EINVAL, "walk request %d: per-walk arrays must be device memory", i);
+        if (q.direction != 0 && q.direction != 1)
+            return fail(h, TEMPEST_EINVAL, "walk request %d: direction %d is neither 0 nor 1", i, q.direction);
+        if (q.direction == 1 && !q.bias_arr && q.bias == TEMPEST_BIAS_EXP_WEIGHT)
+            return fail(h, TEMPEST_EINVAL, "walk request %d: backward walks take biases 0-2", i);
+        tempest_t *vh = view_handle(h, q.direction);
+        if (!vh)
+            return fail(h, TEMPEST_EINVAL, "walk request %d: backward walks of a directed graph need "
+                        "tempest_enable_backward", i);
         ReqDesc &d = out[i];
-        int rc = per_node_k(h, q.start_policy, q.n_walks, d.pn_k, "walk request");
+        int rc = per_node_k(vh, q.start_policy, q.n_walks, d.pn_k, "walk request");
+        if (rc && vh != h) fail(h, rc, "%s", vh->err.c_str());
         if (rc) return rc;
         d.n_walks = q.n_walks;
         d.offset = total;
@@ -63,10 +72,19 @@ static int build_table(tempest_t *h, const tempest_walk_request *reqs, int n, Re
     return TEMPEST_OK;
 }
 
-// Weight sums are needed when a request asks for the weight-based bias, or
-// may (device per-walk biases) once weights are kept.
-static int prepare_for(tempest_t *h, const ReqDesc *t, int n)
+// Derived indexes of a launch in the given direction: the time-bucket tables
+// of the view it reads, and (forward) the weight sums when a request asks for
+// the weight-based bias, or may (device per-walk biases) once weights are kept.
+static int prepare_for(tempest_t *h, int direction, const ReqDesc *t, int n)
 {
+    tempest_t *vh = view_handle(h, direction);
+    if (!vh) return fail(h, TEMPEST_EINVAL, "backward walks of a directed graph need tempest_enable_backward");
+    int rc = prepare_walk_index(vh);
+    if (rc) {
+        if (vh != h) fail(h, rc, "%s", vh->err.c_str());
+        return rc;
+    }
+    if (direction) return TEMPEST_OK;
     for (int i = 0; i < n; i++)
         if ((!t[i].bias_arr && t[i].bias == TEMPEST_BIAS_EXP_WEIGHT) || (t[i].bias_arr && h->w_on))
             return prepare_weights(h);
@@ -193,6 +211,7 @@ int launch_wave(tempest_server *s, tempest_server::Wave &wv, int &rc)
         tempest_server::Req &r = s->reqs[id];
         if (r.kind != 0) break;
         if (!ids.empty() && walks + r.w.n_walks > s->max_wave_walks) break;
+        if (!ids.empty() && r.w.direction != wr[0].direction) break;  // a wave reads one view
         if (r.arena_out && r.bytes == 0) {
             const size_t b = out_bytes(r.w);
             if (b > s->arena_bytes) {  // can never fit
@@ -229,7 +248,8 @@ int launch_wave(tempest_server *s, tempest_server::Wave &wv, int &rc)
     }
     const int n = compact_table(wv.stage, (int)ids.size());
     // derived walk indexes of the current state, built on the handle's stream
-    if ((rc = prepare_walk_index(s->h)) || (rc = prepare_for(s->h, wv.stage, n))) {
+    const int dir = wr[0].direction;
+    if ((rc = prepare_for(s->h, dir, wv.stage, n))) {
         for (uint64_t id : ids) {
             s->reqs[id].state = rc;
             s->reqs[id].t_done = now_s();
@@ -243,7 +263,7 @@ int launch_wave(tempest_server *s, tempest_server::Wave &wv, int &rc)
     ReqDesc *dtab = wv.table.as<ReqDesc>();
     WalkCounters *cnt = reinterpret_cast<WalkCounters *>(wv.table.as<char>() + sizeof(ReqDesc) * (size_t)wv.cap);
     cudaMemcpyAsync(dtab, wv.stage, sizeof(ReqDesc) * (size_t)(n > 0 ? n : 1), cudaMemcpyHostToDevice, wv.st);
-    rc = walks_multi_launch(s->h, dtab, n, total, cnt, wv.st);
+    rc = walks_multi_launch(s->h, dir, dtab, n, total, cnt, wv.st);
     cudaEventRecord(wv.ev, wv.st);
     const double t = now_s();
     for (uint64_t id : ids) {
@@ -267,26 +287,47 @@ int tempest_walks_batch(tempest_t *h, const tempest_walk_request *reqs, int n_re
     if (n_req < 0 || (n_req > 0 && !reqs)) return fail(h, TEMPEST_EINVAL, "tempest_walks_batch: bad request list");
     h->last_ws = tempest_walk_stats{};
     if (n_req == 0) return TEMPEST_OK;
-    std::vector<ReqDesc> tab((size_t)n_req);
-    int64_t total = 0;
-    int rc = build_table(h, reqs, n_req, tab.data(), total);
-    if (rc) return rc;
-    const int n = compact_table(tab.data(), n_req);
-    const size_t tbytes = sizeof(ReqDesc) * (size_t)(n > 0 ? n : 1);
-    if ((rc = ensure(h, h->in_stage, tbytes + 256, true))) return rc;
+    // one launch per direction present (a launch reads one view); each
+    // direction's requests keep their own offsets from 0
+    std::vector<tempest_walk_request> part[2];
+    for (int i = 0; i < n_req; i++) part[reqs[i].direction == 1 ? 1 : 0].push_back(reqs[i]);
+    std::vector<ReqDesc> tab[2];
+    int64_t total[2] = {0, 0};
+    int n[2] = {0, 0};
+    int rc;
+    for (int d = 0; d < 2; d++) {
+        // validation runs on the caller's request list order within a direction
+        tab[d].resize(part[d].size());
+        if (part[d].empty()) continue;
+        if ((rc = build_table(h, part[d].data(), (int)part[d].size(), tab[d].data(), total[d]))) return rc;
+        n[d] = compact_table(tab[d].data(), (int)part[d].size());
+    }
+    const size_t tb0 = (sizeof(ReqDesc) * (size_t)(n[0] > 0 ? n[0] : 1) + 255) & ~(size_t)255;
+    const size_t tb1 = sizeof(ReqDesc) * (size_t)(n[1] > 0 ? n[1] : 1);
+    if ((rc = ensure(h, h->in_stage, tb0 + tb1 + 256, true))) return rc;
     if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
-    // the table is small: a synchronous copy keeps the host array reusable
-    if ((rc = cuda_check(h, cudaMemcpyAsync(h->in_stage.p, tab.data(), tbytes, cudaMemcpyHostToDevice, h->stream),
-                         "batch table")))
-        return rc;
+    char *stage = h->in_stage.as<char>();
+    // the tables are small: a synchronous copy keeps the host arrays reusable
+    for (int d = 0; d < 2; d++)
+        if (n[d] && (rc = cuda_check(h, cudaMemcpyAsync(stage + (d ? tb0 : 0), tab[d].data(), sizeof(ReqDesc) * n[d],
+                                                        cudaMemcpyHostToDevice, h->stream),
+                                     "batch table")))
+            return rc;
     if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "batch table"))) return rc;
     h->kev_valid = false;
-    if ((rc = prepare_walk_index(h))) return rc;
-    if ((rc = prepare_for(h, tab.data(), n))) return rc;
-    rc = walks_multi_launch(h, h->in_stage.as<ReqDesc>(), n, total, h->wcnt.as<WalkCounters>(), h->stream);
-    h->last_ws.n_walks = total;
-    h->last_ws.launches = 1;
-    return rc;
+    int launches = 0;
+    for (int d = 0; d < 2; d++) {
+        if (!n[d] && (d == 1 || n[1])) continue;  // an empty batch still clears the counters
+        if ((rc = prepare_for(h, d, tab[d].data(), n[d]))) return rc;
+        // the second launch adds to the first one's counters
+        rc = walks_multi_launch(h, d, reinterpret_cast<ReqDesc *>(stage + (d ? tb0 : 0)), n[d], total[d],
+                                h->wcnt.as<WalkCounters>(), h->stream, launches == 0);
+        if (rc) return rc;
+        launches++;
+    }
+    h->last_ws.n_walks = total[0] + total[1];
+    h->last_ws.launches = launches;
+    return cuda_check(h, cudaGetLastError(), "walks batch");
 }
 
 int tempest_server_create(tempest_t *h, size_t arena_bytes, int64_t max_wave_walks, int max_inflight,

@@ -37,6 +37,11 @@ struct WalkView {
     const double *gs;
     int bkt_log;
     int directed;
+    // backward walks (the view is the in-view): searches run at t - 1 (the
+    // last group earlier than t ends where the first group later than t - 1
+    // begins), draws mirror the range, and back_swap walks a start edge from
+    // its stored destination to its stored source
+    int back, back_swap;
     ExpRate rate_hop, rate_start;
 };
 
@@ -238,15 +243,22 @@ __device__ __forceinline__ void start_edge(const WalkView &V, const WalkOut &O, 
     int64_t k;
     if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
         k = uniform_index_k(k1, V.m);
+        if (V.back) k = V.m - 1 - k;
     } else {
-        const int64_t g = sampler_index_k(k1, V.G, start_bias(bias), V.rate_start);
+        int64_t g = sampler_index_k(k1, V.G, start_bias(bias), V.rate_start);
+        if (V.back) g = V.G - 1 - g;
         int64_t a, b;
         ts_group_range(V, g, a, b);
-        k = a + uniform_index_k(k2, b - a);
+        k = V.back ? b - 1 - uniform_index_k(k2, b - a) : a + uniform_index_k(k2, b - a);
     }
     s = V.st_src[k];
     d = V.st_dst[k];
     t0 = V.st_ts[k];
+    if (V.back_swap) {
+        const int32_t x = s;
+        s = d;
+        d = x;
+    }
     if (!V.directed && (r.r3 & 1u)) {
         const int32_t x = s;
         s = d;
@@ -281,6 +293,34 @@ __device__ __forceinline__ Entry draw_entry(const WalkView &V, const WalkOut &O,
     return V.ent[idx];
 }
 
+// Backward hop at a node whose groups earlier than t are [g0, c), in the
+// mirrored order: uniform over the edges (position last - q), or group
+// c - 1 - j by the bias, then an edge of it (position last - q).
+__device__ __forceinline__ Entry draw_entry_back(const WalkView &V, const WalkOut &O, int64_t w, uint32_t hop,
+                                                 int bias, int32_t g0, int32_t c)
+{
+    const Rand4 r = walk_rand(O.seed, (uint64_t)w, hop);
+    const uint64_t h1 = u53_bits(r.r0, r.r1);
+    int64_t idx;
+    bias = hop_bias(V, bias, O.cnt);  // no weight sums backward: flagged
+    if (bias == BIAS_UNIFORM) {
+        const int32_t e0 = __ldg(V.ngo + g0), e1 = __ldg(V.ngo + c);
+        idx = e1 - 1 - uniform_index_k(h1, (int64_t)(e1 - e0));
+    } else {
+        const uint64_t h2 = u53_bits(r.r2, r.r3);
+        const int64_t j = sampler_index_k(h1, (int64_t)(c - g0), start_bias(bias), V.rate_hop);
+        const int32_t gg = c - 1 - (int32_t)j;
+        const int32_t e0 = __ldg(V.ngo + gg), e1 = __ldg(V.ngo + gg + 1);
+        idx = e1 - 1 - uniform_index_k(h2, (int64_t)(e1 - e0));
+    }
+    return V.ent[idx];
+}
+
+// The time a walk searches at after reaching a node at time t (forward: t;
+// backward: t - 1), and before its first hop under PER_NODE.
+__device__ __forceinline__ int64_t search_time(const WalkView &V, int64_t t) { return V.back ? t - 1 : t; }
+__device__ __forceinline__ int64_t pernode_time(const WalkView &V) { return V.back ? INT64_MAX - 1 : INT64_MIN; }
+
 // One walk request of a multi-request launch (device copy).  offset is the
 // first global walk id of the request inside the launch.
 struct ReqDesc {
@@ -299,11 +339,12 @@ struct ReqDesc {
     int64_t pn_k;  // PER_NODE: walks per active node
 };
 
-WalkView make_view(tempest_t *h);
-// One persistent streaming launch (plus row padding) over n_req requests
-// whose descriptors are in device memory; counters in cnt (zeroed here).
-int walks_multi_launch(tempest_t *h, const ReqDesc *dev_reqs, int n_req, int64_t total, WalkCounters *cnt,
-                       cudaStream_t st);
+WalkView make_view(tempest_t *h, int back = 0);
+// One persistent streaming launch over n_req requests of one direction whose
+// descriptors are in device memory; counters in cnt (zeroed here unless
+// clear is false, when the launch adds to them).
+int walks_multi_launch(tempest_t *h, int direction, const ReqDesc *dev_reqs, int n_req, int64_t total,
+                       WalkCounters *cnt, cudaStream_t st, bool clear = true);
 int coop_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches);
 int graph_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches);
 

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
             if (O.start_policy == TEMPEST_START_PER_NODE) {
                 // the walk starts at an active node before every live edge
                 v = __ldg(V.pn_nodes + w / O.pn_k);
-                t = INT64_MIN;
+                t = pernode_time(V);
                 nrow[0] = v;
                 trow[0] = INT64_MIN;
                 len = 1;
@@ -51,14 +51,21 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 int64_t k;
                 if (O.start_policy == TEMPEST_START_UNIFORM_EDGE) {
                     k = uniform_index_k(k1, V.m);
+                    if (V.back) k = V.m - 1 - k;
                 } else {
-                    const int64_t g = sampler_index_k(k1, V.G, start_bias(bias), V.rate_start);
+                    int64_t g = sampler_index_k(k1, V.G, start_bias(bias), V.rate_start);
+                    if (V.back) g = V.G - 1 - g;
                     int64_t a, b;
                     ts_group_range(V, g, a, b);
-                    k = a + uniform_index_k(k2, b - a);
+                    k = V.back ? b - 1 - uniform_index_k(k2, b - a) : a + uniform_index_k(k2, b - a);
                 }
                 int32_t s = V.st_src[k], d = V.st_dst[k];
                 const int64_t t0 = V.st_ts[k];
+                if (V.back_swap) {
+                    const int32_t x = s;
+                    s = d;
+                    d = x;
+                }
                 if (!V.directed && (r.r3 & 1u)) {
                     const int32_t x = s;
                     s = d;
@@ -72,14 +79,25 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 hops++;
                 bytes += START_MODEL_BYTES;
                 v = d;
-                t = t0;
+                t = search_time(V, t0);
             }
             while (len < L) {
                 const uint32_t h = (uint32_t)(len - 1);  // counter of the draw for position len
                 int32_t g0, g1;
                 node_groups(V, v, g0, g1);
                 const int32_t c = first_later(V, v, g0, g1, t);
-                if (c == g1) break;  // Gamma_t(v) is empty
+                if (V.back ? c == g0 : c == g1) break;  // Gamma_t(v) is empty
+                if (V.back) {
+                    const Entry e = draw_entry_back(V, O, w, h, bias, g0, c);
+                    nrow[len] = e.other;
+                    trow[len] = e.ts;
+                    hops++;
+                    bytes += hop_model_bytes((int64_t)(g1 - g0));
+                    v = e.other;
+                    t = e.ts - 1;
+                    len++;
+                    continue;
+                }
                 r = walk_rand(O.seed, (uint64_t)w, h);
                 const uint64_t h1 = u53_bits(r.r0, r.r1);
                 int64_t idx;
@@ -336,15 +354,17 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 const Rand4 r = walk_rand(Pv.seed(cx), Pv.wid(cx), 0u);
                 const uint64_t u1 = u53_bits(r.r0, r.r1);
                 s.ud = u53_bits(r.r2, r.r3);
-                s.orient = (!V.directed && (r.r3 & 1u)) ? 1u : 0u;
+                s.orient = ((!V.directed && (r.r3 & 1u)) ? 1u : 0u) ^ (V.back_swap ? 1u : 0u);
                 if (Pv.policy(cx) == TEMPEST_START_UNIFORM_EDGE) {
-                    const int64_t k = uniform_index_k(u1, V.m);
+                    int64_t k = uniform_index_k(u1, V.m);
+                    if (V.back) k = V.m - 1 - k;
                     y0 = __ldg(V.st_ts + k);
                     z0 = __ldg(V.st_src + k);
                     z1 = __ldg(V.st_dst + k);
                     s.state = S_EDGE;
                 } else {
-                    const int64_t g = sampler_index_k(u1, V.G, start_bias(bias), V.rate_start);
+                    int64_t g = sampler_index_k(u1, V.G, start_bias(bias), V.rate_start);
+                    if (V.back) g = V.G - 1 - g;
                     z0 = __ldg(V.tg + g);
                     z1 = __ldg(V.tg + g + 1);
                     s.state = S_SGROUP;
@@ -359,7 +379,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 s.len = 1;
                 s.hop = 0;
                 s.v = z0;
-                s.t = INT64_MIN;
+                s.t = pernode_time(V);
                 load_range(V.ngr + z0, z0, z1, z2, y0, y1);
                 s.state = S_RANGE;
                 break;
@@ -367,7 +387,8 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             case S_SGROUP: {
                 const int32_t x = (int32_t)((uint32_t)z0 - V.s_lo);
                 const int64_t a = x > 0 ? x : 0;
-                const int64_t k = a + uniform_index_k(s.ud, (int64_t)(int32_t)((uint32_t)z1 - V.s_lo) - a);
+                const int64_t b = (int64_t)(int32_t)((uint32_t)z1 - V.s_lo);
+                const int64_t k = V.back ? b - 1 - uniform_index_k(s.ud, b - a) : a + uniform_index_k(s.ud, b - a);
                 y0 = __ldg(V.st_ts + k);
                 z0 = __ldg(V.st_src + k);
                 z1 = __ldg(V.st_dst + k);
@@ -390,7 +411,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 s.len = 2;
                 s.hop = 1;
                 s.v = b;
-                s.t = y0;
+                s.t = search_time(V, y0);
                 hops++;
                 bytes += START_MODEL_BYTES;
                 if (s.len >= s.cap_len) {
@@ -402,16 +423,21 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 break;
             }
             case S_RANGE: {
-                // z0, z1: groups; z2: bucket base; y0, y1: first / last ts
+                // z0, z1: groups; z2: bucket base; y0, y1: first / last ts.
+                // Forward, c = g0 takes every group and c = g1 none;
+                // backward, the range [g0, c) flips both.
                 s.g0 = z0;
                 s.g1 = z1;
                 if (z0 == z1) {
                     finish = true;
                 } else if (s.t < y0) {
                     s.R = s.g0;  // all of the node's groups are later than t
-                    pick = true;
+                    if (V.back) finish = true;
+                    else pick = true;
                 } else if (s.t >= y1) {
-                    finish = true;  // Gamma_t(v) is empty
+                    s.R = s.g1;  // none is later than t: Gamma_t(v) is empty forward
+                    if (V.back) pick = true;
+                    else finish = true;
                 } else if (V.bkt && s.g1 - s.g0 >= BKT_MIN_G) {
                     // y0 <= t < y1: the bucket of t brackets c
                     const uint32_t k = bkt_index(bkt_map(y0, y1, bkt_count(s.g1 - s.g0, V.bkt_log)), s.t);
@@ -498,7 +524,8 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 break;
             }
             case S_PICK2: {
-                const int64_t idx = (int64_t)z0 + uniform_index_k(s.ud, (int64_t)(z1 - z0));
+                const int64_t q = uniform_index_k(s.ud, (int64_t)(z1 - z0));
+                const int64_t idx = V.back ? (int64_t)z1 - 1 - q : (int64_t)z0 + q;
                 const Entry *e = V.ent + idx;
                 y0 = __ldg(&e->ts);
                 z0 = __ldg(&e->other);
@@ -513,7 +540,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 s.len++;
                 s.hop++;
                 s.v = z0;
-                s.t = y0;
+                s.t = search_time(V, y0);
                 if (s.len >= s.cap_len) {
                     finish = true;
                 } else {
@@ -533,7 +560,20 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             const uint64_t u1 = u53_bits(r.r0, r.r1);
             const int hb = hop_bias(V, s.bias, Pv.cnt());
             s.state = S_PICK2;
-            if (hb == BIAS_UNIFORM) {
+            if (V.back) {
+                // groups [g0, c) in the mirrored order (latest first)
+                if (hb == BIAS_UNIFORM) {
+                    s.ud = u1;
+                    z0 = __ldg(V.ngo + s.g0);
+                    z1 = __ldg(V.ngo + c);
+                } else {
+                    s.ud = u53_bits(r.r2, r.r3);
+                    const int32_t gg =
+                        c - 1 - (int32_t)sampler_index_k(u1, (int64_t)(c - s.g0), start_bias(hb), V.rate_hop);
+                    z0 = __ldg(V.ngo + gg);
+                    z1 = __ldg(V.ngo + gg + 1);
+                }
+            } else if (hb == BIAS_UNIFORM) {
                 s.ud = u1;
                 z0 = __ldg(V.ngo + c);
                 z1 = __ldg(V.ngo + s.g1);
@@ -663,12 +703,16 @@ static void kernel_mark(tempest_t *h, int which)
     if (which == 1) h->kev_valid = true;
 }
 
-int walks_multi_launch(tempest_t *h, const ReqDesc *dev_reqs, int n_req, int64_t total, WalkCounters *cnt,
-                       cudaStream_t st)
+int walks_multi_launch(tempest_t *h, int direction, const ReqDesc *dev_reqs, int n_req, int64_t total,
+                       WalkCounters *cnt, cudaStream_t st, bool clear)
 {
-    cudaMemsetAsync(cnt, 0, sizeof(WalkCounters), st);
+    // the walk-id counter always restarts; the statistics only when asked
+    if (clear) cudaMemsetAsync(cnt, 0, sizeof(WalkCounters), st);
+    else cudaMemsetAsync(&cnt->pad, 0, sizeof(cnt->pad), st);
     if (total <= 0 || n_req <= 0) return cuda_check(h, cudaGetLastError(), "walks multi");
-    const WalkView V = make_view(h);
+    tempest_t *vh = view_handle(h, direction);
+    if (!vh) return fail(h, TEMPEST_EINVAL, "backward walks of a directed graph need tempest_enable_backward");
+    const WalkView V = make_view(vh, direction);
     const bool mark = st == h->stream;
     if (mark) kernel_mark(h, 0);
     launch_stream(h, V, ManyReq{dev_reqs, n_req, total, cnt}, &cnt->pad, total, st);
@@ -699,9 +743,27 @@ int sample_index_run(tempest_t *h, const uint64_t *ub, const int64_t *n, int64_t
     return cuda_check(h, cudaGetLastError(), "sample_index");
 }
 
-WalkView make_view(tempest_t *h)
+tempest_t *view_handle(tempest_t *h, int direction)
+{
+    if (direction == 0 || !h->directed) return h;
+    tempest_t *r = h->rev;
+    if (!r) return nullptr;
+    // the reversed index follows the main handle's stream and settings
+    r->stream = h->stream;
+    r->lam_hop = h->lam_hop;
+    r->lam_start = h->lam_start;
+    if (r->bkt_log != h->bkt_log) {
+        r->bkt_log = h->bkt_log;
+        r->bkt_ver = -1;
+    }
+    return r;
+}
+
+WalkView make_view(tempest_t *h, int back)
 {
     WalkView V;
+    V.back = back;
+    V.back_swap = back && !h->directed;
     V.st_src = h->st_src[h->cur].as<int32_t>() + h->s_lo;
     V.st_dst = h->st_dst[h->cur].as<int32_t>() + h->s_lo;
     V.st_ts = h->st_ts[h->cur].as<int64_t>() + h->s_lo;
@@ -716,7 +778,7 @@ WalkView make_view(tempest_t *h)
     const bool bk = h->n_big > 0 && h->bkt_ver == h->state_ver;
     V.bkt = bk ? h->bkt.as<int32_t>() : nullptr;
     V.pn_nodes = h->pn_ver == h->state_ver ? h->pn_nodes.as<int32_t>() : nullptr;
-    V.gs = h->w_on && h->w_valid && h->w_ver == h->state_ver ? h->gs.as<double>() : nullptr;
+    V.gs = !back && h->w_on && h->w_valid && h->w_ver == h->state_ver ? h->gs.as<double>() : nullptr;
     V.bkt_log = h->bkt_log;
     V.directed = h->directed;
     const double ls = h->lam_start > 0.0 ? h->lam_start : (h->G > 0 ? 1.0 / (double)h->G : 1.0);
@@ -729,13 +791,16 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
 {
     int rc;
     h->kev_valid = false;
-    if ((rc = prepare_walk_index(h))) return rc;
-    if ((!rq.bias_arr && rq.bias == TEMPEST_BIAS_EXP_WEIGHT) || rq.want_w || (rq.bias_arr && h->w_on))
+    tempest_t *vh = view_handle(h, rq.direction);
+    if (!vh) return fail(h, TEMPEST_EINVAL, "backward walks of a directed graph need tempest_enable_backward");
+    if ((rc = prepare_walk_index(vh))) return rc;
+    if (rq.direction == 0 &&
+        ((!rq.bias_arr && rq.bias == TEMPEST_BIAS_EXP_WEIGHT) || rq.want_w || (rq.bias_arr && h->w_on)))
         if ((rc = prepare_weights(h))) return rc;
     if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
     cudaStream_t st = h->stream;
     cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);
-    WalkView V = make_view(h);
+    WalkView V = make_view(vh, rq.direction);
     WalkOut O;
     O.n_walks = rq.n_walks;
     O.cap = rq.cap;
