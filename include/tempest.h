@@ -157,10 +157,12 @@ int tempest_set_bias_params(tempest_t *h, double lambda_hop, double lambda_start
  * rest are sorted by timestamp (arrival order among ties) and merged into
  * the edge store; the cut-off advances and the edges before it are evicted;
  * both views are rebuilt (Sec. 2.3).  src, dst: int32[n] node ids >= 0;
- * ts: int64[n], each > INT64_MIN (the time before every edge, which walk
- * outputs give their first node).  stats may be NULL.  EINVAL (state
- * unchanged) on n < 0, NULL arrays with n > 0, a negative id or an INT64_MIN
- * timestamp.  Synchronises the stream. */
+ * ts: int64[n], each strictly between INT64_MIN (the time before every
+ * edge, which walk outputs give their first node) and INT64_MAX (the time
+ * after every edge, where PER_NODE backward walks start).  stats may be
+ * NULL.  EINVAL (state unchanged) on n < 0, NULL arrays with n > 0, a
+ * negative id or an INT64_MIN or INT64_MAX timestamp.  Synchronises the
+ * stream. */
 int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const int64_t *ts,
                    int64_t n, tempest_ingest_stats *stats);
 

@@ -31,7 +31,7 @@ struct DBuf {
 // Small device-side record the ingest kernels fill and the host reads back.
 struct IngestScratch {
     long long ts_min, ts_max;
-    int max_id, neg_id;  // neg_id: bit 0 a negative id, bit 1 an INT64_MIN timestamp
+    int max_id, neg_id;  // neg_id: bit 0 a negative id, bit 1 an INT64_MIN, bit 2 an INT64_MAX timestamp
     unsigned long long late, unsorted;
     long long cut;          // new cut-off
     int has_cut, pad0;

@@ -46,7 +46,7 @@ __global__ void k_batch_stats(const int32_t *__restrict__ src, const int32_t *__
         tmin = min(tmin, t);
         tmax = max(tmax, t);
         maxid = max(maxid, max(a, b));
-        neg |= (a < 0) | (b < 0) | ((t == LLONG_MIN) ? 2 : 0);
+        neg |= (a < 0) | (b < 0) | ((t == LLONG_MIN) ? 2 : 0) | ((t == LLONG_MAX) ? 4 : 0);
         late += (has_cut && t < cut) ? 1ull : 0ull;
         if (i > 0 && ts[i - 1] > t) uns++;
     }
@@ -351,6 +351,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "batch stats"))) return rc;
     if (hs->neg_id & 1) return fail(h, TEMPEST_EINVAL, "tempest_ingest: negative node id");
     if (hs->neg_id & 2) return fail(h, TEMPEST_EINVAL, "tempest_ingest: timestamp INT64_MIN is reserved");
+    if (hs->neg_id & 4) return fail(h, TEMPEST_EINVAL, "tempest_ingest: timestamp INT64_MAX is reserved");
     const int64_t N_new = (n > 0 && (int64_t)hs->max_id + 1 > h->N) ? (int64_t)hs->max_id + 1 : h->N;
     const int64_t late = (int64_t)hs->late;
     const bool sorted = hs->unsorted == 0;

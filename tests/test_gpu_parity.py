@@ -350,12 +350,15 @@ def test_per_node_walks_in_a_batched_launch():
     assert all(torch.equal(a, b) for a, b in zip(alone, outs))
 
 
-def test_int64_min_timestamp_is_rejected():
-    eng, _ = pair(0, 1)
+@pytest.mark.parametrize("bad", [np.iinfo(np.int64).min, np.iinfo(np.int64).max])
+def test_reserved_timestamps_are_rejected(bad):
+    eng, orc = pair(0, 1)
+    ingest_both(eng, orc, [0, 1], [1, 2], [5, 6])
     with pytest.raises(_lib.TempestError) as e:
-        eng.ingest(torch.tensor([0], dtype=torch.int32).cuda(), torch.tensor([1], dtype=torch.int32).cuda(),
-                   torch.tensor([np.iinfo(np.int64).min], dtype=torch.int64).cuda())
+        eng.ingest(torch.tensor([0, 3], dtype=torch.int32).cuda(), torch.tensor([1, 3], dtype=torch.int32).cuda(),
+                   torch.tensor([7, bad], dtype=torch.int64).cuda())
     assert e.value.code == _lib.TEMPEST_EINVAL
+    assert_state_equal(eng.state(), orc.state(), "state unchanged")
 
 
 
