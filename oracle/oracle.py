@@ -21,7 +21,8 @@ SRC = os.path.join(HERE, "tempest_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
 
-BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP, BIAS_EXP_WEIGHT = 0, 1, 2, 3
+BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP, BIAS_EXP_WEIGHT, BIAS_NODE2VEC = 0, 1, 2, 3, 4
+N2V_MAX_TRIALS = 4096
 START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 
 
@@ -56,6 +57,7 @@ def lib():
                                 vp, vp, vp, vp, vp]
         L.orc_counts.argtypes = [vp, vp]
         L.orc_set_weight_rate.argtypes = [vp, dbl]
+        L.orc_set_node2vec.argtypes = [vp, dbl, dbl]
         L.orc_weight_pick.argtypes = [vp, vp, i64, dbl, dbl, vp]
         L.orc_weight_pick.restype = i64
         L.orc_active_nodes.argtypes = [vp, vp]
@@ -171,6 +173,11 @@ class Oracle:
     def set_weight_rate(self, lambda_w):
         if lib().orc_set_weight_rate(self._h, float(lambda_w)) != 0:
             raise ValueError("bad weight rate")
+
+    def set_node2vec(self, p, q):
+        """Return (p) and in-out (q) parameters of Temporal Node2Vec walks (bias 4)."""
+        if lib().orc_set_node2vec(self._h, float(p), float(q)) != 0:
+            raise ValueError("Node2Vec p, q must lie in [1e-3, 1e3]")
 
     def active_nodes(self, direction=0):
         """Nodes with at least one live entry in the node view (the in-view for

@@ -59,6 +59,10 @@
 #define BIAS_LINEAR 1
 #define BIAS_EXP 2
 #define BIAS_EXP_WEIGHT 3
+#define BIAS_NODE2VEC 4
+
+/* Temporal Node2Vec: proposals drawn per hop before the walk ends */
+#define N2V_MAX_TRIALS 4096
 
 #define START_UNIFORM_EDGE 0
 #define START_BIASED_TS 1
@@ -81,6 +85,7 @@ typedef struct orc {
     double lambda_hop;   /* exponential rate per timestamp group for hops */
     double lambda_start; /* > 0: fixed rate for start selection; 0: 1/G_tot */
     double lambda_w;     /* weight-based sampler: rate per timestamp unit */
+    double n2v_p, n2v_q; /* Temporal Node2Vec return / in-out parameters */
 
     orc_edge *live; /* live edges in (ts, seq) order */
     int64_t m;
@@ -127,12 +132,19 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* The random block a walk uses at a hop (hop 0 = start selection). */
-static void walk_block(uint64_t seed, uint64_t walk, uint32_t hop, uint32_t r[4])
+/* The random block a walk uses at a hop (hop 0 = start selection); word 1
+ * of the counter numbers the draws of one hop (0 for every sampler but the
+ * Node2Vec rejection loop). */
+static void draw_block(uint64_t seed, uint64_t walk, uint32_t hop, uint32_t word1, uint32_t r[4])
 {
-    uint32_t ctr[4] = {hop, 0u, (uint32_t)walk, (uint32_t)(walk >> 32)};
+    uint32_t ctr[4] = {hop, word1, (uint32_t)walk, (uint32_t)(walk >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     orc_philox4x32_10(ctr, key, r);
+}
+
+static void walk_block(uint64_t seed, uint64_t walk, uint32_t hop, uint32_t r[4])
+{
+    draw_block(seed, walk, hop, 0u, r);
 }
 
 /* 53-bit uniform in [0, 1) from two 32-bit words. */
@@ -214,6 +226,8 @@ orc *orc_create(int64_t window, int directed)
     o->lambda_hop = 1.0;
     o->lambda_start = 0.0;
     o->lambda_w = 1e-9;
+    o->n2v_p = 1.0;
+    o->n2v_q = 1.0;
     o->ts_group_off = (int64_t *)calloc(1, sizeof(int64_t));
     o->node_off = (int64_t *)calloc(1, sizeof(int64_t));
     o->node_gidx = (int64_t *)calloc(1, sizeof(int64_t));
@@ -274,6 +288,14 @@ int64_t orc_weight_pick(const int64_t *ts, const int64_t *size, int64_t n, doubl
         }
     }
     return n - 1;
+}
+
+int orc_set_node2vec(orc *o, double p, double q)
+{
+    if (!(p >= 1e-3 && p <= 1e3) || !(q >= 1e-3 && q <= 1e3)) return ORC_EINVAL;
+    o->n2v_p = p;
+    o->n2v_q = q;
+    return ORC_OK;
 }
 
 int orc_set_bias_params(orc *o, double lambda_hop, double lambda_start)
@@ -481,6 +503,17 @@ static double rel_margin(double x, int64_t n)
     return r / s;
 }
 
+/* Live (from, to) pairs for the Temporal Node2Vec adjacency test: sorted
+ * keys from << 32 | to, both orientations for undirected graphs. */
+typedef struct {
+    uint64_t *key;
+    int64_t n;
+} orc_pairs;
+
+static int64_t n2v_pick(const orc *o, const orc_pairs *P, const int64_t *group_off, const int64_t *order, int64_t lo,
+                        int64_t hi, int back, int64_t prev, uint64_t seed, uint64_t w, uint32_t h, double *margin,
+                        double *bytes);
+
 /*
  * One walk.  Writes up to max_len nodes and timestamps (the first timestamp
  * is INT64_MIN: the start node is reached at no time), returns the length.
@@ -493,7 +526,7 @@ static double rel_margin(double x, int64_t n)
  * positions receive +inf.  bytes (nullable) accumulates the per-hop sector
  * model of the walk's memory traffic.
  */
-static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int start_policy,
+static int32_t one_walk(const orc *o, const orc_pairs *P, uint64_t w, int32_t max_len, int bias, int start_policy,
                         int64_t start_node, uint64_t seed, int32_t *node, int64_t *tsout, double *margin,
                         double lambda_start, double *bytes)
 {
@@ -508,6 +541,7 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
     double u1, u2;
     int32_t len;
     int64_t v, t;
+    int64_t prev = -1; /* the node before v (Temporal Node2Vec), none at a PER_NODE start */
     if (start_policy == START_PER_NODE) {
         node[0] = (int32_t)start_node;
         len = 1;
@@ -521,8 +555,8 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
         if (start_policy == START_UNIFORM_EDGE) {
             k = uniform_index(u1, o->m);
         } else {
-            /* the weight-based bias starts like the index-based exponential */
-            const int sb = bias == BIAS_EXP_WEIGHT ? BIAS_EXP : bias;
+            /* the weight-based and Node2Vec biases start like the index-based exponential */
+            const int sb = (bias == BIAS_EXP_WEIGHT || bias == BIAS_NODE2VEC) ? BIAS_EXP : bias;
             double x = orc_sampler_x(u1, o->G_tot, sb, lambda_start);
             int64_t g = orc_sampler_index(u1, o->G_tot, sb, lambda_start);
             if (margin && sb != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
@@ -538,6 +572,7 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
         tsout[1] = o->live[k].ts;
         len = 2;
         if (bytes) *bytes += 3 * 32.0 + 4 + 4 + 8 + 8 + 4;
+        prev = s;
         v = d;
         t = o->live[k].ts;
     }
@@ -551,6 +586,25 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
         u1 = orc_u53(r[0], r[1]);
         u2 = orc_u53(r[2], r[3]);
         int64_t idx;
+        if (bias == BIAS_NODE2VEC) {
+            const int64_t slot = n2v_pick(o, P, o->node_group_off, o->node_order, c, g1, 0, prev, seed, w, h,
+                                          margin ? &margin[len] : NULL, bytes);
+            if (slot < 0) break; /* every proposal rejected */
+            node[len] = slot_other(o, slot);
+            tsout[len] = slot_ts(o, slot);
+            if (bytes) {
+                int64_t G = g1 - g0;
+                int lg = 0;
+                while (((int64_t)1 << lg) < G + 1) lg++;
+                int search = lg - 2 > 1 ? lg - 2 : 1;
+                *bytes += 32.0 * (1 + search + 1) + 12 + 16;
+            }
+            prev = v;
+            v = node[len];
+            t = tsout[len];
+            len++;
+            continue;
+        }
         if (bias == BIAS_UNIFORM) {
             int64_t e0 = o->node_group_off[c], e1 = o->node_off[v + 1];
             idx = e0 + uniform_index(u1, e1 - e0);
@@ -593,6 +647,7 @@ static int32_t one_walk(const orc *o, uint64_t w, int32_t max_len, int bias, int
             int search = lg - 2 > 1 ? lg - 2 : 1;
             *bytes += 32.0 * (1 + search + 1) + 12 + 16;
         }
+        prev = v;
         v = node[len];
         t = tsout[len];
         len++;
@@ -685,9 +740,9 @@ static int64_t back_other(const orc *o, int64_t slot)
     return o->directed ? o->live[slot].src : slot_other(o, slot);
 }
 
-static int32_t one_walk_back(const orc *o, const orc_inview *iv, uint64_t w, int32_t max_len, int bias,
-                             int start_policy, int64_t start_node, uint64_t seed, int32_t *node, int64_t *tsout,
-                             double *margin, double lambda_start, double *bytes)
+static int32_t one_walk_back(const orc *o, const orc_inview *iv, const orc_pairs *P, uint64_t w, int32_t max_len,
+                             int bias, int start_policy, int64_t start_node, uint64_t seed, int32_t *node,
+                             int64_t *tsout, double *margin, double lambda_start, double *bytes)
 {
     for (int32_t i = 0; i < max_len; i++) {
         node[i] = -1;
@@ -699,6 +754,7 @@ static int32_t one_walk_back(const orc *o, const orc_inview *iv, uint64_t w, int
     double u1, u2;
     int32_t len;
     int64_t v, t;
+    int64_t prev = -1;
     if (start_policy == START_PER_NODE) {
         node[0] = (int32_t)start_node;
         len = 1;
@@ -712,9 +768,10 @@ static int32_t one_walk_back(const orc *o, const orc_inview *iv, uint64_t w, int
         if (start_policy == START_UNIFORM_EDGE) {
             k = o->m - 1 - uniform_index(u1, o->m);
         } else {
-            double x = orc_sampler_x(u1, o->G_tot, bias, lambda_start);
-            int64_t g = o->G_tot - 1 - orc_sampler_index(u1, o->G_tot, bias, lambda_start);
-            if (margin && bias != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
+            const int sb = bias == BIAS_NODE2VEC ? BIAS_EXP : bias;
+            double x = orc_sampler_x(u1, o->G_tot, sb, lambda_start);
+            int64_t g = o->G_tot - 1 - orc_sampler_index(u1, o->G_tot, sb, lambda_start);
+            if (margin && sb != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
             int64_t a = o->ts_group_off[g], size = o->ts_group_off[g + 1] - a;
             k = a + size - 1 - uniform_index(u2, size);
         }
@@ -727,6 +784,7 @@ static int32_t one_walk_back(const orc *o, const orc_inview *iv, uint64_t w, int
         tsout[1] = o->live[k].ts;
         len = 2;
         if (bytes) *bytes += 3 * 32.0 + 4 + 4 + 8 + 8 + 4;
+        prev = a;
         v = b;
         t = o->live[k].ts;
     }
@@ -742,6 +800,25 @@ static int32_t one_walk_back(const orc *o, const orc_inview *iv, uint64_t w, int
         }
         const int64_t c = lo;
         if (c == g0) break; /* Gamma^-_t(v) is empty */
+        if (bias == BIAS_NODE2VEC) {
+            const int64_t slot = n2v_pick(o, P, iv->group_off, iv->order, g0, c, 1, prev, seed, w, h,
+                                          margin ? &margin[len] : NULL, bytes);
+            if (slot < 0) break; /* every proposal rejected */
+            node[len] = (int32_t)back_other(o, slot);
+            tsout[len] = slot_ts(o, slot);
+            if (bytes) {
+                int64_t G = g1 - g0;
+                int lg = 0;
+                while (((int64_t)1 << lg) < G + 1) lg++;
+                int search = lg - 2 > 1 ? lg - 2 : 1;
+                *bytes += 32.0 * (1 + search + 1) + 12 + 16;
+            }
+            prev = v;
+            v = node[len];
+            t = tsout[len];
+            len++;
+            continue;
+        }
         walk_block(seed, w, h, r);
         u1 = orc_u53(r[0], r[1]);
         u2 = orc_u53(r[2], r[3]);
@@ -768,11 +845,123 @@ static int32_t one_walk_back(const orc *o, const orc_inview *iv, uint64_t w, int
             int search = lg - 2 > 1 ? lg - 2 : 1;
             *bytes += 32.0 * (1 + search + 1) + 12 + 16;
         }
+        prev = v;
         v = node[len];
         t = tsout[len];
         len++;
     }
     return len;
+}
+
+/* ------------------------------------------------------------------ */
+/* Temporal Node2Vec (Sec. 2.5).                                      */
+/* ------------------------------------------------------------------ */
+/*
+ * The second-order factor beta(u, w) of a candidate w, reached from the
+ * current node whose predecessor on the walk is u (node2vec's return and
+ * in-out parameters p, q): 1/p when w is u, 1 when w is a neighbour of u,
+ * 1/q otherwise.  Reading: w is a neighbour of u when the window holds a live
+ * edge u -> w (either orientation for undirected graphs); a backward walk
+ * walks the time-reversed graph, whose edge u -> w is the live edge w -> u.
+ * Each hop draws a proposal from the exponential sampler over the candidate
+ * groups (then an edge uniformly inside the group) and accepts it with
+ * probability beta / beta_max, beta_max = max(1/p, 1, 1/q); a rejected
+ * proposal is drawn again.  Proposal k of the hop uses Philox word 1 = k
+ * (proposal 0 is the plain exponential draw), its acceptance uniform the block
+ * with word 1 = 2^31 + k; a proposal whose beta equals beta_max is accepted
+ * without one.  After N2V_MAX_TRIALS rejections the walk ends.
+ */
+static int cmp_u64(const void *a, const void *b)
+{
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static int build_pairs(const orc *o, orc_pairs *P)
+{
+    const int64_t n = o->directed ? o->m : 2 * o->m;
+    P->key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    P->n = 0;
+    if (!P->key) return ORC_ENOMEM;
+    for (int64_t p = 0; p < o->m; p++) {
+        const uint64_t a = (uint64_t)(uint32_t)o->live[p].src, b = (uint64_t)(uint32_t)o->live[p].dst;
+        P->key[P->n++] = a << 32 | b;
+        if (!o->directed) P->key[P->n++] = b << 32 | a;
+    }
+    qsort(P->key, (size_t)P->n, sizeof(uint64_t), cmp_u64);
+    return ORC_OK;
+}
+
+static int pair_live(const orc_pairs *P, int64_t from, int64_t to)
+{
+    const uint64_t k = (uint64_t)(uint32_t)from << 32 | (uint64_t)(uint32_t)to;
+    int64_t lo = 0, hi = P->n;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (P->key[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < P->n && P->key[lo] == k;
+}
+
+/*
+ * One Node2Vec hop over the candidate groups [lo, hi) of a node view
+ * (group_off, order): forward walks index them from lo, backward walks from
+ * hi - 1 with mirrored edges inside a group.  prev < 0 (a PER_NODE start)
+ * accepts the first proposal.  Returns the chosen slot, or -1 when every
+ * proposal was rejected.  margin (nullable) receives the smallest sampler
+ * margin over the proposals drawn; bytes adds 12 + 16 per proposal after the
+ * first and 32 per adjacency lookup (the sector model of the extra reads).
+ */
+static int64_t n2v_pick(const orc *o, const orc_pairs *P, const int64_t *group_off, const int64_t *order, int64_t lo,
+                        int64_t hi, int back, int64_t prev, uint64_t seed, uint64_t w, uint32_t h, double *margin,
+                        double *bytes)
+{
+    const double inv_p = 1.0 / o->n2v_p, inv_q = 1.0 / o->n2v_q;
+    double bmax = inv_p > 1.0 ? inv_p : 1.0;
+    if (inv_q > bmax) bmax = inv_q;
+    const int64_t n = hi - lo;
+    double mg = INFINITY;
+    for (uint32_t k = 0; k < N2V_MAX_TRIALS; k++) {
+        uint32_t r[4];
+        draw_block(seed, w, h, k, r);
+        const double u1 = orc_u53(r[0], r[1]), u2 = orc_u53(r[2], r[3]);
+        const double x = orc_sampler_x(u1, n, BIAS_EXP, o->lambda_hop);
+        const int64_t j = orc_sampler_index(u1, n, BIAS_EXP, o->lambda_hop);
+        const double m1 = rel_margin(x, n);
+        if (m1 < mg) mg = m1;
+        if (k > 0 && bytes) *bytes += 12 + 16;
+        const int64_t gg = back ? hi - 1 - j : lo + j;
+        const int64_t e0 = group_off[gg], e1 = group_off[gg + 1];
+        const int64_t q = uniform_index(u2, e1 - e0);
+        const int64_t slot = order[back ? e1 - 1 - q : e0 + q];
+        if (prev < 0) {
+            if (margin) *margin = mg;
+            return slot;
+        }
+        const int64_t cand = back ? back_other(o, slot) : slot_other(o, slot);
+        double beta;
+        if (cand == prev) {
+            beta = inv_p;
+        } else if (inv_q == 1.0) {
+            beta = 1.0; /* a neighbour or not, the factor is 1 */
+        } else {
+            if (bytes) *bytes += 32;
+            const int adj = back ? pair_live(P, cand, prev) : pair_live(P, prev, cand);
+            beta = adj ? 1.0 : inv_q;
+        }
+        int accept = beta >= bmax;
+        if (!accept) {
+            draw_block(seed, w, h, 0x80000000u | k, r);
+            accept = orc_u53(r[0], r[1]) * bmax < beta;
+        }
+        if (accept) {
+            if (margin) *margin = mg;
+            return slot;
+        }
+    }
+    if (margin) *margin = mg;
+    return -1;
 }
 
 static double eff_lambda_start(const orc *o)
@@ -823,14 +1012,23 @@ int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
         for (int64_t v = 0; v < o->n_nodes; v++)
             if (gx[v + 1] > gx[v]) active[n_active++] = (int32_t)v;
     }
+    /* live pairs for Node2Vec adjacency tests, when a walk takes that bias */
+    orc_pairs pairs = {NULL, 0};
+    int want_pairs = bias_arr == NULL && bias == BIAS_NODE2VEC;
+    for (int64_t i = 0; bias_arr && i < n && !want_pairs; i++) want_pairs = bias_arr[i] == BIAS_NODE2VEC;
+    if (want_pairs && build_pairs(o, &pairs)) {
+        free(active);
+        ORC_WALKS_FAIL(ORC_ENOMEM);
+    }
     double ls = eff_lambda_start(o);
     if (bytes) *bytes = 0.0;
     for (int64_t i = 0; i < n; i++) {
         uint64_t w = ids ? (uint64_t)ids[i] : (uint64_t)i;
         int32_t L = max_len_arr ? max_len_arr[i] : max_len;
         int b = bias_arr ? (int)bias_arr[i] : bias;
-        if (L < 2 || L > max_len_cap || b < 0 || b > 3 || (direction == 1 && b == BIAS_EXP_WEIGHT)) {
+        if (L < 2 || L > max_len_cap || b < 0 || b > 4 || (direction == 1 && b == BIAS_EXP_WEIGHT)) {
             free(active);
+            free(pairs.key);
             ORC_WALKS_FAIL(ORC_EINVAL);
         }
         int64_t start_node = -1;
@@ -838,6 +1036,7 @@ int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
             const int64_t a = (int64_t)(w / (uint64_t)walks_per_node);
             if (a >= n_active) {
                 free(active);
+                free(pairs.key);
                 ORC_WALKS_FAIL(ORC_EINVAL);
             }
             start_node = active[a];
@@ -851,11 +1050,12 @@ int orc_walks(const orc *o, int64_t n, const int64_t *ids, int32_t max_len_cap,
             if (mr) mr[j] = INFINITY;
         }
         if (direction == 1)
-            len[i] = one_walk_back(o, &iv, w, L, b, start_policy, start_node, seed, nr, tr, mr, ls, bytes);
+            len[i] = one_walk_back(o, &iv, &pairs, w, L, b, start_policy, start_node, seed, nr, tr, mr, ls, bytes);
         else
-            len[i] = one_walk(o, w, L, b, start_policy, start_node, seed, nr, tr, mr, ls, bytes);
+            len[i] = one_walk(o, &pairs, w, L, b, start_policy, start_node, seed, nr, tr, mr, ls, bytes);
     }
     free(active);
+    free(pairs.key);
     if (have_iv) free_inview(&iv);
 #undef ORC_WALKS_FAIL
     return ORC_OK;

@@ -133,6 +133,30 @@ def hop_distribution(live, directed, v, t, bias, lam, lam_w=None):
     return dist
 
 
+def node2vec_hop_distribution(live, directed, v, t, prev, lam, p, q):
+    """Temporal Node2Vec (Sec. 2.5): the exponential proposal of
+    hop_distribution reweighted by beta(prev, w) = 1/p (w == prev), 1 (a live
+    edge prev -> w; either orientation when undirected), 1/q otherwise, then
+    normalised: the law of rejection sampling on that proposal with accept
+    probability beta / max(1/p, 1, 1/q).  prev None: the proposal itself."""
+    d = hop_distribution(live, directed, v, t, 2, lam)
+    if prev is None or not d:
+        return d
+
+    def adjacent(a, b):
+        for (_, _, x, y) in live:
+            if (x, y) == (a, b) or (not directed and (y, x) == (a, b)):
+                return True
+        return False
+
+    out = {}
+    for (w, ts), pr in d.items():
+        beta = 1.0 / p if w == prev else (1.0 if adjacent(prev, w) else 1.0 / q)
+        out[(w, ts)] = pr * beta
+    tot = sum(out.values())
+    return {k: x / tot for k, x in out.items()}
+
+
 def start_distribution(live, directed, policy, bias, lam_start):
     """{(first node, second node, ts): probability} of the start edge."""
     m = len(live)
@@ -160,10 +184,12 @@ def start_distribution(live, directed, policy, bias, lam_start):
     return dist
 
 
-def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start, start_node=None, lam_w=None):
+def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start, start_node=None, lam_w=None,
+                      n2v=None):
     """Exact probability of every complete walk (tuple of (node, ts) pairs).
     With start_node the walk starts at that node and its first hop may take
-    any of the node's live edges (the per-node start policy)."""
+    any of the node's live edges (the per-node start policy).  Bias 4 is
+    Temporal Node2Vec with n2v = (p, q)."""
     out = {}
 
     def rec(path, p):
@@ -173,7 +199,11 @@ def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start,
         if len(path) >= max_len:
             out[tuple(path)] = out.get(tuple(path), 0.0) + p
             return
-        d = hop_distribution(live, directed, v, t, bias, lam_hop, lam_w)
+        if bias == 4:
+            prev = path[-2][0] if len(path) >= 2 else None
+            d = node2vec_hop_distribution(live, directed, v, t, prev, lam_hop, *n2v)
+        else:
+            d = hop_distribution(live, directed, v, t, bias, lam_hop, lam_w)
         if not d:
             out[tuple(path)] = out.get(tuple(path), 0.0) + p
             return
@@ -183,7 +213,7 @@ def walk_distribution(live, directed, max_len, bias, policy, lam_hop, lam_start,
     if start_node is not None:
         rec([(start_node, None)], 1.0)
         return out
-    sb = 2 if bias == 3 else bias  # the weight-based bias starts like the index-based exponential
+    sb = 2 if bias in (3, 4) else bias  # weight-based and Node2Vec start like the index-based exponential
     for (a, b, ts), p in start_distribution(live, directed, policy, sb, lam_start).items():
         rec([(a, None), (b, ts)], p)
     return out

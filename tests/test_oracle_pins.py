@@ -479,7 +479,9 @@ def test_backward_walks_are_forward_walks_of_the_reversed_graph(directed, policy
     b.ingest(*_reversed(src, dst, ts))
     na = len(a.active_nodes(1))
     assert na == len(b.active_nodes())
-    for bias in (0, 1, 2):
+    a.set_node2vec(0.5, 3.0)  # Node2Vec's neighbour test reverses with the graph
+    b.set_node2vec(0.5, 3.0)
+    for bias in (0, 1, 2, 4):
         nw = 5 * na if policy == 2 else 3000
         g = a.walks(nw, 9, bias=bias, start_policy=policy, seed=bias + 7, direction=1)
         f = b.walks(nw, 9, bias=bias, start_policy=policy, seed=bias + 7)
@@ -508,3 +510,116 @@ def test_backward_walks_follow_in_edges_back_in_time():
                 assert tsa[i][p] < tsa[i][p - 1]
     with pytest.raises(ValueError):
         o.walks(10, 5, bias=3, direction=1)  # the weight-based bias runs forward only
+
+
+# ------------------------------------------------------ Temporal Node2Vec (Sec. 2.5)
+@pytest.mark.parametrize("directed,policy,pq", [
+    (True, 0, (0.5, 2.0)), (True, 1, (4.0, 0.25)), (False, 0, (0.5, 2.0)), (False, 1, (2.0, 0.5)),
+])
+def test_node2vec_walks_match_enumeration(directed, policy, pq):
+    """Rejection sampling on the exponential proposal gives the second-order
+    law: each hop's exponential proposal reweighted by beta(prev, w) (1/p on
+    a return, 1 to a neighbour of prev, 1/q otherwise) and normalised."""
+    from scipy.stats import chisquare
+    if directed:
+        src = [0, 0, 0, 1, 1, 2, 2, 3, 0, 2, 3, 1]
+        dst = [1, 2, 1, 2, 0, 0, 3, 0, 0, 2, 1, 3]
+        ts = [1, 2, 2, 3, 4, 5, 5, 6, 7, 6, 7, 8]
+    else:  # sparser, so that many candidates are not neighbours of the previous node
+        src = [0, 1, 2, 1, 3, 4, 2, 5, 1, 3, 0, 4]
+        dst = [1, 2, 3, 4, 0, 5, 5, 0, 2, 4, 1, 2]
+        ts = [1, 2, 3, 3, 4, 4, 5, 6, 6, 7, 7, 8]
+    lam_hop, lam_start, max_len = 0.7, 0.4, 4
+    o = O.Oracle(window=0, directed=directed)
+    o.ingest(src, dst, ts)
+    o.set_bias_params(lam_hop, lam_start)
+    o.set_node2vec(*pq)
+    live = brute.window_state([(src, dst, ts)], 0, directed)[-1]["live"]
+    dist = brute.walk_distribution(live, directed, max_len, 4, policy, lam_hop, lam_start, n2v=pq)
+    assert abs(sum(dist.values()) - 1.0) < 1e-9
+    # the second-order law differs from the first-order one on this graph
+    first = brute.walk_distribution(live, directed, max_len, 2, policy, lam_hop, lam_start)
+    assert sum(abs(dist.get(k, 0.0) - first.get(k, 0.0)) for k in set(dist) | set(first)) / 2 > 0.01
+    n = 60_000
+    node, tsa, ln, _, _ = o.walks(n, max_len, bias=4, start_policy=policy, seed=123)
+    counts = {}
+    for i in range(n):
+        k = _walk_key(node[i], tsa[i], ln[i])
+        assert k in dist, k
+        counts[k] = counts.get(k, 0) + 1
+    keys = [k for k in dist if dist[k] * n > 5]
+    obs = np.array([counts.get(k, 0) for k in keys], np.float64)
+    exp = np.array([dist[k] * n for k in keys], np.float64)
+    exp *= obs.sum() / exp.sum()
+    assert chisquare(obs, exp)[1] > 1e-3
+
+
+@pytest.mark.parametrize("directed", [True, False])
+def test_node2vec_per_node_first_hop_is_first_order(directed):
+    """A PER_NODE walk has no predecessor at its first hop: that hop follows
+    the exponential proposal; later hops the second-order law."""
+    from scipy.stats import chisquare
+    src = [0, 0, 0, 1, 1, 2, 2, 3, 0, 2, 5]
+    dst = [1, 2, 1, 2, 0, 0, 3, 0, 0, 2, 1]
+    ts = [1, 2, 2, 3, 4, 5, 5, 6, 7, 6, 3]
+    pq = (0.4, 3.0)
+    o = O.Oracle(window=0, directed=directed)
+    o.ingest(src, dst, ts)
+    o.set_bias_params(0.7, 0.4)
+    o.set_node2vec(*pq)
+    act = list(o.active_nodes())
+    live = brute.window_state([(src, dst, ts)], 0, directed)[-1]["live"]
+    K = 12_000
+    node, tsa, ln, _, _ = o.walks(K * len(act), 4, bias=4, start_policy=O.START_PER_NODE, seed=6)
+    for a, v in enumerate(act):
+        dist = brute.walk_distribution(live, directed, 4, 4, 0, 0.7, 0.4, start_node=v, n2v=pq)
+        counts = {}
+        for i in range(a * K, (a + 1) * K):
+            k = _walk_key(node[i], tsa[i], ln[i])
+            assert k in dist, k
+            counts[k] = counts.get(k, 0) + 1
+        keys = [k for k in dist if dist[k] * K > 5]
+        if len(keys) < 2:
+            continue
+        obs = np.array([counts.get(k, 0) for k in keys], np.float64)
+        exp = np.array([dist[k] * K for k in keys], np.float64)
+        exp *= obs.sum() / exp.sum()
+        assert chisquare(obs, exp)[1] > 1e-3, v
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_node2vec_with_unit_parameters_is_the_exponential_walk(direction):
+    """p = q = 1 makes every beta equal beta_max: every first proposal is
+    accepted, and it is the exponential walk's own draw (Philox word 1 = 0)."""
+    rng = np.random.default_rng(31)
+    src, dst, ts = (list(rng.integers(0, 30, 500)), list(rng.integers(0, 30, 500)),
+                    list(rng.integers(1, 80, 500)))
+    for directed in (True, False):
+        o = O.Oracle(window=0, directed=directed)
+        o.ingest(src, dst, ts)
+        o.set_node2vec(1.0, 1.0)
+        for policy in (0, 1):
+            a = o.walks(2000, 10, bias=4, start_policy=policy, seed=3, direction=direction)
+            b = o.walks(2000, 10, bias=2, start_policy=policy, seed=3, direction=direction)
+            for x, y in zip(a[:3], b[:3]):
+                assert np.array_equal(x, y)
+
+
+def test_node2vec_rejection_cap():
+    """Edges 0 -> 1 (t 1) and 1 -> 0 (t 2): from 1, reached over 0 -> 1, the
+    only candidate returns to 0, accepted with probability (1/p) / 1 = 1e-3;
+    after 4096 rejections the walk ends, so a walk that starts on 0 -> 1 stops
+    at length 2 with probability (1 - 1e-3)^4096."""
+    from scipy.stats import binomtest
+    o = O.Oracle(window=0, directed=True)
+    o.ingest([0, 1], [1, 0], [1, 2])
+    o.set_node2vec(1000.0, 1.0)
+    node, tsa, ln, _, _ = o.walks(40_000, 3, bias=4, seed=17)
+    on01 = (node[:, 0] == 0) & (node[:, 1] == 1)
+    assert on01.sum() > 15_000
+    stops = int((ln[on01] == 2).sum())
+    p_stop = (1 - 1e-3) ** O.N2V_MAX_TRIALS
+    assert binomtest(stops, int(on01.sum()), p_stop).pvalue > 1e-3, (stops, on01.sum(), p_stop)
+    assert (ln[~on01] == 2).all()  # 1 -> 0 at t 2 has no continuation
+    with pytest.raises(ValueError):
+        o.set_node2vec(0.0, 1.0)
