@@ -59,7 +59,21 @@ enum { TEMPEST_BIAS_UNIFORM = 0, TEMPEST_BIAS_LINEAR = 1, TEMPEST_BIAS_EXP = 2,
         * inverse-CDF draw on the running weight (u1) picks the timestamp
         * group, an edge of it is uniform (u2).  A BIASED_TS start draws as
         * TEMPEST_BIAS_EXP does.  See tempest_set_weight_rate. */
-       TEMPEST_BIAS_EXP_WEIGHT = 3 };
+       TEMPEST_BIAS_EXP_WEIGHT = 3,
+       /* Temporal Node2Vec (Sec. 2.5): a hop from v, reached from u, draws
+        * proposals from the TEMPEST_BIAS_EXP sampler over Gamma_t(v) and
+        * accepts one with probability beta(u, w) / beta_max: beta = 1/p when
+        * w is u, 1 when a live edge u -> w exists (either orientation for
+        * undirected graphs; w -> u for backward walks), 1/q otherwise;
+        * beta_max = max(1/p, 1, 1/q).  Proposal k of a hop uses Philox
+        * counter (hop, k, walk) (proposal 0 is the exponential draw), its
+        * acceptance uniform u = (r0:r1 >> 11) 2^-53 of counter (hop, 2^31 +
+        * k, walk), accepted when u * beta_max < beta (drawn only when beta <
+        * beta_max).  After TEMPEST_N2V_MAX_TRIALS rejections the walk ends.
+        * The first hop of a PER_NODE walk has no u and takes proposal 0.
+        * Starts draw as TEMPEST_BIAS_EXP.  See tempest_set_node2vec. */
+       TEMPEST_BIAS_NODE2VEC = 4 };
+#define TEMPEST_N2V_MAX_TRIALS 4096
 
 /* Start selection (Sec. 2.3, timestamp-grouped view; Sec. 3 workloads).
  * UNIFORM_EDGE: a live edge uniformly.  BIASED_TS: a timestamp group of the
@@ -135,6 +149,13 @@ int tempest_destroy(tempest_t *h);
  * group; the first walk call after a change recomputes all of them.  EINVAL
  * on lambda_w <= 0 or not finite. */
 int tempest_set_weight_rate(tempest_t *h, double lambda_w);
+
+/* Return parameter p and in-out parameter q of Temporal Node2Vec walks
+ * (TEMPEST_BIAS_NODE2VEC; default 1, 1).  With q != 1 the neighbour test
+ * matters: the handle builds a table of the live (from, to) pairs now (about
+ * 64 bytes per live edge) and every ingest keeps it current.  EINVAL unless
+ * 1e-3 <= p, q <= 1e3; ENOMEM when the table does not fit. */
+int tempest_set_node2vec(tempest_t *h, double p, double q);
 
 /* Queue all further device work of the handle on stream (a cudaStream_t). */
 int tempest_set_stream(tempest_t *h, void *stream);

@@ -22,7 +22,8 @@ TEMPEST_ECUDA = -3
 TEMPEST_ETIMEDOUT = -4
 TEMPEST_EBUSY = -5
 
-BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP, BIAS_EXP_WEIGHT = 0, 1, 2, 3
+BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP, BIAS_EXP_WEIGHT, BIAS_NODE2VEC = 0, 1, 2, 3, 4
+N2V_MAX_TRIALS = 4096
 START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH = 0, 1, 2, 3
 TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS = 0, 1, 2, 3
@@ -43,7 +44,7 @@ EXPORTED = (
     "tempest_server_release", "tempest_server_drain", "tempest_server_stats",
     "tempest_set_tuning", "tempest_get_tuning", "tempest_autotune", "tempest_autotune_mixed",
     "tempest_active_nodes", "tempest_set_weight_rate", "tempest_enable_backward", "tempest_walks_backward",
-    "tempest_active_nodes_backward",
+    "tempest_active_nodes_backward", "tempest_set_node2vec",
 )
 NOALLOC_MAX_EDGES = 262144
 
@@ -140,6 +141,7 @@ def load():
     L.tempest_active_nodes.argtypes = [vp, ctypes.POINTER(i64)]
     L.tempest_set_weight_rate.argtypes = [vp, dbl]
     L.tempest_enable_backward.argtypes = [vp]
+    L.tempest_set_node2vec.argtypes = [vp, dbl, dbl]
     L.tempest_walks_backward.argtypes = [vp, i64, i32, ci, ci, u64, vp, vp, vp]
     L.tempest_active_nodes_backward.argtypes = [vp, ctypes.POINTER(i64)]
     L.tempest_autotune_mixed.argtypes = [vp, i64, vp, ctypes.c_int32, vp, ci, ctypes.c_uint64, ctypes.c_int32,
@@ -502,6 +504,10 @@ class Engine:
         """Number of nodes with a live entry (in-entry when direction is 1): PER_NODE walk counts are
         multiples of it."""
         return tempest_active_nodes(self.h, direction)
+
+    def set_node2vec(self, p: float, q: float):
+        """Return / in-out parameters of Temporal Node2Vec walks (BIAS_NODE2VEC)."""
+        _check(self.h, load().tempest_set_node2vec(self.h, float(p), float(q)))
 
     def enable_backward(self):
         """Keep the in-edge index that backward walks of a directed graph read."""

@@ -115,7 +115,7 @@ static void free_all(tempest_t *h)
                     &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt,
                     &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched,   &h->tg2,       &h->nbeg,
                     &h->pn_nodes,  &h->gw,        &h->gs,        &h->wref,      &h->w_cbase,   &h->w_ctot,
-                    &h->w_coff};
+                    &h->w_coff,    &h->co_prev,   &h->pt};
     for (DBuf *b : bufs) release(h, *b);
 }
 
@@ -318,12 +318,14 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
     tempest_t *vh = view_handle(h, direction);
     if (!vh) return fail(h, TEMPEST_EINVAL, "backward walks of a directed graph need tempest_enable_backward");
     if (direction && !bias_arr && bias == TEMPEST_BIAS_EXP_WEIGHT)
-        return fail(h, TEMPEST_EINVAL, "walks: backward walks take biases 0-2");
+        return fail(h, TEMPEST_EINVAL, "walks: the weight-based bias runs forward only");
+    if (!bias_arr && bias == TEMPEST_BIAS_NODE2VEC && h->n2v_q != 1.0 && !h->pt_on)
+        return fail(h, TEMPEST_EINVAL, "walks: the Node2Vec pair table was dropped; call tempest_set_node2vec");
     if (n_walks < 0) return fail(h, TEMPEST_EINVAL, "walks: n_walks < 0");
     if (cap < 2) return fail(h, TEMPEST_EINVAL, "walks: max_len must be >= 2");
     if (start_policy < TEMPEST_START_UNIFORM_EDGE || start_policy > TEMPEST_START_PER_NODE)
         return fail(h, TEMPEST_EINVAL, "walks: unknown start policy %d", start_policy);
-    if (!bias_arr && (bias < 0 || bias > 3)) return fail(h, TEMPEST_EINVAL, "walks: unknown bias %d", bias);
+    if (!bias_arr && (bias < 0 || bias > 4)) return fail(h, TEMPEST_EINVAL, "walks: unknown bias %d", bias);
     if (n_walks > 0 && (!node || !ts || !len)) return fail(h, TEMPEST_EINVAL, "walks: NULL output");
     if (n_walks > 0 && (int64_t)cap * n_walks / n_walks != (int64_t)cap)
         return fail(h, TEMPEST_EINVAL, "walks: output size overflows");
@@ -346,7 +348,7 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
                             len_arr[i], cap);
     if (host_bias)
         for (int64_t i = 0; i < n_walks; i++)
-            if (bias_arr[i] > (direction ? 2 : 3))
+            if (bias_arr[i] > 4 || (direction && bias_arr[i] == TEMPEST_BIAS_EXP_WEIGHT))
                 return fail(h, TEMPEST_EINVAL, "walks_mixed: bias_arr[%lld] = %d unknown%s", (long long)i,
                             bias_arr[i], direction ? " for backward walks" : "");
     if (host_len || host_bias) {
@@ -390,8 +392,11 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
     }
     WalkRequest rq{n_walks, cap, max_len, d_len, bias, d_bias, start_policy, pn_k, seed, d_node, d_ts, d_lenout};
     rq.direction = direction;
-    if (host_bias)
+    if (host_bias) {
         for (int64_t i = 0; i < n_walks && !rq.want_w; i++) rq.want_w = bias_arr[i] == TEMPEST_BIAS_EXP_WEIGHT;
+        rq.may_n2v = 0;
+        for (int64_t i = 0; i < n_walks && !rq.may_n2v; i++) rq.may_n2v = bias_arr[i] == TEMPEST_BIAS_NODE2VEC;
+    }
     if ((rc = walks_run(h, rq))) return rc;
     if (!dev_ts) cudaMemcpyAsync(ts, d_ts, sizeof(int64_t) * cells, cudaMemcpyDeviceToHost, st);
     if (!dev_node) cudaMemcpyAsync(node, d_node, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st);

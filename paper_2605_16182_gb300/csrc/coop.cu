@@ -42,6 +42,7 @@ struct CoopState {
     int32_t *ws_node;   // current node of each walk
     int64_t *ws_t;      // current time
     int32_t *ws_len;    // nodes written so far
+    int32_t *ws_prev;   // the node before the current one (Node2Vec; -1: none)
     const uint32_t *sorted_walks;
     int32_t *next_active;
     unsigned int *n_next;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(256) k_coop_start(const WalkView V, const Walk
             O.len[w] = 0;
             continue;
         }
-        int32_t s, d, len0;
+        int32_t s = -1, d, len0;
         int64_t t0;
         if (O.start_policy == TEMPEST_START_PER_NODE) {
             // the walk starts at an active node before every live edge
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(256) k_coop_start(const WalkView V, const Walk
             S.ws_node[w] = d;
             S.ws_t[w] = t0;
             S.ws_len[w] = len0;
+            S.ws_prev[w] = len0 == 2 ? s : -1;
             const unsigned am = __activemask();
             const int lane = threadIdx.x & 31;
             const int leader = __ffs(am) - 1;
@@ -187,8 +189,17 @@ __device__ __forceinline__ void coop_hop(const WalkView &V, const WalkOut &O, co
         O.len[w] = len;  // Gamma_t(v) is empty
         return;
     }
-    const Entry e = V.back ? draw_entry_back(V, O, w, (uint32_t)(len - 1), bias, g0, c)
-                           : draw_entry(V, O, w, (uint32_t)(len - 1), bias, c, g1);
+    Entry e;
+    if (bias == BIAS_NODE2VEC) {
+        if (!draw_n2v(V, O, w, (uint32_t)(len - 1), g0, c, g1, S.ws_prev[w], e, bytes)) {
+            O.len[w] = len;  // every proposal rejected
+            return;
+        }
+        S.ws_prev[w] = v;
+    } else {
+        e = V.back ? draw_entry_back(V, O, w, (uint32_t)(len - 1), bias, g0, c)
+                   : draw_entry(V, O, w, (uint32_t)(len - 1), bias, c, g1);
+    }
     O.node[w * (int64_t)O.cap + len] = e.other;
     O.ts[w * (int64_t)O.cap + len] = e.ts;
     hops++;
@@ -352,6 +363,7 @@ static void record_graph_walk(tempest_t *h, const WalkView &V, const WalkOut &O,
     S.ws_node = h->co_node.as<int32_t>();
     S.ws_t = h->co_t.as<int64_t>();
     S.ws_len = h->co_len.as<int32_t>();
+    S.ws_prev = h->co_prev.as<int32_t>();
     S.sorted_walks = nullptr;
     S.next_active = h->co_act[0].as<int32_t>();
     S.n_next = ctr;
@@ -378,6 +390,7 @@ int graph_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launch
     if ((rc = ensure(h, h->co_node, sizeof(int32_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_t, sizeof(int64_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_len, sizeof(int32_t) * nz, true))) return rc;
+    if ((rc = ensure(h, h->co_prev, sizeof(int32_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_act[0], sizeof(int32_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_act[1], sizeof(int32_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_ctr, 64 * sizeof(unsigned int)))) return rc;
@@ -455,6 +468,7 @@ int coop_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launche
     if ((rc = ensure(h, h->co_node, sizeof(int32_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_t, sizeof(int64_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_len, sizeof(int32_t) * nz, true))) return rc;
+    if ((rc = ensure(h, h->co_prev, sizeof(int32_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_act[0], sizeof(int32_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_act[1], sizeof(int32_t) * nz, true))) return rc;
     if ((rc = ensure(h, h->co_runs, sizeof(int32_t) * 2 * nz, true))) return rc;
@@ -474,6 +488,7 @@ int coop_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launche
     S.ws_node = h->co_node.as<int32_t>();
     S.ws_t = h->co_t.as<int64_t>();
     S.ws_len = h->co_len.as<int32_t>();
+    S.ws_prev = h->co_prev.as<int32_t>();
     int cur = 0;
     S.next_active = h->co_act[cur].as<int32_t>();
     S.n_next = ctr + 8;

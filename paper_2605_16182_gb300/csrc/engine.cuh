@@ -176,7 +176,7 @@ struct tempest {
     tw::DBuf hist, partials;
     tw::DBuf ev;                 // int32 [N+1] per-node evicted entries (zero between batches)
     // cooperative scheduler: walk state, active lists, runs, tier tasks, counters
-    tw::DBuf co_node, co_t, co_len, co_act[2], co_runs, co_tasks, co_ctr;
+    tw::DBuf co_node, co_t, co_len, co_prev, co_act[2], co_runs, co_tasks, co_ctr;
     int coop_w_warp = 4;         // solo / warp boundary W_warp (Sec. 3.5)
     int coop_mega = 8192;        // mega-hub split (Sec. 2.4.4)
     int stream_ctas = 0;         // persistent walker CTAs per SM (0: occupancy limit)
@@ -191,6 +191,14 @@ struct tempest {
     tw::DBuf in_stage;    // device staging of host walk inputs
     tw::DBuf exp_stage;   // export staging
     void *hstat = nullptr;     // pinned host mirror of IngestScratch / counters
+
+    // Temporal Node2Vec: return / in-out parameters; the live-pair table kept
+    // by ingest once q != 1 (pt_cap slots, a power of two; pt_ub bounds the
+    // used slots)
+    double n2v_p = 1.0, n2v_q = 1.0;
+    bool pt_on = false;
+    tw::DBuf pt;
+    int64_t pt_cap = 0, pt_ub = 0;
 
     // backward walks of directed graphs: a handle over the reversed edges
     // (dst, src, ts), fed every batch; its node view is the in-view
@@ -225,6 +233,11 @@ int nv_export(tempest_t *h, int which, int32_t *out);
 // timestamp-group starts relative to the live head, plus m (G + 1 values)
 int ts_export(tempest_t *h, int32_t *out);
 
+// pairs.cu
+int pt_rebuild(tempest_t *h, unsigned long long *status);
+int pt_update(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_t n_ev, int64_t add_lo,
+              int64_t n_add, unsigned long long *status);
+
 // walks.cu
 struct WalkRequest;
 // the handle whose index a walk of the given direction reads (h itself for
@@ -245,6 +258,7 @@ struct WalkRequest {
     int32_t *len;              // device
     int want_w = 0;            // per-walk biases known to include the weight-based one
     int direction = 0;         // 1: backward walks
+    int may_n2v = 1;           // per-walk biases may include Node2Vec (host arrays are scanned)
 };
 int walks_run(tempest_t *h, const WalkRequest &rq);
 // builds the time-bucket tables of the live state on the handle's stream

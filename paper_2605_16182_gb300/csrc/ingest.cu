@@ -517,6 +517,20 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     }
     if (nv_full && (rc = nv_build(h))) return rc;
 
+    // 7. Node2Vec pair table: the evicted edges out, the kept batch in (a
+    // rebuild after a merge, whose evicted edges are not a store range)
+    if (h->pt_on) {
+        rc = append ? pt_update(h, h->st_src[old_buf].as<int32_t>() + old_lo,
+                                h->st_dst[old_buf].as<int32_t>() + old_lo, i0, new_lo, nbk, &ds->status)
+                    : pt_rebuild(h, &ds->status);
+        if (rc) {
+            // walks need the table again: tempest_set_node2vec rebuilds it
+            h->pt_on = false;
+            release(h, h->pt);
+            return rc;
+        }
+    }
+
     cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ingest"))) return rc;
     if (hs->status)

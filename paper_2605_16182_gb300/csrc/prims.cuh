@@ -42,6 +42,15 @@ __device__ __forceinline__ Rand4 walk_rand(uint64_t seed, uint64_t walk, uint32_
                          (uint32_t)(seed >> 32));
 }
 
+// The block of draw `word1` of a hop (the Node2Vec rejection loop: proposal k
+// uses word1 = k, its acceptance uniform word1 = 2^31 + k; word1 = 0 is
+// walk_rand's block).
+__device__ __forceinline__ Rand4 walk_rand2(uint64_t seed, uint64_t walk, uint32_t hop, uint32_t word1)
+{
+    return philox4x32_10(hop, word1, (uint32_t)walk, (uint32_t)(walk >> 32), (uint32_t)seed,
+                         (uint32_t)(seed >> 32));
+}
+
 // 53-bit uniform in [0, 1): exact in double.
 __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo)
 {

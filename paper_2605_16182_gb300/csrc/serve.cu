@@ -37,7 +37,7 @@ static int build_table(tempest_t *h, const tempest_walk_request *reqs, int n, Re
     for (int i = 0; i < n; i++) {
         const tempest_walk_request &q = reqs[i];
         if (q.n_walks < 0 || q.max_len < 2 || q.start_policy < 0 || q.start_policy > TEMPEST_START_PER_NODE ||
-            (!q.bias_arr && (q.bias < 0 || q.bias > 3)))
+            (!q.bias_arr && (q.bias < 0 || q.bias > 4)))
             return fail(h, TEMPEST_EINVAL, "walk request %d: bad n_walks, max_len, bias or start policy", i);
         if (q.n_walks > 0 && (!is_device_ptr(q.node) || !is_device_ptr(q.ts) || !is_device_ptr(q.len)))
             return fail(h, TEMPEST_EINVAL, "walk request %d: outputs must be device memory", i);
@@ -89,6 +89,15 @@ static int prepare_for(tempest_t *h, int direction, const ReqDesc *t, int n)
         if ((!t[i].bias_arr && t[i].bias == TEMPEST_BIAS_EXP_WEIGHT) || (t[i].bias_arr && h->w_on))
             return prepare_weights(h);
     return TEMPEST_OK;
+}
+
+// Whether a launch table may hold Node2Vec walks (a per-walk bias array, or
+// that scalar bias).
+static bool table_may_n2v(const ReqDesc *t, int n)
+{
+    for (int i = 0; i < n; i++)
+        if (t[i].bias_arr || t[i].bias == TEMPEST_BIAS_NODE2VEC) return true;
+    return false;
 }
 
 // Requests with no walks are dropped from a launch table (offsets stay
@@ -263,7 +272,7 @@ int launch_wave(tempest_server *s, tempest_server::Wave &wv, int &rc)
     ReqDesc *dtab = wv.table.as<ReqDesc>();
     WalkCounters *cnt = reinterpret_cast<WalkCounters *>(wv.table.as<char>() + sizeof(ReqDesc) * (size_t)wv.cap);
     cudaMemcpyAsync(dtab, wv.stage, sizeof(ReqDesc) * (size_t)(n > 0 ? n : 1), cudaMemcpyHostToDevice, wv.st);
-    rc = walks_multi_launch(s->h, dir, dtab, n, total, cnt, wv.st);
+    rc = walks_multi_launch(s->h, dir, dtab, n, total, cnt, wv.st, true, table_may_n2v(wv.stage, n));
     cudaEventRecord(wv.ev, wv.st);
     const double t = now_s();
     for (uint64_t id : ids) {
@@ -321,7 +330,8 @@ int tempest_walks_batch(tempest_t *h, const tempest_walk_request *reqs, int n_re
         if ((rc = prepare_for(h, d, tab[d].data(), n[d]))) return rc;
         // the second launch adds to the first one's counters
         rc = walks_multi_launch(h, d, reinterpret_cast<ReqDesc *>(stage + (d ? tb0 : 0)), n[d], total[d],
-                                h->wcnt.as<WalkCounters>(), h->stream, launches == 0);
+                                h->wcnt.as<WalkCounters>(), h->stream, launches == 0,
+                                table_may_n2v(tab[d].data(), n[d]));
         if (rc) return rc;
         launches++;
     }

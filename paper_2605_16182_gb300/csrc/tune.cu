@@ -145,7 +145,7 @@ int tempest_autotune(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, i
                      int32_t flags, tempest_tune_report *out)
 {
     if (!h) return TEMPEST_EINVAL;
-    if (bias < 0 || bias > 3) return fail(h, TEMPEST_EINVAL, "tempest_autotune: unknown bias %d", bias);
+    if (bias < 0 || bias > 4) return fail(h, TEMPEST_EINVAL, "tempest_autotune: unknown bias %d", bias);
     return autotune_impl(h, n_walks, max_len, nullptr, bias, nullptr, start_policy, seed, flags, out);
 }
 

@@ -8,6 +8,37 @@
 
 namespace tw {
 
+// Slot of the Temporal Node2Vec pair table (csrc/pairs.cu): key = from << 32
+// | to (undirected graphs: the smaller id first), cnt = live edges with that
+// key; PAIR_EMPTY marks an unused slot.
+struct alignas(16) PairSlot {
+    unsigned long long key;
+    int cnt;
+    int pad;
+};
+constexpr unsigned long long PAIR_EMPTY = ~0ull;
+
+__host__ __device__ __forceinline__ unsigned long long pair_key(int32_t a, int32_t b, int directed)
+{
+    if (!directed && b < a) {
+        const int32_t x = a;
+        a = b;
+        b = x;
+    }
+    return (unsigned long long)(uint32_t)a << 32 | (uint32_t)b;
+}
+
+// Stafford's 64-bit finaliser ("Mix13"), the slot a key's probe starts at.
+__host__ __device__ __forceinline__ uint64_t pair_hash(uint64_t k)
+{
+    k ^= k >> 30;
+    k *= 0xbf58476d1ce4e5b9ull;
+    k ^= k >> 27;
+    k *= 0x94d049bb133111ebull;
+    k ^= k >> 31;
+    return k;
+}
+
 struct WalkView {
     // edge store, (ts, arrival) order: the live edges are [0, m) from these
     // pointers
@@ -43,6 +74,11 @@ struct WalkView {
     // its stored destination to its stored source
     int back, back_swap;
     ExpRate rate_hop, rate_start;
+    // Temporal Node2Vec: live-pair table (null when not kept: q == 1) and the
+    // factors 1/p, 1/q and beta_max = max(1/p, 1, 1/q)
+    const PairSlot *pt;
+    uint64_t pt_mask;
+    double n2v_inv_p, n2v_inv_q, n2v_bmax;
 };
 
 // Store range [a, b) of timestamp group g (g < G).
@@ -195,10 +231,10 @@ __device__ __forceinline__ void walk_params(const WalkOut &O, int64_t w, int32_t
 {
     L = O.len_arr ? O.len_arr[w] : O.max_len;
     bias = O.bias_arr ? (int)O.bias_arr[w] : O.bias;
-    if (L < 2 || L > O.cap || bias < 0 || bias > 3) {
+    if (L < 2 || L > O.cap || bias < 0 || bias > 4) {
         atomicOr(&O.cnt->status, 1ull);
         L = L < 2 ? 2 : (L > O.cap ? O.cap : L);
-        bias = (bias < 0 || bias > 3) ? BIAS_UNIFORM : bias;
+        bias = (bias < 0 || bias > 4) ? BIAS_UNIFORM : bias;
     }
 }
 
@@ -207,7 +243,11 @@ __device__ __forceinline__ void walk_params(const WalkOut &O, int64_t w, int32_t
 // bias arrays before the weights were enabled) reports EINVAL and walks as
 // the index-based exponential.
 constexpr int BIAS_EXP_WEIGHT = 3;
-__device__ __forceinline__ int start_bias(int bias) { return bias == BIAS_EXP_WEIGHT ? BIAS_EXP : bias; }
+constexpr int BIAS_NODE2VEC = 4;
+constexpr uint32_t N2V_MAX_TRIALS = 4096;
+// The index sampler behind a bias: the weight-based and Node2Vec biases start
+// (and Node2Vec proposes) like the index-based exponential.
+__device__ __forceinline__ int start_bias(int bias) { return bias >= BIAS_EXP_WEIGHT ? BIAS_EXP : bias; }
 
 __device__ __forceinline__ int hop_bias(const WalkView &V, int bias, WalkCounters *cnt)
 {
@@ -316,6 +356,85 @@ __device__ __forceinline__ Entry draw_entry_back(const WalkView &V, const WalkOu
     return V.ent[idx];
 }
 
+// Temporal Node2Vec factor beta(u, w) of candidate w from a node whose
+// predecessor on the walk is u >= 0 (Sec. 2.5): 1/p when w is u, 1 when w is
+// a neighbour of u (a live edge u -> w; w -> u for backward walks, which walk
+// the time-reversed graph; either orientation undirected), 1/q otherwise.
+// `lookups` counts pair-table tests; a missing table (device per-walk biases
+// before tempest_set_node2vec kept one) is flagged and reads as no neighbour.
+__device__ __forceinline__ double n2v_beta(const WalkView &V, WalkCounters *cnt, int32_t u, int32_t w,
+                                           int &lookups)
+{
+    if (w == u) return V.n2v_inv_p;
+    if (V.n2v_inv_q == 1.0) return 1.0;  // neighbour or not, the factor is 1
+    lookups++;
+    if (!V.pt) {
+        atomicOr(&cnt->status, 1ull);
+        return V.n2v_inv_q;
+    }
+    const unsigned long long key = V.back ? pair_key(w, u, V.directed) : pair_key(u, w, V.directed);
+    uint64_t s = pair_hash(key) & V.pt_mask;
+    for (uint64_t i = 0; i <= V.pt_mask; i++, s = (s + 1) & V.pt_mask) {
+        const PairSlot e = V.pt[s];
+        if (e.key == key) return e.cnt > 0 ? 1.0 : V.n2v_inv_q;
+        if (e.key == PAIR_EMPTY) break;
+    }
+    return V.n2v_inv_q;
+}
+
+// Whether proposal k of a Node2Vec hop with factor beta is accepted: always
+// when beta is beta_max, else when u * beta_max < beta for the uniform u of
+// Philox word 1 = 2^31 + k (the comparison is exact in double, as in the
+// oracle).
+__device__ __forceinline__ bool n2v_accept(const WalkView &V, uint64_t seed, uint64_t w, uint32_t hop, uint32_t k,
+                                           double beta)
+{
+    if (beta >= V.n2v_bmax) return true;
+    const Rand4 a = walk_rand2(seed, w, hop, 0x80000000u | k);
+    return (double)u53_bits(a.r0, a.r1) * 0x1.0p-53 * V.n2v_bmax < beta;
+}
+
+// Proposal k of a Node2Vec hop over the candidate groups (forward [c, g1),
+// backward [g0, c) mirrored): the exponential sampler's group, then an edge
+// uniformly inside it, from Philox word 1 = k.
+__device__ __forceinline__ Entry n2v_propose(const WalkView &V, uint64_t seed, uint64_t w, uint32_t hop, uint32_t k,
+                                             int32_t g0, int32_t c, int32_t g1)
+{
+    const Rand4 r = walk_rand2(seed, w, hop, k);
+    const uint64_t h1 = u53_bits(r.r0, r.r1), h2 = u53_bits(r.r2, r.r3);
+    const int32_t lo = V.back ? g0 : c, hi = V.back ? c : g1;
+    const int32_t j = (int32_t)sampler_index_k(h1, (int64_t)(hi - lo), BIAS_EXP, V.rate_hop);
+    const int32_t gg = V.back ? hi - 1 - j : lo + j;
+    const int32_t e0 = __ldg(V.ngo + gg), e1 = __ldg(V.ngo + gg + 1);
+    const int64_t q = uniform_index_k(h2, (int64_t)(e1 - e0));
+    return V.ent[V.back ? (int64_t)e1 - 1 - q : (int64_t)e0 + q];
+}
+
+// One Node2Vec hop by rejection (Sec. 2.5); u < 0 (a PER_NODE start, no
+// predecessor) takes the first proposal.  False when N2V_MAX_TRIALS
+// proposals were all rejected (the walk ends).  bytes adds the sector model
+// of the extra reads: 12 + 16 per proposal after the first, 32 per lookup.
+__device__ __forceinline__ bool draw_n2v(const WalkView &V, const WalkOut &O, int64_t w, uint32_t hop, int32_t g0,
+                                         int32_t c, int32_t g1, int32_t u, Entry &out, unsigned long long &bytes)
+{
+    for (uint32_t k = 0; k < N2V_MAX_TRIALS; k++) {
+        const Entry e = n2v_propose(V, O.seed, (uint64_t)w, hop, k, g0, c, g1);
+        if (k > 0) bytes += 12 + 16;
+        if (u < 0) {
+            out = e;
+            return true;
+        }
+        int lk = 0;
+        const double beta = n2v_beta(V, O.cnt, u, e.other, lk);
+        bytes += 32ull * (unsigned)lk;
+        if (n2v_accept(V, O.seed, (uint64_t)w, hop, k, beta)) {
+            out = e;
+            return true;
+        }
+    }
+    return false;
+}
+
 // The time a walk searches at after reaching a node at time t (forward: t;
 // backward: t - 1), and before its first hop under PER_NODE.
 __device__ __forceinline__ int64_t search_time(const WalkView &V, int64_t t) { return V.back ? t - 1 : t; }
@@ -340,11 +459,15 @@ struct ReqDesc {
 };
 
 WalkView make_view(tempest_t *h, int back = 0);
+// Node2Vec fields of a view from the handle that keeps the pair table
+void view_n2v(WalkView &V, const tempest_t *h);
 // One persistent streaming launch over n_req requests of one direction whose
 // descriptors are in device memory; counters in cnt (zeroed here unless
 // clear is false, when the launch adds to them).
+// may_n2v: a request may take the Node2Vec bias (a per-walk bias array, or
+// that scalar bias).
 int walks_multi_launch(tempest_t *h, int direction, const ReqDesc *dev_reqs, int n_req, int64_t total,
-                       WalkCounters *cnt, cudaStream_t st, bool clear = true);
+                       WalkCounters *cnt, cudaStream_t st, bool clear = true, bool may_n2v = true);
 int coop_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches);
 int graph_run(tempest_t *h, const WalkView &V, const WalkOut &O, int64_t &launches);
 

@@ -22,18 +22,19 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
          w += (int64_t)gridDim.x * blockDim.x) {
         int32_t L = O.len_arr ? O.len_arr[w] : O.max_len;
         int bias = O.bias_arr ? (int)O.bias_arr[w] : O.bias;
-        if (L < 2 || L > O.cap || bias < 0 || bias > 3) {
+        if (L < 2 || L > O.cap || bias < 0 || bias > 4) {
             // per-walk arrays that live on the device are checked here: the
             // walk is clamped into its row and the call reports EINVAL
             atomicOr(&O.cnt->status, 1ull);
             L = L < 2 ? 2 : (L > O.cap ? O.cap : L);
-            bias = (bias < 0 || bias > 3) ? BIAS_UNIFORM : bias;
+            bias = (bias < 0 || bias > 4) ? BIAS_UNIFORM : bias;
         }
         int32_t *nrow = O.node + w * (int64_t)O.cap;
         int64_t *trow = O.ts + w * (int64_t)O.cap;
         int32_t len = 0;
         if (V.m > 0) {
             int32_t v;
+            int32_t u = -1;  // the node before v (Node2Vec); none at a PER_NODE start
             int64_t t;
             Rand4 r;
             if (O.start_policy == TEMPEST_START_PER_NODE) {
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 len = 2;
                 hops++;
                 bytes += START_MODEL_BYTES;
+                u = s;
                 v = d;
                 t = search_time(V, t0);
             }
@@ -87,14 +89,20 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 node_groups(V, v, g0, g1);
                 const int32_t c = first_later(V, v, g0, g1, t);
                 if (V.back ? c == g0 : c == g1) break;  // Gamma_t(v) is empty
-                if (V.back) {
-                    const Entry e = draw_entry_back(V, O, w, h, bias, g0, c);
+                if (V.back || bias == BIAS_NODE2VEC) {
+                    Entry e;
+                    if (bias == BIAS_NODE2VEC) {
+                        if (!draw_n2v(V, O, w, h, g0, c, g1, u, e, bytes)) break;  // all proposals rejected
+                    } else {
+                        e = draw_entry_back(V, O, w, h, bias, g0, c);
+                    }
                     nrow[len] = e.other;
                     trow[len] = e.ts;
                     hops++;
                     bytes += hop_model_bytes((int64_t)(g1 - g0));
+                    u = v;
                     v = e.other;
-                    t = e.ts - 1;
+                    t = search_time(V, e.ts);
                     len++;
                     continue;
                 }
@@ -112,7 +120,7 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                     idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
                 } else {
                     const uint64_t h2 = u53_bits(r.r2, r.r3);
-                    const int64_t j = sampler_index_k(h1, (int64_t)(g1 - c), bias, V.rate_hop);
+                    const int64_t j = sampler_index_k(h1, (int64_t)(g1 - c), start_bias(hb), V.rate_hop);
                     const int32_t e0 = __ldg(V.ngo + c + j), e1 = __ldg(V.ngo + c + j + 1);
                     idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
                 }
@@ -121,6 +129,7 @@ __global__ void __launch_bounds__(256) k_walks_full(const WalkView V, const Walk
                 trow[len] = e.ts;
                 hops++;
                 bytes += hop_model_bytes((int64_t)(g1 - g0));
+                u = v;
                 v = e.other;
                 t = e.ts;
                 len++;
@@ -169,6 +178,7 @@ enum : int {
     S_WSEARCH,     // one suffix sum loaded (weight-based bias)
     S_PICK2,       // chosen group's entry range loaded
     S_HOP,         // chosen entry loaded
+    S_N2V,         // Node2Vec: one pair-table slot loaded
     S_EXIT
 };
 
@@ -183,9 +193,10 @@ struct SmLane {
     int32_t len, cap_len;
     int32_t state;
     int32_t bias;
-    int32_t prev_w;  // bracket width before the last probe
+    int32_t prev_w;  // bracket width before the last probe (Node2Vec: probes of the pair table)
     uint32_t hop;
-    uint32_t orient;
+    uint32_t orient;  // start: orientation bit; Node2Vec: proposal number of the hop
+    int32_t u;        // the node before v (Node2Vec); -1 at a PER_NODE start
 };
 
 __device__ __forceinline__ int32_t interp_probe(int32_t L, int32_t R, int64_t vL, int64_t vR, int64_t t,
@@ -258,10 +269,10 @@ struct ManyReq {
         }
         L = q.len_arr ? q.len_arr[c.w] : q.max_len;
         bias = q.bias_arr ? (int)q.bias_arr[c.w] : q.bias;
-        if (L < 2 || L > q.cap || bias < 0 || bias > 3) {
+        if (L < 2 || L > q.cap || bias < 0 || bias > 4) {
             atomicOr(&counters->status, 1ull);
             L = L < 2 ? 2 : (L > q.cap ? q.cap : L);
-            bias = (bias < 0 || bias > 3) ? BIAS_UNIFORM : bias;
+            bias = (bias < 0 || bias > 4) ? BIAS_UNIFORM : bias;
         }
     }
     __device__ __forceinline__ uint64_t seed(const Ctx &c) const { return reqs[c.r].seed; }
@@ -283,7 +294,11 @@ struct ManyReq {
 
 // MINB: resident CTAs per SM the register budget is cut for (4: 64
 // registers; 5: 48 registers with a few spills, for more warps in flight).
-template <class P, int MINB>
+// N2V: whether the Temporal Node2Vec rejection states are compiled in (they
+// cost registers); without them a Node2Vec walk takes its first proposal,
+// which is exactly the walk when p = q = 1 (every beta is beta_max) and is
+// flagged otherwise.
+template <class P, int MINB, bool N2V>
 __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, const P Pv,
                                                              unsigned long long *next_walk)
 {
@@ -334,11 +349,64 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
         bool pick = false;   // the bracket closed this iteration: draw now
         bool finish = false; // the walk ended this iteration
 
+        // the chosen entry (z0 other, y0 ts) becomes position len
+        auto commit_hop = [&]() {
+            Pv.nrow(cx)[s.len] = z0;
+            Pv.trow(cx)[s.len] = y0;
+            hops++;
+            bytes += hop_model_bytes((int64_t)(s.g1 - s.g0));
+            s.len++;
+            s.hop++;
+            if (N2V) s.u = s.v;
+            s.v = z0;
+            s.t = search_time(V, y0);
+            if (s.len >= s.cap_len) {
+                finish = true;
+            } else {
+                load_range(V.ngr + z0, z0, z1, z2, y0, y1);
+                s.state = S_RANGE;
+            }
+        };
+        // Node2Vec proposal s.orient of this hop (candidate groups from c =
+        // s.R): loads the chosen group's entry range
+        auto n2v_issue = [&]() {
+            const Rand4 r = walk_rand2(Pv.seed(cx), Pv.wid(cx), s.hop, s.orient);
+            s.ud = u53_bits(r.r2, r.r3);
+            const int32_t lo = V.back ? s.g0 : s.R, hi = V.back ? s.R : s.g1;
+            const int32_t j = (int32_t)sampler_index_k(u53_bits(r.r0, r.r1), (int64_t)(hi - lo), BIAS_EXP, V.rate_hop);
+            const int32_t gg = V.back ? hi - 1 - j : lo + j;
+            z0 = __ldg(V.ngo + gg);
+            z1 = __ldg(V.ngo + gg + 1);
+            s.state = S_PICK2;
+        };
+        // accept the loaded proposal with factor beta, or draw the next one
+        auto n2v_decide = [&](double beta) {
+            if (n2v_accept(V, Pv.seed(cx), Pv.wid(cx), s.hop, s.orient, beta)) {
+                commit_hop();
+            } else if (++s.orient >= N2V_MAX_TRIALS) {
+                finish = true;  // every proposal rejected
+            } else {
+                bytes += 12 + 16;
+                n2v_issue();
+            }
+        };
+        // the pair-table slot of probe s.prev_w for (u, candidate z0)
+        auto n2v_probe = [&]() {
+            const unsigned long long key = V.back ? pair_key(z0, s.u, V.directed) : pair_key(s.u, z0, V.directed);
+            const PairSlot *e = V.pt + ((pair_hash(key) + (uint64_t)(uint32_t)s.prev_w) & V.pt_mask);
+            y1 = (int64_t)__ldg(&e->key);
+            z2 = __ldg(&e->cnt);
+            s.state = S_N2V;
+        };
+
         switch (s.state) {
             case S_NEW: {
                 int32_t L;
                 int bias;
                 Pv.open(s.w, cx, L, bias);
+                // without the rejection states a Node2Vec walk is the
+                // exponential walk (the host picks this form only then)
+                if (!N2V && bias == BIAS_NODE2VEC) bias = BIAS_EXP;
                 s.cap_len = L;
                 s.bias = bias;
                 s.len = 0;
@@ -378,6 +446,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 Pv.trow(cx)[0] = INT64_MIN;
                 s.len = 1;
                 s.hop = 0;
+                if (N2V) s.u = -1;
                 s.v = z0;
                 s.t = pernode_time(V);
                 load_range(V.ngr + z0, z0, z1, z2, y0, y1);
@@ -410,6 +479,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 trow[1] = y0;
                 s.len = 2;
                 s.hop = 1;
+                if (N2V) s.u = a;
                 s.v = b;
                 s.t = search_time(V, y0);
                 hops++;
@@ -533,19 +603,35 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 break;
             }
             case S_HOP: {
-                Pv.nrow(cx)[s.len] = z0;
-                Pv.trow(cx)[s.len] = y0;
-                hops++;
-                bytes += hop_model_bytes((int64_t)(s.g1 - s.g0));
-                s.len++;
-                s.hop++;
-                s.v = z0;
-                s.t = search_time(V, y0);
-                if (s.len >= s.cap_len) {
-                    finish = true;
+                if (!N2V) {
+                    commit_hop();  // the host runs this form only where Node2Vec takes its first proposal
+                } else if (s.bias != BIAS_NODE2VEC || s.u < 0) {
+                    commit_hop();
+                } else if (z0 == s.u) {
+                    n2v_decide(V.n2v_inv_p);
+                } else if (V.n2v_inv_q == 1.0) {
+                    n2v_decide(1.0);  // neighbour or not, the factor is 1
+                } else if (!V.pt) {
+                    atomicOr(&Pv.cnt()->status, 1ull);
+                    n2v_decide(V.n2v_inv_q);
                 } else {
-                    load_range(V.ngr + z0, z0, z1, z2, y0, y1);
-                    s.state = S_RANGE;
+                    bytes += 32;
+                    s.prev_w = 0;
+                    n2v_probe();
+                }
+                break;
+            }
+            case S_N2V: {
+                if (!N2V) break;  // not reached without the rejection states
+                // y1: slot key, z2: its live count
+                const unsigned long long key = V.back ? pair_key(z0, s.u, V.directed) : pair_key(s.u, z0, V.directed);
+                if ((unsigned long long)y1 == key) {
+                    n2v_decide(z2 > 0 ? 1.0 : V.n2v_inv_q);
+                } else if ((unsigned long long)y1 == PAIR_EMPTY || (uint64_t)(uint32_t)s.prev_w >= V.pt_mask) {
+                    n2v_decide(V.n2v_inv_q);
+                } else {
+                    s.prev_w++;
+                    n2v_probe();
                 }
                 break;
             }
@@ -560,7 +646,10 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             const uint64_t u1 = u53_bits(r.r0, r.r1);
             const int hb = hop_bias(V, s.bias, Pv.cnt());
             s.state = S_PICK2;
-            if (V.back) {
+            if (N2V && hb == BIAS_NODE2VEC) {
+                s.orient = 0;  // proposal 0 is the exponential draw of this hop's block
+                n2v_issue();
+            } else if (V.back) {
                 // groups [g0, c) in the mirrored order (latest first)
                 if (hb == BIAS_UNIFORM) {
                     s.ud = u1;
@@ -587,7 +676,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 s.state = S_WTOT;
             } else {
                 s.ud = u53_bits(r.r2, r.r3);
-                const int64_t j = sampler_index_k(u1, (int64_t)(s.g1 - c), s.bias, V.rate_hop);
+                const int64_t j = sampler_index_k(u1, (int64_t)(s.g1 - c), hb, V.rate_hop);
                 z0 = __ldg(V.ngo + c + j);
                 z1 = __ldg(V.ngo + c + j + 1);
             }
@@ -674,25 +763,29 @@ __global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, 
 
 // Launches the streaming walker with the register budget the CTAs-per-SM
 // knob asks for (0: the 64-register build at its occupancy limit).
+// n2v: a walk of the launch may take Node2Vec hops with p, q not both 1
 template <class P>
 static void launch_stream(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
-                          cudaStream_t st)
+                          cudaStream_t st, bool n2v)
 {
-    static int occ4 = 0, occ5 = 0;
+    static int occ4 = 0, occ5 = 0, occn = 0;
     if (occ4 == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ4, k_walks_stream<P, 4>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_stream<P, 5>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ4, k_walks_stream<P, 4, false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_stream<P, 5, false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_stream<P, 3, true>, 256, 0);
         if (occ4 < 1) occ4 = 1;
         if (occ5 < 1) occ5 = 1;
+        if (occn < 1) occn = 1;
     }
-    const bool wide = h->stream_ctas > 4;
-    const int occ = wide ? occ5 : occ4;
+    const bool wide = h->stream_ctas > 4 && !n2v;
+    const int occ = n2v ? occn : (wide ? occ5 : occ4);
     const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, occ) : occ;
     int64_t grid = (int64_t)h->num_sms * bps;
     const int64_t need = (total + 255) / 256;
     if (grid > need) grid = need;
-    if (wide) k_walks_stream<P, 5><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
-    else k_walks_stream<P, 4><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    if (n2v) k_walks_stream<P, 3, true><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else if (wide) k_walks_stream<P, 5, false><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else k_walks_stream<P, 4, false><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
 }
 
 // Events bracketing the walk kernels of a call (created on first use).
@@ -704,7 +797,7 @@ static void kernel_mark(tempest_t *h, int which)
 }
 
 int walks_multi_launch(tempest_t *h, int direction, const ReqDesc *dev_reqs, int n_req, int64_t total,
-                       WalkCounters *cnt, cudaStream_t st, bool clear)
+                       WalkCounters *cnt, cudaStream_t st, bool clear, bool may_n2v)
 {
     // the walk-id counter always restarts; the statistics only when asked
     if (clear) cudaMemsetAsync(cnt, 0, sizeof(WalkCounters), st);
@@ -712,10 +805,12 @@ int walks_multi_launch(tempest_t *h, int direction, const ReqDesc *dev_reqs, int
     if (total <= 0 || n_req <= 0) return cuda_check(h, cudaGetLastError(), "walks multi");
     tempest_t *vh = view_handle(h, direction);
     if (!vh) return fail(h, TEMPEST_EINVAL, "backward walks of a directed graph need tempest_enable_backward");
-    const WalkView V = make_view(vh, direction);
+    WalkView V = make_view(vh, direction);
+    view_n2v(V, h);  // the pair table and parameters live on the main handle
     const bool mark = st == h->stream;
     if (mark) kernel_mark(h, 0);
-    launch_stream(h, V, ManyReq{dev_reqs, n_req, total, cnt}, &cnt->pad, total, st);
+    const bool n2v = may_n2v && (V.n2v_inv_p != 1.0 || V.n2v_inv_q != 1.0);
+    launch_stream(h, V, ManyReq{dev_reqs, n_req, total, cnt}, &cnt->pad, total, st, n2v);
     if (mark) kernel_mark(h, 1);
     return cuda_check(h, cudaGetLastError(), "walks multi");
 }
@@ -784,7 +879,17 @@ WalkView make_view(tempest_t *h, int back)
     const double ls = h->lam_start > 0.0 ? h->lam_start : (h->G > 0 ? 1.0 / (double)h->G : 1.0);
     V.rate_hop = ExpRate{h->lam_hop, (float)h->lam_hop, (float)(1.0 / h->lam_hop)};
     V.rate_start = ExpRate{ls, (float)ls, (float)(1.0 / ls)};
+    view_n2v(V, h);
     return V;
+}
+
+void view_n2v(WalkView &V, const tempest_t *h)
+{
+    V.pt = h->pt_on ? h->pt.as<PairSlot>() : nullptr;
+    V.pt_mask = h->pt_on ? (uint64_t)h->pt_cap - 1 : 0;
+    V.n2v_inv_p = 1.0 / h->n2v_p;
+    V.n2v_inv_q = 1.0 / h->n2v_q;
+    V.n2v_bmax = std::max(std::max(V.n2v_inv_p, 1.0), V.n2v_inv_q);
 }
 
 int walks_run(tempest_t *h, const WalkRequest &rq)
@@ -801,6 +906,7 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     cudaStream_t st = h->stream;
     cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);
     WalkView V = make_view(vh, rq.direction);
+    view_n2v(V, h);  // the pair table and parameters live on the main handle
     WalkOut O;
     O.n_walks = rq.n_walks;
     O.cap = rq.cap;
@@ -838,7 +944,9 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
             launches++;
         } else {
             kernel_mark(h, 0);
-            launch_stream(h, V, OneReq{O}, &O.cnt->pad, rq.n_walks, st);
+            const bool n2v = (rq.bias_arr ? rq.may_n2v != 0 : rq.bias == TEMPEST_BIAS_NODE2VEC) &&
+                             (V.n2v_inv_p != 1.0 || V.n2v_inv_q != 1.0);
+            launch_stream(h, V, OneReq{O}, &O.cnt->pad, rq.n_walks, st, n2v);
             kernel_mark(h, 1);
             launches += 1;  // the walker pads its rows itself
         }
