@@ -52,8 +52,13 @@ def parse():
     p.add_argument("--walks", type=int, default=10_000_000)
     p.add_argument("--max-len", type=int, default=80)
     p.add_argument("--sched", default="stream", choices=["stream", "full", "coop", "graph"])
-    p.add_argument("--bias", default="exp", choices=["uniform", "linear", "exp", "weight"],
-                   help="hop bias of the stream workload (weight: the weight-based sampler, rate 1/window span)")
+    p.add_argument("--bias", default="exp", choices=["uniform", "linear", "exp", "weight", "node2vec"],
+                   help="hop bias of the stream workload (weight: the weight-based sampler, rate 1/window span; "
+                        "node2vec: Temporal Node2Vec with --n2v-p / --n2v-q)")
+    p.add_argument("--n2v-p", type=float, default=0.5, help="Node2Vec return parameter p")
+    p.add_argument("--n2v-q", type=float, default=2.0, help="Node2Vec in-out parameter q")
+    p.add_argument("--direction", default="forward", choices=["forward", "backward"],
+                   help="walk direction of the stream workload (backward: in-edges earlier than t)")
     p.add_argument("--workload", default="stream", choices=["stream", "batched", "serve"])
     p.add_argument("--requests", type=int, default=2000)
     p.add_argument("--no-e2e", action="store_true")
@@ -171,7 +176,12 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     eng = _lib.Engine(window=spec.window, directed=True, device=str(dev), stream=stream)
     bias_id = {"uniform": _lib.BIAS_UNIFORM, "linear": _lib.BIAS_LINEAR, "exp": _lib.BIAS_EXP,
-               "weight": _lib.BIAS_EXP_WEIGHT}[args.bias]
+               "weight": _lib.BIAS_EXP_WEIGHT, "node2vec": _lib.BIAS_NODE2VEC}[args.bias]
+    direction = 1 if args.direction == "backward" else 0
+    if direction:
+        eng.enable_backward()  # before the stream: every batch feeds the in-edge index
+    if bias_id == _lib.BIAS_NODE2VEC:
+        eng.set_node2vec(args.n2v_p, args.n2v_q)
     if bias_id == _lib.BIAS_EXP_WEIGHT:
         # one e-fold per window span: the window holds -window edges at the
         # stream's mean gap of 550 ns
@@ -204,7 +214,7 @@ def run_ours(args, rank, world):
         e0, e1 = ev(), ev()
         e0.record(stream)
         eng.walks(n_walks, L, bias=bias_id, start_policy=_lib.START_UNIFORM_EDGE,
-                  seed=seed_base + step, out=(node, tso, ln))
+                  seed=seed_base + step, out=(node, tso, ln), direction=direction)
         e1.record(stream)
         e1.synchronize()
         ws = eng.last_walk_stats()
@@ -247,13 +257,14 @@ def run_ours(args, rank, world):
 
     # end to end through the C ABI with host buffers (one step, after the timed ones)
     if not args.no_e2e:
-        res["e2e"] = run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id)
+        res["e2e"] = run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id,
+                             direction)
     eng.close()
     del batches
     return res
 
 
-def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id):
+def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id, direction=0):
     """Continue the stream with host-resident batches: every step copies its
     batches from pinned host memory and its walks back to pinned host memory
     inside the timed region."""
@@ -282,8 +293,9 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
             h2d += s.numel() * 4 + d.numel() * 4 + t.numel() * 8
             edges += int(s.shape[0])
         t0 = time.perf_counter()
-        _lib.tempest_walks(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7777 + step,
-                           hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
+        walk_fn = _lib.tempest_walks_backward if direction else _lib.tempest_walks
+        walk_fn(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7777 + step,
+                hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
         walk_s += time.perf_counter() - t0
         hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
         d2h += hnode.numel() * 4 + hts.numel() * 8 + hln.numel() * 4
@@ -679,7 +691,10 @@ def main():
                    "nodes": int(100_000_000 * args.scale) if args.scale != 1.0 else 100_000_000,
                    "batch_edges": int(10_000_000 * args.scale), "window_edges": int(200_000_000 * args.scale),
                    "walks_per_call": res["n_walks"], "max_len": args.max_len,
-                   "bias": {"exp": "exponential", "weight": "weight-based exponential"}.get(args.bias, args.bias),
+                   "bias": {"exp": "exponential", "weight": "weight-based exponential",
+                            "node2vec": "Temporal Node2Vec (p %g, q %g)" % (args.n2v_p, args.n2v_q)}.get(
+                                args.bias, args.bias),
+                   "direction": args.direction,
                    "start": "uniform edge", "batches_per_step": BATCHES_PER_STEP,
                    "scheduler": sched, "l2": "inputs larger than L2 (160 MB batches, GB-sized state)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -75,56 +75,59 @@ struct RunOp {
 __global__ void __launch_bounds__(256) k_coop_start(const WalkView V, const WalkOut O, CoopState S)
 {
     unsigned long long hops = 0, bytes = 0;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < O.n_walks;
-         w += (int64_t)gridDim.x * blockDim.x) {
-        int32_t L;
-        int bias;
-        walk_params(O, w, L, bias);
-        int32_t *nrow = O.node + w * (int64_t)O.cap;
-        int64_t *trow = O.ts + w * (int64_t)O.cap;
-        if (V.m == 0) {
-            O.len[w] = 0;
-            continue;
-        }
-        int32_t s = -1, d, len0;
-        int64_t t0;
-        if (O.start_policy == TEMPEST_START_PER_NODE) {
-            // the walk starts at an active node before every live edge
-            d = __ldg(V.pn_nodes + w / O.pn_k);
-            t0 = pernode_time(V);
-            nrow[0] = d;
-            trow[0] = INT64_MIN;
-            len0 = 1;
-        } else {
-            start_edge(V, O, w, bias, s, d, t0);
-            nrow[0] = s;
-            nrow[1] = d;
-            trow[0] = INT64_MIN;
-            trow[1] = t0;
-            t0 = search_time(V, t0);
-            hops++;
-            bytes += START_MODEL_BYTES;
-            len0 = 2;
-        }
-        if (L <= len0) {
-            O.len[w] = len0;
-        } else {
-            S.ws_node[w] = d;
-            S.ws_t[w] = t0;
-            S.ws_len[w] = len0;
-            S.ws_prev[w] = len0 == 2 ? s : -1;
-            const unsigned am = __activemask();
-            const int lane = threadIdx.x & 31;
-            const int leader = __ffs(am) - 1;
-            unsigned base = 0;
-            if (lane == leader) base = atomicAdd(S.n_next, (unsigned)__popc(am));
-            base = __shfl_sync(am, base, leader);
-            S.next_active[base + __popc(am & ((1u << lane) - 1u))] = (int32_t)w;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < O.n_walks; base += stride) {
+        const int64_t w = base + lane;
+        if (w < O.n_walks) {
+            int32_t L;
+            int bias;
+            walk_params(O, w, L, bias);
+            int32_t *nrow = O.node + w * (int64_t)O.cap;
+            int64_t *trow = O.ts + w * (int64_t)O.cap;
+            if (V.m == 0) {
+                O.len[w] = 0;
+            } else {
+                int32_t s = -1, d, len0;
+                int64_t t0;
+                if (O.start_policy == TEMPEST_START_PER_NODE) {
+                    // the walk starts at an active node before every live edge
+                    d = __ldg(V.pn_nodes + w / O.pn_k);
+                    t0 = pernode_time(V);
+                    nrow[0] = d;
+                    trow[0] = INT64_MIN;
+                    len0 = 1;
+                } else {
+                    start_edge(V, O, w, bias, s, d, t0);
+                    nrow[0] = s;
+                    nrow[1] = d;
+                    trow[0] = INT64_MIN;
+                    trow[1] = t0;
+                    t0 = search_time(V, t0);
+                    hops++;
+                    bytes += START_MODEL_BYTES;
+                    len0 = 2;
+                }
+                if (L <= len0) {
+                    O.len[w] = len0;
+                } else {
+                    S.ws_node[w] = d;
+                    S.ws_t[w] = t0;
+                    S.ws_len[w] = len0;
+                    S.ws_prev[w] = len0 == 2 ? s : -1;
+                    const unsigned am = __activemask();
+                    const int leader = __ffs(am) - 1;
+                    unsigned slot = 0;
+                    if (lane == leader) slot = atomicAdd(S.n_next, (unsigned)__popc(am));
+                    slot = __shfl_sync(am, slot, leader);
+                    S.next_active[slot + __popc(am & ((1u << lane) - 1u))] = (int32_t)w;
+                }
+            }
         }
     }
     hops = warp_sum(hops);
     bytes = warp_sum(bytes);
-    if ((threadIdx.x & 31) == 0 && hops) {
+    if (lane == 0 && hops) {
         atomicAdd(&O.cnt->hops, hops);
         atomicAdd(&O.cnt->model_bytes, bytes);
     }

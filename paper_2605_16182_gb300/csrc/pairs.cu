@@ -32,12 +32,21 @@ __global__ void k_pt_clear(PairSlot *t, int64_t cap)
 }
 
 // delta = +1: insert (or count) every pair; -1: uncount every pair (each must
-// be present).  A probe sequence longer than the table sets a status bit.
+// be present).  Lanes of a warp holding the same key combine first (a Zipf
+// stream repeats its hub pairs in every warp), so a key takes one atomic per
+// warp.  A probe sequence longer than the table sets a status bit.
 __global__ void k_pt_apply(PairSlot *t, uint64_t mask, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
                            int64_t n, int directed, int delta, unsigned long long *status)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long key = pair_key(a[i], b[i], directed);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+        const unsigned long long key = valid ? pair_key(a[i], b[i], directed) : PAIR_EMPTY;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (!valid || lane != __ffs(peers) - 1) continue;
+        const int d = delta * __popc(peers);
         uint64_t s = pair_hash(key) & mask;
         bool done = false;
         for (uint64_t probe = 0; probe <= mask && !done; probe++, s = (s + 1) & mask) {
@@ -45,7 +54,7 @@ __global__ void k_pt_apply(PairSlot *t, uint64_t mask, const int32_t *__restrict
             if (k == PAIR_EMPTY && delta > 0) k = atomicCAS(&t[s].key, PAIR_EMPTY, key);
             if (k == PAIR_EMPTY && delta > 0) k = key;  // this thread claimed the slot
             if (k == key) {
-                atomicAdd(&t[s].cnt, delta);
+                atomicAdd(&t[s].cnt, d);
                 done = true;
             } else if (k == PAIR_EMPTY) {
                 break;  // a decrement of an absent key

@@ -435,6 +435,56 @@ __device__ __forceinline__ bool draw_n2v(const WalkView &V, const WalkOut &O, in
     return false;
 }
 
+// Padding of one walk output row (node -1, ts INT64_MIN) from cell l to the
+// row end, by the whole warp on consecutive cells, with 16-byte stores where
+// the row layout allows (vec).
+__device__ __forceinline__ void warp_pad_row(int32_t *nr, int64_t *tr, int32_t l, int32_t cap, int lane, bool vec)
+{
+    l = l < 0 ? 0 : l;
+    if (vec) {
+        const int4 n4 = make_int4(-1, -1, -1, -1);
+        const longlong2 t2 = make_longlong2(INT64_MIN, INT64_MIN);
+        for (int32_t q = (l >> 2) + lane; q < (cap >> 2); q += 32) {
+            if (4 * q >= l) {
+                reinterpret_cast<int4 *>(nr)[q] = n4;
+            } else {
+                for (int32_t i = l; i < 4 * q + 4; i++) nr[i] = -1;
+            }
+        }
+        for (int32_t q = (l >> 1) + lane; q < (cap >> 1); q += 32) {
+            if (2 * q >= l) reinterpret_cast<longlong2 *>(tr)[q] = t2;
+            else tr[l] = INT64_MIN;  // l odd: the second half of the pair
+        }
+    } else {
+        for (int32_t i = l + lane; i < cap; i += 32) {
+            nr[i] = -1;
+            tr[i] = INT64_MIN;
+        }
+    }
+}
+
+__device__ __forceinline__ bool pad_vec_ok(const int32_t *node, const int64_t *ts, int32_t cap)
+{
+    return (cap & 3) == 0 && ((uintptr_t)node & 15) == 0 && ((uintptr_t)ts & 15) == 0;
+}
+
+// Padding of the rows of the warp's lanes: lane i names walk w (< 0: none)
+// and the cell its padding starts at (from >= cap: none); rows are written
+// one at a time by the whole warp.  Every lane of the warp must call it.
+__device__ __forceinline__ void warp_pad_walk_rows(int32_t *node, int64_t *ts, int32_t cap, int64_t w, int32_t from,
+                                                   int lane)
+{
+    const bool vec = pad_vec_ok(node, ts, cap);
+    unsigned todo = __ballot_sync(0xffffffffu, w >= 0 && from < cap);
+    while (todo) {
+        const int r = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t wr = __shfl_sync(0xffffffffu, w, r);
+        const int32_t l = __shfl_sync(0xffffffffu, from, r);
+        warp_pad_row(node + wr * (int64_t)cap, ts + wr * (int64_t)cap, l, cap, lane, vec);
+    }
+}
+
 // The time a walk searches at after reaching a node at time t (forward: t;
 // backward: t - 1), and before its first hop under PER_NODE.
 __device__ __forceinline__ int64_t search_time(const WalkView &V, int64_t t) { return V.back ? t - 1 : t; }

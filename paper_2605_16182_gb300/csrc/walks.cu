@@ -294,11 +294,13 @@ struct ManyReq {
 
 // MINB: resident CTAs per SM the register budget is cut for (4: 64
 // registers; 5: 48 registers with a few spills, for more warps in flight).
+// BACK: backward walks (the view is the in-view; a compile-time copy of
+// V.back, so forward walks carry no direction tests).
 // N2V: whether the Temporal Node2Vec rejection states are compiled in (they
 // cost registers); without them a Node2Vec walk takes its first proposal,
 // which is exactly the walk when p = q = 1 (every beta is beta_max) and is
 // flagged otherwise.
-template <class P, int MINB, bool N2V>
+template <class P, int MINB, bool N2V, bool BACK>
 __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, const P Pv,
                                                              unsigned long long *next_walk)
 {
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             s.hop++;
             if (N2V) s.u = s.v;
             s.v = z0;
-            s.t = search_time(V, y0);
+            s.t = (BACK ? y0 - 1 : y0);
             if (s.len >= s.cap_len) {
                 finish = true;
             } else {
@@ -372,9 +374,9 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
         auto n2v_issue = [&]() {
             const Rand4 r = walk_rand2(Pv.seed(cx), Pv.wid(cx), s.hop, s.orient);
             s.ud = u53_bits(r.r2, r.r3);
-            const int32_t lo = V.back ? s.g0 : s.R, hi = V.back ? s.R : s.g1;
+            const int32_t lo = BACK ? s.g0 : s.R, hi = BACK ? s.R : s.g1;
             const int32_t j = (int32_t)sampler_index_k(u53_bits(r.r0, r.r1), (int64_t)(hi - lo), BIAS_EXP, V.rate_hop);
-            const int32_t gg = V.back ? hi - 1 - j : lo + j;
+            const int32_t gg = BACK ? hi - 1 - j : lo + j;
             z0 = __ldg(V.ngo + gg);
             z1 = __ldg(V.ngo + gg + 1);
             s.state = S_PICK2;
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
         };
         // the pair-table slot of probe s.prev_w for (u, candidate z0)
         auto n2v_probe = [&]() {
-            const unsigned long long key = V.back ? pair_key(z0, s.u, V.directed) : pair_key(s.u, z0, V.directed);
+            const unsigned long long key = BACK ? pair_key(z0, s.u, V.directed) : pair_key(s.u, z0, V.directed);
             const PairSlot *e = V.pt + ((pair_hash(key) + (uint64_t)(uint32_t)s.prev_w) & V.pt_mask);
             y1 = (int64_t)__ldg(&e->key);
             z2 = __ldg(&e->cnt);
@@ -422,17 +424,17 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 const Rand4 r = walk_rand(Pv.seed(cx), Pv.wid(cx), 0u);
                 const uint64_t u1 = u53_bits(r.r0, r.r1);
                 s.ud = u53_bits(r.r2, r.r3);
-                s.orient = ((!V.directed && (r.r3 & 1u)) ? 1u : 0u) ^ (V.back_swap ? 1u : 0u);
+                s.orient = ((!V.directed && (r.r3 & 1u)) ? 1u : 0u) ^ ((BACK && V.back_swap) ? 1u : 0u);
                 if (Pv.policy(cx) == TEMPEST_START_UNIFORM_EDGE) {
                     int64_t k = uniform_index_k(u1, V.m);
-                    if (V.back) k = V.m - 1 - k;
+                    if (BACK) k = V.m - 1 - k;
                     y0 = __ldg(V.st_ts + k);
                     z0 = __ldg(V.st_src + k);
                     z1 = __ldg(V.st_dst + k);
                     s.state = S_EDGE;
                 } else {
                     int64_t g = sampler_index_k(u1, V.G, start_bias(bias), V.rate_start);
-                    if (V.back) g = V.G - 1 - g;
+                    if (BACK) g = V.G - 1 - g;
                     z0 = __ldg(V.tg + g);
                     z1 = __ldg(V.tg + g + 1);
                     s.state = S_SGROUP;
@@ -448,7 +450,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 s.hop = 0;
                 if (N2V) s.u = -1;
                 s.v = z0;
-                s.t = pernode_time(V);
+                s.t = (BACK ? INT64_MAX - 1 : INT64_MIN);
                 load_range(V.ngr + z0, z0, z1, z2, y0, y1);
                 s.state = S_RANGE;
                 break;
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 const int32_t x = (int32_t)((uint32_t)z0 - V.s_lo);
                 const int64_t a = x > 0 ? x : 0;
                 const int64_t b = (int64_t)(int32_t)((uint32_t)z1 - V.s_lo);
-                const int64_t k = V.back ? b - 1 - uniform_index_k(s.ud, b - a) : a + uniform_index_k(s.ud, b - a);
+                const int64_t k = BACK ? b - 1 - uniform_index_k(s.ud, b - a) : a + uniform_index_k(s.ud, b - a);
                 y0 = __ldg(V.st_ts + k);
                 z0 = __ldg(V.st_src + k);
                 z1 = __ldg(V.st_dst + k);
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 s.hop = 1;
                 if (N2V) s.u = a;
                 s.v = b;
-                s.t = search_time(V, y0);
+                s.t = (BACK ? y0 - 1 : y0);
                 hops++;
                 bytes += START_MODEL_BYTES;
                 if (s.len >= s.cap_len) {
@@ -502,11 +504,11 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                     finish = true;
                 } else if (s.t < y0) {
                     s.R = s.g0;  // all of the node's groups are later than t
-                    if (V.back) finish = true;
+                    if (BACK) finish = true;
                     else pick = true;
                 } else if (s.t >= y1) {
                     s.R = s.g1;  // none is later than t: Gamma_t(v) is empty forward
-                    if (V.back) pick = true;
+                    if (BACK) pick = true;
                     else finish = true;
                 } else if (V.bkt && s.g1 - s.g0 >= BKT_MIN_G) {
                     // y0 <= t < y1: the bucket of t brackets c
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             }
             case S_PICK2: {
                 const int64_t q = uniform_index_k(s.ud, (int64_t)(z1 - z0));
-                const int64_t idx = V.back ? (int64_t)z1 - 1 - q : (int64_t)z0 + q;
+                const int64_t idx = BACK ? (int64_t)z1 - 1 - q : (int64_t)z0 + q;
                 const Entry *e = V.ent + idx;
                 y0 = __ldg(&e->ts);
                 z0 = __ldg(&e->other);
@@ -624,7 +626,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             case S_N2V: {
                 if (!N2V) break;  // not reached without the rejection states
                 // y1: slot key, z2: its live count
-                const unsigned long long key = V.back ? pair_key(z0, s.u, V.directed) : pair_key(s.u, z0, V.directed);
+                const unsigned long long key = BACK ? pair_key(z0, s.u, V.directed) : pair_key(s.u, z0, V.directed);
                 if ((unsigned long long)y1 == key) {
                     n2v_decide(z2 > 0 ? 1.0 : V.n2v_inv_q);
                 } else if ((unsigned long long)y1 == PAIR_EMPTY || (uint64_t)(uint32_t)s.prev_w >= V.pt_mask) {
@@ -649,7 +651,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             if (N2V && hb == BIAS_NODE2VEC) {
                 s.orient = 0;  // proposal 0 is the exponential draw of this hop's block
                 n2v_issue();
-            } else if (V.back) {
+            } else if (BACK) {
                 // groups [g0, c) in the mirrored order (latest first)
                 if (hb == BIAS_UNIFORM) {
                     s.ud = u1;
@@ -719,60 +721,31 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
 }
 
 // Padding of every row after its walk: node -1, ts INT64_MIN from len to the
-// row end.  A warp takes 32 consecutive rows per step: one coalesced load
-// of their lengths, then row by row with the lanes on consecutive cells,
-// as 16-byte stores when the rows are 16-byte aligned (cap % 4 == 0 and
-// aligned bases) and element stores otherwise.
+// row end.  A warp takes 32 consecutive rows per step: one coalesced load of
+// their lengths, then row by row with the lanes on consecutive cells.
 __global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, const int32_t *__restrict__ len,
                                                   int32_t *node, int64_t *ts)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const bool vec = (cap & 3) == 0 && ((uintptr_t)node & 15) == 0 && ((uintptr_t)ts & 15) == 0;
-    const int4 n4 = make_int4(-1, -1, -1, -1);
-    const longlong2 t2 = make_longlong2(INT64_MIN, INT64_MIN);
     for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < n_walks; w0 += warps * 32) {
-        const int32_t mine = w0 + lane < n_walks ? len[w0 + lane] : cap;
-        const int rows = (int)min((int64_t)32, n_walks - w0);
-        for (int r = 0; r < rows; r++) {
-            int32_t l = __shfl_sync(0xffffffffu, mine, r);
-            l = l < 0 ? 0 : (l > cap ? cap : l);
-            int32_t *nr = node + (w0 + r) * (int64_t)cap;
-            int64_t *tr = ts + (w0 + r) * (int64_t)cap;
-            if (vec) {
-                for (int32_t q = (l >> 2) + lane; q < (cap >> 2); q += 32) {
-                    if (4 * q >= l) {
-                        reinterpret_cast<int4 *>(nr)[q] = n4;
-                    } else {
-                        for (int32_t i = l; i < 4 * q + 4; i++) nr[i] = -1;
-                    }
-                }
-                for (int32_t q = (l >> 1) + lane; q < (cap >> 1); q += 32) {
-                    if (2 * q >= l) reinterpret_cast<longlong2 *>(tr)[q] = t2;
-                    else tr[l] = INT64_MIN;  // l odd: the second half of the pair
-                }
-            } else {
-                for (int32_t i = l + lane; i < cap; i += 32) {
-                    nr[i] = -1;
-                    tr[i] = INT64_MIN;
-                }
-            }
-        }
+        const int64_t w = w0 + lane;
+        warp_pad_walk_rows(node, ts, cap, w < n_walks ? w : -1, w < n_walks ? len[w] : cap, lane);
     }
 }
 
 // Launches the streaming walker with the register budget the CTAs-per-SM
 // knob asks for (0: the 64-register build at its occupancy limit).
 // n2v: a walk of the launch may take Node2Vec hops with p, q not both 1
-template <class P>
-static void launch_stream(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
-                          cudaStream_t st, bool n2v)
+template <class P, bool BACK>
+static void launch_stream_dir(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
+                              cudaStream_t st, bool n2v)
 {
     static int occ4 = 0, occ5 = 0, occn = 0;
     if (occ4 == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ4, k_walks_stream<P, 4, false>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_stream<P, 5, false>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_stream<P, 3, true>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ4, k_walks_stream<P, 4, false, BACK>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_stream<P, 5, false, BACK>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_stream<P, 3, true, BACK>, 256, 0);
         if (occ4 < 1) occ4 = 1;
         if (occ5 < 1) occ5 = 1;
         if (occn < 1) occn = 1;
@@ -783,9 +756,17 @@ static void launch_stream(tempest_t *h, const WalkView &V, const P &Pv, unsigned
     int64_t grid = (int64_t)h->num_sms * bps;
     const int64_t need = (total + 255) / 256;
     if (grid > need) grid = need;
-    if (n2v) k_walks_stream<P, 3, true><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
-    else if (wide) k_walks_stream<P, 5, false><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
-    else k_walks_stream<P, 4, false><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    if (n2v) k_walks_stream<P, 3, true, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else if (wide) k_walks_stream<P, 5, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else k_walks_stream<P, 4, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+}
+
+template <class P>
+static void launch_stream(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
+                          cudaStream_t st, bool n2v)
+{
+    if (V.back) launch_stream_dir<P, true>(h, V, Pv, next, total, st, n2v);
+    else launch_stream_dir<P, false>(h, V, Pv, next, total, st, n2v);
 }
 
 // Events bracketing the walk kernels of a call (created on first use).
@@ -929,6 +910,8 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
             int rc2 = h->sched == TEMPEST_SCHED_COOP ? coop_run(h, V, O, launches) : graph_run(h, V, O, launches);
             if (rc2) return rc2;
             kernel_mark(h, 1);
+            // one streaming pass pads the rows (padding inside the short
+            // hop-synchronous kernels measured slower than this pass)
             int64_t pgrid = (rq.n_walks + 7) / 8;
             const int64_t pcap = (int64_t)h->num_sms * 16;
             if (pgrid > pcap) pgrid = pcap;
