@@ -16,11 +16,10 @@
 //   3. one warp per chunk reads the chunk's group timestamps (coalesced);
 //      group g owns the table entries k in (bucket(g - 1), bucket(g)] (it is
 //      the first group of those buckets) and the node's last group also
-//      owns (bucket(g), K] (value g1).  The warp writes the entries of its
-//      32 groups together: a scan of the per-lane counts gives every lane
-//      its share of consecutive entries, so a long run (a time gap that
-//      leaves many buckets empty) is written 32 entries per store
-//      instruction rather than by one lane.  Every entry is written once.
+//      owns (bucket(g), K] (value g1).  A group's lane writes its own few
+//      entries; a long run (a time gap that leaves many buckets empty) is
+//      written by the whole warp, 32 entries per store instruction rather
+//      than by one lane.  Every entry is written once.
 #include "engine.cuh"
 #include "prims.cuh"
 #include "walkcore.cuh"
@@ -29,7 +28,8 @@ namespace tw {
 
 namespace {
 
-constexpr int BKT_UNROLL = 4;  // 32-group steps whose loads are issued together
+constexpr int BKT_UNROLL = 4;     // 32-group steps whose loads are issued together
+constexpr int BKT_SHORT_RUN = 4;  // table entries a group's own lane writes
 
 struct BigNodeOp {
     const int32_t *act;
@@ -121,28 +121,26 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
                 const bool last = valid && g == g1 - 1;
                 const int32_t lo_k = kp + 1;
                 const int32_t cnt = valid ? (last ? (int32_t)K : k) - kp : 0;
-                int32_t incl = cnt;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int32_t excl = incl - cnt;
-                const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                for (int32_t r0 = 0; r0 < total; r0 += 32) {
-                    const int32_t idx = r0 + lane;
-                    // owner: the last lane whose share starts at or before idx
-                    int32_t own = 0;
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const int32_t j = own + step;
-                        if (__shfl_sync(0xffffffffu, excl, j) <= idx) own = j;
+                // a short run (the common case: about one bucket per group) is
+                // written by its own lane; long runs (time gaps that leave
+                // many buckets empty) by the whole warp, 32 entries per store
+                if (cnt <= BKT_SHORT_RUN) {
+                    for (int32_t e = 0; e < cnt; e++) {
+                        const int32_t kk = lo_k + e;
+                        bkt[tb + kk] = kk <= k ? g : g1;
                     }
-                    const int32_t o_lo = __shfl_sync(0xffffffffu, lo_k, own);
-                    const int32_t o_ex = __shfl_sync(0xffffffffu, excl, own);
-                    const int32_t o_g = __shfl_sync(0xffffffffu, g, own);
-                    const int32_t o_k = __shfl_sync(0xffffffffu, k, own);
-                    if (idx < total) {
-                        const int32_t kk = o_lo + (idx - o_ex);
-                        bkt[tb + kk] = kk <= o_k ? o_g : g1;
+                }
+                unsigned longs = __ballot_sync(0xffffffffu, cnt > BKT_SHORT_RUN);
+                while (longs) {
+                    const int r = __ffs(longs) - 1;
+                    longs &= longs - 1;
+                    const int32_t r_lo = __shfl_sync(0xffffffffu, lo_k, r);
+                    const int32_t r_cnt = __shfl_sync(0xffffffffu, cnt, r);
+                    const int32_t r_k = __shfl_sync(0xffffffffu, k, r);
+                    const int32_t r_g = __shfl_sync(0xffffffffu, g, r);
+                    for (int32_t e = lane; e < r_cnt; e += 32) {
+                        const int32_t kk = r_lo + e;
+                        bkt[tb + kk] = kk <= r_k ? r_g : g1;
                     }
                 }
             }

@@ -437,7 +437,8 @@ __device__ __forceinline__ bool draw_n2v(const WalkView &V, const WalkOut &O, in
 
 // Padding of one walk output row (node -1, ts INT64_MIN) from cell l to the
 // row end, by the whole warp on consecutive cells, with 16-byte stores where
-// the row layout allows (vec).
+// the row layout allows (vec); streaming stores, as nothing reads padding back
+// during a walk call.
 __device__ __forceinline__ void warp_pad_row(int32_t *nr, int64_t *tr, int32_t l, int32_t cap, int lane, bool vec)
 {
     l = l < 0 ? 0 : l;
@@ -446,13 +447,13 @@ __device__ __forceinline__ void warp_pad_row(int32_t *nr, int64_t *tr, int32_t l
         const longlong2 t2 = make_longlong2(INT64_MIN, INT64_MIN);
         for (int32_t q = (l >> 2) + lane; q < (cap >> 2); q += 32) {
             if (4 * q >= l) {
-                reinterpret_cast<int4 *>(nr)[q] = n4;
+                __stcs(reinterpret_cast<int4 *>(nr) + q, n4);
             } else {
                 for (int32_t i = l; i < 4 * q + 4; i++) nr[i] = -1;
             }
         }
         for (int32_t q = (l >> 1) + lane; q < (cap >> 1); q += 32) {
-            if (2 * q >= l) reinterpret_cast<longlong2 *>(tr)[q] = t2;
+            if (2 * q >= l) __stcs(reinterpret_cast<longlong2 *>(tr) + q, t2);
             else tr[l] = INT64_MIN;  // l odd: the second half of the pair
         }
     } else {

@@ -706,8 +706,8 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 const int32_t l = __shfl_sync(0xffffffffu, my_len, src);
                 const int32_t cp = __shfl_sync(0xffffffffu, my_cap, src);
                 for (int32_t i = l + lane; i < cp; i += 32) {
-                    nr[i] = -1;
-                    tr[i] = INT64_MIN;
+                    __stcs(nr + i, -1);  // streaming stores: padding is not read back
+                    __stcs(reinterpret_cast<long long *>(tr) + i, (long long)INT64_MIN);
                 }
             }
         }
