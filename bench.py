@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full size)")
     p.add_argument("--walks", type=int, default=10_000_000)
     p.add_argument("--max-len", type=int, default=80)
-    p.add_argument("--sched", default="stream", choices=["stream", "full", "coop", "graph"])
+    p.add_argument("--sched", default="stream", choices=["stream", "full", "coop", "graph", "lane"])
     p.add_argument("--bias", default="exp", choices=["uniform", "linear", "exp", "weight", "node2vec"],
                    help="hop bias of the stream workload (weight: the weight-based sampler, rate 1/window span; "
                         "node2vec: Temporal Node2Vec with --n2v-p / --n2v-q)")
@@ -187,7 +187,7 @@ def run_ours(args, rank, world):
         # stream's mean gap of 550 ns
         eng.set_weight_rate(1.0 / (550.0 * (-spec.window)))
     eng.set_scheduler({"stream": _lib.SCHED_STREAM, "full": _lib.SCHED_FULL_WALK,
-                       "coop": _lib.SCHED_COOP, "graph": _lib.SCHED_GRAPH}[args.sched])
+                       "coop": _lib.SCHED_COOP, "graph": _lib.SCHED_GRAPH, "lane": _lib.SCHED_LANE}[args.sched])
     node = torch.empty((n_walks, L), dtype=torch.int32, device=dev)
     tso = torch.empty((n_walks, L), dtype=torch.int64, device=dev)
     ln = torch.empty((n_walks,), dtype=torch.int32, device=dev)
@@ -413,7 +413,7 @@ def run_batched(args):
         return e0.elapsed_time(e1) / args.steps
 
     results = {}
-    for name, mode in (("stream", _lib.SCHED_STREAM), ("graph", _lib.SCHED_GRAPH),
+    for name, mode in (("stream", _lib.SCHED_STREAM), ("lane", _lib.SCHED_LANE), ("graph", _lib.SCHED_GRAPH),
                        ("full", _lib.SCHED_FULL_WALK), ("coop", _lib.SCHED_COOP)):
         eng.set_scheduler(mode)
         ms = timed(lambda k: eng.walks_mixed(L, bias, seed=k, max_len_cap=cap, out=(node, tso, ln)))
@@ -672,7 +672,7 @@ def main():
     per_launch_bytes = res["model_bytes"] / max(1, len(res["walk_ms"]))
     sched = args.sched
     if res.get("tune"):
-        sched = {0: "full", 1: "coop", 2: "stream", 3: "graph"}[res["tune"]["sched"]]
+        sched = {0: "full", 1: "coop", 2: "stream", 3: "graph", 4: "lane"}[res["tune"]["sched"]]
     out = {
         "metric": METRIC,
         "value": hops / walk_s if walk_s > 0 else 0.0,
@@ -709,7 +709,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": {"stream": "k_walks_stream", "full": "k_walks_full",
-                                "coop": "coop tiers", "graph": "k_graph_hop"}[sched],
+                                "coop": "coop tiers", "graph": "k_graph_hop", "lane": "k_walks_lane"}[sched],
                      "peak_kind": peak_kind + " hbm copy (burst)",
                      "model_bytes_per_launch": per_launch_bytes},
         "ingest_roofline": {"bound": "hbm", "achieved": ing_achieved, "peak": peak, "unit": "GB/s",

@@ -96,9 +96,12 @@ enum {
                                     trip per loop iteration, interpolation
                                     search of Gamma_t(v) (no counterpart in the
                                     paper: a GB300 form of Sec. 2.4.1) */,
-    TEMPEST_SCHED_GRAPH = 3      /* hop-synchronous: one kernel per hop over the
+    TEMPEST_SCHED_GRAPH = 3,     /* hop-synchronous: one kernel per hop over the
                                     active walks, the whole hop loop captured
                                     once as a CUDA graph and replayed */
+    TEMPEST_SCHED_LANE = 4       /* persistent lanes that refill as walks end,
+                                    each advancing one whole hop per loop
+                                    iteration in lockstep with its warp */
 };
 
 /* Per-batch ingest report. */

@@ -231,7 +231,7 @@ int tempest_set_scheduler(tempest_t *h, int mode)
 {
     if (!h) return TEMPEST_EINVAL;
     if (mode != TEMPEST_SCHED_FULL_WALK && mode != TEMPEST_SCHED_COOP && mode != TEMPEST_SCHED_STREAM &&
-        mode != TEMPEST_SCHED_GRAPH)
+        mode != TEMPEST_SCHED_GRAPH && mode != TEMPEST_SCHED_LANE)
         return fail(h, TEMPEST_EINVAL, "tempest_set_scheduler: unknown mode %d", mode);
     h->sched = mode;
     return TEMPEST_OK;

@@ -198,14 +198,15 @@ static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const i
     rc = T.time_cfg(best, best_ms);
     const double start_ms = best_ms;
     if (!rc && (flags & TEMPEST_TUNE_FORMS)) {
-        const int forms[] = {TEMPEST_SCHED_STREAM, TEMPEST_SCHED_FULL_WALK, TEMPEST_SCHED_COOP, TEMPEST_SCHED_GRAPH};
-        rc = T.sweep(best, best_ms, forms, 4, [](Cfg &c, int v) { c.sched = v; });
+        const int forms[] = {TEMPEST_SCHED_STREAM, TEMPEST_SCHED_LANE, TEMPEST_SCHED_FULL_WALK, TEMPEST_SCHED_COOP,
+                             TEMPEST_SCHED_GRAPH};
+        rc = T.sweep(best, best_ms, forms, 5, [](Cfg &c, int v) { c.sched = v; });
     }
     if (!rc) {
         const int logs[] = {0, 1, 2, 3, 4};
         rc = T.sweep(best, best_ms, logs, 5, [](Cfg &c, int v) { c.bkt_log = v; });
     }
-    if (!rc && best.sched == TEMPEST_SCHED_STREAM) {
+    if (!rc && (best.sched == TEMPEST_SCHED_STREAM || best.sched == TEMPEST_SCHED_LANE)) {
         const int ctas[] = {2, 3, 4, 5};
         rc = T.sweep(best, best_ms, ctas, 4, [](Cfg &c, int v) { c.ctas = v; });
     }

@@ -309,7 +309,9 @@ __device__ __forceinline__ void start_edge(const WalkView &V, const WalkOut &O, 
 // Hop h >= 1 at a node whose groups are [c, g1) after the time filter: the
 // drawn entry (uniform over the edges of Gamma_t(v), or a group by bias and
 // then an edge inside it).
-__device__ __forceinline__ Entry draw_entry(const WalkView &V, const WalkOut &O, int64_t w, uint32_t hop, int bias,
+// (O: anything with the walk's seed and counters, .seed and .cnt.)
+template <class OUT>
+__device__ __forceinline__ Entry draw_entry(const WalkView &V, const OUT &O, int64_t w, uint32_t hop, int bias,
                                             int32_t c, int32_t g1)
 {
     const Rand4 r = walk_rand(O.seed, (uint64_t)w, hop);
@@ -326,7 +328,7 @@ __device__ __forceinline__ Entry draw_entry(const WalkView &V, const WalkOut &O,
         idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
     } else {
         const uint64_t h2 = u53_bits(r.r2, r.r3);
-        const int64_t j = sampler_index_k(h1, (int64_t)(g1 - c), bias, V.rate_hop);
+        const int64_t j = sampler_index_k(h1, (int64_t)(g1 - c), start_bias(bias), V.rate_hop);
         const int32_t e0 = __ldg(V.ngo + c + j), e1 = __ldg(V.ngo + c + j + 1);
         idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
     }
@@ -336,7 +338,8 @@ __device__ __forceinline__ Entry draw_entry(const WalkView &V, const WalkOut &O,
 // Backward hop at a node whose groups earlier than t are [g0, c), in the
 // mirrored order: uniform over the edges (position last - q), or group
 // c - 1 - j by the bias, then an edge of it (position last - q).
-__device__ __forceinline__ Entry draw_entry_back(const WalkView &V, const WalkOut &O, int64_t w, uint32_t hop,
+template <class OUT>
+__device__ __forceinline__ Entry draw_entry_back(const WalkView &V, const OUT &O, int64_t w, uint32_t hop,
                                                  int bias, int32_t g0, int32_t c)
 {
     const Rand4 r = walk_rand(O.seed, (uint64_t)w, hop);
@@ -414,7 +417,8 @@ __device__ __forceinline__ Entry n2v_propose(const WalkView &V, uint64_t seed, u
 // predecessor) takes the first proposal.  False when N2V_MAX_TRIALS
 // proposals were all rejected (the walk ends).  bytes adds the sector model
 // of the extra reads: 12 + 16 per proposal after the first, 32 per lookup.
-__device__ __forceinline__ bool draw_n2v(const WalkView &V, const WalkOut &O, int64_t w, uint32_t hop, int32_t g0,
+template <class OUT>
+__device__ __forceinline__ bool draw_n2v(const WalkView &V, const OUT &O, int64_t w, uint32_t hop, int32_t g0,
                                          int32_t c, int32_t g1, int32_t u, Entry &out, unsigned long long &bytes)
 {
     for (uint32_t k = 0; k < N2V_MAX_TRIALS; k++) {

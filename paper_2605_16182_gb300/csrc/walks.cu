@@ -720,6 +720,227 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
     }
 }
 
+// ---------------------------------------------------------------------------
+// Lane walker (TEMPEST_SCHED_LANE): persistent like the streaming walker, but
+// every iteration advances each lane by one whole hop (or one start) in
+// straight-line code, so the lanes of a warp run the same instructions
+// together (the hop-synchronous kernels' efficiency) while a lane whose walk
+// ends takes the next walk id at once (no waiting for the warp's longest
+// walk).  The hop's dependent loads (node record, bucket pair, search probes,
+// group offsets, entry) are issued in sequence; occupancy hides them.
+// ---------------------------------------------------------------------------
+
+// First group of [g0, g1) later than t, for tlo <= t < thi (the node's first
+// and last group timestamps): through the time buckets of a big node, else by
+// interpolation on the group timestamps with a bisection fallback.
+__device__ __forceinline__ int32_t lane_first_later(const WalkView &V, int32_t g0, int32_t g1, int32_t tb, int64_t tlo,
+                                                    int64_t thi, int64_t t)
+{
+    if (V.bkt && g1 - g0 >= BKT_MIN_G) {
+        const uint32_t k = bkt_index(bkt_map(tlo, thi, bkt_count(g1 - g0, V.bkt_log)), t);
+        return upper_bound_ts(V.ngts, __ldg(V.bkt + tb + k), __ldg(V.bkt + tb + k + 1), t);
+    }
+    // ngts[L] <= t < ngts[R]
+    int32_t L = g0, R = g1 - 1;
+    int64_t vL = tlo, vR = thi;
+    int32_t prev_w = R - L;
+    bool bisect = false;  // interpolate first; bisect after a probe that did not halve the bracket
+    while (R - L > 1) {
+        const int32_t p = interp_probe(L, R, vL, vR, t, bisect);
+        const int64_t a = __ldg(V.ngts + p);
+        if (a > t) {
+            R = p;
+            vR = a;
+        } else {
+            L = p;
+            vL = a;
+        }
+        bisect = 2 * (R - L) > prev_w;
+        prev_w = R - L;
+    }
+    return R;
+}
+
+// The seed and counters a draw helper needs, per request.
+struct DrawCtx {
+    uint64_t seed;
+    WalkCounters *cnt;
+};
+
+template <class P, int MINB, bool N2V, bool BACK>
+__global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, const P Pv, unsigned long long *next_walk)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    typename P::Ctx cx;
+    int64_t w = 0;
+    int32_t v = 0, u = -1, len = 0, cap_len = 0, bias = 0;
+    int64_t t = 0;
+    int mode = 0;  // 0: needs a walk, 1: fresh walk, 2: walking, 3: no more walks
+    unsigned long long hops = 0, bytes = 0;
+    const int64_t N = Pv.total();
+    constexpr int64_t WALK_CHUNK = 256;
+    int64_t q_next = 0, q_end = 0;
+    while (true) {
+        unsigned need = __ballot_sync(0xffffffffu, mode == 0);
+        while (need) {
+            if (q_next >= q_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(next_walk, (unsigned long long)WALK_CHUNK);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if ((int64_t)base >= N) {
+                    if (mode == 0) mode = 3;
+                    break;
+                }
+                q_next = (int64_t)base;
+                q_end = min(N, q_next + WALK_CHUNK);
+            }
+            const int64_t avail = q_end - q_next;
+            const int rank = __popc(need & lt);
+            const int take = (int)min((int64_t)__popc(need), avail);
+            if (mode == 0 && rank < take) {
+                w = q_next + rank;
+                mode = 1;
+            }
+            q_next += take;
+            need = __ballot_sync(0xffffffffu, mode == 0);
+        }
+        if (__all_sync(0xffffffffu, mode == 3)) break;
+
+        bool finish = false;
+        if (mode == 1) {
+            int32_t L;
+            int b;
+            Pv.open(w, cx, L, b);
+            if (!N2V && b == BIAS_NODE2VEC) b = BIAS_EXP;  // the host runs this build only when that is exact
+            cap_len = L;
+            bias = b;
+            mode = 2;
+            int32_t *nrow = Pv.nrow(cx);
+            int64_t *trow = Pv.trow(cx);
+            if (V.m == 0) {
+                len = 0;
+                finish = true;
+            } else if (Pv.policy(cx) == TEMPEST_START_PER_NODE) {
+                v = __ldg(V.pn_nodes + (int64_t)(Pv.wid(cx) / (uint64_t)Pv.pn_k(cx)));
+                nrow[0] = v;
+                trow[0] = INT64_MIN;
+                len = 1;
+                u = -1;
+                t = BACK ? INT64_MAX - 1 : INT64_MIN;
+            } else {
+                const Rand4 r = walk_rand(Pv.seed(cx), Pv.wid(cx), 0u);
+                const uint64_t k1 = u53_bits(r.r0, r.r1), k2 = u53_bits(r.r2, r.r3);
+                int64_t k;
+                if (Pv.policy(cx) == TEMPEST_START_UNIFORM_EDGE) {
+                    k = uniform_index_k(k1, V.m);
+                    if (BACK) k = V.m - 1 - k;
+                } else {
+                    int64_t g = sampler_index_k(k1, V.G, start_bias(bias), V.rate_start);
+                    if (BACK) g = V.G - 1 - g;
+                    int64_t a, e;
+                    ts_group_range(V, g, a, e);
+                    k = BACK ? e - 1 - uniform_index_k(k2, e - a) : a + uniform_index_k(k2, e - a);
+                }
+                int32_t s0 = __ldg(V.st_src + k), d0 = __ldg(V.st_dst + k);
+                const int64_t t0 = __ldg(V.st_ts + k);
+                if ((((!V.directed && (r.r3 & 1u)) ? 1u : 0u) ^ ((BACK && V.back_swap) ? 1u : 0u)) != 0u) {
+                    const int32_t x = s0;
+                    s0 = d0;
+                    d0 = x;
+                }
+                nrow[0] = s0;
+                nrow[1] = d0;
+                trow[0] = INT64_MIN;
+                trow[1] = t0;
+                len = 2;
+                u = s0;
+                v = d0;
+                t = BACK ? t0 - 1 : t0;
+                hops++;
+                bytes += START_MODEL_BYTES;
+                if (len >= cap_len) finish = true;
+            }
+        } else if (mode == 2) {
+            // one hop from v at search time t
+            const uint32_t hop = (uint32_t)(len - 1);
+            int32_t g0, g1, tb;
+            int64_t tlo, thi;
+            load_range(V.ngr + v, g0, g1, tb, tlo, thi);
+            int32_t c = g0;
+            if (g0 == g1) {
+                finish = true;
+            } else if (t < tlo) {
+                c = g0;
+            } else if (t >= thi) {
+                c = g1;
+            } else {
+                c = lane_first_later(V, g0, g1, tb, tlo, thi, t);
+            }
+            if (!finish && (BACK ? c == g0 : c == g1)) finish = true;  // Gamma_t(v) is empty
+            if (!finish) {
+                const DrawCtx D{Pv.seed(cx), Pv.cnt()};
+                const uint64_t wid = Pv.wid(cx);
+                Entry e;
+                bool ok = true;
+                if (N2V && bias == BIAS_NODE2VEC) {
+                    ok = draw_n2v(V, D, (int64_t)wid, hop, g0, c, g1, u, e, bytes);
+                } else if (BACK) {
+                    e = draw_entry_back(V, D, (int64_t)wid, hop, bias, g0, c);
+                } else {
+                    e = draw_entry(V, D, (int64_t)wid, hop, bias, c, g1);
+                }
+                if (!ok) {
+                    finish = true;  // every Node2Vec proposal rejected
+                } else {
+                    Pv.nrow(cx)[len] = e.other;
+                    Pv.trow(cx)[len] = e.ts;
+                    hops++;
+                    bytes += hop_model_bytes((int64_t)(g1 - g0));
+                    len++;
+                    u = v;
+                    v = e.other;
+                    t = BACK ? e.ts - 1 : e.ts;
+                    if (len >= cap_len) finish = true;
+                }
+            }
+        }
+        // rows of the walks that ended here: the whole warp writes their
+        // padding, 32 consecutive cells per store
+        unsigned fin = __ballot_sync(0xffffffffu, finish);
+        if (fin) {
+            unsigned long long my_n = 0, my_t = 0;
+            int32_t my_len = 0, my_cap = 0;
+            if (finish) {
+                Pv.finish(cx, len);
+                my_n = (unsigned long long)Pv.nrow(cx);
+                my_t = (unsigned long long)Pv.trow(cx);
+                my_len = len;
+                my_cap = Pv.cap(cx);
+                mode = 0;
+            }
+            while (fin) {
+                const int src = __ffs(fin) - 1;
+                fin &= fin - 1;
+                int32_t *nr = reinterpret_cast<int32_t *>(__shfl_sync(0xffffffffu, my_n, src));
+                int64_t *tr = reinterpret_cast<int64_t *>(__shfl_sync(0xffffffffu, my_t, src));
+                const int32_t l = __shfl_sync(0xffffffffu, my_len, src);
+                const int32_t cp = __shfl_sync(0xffffffffu, my_cap, src);
+                for (int32_t i = l + lane; i < cp; i += 32) {
+                    __stcs(nr + i, -1);
+                    __stcs(reinterpret_cast<long long *>(tr) + i, (long long)INT64_MIN);
+                }
+            }
+        }
+    }
+    hops = warp_sum(hops);
+    bytes = warp_sum(bytes);
+    if (lane == 0 && hops) {
+        atomicAdd(&Pv.cnt()->hops, hops);
+        atomicAdd(&Pv.cnt()->model_bytes, bytes);
+    }
+}
+
 // Padding of every row after its walk: node -1, ts INT64_MIN from len to the
 // row end.  A warp takes 32 consecutive rows per step: one coalesced load of
 // their lengths, then row by row with the lanes on consecutive cells.
@@ -761,10 +982,37 @@ static void launch_stream_dir(tempest_t *h, const WalkView &V, const P &Pv, unsi
     else k_walks_stream<P, 4, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
 }
 
+template <class P, bool BACK>
+static void launch_lane_dir(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
+                            cudaStream_t st, bool n2v)
+{
+    static int occ = 0, occn = 0;
+    if (occ == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walks_lane<P, 4, false, BACK>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_lane<P, 3, true, BACK>, 256, 0);
+        if (occ < 1) occ = 1;
+        if (occn < 1) occn = 1;
+    }
+    const int o = n2v ? occn : occ;
+    const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, o) : o;
+    int64_t grid = (int64_t)h->num_sms * bps;
+    const int64_t need = (total + 255) / 256;
+    if (grid > need) grid = need;
+    if (n2v) k_walks_lane<P, 3, true, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else k_walks_lane<P, 4, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+}
+
+// The persistent walker of the handle's form (the lane walker for
+// TEMPEST_SCHED_LANE, else the streaming walker).
 template <class P>
 static void launch_stream(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
                           cudaStream_t st, bool n2v)
 {
+    if (h->sched == TEMPEST_SCHED_LANE) {
+        if (V.back) launch_lane_dir<P, true>(h, V, Pv, next, total, st, n2v);
+        else launch_lane_dir<P, false>(h, V, Pv, next, total, st, n2v);
+        return;
+    }
     if (V.back) launch_stream_dir<P, true>(h, V, Pv, next, total, st, n2v);
     else launch_stream_dir<P, false>(h, V, Pv, next, total, st, n2v);
 }

@@ -21,7 +21,7 @@ from parity_util import MIN_HOP_AGREEMENT, assert_walks_bit_exact, compare_biase
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULERS = (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_COOP, _lib.SCHED_GRAPH)
+SCHEDULERS = (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_COOP, _lib.SCHED_GRAPH, _lib.SCHED_LANE)
 
 
 def pair(window, directed, enable=True):

@@ -37,7 +37,7 @@ def ingest_both(eng, orc, s, d, t, on_gpu=True):
     return st
 
 
-SCHEDULERS = (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_COOP, _lib.SCHED_GRAPH)
+SCHEDULERS = (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_COOP, _lib.SCHED_GRAPH, _lib.SCHED_LANE)
 
 
 def walks_both(eng, orc, n, L, bias, policy=0, seed=0, margin=False):

@@ -37,7 +37,8 @@ def test_knobs_validate_and_round_trip():
         assert eng.get_tuning(knob) == val
 
 
-@pytest.mark.parametrize("sched", [_lib.SCHED_STREAM, _lib.SCHED_COOP, _lib.SCHED_FULL_WALK, _lib.SCHED_GRAPH])
+@pytest.mark.parametrize("sched", [_lib.SCHED_STREAM, _lib.SCHED_COOP, _lib.SCHED_FULL_WALK, _lib.SCHED_GRAPH,
+                                   _lib.SCHED_LANE])
 def test_every_knob_setting_gives_the_same_walks(sched):
     eng = _engine()
     ref = {b: _walks(eng, b) for b in (0, 2)}
@@ -58,7 +59,7 @@ def test_autotune_reports_and_keeps_its_choice():
     assert len(rep["trials"]) >= 8
     assert rep["best_ms"] <= rep["start_ms"] + 1e-9
     assert rep["best_ms"] == min(t["ms"] for t in rep["trials"])
-    assert {t["sched"] for t in rep["trials"]} == {0, 1, 2, 3}
+    assert {t["sched"] for t in rep["trials"]} == {0, 1, 2, 3, 4}
     assert eng.get_tuning(_lib.TUNE_BKT_LOG) == rep["bkt_log"]
     assert eng.get_tuning(_lib.TUNE_STREAM_CTAS) == rep["stream_ctas"]
     got = eng.walks(20000, 30, bias=2, seed=9)
