@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full size)")
     p.add_argument("--walks", type=int, default=10_000_000)
     p.add_argument("--max-len", type=int, default=80)
-    p.add_argument("--sched", default="stream", choices=["stream", "full", "coop", "graph", "lane"])
+    p.add_argument("--sched", default="lane", choices=["stream", "full", "coop", "graph", "lane"])
     p.add_argument("--bias", default="exp", choices=["uniform", "linear", "exp", "weight", "node2vec"],
                    help="hop bias of the stream workload (weight: the weight-based sampler, rate 1/window span; "
                         "node2vec: Temporal Node2Vec with --n2v-p / --n2v-q)")
@@ -231,7 +231,7 @@ def run_ours(args, rank, world):
     if args.autotune:
         # the autotuner times candidate settings on the warmed-up window
         # (outside the timed region) and leaves the fastest selected
-        tune = eng.autotune(n_walks, L, bias=bias_id, seed=seed_base + 99, forms=True)
+        tune = eng.autotune(n_walks, L, bias=bias_id, seed=seed_base + 99, forms=True, per_ingest=True)
     clocks = ClockSampler()
     if rank == 0:
         clocks.start()

@@ -91,7 +91,7 @@ enum {
     TEMPEST_SCHED_FULL_WALK = 0, /* one thread carries one walk (Sec. 2.4.1) */
     TEMPEST_SCHED_COOP = 1,      /* per-hop regrouping by node, thread / warp /
                                     block tiers (Sec. 2.4.3-2.4.5, Alg. 1) */
-    TEMPEST_SCHED_STREAM = 2     /* default: persistent lanes that refill from a
+    TEMPEST_SCHED_STREAM = 2     /* persistent lanes that refill from a
                                     work counter as walks end, one memory round
                                     trip per loop iteration, interpolation
                                     search of Gamma_t(v) (no counterpart in the
@@ -99,9 +99,10 @@ enum {
     TEMPEST_SCHED_GRAPH = 3,     /* hop-synchronous: one kernel per hop over the
                                     active walks, the whole hop loop captured
                                     once as a CUDA graph and replayed */
-    TEMPEST_SCHED_LANE = 4       /* persistent lanes that refill as walks end,
-                                    each advancing one whole hop per loop
-                                    iteration in lockstep with its warp */
+    TEMPEST_SCHED_LANE = 4       /* default: persistent lanes that refill as
+                                    walks end, each advancing one whole hop
+                                    per loop iteration in lockstep with its
+                                    warp */
 };
 
 /* Per-batch ingest report. */
@@ -349,7 +350,11 @@ typedef struct {
     double start_ms;       /* call time of the configuration it started from */
     tempest_tune_trial trials[TEMPEST_TUNE_MAX_TRIALS];
 } tempest_tune_report;
-#define TEMPEST_TUNE_FORMS 1  /* flags: also choose the walk form */
+#define TEMPEST_TUNE_FORMS 1       /* flags: also choose the walk form */
+#define TEMPEST_TUNE_PER_INGEST 2  /* flags: every timed call also rebuilds the
+                                      derived walk indexes (time buckets,
+                                      active nodes, weight sums), as the first
+                                      walk call after an ingest does */
 
 /* Autotuner: times walk calls of n_walks walks (max_len, bias, start_policy,
  * seed as in tempest_walks) on the current index state for candidate

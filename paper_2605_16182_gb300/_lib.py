@@ -28,6 +28,7 @@ START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH, SCHED_LANE = 0, 1, 2, 3, 4
 TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS = 0, 1, 2, 3
 TUNE_FORMS = 1
+TUNE_PER_INGEST = 2
 TUNE_MAX_TRIALS = 48
 (STATE_SRC, STATE_DST, STATE_TS, STATE_TS_GROUP_OFF, STATE_NODE_OFF, STATE_NODE_ORDER,
  STATE_NODE_GROUP_OFF, STATE_NODE_GIDX) = range(8)
@@ -513,10 +514,12 @@ class Engine:
         """Keep the in-edge index that backward walks of a directed graph read."""
         tempest_enable_backward(self.h)
 
-    def autotune(self, n_walks, max_len, bias=BIAS_EXP, start_policy=0, seed=0, forms=True) -> dict:
-        """Time candidate settings on the live index and keep the fastest."""
-        return tempest_autotune(self.h, n_walks, max_len, bias, start_policy, seed,
-                                TUNE_FORMS if forms else 0).as_dict()
+    def autotune(self, n_walks, max_len, bias=BIAS_EXP, start_policy=0, seed=0, forms=True,
+                 per_ingest=False) -> dict:
+        """Time candidate settings on the live index and keep the fastest; per_ingest charges every
+        timed call the rebuild of the derived indexes (a workload with an ingest before each call)."""
+        flags = (TUNE_FORMS if forms else 0) | (TUNE_PER_INGEST if per_ingest else 0)
+        return tempest_autotune(self.h, n_walks, max_len, bias, start_policy, seed, flags).as_dict()
 
     def autotune_mixed(self, max_len_arr, bias_arr, max_len_cap=None, start_policy=0, seed=0, forms=True) -> dict:
         """Autotune on a mixed request's own per-walk lengths and biases."""

@@ -89,7 +89,7 @@ struct tempest {
     double lam_hop = 1.0;
     double lam_start = 0.0;  // 0: 1 / G_tot
     double lam_w = 1e-9;     // weight-based sampler rate per timestamp unit
-    int sched = TEMPEST_SCHED_STREAM;
+    int sched = TEMPEST_SCHED_LANE;
     cudaStream_t stream = nullptr;
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*release_fn)(void *, void *) = nullptr;

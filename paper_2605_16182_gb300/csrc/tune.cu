@@ -34,6 +34,7 @@ void apply(tempest_t *h, const Cfg &c)
 struct Tuner {
     tempest_t *h;
     WalkRequest rq;
+    bool per_ingest = false;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     tempest_tune_report rep{};
 
@@ -46,6 +47,7 @@ struct Tuner {
         if ((rc = walks_run(h, rq))) return rc;
         double best = 1e300;
         for (int r = 0; r < 3; r++) {
+            if (per_ingest) h->state_ver++;  // as after an ingest: the call rebuilds the derived indexes
             cudaEventRecord(e0, h->stream);
             if ((rc = walks_run(h, rq))) return rc;
             cudaEventRecord(e1, h->stream);
@@ -168,7 +170,8 @@ static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const i
     if (n_walks < 1 || max_len < 2 ||
         (start_policy != TEMPEST_START_UNIFORM_EDGE && start_policy != TEMPEST_START_BIASED_TS))
         return fail(h, TEMPEST_EINVAL, "tempest_autotune: bad n_walks, max_len or start policy");
-    if ((flags & ~TEMPEST_TUNE_FORMS) != 0) return fail(h, TEMPEST_EINVAL, "tempest_autotune: unknown flags");
+    if ((flags & ~(TEMPEST_TUNE_FORMS | TEMPEST_TUNE_PER_INGEST)) != 0)
+        return fail(h, TEMPEST_EINVAL, "tempest_autotune: unknown flags");
     if (n_walks > (int64_t)INT32_MAX / 2) return fail(h, TEMPEST_EINVAL, "tempest_autotune: n_walks too large");
     int rc;
     const size_t cells = (size_t)n_walks * (size_t)max_len;
@@ -178,6 +181,7 @@ static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const i
 
     Tuner T;
     T.h = h;
+    T.per_ingest = (flags & TEMPEST_TUNE_PER_INGEST) != 0;
     T.rq.n_walks = n_walks;
     T.rq.cap = max_len;
     T.rq.max_len = max_len;

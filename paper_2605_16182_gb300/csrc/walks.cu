@@ -986,19 +986,23 @@ template <class P, bool BACK>
 static void launch_lane_dir(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
                             cudaStream_t st, bool n2v)
 {
-    static int occ = 0, occn = 0;
+    static int occ = 0, occ5 = 0, occn = 0;
     if (occ == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walks_lane<P, 4, false, BACK>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_lane<P, 5, false, BACK>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_lane<P, 3, true, BACK>, 256, 0);
         if (occ < 1) occ = 1;
+        if (occ5 < 1) occ5 = 1;
         if (occn < 1) occn = 1;
     }
-    const int o = n2v ? occn : occ;
+    const bool wide = h->stream_ctas > 4 && !n2v;
+    const int o = n2v ? occn : (wide ? occ5 : occ);
     const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, o) : o;
     int64_t grid = (int64_t)h->num_sms * bps;
     const int64_t need = (total + 255) / 256;
     if (grid > need) grid = need;
     if (n2v) k_walks_lane<P, 3, true, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else if (wide) k_walks_lane<P, 5, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
     else k_walks_lane<P, 4, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
 }
 

@@ -52,7 +52,7 @@ def check_back(eng, orc, n, L, policy=0, seed=0, biases=(0, 1, 2), scheds=SCHEDU
                 assert total == 0 or agree / total >= MIN_HOP_AGREEMENT, (where, agree, total)
             else:
                 assert_walks_bit_exact(g, o, where)
-    eng.set_scheduler(_lib.SCHED_STREAM)
+    eng.set_scheduler(_lib.SCHED_LANE)
 
 
 def _stream(rng, n_batches, max_batch, n_nodes, span, monotone):
@@ -97,8 +97,8 @@ def test_backward_streaming_hubs_all_forms(directed):
         ingest_both(eng, orc, s.numpy(), d.numpy(), t.numpy())
         if i in (0, 4, 6):
             check_back(eng, orc, 3000, 14, seed=40 + i, biases=(0, 2),
-                       scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK) if i < 6 else SCHEDULERS)
-    check_back(eng, orc, 3000, 10, policy=_lib.START_BIASED_TS, seed=3, scheds=(_lib.SCHED_STREAM,))
+                       scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_LANE) if i < 6 else SCHEDULERS)
+    check_back(eng, orc, 3000, 10, policy=_lib.START_BIASED_TS, seed=3, scheds=(_lib.SCHED_STREAM, _lib.SCHED_LANE))
 
 
 def test_enable_backward_mid_stream_replays_the_live_edges():
@@ -114,14 +114,14 @@ def test_enable_backward_mid_stream_replays_the_live_edges():
     assert e.value.code == _lib.TEMPEST_EINVAL
     eng.enable_backward()
     eng.enable_backward()  # a second call keeps the index
-    check_back(eng, orc, 2000, 12, seed=5, biases=(0, 1), scheds=(_lib.SCHED_STREAM,))
+    check_back(eng, orc, 2000, 12, seed=5, biases=(0, 1), scheds=(_lib.SCHED_STREAM, _lib.SCHED_LANE))
     # a late batch (timestamps inside the window but older than the newest)
     _, s, d, t = batches[5]
     t_late = t.numpy() - (int(t.numpy().max()) - int(t.numpy().min())) // 2
     ingest_both(eng, orc, s.numpy(), d.numpy(), t_late)
     for _, s, d, t in batches[6:]:
         ingest_both(eng, orc, s.numpy(), d.numpy(), t.numpy())
-    check_back(eng, orc, 2000, 12, seed=6, biases=(0, 2), scheds=(_lib.SCHED_STREAM, _lib.SCHED_COOP))
+    check_back(eng, orc, 2000, 12, seed=6, biases=(0, 2), scheds=(_lib.SCHED_STREAM, _lib.SCHED_COOP, _lib.SCHED_LANE))
 
 
 @pytest.mark.parametrize("directed", [1, 0])

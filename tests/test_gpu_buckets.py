@@ -71,7 +71,7 @@ def test_bucket_density_knob_keeps_walks():
         eng.set_tuning(_lib.TUNE_BKT_LOG, lg)
         got = eng.walks(5000, 20, bias=1, seed=4)
         assert all(torch.equal(a, b) for a, b in zip(ref, got)), lg
-    check_walks(eng, orc, 3000, 20, seed=5, biases=(0, 1), scheds=(_lib.SCHED_STREAM,))
+    check_walks(eng, orc, 3000, 20, seed=5, biases=(0, 1), scheds=(_lib.SCHED_STREAM, _lib.SCHED_LANE))
 
 
 def test_tables_follow_streaming_ingest():
@@ -83,4 +83,4 @@ def test_tables_follow_streaming_ingest():
         ingest_both(eng, orc, s.numpy(), d.numpy(), t.numpy())
         if i in (0, 3, 7, 12, 19):
             check_walks(eng, orc, 3000, 16, seed=100 + i, biases=(0, 2),
-                        scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK))
+                        scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_LANE))

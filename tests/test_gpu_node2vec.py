@@ -46,7 +46,7 @@ def check_n2v(eng, orc, n, L, policy=0, seed=0, direction=0, scheds=SCHEDULERS):
         o = orc.walks(n, L, bias=N2V, start_policy=policy, seed=seed, with_margin=True, direction=direction)
         agree, total, _ = compare_biased(g, o, o[3])
         assert total == 0 or agree / total >= MIN_HOP_AGREEMENT, (sched, agree, total)
-    eng.set_scheduler(_lib.SCHED_STREAM)
+    eng.set_scheduler(_lib.SCHED_LANE)
 
 
 @pytest.mark.parametrize("directed", [1, 0])
@@ -60,8 +60,8 @@ def test_node2vec_streaming_all_forms(directed, pq):
         ingest_both(eng, orc, s.numpy(), d.numpy(), t.numpy())
         if i in (0, 3, 6):
             check_n2v(eng, orc, 3000, 12, seed=60 + i,
-                      scheds=SCHEDULERS if i == 6 else (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK))
-    check_n2v(eng, orc, 3000, 10, policy=_lib.START_BIASED_TS, seed=4, scheds=(_lib.SCHED_STREAM,))
+                      scheds=SCHEDULERS if i == 6 else (_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_LANE))
+    check_n2v(eng, orc, 3000, 10, policy=_lib.START_BIASED_TS, seed=4, scheds=(_lib.SCHED_STREAM, _lib.SCHED_LANE))
 
 
 @pytest.mark.parametrize("directed", [1, 0])
@@ -73,9 +73,9 @@ def test_node2vec_backward_and_per_node(directed):
     check_n2v(eng, orc, 3000, 12, seed=8, direction=1)
     na = eng.active_nodes()
     check_n2v(eng, orc, 2 * na, 10, policy=_lib.START_PER_NODE, seed=9,
-              scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_COOP))
+              scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_COOP, _lib.SCHED_LANE))
     nb = eng.active_nodes(direction=1)
-    check_n2v(eng, orc, nb, 10, policy=_lib.START_PER_NODE, seed=10, direction=1, scheds=(_lib.SCHED_STREAM,))
+    check_n2v(eng, orc, nb, 10, policy=_lib.START_PER_NODE, seed=10, direction=1, scheds=(_lib.SCHED_STREAM, _lib.SCHED_LANE))
 
 
 def test_node2vec_pair_table_under_sliding_window_and_rebuilds():
@@ -95,7 +95,7 @@ def test_node2vec_pair_table_under_sliding_window_and_rebuilds():
             ts = ts - 120  # late: inside the window, older than the newest edges
         ingest_both(eng, orc, s, d, ts)
         if b % 8 == 7 or b == 25:
-            check_n2v(eng, orc, 1500, 10, seed=b, scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK))
+            check_n2v(eng, orc, 1500, 10, seed=b, scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_LANE))
 
 
 def test_node2vec_unit_parameters_equal_exponential_walks():

@@ -59,7 +59,7 @@ def check_walks(eng, orc, n, L, policy=0, seed=0, biases=(0, 1, 2), scheds=SCHED
                 assert total == 0 or agree / total >= MIN_HOP_AGREEMENT, (sched, agree, total)
             else:
                 assert_walks_bit_exact(g, o, "sched %d bias %d" % (sched, bias))
-    eng.set_scheduler(_lib.SCHED_STREAM)
+    eng.set_scheduler(_lib.SCHED_LANE)
 
 
 # ------------------------------------------------------------------ state
@@ -288,7 +288,7 @@ def test_growing_hub_moves_regions_and_rebuilds():
         ingest_both(eng, orc, s, d, ts)
         assert_state_equal(eng.state(), orc.state())
         if b % 4 == 3:
-            check_walks(eng, orc, 2000, 12, seed=b, biases=(0, 1), scheds=(_lib.SCHED_STREAM,))
+            check_walks(eng, orc, 2000, 12, seed=b, biases=(0, 1), scheds=(_lib.SCHED_STREAM, _lib.SCHED_LANE))
 
 
 @pytest.mark.parametrize("directed", [1, 0])
@@ -383,7 +383,7 @@ def test_weight_based_walks_all_forms(directed):
         if i in (0, 3, 6):
             check_walks(eng, orc, 4000, 14, seed=20 + i, biases=(3,))
     check_walks(eng, orc, 3000, 10, policy=_lib.START_BIASED_TS, seed=9, biases=(3,),
-                scheds=(_lib.SCHED_STREAM,))
+                scheds=(_lib.SCHED_STREAM, _lib.SCHED_LANE))
 
 
 def test_weight_based_walks_after_reference_moves():
@@ -400,7 +400,7 @@ def test_weight_based_walks_after_reference_moves():
         ts = (t + np.sort(rng.integers(0, 20000, n))).astype(np.int64)
         t = int(ts[-1])
         ingest_both(eng, orc, s, d, ts)
-        check_walks(eng, orc, 2000, 12, seed=b, biases=(3,), scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK))
+        check_walks(eng, orc, 2000, 12, seed=b, biases=(3,), scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_LANE))
 
 
 def test_weight_bias_in_mixed_and_batched_requests():

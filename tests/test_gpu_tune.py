@@ -81,3 +81,17 @@ def test_autotune_on_a_mixed_request():
     assert all(torch.equal(x, y) for x, y in zip(ref, got))
     with pytest.raises(_lib.TempestError):
         eng.autotune_mixed(lens.cpu(), bias.cpu(), max_len_cap=40)
+
+
+def test_autotune_per_ingest_charges_the_index_rebuild():
+    """With the per-ingest flag every timed call rebuilds the derived walk
+    indexes (as the first call after an ingest does); the walks stay the same
+    and the reported times include the rebuild."""
+    eng = _engine()
+    ref = _walks(eng, 2)
+    plain = eng.autotune(50000, 30, bias=2, seed=1, forms=False)
+    rep = eng.autotune(50000, 30, bias=2, seed=1, forms=False, per_ingest=True)
+    assert rep["best_ms"] == min(t["ms"] for t in rep["trials"])
+    assert rep["start_ms"] >= 0.8 * plain["best_ms"]
+    got = eng.walks(20000, 30, bias=2, seed=9)
+    assert all(torch.equal(x, y) for x, y in zip(ref, got))
