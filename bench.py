@@ -92,14 +92,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(hops):
+def recorded_traffic(hops, kernel):
     """DRAM bytes of the walk kernel from the committed ncu summary, scaled to
-    this launch by hops; None when the kernel changed since the capture."""
+    this launch by hops; None when the summary is of another kernel or the
+    kernel changed since the capture."""
     p = os.path.join(ROOT, "profiles", "walk_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash() or not d.get("kernel", "").startswith(kernel + "<"):
         return None
     return d["dram_bytes_per_hop"] * hops
 
@@ -663,7 +664,12 @@ def main():
     ing_bytes = 32 * b_edges + 24 * res["live"] + 8 * res["n_nodes"] + 4 * (res["G_tot"] + res["Gn"])
     ing_s_mean = ingest_s / max(1, len(res["ingest_ms"]))
     ing_achieved = ing_bytes / ing_s_mean / 1e9 if ing_s_mean > 0 else 0.0
-    traffic = recorded_traffic(res["hops"] / max(1, len(res["walk_ms"])))
+    sched_early = args.sched
+    if res.get("tune"):
+        sched_early = {0: "full", 1: "coop", 2: "stream", 3: "graph", 4: "lane"}[res["tune"]["sched"]]
+    kname = {"stream": "k_walks_stream", "full": "k_walks_full", "coop": "coop tiers", "graph": "k_graph_hop",
+             "lane": "k_walks_lane"}[sched_early]
+    traffic = recorded_traffic(res["hops"] / max(1, len(res["walk_ms"])), kname)
     cpu = None
     if not args.no_cpu:
         o = oracle_sample(seconds_budget=args.cpu_seconds)
@@ -708,8 +714,7 @@ def main():
         "live_edges": res["live"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": {"stream": "k_walks_stream", "full": "k_walks_full",
-                                "coop": "coop tiers", "graph": "k_graph_hop", "lane": "k_walks_lane"}[sched],
+                     "kernel": kname,
                      "peak_kind": peak_kind + " hbm copy (burst)",
                      "model_bytes_per_launch": per_launch_bytes},
         "ingest_roofline": {"bound": "hbm", "achieved": ing_achieved, "peak": peak, "unit": "GB/s",
