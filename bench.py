@@ -254,7 +254,8 @@ def run_ours(args, rank, world):
     res = dict(hops=hops, walk_s=walk_s, ingest_s=ingest_s, edges=edges, total_ms=total_ms,
                model_bytes=model_bytes, launches=launches, ingest_ms=ingest_ms, walk_ms=walk_ms,
                walk_kernel_ms=walk_kernel_ms, live=counts["m"], clocks=clk, gen_s=t_gen, n_walks=n_walks,
-               n_nodes=counts["n_nodes"], G_tot=counts["G_tot"], Gn=counts["Gn"], tune=tune)
+               n_nodes=counts["n_nodes"], G_tot=counts["G_tot"], Gn=counts["Gn"], tune=tune,
+               n_nodes_spec=spec.n_nodes)
 
     # end to end through the C ABI with host buffers (one step, after the timed ones)
     if not args.no_e2e:
@@ -694,7 +695,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": "billion-edge-stream-100M-nodes-1B-edges" + ("" if args.scale == 1.0 else
                                                                          " scaled %g" % args.scale),
-                   "nodes": int(100_000_000 * args.scale) if args.scale != 1.0 else 100_000_000,
+                   "nodes": res["n_nodes_spec"],
                    "batch_edges": int(10_000_000 * args.scale), "window_edges": int(200_000_000 * args.scale),
                    "walks_per_call": res["n_walks"], "max_len": args.max_len,
                    "bias": {"exp": "exponential", "weight": "weight-based exponential",
