@@ -431,7 +431,7 @@ def run_batched(args):
     results["autotuned"] = {"ms_per_call": ms, "hops": ws["hops"], "launches_per_call": ws["launches"],
                             "hops_per_s": ws["hops"] / (ms / 1e3),
                             "choice": {k: tune[k] for k in ("sched", "bkt_log", "coop_w_warp", "coop_mega",
-                                                             "stream_ctas")}}
+                                                             "stream_ctas", "pad_pass")}}
     eng.set_scheduler(_lib.SCHED_STREAM)
     eng.set_tuning(_lib.TUNE_BKT_LOG, 2)
     eng.set_tuning(_lib.TUNE_STREAM_CTAS, 0)
@@ -732,7 +732,7 @@ def main():
     if res.get("tune"):
         t = res["tune"]
         out["autotune"] = {k: t[k] for k in ("sched", "bkt_log", "coop_w_warp", "coop_mega", "stream_ctas",
-                                             "best_ms", "start_ms")}
+                                             "pad_pass", "best_ms", "start_ms")}
         out["autotune"]["trials"] = len(t["trials"])
     print(json.dumps(out), flush=True)
 

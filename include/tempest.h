@@ -332,7 +332,10 @@ enum {
      * walker, 0 = as many as fit; values above 4 select a build with a
      * smaller register budget (more warps in flight, a few spills); 0..16;
      * default 0 */
-    TEMPEST_TUNE_STREAM_CTAS = 3
+    TEMPEST_TUNE_STREAM_CTAS = 3,
+    /* TEMPEST_SCHED_LANE: 0 (default) the walker writes each row's padding
+     * as its walk ends; 1 one streaming pass pads all rows after the walks */
+    TEMPEST_TUNE_PAD_PASS = 4
 };
 /* Set / read one knob.  EINVAL on an unknown knob or a value out of range. */
 int tempest_set_tuning(tempest_t *h, int knob, int64_t value);
@@ -340,12 +343,12 @@ int tempest_get_tuning(tempest_t *h, int knob, int64_t *value);
 
 #define TEMPEST_TUNE_MAX_TRIALS 48
 typedef struct {
-    int32_t sched, bkt_log, coop_w_warp, coop_mega, stream_ctas, pad;
+    int32_t sched, bkt_log, coop_w_warp, coop_mega, stream_ctas, pad_pass;
     double ms;             /* walk-call device time (start to padded rows) */
 } tempest_tune_trial;
 typedef struct {
-    int32_t sched, bkt_log, coop_w_warp, coop_mega, stream_ctas; /* chosen */
-    int32_t n_trials;
+    int32_t sched, bkt_log, coop_w_warp, coop_mega, stream_ctas, pad_pass; /* chosen */
+    int32_t n_trials, reserved;
     double best_ms;        /* call time of the chosen configuration */
     double start_ms;       /* call time of the configuration it started from */
     tempest_tune_trial trials[TEMPEST_TUNE_MAX_TRIALS];

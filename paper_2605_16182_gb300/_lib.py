@@ -26,7 +26,7 @@ BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP, BIAS_EXP_WEIGHT, BIAS_NODE2VEC = 0, 1, 2, 3
 N2V_MAX_TRIALS = 4096
 START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH, SCHED_LANE = 0, 1, 2, 3, 4
-TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS = 0, 1, 2, 3
+TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS, TUNE_PAD_PASS = 0, 1, 2, 3, 4
 TUNE_FORMS = 1
 TUNE_PER_INGEST = 2
 TUNE_MAX_TRIALS = 48
@@ -81,18 +81,19 @@ class WalkStats(ctypes.Structure):
 
 class TuneTrial(ctypes.Structure):
     _fields_ = [("sched", ctypes.c_int32), ("bkt_log", ctypes.c_int32), ("coop_w_warp", ctypes.c_int32),
-                ("coop_mega", ctypes.c_int32), ("stream_ctas", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("coop_mega", ctypes.c_int32), ("stream_ctas", ctypes.c_int32), ("pad_pass", ctypes.c_int32),
                 ("ms", ctypes.c_double)]
 
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("sched", ctypes.c_int32), ("bkt_log", ctypes.c_int32), ("coop_w_warp", ctypes.c_int32),
-                ("coop_mega", ctypes.c_int32), ("stream_ctas", ctypes.c_int32), ("n_trials", ctypes.c_int32),
+                ("coop_mega", ctypes.c_int32), ("stream_ctas", ctypes.c_int32), ("pad_pass", ctypes.c_int32),
+                ("n_trials", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("best_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
                 ("trials", TuneTrial * TUNE_MAX_TRIALS)]
 
     def as_dict(self):
-        keys = ("sched", "bkt_log", "coop_w_warp", "coop_mega", "stream_ctas")
+        keys = ("sched", "bkt_log", "coop_w_warp", "coop_mega", "stream_ctas", "pad_pass")
         d = {k: getattr(self, k) for k in keys + ("best_ms", "start_ms")}
         d["trials"] = [dict({k: getattr(t, k) for k in keys}, ms=t.ms) for t in self.trials[:self.n_trials]]
         return d

@@ -44,12 +44,16 @@ struct IngestScratch {
 
 // The per-node record a hop reads first: the node's live groups [g_lo,
 // g_hi), the base of its time-bucket table (nodes with enough groups; set
-// when the tables are built), and the timestamps of its first and last live
-// groups.  32 bytes, one sector: a hop gets everything it needs before the
-// search in one round trip.
+// when the tables are built), the timestamps of its first and last live
+// groups, and (last_other) the far endpoint of the last group's entry when
+// that group holds exactly one entry (else -1): a biased hop that picks the
+// node's latest group, the likeliest pick of the exponential bias, then has
+// its next node and time without reading the group offsets or the entry.
+// 32 bytes, one sector: a hop gets everything it needs before the search in
+// one round trip.
 struct __align__(32) NodeRange {
     int32_t g_lo, g_hi;
-    int32_t tb, pad;
+    int32_t tb, last_other;
     int64_t t_first, t_last;
 };
 
@@ -90,6 +94,7 @@ struct tempest {
     double lam_start = 0.0;  // 0: 1 / G_tot
     double lam_w = 1e-9;     // weight-based sampler rate per timestamp unit
     int sched = TEMPEST_SCHED_LANE;
+    int pad_pass = 0;  // lane walker: 1 pads rows in one pass after the walks
     cudaStream_t stream = nullptr;
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*release_fn)(void *, void *) = nullptr;

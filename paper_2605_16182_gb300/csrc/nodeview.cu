@@ -142,9 +142,10 @@ __global__ void k_nv_build_nodes(const int32_t *__restrict__ run_node, const int
         x.g_lo = gb;
         x.g_hi = gb + gc;
         x.tb = 0;
-        x.pad = 0;
+        const Entry &last = E[run_pos[r + 1] - 1];
+        x.last_other = (c == 1 || E[run_pos[r + 1] - 2].ts != last.ts) ? last.other : -1;
         x.t_first = E[run_pos[r]].ts;
-        x.t_last = E[run_pos[r + 1] - 1].ts;
+        x.t_last = last.ts;
         ngr[v] = x;
         nbeg[v] = make_int2(eb, gb);
         ngo[gb + gc] = eb + c;
@@ -460,7 +461,12 @@ __global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t
             const int32_t v = run_node[r];
             if (ngr[v].g_lo == run_dg[r]) ngr[v].t_first = x.ts;  // no live group before the batch
         }
-        if (p + 1 == run_pos[r + 1]) ngr[run_node[r]].t_last = x.ts;
+        if (p + 1 == run_pos[r + 1]) {
+            // the node's last group: a single entry when this entry starts it
+            NodeRange &nr = ngr[run_node[r]];
+            nr.t_last = x.ts;
+            nr.last_other = fx[p + 1] != fx[p] ? x.other : -1;
+        }
         if (fx[p + 1] != fx[p]) {
             const int64_t g = (int64_t)run_dg[r] + (fx[p] - run_g[r]);
             if (g < 0 || g >= g_cap) {

@@ -14,10 +14,13 @@ using namespace tw;
 namespace {
 
 struct Cfg {
-    int sched, bkt_log, w_warp, mega, ctas;
+    int sched, bkt_log, w_warp, mega, ctas, pad_pass;
 };
 
-Cfg current(const tempest_t *h) { return Cfg{h->sched, h->bkt_log, h->coop_w_warp, h->coop_mega, h->stream_ctas}; }
+Cfg current(const tempest_t *h)
+{
+    return Cfg{h->sched, h->bkt_log, h->coop_w_warp, h->coop_mega, h->stream_ctas, h->pad_pass};
+}
 
 void apply(tempest_t *h, const Cfg &c)
 {
@@ -29,6 +32,7 @@ void apply(tempest_t *h, const Cfg &c)
     h->coop_w_warp = c.w_warp;
     h->coop_mega = c.mega;
     h->stream_ctas = c.ctas;
+    h->pad_pass = c.pad_pass;
 }
 
 struct Tuner {
@@ -64,6 +68,7 @@ struct Tuner {
             tr.coop_w_warp = c.w_warp;
             tr.coop_mega = c.mega;
             tr.stream_ctas = c.ctas;
+            tr.pad_pass = c.pad_pass;
             tr.ms = best;
         }
         return TEMPEST_OK;
@@ -77,7 +82,7 @@ struct Tuner {
             Cfg c = best;
             set(c, vals[i]);
             if (c.sched == best.sched && c.bkt_log == best.bkt_log && c.w_warp == best.w_warp &&
-                c.mega == best.mega && c.ctas == best.ctas)
+                c.mega == best.mega && c.ctas == best.ctas && c.pad_pass == best.pad_pass)
                 continue;
             double ms;
             int rc = time_cfg(c, ms);
@@ -122,6 +127,11 @@ int tempest_set_tuning(tempest_t *h, int knob, int64_t value)
                                                      (long long)value);
             h->stream_ctas = (int)value;
             return TEMPEST_OK;
+        case TEMPEST_TUNE_PAD_PASS:
+            if (value < 0 || value > 1) return fail(h, TEMPEST_EINVAL, "tuning: padding pass %lld is not 0 or 1",
+                                                    (long long)value);
+            h->pad_pass = (int)value;
+            return TEMPEST_OK;
         default:
             return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
@@ -135,6 +145,7 @@ int tempest_get_tuning(tempest_t *h, int knob, int64_t *value)
         case TEMPEST_TUNE_COOP_W_WARP: *value = h->coop_w_warp; return TEMPEST_OK;
         case TEMPEST_TUNE_COOP_MEGA: *value = h->coop_mega; return TEMPEST_OK;
         case TEMPEST_TUNE_STREAM_CTAS: *value = h->stream_ctas; return TEMPEST_OK;
+        case TEMPEST_TUNE_PAD_PASS: *value = h->pad_pass; return TEMPEST_OK;
         default: return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
 }
@@ -214,6 +225,10 @@ static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const i
         const int ctas[] = {2, 3, 4, 5};
         rc = T.sweep(best, best_ms, ctas, 4, [](Cfg &c, int v) { c.ctas = v; });
     }
+    if (!rc && best.sched == TEMPEST_SCHED_LANE && !T.rq.len_arr) {
+        const int pp[] = {0, 1};
+        rc = T.sweep(best, best_ms, pp, 2, [](Cfg &c, int v) { c.pad_pass = v; });
+    }
     if (!rc && best.sched == TEMPEST_SCHED_COOP) {
         const int ww[] = {1, 2, 4, 8, 16, 32};
         rc = T.sweep(best, best_ms, ww, 6, [](Cfg &c, int v) { c.w_warp = v; });
@@ -231,6 +246,7 @@ static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const i
         T.rep.coop_w_warp = best.w_warp;
         T.rep.coop_mega = best.mega;
         T.rep.stream_ctas = best.ctas;
+        T.rep.pad_pass = best.pad_pass;
         T.rep.best_ms = best_ms;
         T.rep.start_ms = start_ms;
         *out = T.rep;

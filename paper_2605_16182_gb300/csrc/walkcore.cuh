@@ -170,7 +170,7 @@ __device__ __forceinline__ uint32_t bkt_index(const BktMap &m, int64_t t)
 
 // The node record of v (two 16-byte loads of one sector).
 __device__ __forceinline__ void load_range(const NodeRange *r, int32_t &g_lo, int32_t &g_hi, int32_t &tb,
-                                           int64_t &t_first, int64_t &t_last)
+                                           int64_t &t_first, int64_t &t_last, int32_t *last_other = nullptr)
 {
     const int4 a = __ldg(reinterpret_cast<const int4 *>(r));
     const longlong2 b = __ldg(reinterpret_cast<const longlong2 *>(r) + 1);
@@ -179,6 +179,7 @@ __device__ __forceinline__ void load_range(const NodeRange *r, int32_t &g_lo, in
     tb = a.z;
     t_first = b.x;
     t_last = b.y;
+    if (last_other) *last_other = a.w;
 }
 
 // Live groups [g0, g1) of v (the first 8 bytes of its record).
@@ -333,6 +334,34 @@ __device__ __forceinline__ Entry draw_entry(const WalkView &V, const OUT &O, int
         idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
     }
     return V.ent[idx];
+}
+
+// draw_entry for a hop whose node record was read: a pick of the node's last
+// group (g1 - 1) when the record names that group's single entry
+// (last_other >= 0) needs no further loads, as that entry's far endpoint is
+// last_other and its time t_last (the draw inside a one-entry group is 0).
+template <class OUT>
+__device__ __forceinline__ Entry draw_entry_rec(const WalkView &V, const OUT &O, int64_t w, uint32_t hop, int bias,
+                                                int32_t c, int32_t g1, int32_t last_other, int64_t t_last)
+{
+    const Rand4 r = walk_rand(O.seed, (uint64_t)w, hop);
+    const uint64_t h1 = u53_bits(r.r0, r.r1);
+    bias = hop_bias(V, bias, O.cnt);
+    Entry x;
+    x.ts = t_last;
+    x.other = last_other;
+    x.slot = 0;
+    if (bias == BIAS_UNIFORM) {
+        if (c == g1 - 1 && last_other >= 0) return x;  // Gamma is that one entry
+        const int32_t e0 = __ldg(V.ngo + c), e1 = __ldg(V.ngo + g1);
+        return V.ent[e0 + uniform_index_k(h1, (int64_t)(e1 - e0))];
+    }
+    const int32_t k = bias == BIAS_EXP_WEIGHT
+                          ? weight_group(V, c, g1, h1)
+                          : c + (int32_t)sampler_index_k(h1, (int64_t)(g1 - c), start_bias(bias), V.rate_hop);
+    if (k == g1 - 1 && last_other >= 0) return x;
+    const int32_t e0 = __ldg(V.ngo + k), e1 = __ldg(V.ngo + k + 1);
+    return V.ent[e0 + uniform_index_k(u53_bits(r.r2, r.r3), (int64_t)(e1 - e0))];
 }
 
 // Backward hop at a node whose groups earlier than t are [g0, c), in the

@@ -767,7 +767,7 @@ struct DrawCtx {
     WalkCounters *cnt;
 };
 
-template <class P, int MINB, bool N2V, bool BACK>
+template <class P, int MINB, bool N2V, bool BACK, bool PAD>
 __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, const P Pv, unsigned long long *next_walk)
 {
     const int lane = threadIdx.x & 31;
@@ -864,9 +864,9 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
         } else if (mode == 2) {
             // one hop from v at search time t
             const uint32_t hop = (uint32_t)(len - 1);
-            int32_t g0, g1, tb;
+            int32_t g0, g1, tb, last_other;
             int64_t tlo, thi;
-            load_range(V.ngr + v, g0, g1, tb, tlo, thi);
+            load_range(V.ngr + v, g0, g1, tb, tlo, thi, &last_other);
             int32_t c = g0;
             if (g0 == g1) {
                 finish = true;
@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
                 } else if (BACK) {
                     e = draw_entry_back(V, D, (int64_t)wid, hop, bias, g0, c);
                 } else {
-                    e = draw_entry(V, D, (int64_t)wid, hop, bias, c, g1);
+                    e = draw_entry_rec(V, D, (int64_t)wid, hop, bias, c, g1, last_other, thi);
                 }
                 if (!ok) {
                     finish = true;  // every Node2Vec proposal rejected
@@ -906,9 +906,15 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
             }
         }
         // rows of the walks that ended here: the whole warp writes their
-        // padding, 32 consecutive cells per store
+        // padding, 32 consecutive cells per streaming store (PAD; else one
+        // pass after the launch pads every row)
         unsigned fin = __ballot_sync(0xffffffffu, finish);
-        if (fin) {
+        if (!PAD) {
+            if (finish) {
+                Pv.finish(cx, len);
+                mode = 0;
+            }
+        } else if (fin) {  // every lane of the warp takes part in the padding loop
             unsigned long long my_n = 0, my_t = 0;
             int32_t my_len = 0, my_cap = 0;
             if (finish) {
@@ -982,15 +988,15 @@ static void launch_stream_dir(tempest_t *h, const WalkView &V, const P &Pv, unsi
     else k_walks_stream<P, 4, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
 }
 
-template <class P, bool BACK>
-static void launch_lane_dir(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
+template <class P, bool BACK, bool PAD>
+static void launch_lane_pad(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
                             cudaStream_t st, bool n2v)
 {
     static int occ = 0, occ5 = 0, occn = 0;
     if (occ == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walks_lane<P, 4, false, BACK>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_lane<P, 5, false, BACK>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_lane<P, 3, true, BACK>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walks_lane<P, 4, false, BACK, PAD>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_lane<P, 5, false, BACK, PAD>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_lane<P, 3, true, BACK, PAD>, 256, 0);
         if (occ < 1) occ = 1;
         if (occ5 < 1) occ5 = 1;
         if (occn < 1) occn = 1;
@@ -1001,20 +1007,28 @@ static void launch_lane_dir(tempest_t *h, const WalkView &V, const P &Pv, unsign
     int64_t grid = (int64_t)h->num_sms * bps;
     const int64_t need = (total + 255) / 256;
     if (grid > need) grid = need;
-    if (n2v) k_walks_lane<P, 3, true, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
-    else if (wide) k_walks_lane<P, 5, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
-    else k_walks_lane<P, 4, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    if (n2v) k_walks_lane<P, 3, true, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else if (wide) k_walks_lane<P, 5, false, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else k_walks_lane<P, 4, false, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+}
+
+template <class P, bool BACK>
+static void launch_lane_dir(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
+                            cudaStream_t st, bool n2v, bool pad)
+{
+    if (pad) launch_lane_pad<P, BACK, true>(h, V, Pv, next, total, st, n2v);
+    else launch_lane_pad<P, BACK, false>(h, V, Pv, next, total, st, n2v);
 }
 
 // The persistent walker of the handle's form (the lane walker for
 // TEMPEST_SCHED_LANE, else the streaming walker).
 template <class P>
 static void launch_stream(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
-                          cudaStream_t st, bool n2v)
+                          cudaStream_t st, bool n2v, bool pad = true)
 {
     if (h->sched == TEMPEST_SCHED_LANE) {
-        if (V.back) launch_lane_dir<P, true>(h, V, Pv, next, total, st, n2v);
-        else launch_lane_dir<P, false>(h, V, Pv, next, total, st, n2v);
+        if (V.back) launch_lane_dir<P, true>(h, V, Pv, next, total, st, n2v, pad);
+        else launch_lane_dir<P, false>(h, V, Pv, next, total, st, n2v, pad);
         return;
     }
     if (V.back) launch_stream_dir<P, true>(h, V, Pv, next, total, st, n2v);
@@ -1181,9 +1195,18 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
             kernel_mark(h, 0);
             const bool n2v = (rq.bias_arr ? rq.may_n2v != 0 : rq.bias == TEMPEST_BIAS_NODE2VEC) &&
                              (V.n2v_inv_p != 1.0 || V.n2v_inv_q != 1.0);
-            launch_stream(h, V, OneReq{O}, &O.cnt->pad, rq.n_walks, st, n2v);
+            // the lane walker pads rows as walks end, or leaves it to one pass
+            const bool sep = h->sched == TEMPEST_SCHED_LANE && h->pad_pass;
+            launch_stream(h, V, OneReq{O}, &O.cnt->pad, rq.n_walks, st, n2v, !sep);
+            if (sep) {
+                int64_t pgrid = (rq.n_walks + 7) / 8;
+                const int64_t pcap = (int64_t)h->num_sms * 16;
+                if (pgrid > pcap) pgrid = pcap;
+                k_pad_rows<<<(unsigned)pgrid, 256, 0, st>>>(rq.n_walks, rq.cap, rq.len, rq.node, rq.ts);
+                launches++;
+            }
             kernel_mark(h, 1);
-            launches += 1;  // the walker pads its rows itself
+            launches += 1;
         }
     }
     h->last_ws.n_walks = rq.n_walks;

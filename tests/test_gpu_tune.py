@@ -27,12 +27,12 @@ def _walks(eng, bias, seed=9):
 def test_knobs_validate_and_round_trip():
     eng = _engine()
     for knob, bad in ((_lib.TUNE_BKT_LOG, 6), (_lib.TUNE_COOP_W_WARP, 0), (_lib.TUNE_COOP_MEGA, 100),
-                      (_lib.TUNE_STREAM_CTAS, -1), (17, 0)):
+                      (_lib.TUNE_STREAM_CTAS, -1), (_lib.TUNE_PAD_PASS, 2), (17, 0)):
         with pytest.raises(_lib.TempestError) as e:
             eng.set_tuning(knob, bad)
         assert e.value.code == _lib.TEMPEST_EINVAL
     for knob, val in ((_lib.TUNE_BKT_LOG, 4), (_lib.TUNE_COOP_W_WARP, 16), (_lib.TUNE_COOP_MEGA, 2048),
-                      (_lib.TUNE_STREAM_CTAS, 2)):
+                      (_lib.TUNE_STREAM_CTAS, 2), (_lib.TUNE_PAD_PASS, 1)):
         eng.set_tuning(knob, val)
         assert eng.get_tuning(knob) == val
 
@@ -45,7 +45,7 @@ def test_every_knob_setting_gives_the_same_walks(sched):
     eng.set_scheduler(sched)
     for knob, val in ((_lib.TUNE_BKT_LOG, 0), (_lib.TUNE_BKT_LOG, 5), (_lib.TUNE_COOP_W_WARP, 1),
                       (_lib.TUNE_COOP_W_WARP, 64), (_lib.TUNE_COOP_MEGA, 256), (_lib.TUNE_STREAM_CTAS, 1),
-                      (_lib.TUNE_STREAM_CTAS, 5)):
+                      (_lib.TUNE_STREAM_CTAS, 5), (_lib.TUNE_PAD_PASS, 1), (_lib.TUNE_PAD_PASS, 0)):
         eng.set_tuning(knob, val)
         for b in (0, 2):
             got = eng.walks(20000, 30, bias=b, seed=9)
