@@ -303,6 +303,20 @@ int ts_export(tempest_t *h, int32_t *out)
     return cuda_check(h, cudaGetLastError(), "export");
 }
 
+// Store capacity a count window settles at (the live edges never exceed the
+// window by more than a tie group, so this is the size the store grows to):
+// allocating it once the live edges reach 1/16 of the window spares the
+// steady state the reallocation of a buffer, which synchronises the device
+// and stalls a batch.  Duration windows, unbounded stores and windows far
+// above the content grow with their content instead (0).
+static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
+{
+    if (h->window >= 0) return 0;
+    const int64_t W = -h->window;
+    if (W > 16 * (m_new + nbk)) return 0;
+    return 2 * W + W / 2 + nbk + 1024;
+}
+
 int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in, int64_t n,
                  tempest_ingest_stats *stats)
 {
@@ -421,7 +435,8 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
         if (h->s_hi + nbk > h->s_cap) {
             // move the kept range to the front of the other buffer
             const int nxt = h->cur ^ 1;
-            const int64_t cap = std::max<int64_t>(h->s_cap, 2 * m_new + m_new / 2 + nbk + 1024);
+            const int64_t cap = std::max<int64_t>(std::max<int64_t>(h->s_cap, 2 * m_new + m_new / 2 + nbk + 1024),
+                                                  steady_store_cap(h, m_new, nbk));
             if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
             if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
             if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap, true))) return rc;
@@ -455,7 +470,8 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
         h->s_hi += nbk;
     } else {
         const int nxt = h->cur ^ 1;
-        const int64_t cap = std::max<int64_t>(h->s_cap, 2 * m_new + 1024);
+        const int64_t cap =
+            std::max<int64_t>(std::max<int64_t>(h->s_cap, 2 * m_new + 1024), steady_store_cap(h, m_new, nbk));
         if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
         if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
         if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap))) return rc;
@@ -489,7 +505,8 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     if (!ts_full && (int64_t)(h->tg.bytes / sizeof(int32_t)) < h->tg_hi + nbk + 2) {
         // move the live starts [tg_lo, tg_hi] to the front of a larger buffer
         const int64_t live = h->tg_hi - h->tg_lo + 1;
-        if ((rc = ensure(h, h->tg2, sizeof(int32_t) * (size_t)(2 * (live + nbk) + 1024), true))) return rc;
+        const int64_t tcap = std::max<int64_t>(2 * (live + nbk) + 1024, steady_store_cap(h, m_new, nbk));
+        if ((rc = ensure(h, h->tg2, sizeof(int32_t) * (size_t)tcap, true))) return rc;
         cudaMemcpyAsync(h->tg2.p, h->tg.as<int32_t>() + h->tg_lo, sizeof(int32_t) * (size_t)live,
                         cudaMemcpyDeviceToDevice, st);
         std::swap(h->tg, h->tg2);
