@@ -12,8 +12,10 @@
 // state, at the first walk call after an ingest:
 //   1. a compaction over the nodes that own index regions lists the big
 //      nodes and places their tables back to back (prefix of K + 1);
-//   2. a scan over that list numbers their fill chunks (BKT_CHUNK groups);
-//   3. one warp per chunk reads the chunk's group timestamps (coalesced);
+//   2. a scan over that list numbers their fill chunks (BKT_CHUNK groups),
+//      and a map gives every chunk its big node;
+//   3. one warp per chunk reads the chunk's group timestamps, each lane 32
+//      consecutive groups in order (one cached load per group);
 //      group g owns the table entries k in (bucket(g - 1), bucket(g)] (it is
 //      the first group of those buckets) and the node's last group also
 //      owns (bucket(g), K] (value g1).  A group's lane writes its own few
@@ -28,7 +30,6 @@ namespace tw {
 
 namespace {
 
-constexpr int BKT_UNROLL = 4;     // 32-group steps whose loads are issued together
 constexpr int BKT_SHORT_RUN = 4;  // table entries a group's own lane writes
 
 struct BigNodeOp {
@@ -66,27 +67,43 @@ struct ChunkOp {
     __device__ __forceinline__ void emit(int64_t b, uint64_t, uint64_t ex) const { big_c[b] = (int32_t)ex; }
 };
 
-// One warp per chunk (grid-stride); totals of the compaction in tot.
+// The big node owning each fill chunk (one warp per big node writes its
+// chunk range): the fill then finds a chunk's node with one load.
+__global__ void __launch_bounds__(256) k_bkt_owner(const int32_t *__restrict__ big_c, int64_t nb,
+                                                   const uint64_t *__restrict__ tot, int64_t cap_ch,
+                                                   int32_t *owner, WalkCounters *chk)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nch = (int64_t)*tot;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += warps) {
+        const int64_t c0 = __ldg(big_c + b), c1 = b + 1 < nb ? __ldg(big_c + b + 1) : nch;
+        if (c1 > cap_ch || c0 > c1) {  // inconsistent lists
+            if (lane == 0) atomicOr(&chk->status, 1ull << 13);
+            continue;
+        }
+        for (int64_t c = c0 + lane; c < c1; c += 32) owner[c] = (int32_t)b;
+    }
+}
+
+// One warp per chunk of BKT_CHUNK groups (grid-stride); lane i takes the
+// chunk's groups [32 i, 32 i + 32) in order, so a group costs one cached load
+// and a few instructions; totals of the compaction in tot.
 __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ big_node,
                                                   const int32_t *__restrict__ big_t,
-                                                  const int32_t *__restrict__ big_c, int64_t nb,
+                                                  const int32_t *__restrict__ big_c,
+                                                  const int32_t *__restrict__ owner,
                                                   const uint64_t *__restrict__ tot,
                                                   const NodeRange *__restrict__ ngr,
                                                   const int64_t *__restrict__ ngts, int log_b, int64_t cap,
                                                   int32_t *bkt, WalkCounters *chk)
 {
+    static_assert(BKT_CHUNK == 32 * 32, "a chunk is 32 groups per lane");
     const int lane = threadIdx.x & 31;
     const int64_t nch = (int64_t)*tot;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += warps) {
-        // owning big node: last b with big_c[b] <= c
-        int64_t lo = 0, hi = nb - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (__ldg(big_c + mid) <= c) lo = mid;
-            else hi = mid - 1;
-        }
-        const int64_t b = lo;
+        const int64_t b = __ldg(owner + c);
         const int32_t node = __ldg(big_node + b);
         const int32_t g0 = ngr[node].g_lo, g1 = ngr[node].g_hi;
         const uint32_t K = bkt_count(g1 - g0, log_b);
@@ -98,32 +115,39 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
         const BktMap bm = bkt_map(__ldg(ngts + g0), __ldg(ngts + g1 - 1), K);
         const int32_t start = g0 + (int32_t)(c - __ldg(big_c + b)) * BKT_CHUNK;
         const int32_t end = min(g1, start + BKT_CHUNK);
-        // bucket of the group before the chunk (-1 at the node's first group)
-        int32_t k_prev = start == g0 ? -1 : (int32_t)bkt_index(bm, __ldg(ngts + start - 1));
-        for (int32_t base = start; base < end; base += 32 * BKT_UNROLL) {
-            // BKT_UNROLL coalesced loads in flight, then the groups in order
-            int64_t tv[BKT_UNROLL];
+        const int32_t my0 = start + 32 * lane, my1 = min(end, my0 + 32);
+        // bucket of the group before this lane's first (-1 at the node's first group)
+        int32_t kp = (my0 == g0 || my0 >= end) ? -1 : (int32_t)bkt_index(bm, __ldg(ngts + my0 - 1));
+        // timestamps come in 8 at a time (four 16-byte loads in flight when
+        // the lane's groups start 16-byte aligned, else element loads)
+        const bool vec = (((uintptr_t)(ngts + my0)) & 15) == 0;
+        for (int jb = 0; jb < 32; jb += 8) {
+            int64_t tv[8];
+            const int32_t gb = my0 + jb;
+            if (vec && gb + 8 <= my1) {
+                const longlong2 *q = reinterpret_cast<const longlong2 *>(ngts + gb);
 #pragma unroll
-            for (int q = 0; q < BKT_UNROLL; q++) {
-                const int32_t g = base + 32 * q + lane;
-                tv[q] = g < end ? __ldg(ngts + g) : 0;
+                for (int x = 0; x < 4; x++) {
+                    const longlong2 v2 = __ldg(q + x);
+                    tv[2 * x] = v2.x;
+                    tv[2 * x + 1] = v2.y;
+                }
+            } else {
+#pragma unroll
+                for (int x = 0; x < 8; x++) tv[x] = gb + x < my1 ? __ldg(ngts + gb + x) : 0;
             }
 #pragma unroll
-            for (int q = 0; q < BKT_UNROLL; q++) {
-                const int32_t g = base + 32 * q + lane;
-                if (base + 32 * q >= end) break;  // warp-uniform
-                const bool valid = g < end;
-                const int32_t k = valid ? (int32_t)bkt_index(bm, tv[q]) : (int32_t)K;
-                int32_t kp = __shfl_up_sync(0xffffffffu, k, 1);
-                if (lane == 0) kp = k_prev;
-                k_prev = __shfl_sync(0xffffffffu, k, 31);
+            for (int x = 0; x < 8; x++) {
+                const int32_t g = gb + x;
+                const bool valid = g < my1;
+                const int32_t k = valid ? (int32_t)bkt_index(bm, tv[x]) : kp;
                 // entries (kp, k] hold g; the last group adds (k, K] holding g1
                 const bool last = valid && g == g1 - 1;
                 const int32_t lo_k = kp + 1;
                 const int32_t cnt = valid ? (last ? (int32_t)K : k) - kp : 0;
                 // a short run (the common case: about one bucket per group) is
-                // written by its own lane; long runs (time gaps that leave
-                // many buckets empty) by the whole warp, 32 entries per store
+                // written by its own lane; long runs (time gaps that leave many
+                // buckets empty) by the whole warp, 32 entries per store
                 if (cnt <= BKT_SHORT_RUN) {
                     for (int32_t e = 0; e < cnt; e++) {
                         const int32_t kk = lo_k + e;
@@ -143,6 +167,7 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
                         bkt[tb + kk] = kk <= r_k ? r_g : g1;
                     }
                 }
+                kp = k;
             }
         }
     }
@@ -219,13 +244,18 @@ int prepare_walk_index(tempest_t *h)
             // every walk call zeroes before its kernels: read it here
             cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);
             const int64_t nch_max = Gn / BKT_CHUNK + nb;  // chunks <= sum(G / CHUNK + 1)
-            int64_t grid = (nch_max + 7) / 8;
+            if ((rc = ensure(h, h->big_own, sizeof(int32_t) * (size_t)nch_max, true))) return rc;
             const int64_t gcap = (int64_t)h->num_sms * 16;
+            int64_t ogrid = (nb + 7) / 8;
+            if (ogrid > gcap) ogrid = gcap;
+            k_bkt_owner<<<(unsigned)ogrid, 256, 0, st>>>(h->big_c.as<int32_t>(), nb, part + nblk2, nch_max,
+                                                         h->big_own.as<int32_t>(), h->wcnt.as<WalkCounters>());
+            int64_t grid = (nch_max + 7) / 8;
             if (grid > gcap) grid = gcap;
             k_bkt_fill<<<(unsigned)grid, 256, 0, st>>>(h->big_node.as<int32_t>(), h->big_t.as<int32_t>(),
-                                                       h->big_c.as<int32_t>(), nb, part + nblk2, ngr,
-                                                       h->ngts.as<int64_t>(), h->bkt_log, cap, h->bkt.as<int32_t>(),
-                                                       h->wcnt.as<WalkCounters>());
+                                                       h->big_c.as<int32_t>(), h->big_own.as<int32_t>(),
+                                                       part + nblk2, ngr, h->ngts.as<int64_t>(), h->bkt_log, cap,
+                                                       h->bkt.as<int32_t>(), h->wcnt.as<WalkCounters>());
             WalkCounters *hc = static_cast<WalkCounters *>(h->hstat);
             cudaMemcpyAsync(hc, h->wcnt.p, sizeof(WalkCounters), cudaMemcpyDeviceToHost, st);
             if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket fill"))) return rc;

@@ -115,7 +115,7 @@ static void free_all(tempest_t *h)
                     &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt,
                     &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched,   &h->tg2,       &h->nbeg,
                     &h->pn_nodes,  &h->gw,        &h->gs,        &h->wref,      &h->w_cbase,   &h->w_ctot,
-                    &h->w_coff,    &h->co_prev,   &h->pt};
+                    &h->w_coff,    &h->co_prev,   &h->pt,        &h->big_own};
     for (DBuf *b : bufs) release(h, *b);
 }
 

@@ -165,7 +165,7 @@ struct tempest {
     // state version): per node its table base, the tables, the big-segment
     // list and its chunk prefix
     tw::DBuf bkt;        // int32 tables (each big node's base is in its NodeRange)
-    tw::DBuf big_node, big_t, big_c;
+    tw::DBuf big_node, big_t, big_c, big_own;
     int64_t bkt_ver = -1;
     // active nodes in id order, for PER_NODE starts (built lazily per state)
     tw::DBuf pn_nodes;
