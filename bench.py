@@ -192,7 +192,7 @@ def run_ours(args, rank, world):
     node = torch.empty((n_walks, L), dtype=torch.int32, device=dev)
     tso = torch.empty((n_walks, L), dtype=torch.int64, device=dev)
     ln = torch.empty((n_walks,), dtype=torch.int32, device=dev)
-    seed_base = 1_000_003 * rank
+    seed_base = rank_seed(rank)
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
@@ -618,6 +618,27 @@ def barrier(world):
         dist.barrier()
 
 
+def rank_seed(rank):
+    """Seed base of a replica: every rank draws its own walks (weak scaling,
+    no data-path collective; replicas hold the whole window)."""
+    return 1_000_003 * rank
+
+
+def aggregate_ranks(hops, edges, walk_s, ingest_s, total_ms, world, device="cuda"):
+    """Whole-job figures over the replicas: summed units, the slowest rank's
+    times (the contract's max over ranks)."""
+    if world <= 1:
+        return hops, edges, walk_s, ingest_s, total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([hops, edges], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    m = torch.tensor([walk_s, ingest_s, total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    walk_s, ingest_s, total_ms = (float(x) for x in m.tolist())
+    return int(t[0].item()), int(t[1].item()), walk_s, ingest_s, total_ms
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -641,16 +662,8 @@ def main():
     res = run_ours(args, rank, world)
 
     # aggregate over ranks: total hops / max time
-    hops, walk_s, ingest_s, edges, total_ms = res["hops"], res["walk_s"], res["ingest_s"], res["edges"], res["total_ms"]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([hops, edges], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t)
-        m = torch.tensor([walk_s, ingest_s, total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        hops, edges = int(t[0].item()), int(t[1].item())
-        walk_s, ingest_s, total_ms = (float(x) for x in m.tolist())
+    hops, edges, walk_s, ingest_s, total_ms = aggregate_ranks(res["hops"], res["edges"], res["walk_s"],
+                                                               res["ingest_s"], res["total_ms"], world)
     if rank != 0:
         return
     peak, peak_kind = measured_peaks()
