@@ -2,26 +2,38 @@
 // nodes: an index for the first step of every hop, finding the start of
 // Gamma_t(v) among v's timestamp groups (Sec. 2.3, 2.5).
 //
-// A node with G >= BKT_MIN_G groups gets K = G >> bkt_log buckets over its
-// timestamp range and a table of K + 1 group indices (see bkt_map).  A hop at
-// such a node reads the node's first and last group timestamps, one pair of
+// A node with G >= BKT_MIN_G groups gets buckets of 2^s time units aligned on
+// absolute time (about G >> bkt_log of them over its live range) and a table
+// holding, per bucket, the first group whose bucket is at or after it (see
+// bkt_rel).  A hop at such a node reads the node's record, one pair of
 // adjacent table entries and then bisects the few groups of one bucket,
 // instead of bisecting all G groups with one dependent load per level.
 //
 // The tables depend only on the node view, so they are built once per index
-// state, at the first walk call after an ingest:
+// state, at the first walk call after an ingest, and each build starts from
+// the previous one: with buckets on absolute time and groups only appended
+// at a node's end or evicted at its front (node-view moves shift a node's
+// group indices by one offset, tracked through the groups it has lost), a
+// bucket the previous table covers keeps its entry up to that shift, so only
+// the buckets of groups appended since are filled from the groups (a node
+// whose width drifts more than 4x from its target, or any node after the
+// node view was rebuilt, is filled whole):
 //   1. a compaction over the nodes that own index regions lists the big
-//      nodes and places their tables back to back (prefix of K + 1);
-//   2. a scan over that list numbers their fill chunks (BKT_CHUNK groups),
-//      and a map gives every chunk its big node;
-//   3. one warp per chunk reads the chunk's group timestamps, each lane 32
-//      consecutive groups in order (one cached load per group);
-//      group g owns the table entries k in (bucket(g - 1), bucket(g)] (it is
-//      the first group of those buckets) and the node's last group also
-//      owns (bucket(g), K] (value g1).  A group's lane writes its own few
-//      entries; a long run (a time gap that leaves many buckets empty) is
-//      written by the whole warp, 32 entries per store instruction rather
-//      than by one lane.  Every entry is written once.
+//      nodes, plans each table (width, buckets to copy, groups to scan) and
+//      places the tables back to back, each after a small header the next
+//      build reads;
+//   2. a scan over that list numbers their tasks (copy tasks of BKT_COPY
+//      entries, group chunks of BKT_CHUNK groups), and a map gives every task
+//      its big node;
+//   3. one warp per task copies entries, or reads a chunk's group
+//      timestamps, each lane 32 consecutive groups in order: group g owns
+//      the entries k in (bucket(g - 1), bucket(g)] (it is the first group of
+//      those buckets) and the node's last group also (bucket(g), K] (value
+//      g1).  A group's lane writes its own few entries; a long run (a time
+//      gap that leaves many buckets empty) is written by the whole warp, 32
+//      entries per store.  Every entry is written once.
+#include <algorithm>
+
 #include "engine.cuh"
 #include "prims.cuh"
 #include "walkcore.cuh"
@@ -30,39 +42,124 @@ namespace tw {
 
 namespace {
 
-constexpr int BKT_SHORT_RUN = 4;  // table entries a group's own lane writes
+constexpr int BKT_SHORT_RUN = 4;     // table entries a group's own lane writes
+constexpr int32_t BKT_COPY = 8192;   // table entries per copy task
+
+// How a big node's table is built: the bucket width, and which part comes
+// from the previous build's table of the node (the buckets both tables cover,
+// entries shifted by the node's group renumbering delta) and which part from
+// the node's groups (those appended since: from .. g_hi).
+struct BktPlan {
+    int s;            // log2 of the bucket width
+    int64_t bfirst;   // absolute bucket of the node's first live group
+    int32_t K;        // buckets
+    int32_t ncopy;    // buckets [0, ncopy) copied
+    int32_t src;      // previous table's entry for bucket 0, when ncopy > 0
+    int32_t delta;    // group index now minus group index then
+    int32_t from;     // first group whose buckets are filled from the groups
+    int32_t gbase;    // g_lo - groups evicted so far: the group numbering's origin
+};
+
+struct BuildCtx {
+    const int32_t *prev;  // previous build's tables (null: none usable)
+    int prev_gen;         // their generation
+    int log_b;
+    const int32_t *nev;
+};
+
+// Header of a node's table (BKT_HDR int32 before its entries), read by the
+// next build: node, generation, width, g_hi and group origin at build time,
+// first bucket (two words), buckets.
+__device__ __forceinline__ BktPlan bkt_plan(int32_t v, const NodeRange &r, const BuildCtx &bc)
+{
+    BktPlan p;
+    const int32_t G = r.g_hi - r.g_lo;
+    const uint64_t span = (uint64_t)r.t_last - (uint64_t)r.t_first;  // >= 1: distinct group timestamps
+    const uint64_t kt = (uint64_t)max(1, G >> bc.log_b);
+    const uint64_t q = span / kt;
+    const int s_fresh = q == 0 ? 0 : 64 - __clzll((long long)q);  // span >> s < kt
+    p.gbase = r.g_lo - __ldg(bc.nev + v);
+    p.ncopy = 0;
+    p.src = -1;
+    p.delta = 0;
+    p.from = r.g_lo;
+    p.s = s_fresh;
+    bool reuse = false;
+    int64_t old_bfirst = 0;
+    int32_t old_K = 0, old_ghi = 0;
+    if (bc.prev && (r.bs >> 6) == (bc.prev_gen & 0x3ffffff) && r.tb >= BKT_HDR) {
+        const int32_t *hd = bc.prev + r.tb - BKT_HDR;
+        const int old_s = hd[2];
+        if (hd[0] == v && hd[1] == bc.prev_gen && old_s >= s_fresh - 2 && old_s <= s_fresh + 2) {
+            reuse = true;
+            p.s = old_s;
+            old_ghi = hd[3];
+            p.delta = p.gbase - hd[4];
+            old_bfirst = (int64_t)(((uint64_t)(uint32_t)hd[6] << 32) | (uint32_t)hd[5]);
+            old_K = hd[7];
+        }
+    }
+    p.bfirst = r.t_first >> p.s;
+    p.K = (int32_t)((r.t_last >> p.s) - p.bfirst + 1);
+    if (reuse) {
+        // the live groups' first bucket only moves forward (eviction); the
+        // buckets up to the old last one keep their first group
+        const int64_t old_blast = old_bfirst + old_K - 1;
+        const int64_t nc = min(old_blast, p.bfirst + p.K - 1) - p.bfirst + 1;
+        if (p.bfirst >= old_bfirst && nc > 0) {
+            p.ncopy = (int32_t)nc;
+            p.src = r.tb + (int32_t)(p.bfirst - old_bfirst);
+        }
+        p.from = max(r.g_lo, old_ghi + p.delta);
+        if (p.ncopy == 0) p.from = r.g_lo;
+    }
+    return p;
+}
 
 struct BigNodeOp {
     const int32_t *act;
     NodeRange *ngr;
-    int log_b;
+    BuildCtx bc;
+    int gen;
     int32_t *big_node, *big_t;
+    int4 *aux0, *aux1;
+    int64_t *bf;
     __device__ __forceinline__ uint64_t value(int64_t j) const
     {
-        const NodeRange &r = ngr[act[j]];
-        const int32_t G = r.g_hi - r.g_lo;
-        if (G < BKT_MIN_G) return 0;
-        return (1ull << 32) | (uint64_t)(bkt_count(G, log_b) + 1u);
+        const int32_t v = act[j];
+        const NodeRange r = ngr[v];
+        if (r.g_hi - r.g_lo < BKT_MIN_G) return 0;
+        const BktPlan p = bkt_plan(v, r, bc);
+        return (1ull << 32) | (uint64_t)(BKT_HDR + p.K + 1);
     }
-    __device__ __forceinline__ void emit(int64_t j, uint64_t v, uint64_t ex) const
+    __device__ __forceinline__ void emit(int64_t j, uint64_t x, uint64_t ex) const
     {
-        if (!v) return;
+        if (!x) return;
         const uint32_t b = (uint32_t)(ex >> 32);
-        const int32_t node = act[j];
-        big_node[b] = node;
-        big_t[b] = (int32_t)(uint32_t)ex;
-        ngr[node].tb = (int32_t)(uint32_t)ex;
+        const int32_t v = act[j];
+        const NodeRange r = ngr[v];
+        const BktPlan p = bkt_plan(v, r, bc);
+        const int32_t base = (int32_t)(uint32_t)ex;
+        big_node[b] = v;
+        big_t[b] = base;
+        aux0[b] = make_int4(p.s, p.from, p.ncopy, p.src);
+        aux1[b] = make_int4(p.delta, p.K, (p.ncopy + BKT_COPY - 1) / BKT_COPY, p.gbase);
+        bf[b] = p.bfirst;
+        ngr[v].tb = base + BKT_HDR;
+        ngr[v].bs = ((gen & 0x3ffffff) << 6) | p.s;
     }
 };
 
 struct ChunkOp {
     const int32_t *big_node;
     const NodeRange *ngr;
+    const int4 *aux0, *aux1;
     int32_t *big_c;
     __device__ __forceinline__ uint64_t value(int64_t b) const
     {
-        const NodeRange &r = ngr[big_node[b]];
-        return (uint64_t)((r.g_hi - r.g_lo + BKT_CHUNK - 1) / BKT_CHUNK);
+        const int4 a0 = aux0[b], a1 = aux1[b];
+        const int32_t g_hi = ngr[big_node[b]].g_hi;
+        return (uint64_t)a1.z + (uint64_t)((g_hi - a0.y + BKT_CHUNK - 1) / BKT_CHUNK);
     }
     __device__ __forceinline__ void emit(int64_t b, uint64_t, uint64_t ex) const { big_c[b] = (int32_t)ex; }
 };
@@ -86,17 +183,22 @@ __global__ void __launch_bounds__(256) k_bkt_owner(const int32_t *__restrict__ b
     }
 }
 
-// One warp per chunk of BKT_CHUNK groups (grid-stride); lane i takes the
-// chunk's groups [32 i, 32 i + 32) in order, so a group costs one cached load
-// and a few instructions; totals of the compaction in tot.
+// One warp per task (grid-stride).  A node's first tasks copy the buckets its
+// previous table already covers (entry + the node's renumbering delta, the
+// first clamped to the live groups); the rest fill the buckets of its groups
+// from `from` on: lane i takes 32 consecutive groups of a BKT_CHUNK chunk in
+// order, and group g writes the entries (bucket(g - 1), bucket(g)] at or
+// above the first uncopied bucket (the last group also (bucket(g), K], value
+// g_hi).  A node's first task writes its header and its entry K.
 __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ big_node,
                                                   const int32_t *__restrict__ big_t,
                                                   const int32_t *__restrict__ big_c,
                                                   const int32_t *__restrict__ owner,
-                                                  const uint64_t *__restrict__ tot,
+                                                  const int4 *__restrict__ aux0, const int4 *__restrict__ aux1,
+                                                  const int64_t *__restrict__ bfs, const uint64_t *__restrict__ tot,
                                                   const NodeRange *__restrict__ ngr,
-                                                  const int64_t *__restrict__ ngts, int log_b, int64_t cap,
-                                                  int32_t *bkt, WalkCounters *chk)
+                                                  const int64_t *__restrict__ ngts, const int32_t *__restrict__ prev,
+                                                  int gen, int64_t cap, int32_t *bkt, WalkCounters *chk)
 {
     static_assert(BKT_CHUNK == 32 * 32, "a chunk is 32 groups per lane");
     const int lane = threadIdx.x & 31;
@@ -106,18 +208,37 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
         const int64_t b = __ldg(owner + c);
         const int32_t node = __ldg(big_node + b);
         const int32_t g0 = ngr[node].g_lo, g1 = ngr[node].g_hi;
-        const uint32_t K = bkt_count(g1 - g0, log_b);
-        const int64_t tb = __ldg(big_t + b);
-        if (tb + K >= cap || g1 - g0 < BKT_MIN_G) {  // inconsistent lists
-            if (lane == 0) atomicOr(&chk->status, 1ull << 12);
+        const int4 a0 = __ldg(aux0 + b), a1 = __ldg(aux1 + b);
+        const int s = a0.x, from = a0.y, ncopy = a0.z, src = a0.w;
+        const int32_t delta = a1.x, K = a1.y, copy_tasks = a1.z;
+        const int64_t bfirst = __ldg(bfs + b);
+        const int64_t hb = __ldg(big_t + b);  // header
+        const int64_t tb = hb + BKT_HDR;       // entry 0
+        const int32_t local = (int32_t)(c - __ldg(big_c + b));
+        if (tb + K >= cap || g1 - g0 < BKT_MIN_G || K < 1 || ncopy > K || (ncopy > 0 && !prev)) {
+            if (lane == 0) atomicOr(&chk->status, 1ull << 12);  // inconsistent lists
             continue;
         }
-        const BktMap bm = bkt_map(__ldg(ngts + g0), __ldg(ngts + g1 - 1), K);
-        const int32_t start = g0 + (int32_t)(c - __ldg(big_c + b)) * BKT_CHUNK;
+        if (local == 0 && lane < BKT_HDR + 1) {
+            // header (for the next build) and the end entry
+            const int32_t hv[BKT_HDR] = {node, gen, s, g1, a1.w, (int32_t)(uint32_t)bfirst,
+                                         (int32_t)(uint32_t)((uint64_t)bfirst >> 32), K};
+            if (lane < BKT_HDR) bkt[hb + lane] = hv[lane];
+            else bkt[tb + K] = g1;
+        }
+        if (local < copy_tasks) {
+            const int32_t e0 = local * BKT_COPY, e1 = min(ncopy, e0 + BKT_COPY);
+            for (int32_t e = e0 + lane; e < e1; e += 32) {
+                const int32_t x = __ldg(prev + src + e) + delta;
+                bkt[tb + e] = min(max(x, g0), g1);
+            }
+            continue;
+        }
+        const int32_t start = from + (local - copy_tasks) * BKT_CHUNK;
         const int32_t end = min(g1, start + BKT_CHUNK);
         const int32_t my0 = start + 32 * lane, my1 = min(end, my0 + 32);
         // bucket of the group before this lane's first (-1 at the node's first group)
-        int32_t kp = (my0 == g0 || my0 >= end) ? -1 : (int32_t)bkt_index(bm, __ldg(ngts + my0 - 1));
+        int32_t kp = (my0 == g0 || my0 >= end) ? -1 : (int32_t)((__ldg(ngts + my0 - 1) >> s) - bfirst);
         // timestamps come in 8 at a time (four 16-byte loads in flight when
         // the lane's groups start 16-byte aligned, else element loads)
         const bool vec = (((uintptr_t)(ngts + my0)) & 15) == 0;
@@ -140,11 +261,13 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
             for (int x = 0; x < 8; x++) {
                 const int32_t g = gb + x;
                 const bool valid = g < my1;
-                const int32_t k = valid ? (int32_t)bkt_index(bm, tv[x]) : kp;
-                // entries (kp, k] hold g; the last group adds (k, K] holding g1
+                const int32_t k = valid ? (int32_t)((tv[x] >> s) - bfirst) : kp;
+                // entries (kp, k] hold g; the last group adds (k, K] holding
+                // g1; entries below ncopy came from the previous table
                 const bool last = valid && g == g1 - 1;
-                const int32_t lo_k = kp + 1;
-                const int32_t cnt = valid ? (last ? (int32_t)K : k) - kp : 0;
+                const int32_t lo_k = max(kp + 1, ncopy);
+                const int32_t hi_k = last ? K : k;
+                const int32_t cnt = valid && hi_k >= lo_k ? hi_k - lo_k + 1 : 0;
                 // a short run (the common case: about one bucket per group) is
                 // written by its own lane; long runs (time gaps that leave many
                 // buckets empty) by the whole warp, 32 entries per store
@@ -222,28 +345,47 @@ int prepare_walk_index(tempest_t *h)
         if ((rc = ensure(h, h->big_node, sizeof(int32_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->big_t, sizeof(int32_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->big_c, sizeof(int32_t) * Sz, true))) return rc;
+        if ((rc = ensure(h, h->big_aux0, sizeof(int4) * Sz, true))) return rc;
+        if ((rc = ensure(h, h->big_aux1, sizeof(int4) * Sz, true))) return rc;
+        if ((rc = ensure(h, h->big_bf, sizeof(int64_t) * Sz, true))) return rc;
         if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
         if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
+        // the previous build's tables become the copy source; the new ones
+        // go to the other buffer, sized for the most a build can need: a
+        // width within 4x of its target gives K <= 4 max(1, G >> log_b) + 1,
+        // so a node takes at most 4 (G >> log_b) + 14 with its header and end
+        std::swap(h->bkt, h->bkt_prev);
+        const bool prev_ok = h->bkt_prev_ok && h->bkt_prev.p != nullptr;
+        const int prev_gen = h->bkt_gen;
+        const int gen = ++h->bkt_gen;
+        h->bkt_prev_ok = false;
+        const int64_t bound = 4 * (Gn >> h->bkt_log) + 16 * (Gn / BKT_MIN_G + 1) + 64;
+        if (bound >= (int64_t)INT32_MAX)
+            return fail(h, TEMPEST_ENOMEM, "walk index: %lld bucket entries exceed the int32 range",
+                        (long long)bound);
+        if ((rc = ensure(h, h->bkt, sizeof(int32_t) * (size_t)bound, true))) return rc;
         uint64_t *part = h->partials.as<uint64_t>();
         NodeRange *ngr = h->ngr.as<NodeRange>();
-        BigNodeOp op{h->act.as<int32_t>(), ngr, h->bkt_log, h->big_node.as<int32_t>(), h->big_t.as<int32_t>()};
+        const BuildCtx bc{prev_ok ? h->bkt_prev.as<int32_t>() : nullptr, prev_gen, h->bkt_log, h->nev.as<int32_t>()};
+        BigNodeOp op{h->act.as<int32_t>(), ngr, bc, gen, h->big_node.as<int32_t>(), h->big_t.as<int32_t>(),
+                     h->big_aux0.as<int4>(), h->big_aux1.as<int4>(), h->big_bf.as<int64_t>()};
         const int nblk = scan_launch(op, S, part, st);
         uint64_t *hp = static_cast<uint64_t *>(h->hstat);
         cudaMemcpyAsync(hp, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
         if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket lists"))) return rc;
         const uint64_t tot = hp[0];
         const int64_t nb = (int64_t)(tot >> 32), cap = (int64_t)(uint32_t)tot;
-        if (cap >= (int64_t)INT32_MAX)
-            return fail(h, TEMPEST_ENOMEM, "walk index: %lld bucket entries exceed the int32 range",
-                        (long long)cap);
+        if (cap > bound) return fail(h, TEMPEST_ECUDA, "walk index: bucket tables (%lld) above their bound (%lld)",
+                                     (long long)cap, (long long)bound);
         if (nb > 0) {
-            if ((rc = ensure(h, h->bkt, sizeof(int32_t) * (size_t)cap, true))) return rc;
-            ChunkOp cop{h->big_node.as<int32_t>(), ngr, h->big_c.as<int32_t>()};
+            ChunkOp cop{h->big_node.as<int32_t>(), ngr, h->big_aux0.as<int4>(), h->big_aux1.as<int4>(),
+                        h->big_c.as<int32_t>()};
             const int nblk2 = scan_launch(cop, nb, part, st);
             // the fill's consistency flag goes to the walk counters, which
             // every walk call zeroes before its kernels: read it here
             cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);
-            const int64_t nch_max = Gn / BKT_CHUNK + nb;  // chunks <= sum(G / CHUNK + 1)
+            // tasks <= copy tasks + group chunks <= cap / BKT_COPY + Gn / BKT_CHUNK + 2 nb
+            const int64_t nch_max = cap / BKT_COPY + Gn / BKT_CHUNK + 2 * nb + 1;
             if ((rc = ensure(h, h->big_own, sizeof(int32_t) * (size_t)nch_max, true))) return rc;
             const int64_t gcap = (int64_t)h->num_sms * 16;
             int64_t ogrid = (nb + 7) / 8;
@@ -252,10 +394,10 @@ int prepare_walk_index(tempest_t *h)
                                                          h->big_own.as<int32_t>(), h->wcnt.as<WalkCounters>());
             int64_t grid = (nch_max + 7) / 8;
             if (grid > gcap) grid = gcap;
-            k_bkt_fill<<<(unsigned)grid, 256, 0, st>>>(h->big_node.as<int32_t>(), h->big_t.as<int32_t>(),
-                                                       h->big_c.as<int32_t>(), h->big_own.as<int32_t>(),
-                                                       part + nblk2, ngr, h->ngts.as<int64_t>(), h->bkt_log, cap,
-                                                       h->bkt.as<int32_t>(), h->wcnt.as<WalkCounters>());
+            k_bkt_fill<<<(unsigned)grid, 256, 0, st>>>(
+                h->big_node.as<int32_t>(), h->big_t.as<int32_t>(), h->big_c.as<int32_t>(), h->big_own.as<int32_t>(),
+                h->big_aux0.as<int4>(), h->big_aux1.as<int4>(), h->big_bf.as<int64_t>(), part + nblk2, ngr,
+                h->ngts.as<int64_t>(), bc.prev, gen, cap, h->bkt.as<int32_t>(), h->wcnt.as<WalkCounters>());
             WalkCounters *hc = static_cast<WalkCounters *>(h->hstat);
             cudaMemcpyAsync(hc, h->wcnt.p, sizeof(WalkCounters), cudaMemcpyDeviceToHost, st);
             if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket fill"))) return rc;
@@ -264,6 +406,7 @@ int prepare_walk_index(tempest_t *h)
                             (unsigned long long)hc->status);
         }
         h->n_big = nb;
+        h->bkt_prev_ok = true;  // these tables are the next build's source
     }
     h->bkt_ver = h->state_ver;
     return TEMPEST_OK;

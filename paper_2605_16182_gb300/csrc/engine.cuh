@@ -43,17 +43,14 @@ struct IngestScratch {
 };
 
 // The per-node record a hop reads first: the node's live groups [g_lo,
-// g_hi), the base of its time-bucket table (nodes with enough groups; set
-// when the tables are built), the timestamps of its first and last live
-// groups, and (last_other) the far endpoint of the last group's entry when
-// that group holds exactly one entry (else -1): a biased hop that picks the
-// node's latest group, the likeliest pick of the exponential bias, then has
-// its next node and time without reading the group offsets or the entry.
-// 32 bytes, one sector: a hop gets everything it needs before the search in
-// one round trip.
+// g_hi), its time-bucket table (nodes with enough groups; set when the
+// tables are built: tb the table's first entry, bs the bucket width's log2
+// in the low 6 bits and the build's generation above them), and the
+// timestamps of its first and last live groups.  32 bytes, one sector: a
+// hop gets everything it needs before the search in one round trip.
 struct __align__(32) NodeRange {
     int32_t g_lo, g_hi;
-    int32_t tb, last_other;
+    int32_t tb, bs;
     int64_t t_first, t_last;
 };
 
@@ -166,6 +163,11 @@ struct tempest {
     // list and its chunk prefix
     tw::DBuf bkt;        // int32 tables (each big node's base is in its NodeRange)
     tw::DBuf big_node, big_t, big_c, big_own;
+    tw::DBuf big_aux0, big_aux1, big_bf;  // per big node: build plan (int4, int4) and first bucket (int64)
+    tw::DBuf bkt_prev;                    // the previous build's tables, the source of the next build's copies
+    tw::DBuf nev;                         // int32 [N+1]: groups each node has lost to eviction (mod 2^32)
+    int bkt_gen = 0;                      // build generation (the tables in bkt)
+    bool bkt_prev_ok = false;             // bkt_prev holds generation bkt_gen - 1 of the current group numbering
     int64_t bkt_ver = -1;
     // active nodes in id order, for PER_NODE starts (built lazily per state)
     tw::DBuf pn_nodes;

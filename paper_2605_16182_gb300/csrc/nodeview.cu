@@ -142,10 +142,9 @@ __global__ void k_nv_build_nodes(const int32_t *__restrict__ run_node, const int
         x.g_lo = gb;
         x.g_hi = gb + gc;
         x.tb = 0;
-        const Entry &last = E[run_pos[r + 1] - 1];
-        x.last_other = (c == 1 || E[run_pos[r + 1] - 2].ts != last.ts) ? last.other : -1;
+        x.bs = 0;  // no time-bucket table (generation 0 is never a build's)
         x.t_first = E[run_pos[r]].ts;
-        x.t_last = last.ts;
+        x.t_last = E[run_pos[r + 1] - 1].ts;
         ngr[v] = x;
         nbeg[v] = make_int2(eb, gb);
         ngo[gb + gc] = eb + c;
@@ -197,7 +196,7 @@ __global__ void k_nv_evict_count(Items it, int64_t items, int64_t N, int32_t *ev
 
 // Every node that lost entries drops them from the front of its region.
 __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *ev, int4 *nrec, NodeRange *ngr,
-                                 int32_t *ngo, const int64_t *__restrict__ ngts, NvCounters *c)
+                                 int32_t *ngo, const int64_t *__restrict__ ngts, int32_t *nev, NvCounters *c)
 {
     const int64_t n = (int64_t)c->n_ev_nodes;
     long long removed = 0;
@@ -228,6 +227,7 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
             ngr[v].t_first = ngts[ng];
         }
         removed += ng - gx;
+        nev[v] += ng - gx;  // the node's group numbering origin moves with it (time-bucket table reuse)
         r.x = e_lo;
         nrec[v] = r;
         ngr[v].g_lo = ng;
@@ -461,12 +461,7 @@ __global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t
             const int32_t v = run_node[r];
             if (ngr[v].g_lo == run_dg[r]) ngr[v].t_first = x.ts;  // no live group before the batch
         }
-        if (p + 1 == run_pos[r + 1]) {
-            // the node's last group: a single entry when this entry starts it
-            NodeRange &nr = ngr[run_node[r]];
-            nr.t_last = x.ts;
-            nr.last_other = fx[p + 1] != fx[p] ? x.other : -1;
-        }
+        if (p + 1 == run_pos[r + 1]) ngr[run_node[r]].t_last = x.ts;
         if (fx[p + 1] != fx[p]) {
             const int64_t g = (int64_t)run_dg[r] + (fx[p] - run_g[r]);
             if (g < 0 || g >= g_cap) {
@@ -594,7 +589,7 @@ int grow_keep(tempest_t *h, DBuf &b, size_t used, size_t bytes)
 int nv_ensure_nodes(tempest_t *h, int64_t N)
 {
     const int64_t need = N + 1;
-    if (need <= h->nrec_n && h->ngr.p && h->nrec.p && h->ev.p && h->act.p && h->dense.p && h->nbeg.p)
+    if (need <= h->nrec_n && h->ngr.p && h->nrec.p && h->ev.p && h->act.p && h->dense.p && h->nbeg.p && h->nev.p)
         return TEMPEST_OK;
     int rc;
     const size_t used = (size_t)h->nrec_n;
@@ -604,12 +599,14 @@ int nv_ensure_nodes(tempest_t *h, int64_t N)
     if ((rc = grow_keep(h, h->act, sizeof(int32_t) * (size_t)h->n_act, sizeof(int32_t) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->dense, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
     if ((rc = grow_keep(h, h->nbeg, sizeof(int2) * used, sizeof(int2) * (size_t)need))) return rc;
+    if ((rc = grow_keep(h, h->nev, sizeof(int32_t) * used, sizeof(int32_t) * (size_t)need))) return rc;
     int64_t cover = (int64_t)(h->nrec.bytes / sizeof(int4));
     cover = std::min(cover, (int64_t)(h->nbeg.bytes / sizeof(int2)));
     cover = std::min(cover, (int64_t)(h->dense.bytes / sizeof(int32_t)));
     cover = std::min(cover, (int64_t)(h->ngr.bytes / sizeof(NodeRange)));
     cover = std::min(cover, (int64_t)(h->ev.bytes / sizeof(int32_t)));
     cover = std::min(cover, (int64_t)(h->act.bytes / sizeof(int32_t)));
+    cover = std::min(cover, (int64_t)(h->nev.bytes / sizeof(int32_t)));
     h->nrec_n = cover;
     return TEMPEST_OK;
 }
@@ -626,6 +623,7 @@ int nv_build(tempest_t *h)
     if ((rc = ensure(h, h->nvc, sizeof(NvCounters)))) return rc;
     cudaMemsetAsync(h->nrec.p, 0, h->nrec.bytes, st);
     cudaMemsetAsync(h->ngr.p, 0, h->ngr.bytes, st);
+    h->bkt_prev_ok = false;  // groups are renumbered: no table of an earlier build can be reused
     cudaMemsetAsync(h->nvc.p, 0, sizeof(NvCounters), st);
     h->n_act = 0;
     h->Gn = 0;
@@ -731,7 +729,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
                                                           h->ev_nodes.as<int32_t>(), dc);
         k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
             h->ev_nodes.as<int32_t>(), h->ev.as<int32_t>(), h->nrec.as<int4>(), h->ngr.as<NodeRange>(),
-            h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), dc);
+            h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->nev.as<int32_t>(), dc);
         h->pending_launches += 2;
     }
     if (nbe > 0) {

@@ -119,58 +119,28 @@ __device__ __forceinline__ int32_t upper_bound_ts(const int64_t *__restrict__ gt
 
 // Time buckets of a node with G >= BKT_MIN_G groups [g0, g1) and first /
 // last group timestamps tlo < thi (a node's groups have distinct
-// timestamps).  The node has K = G >> log_b buckets over [tlo, thi]; the map
-// from a time to its bucket is monotone non-decreasing and fills [0, K):
-// the offset t - tlo is normalised so that thi - tlo lands in [2^30, 2^31)
-// (32-bit values, so no 64-bit conversion is needed), converted to float
-// and scaled by K / (normalised span + 1), then truncated and clamped to
-// K - 1.  Each step is monotone (int-to-float rounding, a multiply by a
-// positive constant, truncation), and the same inline code builds and reads
-// the tables, so both sides agree bit for bit.  The node's table (K + 1
-// int32 at bkt_base[v]) holds for each k the first group whose bucket is
-// >= k, and g1 at k = K.  By monotonicity every group before table[k] is
-// earlier than any t in bucket k and every group from table[k + 1] on is
-// later, so for tlo <= t < thi the first group later than t lies in
-// [table[k], table[k + 1]], k = bucket(t).
+// timestamps).  A bucket is a run of 2^s time units aligned on absolute time
+// (s chosen per node so that the node has about G >> log_b buckets): t lies
+// in bucket (t >> s) - (tlo >> s) of the node, counted from the bucket of its
+// first live group, a monotone map.  The node's table (at tb, K + 1 int32
+// for its K buckets) holds for each bucket k the first group whose bucket is
+// >= k, and g1 at k = K; entry 0 may name a group evicted since the table was
+// built (the walker clamps it to g0).  Every group before table[k] is earlier
+// than any t in bucket k and every group from table[k + 1] on is later, so
+// for tlo <= t < thi the first group later than t lies in
+// [max(table[k], g0), table[k + 1]], k = bucket(t).  Because buckets sit on
+// absolute time, a table stays valid for the buckets a later state keeps, so
+// each build copies those and fills only the buckets of new groups.
 constexpr int32_t BKT_MIN_G = 32;
 constexpr int32_t BKT_CHUNK = 1024;  // groups per table-fill task
+constexpr int32_t BKT_HDR = 8;       // int32 header before a node's table (build bookkeeping)
 
-__device__ __forceinline__ uint32_t bkt_count(int32_t G, int log_b) { return (uint32_t)(G >> log_b); }
-
-struct BktMap {
-    int64_t tlo;
-    int sh;       // > 0: right shift by sh; < 0: left shift by -sh
-    float scale;  // K / (normalised span + 1)
-    uint32_t K;
-};
-
-__device__ __forceinline__ uint32_t bkt_norm(uint64_t a, int sh)
-{
-    return sh >= 0 ? (uint32_t)(a >> sh) : (uint32_t)(a << (-sh));
-}
-
-__device__ __forceinline__ BktMap bkt_map(int64_t tlo, int64_t thi, uint32_t K)
-{
-    BktMap m;
-    const uint64_t d = (uint64_t)thi - (uint64_t)tlo;  // >= 1
-    m.tlo = tlo;
-    m.sh = (64 - __clzll((long long)d)) - 31;         // bit length - 31
-    const uint32_t dn = bkt_norm(d, m.sh);             // in [2^30, 2^31)
-    m.scale = __fdividef((float)K, (float)(dn + 1u));
-    m.K = K;
-    return m;
-}
-
-__device__ __forceinline__ uint32_t bkt_index(const BktMap &m, int64_t t)
-{
-    const uint32_t an = bkt_norm((uint64_t)t - (uint64_t)m.tlo, m.sh);
-    const uint32_t k = (uint32_t)((float)an * m.scale);
-    return k < m.K ? k : m.K - 1u;
-}
+// bucket of t relative to the node's first live group (tlo), width 2^s
+__device__ __forceinline__ int32_t bkt_rel(int64_t t, int64_t tlo, int s) { return (int32_t)((t >> s) - (tlo >> s)); }
 
 // The node record of v (two 16-byte loads of one sector).
 __device__ __forceinline__ void load_range(const NodeRange *r, int32_t &g_lo, int32_t &g_hi, int32_t &tb,
-                                           int64_t &t_first, int64_t &t_last, int32_t *last_other = nullptr)
+                                           int64_t &t_first, int64_t &t_last, int32_t *bs = nullptr)
 {
     const int4 a = __ldg(reinterpret_cast<const int4 *>(r));
     const longlong2 b = __ldg(reinterpret_cast<const longlong2 *>(r) + 1);
@@ -179,7 +149,7 @@ __device__ __forceinline__ void load_range(const NodeRange *r, int32_t &g_lo, in
     tb = a.z;
     t_first = b.x;
     t_last = b.y;
-    if (last_other) *last_other = a.w;
+    if (bs) *bs = a.w;
 }
 
 // Live groups [g0, g1) of v (the first 8 bytes of its record).
@@ -195,13 +165,13 @@ __device__ __forceinline__ void node_groups(const WalkView &V, int32_t v, int32_
 __device__ __forceinline__ int32_t first_later(const WalkView &V, int32_t v, int32_t g0, int32_t g1, int64_t t)
 {
     if (V.bkt && g1 - g0 >= BKT_MIN_G) {
-        int32_t a, b, tb;
+        int32_t a, b, tb, bs;
         int64_t tlo, thi;
-        load_range(V.ngr + v, a, b, tb, tlo, thi);
+        load_range(V.ngr + v, a, b, tb, tlo, thi, &bs);
         if (t < tlo) return g0;
         if (t >= thi) return g1;
-        const uint32_t k = bkt_index(bkt_map(tlo, thi, bkt_count(g1 - g0, V.bkt_log)), t);
-        const int32_t lo = __ldg(V.bkt + tb + k), hi = __ldg(V.bkt + tb + k + 1);
+        const int32_t k = bkt_rel(t, tlo, bs & 63);
+        const int32_t lo = max(__ldg(V.bkt + tb + k), g0), hi = __ldg(V.bkt + tb + k + 1);
         return upper_bound_ts(V.ngts, lo, hi, t);
     }
     return upper_bound_ts(V.ngts, g0, g1, t);
@@ -334,34 +304,6 @@ __device__ __forceinline__ Entry draw_entry(const WalkView &V, const OUT &O, int
         idx = e0 + uniform_index_k(h2, (int64_t)(e1 - e0));
     }
     return V.ent[idx];
-}
-
-// draw_entry for a hop whose node record was read: a pick of the node's last
-// group (g1 - 1) when the record names that group's single entry
-// (last_other >= 0) needs no further loads, as that entry's far endpoint is
-// last_other and its time t_last (the draw inside a one-entry group is 0).
-template <class OUT>
-__device__ __forceinline__ Entry draw_entry_rec(const WalkView &V, const OUT &O, int64_t w, uint32_t hop, int bias,
-                                                int32_t c, int32_t g1, int32_t last_other, int64_t t_last)
-{
-    const Rand4 r = walk_rand(O.seed, (uint64_t)w, hop);
-    const uint64_t h1 = u53_bits(r.r0, r.r1);
-    bias = hop_bias(V, bias, O.cnt);
-    Entry x;
-    x.ts = t_last;
-    x.other = last_other;
-    x.slot = 0;
-    if (bias == BIAS_UNIFORM) {
-        if (c == g1 - 1 && last_other >= 0) return x;  // Gamma is that one entry
-        const int32_t e0 = __ldg(V.ngo + c), e1 = __ldg(V.ngo + g1);
-        return V.ent[e0 + uniform_index_k(h1, (int64_t)(e1 - e0))];
-    }
-    const int32_t k = bias == BIAS_EXP_WEIGHT
-                          ? weight_group(V, c, g1, h1)
-                          : c + (int32_t)sampler_index_k(h1, (int64_t)(g1 - c), start_bias(bias), V.rate_hop);
-    if (k == g1 - 1 && last_other >= 0) return x;
-    const int32_t e0 = __ldg(V.ngo + k), e1 = __ldg(V.ngo + k + 1);
-    return V.ent[e0 + uniform_index_k(u53_bits(r.r2, r.r3), (int64_t)(e1 - e0))];
 }
 
 // Backward hop at a node whose groups earlier than t are [g0, c), in the

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
     s.w = 0;
     int64_t y0 = 0;           // loaded 64-bit value
     int32_t z0 = 0, z1 = 0;   // loaded 32-bit values
-    int32_t z2 = 0;
+    int32_t z2 = 0, z3 = 0;  // z3: the node record's bucket width word
     int64_t y1 = 0;
     unsigned long long hops = 0, bytes = 0;
     const int64_t N = Pv.total();
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             if (s.len >= s.cap_len) {
                 finish = true;
             } else {
-                load_range(V.ngr + z0, z0, z1, z2, y0, y1);
+                load_range(V.ngr + z0, z0, z1, z2, y0, y1, &z3);
                 s.state = S_RANGE;
             }
         };
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 if (N2V) s.u = -1;
                 s.v = z0;
                 s.t = (BACK ? INT64_MAX - 1 : INT64_MIN);
-                load_range(V.ngr + z0, z0, z1, z2, y0, y1);
+                load_range(V.ngr + z0, z0, z1, z2, y0, y1, &z3);
                 s.state = S_RANGE;
                 break;
             }
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                 if (s.len >= s.cap_len) {
                     finish = true;
                 } else {
-                    load_range(V.ngr + b, z0, z1, z2, y0, y1);
+                    load_range(V.ngr + b, z0, z1, z2, y0, y1, &z3);
                     s.state = S_RANGE;
                 }
                 break;
@@ -512,8 +512,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
                     else finish = true;
                 } else if (V.bkt && s.g1 - s.g0 >= BKT_MIN_G) {
                     // y0 <= t < y1: the bucket of t brackets c
-                    const uint32_t k = bkt_index(bkt_map(y0, y1, bkt_count(s.g1 - s.g0, V.bkt_log)), s.t);
-                    const int32_t *tp = V.bkt + z2 + k;
+                    const int32_t *tp = V.bkt + z2 + bkt_rel(s.t, y0, z3 & 63);
                     z0 = __ldg(tp);
                     z1 = __ldg(tp + 1);
                     s.state = S_BKT;
@@ -536,7 +535,8 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
             }
             case S_BKT: {
                 // c lies in [z0, z1]: groups before z0 are not later than t,
-                // group z1 (or g1) is later
+                // group z1 (or g1) is later (z0 may name an evicted group)
+                z0 = max(z0, s.g0);
                 if (z0 == z1) {
                     s.R = z0;
                     pick = true;
@@ -733,12 +733,12 @@ __global__ void __launch_bounds__(256, MINB) k_walks_stream(const WalkView V, co
 // First group of [g0, g1) later than t, for tlo <= t < thi (the node's first
 // and last group timestamps): through the time buckets of a big node, else by
 // interpolation on the group timestamps with a bisection fallback.
-__device__ __forceinline__ int32_t lane_first_later(const WalkView &V, int32_t g0, int32_t g1, int32_t tb, int64_t tlo,
-                                                    int64_t thi, int64_t t)
+__device__ __forceinline__ int32_t lane_first_later(const WalkView &V, int32_t g0, int32_t g1, int32_t tb, int32_t bs,
+                                                    int64_t tlo, int64_t thi, int64_t t)
 {
     if (V.bkt && g1 - g0 >= BKT_MIN_G) {
-        const uint32_t k = bkt_index(bkt_map(tlo, thi, bkt_count(g1 - g0, V.bkt_log)), t);
-        return upper_bound_ts(V.ngts, __ldg(V.bkt + tb + k), __ldg(V.bkt + tb + k + 1), t);
+        const int32_t k = bkt_rel(t, tlo, bs & 63);
+        return upper_bound_ts(V.ngts, max(__ldg(V.bkt + tb + k), g0), __ldg(V.bkt + tb + k + 1), t);
     }
     // ngts[L] <= t < ngts[R]
     int32_t L = g0, R = g1 - 1;
@@ -864,9 +864,9 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
         } else if (mode == 2) {
             // one hop from v at search time t
             const uint32_t hop = (uint32_t)(len - 1);
-            int32_t g0, g1, tb, last_other;
+            int32_t g0, g1, tb, bs;
             int64_t tlo, thi;
-            load_range(V.ngr + v, g0, g1, tb, tlo, thi, &last_other);
+            load_range(V.ngr + v, g0, g1, tb, tlo, thi, &bs);
             int32_t c = g0;
             if (g0 == g1) {
                 finish = true;
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
             } else if (t >= thi) {
                 c = g1;
             } else {
-                c = lane_first_later(V, g0, g1, tb, tlo, thi, t);
+                c = lane_first_later(V, g0, g1, tb, bs, tlo, thi, t);
             }
             if (!finish && (BACK ? c == g0 : c == g1)) finish = true;  // Gamma_t(v) is empty
             if (!finish) {
@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
                 } else if (BACK) {
                     e = draw_entry_back(V, D, (int64_t)wid, hop, bias, g0, c);
                 } else {
-                    e = draw_entry_rec(V, D, (int64_t)wid, hop, bias, c, g1, last_other, thi);
+                    e = draw_entry(V, D, (int64_t)wid, hop, bias, c, g1);
                 }
                 if (!ok) {
                     finish = true;  // every Node2Vec proposal rejected

@@ -32,9 +32,9 @@ def _rank_main(rank, world, port, out):
 
 def test_two_replicas_aggregate_over_gloo():
     world = 2
-    mgr = mp.Manager()
-    out = mgr.dict()
     ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
     port = _free_port()
     procs = [ctx.Process(target=_rank_main, args=(r, world, port, out)) for r in range(world)]
     for p in procs:
