@@ -84,3 +84,40 @@ def test_tables_follow_streaming_ingest():
         if i in (0, 3, 7, 12, 19):
             check_walks(eng, orc, 3000, 16, seed=100 + i, biases=(0, 2),
                         scheds=(_lib.SCHED_STREAM, _lib.SCHED_FULL_WALK, _lib.SCHED_LANE))
+
+
+@pytest.mark.parametrize("directed", [1, 0])
+def test_tables_carried_across_slides_moves_and_rebuilds(directed):
+    """Walks after every batch of a sliding window in which two hubs keep
+    gaining groups (their regions slide and move, shifting their group
+    indices), a quiet batch (evictions only), a batch that extends a hub's
+    last group (same timestamp), a time gap that empties thousands of
+    buckets, and a late batch (a merge, which renumbers every group): each
+    build carries the previous tables forward and must still bracket the
+    first later group everywhere."""
+    rng = np.random.default_rng(40 + directed)
+    eng, orc = pair(-3000, directed)
+    t = 0
+    last_ts = 0
+    for b in range(45):
+        n = 300
+        if b == 20:
+            n = 0  # evictions only (count window keeps the newest 3000)
+        hubs = rng.random(n) < 0.7
+        s = np.where(hubs, rng.integers(0, 2, n), rng.integers(2, 400, n)).astype(np.int32)
+        d = np.where(rng.random(n) < 0.5, rng.integers(0, 2, n), rng.integers(2, 400, n)).astype(np.int32)
+        gaps = rng.integers(1, 5, n)
+        if b == 30:
+            gaps[n // 2] = 10**9  # a time gap inside the batch
+        ts = (t + np.cumsum(gaps)).astype(np.int64)
+        if b == 25:
+            ts[: n // 3] = last_ts  # extends the hubs' last groups
+            ts = np.sort(ts)
+        if b == 36:
+            ts = ts - 600  # late: inside the window, older than the newest edges
+        if n:
+            t = int(ts.max())
+            last_ts = int(ts.max())
+        ingest_both(eng, orc, s, d, ts)
+        check_walks(eng, orc, 1500, 16, seed=b, biases=(0, 2),
+                    scheds=(_lib.SCHED_LANE, _lib.SCHED_STREAM) if b % 5 else SCHEDULERS)
