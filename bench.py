@@ -300,7 +300,9 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
                 hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
         walk_s += time.perf_counter() - t0
         hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
-        d2h += hnode.numel() * 4 + hts.numel() * 8 + hln.numel() * 4
+        # the bytes the call moved device to host (rows travel compacted: each
+        # walk's cells with its length and offset; the host writes the padding)
+        d2h += _lib.tempest_last_walk_stats(eng.h).d2h_bytes
     return dict(value=hops / walk_s, unit="hops/s", h2d_bytes_per_step=h2d // e2e_steps,
                 d2h_bytes_per_step=d2h // e2e_steps, ingest_edges_per_s=edges / ingest_s, steps=e2e_steps)
 

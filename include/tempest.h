@@ -133,6 +133,14 @@ typedef struct {
                               draw and hops, without the row padding and
                               without the index preparation), from CUDA
                               events on the handle's stream; 0 if none ran */
+    int64_t d2h_bytes;     /* bytes copied device to host for host outputs.
+                              When node and ts are both host buffers, a
+                              share of the rows (TEMPEST_TUNE_HOST_LINK_PCT)
+                              is padded on the device and copied whole; the
+                              others travel as their walks' cells, lengths
+                              and offsets and host threads write their rows
+                              and padding, overlapped with the first copy
+                              when the caller's buffers are pinned */
 } tempest_walk_stats;
 
 /* Create an engine.  window > 0: duration Delta in timestamp units, the
@@ -335,7 +343,11 @@ enum {
     TEMPEST_TUNE_STREAM_CTAS = 3,
     /* TEMPEST_SCHED_LANE: 0 (default) the walker writes each row's padding
      * as its walk ends; 1 one streaming pass pads all rows after the walks */
-    TEMPEST_TUNE_PAD_PASS = 4
+    TEMPEST_TUNE_PAD_PASS = 4,
+    /* walks into host buffers: percent of the rows padded on the device and
+     * copied whole (0-100, default 62); the others travel as their walks'
+     * cells only and host threads write their rows and padding meanwhile */
+    TEMPEST_TUNE_HOST_LINK_PCT = 5
 };
 /* Set / read one knob.  EINVAL on an unknown knob or a value out of range. */
 int tempest_set_tuning(tempest_t *h, int knob, int64_t value);

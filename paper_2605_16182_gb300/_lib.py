@@ -26,7 +26,7 @@ BIAS_UNIFORM, BIAS_LINEAR, BIAS_EXP, BIAS_EXP_WEIGHT, BIAS_NODE2VEC = 0, 1, 2, 3
 N2V_MAX_TRIALS = 4096
 START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH, SCHED_LANE = 0, 1, 2, 3, 4
-TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS, TUNE_PAD_PASS = 0, 1, 2, 3, 4
+TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS, TUNE_PAD_PASS, TUNE_HOST_LINK_PCT = 0, 1, 2, 3, 4, 5
 TUNE_FORMS = 1
 TUNE_PER_INGEST = 2
 TUNE_MAX_TRIALS = 48
@@ -71,7 +71,8 @@ class IngestStats(ctypes.Structure):
 class WalkStats(ctypes.Structure):
     _fields_ = [("n_walks", ctypes.c_int64), ("hops", ctypes.c_int64),
                 ("model_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("tier_launches", ctypes.c_int64 * 5), ("kernel_ms", ctypes.c_double)]
+                ("tier_launches", ctypes.c_int64 * 5), ("kernel_ms", ctypes.c_double),
+                ("d2h_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -4,7 +4,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "engine.cuh"
 #include "prims.cuh"
@@ -102,6 +105,75 @@ int ensure(tempest_t *h, DBuf &b, size_t bytes, bool headroom)
     return TEMPEST_OK;
 }
 
+// Offsets of the walks' cells in the compacted copy (exclusive prefix of the
+// lengths, each clamped to the row).
+struct LenScanOp {
+    const int32_t *len;
+    int32_t cap;
+    int64_t *off;
+    __device__ __forceinline__ uint64_t value(int64_t i) const
+    {
+        const int32_t l = len[i];
+        return (uint64_t)(l < 0 ? 0 : (l > cap ? cap : l));
+    }
+    __device__ __forceinline__ void emit(int64_t i, uint64_t, uint64_t ex) const { off[i] = (int64_t)ex; }
+};
+
+// The cells [0, len) of every row, back to back (a thread per walk: walks
+// are a few cells long).
+__global__ void k_compact_rows(const int32_t *__restrict__ node, const int64_t *__restrict__ ts,
+                               const int32_t *__restrict__ len, const int64_t *__restrict__ off, int64_t n,
+                               int32_t cap, int32_t *cnode, int64_t *cts)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t l = len[i];
+        l = l < 0 ? 0 : (l > cap ? cap : l);
+        const int64_t o = off[i];
+        const int32_t *nr = node + i * (int64_t)cap;
+        const int64_t *tr = ts + i * (int64_t)cap;
+        for (int32_t j = 0; j < l; j++) {
+            cnode[o + j] = nr[j];
+            cts[o + j] = tr[j];
+        }
+    }
+}
+
+// Pinned host staging of at least `bytes` (kept, grown by half again).
+static int ensure_pinned(tempest_t *h, size_t bytes)
+{
+    if (h->hpin_bytes >= bytes) return TEMPEST_OK;
+    if (h->hpin) cudaFreeHost(h->hpin);
+    h->hpin = nullptr;
+    h->hpin_bytes = 0;
+    const size_t want = bytes + bytes / 2;
+    if (cudaMallocHost(&h->hpin, want) != cudaSuccess) {
+        cudaGetLastError();
+        h->hpin = nullptr;
+        return fail(h, TEMPEST_ENOMEM, "walks: pinned host staging of %zu bytes", want);
+    }
+    h->hpin_bytes = want;
+    return TEMPEST_OK;
+}
+
+// Host side of a walk call into host buffers: rows [i0, i1) from the
+// compacted cells.  The rows of a range are contiguous, so the range is
+// first filled with padding in two long sweeps (node -1 bytewise, ts
+// INT64_MIN), then each walk's cells are copied over its row's head.
+static void expand_rows(int64_t i0, int64_t i1, int32_t cap, const int32_t *len, const int64_t *off,
+                        const int32_t *cnode, const int64_t *cts, int32_t *node, int64_t *ts)
+{
+    const size_t cells = (size_t)(i1 - i0) * (size_t)cap;
+    memset(node + i0 * (int64_t)cap, 0xff, sizeof(int32_t) * cells);
+    int64_t *t0 = ts + i0 * (int64_t)cap;
+    for (size_t k = 0; k < cells; k++) t0[k] = INT64_MIN;
+    for (int64_t i = i0; i < i1; i++) {
+        int32_t l = len[i];
+        l = l < 0 ? 0 : (l > cap ? cap : l);
+        memcpy(node + i * (int64_t)cap, cnode + off[i], sizeof(int32_t) * (size_t)l);
+        memcpy(ts + i * (int64_t)cap, cts + off[i], sizeof(int64_t) * (size_t)l);
+    }
+}
+
 static void free_all(tempest_t *h)
 {
     DBuf *bufs[] = {&h->st_src[0], &h->st_src[1], &h->st_dst[0], &h->st_dst[1], &h->st_ts[0], &h->st_ts[1],
@@ -115,7 +187,8 @@ static void free_all(tempest_t *h)
                     &h->co_act[1], &h->co_runs,   &h->co_tasks,  &h->co_ctr,    &h->bkt,
                     &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched,   &h->tg2,       &h->nbeg,
                     &h->pn_nodes,  &h->gw,        &h->gs,        &h->wref,      &h->w_cbase,   &h->w_ctot,
-                    &h->w_coff,    &h->co_prev,   &h->pt,        &h->big_own};
+                    &h->w_coff,    &h->co_prev,   &h->pt,        &h->big_own,   &h->big_aux0,
+                    &h->big_aux1,  &h->big_bf,    &h->bkt_prev,  &h->nev,       &h->cmp_stage, &h->cmp_off};
     for (DBuf *b : bufs) release(h, *b);
 }
 
@@ -191,6 +264,7 @@ int tempest_destroy(tempest_t *h)
         if (e) cudaEventDestroy(e);
     free_all(h);
     if (h->hstat) cudaFreeHost(h->hstat);
+    if (h->hpin) cudaFreeHost(h->hpin);
     delete h;
     return TEMPEST_OK;
 }
@@ -310,6 +384,93 @@ int tempest_active_nodes(tempest_t *h, int64_t *n) { return active_nodes_dir(h, 
 
 int tempest_active_nodes_backward(tempest_t *h, int64_t *n) { return active_nodes_dir(h, 1, n); }
 
+// Walk rows into host buffers.  The host link and the host's own stores move
+// a few hundred GB/s each, and padding is most of a row, so the rows are
+// split: a share of them (h->host_link_pct percent, a tuning knob) is padded
+// on the device and copied whole, while for the rest only each walk's cells
+// travel (gathered back to back on the device, with the lengths and offsets)
+// and host threads write those rows and their padding, during the copy of the
+// first part.
+
+static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, int64_t *d_ts, const int32_t *d_len,
+                         int32_t *node, int64_t *ts, int32_t *len, bool dev_len)
+{
+    cudaStream_t st = h->stream;
+    int rc;
+    const int64_t nd = std::min<int64_t>(n, n * h->host_link_pct / 100);  // rows copied whole
+    const int64_t nh = n - nd;                                                          // rows the host writes
+    const size_t rowb = sizeof(int32_t) * (size_t)cap, rowt = sizeof(int64_t) * (size_t)cap;
+    int64_t grid = (n + 255) / 256;
+    const int64_t gcap = (int64_t)h->num_sms * 16;
+    if (grid > gcap) grid = gcap;
+    if (nd > 0) pad_rows(h, nd, cap, d_len, d_node, d_ts);
+    if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
+    if ((rc = ensure(h, h->cmp_off, sizeof(int64_t) * (size_t)(nh > 0 ? nh : 1) + 256, true))) return rc;
+    int64_t *d_off = h->cmp_off.as<int64_t>();
+    uint64_t *part = h->partials.as<uint64_t>();
+    const int32_t *hlen_d = d_len + nd;
+    const int nblk = scan_launch(LenScanOp{hlen_d, cap, d_off}, nh, part, st);
+    uint64_t *hp = static_cast<uint64_t *>(h->hstat);
+    cudaMemcpyAsync(hp, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "walks (compact)"))) return rc;
+    const int64_t tot = nh > 0 ? (int64_t)hp[0] : 0;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b_off = up(sizeof(int64_t) * (size_t)nh), b_node = up(sizeof(int32_t) * (size_t)tot),
+                 b_ts = up(sizeof(int64_t) * (size_t)tot), b_len = up(sizeof(int32_t) * (size_t)n);
+    if ((rc = ensure(h, h->cmp_stage, b_node + b_ts + 256, true))) return rc;
+    int32_t *c_node = h->cmp_stage.as<int32_t>();
+    int64_t *c_ts = reinterpret_cast<int64_t *>(h->cmp_stage.as<char>() + b_node);
+    if (tot > 0)
+        k_compact_rows<<<(unsigned)grid, 256, 0, st>>>(d_node + nd * (int64_t)cap, d_ts + nd * (int64_t)cap, hlen_d,
+                                                       d_off, nh, cap, c_node, c_ts);
+    if ((rc = ensure_pinned(h, b_off + b_node + b_ts + b_len + 256))) return rc;
+    char *hb = static_cast<char *>(h->hpin);
+    int64_t *h_off = reinterpret_cast<int64_t *>(hb);
+    int32_t *h_node = reinterpret_cast<int32_t *>(hb + b_off);
+    int64_t *h_ts = reinterpret_cast<int64_t *>(hb + b_off + b_node);
+    int32_t *h_len = dev_len ? reinterpret_cast<int32_t *>(hb + b_off + b_node + b_ts) : len;
+    // the host part's inputs first, then the whole rows of the other part
+    cudaMemcpyAsync(h_len, d_len, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (nh > 0) cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (size_t)nh, cudaMemcpyDeviceToHost, st);
+    if (tot > 0) {
+        cudaMemcpyAsync(h_node, c_node, sizeof(int32_t) * (size_t)tot, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(h_ts, c_ts, sizeof(int64_t) * (size_t)tot, cudaMemcpyDeviceToHost, st);
+    }
+    cudaEvent_t ready;
+    if ((rc = cuda_check(h, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "walks (host event)"))) return rc;
+    cudaEventRecord(ready, st);
+    if (nd > 0) {
+        cudaMemcpyAsync(node, d_node, rowb * (size_t)nd, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(ts, d_ts, rowt * (size_t)nd, cudaMemcpyDeviceToHost, st);
+    }
+    rc = cuda_check(h, cudaEventSynchronize(ready), "walks (host outputs)");
+    cudaEventDestroy(ready);
+    if (rc) return rc;
+    h->last_d2h = (int64_t)(sizeof(int32_t) * (size_t)n + sizeof(int64_t) * (size_t)nh + 12 * (size_t)tot +
+                            (rowb + rowt) * (size_t)nd);
+    // rows [nd, n) and their padding on the host, in parallel threads, while
+    // the copy engine moves rows [0, nd)
+    if (nh > 0) {
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int64_t nt = std::min<int64_t>(std::min<int64_t>(hw, 64), std::max<int64_t>(1, nh / 4096));
+        int32_t *node_h = node + nd * (int64_t)cap;
+        int64_t *ts_h = ts + nd * (int64_t)cap;
+        const int32_t *len_h = h_len + nd;
+        if (nt <= 1) {
+            expand_rows(0, nh, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
+        } else {
+            std::vector<std::thread> th;
+            th.reserve((size_t)nt);
+            for (int64_t k = 0; k < nt; k++) {
+                const int64_t i0 = nh * k / nt, i1 = nh * (k + 1) / nt;
+                th.emplace_back(expand_rows, i0, i1, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
+            }
+            for (auto &x : th) x.join();
+        }
+    }
+    return cuda_check(h, cudaStreamSynchronize(st), "walks (host outputs)");
+}
+
 static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_len, const int32_t *len_arr,
                         int bias, const uint8_t *bias_arr, int start_policy, uint64_t seed, int32_t *node,
                         int64_t *ts, int32_t *len, int direction = 0)
@@ -392,15 +553,22 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
     }
     WalkRequest rq{n_walks, cap, max_len, d_len, bias, d_bias, start_policy, pn_k, seed, d_node, d_ts, d_lenout};
     rq.direction = direction;
+    // host rows: the device keeps only each walk's cells, the host pads
+    const bool compact = !dev_node && !dev_ts;
+    rq.no_pad = compact ? 1 : 0;
     if (host_bias) {
         for (int64_t i = 0; i < n_walks && !rq.want_w; i++) rq.want_w = bias_arr[i] == TEMPEST_BIAS_EXP_WEIGHT;
         rq.may_n2v = 0;
         for (int64_t i = 0; i < n_walks && !rq.may_n2v; i++) rq.may_n2v = bias_arr[i] == TEMPEST_BIAS_NODE2VEC;
     }
     if ((rc = walks_run(h, rq))) return rc;
+    h->last_d2h = 0;
+    if (compact) return walks_to_host(h, n_walks, cap, d_node, d_ts, d_lenout, node, ts, len, dev_len);
     if (!dev_ts) cudaMemcpyAsync(ts, d_ts, sizeof(int64_t) * cells, cudaMemcpyDeviceToHost, st);
     if (!dev_node) cudaMemcpyAsync(node, d_node, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st);
     if (!dev_len) cudaMemcpyAsync(len, d_lenout, sizeof(int32_t) * (size_t)n_walks, cudaMemcpyDeviceToHost, st);
+    h->last_d2h = (int64_t)((dev_ts ? 0 : sizeof(int64_t) * cells) + (dev_node ? 0 : sizeof(int32_t) * cells) +
+                            (dev_len ? 0 : sizeof(int32_t) * (size_t)n_walks));
     if (!dev_node || !dev_ts || !dev_len || host_len || host_bias)
         return cuda_check(h, cudaStreamSynchronize(st), "walks (host outputs)");
     return cuda_check(h, cudaGetLastError(), "walks");
@@ -453,6 +621,7 @@ int tempest_last_walk_stats(tempest_t *h, tempest_walk_stats *out)
         if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "walk stats"))) return rc;
         h->last_ws.hops = (int64_t)hc->hops;
         h->last_ws.model_bytes = (int64_t)hc->model_bytes;
+        h->last_ws.d2h_bytes = h->last_d2h;
         if (h->kev_valid) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, h->kev[0], h->kev[1]) == cudaSuccess) h->last_ws.kernel_ms = ms;

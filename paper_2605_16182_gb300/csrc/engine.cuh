@@ -198,6 +198,13 @@ struct tempest {
     tw::DBuf in_stage;    // device staging of host walk inputs
     tw::DBuf exp_stage;   // export staging
     void *hstat = nullptr;     // pinned host mirror of IngestScratch / counters
+    // walks into host buffers: rows are compacted on the device, copied, and
+    // expanded on the host (pinned host staging, grown as needed)
+    void *hpin = nullptr;
+    size_t hpin_bytes = 0;
+    tw::DBuf cmp_off, cmp_stage;  // offsets and compacted cells of the rows on the device
+    int64_t last_d2h = 0;      // bytes the last walk call copied device to host
+    int host_link_pct = 62;    // percent of host-output rows copied whole (the rest expanded on the host)
 
     // Temporal Node2Vec: return / in-out parameters; the live-pair table kept
     // by ingest once q != 1 (pt_cap slots, a power of two; pt_ub bounds the
@@ -266,8 +273,12 @@ struct WalkRequest {
     int want_w = 0;            // per-walk biases known to include the weight-based one
     int direction = 0;         // 1: backward walks
     int may_n2v = 1;           // per-walk biases may include Node2Vec (host arrays are scanned)
+    int no_pad = 0;            // the lane walker may leave the cells after each walk unwritten
 };
 int walks_run(tempest_t *h, const WalkRequest &rq);
+// pads rows [0, n) of a walk output after their lengths (node -1, ts
+// INT64_MIN), one streaming pass on the handle's stream
+void pad_rows(tempest_t *h, int64_t n, int32_t cap, const int32_t *len, int32_t *node, int64_t *ts);
 // builds the time-bucket tables of the live state on the handle's stream
 // (no-op when they are current); every walk form calls it before launching
 int prepare_walk_index(tempest_t *h);

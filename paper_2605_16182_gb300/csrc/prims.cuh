@@ -395,7 +395,7 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
-constexpr int SORT_MAX_BLOCKS = 1024;
+constexpr int SORT_MAX_BLOCKS = 4096;  // one 2048-key tile per block up to 8M keys (part[] holds <= 256 chunks)
 
 template <typename K>
 struct ArrayLoader {

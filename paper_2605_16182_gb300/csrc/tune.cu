@@ -132,6 +132,11 @@ int tempest_set_tuning(tempest_t *h, int knob, int64_t value)
                                                     (long long)value);
             h->pad_pass = (int)value;
             return TEMPEST_OK;
+        case TEMPEST_TUNE_HOST_LINK_PCT:
+            if (value < 0 || value > 100) return fail(h, TEMPEST_EINVAL, "tuning: host link share %lld outside [0, 100]",
+                                                      (long long)value);
+            h->host_link_pct = (int)value;
+            return TEMPEST_OK;
         default:
             return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
@@ -146,6 +151,7 @@ int tempest_get_tuning(tempest_t *h, int knob, int64_t *value)
         case TEMPEST_TUNE_COOP_MEGA: *value = h->coop_mega; return TEMPEST_OK;
         case TEMPEST_TUNE_STREAM_CTAS: *value = h->stream_ctas; return TEMPEST_OK;
         case TEMPEST_TUNE_PAD_PASS: *value = h->pad_pass; return TEMPEST_OK;
+        case TEMPEST_TUNE_HOST_LINK_PCT: *value = h->host_link_pct; return TEMPEST_OK;
         default: return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
 }

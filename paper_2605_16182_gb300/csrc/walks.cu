@@ -961,6 +961,14 @@ __global__ void __launch_bounds__(256) k_pad_rows(int64_t n_walks, int32_t cap, 
     }
 }
 
+void pad_rows(tempest_t *h, int64_t n, int32_t cap, const int32_t *len, int32_t *node, int64_t *ts)
+{
+    int64_t pgrid = (n + 7) / 8;
+    const int64_t pcap = (int64_t)h->num_sms * 16;
+    if (pgrid > pcap) pgrid = pcap;
+    if (n > 0) k_pad_rows<<<(unsigned)pgrid, 256, 0, h->stream>>>(n, cap, len, node, ts);
+}
+
 // Launches the streaming walker with the register budget the CTAs-per-SM
 // knob asks for (0: the 64-register build at its occupancy limit).
 // n2v: a walk of the launch may take Node2Vec hops with p, q not both 1
@@ -1196,8 +1204,8 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
             const bool n2v = (rq.bias_arr ? rq.may_n2v != 0 : rq.bias == TEMPEST_BIAS_NODE2VEC) &&
                              (V.n2v_inv_p != 1.0 || V.n2v_inv_q != 1.0);
             // the lane walker pads rows as walks end, or leaves it to one pass
-            const bool sep = h->sched == TEMPEST_SCHED_LANE && h->pad_pass;
-            launch_stream(h, V, OneReq{O}, &O.cnt->pad, rq.n_walks, st, n2v, !sep);
+            const bool sep = h->sched == TEMPEST_SCHED_LANE && h->pad_pass && !rq.no_pad;
+            launch_stream(h, V, OneReq{O}, &O.cnt->pad, rq.n_walks, st, n2v, !sep && !rq.no_pad);
             if (sep) {
                 int64_t pgrid = (rq.n_walks + 7) / 8;
                 const int64_t pcap = (int64_t)h->num_sms * 16;

@@ -178,21 +178,35 @@ def test_mid_config_scaled_stream():
                 assert (g[1][lin_or_uni] == o[1][lin_or_uni]).all()
 
 
-def test_host_and_device_outputs_agree():
+@pytest.mark.parametrize("share", [62, 0, 100, 37])
+def test_host_and_device_outputs_agree(share):
+    """Walks into host buffers (part padded on the device and copied whole,
+    part sent as cells and expanded by host threads, split by the host-link
+    share) equal the device-output walks row for row, padding included."""
     spec = synth.config_small(scale=0.3)
     eng, orc = pair(0, False)
     for k, s, d, t in spec.batches():
         ingest_both(eng, orc, s, d, t, on_gpu=False)
-    gd = eng.walks(3000, 9, bias=1, seed=11)
-    torch.cuda.synchronize()
-    node = np.zeros((3000, 9), np.int32)
-    ts = np.zeros((3000, 9), np.int64)
-    ln = np.zeros(3000, np.int32)
-    _lib.tempest_walks(eng.h, 3000, 9, 1, 0, 11, node.ctypes.data, ts.ctypes.data, ln.ctypes.data)
-    assert np.array_equal(node, gd[0].cpu().numpy()) and np.array_equal(ts, gd[1].cpu().numpy())
-    assert np.array_equal(ln, gd[2].cpu().numpy())
-    o = orc.walks(3000, 9, bias=1, seed=11)
-    assert_walks_bit_exact((node, ts, ln), o)
+    eng.set_tuning(_lib.TUNE_HOST_LINK_PCT, share)
+    assert eng.get_tuning(_lib.TUNE_HOST_LINK_PCT) == share
+    for n, L in ((3000, 9), (40_000, 13), (1, 5)):
+        gd = eng.walks(n, L, bias=1, seed=11)
+        torch.cuda.synchronize()
+        node = np.full((n, L), 7, np.int32)
+        ts = np.full((n, L), 7, np.int64)
+        ln = np.full(n, 7, np.int32)
+        _lib.tempest_walks(eng.h, n, L, 1, 0, 11, node.ctypes.data, ts.ctypes.data, ln.ctypes.data)
+        assert np.array_equal(node, gd[0].cpu().numpy()) and np.array_equal(ts, gd[1].cpu().numpy())
+        assert np.array_equal(ln, gd[2].cpu().numpy())
+        ws = eng.last_walk_stats()
+        nd = n * share // 100
+        cells = int(ln[nd:].sum())
+        assert ws["d2h_bytes"] == 4 * n + 8 * (n - nd) + 12 * cells + 12 * L * nd
+        if n == 3000:
+            o = orc.walks(n, L, bias=1, seed=11)
+            assert_walks_bit_exact((node, ts, ln), o)
+    with pytest.raises(_lib.TempestError):
+        eng.set_tuning(_lib.TUNE_HOST_LINK_PCT, 101)
 
 
 # ------------------------------------------------------------------ edges
