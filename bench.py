@@ -269,15 +269,16 @@ def run_ours(args, rank, world):
 def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id, direction=0):
     """Continue the stream with host-resident batches: every step copies its
     batches from pinned host memory and its walks back to pinned host memory
-    inside the timed region."""
+    inside the timed region.  One untimed step first sizes the staging
+    buffers (device and pinned) the host-buffer calls keep for later calls."""
     import torch
     from paper_2605_16182_gb300 import _lib
 
-    e2e_steps = 2
+    e2e_warm, e2e_steps = 1, 3
     host = []
     start = n_batches * spec.batch
     ts_base = int(batches[-1][2][-1].item())
-    for k in range(e2e_steps * BATCHES_PER_STEP):
+    for k in range((e2e_warm + e2e_steps) * BATCHES_PER_STEP):
         s, d, t = spec.edges(start + k * spec.batch, spec.batch, device=batches[0][0].device, ts_base=ts_base)
         ts_base = int(t[-1].item())
         host.append((s.cpu().pin_memory(), d.cpu().pin_memory(), t.cpu().pin_memory()))
@@ -286,22 +287,28 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
     hln = torch.empty((n_walks,), dtype=torch.int32).pin_memory()
     torch.cuda.synchronize()
     hops, walk_s, ingest_s, h2d, d2h, edges = 0, 0.0, 0.0, 0, 0, 0
-    for step in range(e2e_steps):
+    walk_fn = _lib.tempest_walks_backward if direction else _lib.tempest_walks
+    for step in range(e2e_warm):
         for b in range(BATCHES_PER_STEP):
             s, d, t = host[step * BATCHES_PER_STEP + b]
+            _lib.tempest_ingest(eng.h, s.data_ptr(), d.data_ptr(), t.data_ptr(), int(s.shape[0]))
+        walk_fn(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7700 + step,
+                hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
+    for step in range(e2e_steps):
+        for b in range(BATCHES_PER_STEP):
+            s, d, t = host[(e2e_warm + step) * BATCHES_PER_STEP + b]
             t0 = time.perf_counter()
             _lib.tempest_ingest(eng.h, s.data_ptr(), d.data_ptr(), t.data_ptr(), int(s.shape[0]))
             ingest_s += time.perf_counter() - t0
             h2d += s.numel() * 4 + d.numel() * 4 + t.numel() * 8
             edges += int(s.shape[0])
         t0 = time.perf_counter()
-        walk_fn = _lib.tempest_walks_backward if direction else _lib.tempest_walks
         walk_fn(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7777 + step,
                 hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
         walk_s += time.perf_counter() - t0
         hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
-        # the bytes the call moved device to host (rows travel compacted: each
-        # walk's cells with its length and offset; the host writes the padding)
+        # the bytes the call moved device to host (whole rows for a share of
+        # the walks, each other walk's cells with its length and offset)
         d2h += _lib.tempest_last_walk_stats(eng.h).d2h_bytes
     return dict(value=hops / walk_s, unit="hops/s", h2d_bytes_per_step=h2d // e2e_steps,
                 d2h_bytes_per_step=d2h // e2e_steps, ingest_edges_per_s=edges / ingest_s, steps=e2e_steps)

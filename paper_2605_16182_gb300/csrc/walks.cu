@@ -767,11 +767,35 @@ struct DrawCtx {
     WalkCounters *cnt;
 };
 
+// With PAD, the first LANE_STAGE cells of each walk wait in shared memory
+// (LANE_STAGE + 1 words per lane, so that lanes writing their own cells and
+// the warp reading one lane's cells both stay off shared bank conflicts);
+// when the walk ends, the warp writes the row in one pass, cells and padding
+// together, so each 32-byte sector of the row is written whole by one store
+// instruction instead of once by scattered cell stores and again by the
+// padding (two partial writes of the same sector, merged in DRAM when L2
+// has evicted the first).  Cells past the staged ones go to the row directly.
+constexpr int LANE_STAGE = 8;
+constexpr int LANE_STAGE_STRIDE = LANE_STAGE + 1;
+
 template <class P, int MINB, bool N2V, bool BACK, bool PAD>
 __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, const P Pv, unsigned long long *next_walk)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
+    __shared__ int32_t s_node[PAD ? 256 * LANE_STAGE_STRIDE : 1];
+    __shared__ long long s_ts[PAD ? 256 * LANE_STAGE_STRIDE : 1];
+    const int my_stage = PAD ? (int)threadIdx.x * LANE_STAGE_STRIDE : 0;
+    // cell i of the lane's walk: staged (PAD, i < LANE_STAGE) or to its row
+    auto put = [&](const typename P::Ctx &c, int32_t i, int32_t nv, int64_t tv) {
+        if (PAD && i < LANE_STAGE) {
+            s_node[my_stage + i] = nv;
+            s_ts[my_stage + i] = (long long)tv;
+        } else {
+            Pv.nrow(c)[i] = nv;
+            Pv.trow(c)[i] = tv;
+        }
+    };
     typename P::Ctx cx;
     int64_t w = 0;
     int32_t v = 0, u = -1, len = 0, cap_len = 0, bias = 0;
@@ -816,15 +840,12 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
             cap_len = L;
             bias = b;
             mode = 2;
-            int32_t *nrow = Pv.nrow(cx);
-            int64_t *trow = Pv.trow(cx);
             if (V.m == 0) {
                 len = 0;
                 finish = true;
             } else if (Pv.policy(cx) == TEMPEST_START_PER_NODE) {
                 v = __ldg(V.pn_nodes + (int64_t)(Pv.wid(cx) / (uint64_t)Pv.pn_k(cx)));
-                nrow[0] = v;
-                trow[0] = INT64_MIN;
+                put(cx, 0, v, INT64_MIN);
                 len = 1;
                 u = -1;
                 t = BACK ? INT64_MAX - 1 : INT64_MIN;
@@ -849,10 +870,8 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
                     s0 = d0;
                     d0 = x;
                 }
-                nrow[0] = s0;
-                nrow[1] = d0;
-                trow[0] = INT64_MIN;
-                trow[1] = t0;
+                put(cx, 0, s0, INT64_MIN);
+                put(cx, 1, d0, t0);
                 len = 2;
                 u = s0;
                 v = d0;
@@ -893,8 +912,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
                 if (!ok) {
                     finish = true;  // every Node2Vec proposal rejected
                 } else {
-                    Pv.nrow(cx)[len] = e.other;
-                    Pv.trow(cx)[len] = e.ts;
+                    put(cx, len, e.other, e.ts);
                     hops++;
                     bytes += hop_model_bytes((int64_t)(g1 - g0));
                     len++;
@@ -905,9 +923,10 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
                 }
             }
         }
-        // rows of the walks that ended here: the whole warp writes their
-        // padding, 32 consecutive cells per streaming store (PAD; else one
-        // pass after the launch pads every row)
+        // rows of the walks that ended here: the whole warp writes each row,
+        // its staged cells and its padding, 32 consecutive cells per
+        // streaming store (PAD; else one pass after the launch pads every
+        // row)
         unsigned fin = __ballot_sync(0xffffffffu, finish);
         if (!PAD) {
             if (finish) {
@@ -925,6 +944,8 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
                 my_cap = Pv.cap(cx);
                 mode = 0;
             }
+            __syncwarp();  // the staged cells of every lane are visible to the warp
+            const int warp_stage = (int)(threadIdx.x & ~31u) * LANE_STAGE_STRIDE;
             while (fin) {
                 const int src = __ffs(fin) - 1;
                 fin &= fin - 1;
@@ -932,11 +953,20 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
                 int64_t *tr = reinterpret_cast<int64_t *>(__shfl_sync(0xffffffffu, my_t, src));
                 const int32_t l = __shfl_sync(0xffffffffu, my_len, src);
                 const int32_t cp = __shfl_sync(0xffffffffu, my_cap, src);
-                for (int32_t i = l + lane; i < cp; i += 32) {
-                    __stcs(nr + i, -1);
-                    __stcs(reinterpret_cast<long long *>(tr) + i, (long long)INT64_MIN);
+                const int sb = warp_stage + src * LANE_STAGE_STRIDE;
+                for (int32_t i = lane; i < cp; i += 32) {
+                    if (i >= LANE_STAGE && i < l) continue;  // written at its hop
+                    int32_t nv = -1;
+                    long long tv = (long long)INT64_MIN;
+                    if (i < l) {
+                        nv = s_node[sb + i];
+                        tv = s_ts[sb + i];
+                    }
+                    __stcs(nr + i, nv);
+                    __stcs(reinterpret_cast<long long *>(tr) + i, tv);
                 }
             }
+            __syncwarp();  // a lane's next walk stages its cells after these reads
         }
     }
     hops = warp_sum(hops);
