@@ -287,6 +287,7 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
     hln = torch.empty((n_walks,), dtype=torch.int32).pin_memory()
     torch.cuda.synchronize()
     hops, walk_s, ingest_s, h2d, d2h, edges = 0, 0.0, 0.0, 0, 0, 0
+    ingest_calls = []
     walk_fn = _lib.tempest_walks_backward if direction else _lib.tempest_walks
     for step in range(e2e_warm):
         for b in range(BATCHES_PER_STEP):
@@ -299,7 +300,8 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
             s, d, t = host[(e2e_warm + step) * BATCHES_PER_STEP + b]
             t0 = time.perf_counter()
             _lib.tempest_ingest(eng.h, s.data_ptr(), d.data_ptr(), t.data_ptr(), int(s.shape[0]))
-            ingest_s += time.perf_counter() - t0
+            ingest_calls.append(time.perf_counter() - t0)
+            ingest_s += ingest_calls[-1]
             h2d += s.numel() * 4 + d.numel() * 4 + t.numel() * 8
             edges += int(s.shape[0])
         t0 = time.perf_counter()
@@ -311,7 +313,9 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
         # the walks, each other walk's cells with its length and offset)
         d2h += _lib.tempest_last_walk_stats(eng.h).d2h_bytes
     return dict(value=hops / walk_s, unit="hops/s", h2d_bytes_per_step=h2d // e2e_steps,
-                d2h_bytes_per_step=d2h // e2e_steps, ingest_edges_per_s=edges / ingest_s, steps=e2e_steps)
+                d2h_bytes_per_step=d2h // e2e_steps, ingest_edges_per_s=edges / ingest_s, steps=e2e_steps,
+                ingest_call_ms={"p50": 1e3 * percentile(ingest_calls, 50), "max": 1e3 * max(ingest_calls)},
+                walk_call_ms=1e3 * walk_s / e2e_steps)
 
 
 # --------------------------------------------------------------------------
