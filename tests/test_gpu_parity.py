@@ -209,6 +209,36 @@ def test_host_and_device_outputs_agree(share):
         eng.set_tuning(_lib.TUNE_HOST_LINK_PCT, 101)
 
 
+@pytest.mark.parametrize("cap", [2, 3, 7, 8, 9, 12, 16, 33, 41, 64])
+def test_row_lengths_around_the_staged_cells(cap):
+    """A time-ordered chain 0 -> 1 -> ... -> 40 gives walks of every length
+    from 2 to 41 nodes (a walk from edge i runs to the chain's end), so rows
+    end before, at and after the cells a walker keeps on chip, at row widths
+    that are and are not multiples of 4; every form, device and host outputs,
+    and a mixed request with per-walk caps must give the oracle's rows."""
+    eng, orc = pair(0, True)
+    K = 40
+    ingest_both(eng, orc, np.arange(K), np.arange(1, K + 1), np.arange(1, K + 1))
+    check_walks(eng, orc, 2000, cap, seed=cap, biases=(0, 1))
+    o = orc.walks(2000, cap, bias=0, seed=cap)
+    assert set(np.unique(o[2])) == set(range(2, min(cap, K + 1) + 1))
+    node = np.full((2000, cap), 5, np.int32)
+    ts = np.full((2000, cap), 5, np.int64)
+    ln = np.full(2000, 5, np.int32)
+    _lib.tempest_walks(eng.h, 2000, cap, 0, 0, cap, node.ctypes.data, ts.ctypes.data, ln.ctypes.data)
+    assert_walks_bit_exact((node, ts, ln), o, "host outputs")
+    if cap >= 3:
+        lens = np.random.default_rng(cap).integers(2, cap + 1, 2000).astype(np.int32)
+        bias = np.zeros(2000, np.uint8)
+        om = orc.walks(2000, cap, max_len_arr=lens, bias_arr=bias, seed=cap + 1)
+        for sched in (_lib.SCHED_LANE, _lib.SCHED_STREAM):
+            eng.set_scheduler(sched)
+            g = [x.cpu().numpy() for x in eng.walks_mixed(torch.from_numpy(lens).cuda(), torch.from_numpy(bias).cuda(),
+                                                          seed=cap + 1, max_len_cap=cap)]
+            assert_walks_bit_exact(g, om, "mixed, sched %d" % sched)
+        eng.set_scheduler(_lib.SCHED_LANE)
+
+
 # ------------------------------------------------------------------ edges
 def test_empty_and_degenerate():
     eng, orc = pair(0, True)
