@@ -198,9 +198,10 @@ def run_ours(args, rank, world):
         return torch.cuda.Event(enable_timing=True)
 
     ingest_ms, walk_ms, walk_kernel_ms, hops, model_bytes, launches, edges = [], [], [], 0, 0, 0, 0
+    evict_ms, evicted = [], 0
 
     def one_step(step, timed):
-        nonlocal hops, model_bytes, launches, edges
+        nonlocal hops, model_bytes, launches, edges, evicted
         for b in range(BATCHES_PER_STEP):
             s, d, t = batches[step * BATCHES_PER_STEP + b]
             e0, e1 = ev(), ev()
@@ -210,6 +211,9 @@ def run_ours(args, rank, world):
             if timed:
                 e1.synchronize()
                 ingest_ms.append(e0.elapsed_time(e1))
+                if st["n_evicted"] > 0 and st["evict_ms"] > 0:
+                    evict_ms.append(st["evict_ms"])
+                    evicted += st["n_evicted"]
                 launches += st["launches"]
                 edges += int(s.shape[0])
         e0, e1 = ev(), ev()
@@ -255,7 +259,7 @@ def run_ours(args, rank, world):
                model_bytes=model_bytes, launches=launches, ingest_ms=ingest_ms, walk_ms=walk_ms,
                walk_kernel_ms=walk_kernel_ms, live=counts["m"], clocks=clk, gen_s=t_gen, n_walks=n_walks,
                n_nodes=counts["n_nodes"], G_tot=counts["G_tot"], Gn=counts["Gn"], tune=tune,
-               n_nodes_spec=spec.n_nodes)
+               n_nodes_spec=spec.n_nodes, evict_ms=evict_ms, evicted=evicted)
 
     # end to end through the C ABI with host buffers (one step, after the timed ones)
     if not args.no_e2e:
@@ -739,6 +743,14 @@ def main():
                        "ingest_batch_p99": percentile(res["ingest_ms"], 99),
                        "walk_call_p50": percentile(res["walk_ms"], 50),
                        "walk_call_p99": percentile(res["walk_ms"], 99)},
+        "eviction": {"evict_ms_p50": percentile(res["evict_ms"], 50) if res["evict_ms"] else 0.0,
+                     "evict_ms_p99": percentile(res["evict_ms"], 99) if res["evict_ms"] else 0.0,
+                     "evicted_per_batch": res["evicted"] / max(1, len(res["evict_ms"])),
+                     "evicted_edges_per_s": (res["evicted"] / (sum(res["evict_ms"]) / 1e3)
+                                             if res["evict_ms"] else 0.0),
+                     "batches": len(res["evict_ms"]),
+                     "time": "node view eviction kernels inside tempest_ingest (CUDA events); the store and "
+                             "the timestamp view evict by moving a head"},
         "hops_per_walk": res["hops"] / max(1, res["n_walks"] * len(res["walk_ms"])),
         "live_edges": res["live"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -118,6 +118,13 @@ typedef struct {
     int32_t has_cutoff;
     int32_t sorted_input;  /* the batch arrived in timestamp order */
     int64_t launches;      /* kernels this library launched for the batch */
+    double evict_ms;       /* device time of the node view's eviction (the
+                              per-node counts of the evicted edges and the
+                              advance of each touched node's head), from CUDA
+                              events on the handle's stream; the store and the
+                              timestamp view evict by moving a head, O(1).  0
+                              when nothing was evicted or the batch rebuilt
+                              the node view (eviction is then part of it) */
 } tempest_ingest_stats;
 
 /* Per-call walk report (valid once the call's work has finished). */

@@ -262,6 +262,8 @@ int tempest_destroy(tempest_t *h)
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     for (cudaEvent_t &e : h->kev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t &e : h->eev)
+        if (e) cudaEventDestroy(e);
     free_all(h);
     if (h->hstat) cudaFreeHost(h->hstat);
     if (h->hpin) cudaFreeHost(h->hpin);

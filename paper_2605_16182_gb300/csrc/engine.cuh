@@ -220,6 +220,8 @@ struct tempest {
     tempest_walk_stats last_ws{};
     cudaEvent_t kev[2] = {nullptr, nullptr};  // brackets the walk kernels of the last call
     bool kev_valid = false;
+    cudaEvent_t eev[2] = {nullptr, nullptr};  // brackets the node view's eviction of the last batch
+    bool eev_valid = false;
     int64_t pending_launches = 0;
     std::string err;
 };

@@ -327,6 +327,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     if (n >= (int64_t)INT32_MAX) return fail(h, TEMPEST_EINVAL, "tempest_ingest: batch of %lld edges too large",
                                              (long long)n);
     h->pending_launches = 0;
+    h->eev_valid = false;
     h->state_ver++;  // derived walk indexes are rebuilt on the next walk call
     if ((rc = ensure(h, h->dstat, sizeof(IngestScratch)))) return rc;
     if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
@@ -574,6 +575,11 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
         stats->has_cutoff = h->has_cutoff;
         stats->sorted_input = sorted ? 1 : 0;
         stats->launches = h->pending_launches;
+        float ms = 0.f;
+        // the events ran before the sync above; a rebuild after the append
+        // makes the batch's eviction part of the rebuild
+        stats->evict_ms = (h->eev_valid && !nv_full && cudaEventElapsedTime(&ms, h->eev[0], h->eev[1]) == cudaSuccess)
+                              ? (double)ms : 0.0;
     }
     return TEMPEST_OK;
 }

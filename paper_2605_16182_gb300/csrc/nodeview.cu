@@ -725,11 +725,16 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
     if (ne > 0) {
         if ((rc = ensure(h, h->ev_nodes, sizeof(int32_t) * (size_t)std::min(ne, N_old + 1), true))) return rc;
         const Items ei{ev_src, ev_dst, nullptr, directed};
+        for (cudaEvent_t &e : h->eev)
+            if (!e) cudaEventCreate(&e);
+        cudaEventRecord(h->eev[0], st);
         k_nv_evict_count<<<grid_for(h, ne), 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
                                                           h->ev_nodes.as<int32_t>(), dc);
         k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
             h->ev_nodes.as<int32_t>(), h->ev.as<int32_t>(), h->nrec.as<int4>(), h->ngr.as<NodeRange>(),
             h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->nev.as<int32_t>(), dc);
+        cudaEventRecord(h->eev[1], st);
+        h->eev_valid = true;
         h->pending_launches += 2;
     }
     if (nbe > 0) {

@@ -343,6 +343,7 @@ def test_sliding_window_moves_store_and_regions(directed):
     eng, orc = pair(-700, directed)
     rng = np.random.default_rng(5 + directed)
     t = 0
+    timed = 0
     for b in range(40):
         n = int(rng.integers(0, 400))
         s = rng.integers(0, 30 + b, n).astype(np.int32)
@@ -350,8 +351,15 @@ def test_sliding_window_moves_store_and_regions(directed):
         ts = (t + np.sort(rng.integers(0, 3 * n + 1, n))).astype(np.int64)
         if n:
             t = int(ts[-1])
-        ingest_both(eng, orc, s, d, ts)
+        st = ingest_both(eng, orc, s, d, ts)
         assert_state_equal(eng.state(), orc.state())
+        # the eviction's device time is reported when the batch evicted
+        # edges (0 when none were, or when the batch rebuilt the node view)
+        assert st["evict_ms"] >= 0.0
+        if st["n_evicted"] == 0:
+            assert st["evict_ms"] == 0.0
+        timed += st["evict_ms"] > 0.0
+    assert timed > 10
     check_walks(eng, orc, 3000, 16, seed=1, biases=(0, 2))
 
 
