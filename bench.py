@@ -291,7 +291,7 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
     hln = torch.empty((n_walks,), dtype=torch.int32).pin_memory()
     torch.cuda.synchronize()
     hops, walk_s, ingest_s, h2d, d2h, edges = 0, 0.0, 0.0, 0, 0, 0
-    ingest_calls = []
+    ingest_calls, walk_calls = [], []
     walk_fn = _lib.tempest_walks_backward if direction else _lib.tempest_walks
     for step in range(e2e_warm):
         for b in range(BATCHES_PER_STEP):
@@ -311,7 +311,8 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
         t0 = time.perf_counter()
         walk_fn(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7777 + step,
                 hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
-        walk_s += time.perf_counter() - t0
+        walk_calls.append(time.perf_counter() - t0)
+        walk_s += walk_calls[-1]
         hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
         # the bytes the call moved device to host (whole rows for a share of
         # the walks, each other walk's cells with its length and offset)
@@ -319,7 +320,7 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
     return dict(value=hops / walk_s, unit="hops/s", h2d_bytes_per_step=h2d // e2e_steps,
                 d2h_bytes_per_step=d2h // e2e_steps, ingest_edges_per_s=edges / ingest_s, steps=e2e_steps,
                 ingest_call_ms={"p50": 1e3 * percentile(ingest_calls, 50), "max": 1e3 * max(ingest_calls)},
-                walk_call_ms=1e3 * walk_s / e2e_steps)
+                walk_call_ms=1e3 * walk_s / e2e_steps, walk_calls_ms=[round(1e3 * x, 2) for x in walk_calls])
 
 
 # --------------------------------------------------------------------------

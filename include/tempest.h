@@ -354,7 +354,11 @@ enum {
     /* walks into host buffers: percent of the rows padded on the device and
      * copied whole (0-100, default 62); the others travel as their walks'
      * cells only and host threads write their rows and padding meanwhile */
-    TEMPEST_TUNE_HOST_LINK_PCT = 5
+    TEMPEST_TUNE_HOST_LINK_PCT = 5,
+    /* walks into host buffers: host threads that write the rows sent as
+     * cells (0-256; 0, the default: the CPUs this process may run on, from
+     * its affinity mask and cgroup CPU quota, at most 32) */
+    TEMPEST_TUNE_HOST_THREADS = 6
 };
 /* Set / read one knob.  EINVAL on an unknown knob or a value out of range. */
 int tempest_set_tuning(tempest_t *h, int knob, int64_t value);

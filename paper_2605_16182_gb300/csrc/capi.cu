@@ -1,7 +1,9 @@
 // capi.cu -- the extern "C" entry points declared in include/tempest.h, and
 // the handle's memory management.
+#include <sched.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -139,6 +141,31 @@ __global__ void k_compact_rows(const int32_t *__restrict__ node, const int64_t *
 }
 
 // Pinned host staging of at least `bytes` (kept, grown by half again).
+// CPUs this process may run on: its affinity mask, capped by a cgroup v2 CPU
+// quota ("quota period" in cpu.max) when one is set.  More threads than that
+// only time-slice, and past a quota the scheduler stalls them all until its
+// next period.
+static int host_cpus()
+{
+    static const int n = [] {
+        int c = (int)std::thread::hardware_concurrency();
+        cpu_set_t set;
+        CPU_ZERO(&set);
+        if (sched_getaffinity(0, sizeof(set), &set) == 0 && CPU_COUNT(&set) > 0) c = CPU_COUNT(&set);
+        if (FILE *f = fopen("/sys/fs/cgroup/cpu.max", "r")) {
+            char q[32] = {0};
+            long long per = 0;
+            if (fscanf(f, "%31s %lld", q, &per) == 2 && strcmp(q, "max") != 0 && per > 0) {
+                const long long quota = atoll(q);
+                if (quota > 0) c = std::min<long long>(c, std::max(1LL, quota / per));
+            }
+            fclose(f);
+        }
+        return std::max(1, c);
+    }();
+    return n;
+}
+
 static int ensure_pinned(tempest_t *h, size_t bytes)
 {
     if (h->hpin_bytes >= bytes) return TEMPEST_OK;
@@ -453,8 +480,8 @@ static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, 
     // rows [nd, n) and their padding on the host, in parallel threads, while
     // the copy engine moves rows [0, nd)
     if (nh > 0) {
-        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-        const int64_t nt = std::min<int64_t>(std::min<int64_t>(hw, 64), std::max<int64_t>(1, nh / 4096));
+        const int64_t want = h->host_threads > 0 ? h->host_threads : std::min(host_cpus(), 32);
+        const int64_t nt = std::min<int64_t>(want, std::max<int64_t>(1, nh / 4096));
         int32_t *node_h = node + nd * (int64_t)cap;
         int64_t *ts_h = ts + nd * (int64_t)cap;
         const int32_t *len_h = h_len + nd;

@@ -205,6 +205,7 @@ struct tempest {
     tw::DBuf cmp_off, cmp_stage;  // offsets and compacted cells of the rows on the device
     int64_t last_d2h = 0;      // bytes the last walk call copied device to host
     int host_link_pct = 62;    // percent of host-output rows copied whole (the rest expanded on the host)
+    int host_threads = 0;      // host threads expanding those rows (0: the CPUs the process may use, <= 32)
 
     // Temporal Node2Vec: return / in-out parameters; the live-pair table kept
     // by ingest once q != 1 (pt_cap slots, a power of two; pt_ub bounds the

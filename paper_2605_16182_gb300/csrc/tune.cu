@@ -137,6 +137,11 @@ int tempest_set_tuning(tempest_t *h, int knob, int64_t value)
                                                       (long long)value);
             h->host_link_pct = (int)value;
             return TEMPEST_OK;
+        case TEMPEST_TUNE_HOST_THREADS:
+            if (value < 0 || value > 256) return fail(h, TEMPEST_EINVAL, "tuning: host threads %lld outside [0, 256]",
+                                                      (long long)value);
+            h->host_threads = (int)value;
+            return TEMPEST_OK;
         default:
             return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
@@ -152,6 +157,7 @@ int tempest_get_tuning(tempest_t *h, int knob, int64_t *value)
         case TEMPEST_TUNE_STREAM_CTAS: *value = h->stream_ctas; return TEMPEST_OK;
         case TEMPEST_TUNE_PAD_PASS: *value = h->pad_pass; return TEMPEST_OK;
         case TEMPEST_TUNE_HOST_LINK_PCT: *value = h->host_link_pct; return TEMPEST_OK;
+        case TEMPEST_TUNE_HOST_THREADS: *value = h->host_threads; return TEMPEST_OK;
         default: return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
 }
