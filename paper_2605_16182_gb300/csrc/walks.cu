@@ -8,6 +8,7 @@
 // (seed, walk, hop), so the result is independent of how walks are mapped to
 // threads.
 #include <algorithm>
+#include <type_traits>
 
 #include "engine.cuh"
 #include "prims.cuh"
@@ -1026,6 +1027,11 @@ static void launch_stream_dir(tempest_t *h, const WalkView &V, const P &Pv, unsi
     else k_walks_stream<P, 4, false, BACK><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
 }
 
+// CTAs per SM the Node2Vec lane walker is built for: one request's walks fit
+// 64 registers without spills, the multi-request form needs more.
+template <class P>
+constexpr int LANE_N2V_MINB = std::is_same<P, OneReq>::value ? 4 : 3;
+
 template <class P, bool BACK, bool PAD>
 static void launch_lane_pad(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
                             cudaStream_t st, bool n2v)
@@ -1034,7 +1040,7 @@ static void launch_lane_pad(tempest_t *h, const WalkView &V, const P &Pv, unsign
     if (occ == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walks_lane<P, 4, false, BACK, PAD>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_lane<P, 5, false, BACK, PAD>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_lane<P, 3, true, BACK, PAD>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_lane<P, LANE_N2V_MINB<P>, true, BACK, PAD>, 256, 0);
         if (occ < 1) occ = 1;
         if (occ5 < 1) occ5 = 1;
         if (occn < 1) occn = 1;
@@ -1045,7 +1051,7 @@ static void launch_lane_pad(tempest_t *h, const WalkView &V, const P &Pv, unsign
     int64_t grid = (int64_t)h->num_sms * bps;
     const int64_t need = (total + 255) / 256;
     if (grid > need) grid = need;
-    if (n2v) k_walks_lane<P, 3, true, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    if (n2v) k_walks_lane<P, LANE_N2V_MINB<P>, true, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
     else if (wide) k_walks_lane<P, 5, false, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
     else k_walks_lane<P, 4, false, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
 }
