@@ -326,7 +326,7 @@ def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, 
 # --------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and --impl reference arm)
 # --------------------------------------------------------------------------
-def oracle_sample(seconds_budget=15.0, scale=0.01, n_walks=20_000, max_len=80):
+def oracle_sample(seconds_budget=15.0, scale=0.01, n_walks=4_000_000, max_len=80):
     """The oracle on the same workload scaled by `scale` (node count, batch
     and window): it ingests the stream up to the first walk point after the
     window is full, then draws exponential walks.  Returns rates."""
@@ -351,7 +351,7 @@ def oracle_sample(seconds_budget=15.0, scale=0.01, n_walks=20_000, max_len=80):
     t0 = time.perf_counter()
     hops = 0
     done = 0
-    chunk = 2000
+    chunk = 20_000
     while done < n_walks and time.perf_counter() - t0 < seconds_budget * 0.4:
         ids = list(range(done, done + chunk))
         import numpy as np
