@@ -189,6 +189,7 @@ def test_host_and_device_outputs_agree(share):
         ingest_both(eng, orc, s, d, t, on_gpu=False)
     eng.set_tuning(_lib.TUNE_HOST_LINK_PCT, share)
     assert eng.get_tuning(_lib.TUNE_HOST_LINK_PCT) == share
+    eng.set_tuning(_lib.TUNE_HOST_THREADS, {62: 0, 0: 1, 100: 0, 37: 5}[share])  # 0: the process's CPUs
     for n, L in ((3000, 9), (40_000, 13), (1, 5)):
         gd = eng.walks(n, L, bias=1, seed=11)
         torch.cuda.synchronize()

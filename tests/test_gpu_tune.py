@@ -27,12 +27,14 @@ def _walks(eng, bias, seed=9):
 def test_knobs_validate_and_round_trip():
     eng = _engine()
     for knob, bad in ((_lib.TUNE_BKT_LOG, 6), (_lib.TUNE_COOP_W_WARP, 0), (_lib.TUNE_COOP_MEGA, 100),
-                      (_lib.TUNE_STREAM_CTAS, -1), (_lib.TUNE_PAD_PASS, 2), (17, 0)):
+                      (_lib.TUNE_STREAM_CTAS, -1), (_lib.TUNE_PAD_PASS, 2), (_lib.TUNE_HOST_LINK_PCT, 101),
+                      (_lib.TUNE_HOST_THREADS, -1), (_lib.TUNE_HOST_THREADS, 257), (17, 0)):
         with pytest.raises(_lib.TempestError) as e:
             eng.set_tuning(knob, bad)
         assert e.value.code == _lib.TEMPEST_EINVAL
     for knob, val in ((_lib.TUNE_BKT_LOG, 4), (_lib.TUNE_COOP_W_WARP, 16), (_lib.TUNE_COOP_MEGA, 2048),
-                      (_lib.TUNE_STREAM_CTAS, 2), (_lib.TUNE_PAD_PASS, 1)):
+                      (_lib.TUNE_STREAM_CTAS, 2), (_lib.TUNE_PAD_PASS, 1), (_lib.TUNE_HOST_LINK_PCT, 30),
+                      (_lib.TUNE_HOST_THREADS, 3), (_lib.TUNE_HOST_THREADS, 0)):
         eng.set_tuning(knob, val)
         assert eng.get_tuning(knob) == val
 
