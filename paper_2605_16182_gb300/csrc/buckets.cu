@@ -43,7 +43,7 @@ namespace tw {
 namespace {
 
 constexpr int BKT_SHORT_RUN = 4;     // table entries a group's own lane writes
-constexpr int32_t BKT_COPY = 8192;   // table entries per copy task
+constexpr int32_t BKT_COPY = 2048;   // table entries per copy task
 
 // How a big node's table is built: the bucket width, and which part comes
 // from the previous build's table of the node (the buckets both tables cover,
@@ -227,10 +227,16 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
             else bkt[tb + K] = g1;
         }
         if (local < copy_tasks) {
+            // eight loads in flight per lane before their stores (the table
+            // stores could alias the loads for all the compiler knows)
             const int32_t e0 = local * BKT_COPY, e1 = min(ncopy, e0 + BKT_COPY);
-            for (int32_t e = e0 + lane; e < e1; e += 32) {
-                const int32_t x = __ldg(prev + src + e) + delta;
-                bkt[tb + e] = min(max(x, g0), g1);
+            for (int32_t e = e0 + lane; e < e1; e += 32 * 8) {
+                int32_t x[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) x[j] = e + 32 * j < e1 ? __ldg(prev + src + e + 32 * j) : 0;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (e + 32 * j < e1) bkt[tb + e + 32 * j] = min(max(x[j] + delta, g0), g1);
             }
             continue;
         }
@@ -257,40 +263,54 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
 #pragma unroll
                 for (int x = 0; x < 8; x++) tv[x] = gb + x < my1 ? __ldg(ngts + gb + x) : 0;
             }
+            // entries (kp, k] hold g; the last group adds (k, K] holding g1;
+            // entries below ncopy came from the previous table.  A short run
+            // (the common case: a bucket or a few per group) is written by
+            // its own lane here; long runs (time gaps that leave many buckets
+            // empty) are marked and written below by the whole warp
+            const int32_t kp0 = kp;
+            unsigned longm = 0;
 #pragma unroll
             for (int x = 0; x < 8; x++) {
                 const int32_t g = gb + x;
                 const bool valid = g < my1;
                 const int32_t k = valid ? (int32_t)((tv[x] >> s) - bfirst) : kp;
-                // entries (kp, k] hold g; the last group adds (k, K] holding
-                // g1; entries below ncopy came from the previous table
-                const bool last = valid && g == g1 - 1;
                 const int32_t lo_k = max(kp + 1, ncopy);
-                const int32_t hi_k = last ? K : k;
+                const int32_t hi_k = (valid && g == g1 - 1) ? K : k;
                 const int32_t cnt = valid && hi_k >= lo_k ? hi_k - lo_k + 1 : 0;
-                // a short run (the common case: about one bucket per group) is
-                // written by its own lane; long runs (time gaps that leave many
-                // buckets empty) by the whole warp, 32 entries per store
-                if (cnt <= BKT_SHORT_RUN) {
-                    for (int32_t e = 0; e < cnt; e++) {
-                        const int32_t kk = lo_k + e;
-                        bkt[tb + kk] = kk <= k ? g : g1;
-                    }
-                }
-                unsigned longs = __ballot_sync(0xffffffffu, cnt > BKT_SHORT_RUN);
-                while (longs) {
-                    const int r = __ffs(longs) - 1;
-                    longs &= longs - 1;
-                    const int32_t r_lo = __shfl_sync(0xffffffffu, lo_k, r);
-                    const int32_t r_cnt = __shfl_sync(0xffffffffu, cnt, r);
-                    const int32_t r_k = __shfl_sync(0xffffffffu, k, r);
-                    const int32_t r_g = __shfl_sync(0xffffffffu, g, r);
-                    for (int32_t e = lane; e < r_cnt; e += 32) {
-                        const int32_t kk = r_lo + e;
-                        bkt[tb + kk] = kk <= r_k ? r_g : g1;
-                    }
+                if (cnt > BKT_SHORT_RUN) {
+                    longm |= 1u << x;
+                } else if (cnt > 0) {
+                    bkt[tb + lo_k] = lo_k <= k ? g : g1;
+                    for (int32_t kk = lo_k + 1; kk <= hi_k; kk++) bkt[tb + kk] = kk <= k ? g : g1;
                 }
                 kp = k;
+            }
+            if (__any_sync(0xffffffffu, longm != 0)) {
+                int32_t kq = kp0;
+#pragma unroll
+                for (int x = 0; x < 8; x++) {
+                    const int32_t g = gb + x;
+                    const bool valid = g < my1;
+                    const int32_t k = valid ? (int32_t)((tv[x] >> s) - bfirst) : kq;
+                    const int32_t lo_k = max(kq + 1, ncopy);
+                    const int32_t hi_k = (valid && g == g1 - 1) ? K : k;
+                    const int32_t cnt = (longm >> x) & 1u ? hi_k - lo_k + 1 : 0;
+                    unsigned longs = __ballot_sync(0xffffffffu, cnt > 0);
+                    while (longs) {  // 32 entries per store
+                        const int r = __ffs(longs) - 1;
+                        longs &= longs - 1;
+                        const int32_t r_lo = __shfl_sync(0xffffffffu, lo_k, r);
+                        const int32_t r_cnt = __shfl_sync(0xffffffffu, cnt, r);
+                        const int32_t r_k = __shfl_sync(0xffffffffu, k, r);
+                        const int32_t r_g = __shfl_sync(0xffffffffu, g, r);
+                        for (int32_t e = lane; e < r_cnt; e += 32) {
+                            const int32_t kk = r_lo + e;
+                            bkt[tb + kk] = kk <= r_k ? r_g : g1;
+                        }
+                    }
+                    kq = k;
+                }
             }
         }
     }
