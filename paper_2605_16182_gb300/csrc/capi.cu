@@ -488,12 +488,26 @@ static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, 
         if (nt <= 1) {
             expand_rows(0, nh, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
         } else {
+            // ranges k >= 1 go to new threads and range 0 to this one; a
+            // range whose thread cannot start (no exception crosses the C
+            // ABI) is written here too
+            bool started[256] = {};  // nt <= 256 (the knob's range; automatic <= 32)
             std::vector<std::thread> th;
-            th.reserve((size_t)nt);
-            for (int64_t k = 0; k < nt; k++) {
-                const int64_t i0 = nh * k / nt, i1 = nh * (k + 1) / nt;
-                th.emplace_back(expand_rows, i0, i1, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
+            try {
+                th.reserve((size_t)nt);
+            } catch (...) {
             }
+            for (int64_t k = 1; k < nt; k++) {
+                const int64_t i0 = nh * k / nt, i1 = nh * (k + 1) / nt;
+                try {
+                    th.emplace_back(expand_rows, i0, i1, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
+                    started[k] = true;
+                } catch (...) {
+                }
+            }
+            expand_rows(0, nh / nt, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
+            for (int64_t k = 1; k < nt; k++)
+                if (!started[k]) expand_rows(nh * k / nt, nh * (k + 1) / nt, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
             for (auto &x : th) x.join();
         }
     }
