@@ -288,56 +288,71 @@ int launch_wave(tempest_server *s, tempest_server::Wave &wv, int &rc)
 
 }  // namespace
 
+// A host allocation inside a C ABI call failed (the containers of the
+// request queue and the wave tables): report it as ENOMEM.
+static int host_oom(tempest_t *h, const char *what) noexcept
+{
+    try {
+        if (h) fail(h, TEMPEST_ENOMEM, "%s: host memory exhausted", what);
+    } catch (...) {
+    }
+    return TEMPEST_ENOMEM;
+}
+
 extern "C" {
 
 int tempest_walks_batch(tempest_t *h, const tempest_walk_request *reqs, int n_req)
 {
-    if (!h) return TEMPEST_EINVAL;
-    if (n_req < 0 || (n_req > 0 && !reqs)) return fail(h, TEMPEST_EINVAL, "tempest_walks_batch: bad request list");
-    h->last_ws = tempest_walk_stats{};
-    if (n_req == 0) return TEMPEST_OK;
-    // one launch per direction present (a launch reads one view); each
-    // direction's requests keep their own offsets from 0
-    std::vector<tempest_walk_request> part[2];
-    for (int i = 0; i < n_req; i++) part[reqs[i].direction == 1 ? 1 : 0].push_back(reqs[i]);
-    std::vector<ReqDesc> tab[2];
-    int64_t total[2] = {0, 0};
-    int n[2] = {0, 0};
-    int rc;
-    for (int d = 0; d < 2; d++) {
-        // validation runs on the caller's request list order within a direction
-        tab[d].resize(part[d].size());
-        if (part[d].empty()) continue;
-        if ((rc = build_table(h, part[d].data(), (int)part[d].size(), tab[d].data(), total[d]))) return rc;
-        n[d] = compact_table(tab[d].data(), (int)part[d].size());
+    try {
+        if (!h) return TEMPEST_EINVAL;
+        if (n_req < 0 || (n_req > 0 && !reqs)) return fail(h, TEMPEST_EINVAL, "tempest_walks_batch: bad request list");
+        h->last_ws = tempest_walk_stats{};
+        if (n_req == 0) return TEMPEST_OK;
+        // one launch per direction present (a launch reads one view); each
+        // direction's requests keep their own offsets from 0
+        std::vector<tempest_walk_request> part[2];
+        for (int i = 0; i < n_req; i++) part[reqs[i].direction == 1 ? 1 : 0].push_back(reqs[i]);
+        std::vector<ReqDesc> tab[2];
+        int64_t total[2] = {0, 0};
+        int n[2] = {0, 0};
+        int rc;
+        for (int d = 0; d < 2; d++) {
+            // validation runs on the caller's request list order within a direction
+            tab[d].resize(part[d].size());
+            if (part[d].empty()) continue;
+            if ((rc = build_table(h, part[d].data(), (int)part[d].size(), tab[d].data(), total[d]))) return rc;
+            n[d] = compact_table(tab[d].data(), (int)part[d].size());
+        }
+        const size_t tb0 = (sizeof(ReqDesc) * (size_t)(n[0] > 0 ? n[0] : 1) + 255) & ~(size_t)255;
+        const size_t tb1 = sizeof(ReqDesc) * (size_t)(n[1] > 0 ? n[1] : 1);
+        if ((rc = ensure(h, h->in_stage, tb0 + tb1 + 256, true))) return rc;
+        if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
+        char *stage = h->in_stage.as<char>();
+        // the tables are small: a synchronous copy keeps the host arrays reusable
+        for (int d = 0; d < 2; d++)
+            if (n[d] && (rc = cuda_check(h, cudaMemcpyAsync(stage + (d ? tb0 : 0), tab[d].data(), sizeof(ReqDesc) * n[d],
+                                                            cudaMemcpyHostToDevice, h->stream),
+                                         "batch table")))
+                return rc;
+        if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "batch table"))) return rc;
+        h->kev_valid = false;
+        int launches = 0;
+        for (int d = 0; d < 2; d++) {
+            if (!n[d] && (d == 1 || n[1])) continue;  // an empty batch still clears the counters
+            if ((rc = prepare_for(h, d, tab[d].data(), n[d]))) return rc;
+            // the second launch adds to the first one's counters
+            rc = walks_multi_launch(h, d, reinterpret_cast<ReqDesc *>(stage + (d ? tb0 : 0)), n[d], total[d],
+                                    h->wcnt.as<WalkCounters>(), h->stream, launches == 0,
+                                    table_may_n2v(tab[d].data(), n[d]));
+            if (rc) return rc;
+            launches++;
+        }
+        h->last_ws.n_walks = total[0] + total[1];
+        h->last_ws.launches = launches;
+        return cuda_check(h, cudaGetLastError(), "walks batch");
+    } catch (...) {  // no C++ exception crosses the C ABI
+        return host_oom(h, "tempest_walks_batch");
     }
-    const size_t tb0 = (sizeof(ReqDesc) * (size_t)(n[0] > 0 ? n[0] : 1) + 255) & ~(size_t)255;
-    const size_t tb1 = sizeof(ReqDesc) * (size_t)(n[1] > 0 ? n[1] : 1);
-    if ((rc = ensure(h, h->in_stage, tb0 + tb1 + 256, true))) return rc;
-    if ((rc = ensure(h, h->wcnt, sizeof(WalkCounters)))) return rc;
-    char *stage = h->in_stage.as<char>();
-    // the tables are small: a synchronous copy keeps the host arrays reusable
-    for (int d = 0; d < 2; d++)
-        if (n[d] && (rc = cuda_check(h, cudaMemcpyAsync(stage + (d ? tb0 : 0), tab[d].data(), sizeof(ReqDesc) * n[d],
-                                                        cudaMemcpyHostToDevice, h->stream),
-                                     "batch table")))
-            return rc;
-    if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "batch table"))) return rc;
-    h->kev_valid = false;
-    int launches = 0;
-    for (int d = 0; d < 2; d++) {
-        if (!n[d] && (d == 1 || n[1])) continue;  // an empty batch still clears the counters
-        if ((rc = prepare_for(h, d, tab[d].data(), n[d]))) return rc;
-        // the second launch adds to the first one's counters
-        rc = walks_multi_launch(h, d, reinterpret_cast<ReqDesc *>(stage + (d ? tb0 : 0)), n[d], total[d],
-                                h->wcnt.as<WalkCounters>(), h->stream, launches == 0,
-                                table_may_n2v(tab[d].data(), n[d]));
-        if (rc) return rc;
-        launches++;
-    }
-    h->last_ws.n_walks = total[0] + total[1];
-    h->last_ws.launches = launches;
-    return cuda_check(h, cudaGetLastError(), "walks batch");
 }
 
 int tempest_server_create(tempest_t *h, size_t arena_bytes, int64_t max_wave_walks, int max_inflight,
@@ -388,100 +403,112 @@ int tempest_server_destroy(tempest_server *s)
 
 int tempest_server_submit_walks(tempest_server *s, const tempest_walk_request *req, uint64_t *ticket)
 {
-    if (!s || !req || !ticket) return TEMPEST_EINVAL;
-    tempest_server::Req r;
-    r.kind = 0;
-    r.w = *req;
-    r.arena_out = !req->node && !req->ts && !req->len;
-    if (r.arena_out && !s->arena_bytes)
-        return fail(s->h, TEMPEST_EINVAL, "server: request without outputs and no output arena");
-    r.t_submit = now_s();
-    const uint64_t id = s->next_id++;
-    s->reqs.emplace(id, r);
-    s->queue.push_back(id);
-    *ticket = id;
-    return TEMPEST_OK;
+    try {
+        if (!s || !req || !ticket) return TEMPEST_EINVAL;
+        tempest_server::Req r;
+        r.kind = 0;
+        r.w = *req;
+        r.arena_out = !req->node && !req->ts && !req->len;
+        if (r.arena_out && !s->arena_bytes)
+            return fail(s->h, TEMPEST_EINVAL, "server: request without outputs and no output arena");
+        r.t_submit = now_s();
+        const uint64_t id = s->next_id++;
+        s->reqs.emplace(id, r);
+        s->queue.push_back(id);
+        *ticket = id;
+        return TEMPEST_OK;
+    } catch (...) {  // no C++ exception crosses the C ABI
+        return host_oom(s ? s->h : nullptr, "tempest_server_submit_walks");
+    }
 }
 
 int tempest_server_submit_ingest(tempest_server *s, const int32_t *src, const int32_t *dst, const int64_t *ts,
                                  int64_t n, uint64_t *ticket)
 {
-    if (!s || !ticket) return TEMPEST_EINVAL;
-    tempest_server::Req r;
-    r.kind = 1;
-    r.src = src;
-    r.dst = dst;
-    r.ts = ts;
-    r.n = n;
-    r.t_submit = now_s();
-    const uint64_t id = s->next_id++;
-    s->reqs.emplace(id, r);
-    s->queue.push_back(id);
-    *ticket = id;
-    return TEMPEST_OK;
+    try {
+        if (!s || !ticket) return TEMPEST_EINVAL;
+        tempest_server::Req r;
+        r.kind = 1;
+        r.src = src;
+        r.dst = dst;
+        r.ts = ts;
+        r.n = n;
+        r.t_submit = now_s();
+        const uint64_t id = s->next_id++;
+        s->reqs.emplace(id, r);
+        s->queue.push_back(id);
+        *ticket = id;
+        return TEMPEST_OK;
+    } catch (...) {  // no C++ exception crosses the C ABI
+        return host_oom(s ? s->h : nullptr, "tempest_server_submit_ingest");
+    }
 }
 
 int tempest_server_progress(tempest_server *s, int *n_completed)
 {
-    if (!s) return TEMPEST_EINVAL;
-    int done = 0;
-    for (auto &wv : s->waves) {
-        if (!wv.busy) continue;
-        const cudaError_t e = cudaEventQuery(wv.ev);
-        if (e == cudaErrorNotReady) continue;
-        int st = (e == cudaSuccess) ? 2 : TEMPEST_ECUDA;
-        if (e != cudaSuccess) cudaGetLastError();
-        if (st == 2) {
-            WalkCounters hc;
-            const WalkCounters *cnt =
-                reinterpret_cast<const WalkCounters *>(wv.table.as<char>() + sizeof(ReqDesc) * (size_t)wv.cap);
-            if (cudaMemcpy(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost) != cudaSuccess) {
-                cudaGetLastError();
-                st = TEMPEST_ECUDA;
-            } else if (hc.status) {
-                st = TEMPEST_EINVAL;  // a request table or per-walk check failed
-                fail(s->h, TEMPEST_EINVAL, "server: wave check failed (code 0x%llx)", (unsigned long long)hc.status);
+    try {
+        if (!s) return TEMPEST_EINVAL;
+        int done = 0;
+        for (auto &wv : s->waves) {
+            if (!wv.busy) continue;
+            const cudaError_t e = cudaEventQuery(wv.ev);
+            if (e == cudaErrorNotReady) continue;
+            int st = (e == cudaSuccess) ? 2 : TEMPEST_ECUDA;
+            if (e != cudaSuccess) cudaGetLastError();
+            if (st == 2) {
+                WalkCounters hc;
+                const WalkCounters *cnt =
+                    reinterpret_cast<const WalkCounters *>(wv.table.as<char>() + sizeof(ReqDesc) * (size_t)wv.cap);
+                if (cudaMemcpy(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                    cudaGetLastError();
+                    st = TEMPEST_ECUDA;
+                } else if (hc.status) {
+                    st = TEMPEST_EINVAL;  // a request table or per-walk check failed
+                    fail(s->h, TEMPEST_EINVAL, "server: wave check failed (code 0x%llx)", (unsigned long long)hc.status);
+                }
             }
+            const double t = now_s();
+            for (uint64_t id : wv.ids) {
+                s->reqs[id].state = st;
+                s->reqs[id].t_done = t;
+                done++;
+            }
+            wv.ids.clear();
+            wv.busy = false;
         }
-        const double t = now_s();
-        for (uint64_t id : wv.ids) {
-            s->reqs[id].state = st;
-            s->reqs[id].t_done = t;
-            done++;
+        int rc = TEMPEST_OK;
+        while (!s->queue.empty()) {
+            const uint64_t id = s->queue.front();
+            tempest_server::Req &r = s->reqs[id];
+            if (r.kind == 1) {
+                bool busy = false;
+                for (auto &wv : s->waves) busy |= wv.busy;
+                if (busy) break;  // ingest is an epoch barrier
+                r.t_start = now_s();
+                r.state = 1;
+                const int irc = tempest_ingest(s->h, r.src, r.dst, r.ts, r.n, nullptr);
+                r.state = irc ? irc : 2;
+                r.t_done = now_s();
+                s->queue.pop_front();
+                s->n_ingests++;
+                done++;
+                continue;
+            }
+            int free_slot = -1, inflight = 0;
+            for (int i = 0; i < 2; i++) {
+                if (s->waves[i].busy) inflight++;
+                else if (free_slot < 0) free_slot = i;
+            }
+            if (free_slot < 0 || inflight >= s->max_inflight) break;
+            const int took = launch_wave(s, s->waves[free_slot], rc);
+            if (rc) break;
+            if (took == 0) break;  // head waits for output memory
         }
-        wv.ids.clear();
-        wv.busy = false;
+        if (n_completed) *n_completed = done;
+        return rc;
+    } catch (...) {  // no C++ exception crosses the C ABI
+        return host_oom(s ? s->h : nullptr, "tempest_server_progress");
     }
-    int rc = TEMPEST_OK;
-    while (!s->queue.empty()) {
-        const uint64_t id = s->queue.front();
-        tempest_server::Req &r = s->reqs[id];
-        if (r.kind == 1) {
-            bool busy = false;
-            for (auto &wv : s->waves) busy |= wv.busy;
-            if (busy) break;  // ingest is an epoch barrier
-            r.t_start = now_s();
-            r.state = 1;
-            const int irc = tempest_ingest(s->h, r.src, r.dst, r.ts, r.n, nullptr);
-            r.state = irc ? irc : 2;
-            r.t_done = now_s();
-            s->queue.pop_front();
-            s->n_ingests++;
-            done++;
-            continue;
-        }
-        int free_slot = -1, inflight = 0;
-        for (int i = 0; i < 2; i++) {
-            if (s->waves[i].busy) inflight++;
-            else if (free_slot < 0) free_slot = i;
-        }
-        if (free_slot < 0 || inflight >= s->max_inflight) break;
-        const int took = launch_wave(s, s->waves[free_slot], rc);
-        if (rc) break;
-        if (took == 0) break;  // head waits for output memory
-    }
-    if (n_completed) *n_completed = done;
-    return rc;
 }
 
 int tempest_server_status(tempest_server *s, uint64_t ticket, int *state, int32_t **node, int64_t **ts,
@@ -513,24 +540,28 @@ int tempest_server_release(tempest_server *s, uint64_t ticket)
 
 int tempest_server_drain(tempest_server *s)
 {
-    if (!s) return TEMPEST_EINVAL;
-    int rc = TEMPEST_OK;
-    while (true) {
-        int n = 0;
-        if ((rc = tempest_server_progress(s, &n))) return rc;
-        bool busy = !s->queue.empty();
-        for (auto &wv : s->waves) busy |= wv.busy;
-        if (!busy) return TEMPEST_OK;
-        bool waiting = false;
-        for (auto &wv : s->waves)
-            if (wv.busy) {
-                cudaEventSynchronize(wv.ev);
-                waiting = true;
+    try {
+        if (!s) return TEMPEST_EINVAL;
+        int rc = TEMPEST_OK;
+        while (true) {
+            int n = 0;
+            if ((rc = tempest_server_progress(s, &n))) return rc;
+            bool busy = !s->queue.empty();
+            for (auto &wv : s->waves) busy |= wv.busy;
+            if (!busy) return TEMPEST_OK;
+            bool waiting = false;
+            for (auto &wv : s->waves)
+                if (wv.busy) {
+                    cudaEventSynchronize(wv.ev);
+                    waiting = true;
+                }
+            if (!waiting && !s->queue.empty()) {
+                // the head waits for arena memory that only a release can free
+                return fail(s->h, TEMPEST_EBUSY, "server: queue head needs output memory held by unreleased results");
             }
-        if (!waiting && !s->queue.empty()) {
-            // the head waits for arena memory that only a release can free
-            return fail(s->h, TEMPEST_EBUSY, "server: queue head needs output memory held by unreleased results");
         }
+    } catch (...) {  // no C++ exception crosses the C ABI
+        return host_oom(s ? s->h : nullptr, "tempest_server_drain");
     }
 }
 
