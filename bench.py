@@ -106,6 +106,13 @@ def recorded_traffic(hops, kernel):
 
 
 class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 50 ms, started before
+    the work it brackets (nvidia-smi needs a moment to start); stop() keeps
+    the samples whose timestamps fall inside the timed region."""
+    FIELDS = ["timestamp", "index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
     def __init__(self):
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
@@ -115,15 +122,15 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
-                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=self.f, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self, gpu_index=0):
+    def stop(self, gpu_index=0, t0=None, t1=None):
+        """Summary of the samples in [t0, t1] (wall clock, time.time()); all
+        samples when none falls there."""
+        import datetime
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -132,24 +139,28 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != gpu_index:
+            if len(parts) < 10 or not parts[1].isdigit() or int(parts[1]) != gpu_index:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                when = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                when = None
+            try:
+                rows.append((when, float(parts[2]), float(parts[3]),
+                             [nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [r for r in rows if r[0] is not None and t0 is not None and t0 - 0.05 <= r[0] <= t1 + 0.05]
+        use = inside or rows
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": use[-1][2],
+                "reasons": sorted({nm for r in use for nm in r[3]}), "samples": len(use),
+                "window": "timed steps" if inside else "autotune and timed steps"}
 
 
 # --------------------------------------------------------------------------
@@ -232,24 +243,28 @@ def run_ours(args, rank, world):
 
     for s in range(warm):
         one_step(s, False)
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start()  # running well before the timed steps
     tune = None
     if args.autotune:
         # the autotuner times candidate settings on the warmed-up window
         # (outside the timed region) and leaves the fastest selected
         tune = eng.autotune(n_walks, L, bias=bias_id, seed=seed_base + 99, forms=True, per_ingest=True)
-    clocks = ClockSampler()
-    if rank == 0:
-        clocks.start()
+    else:
+        time.sleep(0.5)
     barrier(world)
     torch.cuda.synchronize()
     t_all0, t_all1 = ev(), ev()
+    wall0 = time.time()
     t_all0.record(stream)
     for s in range(warm, warm + steps):
         one_step(s, True)
     t_all1.record(stream)
     torch.cuda.synchronize()
+    wall1 = time.time()
     barrier(world)
-    clk = clocks.stop(dev.index or 0) if rank == 0 else None
+    clk = clocks.stop(dev.index or 0, wall0, wall1) if rank == 0 else None
     total_ms = t_all0.elapsed_time(t_all1)
 
     walk_s = sum(walk_ms) / 1e3
