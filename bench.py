@@ -401,7 +401,11 @@ def run_reference(args, rank):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "hops/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64", "data": "synthetic",
-           "config": {"workload": "billion-edge-stream-100M-nodes-1B-edges (oracle on a 1/100 sample)"},
+           "config": {"workload": "billion-edge-stream-100M-nodes-1B-edges", "nodes": 100_000_000,
+                      "batch_edges": 10_000_000, "window_edges": 200_000_000, "max_len": 80, "bias": "exponential",
+                      "direction": "forward", "start": "uniform edge",
+                      "oracle_sample": "each step the oracle on the stream scaled by 1/100 (nodes, batch, window), "
+                                       "walks of the same length and bias"},
            "cpu_baseline": {"value": v, "unit": "hops/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
            "ingest_edges_per_s": last["edges_per_s"],
            "e2e": {"value": v, "unit": "hops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
