@@ -66,6 +66,8 @@ def parse():
                    help="keep --sched instead of letting the autotuner pick the walk form and knobs")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--clock-log", default=None,
+                   help="file for the raw nvidia-smi clock samples (default: a file in the temp directory)")
     return p.parse_args()
 
 
@@ -113,9 +115,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
 
-    def __init__(self):
+    def __init__(self, path=None):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), "tempest_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -243,7 +246,7 @@ def run_ours(args, rank, world):
 
     for s in range(warm):
         one_step(s, False)
-    clocks = ClockSampler()
+    clocks = ClockSampler(args.clock_log)
     if rank == 0:
         clocks.start()  # running well before the timed steps
     tune = None
