@@ -19,7 +19,7 @@ Printed (rank 0, one JSON line):
 Before the timed steps the autotuner picks the walk form and its knobs on the
 warmed-up window (outside the timing; --no-autotune keeps --sched).
 
-``--impl reference`` times the CPU oracle (the reference arm of this build).
+``--impl reference`` times the CPU oracle (the reference arm).
 Under torchrun every rank holds a replica of the window and draws its own
 walks (replicas only: nothing is exchanged on the data path).
 """

@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(256, MINB) k_walks_lane(const WalkView V, cons
             int32_t L;
             int b;
             Pv.open(w, cx, L, b);
-            if (!N2V && b == BIAS_NODE2VEC) b = BIAS_EXP;  // the host runs this build only when that is exact
+            if (!N2V && b == BIAS_NODE2VEC) b = BIAS_EXP;  // launched only when that is exact (p = q = 1)
             cap_len = L;
             bias = b;
             mode = 2;
