@@ -91,3 +91,32 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_enum_constants_match_the_header(tmp_path):
+    """Every enumerator of include/tempest.h that the binding mirrors (knobs,
+    forms, biases, start policies, status codes) has the header's value."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "tempest.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(TEMPEST_[A-Z0-9_]+)\s*=", txt)))
+    pairs = []
+    for n in names:
+        short = n[len("TEMPEST_"):]
+        if hasattr(_lib, short):
+            pairs.append((n, getattr(_lib, short)))
+        elif hasattr(_lib, n):
+            pairs.append((n, getattr(_lib, n)))
+    assert len(pairs) >= 20
+    lines = ['#include <stdio.h>', '#include "tempest.h"', "int main(void) {"]
+    lines += ['printf("%s %%lld\\n", (long long)%s);' % (n, n) for n, _ in pairs]
+    lines.append("return 0; }")
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "enums"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().split("\n") if line)
+    for n, v in pairs:
+        assert int(got[n]) == int(v), n
