@@ -219,8 +219,12 @@ int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const i
  * Outputs, row-major with row stride max_len: node int32[n_walks*max_len],
  * ts int64[n_walks*max_len] (ts of node 0 is INT64_MIN; padding is node -1,
  * ts INT64_MIN), len int32[n_walks] (nodes written; 0 on an empty window).
- * EINVAL on n_walks < 0, max_len < 2, bad bias / start policy or NULL
- * outputs. */
+ * The outputs may be device or host memory (each pointer is classified);
+ * device outputs are written by the kernels in stream order, host outputs
+ * are complete when the call returns (see tempest_walk_stats.d2h_bytes for
+ * how they travel; pinned host buffers let the copy overlap the host-side
+ * row writes).  EINVAL on n_walks < 0, max_len < 2, bad bias / start policy
+ * or NULL outputs. */
 int tempest_walks(tempest_t *h, int64_t n_walks, int32_t max_len, int bias, int start_policy,
                   uint64_t seed, int32_t *node, int64_t *ts, int32_t *len);
 
