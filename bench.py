@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--workload", default="stream", choices=["stream", "batched", "serve"])
     p.add_argument("--requests", type=int, default=2000)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=10, help="timed steps of the host-buffer (e2e) leg")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep --sched instead of letting the autotuner pick the walk form and knobs")
     p.add_argument("--no-cpu", action="store_true")
@@ -169,6 +170,35 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def batch_plan(steps, warmup, per_step=BATCHES_PER_STEP):
+    """The run's steps as (step, timed, first batch, last batch): the warm-up
+    steps, then the timed ones; each step ingests per_step consecutive
+    batches of the stream."""
+    return [(s, s >= warmup, s * per_step, (s + 1) * per_step) for s in range(warmup + steps)]
+
+
+class StepFeeder:
+    """Generates a step's batches on the device just before the step runs
+    (outside its timed region), carrying the stream's last timestamp from one
+    step to the next.  A run longer than the stream's 100 batches continues
+    it with the same generator (ids, gap rates and their switching); under the
+    count window the live set then stays at its steady-state size."""
+
+    def __init__(self, spec, device):
+        self.spec, self.device = spec, device
+        self.next, self.ts_base = 0, None
+
+    def take(self, first, last):
+        if first != self.next:
+            raise ValueError("batches must be taken in stream order (next %d, asked %d)" % (self.next, first))
+        out = [(s, d, t) for _, s, d, t in self.spec.batches(device=self.device, first=first, last=last,
+                                                             extend=True, ts_base=self.ts_base)]
+        if out and self.spec.ts_kind != "uniform":
+            self.ts_base = int(out[-1][2][-1].item())
+        self.next = last
+        return out
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2605_16182_gb300 import _lib, synth
@@ -179,14 +209,8 @@ def run_ours(args, rank, world):
     n_walks = max(1, int(args.walks * args.scale)) if args.scale != 1.0 else args.walks
     L = args.max_len
     steps, warm = args.steps, args.warmup
-    n_batches = (steps + warm) * BATCHES_PER_STEP
-
-    # inputs resident in HBM before timing: every batch of the run
-    t_gen = time.time()
-    gen = spec.batches(device=dev, first=0, last=n_batches)
-    batches = [(s, d, t) for _, s, d, t in gen]
-    torch.cuda.synchronize()
-    t_gen = time.time() - t_gen
+    plan = batch_plan(steps, warm)
+    feeder = StepFeeder(spec, dev)
 
     stream = torch.cuda.current_stream(dev)
     eng = _lib.Engine(window=spec.window, directed=True, device=str(dev), stream=stream)
@@ -212,12 +236,11 @@ def run_ours(args, rank, world):
         return torch.cuda.Event(enable_timing=True)
 
     ingest_ms, walk_ms, walk_kernel_ms, hops, model_bytes, launches, edges = [], [], [], 0, 0, 0, 0
-    evict_ms, evicted = [], 0
+    evict_ms, evicted, step_ms, gen_s = [], 0, [], 0.0
 
-    def one_step(step, timed):
+    def one_step(batches, step, timed):
         nonlocal hops, model_bytes, launches, edges, evicted
-        for b in range(BATCHES_PER_STEP):
-            s, d, t = batches[step * BATCHES_PER_STEP + b]
+        for s, d, t in batches:
             e0, e1 = ev(), ev()
             e0.record(stream)
             st = eng.ingest(s, d, t)
@@ -244,110 +267,148 @@ def run_ours(args, rank, world):
             model_bytes += ws["model_bytes"]
             launches += ws["launches"]
 
-    for s in range(warm):
-        one_step(s, False)
     clocks = ClockSampler(args.clock_log)
-    if rank == 0:
-        clocks.start()  # running well before the timed steps
     tune = None
-    if args.autotune:
-        # the autotuner times candidate settings on the warmed-up window
-        # (outside the timed region) and leaves the fastest selected
-        tune = eng.autotune(n_walks, L, bias=bias_id, seed=seed_base + 99, forms=True, per_ingest=True)
-    else:
-        time.sleep(0.5)
-    barrier(world)
-    torch.cuda.synchronize()
-    t_all0, t_all1 = ev(), ev()
-    wall0 = time.time()
-    t_all0.record(stream)
-    for s in range(warm, warm + steps):
-        one_step(s, True)
-    t_all1.record(stream)
-    torch.cuda.synchronize()
+    wall0 = wall1 = None
+    for step, timed, b0, b1 in plan:
+        # this step's inputs, generated into HBM before its timed region
+        t0 = time.time()
+        batches = feeder.take(b0, b1)
+        torch.cuda.synchronize()
+        gen_s += time.time() - t0
+        if not timed:
+            one_step(batches, step, False)
+            continue
+        if wall0 is None:
+            if rank == 0:
+                clocks.start()  # running well before the timed steps
+            if args.autotune:
+                # the autotuner times candidate settings on the warmed-up
+                # window (outside the timed region) and keeps the fastest
+                tune = eng.autotune(n_walks, L, bias=bias_id, seed=seed_base + 99, forms=True, per_ingest=True)
+            else:
+                time.sleep(0.5)
+            wall0 = time.time()
+        barrier(world)
+        torch.cuda.synchronize()
+        s0, s1 = ev(), ev()
+        s0.record(stream)
+        one_step(batches, step, True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        step_ms.append(s0.elapsed_time(s1))
+        del batches
     wall1 = time.time()
-    barrier(world)
-    clk = clocks.stop(dev.index or 0, wall0, wall1) if rank == 0 else None
-    total_ms = t_all0.elapsed_time(t_all1)
+    clk = clocks.stop(dev.index or 0, wall0, wall1) if rank == 0 and wall0 is not None else None
+    total_ms = sum(step_ms)
 
     walk_s = sum(walk_ms) / 1e3
     ingest_s = sum(ingest_ms) / 1e3
     counts = eng.counts()
     res = dict(hops=hops, walk_s=walk_s, ingest_s=ingest_s, edges=edges, total_ms=total_ms,
                model_bytes=model_bytes, launches=launches, ingest_ms=ingest_ms, walk_ms=walk_ms,
-               walk_kernel_ms=walk_kernel_ms, live=counts["m"], clocks=clk, gen_s=t_gen, n_walks=n_walks,
+               walk_kernel_ms=walk_kernel_ms, live=counts["m"], clocks=clk, gen_s=gen_s, n_walks=n_walks,
                n_nodes=counts["n_nodes"], G_tot=counts["G_tot"], Gn=counts["Gn"], tune=tune,
-               n_nodes_spec=spec.n_nodes, evict_ms=evict_ms, evicted=evicted)
+               n_nodes_spec=spec.n_nodes, evict_ms=evict_ms, evicted=evicted, step_ms=step_ms,
+               batches_run=feeder.next, stream_batches=spec.n_batches)
 
-    # end to end through the C ABI with host buffers (one step, after the timed ones)
+    # end to end through the C ABI with host buffers (after the timed steps)
     if not args.no_e2e:
-        res["e2e"] = run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id,
-                             direction)
+        res["e2e"] = run_e2e(args, eng, feeder, n_walks, L, seed_base, bias_id, direction)
     eng.close()
-    del batches
     return res
 
 
-def run_e2e(args, eng, spec, batches, n_batches, n_walks, L, seed_base, stream, bias_id, direction=0):
+def run_e2e(args, eng, feeder, n_walks, L, seed_base, bias_id, direction=0):
     """Continue the stream with host-resident batches: every step copies its
     batches from pinned host memory and its walks back to pinned host memory
-    inside the timed region.  One untimed step first sizes the staging
-    buffers (device and pinned) the host-buffer calls keep for later calls."""
+    inside the timed calls.  The batches of a step are generated (on the
+    device, then copied into reused pinned buffers) before the step, outside
+    the timing.  One untimed step first sizes the staging buffers (device and
+    pinned) that host-buffer calls keep for later calls."""
     import torch
     from paper_2605_16182_gb300 import _lib
 
-    e2e_warm, e2e_steps = 1, 3
-    host = []
-    start = n_batches * spec.batch
-    ts_base = int(batches[-1][2][-1].item())
-    for k in range((e2e_warm + e2e_steps) * BATCHES_PER_STEP):
-        s, d, t = spec.edges(start + k * spec.batch, spec.batch, device=batches[0][0].device, ts_base=ts_base)
-        ts_base = int(t[-1].item())
-        host.append((s.cpu().pin_memory(), d.cpu().pin_memory(), t.cpu().pin_memory()))
+    e2e_warm, e2e_steps = 1, max(1, args.e2e_steps)
+    hsrc = [torch.empty((feeder.spec.batch,), dtype=torch.int32).pin_memory() for _ in range(BATCHES_PER_STEP)]
+    hdst = [torch.empty((feeder.spec.batch,), dtype=torch.int32).pin_memory() for _ in range(BATCHES_PER_STEP)]
+    hts = [torch.empty((feeder.spec.batch,), dtype=torch.int64).pin_memory() for _ in range(BATCHES_PER_STEP)]
     hnode = torch.empty((n_walks, L), dtype=torch.int32).pin_memory()
-    hts = torch.empty((n_walks, L), dtype=torch.int64).pin_memory()
+    hwts = torch.empty((n_walks, L), dtype=torch.int64).pin_memory()
     hln = torch.empty((n_walks,), dtype=torch.int32).pin_memory()
-    torch.cuda.synchronize()
-    hops, walk_s, ingest_s, h2d, d2h, edges = 0, 0.0, 0.0, 0, 0, 0
+    hops, h2d, d2h, edges = 0, 0, 0, 0
     ingest_calls, walk_calls = [], []
     walk_fn = _lib.tempest_walks_backward if direction else _lib.tempest_walks
-    for step in range(e2e_warm):
-        for b in range(BATCHES_PER_STEP):
-            s, d, t = host[step * BATCHES_PER_STEP + b]
-            _lib.tempest_ingest(eng.h, s.data_ptr(), d.data_ptr(), t.data_ptr(), int(s.shape[0]))
-        walk_fn(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7700 + step,
-                hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
-    for step in range(e2e_steps):
-        for b in range(BATCHES_PER_STEP):
-            s, d, t = host[(e2e_warm + step) * BATCHES_PER_STEP + b]
+    for step in range(e2e_warm + e2e_steps):
+        b0 = feeder.next
+        for i, (s, d, t) in enumerate(feeder.take(b0, b0 + BATCHES_PER_STEP)):
+            hsrc[i][:s.shape[0]].copy_(s)
+            hdst[i][:d.shape[0]].copy_(d)
+            hts[i][:t.shape[0]].copy_(t)
+        torch.cuda.synchronize()
+        timed = step >= e2e_warm
+        for i in range(BATCHES_PER_STEP):
+            n = feeder.spec.batch
             t0 = time.perf_counter()
-            _lib.tempest_ingest(eng.h, s.data_ptr(), d.data_ptr(), t.data_ptr(), int(s.shape[0]))
-            ingest_calls.append(time.perf_counter() - t0)
-            ingest_s += ingest_calls[-1]
-            h2d += s.numel() * 4 + d.numel() * 4 + t.numel() * 8
-            edges += int(s.shape[0])
+            _lib.tempest_ingest(eng.h, hsrc[i].data_ptr(), hdst[i].data_ptr(), hts[i].data_ptr(), n)
+            dt = time.perf_counter() - t0
+            if timed:
+                ingest_calls.append(dt)
+                h2d += n * (4 + 4 + 8)
+                edges += n
         t0 = time.perf_counter()
-        walk_fn(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7777 + step,
-                hnode.data_ptr(), hts.data_ptr(), hln.data_ptr())
-        walk_calls.append(time.perf_counter() - t0)
-        walk_s += walk_calls[-1]
-        hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
-        # the bytes the call moved device to host (whole rows for a share of
-        # the walks, each other walk's cells with its length and offset)
-        d2h += _lib.tempest_last_walk_stats(eng.h).d2h_bytes
+        walk_fn(eng.h, n_walks, L, bias_id, _lib.START_UNIFORM_EDGE, seed_base + 7700 + step,
+                hnode.data_ptr(), hwts.data_ptr(), hln.data_ptr())
+        dt = time.perf_counter() - t0
+        if timed:
+            walk_calls.append(dt)
+            hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
+            # the bytes the call moved device to host (whole rows for a share
+            # of the walks, each other walk's cells with its length and offset)
+            d2h += _lib.tempest_last_walk_stats(eng.h).d2h_bytes
+    threads = eng.get_tuning(_lib.TUNE_HOST_THREADS)
+    cpus = host_cpus()
+    walk_s = sum(walk_calls)
     return dict(value=hops / walk_s, unit="hops/s", h2d_bytes_per_step=h2d // e2e_steps,
-                d2h_bytes_per_step=d2h // e2e_steps, ingest_edges_per_s=edges / ingest_s, steps=e2e_steps,
-                ingest_call_ms={"p50": 1e3 * percentile(ingest_calls, 50), "max": 1e3 * max(ingest_calls)},
-                walk_call_ms=1e3 * walk_s / e2e_steps, walk_calls_ms=[round(1e3 * x, 2) for x in walk_calls])
+                d2h_bytes_per_step=d2h // e2e_steps, ingest_edges_per_s=edges / sum(ingest_calls),
+                steps=e2e_steps,
+                ingest_call_ms={"p50": 1e3 * percentile(ingest_calls, 50), "p99": 1e3 * percentile(ingest_calls, 99),
+                                "max": 1e3 * max(ingest_calls)},
+                walk_call_ms={"mean": 1e3 * walk_s / e2e_steps, "p50": 1e3 * percentile(walk_calls, 50),
+                              "p99": 1e3 * percentile(walk_calls, 99)},
+                walk_calls_ms=[round(1e3 * x, 2) for x in walk_calls],
+                host_threads=threads if threads > 0 else min(cpus, 32),
+                host_threads_rule="set" if threads > 0 else "the CPUs this process may use (affinity mask and "
+                                                            "cgroup quota), at most 32",
+                host_cpus=cpus)
+
+
+def host_cpus():
+    """CPUs this process may run on: the affinity mask, capped by a cgroup v2
+    CPU quota (the rule the library's host-output threads follow)."""
+    c = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    try:
+        q, per = open("/sys/fs/cgroup/cpu.max").read().split()[:2]
+        if q != "max":
+            c = max(1, min(c, int(q) // int(per)))
+    except (OSError, ValueError):
+        pass
+    return c
 
 
 # --------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and --impl reference arm)
 # --------------------------------------------------------------------------
-def oracle_sample(seconds_budget=15.0, scale=0.01, n_walks=4_000_000, max_len=80):
+def oracle_sample(seconds_budget=15.0, scale=0.01, n_walks=4_000_000, max_len=80, threads=0):
     """The oracle on the same workload scaled by `scale` (node count, batch
     and window): it ingests the stream up to the first walk point after the
-    window is full, then draws exponential walks.  Returns rates."""
+    window is full, then draws exponential walks on one thread.  With threads
+    > 1 it then draws the same number of walk ids again on that many threads
+    (each thread a contiguous range of ids through the same read-only state;
+    the walks are keyed per id, so the rows are the same) and checks that the
+    rows equal the one-thread run.  Returns rates."""
+    import numpy as np
     from oracle import oracle as O
     from paper_2605_16182_gb300 import synth
     spec = synth.config_billion(scale=scale)
@@ -371,16 +432,34 @@ def oracle_sample(seconds_budget=15.0, scale=0.01, n_walks=4_000_000, max_len=80
     done = 0
     chunk = 20_000
     while done < n_walks and time.perf_counter() - t0 < seconds_budget * 0.4:
-        ids = list(range(done, done + chunk))
-        import numpy as np
-        _, _, ln, _, _ = orc.walks(ids=np.array(ids, np.int64), max_len=max_len, bias=O.BIAS_EXP, seed=3)
+        _, _, ln, _, _ = orc.walks(ids=np.arange(done, done + chunk, dtype=np.int64), max_len=max_len,
+                                   bias=O.BIAS_EXP, seed=3)
         hops += int(np.clip(ln - 1, 0, None).sum())
         done += chunk
     walk_s = time.perf_counter() - t0
+    multi = None
+    if threads > 1 and done:
+        import concurrent.futures as cf
+        # ctypes releases the GIL for the duration of each oracle call
+        per = -(-done // threads)
+        ranges = [(a, min(done, a + per)) for a in range(0, done, per)]
+        t1 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=len(ranges)) as ex:
+            parts = list(ex.map(lambda r: orc.walks(ids=np.arange(r[0], r[1], dtype=np.int64), max_len=max_len,
+                                                    bias=O.BIAS_EXP, seed=3), ranges))
+        mt_s = time.perf_counter() - t1
+        mt_hops = sum(int(np.clip(p[2] - 1, 0, None).sum()) for p in parts)
+        # spot check: the last one-thread chunk equals the same ids of the threaded run
+        _, _, ln1, _, _ = orc.walks(ids=np.arange(done - chunk, done, dtype=np.int64), max_len=max_len,
+                                    bias=O.BIAS_EXP, seed=3)
+        same = bool(np.array_equal(np.concatenate([p[2] for p in parts])[done - chunk:done], ln1)) and \
+            mt_hops == hops
+        multi = dict(hops_per_s=mt_hops / mt_s if mt_s > 0 else 0.0, threads=len(ranges), walk_s=mt_s,
+                     same_rows=same)
     c = orc.counts()
     orc.close()
     return dict(hops_per_s=hops / walk_s if walk_s > 0 else 0.0, edges_per_s=edges / ing_s if ing_s else 0.0,
-                walks=done, hops=hops, walk_s=walk_s, edges=edges, ingest_s=ing_s, live=c["m"],
+                walks=done, hops=hops, walk_s=walk_s, edges=edges, ingest_s=ing_s, live=c["m"], multi=multi,
                 sample="oracle (1 thread) on the billion-edge stream scaled by %g: %d nodes, batches of %d, "
                        "window %d; %d batches ingested (%.1f s), then %d exponential walks of max_len %d "
                        "(%.1f s)" % (scale, spec.n_nodes, spec.batch, -spec.window, len(lat), ing_s, done,
@@ -728,9 +807,15 @@ def main():
     traffic = recorded_traffic(res["hops"] / max(1, len(res["walk_ms"])), kname)
     cpu = None
     if not args.no_cpu:
-        o = oracle_sample(seconds_budget=args.cpu_seconds)
+        o = oracle_sample(seconds_budget=args.cpu_seconds, threads=host_cpus())
         cpu = {"value": o["hops_per_s"], "unit": "hops/s", "cores": 1, "kind": "oracle", "sample": o["sample"],
                "ingest_edges_per_s": o["edges_per_s"]}
+        if o["multi"]:
+            m = o["multi"]
+            cpu["all_cores"] = {"value": m["hops_per_s"], "unit": "hops/s", "cores": m["threads"],
+                                "label": "baseline, not target",
+                                "sample": "the same walk ids on %d threads (%.1f s), rows equal to the one-thread "
+                                          "run: %s" % (m["threads"], m["walk_s"], m["same_rows"])}
     per_launch_bytes = res["model_bytes"] / max(1, len(res["walk_ms"]))
     sched = args.sched
     if res.get("tune"):
@@ -759,6 +844,10 @@ def main():
                    "direction": args.direction,
                    "start": "uniform edge", "batches_per_step": BATCHES_PER_STEP,
                    "scheduler": sched, "l2": "inputs larger than L2 (160 MB batches, GB-sized state)",
+                   "stream": "batches %d-%d of a stream of %d batches; past its end the same generator continues "
+                             "it at steady state (full count window)" % (0, res["batches_run"] - 1,
+                                                                          res["stream_batches"]),
+                   "inputs": "each step's batches generated into HBM before the step, outside its timed region",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "ingest_edges_per_s": edges / ingest_s if ingest_s > 0 else 0.0,
         "stream_hops_per_s": hops / (total_ms / 1e3) if total_ms > 0 else 0.0,

@@ -98,10 +98,26 @@ def _coprime_multiplier(N: int) -> int:
     return a
 
 
+_ZIPF_DEVICE = {}
+
+
+def _thresholds_on(N: int, alpha: float, device) -> torch.Tensor:
+    """zipf_thresholds on `device`, kept there for the next call (the table of
+    a 100M-node stream is 800 MB)."""
+    dev = torch.device(device)
+    key = (int(N), float(alpha), str(dev))
+    t = _ZIPF_DEVICE.get(key)
+    if t is None:
+        t = zipf_thresholds(N, alpha).to(dev)
+        _ZIPF_DEVICE.clear()
+        _ZIPF_DEVICE[key] = t
+    return t
+
+
 def zipf_ids(N: int, alpha: float, seed: int, stream: int, start: int, n: int, device,
              perm_seed: Optional[int] = None) -> torch.Tensor:
     """n Zipf(alpha) node ids in [0, N) as int32."""
-    thr = zipf_thresholds(N, alpha).to(device)
+    thr = _thresholds_on(N, alpha, device)
     u = u63(seed, stream, start, n, device)
     rank = torch.searchsorted(thr, u, right=True).clamp_(max=N - 1)
     ps = seed if perm_seed is None else perm_seed
@@ -183,6 +199,8 @@ class StreamSpec:
         For Poisson streams the timestamps are a prefix sum of all gaps from
         edge 0, so ts_base (the timestamp of edge start-1, or t0 when
         start == 0) may be passed to avoid recomputing the prefix."""
+        if start < 0 or n < 0:
+            raise ValueError("edge range start %d, count %d" % (start, n))
         src = zipf_ids(self.n_nodes, self.alpha, self.seed, 1, start, n, device)
         dst = zipf_ids(self.n_nodes, self.alpha, self.seed, 2, start, n, device,
                        perm_seed=self.seed)
@@ -206,14 +224,29 @@ class StreamSpec:
             s += n
         return t
 
-    def batches(self, device="cpu", first: int = 0, last: Optional[int] = None) -> Iterator:
-        """Yield (k, src, dst, ts) for batches first..last-1."""
+    def batches(self, device="cpu", first: int = 0, last: Optional[int] = None,
+                extend: bool = False, ts_base: Optional[int] = None) -> Iterator:
+        """Yield (k, src, dst, ts) for batches first..last-1.
+
+        The stream holds n_batches batches (the last one possibly short).  A
+        batch past the end raises ValueError unless extend is set: then the
+        same generator continues past n_edges and every batch is full (the
+        counter of every draw is the edge index, so a full batch k is the same
+        whichever call produces it).  ts_base, for Poisson streams, is the
+        timestamp of the edge before batch `first` (saves recomputing the
+        prefix of gaps)."""
         last = self.n_batches if last is None else last
+        if first < 0 or last < first:
+            raise ValueError("batch range [%d, %d) is empty or negative" % (first, last))
+        if last > self.n_batches and not extend:
+            raise ValueError("the stream %s has %d batches; batches up to %d were asked for (extend=True "
+                             "continues it)" % (self.name, self.n_batches, last))
         start = first * self.batch
-        ts_base = None if self.ts_kind == "uniform" else self.ts_before(start, device)
+        if self.ts_kind != "uniform" and ts_base is None:
+            ts_base = self.ts_before(start, device)
         for k in range(first, last):
             s = k * self.batch
-            n = min(self.batch, self.n_edges - s)
+            n = self.batch if extend else min(self.batch, self.n_edges - s)
             src, dst, ts = self.edges(s, n, device, ts_base)
             if self.ts_kind != "uniform":
                 ts_base = int(ts[-1].item()) if n else ts_base

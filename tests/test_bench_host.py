@@ -93,3 +93,64 @@ def test_recorded_traffic_is_keyed_to_the_kernel_source(tmp_path, monkeypatch):
     assert bench.recorded_traffic(1000.0, "k_walks_lane") is None
     path.unlink()
     assert bench.recorded_traffic(1000.0, "k_walks_lane") is None
+
+
+@pytest.mark.parametrize("steps,warmup", [(20, 5), (7, 3), (1, 1), (12, 0)])
+def test_batch_plan_runs_any_step_count(steps, warmup):
+    """The bench's batch plan for any --steps / --warmup: every step ingests
+    BATCHES_PER_STEP full batches, in stream order, past the stream's nominal
+    100 batches when the run is longer; timestamps never decrease across the
+    whole run, and a batch continued past the end is the same as the one the
+    generator gives for that edge range from scratch."""
+    import torch
+    from paper_2605_16182_gb300 import synth
+    bench = _bench()
+    spec = synth.config_billion(scale=1e-4)
+    spec.n_nodes = 5000  # a small id table; the plan does not depend on it
+    plan = bench.batch_plan(steps, warmup)
+    assert len(plan) == steps + warmup
+    assert [p[1] for p in plan] == [False] * warmup + [True] * steps
+    feeder = bench.StepFeeder(spec, "cpu")
+    last_ts = None
+    n_batches = 0
+    for step, timed, b0, b1 in plan:
+        got = feeder.take(b0, b1)
+        assert len(got) == bench.BATCHES_PER_STEP == b1 - b0
+        for s, d, t in got:
+            assert s.shape[0] == d.shape[0] == t.shape[0] == spec.batch
+            assert bool((t[1:] >= t[:-1]).all())
+            if last_ts is not None:
+                assert int(t[0]) >= last_ts
+            last_ts = int(t[-1])
+        n_batches = b1
+    assert n_batches == (steps + warmup) * bench.BATCHES_PER_STEP
+    # the first batch past the stream's end equals the generator's own edges there
+    k = spec.n_batches
+    if n_batches > k:
+        ref = spec.edges(k * spec.batch, spec.batch, "cpu")
+        feeder2 = bench.StepFeeder(spec, "cpu")
+        feeder2.take(0, k)
+        (s, d, t), = feeder2.take(k, k + 1)
+        assert torch.equal(s, ref[0]) and torch.equal(d, ref[1]) and torch.equal(t, ref[2])
+
+
+def test_stream_refuses_batches_past_its_end():
+    from paper_2605_16182_gb300 import synth
+    spec = synth.config_billion(scale=1e-4)
+    spec.n_nodes = 5000
+    with pytest.raises(ValueError):
+        list(spec.batches(first=98, last=101))
+    with pytest.raises(ValueError):
+        spec.edges(10, -1)
+    assert len(list(spec.batches(first=98, last=101, extend=True))) == 3
+
+
+def test_feeder_takes_batches_in_order():
+    from paper_2605_16182_gb300 import synth
+    bench = _bench()
+    spec = synth.config_billion(scale=1e-4)
+    spec.n_nodes = 5000
+    f = bench.StepFeeder(spec, "cpu")
+    f.take(0, 2)
+    with pytest.raises(ValueError):
+        f.take(5, 6)
