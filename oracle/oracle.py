@@ -71,6 +71,8 @@ def lib():
         L.orc_sampler_x.restype = dbl
         L.orc_sampler_x.argtypes = [dbl, i64, ctypes.c_int, dbl]
         L.orc_sampler_index.restype = i64
+        L.orc_sampler_x_bound.restype = dbl
+        L.orc_sampler_x_bound.argtypes = [dbl, i64, ctypes.c_int, dbl]
         L.orc_sampler_index.argtypes = [dbl, i64, ctypes.c_int, dbl]
         L.orc_sampler_batch.argtypes = [vp, vp, i64, ctypes.c_int, dbl, vp, vp]
         _lib = L
@@ -101,8 +103,15 @@ def sampler_index(u, n, bias, lam=1.0):
     return lib().orc_sampler_index(float(u), int(n), int(bias), float(lam))
 
 
+def sampler_x_bound(u, n, bias, lam=1.0):
+    """Bound on the rounding error of sampler_x's double evaluation (units of x)."""
+    return lib().orc_sampler_x_bound(float(u), int(n), int(bias), float(lam))
+
+
 def sampler_batch(k, n, bias, lam=1.0):
-    """(index int64[count], margin float64[count]) for u = k * 2^-53."""
+    """(index int64[count], margin float64[count]) for u = k * 2^-53; the
+    margin is the distance of x to the nearest integer in units of
+    sampler_x_bound."""
     k = np.ascontiguousarray(k, dtype=np.uint64)
     n = np.ascontiguousarray(n, dtype=np.int64)
     out = np.zeros(k.shape[0], np.int64)

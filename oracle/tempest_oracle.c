@@ -191,20 +191,61 @@ int64_t orc_sampler_index(double u, int64_t n, int bias, double lambda)
     return (int64_t)f;
 }
 
+/*
+ * Error bound of the double evaluation of orc_sampler_x, in units of x: the
+ * largest |x_fl - x| that rounding can cause, by first-order analysis with
+ * unit roundoff eps = 2^-53 per IEEE operation and exp / log within one ulp
+ * (2 eps relative), the accuracy glibc and CUDA state for them.  Two
+ * evaluations of the same formula (this one and the GPU's) can floor to
+ * different indexes only where x lies within twice this bound of an integer.
+ *   uniform (Eq. 1): one rounded product, eps x.
+ *   linear (Eq. 2): 4 u n (n + 1) + 1 rounded four times, the square root
+ *     and the last two steps once each: within 4 eps (x + 1).
+ *   exponential (exact form of Eq. 3), y = x - n = log(s) / lambda:
+ *     a = fl(lambda n) errs by eps lambda n, so exp(a) carries
+ *     eps (lambda n + 2) relative; 1 - u is exact for u = k 2^-53; the
+ *     product and the sum give s a relative error of at most
+ *     eps (1 + m (3 + lambda n)), m = (1 - u) e / s <= 1; log adds
+ *     2 eps |lambda y| (that is 2 eps |y| after the division), the division
+ *     eps |y| and the final sum eps |x|:
+ *       |x_fl - x| <= eps (|x| + 3 |y| + (1 + m (3 + lambda n)) / lambda).
+ *   Every coefficient is doubled below to cover the second-order terms.
+ */
+double orc_sampler_x_bound(double u, int64_t n, int bias, double lambda)
+{
+    const double eps = 1.0 / 9007199254740992.0; /* 2^-53 */
+    const double nd = (double)n;
+    const double x = orc_sampler_x(u, n, bias, lambda);
+    const double ax = x == x ? fabs(x) : 0.0;
+    if (bias == BIAS_UNIFORM) return 2.0 * eps * ax;
+    if (bias == BIAS_LINEAR) return 8.0 * eps * (ax + 1.0);
+    const double e = exp(-lambda * nd);
+    const double s = u + (1.0 - u) * e;
+    const double m = s > 0.0 ? (1.0 - u) * e / s : 1.0;
+    const double ay = x == x ? fabs(x - nd) : 0.0;
+    return eps * (2.0 * ax + 6.0 * ay + (2.0 + m * (6.0 + 2.0 * lambda * nd)) / lambda);
+}
+
+/* Distance of x to the nearest integer in units of the bound b (0 for NaN). */
+static double bound_margin(double x, double b)
+{
+    if (!(x == x)) return 0.0;
+    double r = x - floor(x + 0.5);
+    if (r < 0) r = -r;
+    return r / (b > 0.0 ? b : 4.9406564584124654e-324);
+}
+
 /* Many draws: u = k[i] * 2^-53.  out[i] = index; margin[i] (nullable) =
- * |x - nearest integer| / max(1, n[i]). */
+ * |x - nearest integer| in units of orc_sampler_x_bound. */
 void orc_sampler_batch(const uint64_t *k, const int64_t *n, int64_t count, int bias, double lambda,
                        int64_t *out, double *margin)
 {
     for (int64_t i = 0; i < count; i++) {
         double u = (double)(k[i] & ((1ull << 53) - 1)) * (1.0 / 9007199254740992.0);
         out[i] = orc_sampler_index(u, n[i], bias, lambda);
-        if (margin) {
-            double x = orc_sampler_x(u, n[i], bias, lambda);
-            double r = x - floor(x + 0.5);
-            if (r < 0) r = -r;
-            margin[i] = (x == x) ? r / (n[i] > 1 ? (double)n[i] : 1.0) : 0.0;
-        }
+        if (margin)
+            margin[i] = bound_margin(orc_sampler_x(u, n[i], bias, lambda),
+                                     orc_sampler_x_bound(u, n[i], bias, lambda));
     }
 }
 
@@ -494,13 +535,10 @@ static int64_t first_group_after(const orc *o, int64_t g0, int64_t g1, int64_t t
     return lo;
 }
 
-static double rel_margin(double x, int64_t n)
+/* Margin of a draw with u of n outcomes (see orc_sampler_x_bound). */
+static double draw_margin(double u, int64_t n, int bias, double lambda)
 {
-    double r = x - floor(x + 0.5);
-    if (r < 0) r = -r;
-    double s = n > 1 ? (double)n : 1.0;
-    if (!(x == x)) return 0.0;
-    return r / s;
+    return bound_margin(orc_sampler_x(u, n, bias, lambda), orc_sampler_x_bound(u, n, bias, lambda));
 }
 
 /* Live (from, to) pairs for the Temporal Node2Vec adjacency test: sorted
@@ -557,9 +595,8 @@ static int32_t one_walk(const orc *o, const orc_pairs *P, uint64_t w, int32_t ma
         } else {
             /* the weight-based and Node2Vec biases start like the index-based exponential */
             const int sb = (bias == BIAS_EXP_WEIGHT || bias == BIAS_NODE2VEC) ? BIAS_EXP : bias;
-            double x = orc_sampler_x(u1, o->G_tot, sb, lambda_start);
             int64_t g = orc_sampler_index(u1, o->G_tot, sb, lambda_start);
-            if (margin && sb != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
+            if (margin && sb != BIAS_UNIFORM) margin[1] = draw_margin(u1, o->G_tot, sb, lambda_start);
             int64_t a = o->ts_group_off[g], size = o->ts_group_off[g + 1] - a;
             k = a + uniform_index(u2, size);
         }
@@ -626,14 +663,18 @@ static int32_t one_walk(const orc *o, const orc_pairs *P, uint64_t w, int32_t ma
             const int64_t j = orc_weight_pick(gts, gsz, n, o->lambda_w, u1, &mg);
             free(gts);
             free(gsz);
-            if (margin) margin[len] = mg;
+            /* in units of the rounding either evaluation can make in the
+             * running weight: each weight carries about eps (|exponent| + 2)
+             * relative (exponents stay within 750 where a weight is not
+             * zero), and a running or suffix sum over the node's g1 - g0
+             * groups adds eps per group */
+            if (margin) margin[len] = mg / ((double)(g1 - g0 + 800) * (1.0 / 9007199254740992.0));
             int64_t e0 = o->node_group_off[c + j], e1 = o->node_group_off[c + j + 1];
             idx = e0 + uniform_index(u2, e1 - e0);
         } else {
             int64_t n = g1 - c;
-            double x = orc_sampler_x(u1, n, bias, o->lambda_hop);
             int64_t j = orc_sampler_index(u1, n, bias, o->lambda_hop);
-            if (margin) margin[len] = rel_margin(x, n);
+            if (margin) margin[len] = draw_margin(u1, n, bias, o->lambda_hop);
             int64_t e0 = o->node_group_off[c + j], e1 = o->node_group_off[c + j + 1];
             idx = e0 + uniform_index(u2, e1 - e0);
         }
@@ -769,9 +810,8 @@ static int32_t one_walk_back(const orc *o, const orc_inview *iv, const orc_pairs
             k = o->m - 1 - uniform_index(u1, o->m);
         } else {
             const int sb = bias == BIAS_NODE2VEC ? BIAS_EXP : bias;
-            double x = orc_sampler_x(u1, o->G_tot, sb, lambda_start);
             int64_t g = o->G_tot - 1 - orc_sampler_index(u1, o->G_tot, sb, lambda_start);
-            if (margin && sb != BIAS_UNIFORM) margin[1] = rel_margin(x, o->G_tot);
+            if (margin && sb != BIAS_UNIFORM) margin[1] = draw_margin(u1, o->G_tot, sb, lambda_start);
             int64_t a = o->ts_group_off[g], size = o->ts_group_off[g + 1] - a;
             k = a + size - 1 - uniform_index(u2, size);
         }
@@ -828,9 +868,8 @@ static int32_t one_walk_back(const orc *o, const orc_inview *iv, const orc_pairs
             idx = e1 - 1 - uniform_index(u1, e1 - e0);
         } else {
             int64_t n = c - g0;
-            double x = orc_sampler_x(u1, n, bias, o->lambda_hop);
             int64_t j = orc_sampler_index(u1, n, bias, o->lambda_hop);
-            if (margin) margin[len] = rel_margin(x, n);
+            if (margin) margin[len] = draw_margin(u1, n, bias, o->lambda_hop);
             int64_t gg = c - 1 - j;
             int64_t e0 = iv->group_off[gg], e1 = iv->group_off[gg + 1];
             idx = e1 - 1 - uniform_index(u2, e1 - e0);
@@ -926,9 +965,8 @@ static int64_t n2v_pick(const orc *o, const orc_pairs *P, const int64_t *group_o
         uint32_t r[4];
         draw_block(seed, w, h, k, r);
         const double u1 = orc_u53(r[0], r[1]), u2 = orc_u53(r[2], r[3]);
-        const double x = orc_sampler_x(u1, n, BIAS_EXP, o->lambda_hop);
         const int64_t j = orc_sampler_index(u1, n, BIAS_EXP, o->lambda_hop);
-        const double m1 = rel_margin(x, n);
+        const double m1 = draw_margin(u1, n, BIAS_EXP, o->lambda_hop);
         if (m1 < mg) mg = m1;
         if (k > 0 && bytes) *bytes += 12 + 16;
         const int64_t gg = back ? hi - 1 - j : lo + j;

@@ -69,13 +69,19 @@ def full_size():
 
 
 @pytest.mark.parametrize("form", FORMS)
-def test_full_size_sampled_walks(full_size, form):
+def test_full_size_sampled_walks(full_size, form, record_property):
     runs, ref, counts = full_size
     assert counts["m"] >= 200_000_000
     g = runs[(form, _lib.BIAS_UNIFORM)]
     assert_walks_bit_exact(g, ref[_lib.BIAS_UNIFORM][:3], "uniform, form %d" % form)
     g = runs[(form, _lib.BIAS_EXP)]
     o = ref[_lib.BIAS_EXP]
-    agree, total, _ = compare_biased(g, o, o[3])
+    agree, total, div = compare_biased(g, o, o[3])
+    # reported (pytest -rA / the junit record): how many sampled walks left
+    # the oracle's path, and the margins (in double-evaluation bounds) where
+    record_property("divergent_walks", len(div))
+    record_property("divergent_margins", [round(m, 3) for _, _, m in div])
+    print("form %d: %d of %d sampled exponential walks diverge (%d of %d hops agree), margins %s"
+          % (form, len(div), SAMPLE, agree, total, [round(m, 3) for _, _, m in div]))
     assert total > SAMPLE  # the sample walks past its start edges
     assert agree / total >= MIN_HOP_AGREEMENT, (form, agree, total)

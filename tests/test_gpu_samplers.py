@@ -3,8 +3,8 @@
 The GPU evaluates uniform draws with integer arithmetic, exponential draws in
 FP32 with an error bound and an FP64 fallback, and linear draws in FP64; all
 must return the oracle's FP64 result.  Uniform and linear must agree on every
-draw; exponential draws may differ only where the oracle's x is within
-1e-12 * max(1, n) of an integer.  The inputs mix random draws with draws
+draw; exponential draws may differ only where the oracle's x is within twice
+the double evaluation's own rounding bound of an integer (BOUND_UNITS).  The inputs mix random draws with draws
 placed on and around the bucket boundaries, where a rounding slip would show.
 """
 import math
@@ -15,7 +15,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2605_16182_gb300 import _lib
-from parity_util import REL_BOUNDARY
+from parity_util import BOUND_UNITS
 
 pytestmark = pytest.mark.gpu
 TWO53 = float(1 << 53)
@@ -110,6 +110,55 @@ def test_exponential_agrees_up_to_boundary(eng, lam):
     got = _gpu(eng, k, n, 2, lam)
     want, margin = O.sampler_batch(k, n, 2, lam)
     bad = got != want
-    assert (margin[bad] <= REL_BOUNDARY).all(), "disagreement away from a boundary"
+    assert (margin[bad] <= BOUND_UNITS).all(), "disagreement away from a boundary"
     assert bad.mean() <= 1e-4
     assert ((got >= 0) & (got < n)).all()
+
+
+def _exp_band(n, lam, rng, mp):
+    """Draws whose exact x lies 1e-12 ... 1e-4 (in x) on either side of a
+    bucket edge: the band in which the GPU's FP32 bound alone decides (no
+    FP64 fallback) once the distance exceeds that bound."""
+    E = mp.exp(-lam * n)
+    if lam >= 1.0:
+        edges = [n - 1 - j for j in range(8)]
+    elif lam * n > 20:
+        edges = [n - int(rng.integers(1, int(20 / lam))) for _ in range(8)]
+    else:
+        edges = [int(rng.integers(1, n)) for _ in range(8)]
+    ks = []
+    for i in edges:
+        if i <= 0:
+            continue
+        for d in (1e-12, 1e-11, 1e-10, 1e-9, 3e-9, 1e-8, 3e-8, 1e-7, 3e-7, 1e-6, 3e-6, 1e-5, 1e-4):
+            for sgn in (-1, 1):
+                x = mp.mpf(i) + sgn * mp.mpf(d)
+                u = (mp.exp(lam * (x - n)) - E) / (1 - E)
+                k = int(mp.nint(u * TWO53))
+                if 0 < k < (1 << 53):
+                    ks.append(k)
+    return ks
+
+
+@pytest.mark.parametrize("n", [10**6, 1 << 24, 10**8, (1 << 31) - 1])
+def test_exponential_fp32_band(eng, n):
+    """Exponential draws placed 1e-12 ... 1e-4 from a bucket edge, for n up
+    to 2^31 - 1 and rates 1, 1e-3 and 1/n: the GPU decides most of them in
+    FP32 with its error bound and must return the oracle's index on every
+    draw more than BOUND_UNITS double-evaluation bounds from the edge."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    rng = np.random.default_rng(n % 1000 + 5)
+    checked = 0
+    for lam in (1.0, 1e-3, 1.0 / n):
+        k = np.array(_exp_band(n, lam, rng, mp), dtype=np.uint64)
+        nn = np.full(k.shape[0], n, np.int64)
+        got = _gpu(eng, k, nn, 2, lam)
+        want, margin = O.sampler_batch(k, nn, 2, lam)
+        bad = got != want
+        assert (margin[bad] <= BOUND_UNITS).all(), (
+            "lambda %g: %d draws disagree beyond the bound (worst margin %g bounds)"
+            % (lam, int((margin[bad] > BOUND_UNITS).sum()), float(margin[bad].max())))
+        checked += int((margin > BOUND_UNITS).sum())
+    # draws that must agree: most of the band lies beyond the double's bound
+    assert checked > 80

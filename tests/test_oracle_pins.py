@@ -623,3 +623,75 @@ def test_node2vec_rejection_cap():
     assert (ln[~on01] == 2).all()  # 1 -> 0 at t 2 has no continuation
     with pytest.raises(ValueError):
         o.set_node2vec(0.0, 1.0)
+
+
+# ------------------------------------------------ the agreement rule's bound
+def _exact_x(u, n, bias, lam, mp):
+    """x of the sampler in 80-digit arithmetic from the exact u."""
+    u, n, lam = mp.mpf(u), mp.mpf(n), mp.mpf(lam)
+    if bias == 0:
+        return u * n
+    if bias == 1:
+        return (mp.sqrt(1 + 4 * u * n * (n + 1)) - 1) / 2
+    return n + mp.log(u + (1 - u) * mp.exp(-lam * n)) / lam
+
+
+def _bound_cases(rng):
+    ns = [1, 2, 7, 100, 10**4, 10**6, 1 << 24, 10**8, (1 << 31) - 1]
+    for _ in range(4000):
+        n = rng.choice(ns + [rng.randrange(1, 1 << 31)])
+        lam = rng.choice([1.0, 3.0, 0.5, 1e-3, 1e-8, 1.0 / n, 30.0 / n])
+        k = rng.choice([rng.randrange(1, 1 << 53), rng.randrange(1, 1 << 20), (1 << 53) - rng.randrange(1, 1 << 20)])
+        yield k * 2.0 ** -53, n, lam
+
+
+@pytest.mark.parametrize("bias", [0, 1, 2])
+def test_double_evaluation_stays_within_its_bound(bias):
+    """orc_sampler_x_bound bounds the rounding error of the oracle's own
+    double evaluation of Eq. 1 / Eq. 2 / exact Eq. 3 against the value in
+    80-digit arithmetic, for n up to 2^31 - 1, rates from 1e-8 to 30, and u
+    near 0, near 1 and in between; the error reaches a visible share of the
+    bound (it is not vacuous)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 80
+    rng = random.Random(300 + bias)
+    worst = 0.0
+    for u, n, lam in _bound_cases(rng):
+        if bias != 2:
+            lam = 1.0
+        x = O.sampler_x(u, n, bias, lam)
+        b = O.sampler_x_bound(u, n, bias, lam)
+        err = abs(mp.mpf(x) - _exact_x(u, n, bias, lam, mp))
+        assert err <= b, (bias, u, n, lam, float(err), b)
+        worst = max(worst, float(err / b))
+    assert worst > 0.02
+
+
+def test_exponential_bound_needs_its_rate_term():
+    """A bound without the term in 1/lambda (the error of s carried through
+    log(s) / lambda) is broken at small rates: the planted omission fails
+    the same comparison, so the test above can see a dropped term."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 80
+    rng = random.Random(77)
+    eps = 2.0 ** -53
+    broken = 0
+    for _ in range(3000):
+        n = rng.choice([10**4, 10**6, 10**8])
+        lam = rng.choice([1e-8, 1e-3 / n, 1.0 / n])
+        u = rng.randrange(1, 1 << 53) * 2.0 ** -53
+        x = O.sampler_x(u, n, 2, lam)
+        planted = eps * (2 * abs(x) + 6 * abs(x - n))
+        if abs(mp.mpf(x) - _exact_x(u, n, 2, lam, mp)) > planted:
+            broken += 1
+    assert broken > 30
+
+
+def test_agreement_margin_units():
+    """sampler_batch's margin is |x - round(x)| / bound: zero on an exact
+    boundary (linear u = 1/3 at n = 2 gives x = 1), large far from one."""
+    k = np.array([int(round(2.0 ** 53 / 3)), 1 << 52], dtype=np.uint64)
+    idx, mg = O.sampler_batch(k, np.array([2, 2], np.int64), 1)
+    x = O.sampler_x(float(k[0]) * 2.0 ** -53, 2, 1)
+    assert mg[0] == pytest.approx(abs(x - round(x)) / O.sampler_x_bound(float(k[0]) * 2.0 ** -53, 2, 1))
+    assert mg[1] > 1e10  # u = 1/2: x = 1.3028, far from an integer
