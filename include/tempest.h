@@ -41,7 +41,9 @@ enum {
     TEMPEST_EINVAL = -1,    /* bad argument; no state changed */
     TEMPEST_ENOMEM = -2,    /* allocation failed or HBM budget exceeded */
     TEMPEST_ECUDA = -3,     /* a CUDA runtime call failed */
-    TEMPEST_ETIMEDOUT = -4, /* a bounded device wait gave up */
+    TEMPEST_ETIMEDOUT = -4, /* reserved for a bounded device wait that gives up:
+                             * no kernel of this library waits on a flag or a
+                             * peer, so no call returns it */
     TEMPEST_EBUSY = -5      /* the serving queue is full */
 };
 
@@ -201,8 +203,14 @@ int tempest_set_bias_params(tempest_t *h, double lambda_hop, double lambda_start
  * edge, which walk outputs give their first node) and INT64_MAX (the time
  * after every edge, where PER_NODE backward walks start).  stats may be
  * NULL.  EINVAL (state unchanged) on n < 0, NULL arrays with n > 0, a
- * negative id or an INT64_MIN or INT64_MAX timestamp.  Synchronises the
- * stream. */
+ * negative id or an INT64_MIN or INT64_MAX timestamp.  ENOMEM (a failed
+ * allocation or the HBM budget) and ECUDA (a failed consistency check) also
+ * leave the state as it was: the batch is not ingested (nor into the in-edge
+ * index of backward walks), the edge store's counters are restored (its
+ * previous live edges are still in place) and the derived views are rebuilt
+ * from it, at once or, when that needs memory that is not there, before the
+ * next call that reads them (which then returns ENOMEM itself while the
+ * memory stays short).  Synchronises the stream. */
 int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const int64_t *ts,
                    int64_t n, tempest_ingest_stats *stats);
 

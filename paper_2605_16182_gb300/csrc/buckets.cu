@@ -335,9 +335,10 @@ struct ActiveOp {
 
 int prepare_active_nodes(tempest_t *h)
 {
+    int rc;
+    if ((rc = views_repair(h))) return rc;
     if (h->pn_ver == h->state_ver) return TEMPEST_OK;
     const int64_t N = h->N;
-    int rc;
     h->n_pn = 0;
     if (N > 0 && h->nv_ready && h->M > 0) {
         if ((rc = ensure(h, h->pn_nodes, sizeof(int32_t) * (size_t)N, true))) return rc;
@@ -355,10 +356,11 @@ int prepare_active_nodes(tempest_t *h)
 
 int prepare_walk_index(tempest_t *h)
 {
+    int rc;
+    if ((rc = views_repair(h))) return rc;
     if (h->bkt_ver == h->state_ver) return TEMPEST_OK;
     cudaStream_t st = h->stream;
     const int64_t S = h->n_act, Gn = h->Gn;
-    int rc;
     h->n_big = 0;
     if (S > 0 && Gn >= BKT_MIN_G) {
         const size_t Sz = (size_t)S;

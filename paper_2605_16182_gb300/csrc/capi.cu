@@ -344,7 +344,8 @@ int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const i
                    tempest_ingest_stats *stats)
 {
     if (!h) return TEMPEST_EINVAL;
-    int rc = ingest_batch(h, src, dst, ts, n, stats);
+    IngestUndo undo;
+    int rc = ingest_batch(h, src, dst, ts, n, stats, &undo);
     if (rc || !h->rev) return rc;
     // the reversed index takes the same batch with the endpoints swapped; it
     // sees the same timestamps in the same order, so its window evicts the
@@ -352,11 +353,12 @@ int tempest_ingest(tempest_t *h, const int32_t *src, const int32_t *dst, const i
     h->rev->stream = h->stream;
     rc = ingest_batch(h->rev, dst, src, ts, n, nullptr);
     if (rc) {
-        fail(h, rc, "tempest_ingest: the in-edge index failed (%s); backward walks are off until "
-                    "tempest_enable_backward", h->rev->err.c_str());
-        cudaStreamSynchronize(h->stream);
-        tempest_destroy(h->rev);
-        h->rev = nullptr;
+        // the in-edge index restored itself; the main index is undone too, so
+        // that both hold the same edges and the call changed nothing
+        const std::string why = h->rev->err;
+        ingest_undo(h, undo);
+        views_repair(h);  // best effort: a repair that fails is retried by the next call
+        fail(h, rc, "tempest_ingest: the in-edge index failed (%s); the batch was not ingested", why.c_str());
     }
     return rc;
 }
@@ -720,6 +722,7 @@ int tempest_export_state(tempest_t *h, int which, void *dst, int64_t cap, int64_
     const size_t bytes = esz * (size_t)cnt;
     const bool dev = is_device_ptr(dst);
     int rc;
+    if ((rc = views_repair(h))) return rc;
     if (!h->nv_ready || !h->tg.p) {
         // nothing ingested yet: every remaining array is the single offset 0
         if (dev) return cuda_check(h, cudaMemsetAsync(dst, 0, bytes, st), "export");

@@ -157,6 +157,10 @@ struct tempest {
     tw::DBuf touched;  // int32: node of each batch-local id
     int64_t S = 0;     // nodes that own regions (for the bucket index)
     int64_t state_ver = 0;  // bumped by every ingest
+    // an ingest that failed after changing the store restored the store's
+    // counters; the views (and the pair table) are rebuilt from the store
+    // before their next use
+    bool views_dirty = false;
 
     // time buckets of high-degree nodes (built lazily for the walks of a
     // state version): per node its table base, the tables, the big-segment
@@ -237,8 +241,27 @@ int cuda_check(tempest_t *h, cudaError_t e, const char *what);
 bool is_device_ptr(const void *p);
 
 // ingest.cu
+// The handle's counters before an ingest.  Through one ingest the store's
+// previous live range stays in place (an append writes past it, a move or a
+// merge writes the other buffer), so restoring these counters and rebuilding
+// the views from the store undoes the ingest.
+struct IngestUndo {
+    int64_t m, G, N, M, Gn, dropped, evicted, seq_next, cutoff;
+    int64_t s_lo, s_hi, s_cap, s_base, tg_lo, tg_hi, n_act, S;
+    int has_cutoff, cur;
+};
+// Ingests one batch; on an error after the store changed (a failed
+// allocation, a failed consistency check) the state is restored first, so
+// a failed call leaves the handle as it was.  undo (nullable) receives the
+// state before a successful call, for ingest_undo.
 int ingest_batch(tempest_t *h, const int32_t *src, const int32_t *dst, const int64_t *ts, int64_t n,
-                 tempest_ingest_stats *stats);
+                 tempest_ingest_stats *stats, IngestUndo *undo = nullptr);
+// Restores the state recorded before the handle's last ingest (no other
+// ingest since) and marks the views for a rebuild.
+void ingest_undo(tempest_t *h, const IngestUndo &u);
+// Rebuilds the views and the pair table from the store when an undo left them
+// stale (no-op otherwise).  Every call that reads a view runs it first.
+int views_repair(tempest_t *h);
 
 // nodeview.cu
 int nv_ensure_nodes(tempest_t *h, int64_t N);

@@ -317,8 +317,127 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
     return 2 * W + W / 2 + nbk + 1024;
 }
 
+static IngestUndo undo_record(const tempest_t *h)
+{
+    IngestUndo u;
+    u.m = h->m;
+    u.G = h->G;
+    u.N = h->N;
+    u.M = h->M;
+    u.Gn = h->Gn;
+    u.dropped = h->dropped;
+    u.evicted = h->evicted;
+    u.seq_next = h->seq_next;
+    u.cutoff = h->cutoff;
+    u.s_lo = h->s_lo;
+    u.s_hi = h->s_hi;
+    u.s_cap = h->s_cap;
+    u.s_base = h->s_base;
+    u.tg_lo = h->tg_lo;
+    u.tg_hi = h->tg_hi;
+    u.n_act = h->n_act;
+    u.S = h->S;
+    u.has_cutoff = h->has_cutoff;
+    u.cur = h->cur;
+    return u;
+}
+
+void ingest_undo(tempest_t *h, const IngestUndo &u)
+{
+    h->m = u.m;
+    h->G = u.G;
+    h->N = u.N;
+    h->M = u.M;
+    h->Gn = u.Gn;
+    h->dropped = u.dropped;
+    h->evicted = u.evicted;
+    h->seq_next = u.seq_next;
+    h->cutoff = u.cutoff;
+    h->s_lo = u.s_lo;
+    h->s_hi = u.s_hi;
+    h->s_cap = u.s_cap;
+    h->s_base = u.s_base;
+    h->tg_lo = u.tg_lo;
+    h->tg_hi = u.tg_hi;
+    h->n_act = u.n_act;
+    h->S = u.S;
+    h->has_cutoff = u.has_cutoff;
+    h->cur = u.cur;
+    // the views may hold part of the undone batch: rebuilt from the store
+    h->nv_ready = false;
+    h->w_valid = false;
+    h->views_dirty = true;
+    h->state_ver++;
+}
+
+int views_repair(tempest_t *h)
+{
+    if (!h->views_dirty) return TEMPEST_OK;
+    cudaStream_t st = h->stream;
+    int rc;
+    if ((rc = ensure(h, h->dstat, sizeof(IngestScratch)))) return rc;
+    if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
+    if ((rc = ensure(h, h->hist, sizeof(uint32_t) * (size_t)SORT_HIST_WORDS))) return rc;
+    IngestScratch *ds = h->dstat.as<IngestScratch>();
+    IngestScratch *hs = static_cast<IngestScratch *>(h->hstat);
+    h->state_ver++;
+    if (h->m == 0) {
+        // the state of a handle with no live edge: empty views, built by the
+        // next ingest
+        h->tg_lo = h->tg_hi = 0;
+        h->G = 0;
+        h->views_dirty = false;
+        return TEMPEST_OK;
+    }
+    k_init_scratch<<<1, 1, 0, st>>>(ds);
+    if ((rc = ts_view_build(h))) return rc;
+    cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "view repair"))) return rc;
+    h->tg_lo = 0;
+    h->tg_hi = hs->tg_added;
+    h->G = h->tg_hi;
+    if ((rc = nv_build(h))) return rc;
+    if (h->pt_on) {
+        if ((rc = pt_rebuild(h, &ds->status))) return rc;
+        cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
+        if ((rc = cuda_check(h, cudaStreamSynchronize(st), "view repair"))) return rc;
+        if (hs->status)
+            return fail(h, TEMPEST_ECUDA, "view repair: pair table check failed (code 0x%llx)",
+                        (unsigned long long)hs->status);
+    }
+    h->views_dirty = false;
+    return TEMPEST_OK;
+}
+
+static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in,
+                             int64_t n, tempest_ingest_stats *stats, bool *changing);
+
 int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in, int64_t n,
-                 tempest_ingest_stats *stats)
+                 tempest_ingest_stats *stats, IngestUndo *undo)
+{
+    int rc = views_repair(h);
+    if (rc) return rc;
+    const IngestUndo u = undo_record(h);
+    bool changing = false;
+    rc = ingest_batch_impl(h, src_in, dst_in, ts_in, n, stats, &changing);
+    if (rc == TEMPEST_OK) {
+        if (undo) *undo = u;
+        return rc;
+    }
+    // nothing to undo when the call failed before it began to change the state
+    if (changing) {
+        // keep the first error's message: the repair is best effort here (a
+        // repair that fails again is retried by the next call)
+        const std::string msg = h->err;
+        ingest_undo(h, u);
+        views_repair(h);
+        h->err = msg;
+    }
+    return rc;
+}
+
+static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in,
+                             int64_t n, tempest_ingest_stats *stats, bool *changing)
 {
     cudaStream_t st = h->stream;
     int rc;
@@ -425,11 +544,12 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
     const int64_t m_new = na + nbk;
     const bool append = na == 0 || nbk == 0 || hs->store_last_ts <= hs->kept_batch_min_ts;
 
-    // 4. store
+    // 4. store (from here on a failure is undone by the caller)
+    *changing = true;
     const int64_t N_old = h->N;
     const int old_buf = h->cur;
     const int64_t old_lo = h->s_lo;
-    bool ts_full = !append || !h->tg.p;
+    bool ts_full = !append || !h->tg.p || h->views_dirty;
     bool nv_full = !append || !h->nv_ready;
     int64_t new_lo = 0;  // first appended index
     if (append) {
@@ -541,12 +661,7 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
         rc = append ? pt_update(h, h->st_src[old_buf].as<int32_t>() + old_lo,
                                 h->st_dst[old_buf].as<int32_t>() + old_lo, i0, new_lo, nbk, &ds->status)
                     : pt_rebuild(h, &ds->status);
-        if (rc) {
-            // walks need the table again: tempest_set_node2vec rebuilds it
-            h->pt_on = false;
-            release(h, h->pt);
-            return rc;
-        }
+        if (rc) return rc;  // undone by the caller, which rebuilds the table from the restored store
     }
 
     cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
