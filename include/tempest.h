@@ -474,7 +474,9 @@ const char *tempest_version(void);
  * Scratch is a static device array of TEMPEST_NOALLOC_SCRATCH_BYTES that
  * every GPU loading the library holds until the process exits; nothing is
  * allocated or freed.  The first call on a device looks up that array's
- * device address, so make it before any stream capture.  All calls share the
+ * device address, so make it before any stream capture; the address is
+ * looked up again when the device's context has changed since (after a
+ * cudaDeviceReset), so call it again outside a capture then.  All calls share the
  * array: calls whose work overlaps on the GPU race.  Returns EINVAL (see
  * tempest_last_error(NULL)) for n < 0, n > TEMPEST_NOALLOC_MAX_EDGES or a
  * non-device array; n == 0 does nothing. */

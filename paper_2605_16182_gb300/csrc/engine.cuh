@@ -7,6 +7,8 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tempest.h"
 
 namespace tw {
@@ -232,6 +234,33 @@ struct tempest {
 };
 
 namespace tw {
+
+// A named NVTX range on the calling host thread for the lifetime of the
+// object: the stages of an ingest and of a walk call show up by name in a
+// timeline profiler (NVTX is header-only; without a tool attached a range
+// costs a branch).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// Consecutive stages of one function: next() closes the open range and
+// opens the next; the last one closes with the object.
+struct NvtxStages {
+    bool open = false;
+    void next(const char *name)
+    {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~NvtxStages()
+    {
+        if (open) nvtxRangePop();
+    }
+};
 
 // allocation helpers (capi.cu)
 int ensure(tempest_t *h, DBuf &b, size_t bytes, bool headroom = false);

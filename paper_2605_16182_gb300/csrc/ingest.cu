@@ -370,9 +370,24 @@ void ingest_undo(tempest_t *h, const IngestUndo &u)
     h->state_ver++;
 }
 
+static int views_rebuild(tempest_t *h);
+
 int views_repair(tempest_t *h)
 {
     if (!h->views_dirty) return TEMPEST_OK;
+    // the rebuild resets the view counters before it allocates: keep them
+    // for a rebuild that fails (the state the counters describe is unchanged)
+    const IngestUndo u = undo_record(h);
+    const int rc = views_rebuild(h);
+    if (rc) {
+        ingest_undo(h, u);
+        return rc;
+    }
+    return TEMPEST_OK;
+}
+
+static int views_rebuild(tempest_t *h)
+{
     cudaStream_t st = h->stream;
     int rc;
     if ((rc = ensure(h, h->dstat, sizeof(IngestScratch)))) return rc;
@@ -415,6 +430,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
 int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in, int64_t n,
                  tempest_ingest_stats *stats, IngestUndo *undo)
 {
+    NvtxRange range("tempest_ingest");
     int rc = views_repair(h);
     if (rc) return rc;
     const IngestUndo u = undo_record(h);
@@ -439,6 +455,8 @@ int ingest_batch(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, con
 static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t *dst_in, const int64_t *ts_in,
                              int64_t n, tempest_ingest_stats *stats, bool *changing)
 {
+    NvtxStages stage;
+    stage.next("ingest: stage inputs");
     cudaStream_t st = h->stream;
     int rc;
     if (n < 0) return fail(h, TEMPEST_EINVAL, "tempest_ingest: n = %lld < 0", (long long)n);
@@ -477,6 +495,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     }
 
     // 1. batch statistics
+    stage.next("ingest: batch statistics");
     k_init_scratch<<<1, 1, 0, st>>>(ds);
     if (n > 0)
         k_batch_stats<<<grid_for(h, n), 256, 0, st>>>(src, dst, ts, n, h->has_cutoff, h->cutoff, ds);
@@ -500,6 +519,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
                     (long long)M_max);
 
     // 2. sort the batch by timestamp (stable), late edges become a prefix
+    stage.next("ingest: batch sort");
     const int32_t *bs = src;
     const int32_t *bd = dst;
     const int64_t *bt = ts;
@@ -532,6 +552,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     const int64_t nb = n - late;
 
     // 3. window cut-off
+    stage.next("ingest: window cut-off");
     const int mode = h->window > 0 ? 1 : (h->window < 0 ? 2 : 0);
     const long long param = h->window > 0 ? h->window : -h->window;
     const int64_t *old_ts = h->m > 0 ? h->st_ts[h->cur].as<int64_t>() + h->s_lo : nullptr;
@@ -545,6 +566,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     const bool append = na == 0 || nbk == 0 || hs->store_last_ts <= hs->kept_batch_min_ts;
 
     // 4. store (from here on a failure is undone by the caller)
+    stage.next("ingest: store");
     *changing = true;
     const int64_t N_old = h->N;
     const int old_buf = h->cur;
@@ -623,6 +645,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     h->cutoff = hs->cut;
 
     // 5. timestamp view
+    stage.next("ingest: timestamp view");
     if (!ts_full && (int64_t)(h->tg.bytes / sizeof(int32_t)) < h->tg_hi + nbk + 2) {
         // move the live starts [tg_lo, tg_hi] to the front of a larger buffer
         const int64_t live = h->tg_hi - h->tg_lo + 1;
@@ -646,6 +669,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     }
 
     // 6. node view
+    stage.next("ingest: node view");
     if (!nv_full) {
         bool rebuild = false;
         rc = nv_append(h, h->st_src[old_buf].as<int32_t>() + old_lo, h->st_dst[old_buf].as<int32_t>() + old_lo, i0,
@@ -655,6 +679,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     }
     if (nv_full && (rc = nv_build(h))) return rc;
 
+    stage.next("ingest: pair table");
     // 7. Node2Vec pair table: the evicted edges out, the kept batch in (a
     // rebuild after a merge, whose evicted edges are not a store range)
     if (h->pt_on) {

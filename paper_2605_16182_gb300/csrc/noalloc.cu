@@ -14,6 +14,8 @@
 // it has to start at zero, because every sort pass writes the histogram and
 // the key / value buffers it later reads.  Calls whose work overlaps on the
 // GPU (different streams, or different host threads) race on the array.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "engine.cuh"
@@ -64,11 +66,47 @@ __global__ void k_noalloc_gather(const uint32_t *__restrict__ perm, const int32_
     }
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (a host-side use of the symbol's name would not be a device
-// address).
-static unsigned char *g_scratch_addr[64];
+// Device address of the scratch array, looked up once per device and
+// context with that device current (a host-side use of the symbol's name
+// would not be a device address).  The address belongs to the context that
+// loaded the module: after cudaDeviceReset the next context may load it
+// elsewhere, so each cached address carries its context's unique id and is
+// looked up again when the current context's id differs.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    unsigned char *p;
+};
+static ScratchAddr g_scratch_addr[64];
 static std::mutex g_scratch_mu;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 when there is none or
+// the driver does not report one).
+static unsigned long long current_ctx_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess && qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+            get_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+        cudaGetLastError();
+        resolved = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 static int scratch_for_current_device(unsigned char **out)
 {
@@ -80,17 +118,21 @@ static int scratch_for_current_device(unsigned char **out)
     }
     if (dev < 0 || dev >= 64) return fail(nullptr, TEMPEST_EINVAL, "tempest_sort_batch_noalloc: device %d", dev);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    ScratchAddr &c = g_scratch_addr[dev];
+    if (!c.p || id == 0 || c.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
+            c.p = nullptr;
             return fail(nullptr, TEMPEST_ECUDA, "tempest_sort_batch_noalloc: cudaGetSymbolAddress: %s",
                         cudaGetErrorString(e));
         }
-        g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+        c.p = static_cast<unsigned char *>(p);
+        c.ctx_id = current_ctx_id();  // the lookup made the device's primary context current
     }
-    *out = g_scratch_addr[dev];
+    *out = c.p;
     return TEMPEST_OK;
 }
 

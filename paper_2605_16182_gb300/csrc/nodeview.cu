@@ -614,6 +614,7 @@ int nv_ensure_nodes(tempest_t *h, int64_t N)
 // Whole view from the live store.
 int nv_build(tempest_t *h)
 {
+    NvtxRange range("node view: rebuild");
     cudaStream_t st = h->stream;
     const int64_t m = h->s_hi - h->s_lo;
     const int64_t M = h->directed ? m : 2 * m;
@@ -716,6 +717,8 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
     const int64_t ne = directed ? n_ev : 2 * n_ev, nbe = directed ? nbk : 2 * nbk;
     int rc;
     *rebuild = false;
+    NvtxStages stage;
+    stage.next("node view: eviction");
     if ((rc = nv_ensure_nodes(h, N))) return rc;
     if ((rc = ensure(h, h->nvc, sizeof(NvCounters)))) return rc;
     NvCounters *dc = h->nvc.as<NvCounters>();
@@ -744,6 +747,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         if ((rc = ensure(h, h->nv_tmp, sizeof(int32_t) * (size_t)(runs_max + 1), true))) return rc;
         const Items it = items_at(h, h->cur, new_lo);
         // batch-local node ids (keys in run_of, which the run scan rewrites later)
+        stage.next("node view: batch ids and sort");
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
         cudaMemsetAsync(h->touched.p, 0xff, sizeof(int32_t) * (size_t)nbe, st);
         uint32_t *dkeys = reinterpret_cast<uint32_t *>(h->run_of.as<int32_t>());
@@ -767,6 +771,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
             k_iota<<<grid_for(h, nbe), 256, 0, st>>>(vb[0], nbe);
             r = 0;
         }
+        stage.next("node view: runs and regions");
         uint64_t *part = h->partials.as<uint64_t>();
         AppendRunOp op{kb[r], vb[r], h->touched.as<int32_t>(), it, h->ngr.as<NodeRange>(),
                        h->run_of.as<int32_t>(),
@@ -791,6 +796,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
             return TEMPEST_OK;
         }
         const int64_t n_reloc = (int64_t)hc->n_reloc;
+        stage.next("node view: region moves and scatter");
         if (n_reloc > 0) {
             RelocChunkOp rop{h->reloc.as<Reloc>(), h->nv_tmp.as<int32_t>()};
             const int nb2 = scan_launch(rop, n_reloc, part, st);

@@ -1189,6 +1189,8 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     h->kev_valid = false;
     tempest_t *vh = view_handle(h, rq.direction);
     if (!vh) return fail(h, TEMPEST_EINVAL, "backward walks of a directed graph need tempest_enable_backward");
+    NvtxStages stage;
+    stage.next("walks: index");
     if ((rc = prepare_walk_index(vh))) return rc;
     if (rq.direction == 0 &&
         ((!rq.bias_arr && rq.bias == TEMPEST_BIAS_EXP_WEIGHT) || rq.want_w || (rq.bias_arr && h->w_on)))
@@ -1214,6 +1216,7 @@ int walks_run(tempest_t *h, const WalkRequest &rq)
     O.cnt = h->wcnt.as<WalkCounters>();
     int64_t launches = 0;
     for (int t = 0; t < 5; t++) h->coop_tier_launches[t] = 0;
+    stage.next("walks: kernels");
     if (rq.n_walks > 0) {
         if (h->sched == TEMPEST_SCHED_COOP || h->sched == TEMPEST_SCHED_GRAPH) {
             kernel_mark(h, 0);

@@ -5,11 +5,14 @@ a fixed static scratch array instead.  The GPU test calls it through the C
 ABI twice in a row -- the second call runs on whatever the first left in the
 shared scratch -- and checks both results against the batch order the
 regular ingest path produces (tempest_ingest into an unbounded window, then
-the exported edge store).  Integer results, so the comparison is exact.
+the exported edge store) and against the oracle's live edges after the same
+batch (a stable sort by timestamp, arrival order among ties).  Integer
+results, so the comparison is exact.
 """
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2605_16182_gb300 import _lib
 
 
@@ -52,8 +55,13 @@ def test_noalloc_sort_matches_ingest_on_two_calls_in_a_row():
     for s, d, t in batches:
         got = _via_noalloc(s, d, t)
         want = _via_ingest(s, d, t)
-        for g, w, name in zip(got, want, ("src", "dst", "ts")):
-            assert np.array_equal(g, w), name
+        orc = O.Oracle(0, True)
+        orc.ingest(s, d, t)
+        st = orc.state()
+        orc.close()
+        for g, w, o, name in zip(got, want, (st["src"], st["dst"], st["ts"]), ("src", "dst", "ts")):
+            assert np.array_equal(g, w), name + " (ingest)"
+            assert np.array_equal(g, o), name + " (oracle)"
 
 
 def test_noalloc_rejects_oversized_batch():
