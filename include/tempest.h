@@ -127,6 +127,17 @@ typedef struct {
                               timestamp view evict by moving a head, O(1).  0
                               when nothing was evicted or the batch rebuilt
                               the node view (eviction is then part of it) */
+    int64_t model_bytes;   /* algorithmic bytes of this batch in this library's
+                              design: each array the batch touches (the batch,
+                              the store append, the timestamp view's new
+                              group starts, the evicted edges' ids and their
+                              nodes' records, the node view's batch sort
+                              passes, runs, region moves and scatter) read or
+                              written once for its role; a full rebuild of
+                              the node view counts its whole sort and
+                              scatter over the live entries */
+    int32_t view_rebuilt;  /* 1 when the batch rebuilt the node view whole */
+    int32_t reserved;
 } tempest_ingest_stats;
 
 /* Per-call walk report (valid once the call's work has finished). */

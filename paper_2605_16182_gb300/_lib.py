@@ -63,7 +63,8 @@ class IngestStats(ctypes.Structure):
                 ("n_ts_groups", ctypes.c_int64), ("n_node_groups", ctypes.c_int64),
                 ("n_nodes", ctypes.c_int64), ("cutoff", ctypes.c_int64),
                 ("has_cutoff", ctypes.c_int32), ("sorted_input", ctypes.c_int32),
-                ("launches", ctypes.c_int64), ("evict_ms", ctypes.c_double)]
+                ("launches", ctypes.c_int64), ("evict_ms", ctypes.c_double),
+                ("model_bytes", ctypes.c_int64), ("view_rebuilt", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -67,6 +67,19 @@ struct NvCounters {
     unsigned long long status;        // nonzero: a consistency check failed
     unsigned long long n_dense;       // batch-local node ids handed out
     unsigned long long w_rebase;      // a group weight's exponent grew too large
+    unsigned long long moved_e;       // live entries of the regions that move (a batch's report)
+    unsigned long long moved_g;       // live groups of the regions that move
+    unsigned long long g_added;       // groups the batch adds
+};
+
+// What the node view did for one batch: the counts its algorithmic-bytes
+// model needs (see ingest_model_bytes).
+struct NvBatchReport {
+    int64_t ev_entries = 0, ev_nodes = 0;              // evicted entries and the nodes that lost them
+    int64_t entries = 0, ids = 0, passes = 0, runs = 0;  // appended entries, distinct nodes, sort passes, node runs
+    int64_t moved_e = 0, moved_g = 0, g_added = 0;     // region moves; groups added
+    bool rebuilt = false;                               // the whole view was rebuilt instead
+    int64_t rb_entries = 0, rb_passes = 0, rb_nodes = 0, rb_groups = 0;
 };
 
 // A region move: live entries and groups of one node to fresh regions.
@@ -163,6 +176,7 @@ struct tempest {
     // counters; the views (and the pair table) are rebuilt from the store
     // before their next use
     bool views_dirty = false;
+    tw::NvBatchReport nv_rep;  // the node view's part of the last batch
 
     // time buckets of high-degree nodes (built lazily for the walks of a
     // state version): per node its table base, the tables, the big-segment

@@ -317,6 +317,53 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
     return 2 * W + W / 2 + nbk + 1024;
 }
 
+// Algorithmic bytes of one ingest in this design: each array the batch
+// touches, read or written once for its role, per-node records at their
+// size (not the sectors a random access occupies).  b = batch edges, k =
+// kept edges, E / P / U / R = the node view's appended entries, radix
+// passes, distinct nodes and node runs, e / u = evicted entries and the
+// nodes that lost them:
+//   16 b                 batch statistics (src, dst, ts read)
+//   P_ts (24 b) + 32 b   timestamp sort of an unsorted batch (8-byte key and
+//                        4-byte index read and written per pass), gather
+//   32 k                 store append (kept batch read, store written); a
+//                        merge instead reads both sides and writes the store
+//   8 k + 4 G_new        timestamp view (group starts of the kept batch)
+//   4 e + 104 u          eviction: endpoint ids read; per node its counter
+//                        (8) and its records (16 + 32) read and written
+//   8 E + 16 U           batch-local ids (ids read, keys written, id table)
+//   20 P E               node sort passes (key read for the histogram, key
+//                        and value read and written by the scatter)
+//   24 E + 148 R         runs (keys, values and timestamps read, run index
+//                        written; per run its arrays, node record and the
+//                        region reservation)
+//   32 E_moved + 24 G_moved   region moves (entries, group starts and times)
+//   44 E + 12 G_added    scatter (index, run and group ids read, the store
+//                        item gathered, the 16-byte entry and new groups
+//                        written)
+// A full rebuild of the node view (after a merge or a pool exhaustion)
+// counts its whole sort and scatter over the live entries instead.
+static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, int64_t kept_old, int64_t m_new,
+                                  int ts_passes, bool append, bool ts_full, int64_t tg_added, int64_t G)
+{
+    int64_t x = 16 * b;
+    if (ts_passes > 0) x += ts_passes * 24 * b + 32 * b;
+    x += append ? 32 * k : 16 * (kept_old + k) + 16 * m_new;
+    x += ts_full ? 8 * m_new + 4 * G : 8 * k + 4 * tg_added;
+    if (r.rebuilt) {
+        const int64_t M = r.rb_entries;
+        x += M * (8 + 20 * r.rb_passes + 32 + 32 + 32) + 12 * r.rb_groups + 104 * r.rb_nodes;
+    } else {
+        x += 4 * r.ev_entries + 104 * r.ev_nodes;
+        x += 8 * r.entries + 16 * r.ids;
+        x += 20 * r.passes * r.entries;
+        x += 24 * r.entries + 148 * r.runs;
+        x += 32 * r.moved_e + 24 * r.moved_g;
+        x += 44 * r.entries + 12 * r.g_added;
+    }
+    return x;
+}
+
 static IngestUndo undo_record(const tempest_t *h)
 {
     IngestUndo u;
@@ -457,6 +504,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
 {
     NvtxStages stage;
     stage.next("ingest: stage inputs");
+    h->nv_rep = NvBatchReport{};
     cudaStream_t st = h->stream;
     int rc;
     if (n < 0) return fail(h, TEMPEST_EINVAL, "tempest_ingest: n = %lld < 0", (long long)n);
@@ -694,6 +742,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     if (hs->status)
         return fail(h, TEMPEST_ECUDA, "ingest: index consistency check failed (code 0x%llx)",
                     (unsigned long long)hs->status);
+    const int64_t tg_added_now = (int64_t)hs->tg_added;
     if (ts_full) {
         h->tg_lo = 0;
         h->tg_hi = hs->tg_added;
@@ -720,6 +769,11 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
         // makes the batch's eviction part of the rebuild
         stats->evict_ms = (h->eev_valid && !nv_full && cudaEventElapsedTime(&ms, h->eev[0], h->eev[1]) == cudaSuccess)
                               ? (double)ms : 0.0;
+        const int ts_passes = sorted ? 0 : (bits_for(span) + RADIX_BITS - 1) / RADIX_BITS;
+        stats->model_bytes = ingest_model_bytes(h->nv_rep, n, nbk, na, m_new, ts_passes, append, ts_full,
+                                                tg_added_now, h->G);
+        stats->view_rebuilt = h->nv_rep.rebuilt ? 1 : 0;
+        stats->reserved = 0;
     }
     return TEMPEST_OK;
 }

@@ -377,6 +377,8 @@ __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t
                 nbeg[v] = make_int2((int32_t)eb, (int32_t)gb);
             }
             if (live_e > 0 || live_g > 0) {
+                atomicAdd(&c->moved_e, (unsigned long long)live_e);
+                atomicAdd(&c->moved_g, (unsigned long long)live_g);
                 const unsigned long long t = atomicAdd(&c->n_reloc, 1ull);
                 reloc[t] = Reloc{rec.x, live_e, (int32_t)eb, g.x, live_g, (int32_t)gb};
             }
@@ -396,7 +398,10 @@ __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t
         added += gc;
     }
     added = warp_sum((unsigned long long)added);
-    if ((threadIdx.x & 31) == 0 && added) atomicAdd((unsigned long long *)&c->gn_delta, (unsigned long long)added);
+    if ((threadIdx.x & 31) == 0 && added) {
+        atomicAdd((unsigned long long *)&c->gn_delta, (unsigned long long)added);
+        atomicAdd(&c->g_added, (unsigned long long)added);
+    }
 }
 
 struct RelocChunkOp {
@@ -701,6 +706,11 @@ int nv_build(tempest_t *h)
     h->Gn = Gn;
     h->nv_ready = true;
     h->w_valid = false;  // new regions: the weights are recomputed for the next walks
+    h->nv_rep.rebuilt = true;
+    h->nv_rep.rb_entries = M;
+    h->nv_rep.rb_passes = (bits_for((uint64_t)(N > 0 ? N - 1 : 0)) + RADIX_BITS - 1) / RADIX_BITS;
+    h->nv_rep.rb_nodes = S;
+    h->nv_rep.rb_groups = Gn;
     return TEMPEST_OK;
 }
 
@@ -719,6 +729,9 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
     *rebuild = false;
     NvtxStages stage;
     stage.next("node view: eviction");
+    NvBatchReport &rep = h->nv_rep;
+    rep.ev_entries = ne;
+    rep.entries = nbe;
     if ((rc = nv_ensure_nodes(h, N))) return rc;
     if ((rc = ensure(h, h->nvc, sizeof(NvCounters)))) return rc;
     NvCounters *dc = h->nvc.as<NvCounters>();
@@ -764,6 +777,9 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
         int launches = 0;
         const DenseLoader dl{dkeys};
+        rep.ids = n_ids;
+        rep.runs = n_ids;  // one run per distinct node of the batch
+        rep.passes = (bits_for((uint64_t)(n_ids > 0 ? n_ids - 1 : 0)) + RADIX_BITS - 1) / RADIX_BITS;
         int r = radix_sort_launch<uint32_t>(dl, nbe, bits_for((uint64_t)(n_ids > 0 ? n_ids - 1 : 0)), kb, vb,
                                             h->hist.as<uint32_t>(), st, &launches);
         if (r < 0) {  // a single distinct node: the batch order is already grouped
@@ -826,6 +842,10 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         return fail(h, TEMPEST_ECUDA, "node view: consistency check failed (code 0x%llx)",
                     (unsigned long long)hc->status);
     h->Gn += (int64_t)hc->gn_delta;
+    rep.ev_nodes = (int64_t)hc->n_ev_nodes;
+    rep.moved_e = (int64_t)hc->moved_e;
+    rep.moved_g = (int64_t)hc->moved_g;
+    rep.g_added = (int64_t)hc->g_added;
     if (hc->w_rebase) h->w_valid = false;  // a weight exponent grew large: move every reference
     h->n_act = (int64_t)hc->n_act;
     h->S = h->n_act;

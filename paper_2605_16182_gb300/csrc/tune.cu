@@ -234,8 +234,8 @@ static int autotune_impl(tempest_t *h, int64_t n_walks, int32_t max_len, const i
         rc = T.sweep(best, best_ms, logs, 5, [](Cfg &c, int v) { c.bkt_log = v; });
     }
     if (!rc && (best.sched == TEMPEST_SCHED_STREAM || best.sched == TEMPEST_SCHED_LANE)) {
-        const int ctas[] = {2, 3, 4, 5};
-        rc = T.sweep(best, best_ms, ctas, 4, [](Cfg &c, int v) { c.ctas = v; });
+        const int ctas[] = {2, 3, 4, 5, 6};
+        rc = T.sweep(best, best_ms, ctas, 5, [](Cfg &c, int v) { c.ctas = v; });
     }
     if (!rc && best.sched == TEMPEST_SCHED_LANE && !T.rq.len_arr) {
         const int pp[] = {0, 1};

@@ -1036,23 +1036,28 @@ template <class P, bool BACK, bool PAD>
 static void launch_lane_pad(tempest_t *h, const WalkView &V, const P &Pv, unsigned long long *next, int64_t total,
                             cudaStream_t st, bool n2v)
 {
-    static int occ = 0, occ5 = 0, occn = 0;
+    static int occ = 0, occ5 = 0, occ6 = 0, occn = 0;
     if (occ == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walks_lane<P, 4, false, BACK, PAD>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_walks_lane<P, 5, false, BACK, PAD>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ6, k_walks_lane<P, 6, false, BACK, PAD>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_walks_lane<P, LANE_N2V_MINB<P>, true, BACK, PAD>, 256, 0);
         if (occ < 1) occ = 1;
         if (occ5 < 1) occ5 = 1;
+        if (occ6 < 1) occ6 = 1;
         if (occn < 1) occn = 1;
     }
-    const bool wide = h->stream_ctas > 4 && !n2v;
-    const int o = n2v ? occn : (wide ? occ5 : occ);
+    // the build for the CTAs per SM the knob asks for: 4 (no spills), 5 or
+    // 6 (fewer registers, more warps to hide the hops' dependent loads)
+    const int minb = n2v ? 0 : (h->stream_ctas >= 6 ? 6 : (h->stream_ctas == 5 ? 5 : 4));
+    const int o = n2v ? occn : (minb == 6 ? occ6 : (minb == 5 ? occ5 : occ));
     const int bps = h->stream_ctas > 0 ? std::min(h->stream_ctas, o) : o;
     int64_t grid = (int64_t)h->num_sms * bps;
     const int64_t need = (total + 255) / 256;
     if (grid > need) grid = need;
     if (n2v) k_walks_lane<P, LANE_N2V_MINB<P>, true, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
-    else if (wide) k_walks_lane<P, 5, false, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else if (minb == 6) k_walks_lane<P, 6, false, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
+    else if (minb == 5) k_walks_lane<P, 5, false, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
     else k_walks_lane<P, 4, false, BACK, PAD><<<(unsigned)grid, 256, 0, st>>>(V, Pv, next);
 }
 

@@ -185,32 +185,28 @@ def test_memory_that_stays_short_is_repaired_later(directed):
 
 
 def test_hbm_budget_below_the_next_batch():
-    """A budget under what the stream grows to: the first ingest past it
-    returns ENOMEM with the state unchanged; with a larger budget (same
-    allocator) the same batch goes in and the stream ends in the oracle's
-    state."""
+    """A budget set just above what the handle holds, before a batch that
+    needs more: that ingest returns ENOMEM (the budget's message) with the
+    state unchanged; with the budget lifted (same allocator) the same batch
+    goes in and the stream ends in the oracle's state."""
     spec, batches = stream_batches()
     _, states = oracle_states(spec, batches, True)
+    counts = alloc_counts(spec, batches, True, False)
+    k = next(i for i, c in enumerate(counts) if i >= 2 and c > 0)
     eng, fa = engine(spec.window, True)
-    for b in batches:
+    for b in batches[:k]:
         ingest(eng, b)
-    peak = fa.peak
-    eng.close()
-    eng, fa = engine(spec.window, True, budget=int(peak * 0.6))
-    failed_at = None
-    for k, b in enumerate(batches):
-        try:
-            ingest(eng, b)
-        except _lib.TempestError as e:
-            assert e.code == _lib.TEMPEST_ENOMEM and "budget" in str(e), str(e)
-            failed_at = k
-            break
-    assert failed_at is not None and failed_at > 0
-    assert_state_equal(eng.state(), states[failed_at], "budget reached at batch %d" % failed_at)
+    held = sum(fa.live.values())
+    _lib.tempest_set_allocator(eng.h, fa.fns[0], fa.fns[1], None, held + 256)
+    with pytest.raises(_lib.TempestError) as ei:
+        ingest(eng, batches[k])
+    assert ei.value.code == _lib.TEMPEST_ENOMEM and "budget" in str(ei.value), str(ei.value)
+    assert sum(fa.live.values()) <= held + 256
+    assert_state_equal(eng.state(), states[k], "budget reached at batch %d" % k)
     _lib.tempest_set_allocator(eng.h, fa.fns[0], fa.fns[1], None, 0)
-    for b in batches[failed_at:]:
+    for b in batches[k:]:
         ingest(eng, b)
-    assert_state_equal(eng.state(), states[-1], "end of stream after the budget was raised")
+    assert_state_equal(eng.state(), states[-1], "end of stream after the budget was lifted")
     eng.close()
 
 
@@ -258,8 +254,19 @@ def test_failed_ingest_keeps_the_node2vec_pair_table():
     orc.set_node2vec(0.5, 2.0)
     eng, fa = engine(spec.window, True)
     eng.set_node2vec(0.5, 2.0)
+    # the batches whose ingest allocates (the pair table grows with the window)
+    ceng, cfa = engine(spec.window, True)
+    ceng.set_node2vec(0.5, 2.0)
+    grow = []
     for k, b in enumerate(batches):
-        if k in (4, 9):
+        c0 = cfa.count
+        ingest(ceng, b)
+        if cfa.count > c0 and k >= 1:
+            grow.append(k)
+    ceng.close()
+    assert len(grow) >= 2, grow
+    for k, b in enumerate(batches):
+        if k in grow[:2]:
             fa.arm(0, persist=True)
             with pytest.raises(_lib.TempestError):
                 ingest(eng, b)
