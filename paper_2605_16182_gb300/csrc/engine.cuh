@@ -311,6 +311,8 @@ int nv_ensure_nodes(tempest_t *h, int64_t N);
 int nv_build(tempest_t *h);
 int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_t n_ev, int64_t new_lo, int64_t nbk,
               int64_t N_old, bool *rebuild);
+// allocates what nv_append will need for the batch, before anything changes
+int nv_prepare_append(tempest_t *h, int64_t n_ev, int64_t nbk, int64_t N_old, int64_t N_new);
 // canonical NODE_OFF / NODE_ORDER / NODE_GROUP_OFF / NODE_GIDX into device memory
 int nv_export(tempest_t *h, int which, int32_t *out);
 // timestamp-group starts relative to the live head, plus m (G + 1 values)

@@ -32,23 +32,46 @@ namespace tw {
 // ---------------------------------------------------------------------------
 // batch statistics
 // ---------------------------------------------------------------------------
-__global__ void k_batch_stats(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                              const int64_t *__restrict__ ts, int64_t n, int has_cut, long long cut,
-                              IngestScratch *o)
+// One pass over the batch: timestamp range, largest id, reserved values,
+// late edges and whether the timestamps already ascend.  Each thread keeps
+// four loads of each array in flight (grid-stride, unrolled); each warp and
+// then each block reduce in registers and shared memory, so the global
+// atomics are one set per block (per-warp atomics on the same six words
+// serialised at L2).
+constexpr int STATS_THREADS = 256;
+constexpr int STATS_UNROLL = 4;
+
+__global__ void __launch_bounds__(STATS_THREADS) k_batch_stats(const int32_t *__restrict__ src,
+                                                               const int32_t *__restrict__ dst,
+                                                               const int64_t *__restrict__ ts, int64_t n,
+                                                               int has_cut, long long cut, IngestScratch *o)
 {
     long long tmin = LLONG_MAX, tmax = LLONG_MIN;
     int maxid = 0, neg = 0;
     unsigned long long late = 0, uns = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a = src[i], b = dst[i];
-        const long long t = ts[i];
-        tmin = min(tmin, t);
-        tmax = max(tmax, t);
-        maxid = max(maxid, max(a, b));
-        neg |= (a < 0) | (b < 0) | ((t == LLONG_MIN) ? 2 : 0) | ((t == LLONG_MAX) ? 4 : 0);
-        late += (has_cut && t < cut) ? 1ull : 0ull;
-        if (i > 0 && ts[i - 1] > t) uns++;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * STATS_UNROLL) {
+        int32_t a[STATS_UNROLL], b[STATS_UNROLL];
+        long long t[STATS_UNROLL], tp[STATS_UNROLL];
+#pragma unroll
+        for (int r = 0; r < STATS_UNROLL; r++) {
+            const int64_t i = i0 + r * stride;
+            const bool ok = i < n;
+            a[r] = ok ? __ldg(src + i) : 0;
+            b[r] = ok ? __ldg(dst + i) : 0;
+            t[r] = ok ? __ldg(ts + i) : 0;
+            tp[r] = (ok && i > 0) ? __ldg(ts + i - 1) : LLONG_MIN;
+        }
+#pragma unroll
+        for (int r = 0; r < STATS_UNROLL; r++) {
+            if (i0 + r * stride >= n) continue;
+            tmin = min(tmin, t[r]);
+            tmax = max(tmax, t[r]);
+            maxid = max(maxid, max(a[r], b[r]));
+            neg |= (a[r] < 0) | (b[r] < 0) | ((t[r] == LLONG_MIN) ? 2 : 0) | ((t[r] == LLONG_MAX) ? 4 : 0);
+            late += (has_cut && t[r] < cut) ? 1ull : 0ull;
+            uns += tp[r] > t[r] ? 1ull : 0ull;
+        }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -59,7 +82,29 @@ __global__ void k_batch_stats(const int32_t *__restrict__ src, const int32_t *__
         late += __shfl_xor_sync(0xffffffffu, late, d);
         uns += __shfl_xor_sync(0xffffffffu, uns, d);
     }
+    constexpr int W = STATS_THREADS / 32;
+    __shared__ long long s_min[W], s_max[W];
+    __shared__ int s_id[W], s_neg[W];
+    __shared__ unsigned long long s_late[W], s_uns[W];
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+        s_min[w] = tmin;
+        s_max[w] = tmax;
+        s_id[w] = maxid;
+        s_neg[w] = neg;
+        s_late[w] = late;
+        s_uns[w] = uns;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < W; k++) {
+            tmin = min(tmin, s_min[k]);
+            tmax = max(tmax, s_max[k]);
+            maxid = max(maxid, s_id[k]);
+            neg |= s_neg[k];
+            late += s_late[k];
+            uns += s_uns[k];
+        }
         atomicMin(&o->ts_min, tmin);
         atomicMax(&o->ts_max, tmax);
         atomicMax(&o->max_id, maxid);
@@ -546,7 +591,9 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     stage.next("ingest: batch statistics");
     k_init_scratch<<<1, 1, 0, st>>>(ds);
     if (n > 0)
-        k_batch_stats<<<grid_for(h, n), 256, 0, st>>>(src, dst, ts, n, h->has_cutoff, h->cutoff, ds);
+        k_batch_stats<<<std::min<unsigned>(grid_for(h, (n + STATS_UNROLL - 1) / STATS_UNROLL, STATS_THREADS),
+                                           (unsigned)h->num_sms * 4),
+                        STATS_THREADS, 0, st>>>(src, dst, ts, n, h->has_cutoff, h->cutoff, ds);
     cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
     h->pending_launches += 2;
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "batch stats"))) return rc;
@@ -613,14 +660,44 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     const int64_t m_new = na + nbk;
     const bool append = na == 0 || nbk == 0 || hs->store_last_ts <= hs->kept_batch_min_ts;
 
-    // 4. store (from here on a failure is undone by the caller)
-    stage.next("ingest: store");
-    *changing = true;
+    // 4. the allocations of the steps below, made before anything changes:
+    // a call whose memory runs short fails here and leaves the state as it
+    // was, without a rebuild (only a node view pool that proves too small,
+    // and the Node2Vec pair table, allocate later)
+    stage.next("ingest: reserve");
     const int64_t N_old = h->N;
     const int old_buf = h->cur;
     const int64_t old_lo = h->s_lo;
     bool ts_full = !append || !h->tg.p || h->views_dirty;
     bool nv_full = !append || !h->nv_ready;
+    {
+        const int nxt = h->cur ^ 1;
+        if (append && h->s_hi + nbk > h->s_cap) {
+            const int64_t cap = std::max<int64_t>(std::max<int64_t>(h->s_cap, 2 * m_new + m_new / 2 + nbk + 1024),
+                                                  steady_store_cap(h, m_new, nbk));
+            if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
+            if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
+            if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap, true))) return rc;
+        } else if (!append) {
+            const int64_t cap =
+                std::max<int64_t>(std::max<int64_t>(h->s_cap, 2 * m_new + 1024), steady_store_cap(h, m_new, nbk));
+            if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
+            if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
+            if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap))) return rc;
+        }
+        if (ts_full) {
+            if ((rc = ensure(h, h->tg, sizeof(int32_t) * (size_t)(2 * m_new + 1024), true))) return rc;
+        } else if ((int64_t)(h->tg.bytes / sizeof(int32_t)) < h->tg_hi + nbk + 2) {
+            const int64_t live = h->tg_hi - h->tg_lo + 1;
+            const int64_t tcap = std::max<int64_t>(2 * (live + nbk) + 1024, steady_store_cap(h, m_new, nbk));
+            if ((rc = ensure(h, h->tg2, sizeof(int32_t) * (size_t)tcap, true))) return rc;
+        }
+        if (!nv_full && (rc = nv_prepare_append(h, i0, nbk, N_old, N_new))) return rc;
+    }
+
+    // 5. store (from here on a failure is undone by the caller)
+    stage.next("ingest: store");
+    *changing = true;
     int64_t new_lo = 0;  // first appended index
     if (append) {
         if (h->s_hi + nbk > h->s_cap) {
@@ -692,7 +769,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     h->has_cutoff = hs->has_cut;
     h->cutoff = hs->cut;
 
-    // 5. timestamp view
+    // 6. timestamp view
     stage.next("ingest: timestamp view");
     if (!ts_full && (int64_t)(h->tg.bytes / sizeof(int32_t)) < h->tg_hi + nbk + 2) {
         // move the live starts [tg_lo, tg_hi] to the front of a larger buffer
@@ -716,7 +793,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
         h->pending_launches += 5;
     }
 
-    // 6. node view
+    // 7. node view
     stage.next("ingest: node view");
     if (!nv_full) {
         bool rebuild = false;
@@ -728,7 +805,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     if (nv_full && (rc = nv_build(h))) return rc;
 
     stage.next("ingest: pair table");
-    // 7. Node2Vec pair table: the evicted edges out, the kept batch in (a
+    // 8. Node2Vec pair table: the evicted edges out, the kept batch in (a
     // rebuild after a merge, whose evicted edges are not a store range)
     if (h->pt_on) {
         rc = append ? pt_update(h, h->st_src[old_buf].as<int32_t>() + old_lo,

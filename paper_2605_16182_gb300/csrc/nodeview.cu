@@ -174,24 +174,66 @@ __global__ void k_nv_build_scatter(const Entry *__restrict__ E, const int32_t *_
 
 // ----------------------------------------------------------- batch append
 
-__global__ void k_nv_evict_count(Items it, int64_t items, int64_t N, int32_t *ev, int32_t *ev_nodes,
-                                 NvCounters *c)
+// Per-node counts of the evicted entries (ev[v] += entries of v; each node
+// that gets its first count is listed once in ev_nodes).  A Zipf stream puts
+// most entries on a few hubs, and per-warp atomics on one hub's counter
+// serialise at L2, so each block first sums its contiguous share of the
+// items in a shared-memory table (warp peers combined by __match_any_sync,
+// open addressing over EV_SLOTS keys, 16 probes) and adds each key's total
+// once; a key that finds no slot goes straight to the global counter.
+constexpr int EV_SLOTS = 2048;
+constexpr int EV_PROBES = 16;
+
+__device__ __forceinline__ void ev_add(int32_t v, int32_t cnt, int32_t *ev, int32_t *ev_nodes, NvCounters *c)
 {
+    const int32_t old = atomicAdd(&ev[v], cnt);
+    if (old == 0) ev_nodes[atomicAdd(&c->n_ev_nodes, 1ull)] = v;
+}
+
+__global__ void __launch_bounds__(256) k_nv_evict_count(Items it, int64_t items, int64_t N, int32_t *ev,
+                                                        int32_t *ev_nodes, NvCounters *c)
+{
+    __shared__ int32_t s_key[EV_SLOTS];
+    __shared__ int32_t s_cnt[EV_SLOTS];
+    for (int i = threadIdx.x; i < EV_SLOTS; i += blockDim.x) {
+        s_key[i] = -1;
+        s_cnt[i] = 0;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t v = (int32_t)it.key(i);
-        if (v < 0 || v >= N) {
-            atomicOr(&c->status, 1ull << 0);
-            v = -1;
+    const int64_t per = (items + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per;
+    const int64_t b1 = min(items, b0 + per);
+    for (int64_t base = b0; base < b1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int32_t v = -1;
+        if (i < b1) {
+            v = (int32_t)it.key(i);
+            if (v < 0 || v >= N) {
+                atomicOr(&c->status, 1ull << 0);
+                v = -1;
+            }
         }
-        const unsigned am = __activemask();
-        const unsigned peers = __match_any_sync(am, v);
+        const unsigned peers = __match_any_sync(0xffffffffu, v);
         if (v >= 0 && lane == __ffs(peers) - 1) {
-            const int32_t old = atomicAdd(&ev[v], __popc(peers));
-            if (old == 0) ev_nodes[atomicAdd(&c->n_ev_nodes, 1ull)] = v;
+            const int32_t cnt = __popc(peers);
+            const uint32_t h0 = ((uint32_t)v * 2654435761u) >> 21;  // 11 bits: EV_SLOTS
+            bool done = false;
+            for (int p = 0; p < EV_PROBES && !done; p++) {
+                const int slot = (int)((h0 + (uint32_t)p) & (EV_SLOTS - 1));
+                int32_t k = s_key[slot];
+                if (k == -1) k = atomicCAS(&s_key[slot], -1, v);
+                if (k == -1 || k == v) {
+                    atomicAdd(&s_cnt[slot], cnt);
+                    done = true;
+                }
+            }
+            if (!done) ev_add(v, cnt, ev, ev_nodes, c);
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < EV_SLOTS; i += blockDim.x)
+        if (s_key[i] >= 0) ev_add(s_key[i], s_cnt[i], ev, ev_nodes, c);
 }
 
 // Every node that lost entries drops them from the front of its region.
@@ -237,35 +279,33 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
 }
 
 // Batch-local node ids, so that the batch's node sort needs only as many
-// key bits as the batch has distinct nodes.  The first warp leader to see a
-// node claims an id with a compare-and-swap; a leader that loses the race
-// adopts the winner's id (its own candidate id stays unused: touched[] keeps
-// -1 there).  Ids are in arbitrary order; only grouping matters downstream.
-__global__ void k_nv_dense(Items it, int64_t nbe, int32_t *dense, int32_t *touched, uint32_t *keys, NvCounters *c)
+// key bits as the batch has distinct nodes.  The ids are exactly 0 ..
+// distinct - 1: a warp's peers elect one leader per node, and a leader that
+// finds the node unclaimed takes it with a compare-and-swap (0 -> -1) before
+// it draws the next id (drawing first, as every racing warp of a hub would,
+// spends ids that no node keeps, and a sparser id range costs sort passes).
+// touched[id] names the node of each id; the keys follow in k_nv_keys, once
+// every claim is done.
+__global__ void k_nv_claim(Items it, int64_t nbe, int32_t *dense, int32_t *touched, NvCounters *c)
 {
     const int lane = threadIdx.x & 31;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nbe; j += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = (int32_t)it.key(j);
         const unsigned am = __activemask();
         const unsigned peers = __match_any_sync(am, v);
-        const int leader = __ffs(peers) - 1;
-        int32_t id = 0;
-        if (lane == leader) {
-            id = dense[v];
-            if (id == 0) {
-                const int32_t cand = (int32_t)atomicAdd(&c->n_dense, 1ull) + 1;
-                const int32_t prev = atomicCAS(&dense[v], 0, cand);
-                if (prev == 0) {
-                    id = cand;
-                    touched[cand - 1] = v;
-                } else {
-                    id = prev;
-                }
-            }
+        if (lane == __ffs(peers) - 1 && *(volatile int32_t *)(dense + v) == 0 && atomicCAS(&dense[v], 0, -1) == 0) {
+            const int32_t id = (int32_t)atomicAdd(&c->n_dense, 1ull);
+            touched[id] = v;
+            dense[v] = id + 1;
         }
-        id = __shfl_sync(am, id, leader);
-        keys[j] = (uint32_t)(id - 1);
     }
+}
+
+// Sort key of every entry: its node's batch-local id.
+__global__ void k_nv_keys(Items it, int64_t nbe, const int32_t *__restrict__ dense, uint32_t *keys)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nbe; j += (int64_t)gridDim.x * blockDim.x)
+        keys[j] = (uint32_t)(__ldg(dense + (int32_t)it.key(j)) - 1);
 }
 
 __global__ void k_iota(uint32_t *v, int64_t n)
@@ -714,6 +754,27 @@ int nv_build(tempest_t *h)
     return TEMPEST_OK;
 }
 
+// Every buffer nv_append will need for a batch of nbk kept edges after
+// evicting n_ev edges, allocated now (nv_append's own ensure calls then find
+// them in place), so that an ingest whose memory runs short fails before it
+// changes anything.  A pool that later proves too small still rebuilds.
+int nv_prepare_append(tempest_t *h, int64_t n_ev, int64_t nbk, int64_t N_old, int64_t N_new)
+{
+    const int64_t ne = h->directed ? n_ev : 2 * n_ev, nbe = h->directed ? nbk : 2 * nbk;
+    int rc;
+    if ((rc = nv_ensure_nodes(h, N_new))) return rc;
+    if ((rc = ensure(h, h->nvc, sizeof(NvCounters)))) return rc;
+    if (ne > 0 && (rc = ensure(h, h->ev_nodes, sizeof(int32_t) * (size_t)std::min(ne, N_old + 1), true))) return rc;
+    if (nbe > 0) {
+        const int64_t runs_max = std::min(nbe, N_new);
+        if ((rc = ensure_runs(h, nbe, runs_max))) return rc;
+        if ((rc = ensure(h, h->reloc, sizeof(Reloc) * (size_t)(runs_max + 1), true))) return rc;
+        if ((rc = ensure(h, h->nv_tmp, sizeof(int32_t) * (size_t)(runs_max + 1), true))) return rc;
+        if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
+    }
+    return TEMPEST_OK;
+}
+
 // Appends the store items of the edges [new_lo, new_lo + nbk) of the current
 // buffer after evicting the n_ev oldest edges, whose endpoints are ev_src /
 // ev_dst.  Returns TEMPEST_OK with *rebuild set when a pool ran out (the
@@ -744,8 +805,10 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         for (cudaEvent_t &e : h->eev)
             if (!e) cudaEventCreate(&e);
         cudaEventRecord(h->eev[0], st);
-        k_nv_evict_count<<<grid_for(h, ne), 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
-                                                          h->ev_nodes.as<int32_t>(), dc);
+        // contiguous shares of at least 8192 items per block, at most 2 blocks per SM
+        const int64_t eg = std::max<int64_t>(1, std::min<int64_t>((ne + 8191) / 8192, 2 * (int64_t)h->num_sms));
+        k_nv_evict_count<<<(unsigned)eg, 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
+                                                       h->ev_nodes.as<int32_t>(), dc);
         k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
             h->ev_nodes.as<int32_t>(), h->ev.as<int32_t>(), h->nrec.as<int4>(), h->ngr.as<NodeRange>(),
             h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->nev.as<int32_t>(), dc);
@@ -764,8 +827,8 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
         cudaMemsetAsync(h->touched.p, 0xff, sizeof(int32_t) * (size_t)nbe, st);
         uint32_t *dkeys = reinterpret_cast<uint32_t *>(h->run_of.as<int32_t>());
-        k_nv_dense<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), h->touched.as<int32_t>(),
-                                                     dkeys, dc);
+        k_nv_claim<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), h->touched.as<int32_t>(), dc);
+        k_nv_keys<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), dkeys);
         NvCounters *hd = static_cast<NvCounters *>(h->hstat);
         cudaMemcpyAsync(hd, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
         if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view ids"))) return rc;
@@ -805,7 +868,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
             dc);
         NvCounters *hc = static_cast<NvCounters *>(h->hstat);
         cudaMemcpyAsync(hc, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
-        h->pending_launches += launches + 5;
+        h->pending_launches += launches + 6;
         if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view reserve"))) return rc;
         if (hc->overflow) {
             *rebuild = true;

@@ -93,14 +93,17 @@ def ingest(eng, b):
     return eng.ingest(s, d, t)
 
 
-def alloc_counts(spec, batches, directed, backward):
-    """Allocations each batch's ingest makes on a clean run."""
+def alloc_counts(spec, batches, directed, backward, rebuilt=None):
+    """Allocations each batch's ingest makes on a clean run (and, into the
+    list rebuilt, whether it rebuilt the node view whole)."""
     eng, fa = engine(spec.window, directed, backward)
     counts = []
     for b in batches:
         c0 = fa.count
-        ingest(eng, b)
+        st = ingest(eng, b)
         counts.append(fa.count - c0)
+        if rebuilt is not None:
+            rebuilt.append(st["view_rebuilt"])
     eng.close()
     return counts
 
@@ -185,14 +188,16 @@ def test_memory_that_stays_short_is_repaired_later(directed):
 
 
 def test_hbm_budget_below_the_next_batch():
-    """A budget set just above what the handle holds, before a batch that
-    needs more: that ingest returns ENOMEM (the budget's message) with the
-    state unchanged; with the budget lifted (same allocator) the same batch
-    goes in and the stream ends in the oracle's state."""
+    """A budget set just above what the handle holds, before an appending
+    batch that needs more: that ingest returns ENOMEM (the budget's message)
+    before it changes anything, so the state of before the batch reads out
+    under the same budget; with the budget lifted (same allocator) the same
+    batch goes in and the stream ends in the oracle's state."""
     spec, batches = stream_batches()
     _, states = oracle_states(spec, batches, True)
-    counts = alloc_counts(spec, batches, True, False)
-    k = next(i for i, c in enumerate(counts) if i >= 2 and c > 0)
+    rebuilt = []
+    counts = alloc_counts(spec, batches, True, False, rebuilt)
+    k = next(i for i, c in enumerate(counts) if i >= 2 and c > 0 and not rebuilt[i])
     eng, fa = engine(spec.window, True)
     for b in batches[:k]:
         ingest(eng, b)
