@@ -201,6 +201,9 @@ def test_hbm_budget_below_the_next_batch():
     eng, fa = engine(spec.window, True)
     for b in batches[:k]:
         ingest(eng, b)
+    # one read-out first: it sizes the export's staging buffer, which a
+    # read-out of the same state under the budget then finds in place
+    assert_state_equal(eng.state(), states[k], "before the budget")
     held = sum(fa.live.values())
     _lib.tempest_set_allocator(eng.h, fa.fns[0], fa.fns[1], None, held + 256)
     with pytest.raises(_lib.TempestError) as ei:
