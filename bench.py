@@ -95,17 +95,24 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(hops, kernel):
-    """DRAM bytes of the walk kernel from the committed ncu summary, scaled to
-    this launch by hops; None when the summary is of another kernel or the
-    kernel changed since the capture."""
+def recorded_capture(kernel):
+    """The committed ncu summary of the walk kernel, or None when it is of
+    another kernel or the kernel changed since the capture."""
     p = os.path.join(ROOT, "profiles", "walk_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("kernel_source_hash") != kernel_source_hash() or not d.get("kernel", "").startswith(kernel + "<"):
         return None
-    return d["dram_bytes_per_hop"] * hops
+    return d
+
+
+def recorded_traffic(hops, kernel):
+    """DRAM bytes of the walk kernel from the committed ncu summary, scaled to
+    this launch by hops; None when the summary is of another kernel or the
+    kernel changed since the capture."""
+    d = recorded_capture(kernel)
+    return None if d is None else d["dram_bytes_per_hop"] * hops
 
 
 class ClockSampler:
@@ -807,7 +814,14 @@ def main():
         sched_early = {0: "full", 1: "coop", 2: "stream", 3: "graph", 4: "lane"}[res["tune"]["sched"]]
     kname = {"stream": "k_walks_stream", "full": "k_walks_full", "coop": "coop tiers", "graph": "k_graph_hop",
              "lane": "k_walks_lane"}[sched_early]
-    traffic = recorded_traffic(res["hops"] / max(1, len(res["walk_ms"])), kname)
+    hops_per_call = res["hops"] / max(1, len(res["walk_ms"]))
+    traffic = recorded_traffic(hops_per_call, kname)
+    cap = recorded_capture(kname)
+    # each walk writes its row whole: len cells (the start edge's two nodes
+    # and one per later hop, so sum(len) = hops + walks) and padding to max_len
+    cells = 12 * (hops_per_call + res["n_walks"])
+    padding = 12 * res["n_walks"] * args.max_len - cells
+    walk_kernel_call_s = sum(res["walk_kernel_ms"]) / 1e3 / max(1, len(res["walk_ms"]))
     cpu = None
     if not args.no_cpu:
         o = oracle_sample(seconds_budget=args.cpu_seconds, threads=host_cpus())
@@ -870,6 +884,11 @@ def main():
         "live_edges": res["live"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "row_write_bytes": {"cells": cells, "padding": padding,
+                                         "note": "12 B per cell (int32 node, int64 ts), rows of max_len cells"},
+                     "dram_read_bytes_per_hop": (cap["dram_bytes_read"] / cap["hops"]) if cap else None,
+                     "frac_on_traffic": (traffic / walk_kernel_call_s / 1e9 / peak
+                                         if traffic and walk_kernel_call_s > 0 else None),
                      "kernel": kname,
                      "peak_kind": peak_kind + " hbm copy (burst)",
                      "model_bytes_per_launch": per_launch_bytes},
@@ -897,7 +916,8 @@ def main():
         t = res["tune"]
         out["autotune"] = {k: t[k] for k in ("sched", "bkt_log", "coop_w_warp", "coop_mega", "stream_ctas",
                                              "pad_pass", "best_ms", "start_ms")}
-        out["autotune"]["trials"] = len(t["trials"])
+        out["autotune"]["trials"] = [{k: tr[k] for k in ("sched", "bkt_log", "stream_ctas", "pad_pass", "ms")}
+                                     for tr in t["trials"]]
     print(json.dumps(out), flush=True)
 
 

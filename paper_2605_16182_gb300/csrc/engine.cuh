@@ -170,6 +170,7 @@ struct tempest {
     bool w_valid = false;  // every live group's weight is current
     int64_t w_ver = -1;    // state version of the suffix sums
     tw::DBuf touched;  // int32: node of each batch-local id
+    tw::DBuf ent_tmp;  // Entry: a batch's node view entries in (node, ts, arrival) order
     int64_t S = 0;     // nodes that own regions (for the bucket index)
     int64_t state_ver = 0;  // bumped by every ingest
     // an ingest that failed after changing the store restored the store's

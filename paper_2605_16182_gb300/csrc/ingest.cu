@@ -189,10 +189,21 @@ __device__ __forceinline__ int64_t lower_bound_i64(const int64_t *a, int64_t n, 
 
 // One thread: new cut-off and the first kept element of store / batch.
 // mode: 0 none, 1 duration (param = Delta), 2 count (param = W).
+// With `fused` the kernel runs right after k_batch_stats on the batch as it
+// came: when the statistics found it sorted, its late edges are the first
+// o->late ones and the window is computed on the rest (one host round trip
+// for both steps); an unsorted batch is left to a second launch on the
+// sorted batch.
 __global__ void k_window(int mode, long long param, const int64_t *old_ts, int64_t m_old,
-                         const int64_t *bts, int64_t nb, int has_old, long long cut_old, IngestScratch *o)
+                         const int64_t *bts, int64_t nb, int has_old, long long cut_old, int fused, IngestScratch *o)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (fused) {
+        if (o->unsorted) return;
+        const int64_t late = (int64_t)o->late;
+        bts += late;
+        nb -= late;
+    }
     int has = has_old;
     long long cut = cut_old;
     if (mode == 1 && m_old + nb > 0) {
@@ -379,13 +390,15 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 //   8 E + 16 U           batch-local ids (ids read, keys written, id table)
 //   20 P E               node sort passes (key read for the histogram, key
 //                        and value read and written by the scatter)
-//   24 E + 148 R         runs (keys, values and timestamps read, run index
-//                        written; per run its arrays, node record and the
-//                        region reservation)
+//   36 E                 entries packed in sorted order (index read, the
+//                        store item's far end and time gathered, 16-byte
+//                        entry written)
+//   32 E + 148 R         runs (keys and timestamps read by both scan
+//                        passes, run index written; per run its arrays,
+//                        node record and the region reservation)
 //   32 E_moved + 24 G_moved   region moves (entries, group starts and times)
-//   44 E + 12 G_added    scatter (index, run and group ids read, the store
-//                        item gathered, the 16-byte entry and new groups
-//                        written)
+//   40 E + 12 G_added    scatter (run and group ids and the packed entry
+//                        read, the entry and new groups written)
 // A full rebuild of the node view (after a merge or a pool exhaustion)
 // counts its whole sort and scatter over the live entries instead.
 static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, int64_t kept_old, int64_t m_new,
@@ -402,9 +415,10 @@ static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, 
         x += 4 * r.ev_entries + 104 * r.ev_nodes;
         x += 8 * r.entries + 16 * r.ids;
         x += 20 * r.passes * r.entries;
-        x += 24 * r.entries + 148 * r.runs;
+        x += 36 * r.entries;
+        x += 32 * r.entries + 148 * r.runs;
         x += 32 * r.moved_e + 24 * r.moved_g;
-        x += 44 * r.entries + 12 * r.g_added;
+        x += 40 * r.entries + 12 * r.g_added;
     }
     return x;
 }
@@ -594,8 +608,14 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
         k_batch_stats<<<std::min<unsigned>(grid_for(h, (n + STATS_UNROLL - 1) / STATS_UNROLL, STATS_THREADS),
                                            (unsigned)h->num_sms * 4),
                         STATS_THREADS, 0, st>>>(src, dst, ts, n, h->has_cutoff, h->cutoff, ds);
+    // the window of a batch that turns out sorted (the usual stream), in the
+    // same round trip
+    const int mode = h->window > 0 ? 1 : (h->window < 0 ? 2 : 0);
+    const long long param = h->window > 0 ? h->window : -h->window;
+    const int64_t *old_ts = h->m > 0 ? h->st_ts[h->cur].as<int64_t>() + h->s_lo : nullptr;
+    k_window<<<1, 32, 0, st>>>(mode, param, old_ts, h->m, ts, n, h->has_cutoff, h->cutoff, 1, ds);
     cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
-    h->pending_launches += 2;
+    h->pending_launches += 3;
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "batch stats"))) return rc;
     if (hs->neg_id & 1) return fail(h, TEMPEST_EINVAL, "tempest_ingest: negative node id");
     if (hs->neg_id & 2) return fail(h, TEMPEST_EINVAL, "tempest_ingest: timestamp INT64_MIN is reserved");
@@ -648,13 +668,12 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
 
     // 3. window cut-off
     stage.next("ingest: window cut-off");
-    const int mode = h->window > 0 ? 1 : (h->window < 0 ? 2 : 0);
-    const long long param = h->window > 0 ? h->window : -h->window;
-    const int64_t *old_ts = h->m > 0 ? h->st_ts[h->cur].as<int64_t>() + h->s_lo : nullptr;
-    k_window<<<1, 32, 0, st>>>(mode, param, old_ts, h->m, bt, nb, h->has_cutoff, h->cutoff, ds);
-    cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
-    h->pending_launches++;
-    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "window"))) return rc;
+    if (!sorted) {
+        k_window<<<1, 32, 0, st>>>(mode, param, old_ts, h->m, bt, nb, h->has_cutoff, h->cutoff, 0, ds);
+        cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
+        h->pending_launches++;
+        if ((rc = cuda_check(h, cudaStreamSynchronize(st), "window"))) return rc;
+    }
     const int64_t i0 = hs->i0, j0 = hs->j0;
     const int64_t na = h->m - i0, nbk = nb - j0;
     const int64_t m_new = na + nbk;

@@ -293,7 +293,8 @@ __global__ void k_nv_claim(Items it, int64_t nbe, int32_t *dense, int32_t *touch
         const int32_t v = (int32_t)it.key(j);
         const unsigned am = __activemask();
         const unsigned peers = __match_any_sync(am, v);
-        if (lane == __ffs(peers) - 1 && *(volatile int32_t *)(dense + v) == 0 && atomicCAS(&dense[v], 0, -1) == 0) {
+        // a stale 0 from the cached read only costs a compare-and-swap that fails
+        if (lane == __ffs(peers) - 1 && dense[v] == 0 && atomicCAS(&dense[v], 0, -1) == 0) {
             const int32_t id = (int32_t)atomicAdd(&c->n_dense, 1ull);
             touched[id] = v;
             dense[v] = id + 1;
@@ -330,24 +331,26 @@ struct DenseLoader {
 };
 
 // Node runs and new groups of the batch's entries in (node, ts, arrival)
-// order (kb: batch-local node ids, vb: batch items, groups as of after the
-// eviction).
+// order (kb: batch-local node ids, E: the entries packed in that order by
+// k_nv_entries, groups as of after the eviction).  Reading the packed
+// entries keeps every load coalesced (gathering each timestamp through the
+// sort's index cost four scattered loads per entry over the two passes).
 struct AppendRunOp {
-    const uint32_t *kb, *vb;
+    const uint32_t *kb;
+    const Entry *E;
     const int32_t *touched;
-    Items it;
     const NodeRange *ngr;
     int32_t *run_of, *fx, *run_node, *run_pos, *run_g;
     __device__ __forceinline__ uint64_t value(int64_t p) const
     {
-        const int64_t t = it.ts[it.edge(vb[p])];
+        const int64_t t = E[p].ts;
         const bool nc = p == 0 || kb[p] != kb[p - 1];
         bool gc;
         if (nc) {
             const NodeRange &g = ngr[touched[kb[p]]];
             gc = g.g_lo == g.g_hi || g.t_last != t;
         } else {
-            gc = it.ts[it.edge(vb[p - 1])] != t;
+            gc = E[p - 1].ts != t;
         }
         return ((uint64_t)nc << 32) | (uint64_t)gc;
     }
@@ -444,11 +447,16 @@ __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t
     }
 }
 
+// Chunks of each move, over a bound on the moves (the count is read on the
+// device, so the host needs no round trip between the reservation and the
+// moves).
 struct RelocChunkOp {
     const Reloc *reloc;
     int32_t *cbase;
+    const NvCounters *c;
     __device__ __forceinline__ uint64_t value(int64_t t) const
     {
+        if (t >= (int64_t)c->n_reloc || c->overflow) return 0;
         const Reloc x = reloc[t];
         return (uint64_t)((max(x.n_e, x.n_g) + RELOC_CHUNK - 1) / RELOC_CHUNK);
     }
@@ -457,10 +465,12 @@ struct RelocChunkOp {
 
 // One warp per chunk of a move: entries copied, group timestamps copied,
 // group starts rebased to the new entry region.
-__global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__restrict__ cbase, int64_t n_reloc,
+__global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__restrict__ cbase, const NvCounters *c,
                            const uint64_t *__restrict__ tot, Entry *ent, int32_t *ngo, int64_t *ngts, double *gw)
 {
+    if (c->overflow) return;  // the batch rebuilds the view instead
     const int lane = threadIdx.x & 31;
+    const int64_t n_reloc = (int64_t)c->n_reloc;
     const int64_t nch = (int64_t)*tot;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += warps) {
@@ -483,13 +493,14 @@ __global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__res
     }
 }
 
-__global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t slot_base, int64_t nbe,
+__global__ void k_nv_scatter(const Entry *__restrict__ E, int64_t nbe,
                              const int32_t *__restrict__ run_of, const int32_t *__restrict__ fx,
                              const int32_t *__restrict__ run_pos, const int32_t *__restrict__ run_g,
                              const int32_t *__restrict__ run_de, const int32_t *__restrict__ run_dg,
                              const int32_t *__restrict__ run_node, int64_t e_cap, int64_t g_cap, Entry *ent,
                              int32_t *ngo, int64_t *ngts, NodeRange *ngr, NvCounters *c)
 {
+    if (c->overflow) return;  // a pool could not serve a region: the batch rebuilds the view instead
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nbe; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = run_of[p];
         const int32_t de = run_de[r];
@@ -499,7 +510,7 @@ __global__ void k_nv_scatter(const uint32_t *__restrict__ vb, Items it, uint32_t
             atomicOr(&c->status, 1ull << 3);
             continue;
         }
-        const Entry x = it.entry(vb[p], slot_base);
+        const Entry x = E[p];
         ent[e] = x;
         // the node record's first / last group timestamps
         if (p == run_pos[r]) {
@@ -771,6 +782,7 @@ int nv_prepare_append(tempest_t *h, int64_t n_ev, int64_t nbk, int64_t N_old, in
         if ((rc = ensure(h, h->reloc, sizeof(Reloc) * (size_t)(runs_max + 1), true))) return rc;
         if ((rc = ensure(h, h->nv_tmp, sizeof(int32_t) * (size_t)(runs_max + 1), true))) return rc;
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
+        if ((rc = ensure(h, h->ent_tmp, sizeof(Entry) * (size_t)nbe, true))) return rc;
     }
     return TEMPEST_OK;
 }
@@ -805,8 +817,8 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         for (cudaEvent_t &e : h->eev)
             if (!e) cudaEventCreate(&e);
         cudaEventRecord(h->eev[0], st);
-        // contiguous shares of at least 8192 items per block, at most 2 blocks per SM
-        const int64_t eg = std::max<int64_t>(1, std::min<int64_t>((ne + 8191) / 8192, 2 * (int64_t)h->num_sms));
+        // contiguous shares of at least 2048 items per block, at most 4 blocks per SM
+        const int64_t eg = std::max<int64_t>(1, std::min<int64_t>((ne + 2047) / 2048, 4 * (int64_t)h->num_sms));
         k_nv_evict_count<<<(unsigned)eg, 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
                                                        h->ev_nodes.as<int32_t>(), dc);
         k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
@@ -825,6 +837,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         // batch-local node ids (keys in run_of, which the run scan rewrites later)
         stage.next("node view: batch ids and sort");
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
+        if ((rc = ensure(h, h->ent_tmp, sizeof(Entry) * (size_t)nbe, true))) return rc;
         cudaMemsetAsync(h->touched.p, 0xff, sizeof(int32_t) * (size_t)nbe, st);
         uint32_t *dkeys = reinterpret_cast<uint32_t *>(h->run_of.as<int32_t>());
         k_nv_claim<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), h->touched.as<int32_t>(), dc);
@@ -852,8 +865,11 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         }
         stage.next("node view: runs and regions");
         uint64_t *part = h->partials.as<uint64_t>();
-        AppendRunOp op{kb[r], vb[r], h->touched.as<int32_t>(), it, h->ngr.as<NodeRange>(),
-                       h->run_of.as<int32_t>(),
+        // the entries in sorted order, packed once (the runs and the scatter
+        // read them coalesced)
+        Entry *E = h->ent_tmp.as<Entry>();
+        k_nv_entries<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], it, nbe, slot_base(h, new_lo), E);
+        AppendRunOp op{kb[r], E, h->touched.as<int32_t>(), h->ngr.as<NodeRange>(), h->run_of.as<int32_t>(),
                        h->fx.as<int32_t>(), h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
                        h->run_g.as<int32_t>()};
         const int nb = scan_launch(op, nbe, part, st);
@@ -866,30 +882,25 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
             h->g_cap, h->nrec.as<int4>(), h->ngr.as<NodeRange>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
             h->act.as<int32_t>(), h->nrec_n, h->reloc.as<Reloc>(), h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(),
             dc);
-        NvCounters *hc = static_cast<NvCounters *>(h->hstat);
-        cudaMemcpyAsync(hc, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
-        h->pending_launches += launches + 6;
-        if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view reserve"))) return rc;
-        if (hc->overflow) {
-            *rebuild = true;
-            return TEMPEST_OK;
-        }
-        const int64_t n_reloc = (int64_t)hc->n_reloc;
+        h->pending_launches += launches + 7;
+        // moves and scatter are queued without a round trip: they read the
+        // move count on the device and do nothing when a pool overflowed
+        // (the host sees that at the end and rebuilds the view)
         stage.next("node view: region moves and scatter");
-        if (n_reloc > 0) {
-            RelocChunkOp rop{h->reloc.as<Reloc>(), h->nv_tmp.as<int32_t>()};
-            const int nb2 = scan_launch(rop, n_reloc, part, st);
-            const int64_t nch_max = (2 * h->e_cap) / RELOC_CHUNK + n_reloc;  // bound for the grid only
+        {
+            RelocChunkOp rop{h->reloc.as<Reloc>(), h->nv_tmp.as<int32_t>(), dc};
+            const int nb2 = scan_launch(rop, n_ids, part, st);  // at most one move per node run
+            const int64_t nch_max = (2 * h->e_cap) / RELOC_CHUNK + n_ids;  // bound for the grid only
             int64_t grid = (nch_max + 7) / 8;
             const int64_t gcap = (int64_t)h->num_sms * 16;
             if (grid > gcap) grid = gcap;
-            k_nv_reloc<<<(unsigned)grid, 256, 0, st>>>(h->reloc.as<Reloc>(), h->nv_tmp.as<int32_t>(), n_reloc,
+            k_nv_reloc<<<(unsigned)grid, 256, 0, st>>>(h->reloc.as<Reloc>(), h->nv_tmp.as<int32_t>(), dc,
                                                        part + nb2, h->ent.as<Entry>(), h->ngo.as<int32_t>(),
                                                        h->ngts.as<int64_t>(),
                                                        h->w_on && h->w_valid && h->gw.p ? h->gw.as<double>() : nullptr);
             h->pending_launches += 4;
         }
-        k_nv_scatter<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], it, slot_base(h, new_lo), nbe, h->run_of.as<int32_t>(),
+        k_nv_scatter<<<grid_for(h, nbe), 256, 0, st>>>(E, nbe, h->run_of.as<int32_t>(),
                                                        h->fx.as<int32_t>(), h->run_pos.as<int32_t>(),
                                                        h->run_g.as<int32_t>(), h->run_de.as<int32_t>(),
                                                        h->run_dg.as<int32_t>(), h->run_node.as<int32_t>(), h->e_cap,
@@ -904,6 +915,10 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
     if (hc->status)
         return fail(h, TEMPEST_ECUDA, "node view: consistency check failed (code 0x%llx)",
                     (unsigned long long)hc->status);
+    if (hc->overflow) {
+        *rebuild = true;  // nothing was moved or scattered; the caller rebuilds the whole view
+        return TEMPEST_OK;
+    }
     h->Gn += (int64_t)hc->gn_delta;
     rep.ev_nodes = (int64_t)hc->n_ev_nodes;
     rep.moved_e = (int64_t)hc->moved_e;

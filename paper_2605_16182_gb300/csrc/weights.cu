@@ -96,6 +96,7 @@ __global__ void k_w_append(int64_t nbe, const int32_t *__restrict__ run_of, cons
                            const NodeRange *__restrict__ ngr, const int32_t *__restrict__ ngo,
                            const int64_t *__restrict__ ngts, double lam, int64_t *wref, double *gw, NvCounters *cnt)
 {
+    if (cnt->overflow) return;  // the batch rebuilds the view (and the weights) instead
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nbe; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = run_of[p];
         const bool opens = fx[p + 1] != fx[p];
