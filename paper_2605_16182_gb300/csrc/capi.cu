@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <thread>
 #include <vector>
@@ -490,26 +491,32 @@ static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, 
         if (nt <= 1) {
             expand_rows(0, nh, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
         } else {
-            // ranges k >= 1 go to new threads and range 0 to this one; a
-            // range whose thread cannot start (no exception crosses the C
-            // ABI) is written here too
-            bool started[256] = {};  // nt <= 256 (the knob's range; automatic <= 32)
+            // the threads (this one included) take chunks of rows from a
+            // shared counter until none is left: a thread that the host
+            // deschedules (its CPUs are shared) delays one chunk, not a
+            // fixed share of the rows; a thread that cannot start (no
+            // exception crosses the C ABI) leaves its chunks to the others
+            constexpr int64_t CHUNK = 2048;
+            std::atomic<int64_t> next{0};
+            auto work = [&]() {
+                for (;;) {
+                    const int64_t i0 = next.fetch_add(CHUNK, std::memory_order_relaxed);
+                    if (i0 >= nh) break;
+                    expand_rows(i0, std::min(nh, i0 + CHUNK), cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
+                }
+            };
             std::vector<std::thread> th;
             try {
                 th.reserve((size_t)nt);
             } catch (...) {
             }
             for (int64_t k = 1; k < nt; k++) {
-                const int64_t i0 = nh * k / nt, i1 = nh * (k + 1) / nt;
                 try {
-                    th.emplace_back(expand_rows, i0, i1, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
-                    started[k] = true;
+                    th.emplace_back(work);
                 } catch (...) {
                 }
             }
-            expand_rows(0, nh / nt, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
-            for (int64_t k = 1; k < nt; k++)
-                if (!started[k]) expand_rows(nh * k / nt, nh * (k + 1) / nt, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
+            work();
             for (auto &x : th) x.join();
         }
     }
