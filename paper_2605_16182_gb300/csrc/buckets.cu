@@ -150,13 +150,18 @@ struct BigNodeOp {
     }
 };
 
+// Tasks of each big node, over a bound on the big nodes (their count is the
+// high half of the big-node scan's total, read on the device: no host round
+// trip between the two scans).
 struct ChunkOp {
     const int32_t *big_node;
     const NodeRange *ngr;
     const int4 *aux0, *aux1;
     int32_t *big_c;
+    const uint64_t *big_tot;
     __device__ __forceinline__ uint64_t value(int64_t b) const
     {
+        if (b >= (int64_t)(*big_tot >> 32)) return 0;
         const int4 a0 = aux0[b], a1 = aux1[b];
         const int32_t g_hi = ngr[big_node[b]].g_hi;
         return (uint64_t)a1.z + (uint64_t)((g_hi - a0.y + BKT_CHUNK - 1) / BKT_CHUNK);
@@ -166,11 +171,14 @@ struct ChunkOp {
 
 // The big node owning each fill chunk (one warp per big node writes its
 // chunk range): the fill then finds a chunk's node with one load.
-__global__ void __launch_bounds__(256) k_bkt_owner(const int32_t *__restrict__ big_c, int64_t nb,
-                                                   const uint64_t *__restrict__ tot, int64_t cap_ch,
+__global__ void __launch_bounds__(256) k_bkt_owner(const int32_t *__restrict__ big_c, const uint64_t *big_tot,
+                                                   int64_t cap_tab, const uint64_t *__restrict__ tot, int64_t cap_ch,
                                                    int32_t *owner, WalkCounters *chk)
 {
     const int lane = threadIdx.x & 31;
+    const int64_t nb = (int64_t)(*big_tot >> 32);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)(uint32_t)*big_tot > cap_tab)
+        atomicOr(&chk->status, 1ull << 14);  // tables above their allocated bound (the fill skips them)
     const int64_t nch = (int64_t)*tot;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += warps) {
@@ -392,41 +400,39 @@ int prepare_walk_index(tempest_t *h)
         BigNodeOp op{h->act.as<int32_t>(), ngr, bc, gen, h->big_node.as<int32_t>(), h->big_t.as<int32_t>(),
                      h->big_aux0.as<int4>(), h->big_aux1.as<int4>(), h->big_bf.as<int64_t>()};
         const int nblk = scan_launch(op, S, part, st);
-        uint64_t *hp = static_cast<uint64_t *>(h->hstat);
-        cudaMemcpyAsync(hp, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-        if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket lists"))) return rc;
-        const uint64_t tot = hp[0];
-        const int64_t nb = (int64_t)(tot >> 32), cap = (int64_t)(uint32_t)tot;
-        if (cap > bound) return fail(h, TEMPEST_ECUDA, "walk index: bucket tables (%lld) above their bound (%lld)",
-                                     (long long)cap, (long long)bound);
-        if (nb > 0) {
-            ChunkOp cop{h->big_node.as<int32_t>(), ngr, h->big_aux0.as<int4>(), h->big_aux1.as<int4>(),
-                        h->big_c.as<int32_t>()};
-            const int nblk2 = scan_launch(cop, nb, part, st);
-            // the fill's consistency flag goes to the walk counters, which
-            // every walk call zeroes before its kernels: read it here
-            cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);
-            // tasks <= copy tasks + group chunks <= cap / BKT_COPY + Gn / BKT_CHUNK + 2 nb
-            const int64_t nch_max = cap / BKT_COPY + Gn / BKT_CHUNK + 2 * nb + 1;
-            if ((rc = ensure(h, h->big_own, sizeof(int32_t) * (size_t)nch_max, true))) return rc;
-            const int64_t gcap = (int64_t)h->num_sms * 16;
-            int64_t ogrid = (nb + 7) / 8;
-            if (ogrid > gcap) ogrid = gcap;
-            k_bkt_owner<<<(unsigned)ogrid, 256, 0, st>>>(h->big_c.as<int32_t>(), nb, part + nblk2, nch_max,
-                                                         h->big_own.as<int32_t>(), h->wcnt.as<WalkCounters>());
-            int64_t grid = (nch_max + 7) / 8;
-            if (grid > gcap) grid = gcap;
-            k_bkt_fill<<<(unsigned)grid, 256, 0, st>>>(
-                h->big_node.as<int32_t>(), h->big_t.as<int32_t>(), h->big_c.as<int32_t>(), h->big_own.as<int32_t>(),
-                h->big_aux0.as<int4>(), h->big_aux1.as<int4>(), h->big_bf.as<int64_t>(), part + nblk2, ngr,
-                h->ngts.as<int64_t>(), bc.prev, gen, cap, h->bkt.as<int32_t>(), h->wcnt.as<WalkCounters>());
-            WalkCounters *hc = static_cast<WalkCounters *>(h->hstat);
-            cudaMemcpyAsync(hc, h->wcnt.p, sizeof(WalkCounters), cudaMemcpyDeviceToHost, st);
-            if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket fill"))) return rc;
-            if (hc->status)
-                return fail(h, TEMPEST_ECUDA, "walk index: bucket table check failed (code 0x%llx)",
-                            (unsigned long long)hc->status);
-        }
+        // the big-node count and table size stay on the device (kept apart:
+        // the next scan reuses the partials); sizes below use host bounds
+        uint64_t *big_tot = part + SCAN_MAX_BLOCKS + 1;
+        cudaMemcpyAsync(big_tot, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+        ChunkOp cop{h->big_node.as<int32_t>(), ngr, h->big_aux0.as<int4>(), h->big_aux1.as<int4>(),
+                    h->big_c.as<int32_t>(), big_tot};
+        const int nblk2 = scan_launch(cop, S, part, st);
+        // the fill's consistency flag goes to the walk counters, which
+        // every walk call zeroes before its kernels: read it here
+        cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);
+        // tasks <= copy tasks + group chunks <= bound / BKT_COPY + Gn / BKT_CHUNK + 2 S
+        const int64_t nch_max = bound / BKT_COPY + Gn / BKT_CHUNK + 2 * S + 1;
+        if ((rc = ensure(h, h->big_own, sizeof(int32_t) * (size_t)nch_max, true))) return rc;
+        const int64_t gcap = (int64_t)h->num_sms * 16;
+        int64_t ogrid = (S + 7) / 8;
+        if (ogrid > gcap) ogrid = gcap;
+        k_bkt_owner<<<(unsigned)ogrid, 256, 0, st>>>(h->big_c.as<int32_t>(), big_tot, bound, part + nblk2, nch_max,
+                                                     h->big_own.as<int32_t>(), h->wcnt.as<WalkCounters>());
+        int64_t grid = (nch_max + 7) / 8;
+        if (grid > gcap) grid = gcap;
+        k_bkt_fill<<<(unsigned)grid, 256, 0, st>>>(
+            h->big_node.as<int32_t>(), h->big_t.as<int32_t>(), h->big_c.as<int32_t>(), h->big_own.as<int32_t>(),
+            h->big_aux0.as<int4>(), h->big_aux1.as<int4>(), h->big_bf.as<int64_t>(), part + nblk2, ngr,
+            h->ngts.as<int64_t>(), bc.prev, gen, bound, h->bkt.as<int32_t>(), h->wcnt.as<WalkCounters>());
+        WalkCounters *hc = static_cast<WalkCounters *>(h->hstat);
+        uint64_t *hb = reinterpret_cast<uint64_t *>(static_cast<char *>(h->hstat) + 2048);
+        cudaMemcpyAsync(hc, h->wcnt.p, sizeof(WalkCounters), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(hb, big_tot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+        if ((rc = cuda_check(h, cudaStreamSynchronize(st), "bucket fill"))) return rc;
+        if (hc->status)
+            return fail(h, TEMPEST_ECUDA, "walk index: bucket table check failed (code 0x%llx)",
+                        (unsigned long long)hc->status);
+        const int64_t nb = (int64_t)(hb[0] >> 32);
         h->n_big = nb;
         h->bkt_prev_ok = true;  // these tables are the next build's source
     }

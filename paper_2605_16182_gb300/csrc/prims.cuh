@@ -472,7 +472,7 @@ static __global__ void __launch_bounds__(1024) k_hscan_part(uint32_t *part, int 
 }
 
 template <typename K, class L>
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(L ld, K *kout, uint32_t *vout,
+__global__ void __launch_bounds__(SORT_THREADS, sizeof(K) == 4 ? 5 : 3) k_radix_scatter(L ld, K *kout, uint32_t *vout,
                                                                 int64_t n, int64_t per_blk, int shift,
                                                                 const uint32_t *offs, const uint32_t *part,
                                                                 int nblk)
