@@ -311,7 +311,10 @@ int views_repair(tempest_t *h);
 int nv_ensure_nodes(tempest_t *h, int64_t N);
 int nv_build(tempest_t *h);
 int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_t n_ev, int64_t new_lo, int64_t nbk,
-              int64_t N_old, bool *rebuild);
+              int64_t N_old);
+// the append's bookkeeping once its counters (h->nvc) were read back into hc;
+// *rebuild when a pool could not serve a region (nothing was applied)
+int nv_append_finish(tempest_t *h, const NvCounters *hc, bool *rebuild);
 // allocates what nv_append will need for the batch, before anything changes
 int nv_prepare_append(tempest_t *h, int64_t n_ev, int64_t nbk, int64_t N_old, int64_t N_new);
 // canonical NODE_OFF / NODE_ORDER / NODE_GROUP_OFF / NODE_GIDX into device memory

@@ -814,14 +814,15 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
 
     // 7. node view
     stage.next("ingest: node view");
+    bool nv_pending = false;
     if (!nv_full) {
-        bool rebuild = false;
         rc = nv_append(h, h->st_src[old_buf].as<int32_t>() + old_lo, h->st_dst[old_buf].as<int32_t>() + old_lo, i0,
-                       new_lo, nbk, N_old, &rebuild);
+                       new_lo, nbk, N_old);
         if (rc) return rc;
-        nv_full = rebuild;
+        nv_pending = true;  // finished after the round trip below
+    } else if ((rc = nv_build(h))) {
+        return rc;
     }
-    if (nv_full && (rc = nv_build(h))) return rc;
 
     stage.next("ingest: pair table");
     // 8. Node2Vec pair table: the evicted edges out, the kept batch in (a
@@ -834,10 +835,21 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     }
 
     cudaMemcpyAsync(hs, ds, sizeof(IngestScratch), cudaMemcpyDeviceToHost, st);
+    // the node view's counters in the same round trip (their own pinned slot)
+    NvCounters *hn = reinterpret_cast<NvCounters *>(static_cast<char *>(h->hstat) + 1024);
+    if (nv_pending) cudaMemcpyAsync(hn, h->nvc.p, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
     if ((rc = cuda_check(h, cudaStreamSynchronize(st), "ingest"))) return rc;
     if (hs->status)
         return fail(h, TEMPEST_ECUDA, "ingest: index consistency check failed (code 0x%llx)",
                     (unsigned long long)hs->status);
+    if (nv_pending) {
+        bool rebuild = false;
+        if ((rc = nv_append_finish(h, hn, &rebuild))) return rc;
+        if (rebuild) {
+            nv_full = true;
+            if ((rc = nv_build(h))) return rc;
+        }
+    }
     const int64_t tg_added_now = (int64_t)hs->tg_added;
     if (ts_full) {
         h->tg_lo = 0;

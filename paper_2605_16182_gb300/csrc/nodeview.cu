@@ -787,19 +787,19 @@ int nv_prepare_append(tempest_t *h, int64_t n_ev, int64_t nbk, int64_t N_old, in
     return TEMPEST_OK;
 }
 
-// Appends the store items of the edges [new_lo, new_lo + nbk) of the current
-// buffer after evicting the n_ev oldest edges, whose endpoints are ev_src /
-// ev_dst.  Returns TEMPEST_OK with *rebuild set when a pool ran out (the
-// caller then rebuilds the whole view).
+// Queues the append of the store items of the edges [new_lo, new_lo + nbk)
+// of the current buffer after evicting the n_ev oldest edges, whose
+// endpoints are ev_src / ev_dst.  The node view's counters are read by the
+// caller's next round trip and passed to nv_append_finish, which reports a
+// pool that ran out (the caller then rebuilds the whole view).
 int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_t n_ev, int64_t new_lo, int64_t nbk,
-              int64_t N_old, bool *rebuild)
+              int64_t N_old)
 {
     cudaStream_t st = h->stream;
     const int directed = h->directed;
     const int64_t N = h->N;
     const int64_t ne = directed ? n_ev : 2 * n_ev, nbe = directed ? nbk : 2 * nbk;
     int rc;
-    *rebuild = false;
     NvtxStages stage;
     stage.next("node view: eviction");
     NvBatchReport &rep = h->nv_rep;
@@ -909,9 +909,14 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         h->pending_launches++;
         if ((rc = nv_append_weights(h, nbe))) return rc;
     }
-    NvCounters *hc = static_cast<NvCounters *>(h->hstat);
-    cudaMemcpyAsync(hc, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
-    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view append"))) return rc;
+    return cuda_check(h, cudaGetLastError(), "node view append");
+}
+
+int nv_append_finish(tempest_t *h, const NvCounters *hc, bool *rebuild)
+{
+    *rebuild = false;
+    NvBatchReport &rep = h->nv_rep;
+    const int directed = h->directed;
     if (hc->status)
         return fail(h, TEMPEST_ECUDA, "node view: consistency check failed (code 0x%llx)",
                     (unsigned long long)hc->status);

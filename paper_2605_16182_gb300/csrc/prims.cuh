@@ -293,7 +293,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Op op, int64_t n, 
     const int64_t b0 = (int64_t)blockIdx.x * per_blk;
     const int64_t b1 = min(n, b0 + per_blk);
     uint64_t s = 0;
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += op.value(i);
+    // SCAN_ITEMS values per thread per chunk, evaluated together (their
+    // loads are independent), in the striped order the emit pass reads
+    for (int64_t c = b0; c < b1; c += SCAN_CHUNK) {
+        uint64_t v[SCAN_ITEMS];
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            const int64_t i = c + k * SCAN_THREADS + threadIdx.x;
+            v[k] = (i < b1) ? op.value(i) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++) s += v[k];
+    }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) wt[threadIdx.x >> 5] = s;
     __syncthreads();
