@@ -43,6 +43,7 @@ namespace tw {
 namespace {
 
 constexpr int BKT_SHORT_RUN = 4;     // table entries a group's own lane writes
+constexpr int BKT_ROUNDS = 4;        // rounds of 32 groups whose timestamps a warp loads together
 constexpr int32_t BKT_COPY = 2048;   // table entries per copy task
 
 // How a big node's table is built: the bucket width, and which part comes
@@ -194,10 +195,11 @@ __global__ void __launch_bounds__(256) k_bkt_owner(const int32_t *__restrict__ b
 // One warp per task (grid-stride).  A node's first tasks copy the buckets its
 // previous table already covers (entry + the node's renumbering delta, the
 // first clamped to the live groups); the rest fill the buckets of its groups
-// from `from` on: lane i takes 32 consecutive groups of a BKT_CHUNK chunk in
-// order, and group g writes the entries (bucket(g - 1), bucket(g)] at or
-// above the first uncopied bucket (the last group also (bucket(g), K], value
-// g_hi).  A node's first task writes its header and its entry K.
+// from `from` on: a BKT_CHUNK chunk in rounds of 32 consecutive groups (lane
+// i the round's group i), and group g writes the entries (bucket(g - 1),
+// bucket(g)] at or above the first uncopied bucket (the last group also
+// (bucket(g), K], value g_hi).  A node's first task writes its header and its
+// entry K.
 __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ big_node,
                                                   const int32_t *__restrict__ big_t,
                                                   const int32_t *__restrict__ big_c,
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
                                                   const int64_t *__restrict__ ngts, const int32_t *__restrict__ prev,
                                                   int gen, int64_t cap, int32_t *bkt, WalkCounters *chk)
 {
-    static_assert(BKT_CHUNK == 32 * 32, "a chunk is 32 groups per lane");
+    static_assert(BKT_CHUNK % (32 * BKT_ROUNDS) == 0, "a chunk is whole rounds");
     const int lane = threadIdx.x & 31;
     const int64_t nch = (int64_t)*tot;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -250,74 +252,49 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
         }
         const int32_t start = from + (local - copy_tasks) * BKT_CHUNK;
         const int32_t end = min(g1, start + BKT_CHUNK);
-        const int32_t my0 = start + 32 * lane, my1 = min(end, my0 + 32);
-        // bucket of the group before this lane's first (-1 at the node's first group)
-        int32_t kp = (my0 == g0 || my0 >= end) ? -1 : (int32_t)((__ldg(ngts + my0 - 1) >> s) - bfirst);
-        // timestamps come in 8 at a time (four 16-byte loads in flight when
-        // the lane's groups start 16-byte aligned, else element loads)
-        const bool vec = (((uintptr_t)(ngts + my0)) & 15) == 0;
-        for (int jb = 0; jb < 32; jb += 8) {
-            int64_t tv[8];
-            const int32_t gb = my0 + jb;
-            if (vec && gb + 8 <= my1) {
-                const longlong2 *q = reinterpret_cast<const longlong2 *>(ngts + gb);
+        // rounds of 32 consecutive groups, one per lane (coalesced loads,
+        // BKT_ROUNDS rounds in flight); a group's predecessor bucket comes
+        // from the lane before it, lane 0's from the previous round (-1 at
+        // the node's first group)
+        int32_t kcarry = start == g0 ? -1 : (int32_t)((__ldg(ngts + start - 1) >> s) - bfirst);
+        for (int32_t gb = start; gb < end; gb += 32 * BKT_ROUNDS) {
+            int64_t tv[BKT_ROUNDS];
 #pragma unroll
-                for (int x = 0; x < 4; x++) {
-                    const longlong2 v2 = __ldg(q + x);
-                    tv[2 * x] = v2.x;
-                    tv[2 * x + 1] = v2.y;
-                }
-            } else {
-#pragma unroll
-                for (int x = 0; x < 8; x++) tv[x] = gb + x < my1 ? __ldg(ngts + gb + x) : 0;
+            for (int x = 0; x < BKT_ROUNDS; x++) {
+                const int32_t g = gb + 32 * x + lane;
+                tv[x] = g < end ? __ldg(ngts + g) : 0;
             }
-            // entries (kp, k] hold g; the last group adds (k, K] holding g1;
-            // entries below ncopy came from the previous table.  A short run
-            // (the common case: a bucket or a few per group) is written by
-            // its own lane here; long runs (time gaps that leave many buckets
-            // empty) are marked and written below by the whole warp
-            const int32_t kp0 = kp;
-            unsigned longm = 0;
 #pragma unroll
-            for (int x = 0; x < 8; x++) {
-                const int32_t g = gb + x;
-                const bool valid = g < my1;
-                const int32_t k = valid ? (int32_t)((tv[x] >> s) - bfirst) : kp;
+            for (int x = 0; x < BKT_ROUNDS; x++) {
+                const int32_t g = gb + 32 * x + lane;
+                const bool valid = g < end;  // the invalid lanes are the last ones of the chunk's last round
+                const int32_t kown = valid ? (int32_t)((tv[x] >> s) - bfirst) : 0;
+                int32_t kp = __shfl_up_sync(0xffffffffu, kown, 1);
+                if (lane == 0) kp = kcarry;
+                kcarry = __shfl_sync(0xffffffffu, kown, 31);
+                // entries (kp, k] hold g; the last group adds (k, K] holding
+                // g1; entries below ncopy came from the previous table.  A
+                // short run (the common case) is written by its own lane,
+                // long runs (time gaps) by the whole warp
+                const int32_t k = valid ? kown : kp;
                 const int32_t lo_k = max(kp + 1, ncopy);
                 const int32_t hi_k = (valid && g == g1 - 1) ? K : k;
                 const int32_t cnt = valid && hi_k >= lo_k ? hi_k - lo_k + 1 : 0;
-                if (cnt > BKT_SHORT_RUN) {
-                    longm |= 1u << x;
-                } else if (cnt > 0) {
-                    bkt[tb + lo_k] = lo_k <= k ? g : g1;
-                    for (int32_t kk = lo_k + 1; kk <= hi_k; kk++) bkt[tb + kk] = kk <= k ? g : g1;
+                if (cnt > 0 && cnt <= BKT_SHORT_RUN) {
+                    for (int32_t kk = lo_k; kk <= hi_k; kk++) bkt[tb + kk] = kk <= k ? g : g1;
                 }
-                kp = k;
-            }
-            if (__any_sync(0xffffffffu, longm != 0)) {
-                int32_t kq = kp0;
-#pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    const int32_t g = gb + x;
-                    const bool valid = g < my1;
-                    const int32_t k = valid ? (int32_t)((tv[x] >> s) - bfirst) : kq;
-                    const int32_t lo_k = max(kq + 1, ncopy);
-                    const int32_t hi_k = (valid && g == g1 - 1) ? K : k;
-                    const int32_t cnt = (longm >> x) & 1u ? hi_k - lo_k + 1 : 0;
-                    unsigned longs = __ballot_sync(0xffffffffu, cnt > 0);
-                    while (longs) {  // 32 entries per store
-                        const int r = __ffs(longs) - 1;
-                        longs &= longs - 1;
-                        const int32_t r_lo = __shfl_sync(0xffffffffu, lo_k, r);
-                        const int32_t r_cnt = __shfl_sync(0xffffffffu, cnt, r);
-                        const int32_t r_k = __shfl_sync(0xffffffffu, k, r);
-                        const int32_t r_g = __shfl_sync(0xffffffffu, g, r);
-                        for (int32_t e = lane; e < r_cnt; e += 32) {
-                            const int32_t kk = r_lo + e;
-                            bkt[tb + kk] = kk <= r_k ? r_g : g1;
-                        }
+                unsigned longs = __ballot_sync(0xffffffffu, cnt > BKT_SHORT_RUN);
+                while (longs) {  // 32 entries per store
+                    const int r = __ffs(longs) - 1;
+                    longs &= longs - 1;
+                    const int32_t r_lo = __shfl_sync(0xffffffffu, lo_k, r);
+                    const int32_t r_cnt = __shfl_sync(0xffffffffu, cnt, r);
+                    const int32_t r_k = __shfl_sync(0xffffffffu, k, r);
+                    const int32_t r_g = __shfl_sync(0xffffffffu, g, r);
+                    for (int32_t e = lane; e < r_cnt; e += 32) {
+                        const int32_t kk = r_lo + e;
+                        bkt[tb + kk] = kk <= r_k ? r_g : g1;
                     }
-                    kq = k;
                 }
             }
         }
