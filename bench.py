@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--workload", default="stream", choices=["stream", "batched", "serve"])
     p.add_argument("--requests", type=int, default=2000)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the batched and served forms (scale 0.1) that follow the stream's measurement")
     p.add_argument("--e2e-steps", type=int, default=10, help="timed steps of the host-buffer (e2e) leg")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep --sched instead of letting the autotuner pick the walk form and knobs")
@@ -587,13 +589,13 @@ def run_batched(args):
                       "live_edges": st["n_live"], "node_view_entries": eng.counts()["M"]},
            "forms": results, "fastest": best}
     eng.close()
-    print(json.dumps(out), flush=True)
+    return out
 
 
 # --------------------------------------------------------------------------
 # serving: continuous batching vs one launch per request
 # --------------------------------------------------------------------------
-def run_serve(args):
+def run_serve(args, quiet=False):
     import math
     import random
     import torch
@@ -728,7 +730,8 @@ def run_serve(args):
                        "walk_p50_ms": pct(sl["walks"], 50), "walk_p99_ms": pct(sl["walks"], 99),
                        "ingest_p50_ms": pct(sl["ingest"], 50), "ingest_p99_ms": pct(sl["ingest"], 99),
                        "waves": sst["waves"], "requests_per_wave": sst["wave_requests"] / max(1, sst["waves"])}})
-        print(json.dumps(out["loads"][-1]), flush=True)
+        if not quiet:
+            print(json.dumps(out["loads"][-1]), flush=True)
     # saturation: every request present at t = 0 (throughput at full load)
     zero = [0.0] * len(reqs)
     pm, pl, _ = plain(zero)
@@ -738,10 +741,47 @@ def run_serve(args):
         "served": {"hops_per_s": total_hops / sm, "makespan_s": sm, "walk_p99_ms": pct(sl["walks"], 99),
                    "waves": sst["waves"], "requests_per_wave": sst["wave_requests"] / max(1, sst["waves"])}}
     out["value"] = out["saturated"]["served"]["hops_per_s"]
-    print(json.dumps(out), flush=True)
+    return out
 
 
 # --------------------------------------------------------------------------
+# batched and served forms beside the stream (scaled down, a few seconds)
+# --------------------------------------------------------------------------
+def run_forms(args):
+    """The batched mixed workload and the serving loop at scale 0.1, after the
+    stream's measurement (its engine closed): one persistent launch against
+    one launch per batch of walks, and the server's waves against one call
+    per request, each pair on the same GPU, inputs and exactness."""
+    import copy
+    import torch
+    a = copy.copy(args)
+    a.scale, a.steps, a.warmup, a.requests = 0.1, 3, 1, 300
+    a.sched = "lane"
+    out = {"scale": 0.1}
+    torch.cuda.empty_cache()
+    b = run_batched(a)
+    out["batched"] = {"workload": b["config"]["workload"], "walks": b["config"]["walks"],
+                      "one_launch_lane_ms": b["forms"]["lane"]["ms_per_call"],
+                      "one_launch_lane_hops_per_s": b["forms"]["lane"]["hops_per_s"],
+                      "autotuned_hops_per_s": b["forms"]["autotuned"]["hops_per_s"],
+                      "per_batch_launches_ms": b["forms"]["per_batch_stream"]["ms_per_call"],
+                      "per_batch_launches_hops_per_s": b["forms"]["per_batch_stream"]["hops_per_s"],
+                      "per_batch_walks": b["forms"]["per_batch_stream"]["batch_walks"]}
+    torch.cuda.empty_cache()
+    sv = run_serve(a, quiet=True)
+    out["served"] = {"workload": sv["config"]["workload"], "requests": sv["config"]["requests"],
+                     "saturated": sv["saturated"],
+                     "loads": [{"offered_load": l["offered_load"],
+                                "plain_walk_p50_ms": l["plain"]["walk_p50_ms"],
+                                "plain_walk_p99_ms": l["plain"]["walk_p99_ms"],
+                                "served_walk_p50_ms": l["served"]["walk_p50_ms"],
+                                "served_walk_p99_ms": l["served"]["walk_p99_ms"],
+                                "plain_hops_per_s": l["plain"]["hops_per_s"],
+                                "served_hops_per_s": l["served"]["hops_per_s"]} for l in sv["loads"]]}
+    torch.cuda.empty_cache()
+    return out
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -783,13 +823,16 @@ def main():
     __graft_entry__.build()
     if args.workload == "batched":
         if rank == 0:
-            run_batched(args)
+            print(json.dumps(run_batched(args)), flush=True)
         return
     if args.workload == "serve":
         if rank == 0:
-            run_serve(args)
+            print(json.dumps(run_serve(args)), flush=True)
         return
     res = run_ours(args, rank, world)
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = run_forms(args)
 
     # aggregate over ranks: total hops / max time
     hops, edges, walk_s, ingest_s, total_ms = aggregate_ranks(res["hops"], res["edges"], res["walk_s"],
@@ -912,6 +955,8 @@ def main():
     }
     if "e2e" in res:
         out["e2e"] = res["e2e"]
+    if forms:
+        out["forms"] = forms
     if res.get("tune"):
         t = res["tune"]
         out["autotune"] = {k: t[k] for k in ("sched", "bkt_log", "coop_w_warp", "coop_mega", "stream_ctas",
