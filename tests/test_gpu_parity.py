@@ -134,6 +134,30 @@ def test_late_edges_and_general_merge():
     assert_state_equal(eng.state(), orc.state())
 
 
+@pytest.mark.parametrize("window", [20, -6])
+@pytest.mark.parametrize("directed", [True, False])
+def test_sorted_batches_with_late_prefix(window, directed):
+    """Batches that arrive in timestamp order but start below the cut-off in
+    force: their late edges are a prefix, which the window step (computed in
+    the statistics' round trip) skips on the device; ties sit at the cut."""
+    eng, orc = pair(window, directed)
+    rng = np.random.default_rng(5 + abs(window))
+    t0, late = 100, 0
+    for b in range(8):
+        n = int(rng.integers(5, 15))
+        ts = np.sort(rng.integers(t0 - 40, t0 + 40, n)).astype(np.int64)
+        ts[: n // 3] = ts[0]  # a tie group at the front
+        s = rng.integers(0, 7, n)
+        d = rng.integers(0, 7, n)
+        st = ingest_both(eng, orc, s, d, ts)
+        assert st["sorted_input"] == 1
+        late += st["n_dropped_late"]
+        assert_state_equal(eng.state(), orc.state(), "batch %d" % b)
+        t0 += 30
+    assert late > 0
+    check_walks(eng, orc, 500, 6, seed=3, biases=(0, 1), scheds=(_lib.SCHED_LANE, _lib.SCHED_STREAM))
+
+
 def test_small_config_state_and_walks():
     spec = synth.config_small()
     eng, orc = pair(spec.window, True)
