@@ -171,6 +171,7 @@ struct tempest {
     int64_t w_ver = -1;    // state version of the suffix sums
     tw::DBuf touched;  // int32: node of each batch-local id
     tw::DBuf ent_tmp;  // Entry: a batch's node view entries in (node, ts, arrival) order
+    tw::DBuf nv_flags; // uint8 per batch entry: run start (bit 0), group start (bit 1)
     int64_t S = 0;     // nodes that own regions (for the bucket index)
     int64_t state_ver = 0;  // bumped by every ingest
     // an ingest that failed after changing the store restored the store's
@@ -199,6 +200,7 @@ struct tempest {
 
     // scratch
     tw::DBuf b_src, b_dst, b_ts;     // batch staged from host
+    tw::DBuf b_gflag;                // uint8 per batch edge: its timestamp differs from the edge before it
     tw::DBuf sb_src, sb_dst, sb_ts;  // batch sorted by timestamp
     tw::DBuf sk64[2], sk32[2], sv[2];
     tw::DBuf hist, partials;

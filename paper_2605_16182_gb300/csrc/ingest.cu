@@ -33,7 +33,9 @@ namespace tw {
 // batch statistics
 // ---------------------------------------------------------------------------
 // One pass over the batch: timestamp range, largest id, reserved values,
-// late edges and whether the timestamps already ascend.  Each thread keeps
+// late edges, whether the timestamps already ascend, and a byte per edge
+// that says whether its timestamp differs from the edge before it (for a
+// batch that arrives sorted, the starts of its timestamp groups).  Each thread keeps
 // four loads of each array in flight (grid-stride, unrolled); each warp and
 // then each block reduce in registers and shared memory, so the global
 // atomics are one set per block (per-warp atomics on the same six words
@@ -44,7 +46,8 @@ constexpr int STATS_UNROLL = 4;
 __global__ void __launch_bounds__(STATS_THREADS) k_batch_stats(const int32_t *__restrict__ src,
                                                                const int32_t *__restrict__ dst,
                                                                const int64_t *__restrict__ ts, int64_t n,
-                                                               int has_cut, long long cut, IngestScratch *o)
+                                                               int has_cut, long long cut, uint8_t *gflag,
+                                                               IngestScratch *o)
 {
     long long tmin = LLONG_MAX, tmax = LLONG_MIN;
     int maxid = 0, neg = 0;
@@ -71,6 +74,9 @@ __global__ void __launch_bounds__(STATS_THREADS) k_batch_stats(const int32_t *__
             neg |= (a[r] < 0) | (b[r] < 0) | ((t[r] == LLONG_MIN) ? 2 : 0) | ((t[r] == LLONG_MAX) ? 4 : 0);
             late += (has_cut && t[r] < cut) ? 1ull : 0ull;
             uns += tp[r] > t[r] ? 1ull : 0ull;
+            // a timestamp group starts here (against the batch's previous
+            // edge; the first kept edge is compared with the store later)
+            gflag[i0 + r * stride] = tp[r] != t[r] ? 1 : 0;
         }
     }
 #pragma unroll
@@ -161,6 +167,30 @@ __global__ void k_gather_batch(const uint32_t *__restrict__ perm, const int32_t 
 // equal timestamps, since every batch edge arrived after every store edge.
 // Returns the number of a-elements among the first r merged elements.
 // ---------------------------------------------------------------------------
+// First index in [lo, hi) where a monotone predicate (false ... false true
+// ... true) holds, hi if none, found by the 32 lanes of a warp together: each
+// step probes 32 evenly spaced points of the bracket, so a search over 2^28
+// elements takes 6 dependent loads instead of 28.  Every lane returns the
+// answer.
+template <class Pred>
+__device__ __forceinline__ int64_t warp_partition_point(int64_t lo, int64_t hi, const Pred &pred)
+{
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const int64_t w = hi - lo;
+        const int64_t pnt = lo + (w * (lane + 1)) / 33;  // strictly inside [lo, hi)
+        const unsigned t = __ballot_sync(0xffffffffu, pred(pnt));
+        const int c = __popc(~t);  // probes where the predicate is false: a prefix
+        const int64_t plo = c > 0 ? lo + (w * c) / 33 + 1 : lo;        // after the last false probe
+        const int64_t phi = c < 32 ? lo + (w * (c + 1)) / 33 : hi;     // the first true probe
+        lo = plo;
+        hi = phi;
+    }
+    const int64_t q = lo + lane;
+    const unsigned t = __ballot_sync(0xffffffffu, q < hi && !pred(q));
+    return lo + __popc(t);
+}
+
 __device__ __forceinline__ int64_t merge_split(const int64_t *a, int64_t na, const int64_t *b, int64_t nb,
                                                int64_t r)
 {
@@ -197,7 +227,8 @@ __device__ __forceinline__ int64_t lower_bound_i64(const int64_t *a, int64_t n, 
 __global__ void k_window(int mode, long long param, const int64_t *old_ts, int64_t m_old,
                          const int64_t *bts, int64_t nb, int has_old, long long cut_old, int fused, IngestScratch *o)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // one warp: lane 0's results are written; the searches run on all lanes
+    if (threadIdx.x >= 32 || blockIdx.x != 0) return;
     if (fused) {
         if (o->unsorted) return;
         const int64_t late = (int64_t)o->late;
@@ -206,6 +237,7 @@ __global__ void k_window(int mode, long long param, const int64_t *old_ts, int64
     }
     int has = has_old;
     long long cut = cut_old;
+    const int lane = threadIdx.x;
     if (mode == 1 && m_old + nb > 0) {
         long long tmax = LLONG_MIN;
         if (m_old > 0) tmax = old_ts[m_old - 1];
@@ -215,7 +247,11 @@ __global__ void k_window(int mode, long long param, const int64_t *old_ts, int64
         has = 1;
     } else if (mode == 2 && m_old + nb > param) {
         const int64_t r = m_old + nb - param;  // rank of the W-th newest element
-        const int64_t i = merge_split(old_ts, m_old, bts, nb, r);
+        // merge split: the first i with a[i] after b[r - i - 1] (see merge_split)
+        const int64_t i = warp_partition_point(r > nb ? r - nb : 0, r < m_old ? r : m_old, [&](int64_t x) {
+            const int64_t jj = r - x;
+            return jj == 0 || bts[jj - 1] < old_ts[x];
+        });
         const int64_t j = r - i;
         long long c;
         if (j >= nb || (i < m_old && old_ts[i] <= bts[j])) c = old_ts[i];
@@ -225,9 +261,10 @@ __global__ void k_window(int mode, long long param, const int64_t *old_ts, int64
     }
     int64_t i0 = 0, j0 = 0;
     if (has) {
-        i0 = lower_bound_i64(old_ts, m_old, cut);
-        j0 = lower_bound_i64(bts, nb, cut);
+        i0 = warp_partition_point(0, m_old, [&](int64_t x) { return old_ts[x] >= cut; });
+        j0 = warp_partition_point(0, nb, [&](int64_t x) { return bts[x] >= cut; });
     }
+    if (lane != 0) return;
     o->cut = cut;
     o->has_cut = has;
     o->i0 = i0;
@@ -289,17 +326,36 @@ struct TsGroupOp {
     }
 };
 
+// The same starts for a batch that arrived sorted, from the batch statistics'
+// bytes (flags[i] for the kept edge i, i >= 1); the first kept edge is
+// compared with the store's previous edge.  One byte per edge on both scan
+// passes instead of two timestamps.
+struct TsGroupFlagOp {
+    const uint8_t *flags;
+    const int64_t *ts;
+    int64_t lo, first;
+    uint32_t abs0;
+    int32_t *tg;
+    __device__ __forceinline__ uint64_t value(int64_t i) const
+    {
+        if (i > 0) return flags[i];
+        const int64_t p = lo;
+        return (p == first || ts[p] != ts[p - 1]) ? 1u : 0u;
+    }
+    __device__ __forceinline__ void emit(int64_t i, uint64_t v, uint64_t ex) const
+    {
+        if (v) tg[ex] = (int32_t)(abs0 + (uint32_t)(lo + i));
+    }
+};
+
 // First live group after the head moved to absolute position s_lo: the first
 // g in [lo, hi) whose successor starts after s_lo (tg[hi] is the old tail),
 // else hi.  Positions compare modulo 2^32 (the live span is below 2^31).
 __global__ void k_ts_evict(const int32_t *__restrict__ tg, int64_t lo, int64_t hi, uint32_t s_lo, IngestScratch *o)
 {
-    while (lo < hi) {
-        const int64_t mid = lo + ((hi - lo) >> 1);
-        if ((int32_t)((uint32_t)tg[mid + 1] - s_lo) > 0) hi = mid;
-        else lo = mid + 1;
-    }
-    o->tg_lo = lo;
+    if (threadIdx.x >= 32) return;  // one warp
+    const int64_t g = warp_partition_point(lo, hi, [&](int64_t x) { return (int32_t)((uint32_t)tg[x + 1] - s_lo) > 0; });
+    if (threadIdx.x == 0) o->tg_lo = g;
 }
 
 // After a compaction of n appended starts written from tg + base: the tail
@@ -379,23 +435,26 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 // kept edges, E / P / U / R = the node view's appended entries, radix
 // passes, distinct nodes and node runs, e / u = evicted entries and the
 // nodes that lost them:
-//   16 b                 batch statistics (src, dst, ts read)
+//   17 b                 batch statistics (src, dst, ts read; a group-start
+//                        byte written per edge)
 //   P_ts (24 b) + 32 b   timestamp sort of an unsorted batch (8-byte key and
 //                        4-byte index read and written per pass), gather
 //   32 k                 store append (kept batch read, store written); a
 //                        merge instead reads both sides and writes the store
-//   8 k + 4 G_new        timestamp view (group starts of the kept batch)
+//   2 k + 4 G_new        timestamp view (both scan passes read the kept
+//                        edges' group-start bytes; 16 k when the batch came
+//                        unsorted and its timestamps are read instead)
 //   4 e + 104 u          eviction: endpoint ids read; per node its counter
 //                        (8) and its records (16 + 32) read and written
 //   8 E + 16 U           batch-local ids (ids read, keys written, id table)
 //   20 P E               node sort passes (key read for the histogram, key
 //                        and value read and written by the scatter)
-//   36 E                 entries packed in sorted order (index read, the
-//                        store item's far end and time gathered, 16-byte
-//                        entry written)
-//   32 E + 148 R         runs (keys and timestamps read by both scan
-//                        passes, run index written; per run its arrays,
-//                        node record and the region reservation)
+//   41 E                 entries packed in sorted order (index and key
+//                        read, the store item's far end and time gathered,
+//                        16-byte entry and a run/group-start byte written)
+//   10 E + 148 R         runs (both scan passes read the start bytes, run
+//                        index written; per run its arrays, node record and
+//                        the region reservation)
 //   32 E_moved + 24 G_moved   region moves (entries, group starts and times)
 //   40 E + 12 G_added    scatter (run and group ids and the packed entry
 //                        read, the entry and new groups written)
@@ -404,10 +463,10 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, int64_t kept_old, int64_t m_new,
                                   int ts_passes, bool append, bool ts_full, int64_t tg_added, int64_t G)
 {
-    int64_t x = 16 * b;
+    int64_t x = 17 * b;
     if (ts_passes > 0) x += ts_passes * 24 * b + 32 * b;
     x += append ? 32 * k : 16 * (kept_old + k) + 16 * m_new;
-    x += ts_full ? 8 * m_new + 4 * G : 8 * k + 4 * tg_added;
+    x += ts_full ? 16 * m_new + 4 * G : (ts_passes > 0 ? 16 * k : 2 * k) + 4 * tg_added;
     if (r.rebuilt) {
         const int64_t M = r.rb_entries;
         x += M * (8 + 20 * r.rb_passes + 32 + 32 + 32) + 12 * r.rb_groups + 104 * r.rb_nodes;
@@ -415,8 +474,8 @@ static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, 
         x += 4 * r.ev_entries + 104 * r.ev_nodes;
         x += 8 * r.entries + 16 * r.ids;
         x += 20 * r.passes * r.entries;
-        x += 36 * r.entries;
-        x += 32 * r.entries + 148 * r.runs;
+        x += 41 * r.entries;
+        x += 10 * r.entries + 148 * r.runs;
         x += 32 * r.moved_e + 24 * r.moved_g;
         x += 40 * r.entries + 12 * r.g_added;
     }
@@ -576,6 +635,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     if ((rc = ensure(h, h->dstat, sizeof(IngestScratch)))) return rc;
     if ((rc = ensure(h, h->partials, sizeof(uint64_t) * (SCAN_MAX_BLOCKS + 2)))) return rc;
     if ((rc = ensure(h, h->hist, sizeof(uint32_t) * (size_t)SORT_HIST_WORDS))) return rc;
+    if ((rc = ensure(h, h->b_gflag, (size_t)n + 1, true))) return rc;
     IngestScratch *ds = h->dstat.as<IngestScratch>();
     IngestScratch *hs = static_cast<IngestScratch *>(h->hstat);
 
@@ -607,7 +667,8 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     if (n > 0)
         k_batch_stats<<<std::min<unsigned>(grid_for(h, (n + STATS_UNROLL - 1) / STATS_UNROLL, STATS_THREADS),
                                            (unsigned)h->num_sms * 4),
-                        STATS_THREADS, 0, st>>>(src, dst, ts, n, h->has_cutoff, h->cutoff, ds);
+                        STATS_THREADS, 0, st>>>(src, dst, ts, n, h->has_cutoff, h->cutoff,
+                                                h->b_gflag.as<uint8_t>(), ds);
     // the window of a batch that turns out sorted (the usual stream), in the
     // same round trip
     const int mode = h->window > 0 ? 1 : (h->window < 0 ? 2 : 0);
@@ -804,9 +865,18 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     if (ts_full) {
         if ((rc = ts_view_build(h))) return rc;
     } else {
-        k_ts_evict<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), h->tg_lo, h->tg_hi, abs32(h, h->s_lo), ds);
-        TsGroupOp op{h->st_ts[h->cur].as<int64_t>(), new_lo, h->s_lo, abs32(h, 0), h->tg.as<int32_t>() + h->tg_hi};
-        const int nbl = scan_launch(op, nbk, h->partials.as<uint64_t>(), st);
+        k_ts_evict<<<1, 32, 0, st>>>(h->tg.as<int32_t>(), h->tg_lo, h->tg_hi, abs32(h, h->s_lo), ds);
+        int nbl;
+        if (sorted) {
+            // the kept edges are the batch's edges late + j0 onwards, in order
+            TsGroupFlagOp op{h->b_gflag.as<uint8_t>() + late + j0, h->st_ts[h->cur].as<int64_t>(), new_lo, h->s_lo,
+                             abs32(h, 0), h->tg.as<int32_t>() + h->tg_hi};
+            nbl = scan_launch(op, nbk, h->partials.as<uint64_t>(), st);
+        } else {
+            TsGroupOp op{h->st_ts[h->cur].as<int64_t>(), new_lo, h->s_lo, abs32(h, 0),
+                         h->tg.as<int32_t>() + h->tg_hi};
+            nbl = scan_launch(op, nbk, h->partials.as<uint64_t>(), st);
+        }
         k_ts_tail<<<1, 1, 0, st>>>(h->tg.as<int32_t>(), h->tg_hi, h->partials.as<uint64_t>() + nbl,
                                    abs32(h, h->s_hi), ds);
         h->pending_launches += 5;

@@ -77,6 +77,51 @@ __global__ void k_nv_entries(const uint32_t *__restrict__ vb, Items it, int64_t 
         E[p] = it.entry(vb[p], slot_base);
 }
 
+// An appending batch's entries in sorted order (kb: batch-local node ids,
+// vb: batch items), packed, with a byte per entry for the run scan: bit 0 a
+// node run starts here, bit 1 a (node, timestamp) group starts here (against
+// the previous entry of the run, or at a run start against the node's last
+// live group before the batch).  The previous entry's id and timestamp come
+// from the lane before (lane 0 loads them), so the scan passes read one byte
+// per entry instead of the entries.
+__global__ void __launch_bounds__(256) k_nv_entries_runs(const uint32_t *__restrict__ vb,
+                                                         const uint32_t *__restrict__ kb, Items it, int64_t M,
+                                                         uint32_t slot_base, const int32_t *__restrict__ touched,
+                                                         const NodeRange *__restrict__ ngr, Entry *E, uint8_t *flags)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count: every lane of a warp takes part in the shuffles
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < M; base += stride) {
+        const int64_t p = base + lane;
+        const bool ok = p < M;
+        Entry x{};
+        uint32_t k = 0;
+        if (ok) {
+            x = it.entry(vb[p], slot_base);
+            k = kb[p];
+            E[p] = x;
+        }
+        uint32_t kprev = __shfl_up_sync(0xffffffffu, k, 1);
+        long long tprev = __shfl_up_sync(0xffffffffu, (long long)x.ts, 1);
+        if (lane == 0 && ok && p > 0) {
+            kprev = kb[p - 1];
+            tprev = it.entry(vb[p - 1], slot_base).ts;
+        }
+        if (ok) {
+            const bool nc = p == 0 || k != kprev;
+            bool gc;
+            if (nc) {
+                const NodeRange g = ngr[touched[k]];
+                gc = g.g_lo == g.g_hi || g.t_last != x.ts;
+            } else {
+                gc = tprev != x.ts;
+            }
+            flags[p] = (uint8_t)((nc ? 1 : 0) | (gc ? 2 : 0));
+        }
+    }
+}
+
 // Node runs and groups over all entries in (node, ts, arrival) order.
 struct BuildRunOp {
     const uint32_t *kb;
@@ -331,28 +376,20 @@ struct DenseLoader {
 };
 
 // Node runs and new groups of the batch's entries in (node, ts, arrival)
-// order (kb: batch-local node ids, E: the entries packed in that order by
-// k_nv_entries, groups as of after the eviction).  Reading the packed
-// entries keeps every load coalesced (gathering each timestamp through the
-// sort's index cost four scattered loads per entry over the two passes).
+// order (kb: batch-local node ids; the run and group starts come as one byte
+// per entry from k_nv_entries_runs, groups as of after the eviction).  The
+// two scan passes read that byte; gathering each timestamp through the
+// sort's index had cost four scattered loads per entry, and reading the
+// packed 16-byte entries 160 MB per pass for a 10M-edge batch.
 struct AppendRunOp {
     const uint32_t *kb;
-    const Entry *E;
+    const uint8_t *flags;  // k_nv_entries_runs: bit 0 run start, bit 1 group start
     const int32_t *touched;
-    const NodeRange *ngr;
     int32_t *run_of, *fx, *run_node, *run_pos, *run_g;
     __device__ __forceinline__ uint64_t value(int64_t p) const
     {
-        const int64_t t = E[p].ts;
-        const bool nc = p == 0 || kb[p] != kb[p - 1];
-        bool gc;
-        if (nc) {
-            const NodeRange &g = ngr[touched[kb[p]]];
-            gc = g.g_lo == g.g_hi || g.t_last != t;
-        } else {
-            gc = E[p - 1].ts != t;
-        }
-        return ((uint64_t)nc << 32) | (uint64_t)gc;
+        const uint32_t f = flags[p];
+        return ((uint64_t)(f & 1u) << 32) | (uint64_t)((f >> 1) & 1u);
     }
     __device__ __forceinline__ void emit(int64_t p, uint64_t v, uint64_t ex) const
     {
@@ -783,6 +820,7 @@ int nv_prepare_append(tempest_t *h, int64_t n_ev, int64_t nbk, int64_t N_old, in
         if ((rc = ensure(h, h->nv_tmp, sizeof(int32_t) * (size_t)(runs_max + 1), true))) return rc;
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->ent_tmp, sizeof(Entry) * (size_t)nbe, true))) return rc;
+        if ((rc = ensure(h, h->nv_flags, (size_t)nbe, true))) return rc;
     }
     return TEMPEST_OK;
 }
@@ -838,6 +876,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         stage.next("node view: batch ids and sort");
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->ent_tmp, sizeof(Entry) * (size_t)nbe, true))) return rc;
+        if ((rc = ensure(h, h->nv_flags, (size_t)nbe, true))) return rc;
         cudaMemsetAsync(h->touched.p, 0xff, sizeof(int32_t) * (size_t)nbe, st);
         uint32_t *dkeys = reinterpret_cast<uint32_t *>(h->run_of.as<int32_t>());
         k_nv_claim<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), h->touched.as<int32_t>(), dc);
@@ -868,10 +907,12 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         // the entries in sorted order, packed once (the runs and the scatter
         // read them coalesced)
         Entry *E = h->ent_tmp.as<Entry>();
-        k_nv_entries<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], it, nbe, slot_base(h, new_lo), E);
-        AppendRunOp op{kb[r], E, h->touched.as<int32_t>(), h->ngr.as<NodeRange>(), h->run_of.as<int32_t>(),
-                       h->fx.as<int32_t>(), h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
-                       h->run_g.as<int32_t>()};
+        uint8_t *rflags = h->nv_flags.as<uint8_t>();
+        k_nv_entries_runs<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], kb[r], it, nbe, slot_base(h, new_lo),
+                                                            h->touched.as<int32_t>(), h->ngr.as<NodeRange>(), E,
+                                                            rflags);
+        AppendRunOp op{kb[r], rflags, h->touched.as<int32_t>(), h->run_of.as<int32_t>(), h->fx.as<int32_t>(),
+                       h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(), h->run_g.as<int32_t>()};
         const int nb = scan_launch(op, nbe, part, st);
         // keep the run totals apart: the next scans reuse the partials
         uint64_t *tot = part + SCAN_MAX_BLOCKS + 1;
