@@ -302,12 +302,26 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
         if (e_lo == r.y) {
             ng = gy;
         } else {
-            // first group whose range ends after e_lo (ngo[gy] = r.y > e_lo)
+            // first group whose range ends after e_lo (ngo[gy] = r.y > e_lo):
+            // the group starts grow about linearly with the group index (a
+            // hub's groups hold about one entry each), so the first probes
+            // interpolate, then the search bisects
             int32_t lo = gx, hi = gy - 1;
-            while (lo < hi) {
-                const int32_t mid = lo + ((hi - lo) >> 1);
-                if (ngo[mid + 1] > e_lo) hi = mid;
-                else lo = mid + 1;
+            int64_t vlo = ngo[lo], vhi = ngo[hi + 1];  // start of group lo, end of group hi
+            for (int step = 0; lo < hi; step++) {
+                int32_t mid = lo + ((hi - lo) >> 1);
+                if (step < 4 && hi - lo > 16 && vhi > vlo) {
+                    const int64_t est = lo + (e_lo - vlo) * (int64_t)(hi + 1 - lo) / (vhi - vlo);
+                    mid = (int32_t)min(max(est, (int64_t)lo), (int64_t)(hi - 1));
+                }
+                const int32_t v = ngo[mid + 1];
+                if (v > e_lo) {
+                    hi = mid;
+                    vhi = v;
+                } else {
+                    lo = mid + 1;
+                    vlo = v;
+                }
             }
             ng = lo;
             ngo[ng] = e_lo;  // the first kept group may have lost a prefix
@@ -347,13 +361,6 @@ __global__ void k_nv_claim(Items it, int64_t nbe, int32_t *dense, int32_t *touch
     }
 }
 
-// Sort key of every entry: its node's batch-local id.
-__global__ void k_nv_keys(Items it, int64_t nbe, const int32_t *__restrict__ dense, uint32_t *keys)
-{
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nbe; j += (int64_t)gridDim.x * blockDim.x)
-        keys[j] = (uint32_t)(__ldg(dense + (int32_t)it.key(j)) - 1);
-}
-
 __global__ void k_iota(uint32_t *v, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -369,9 +376,12 @@ __global__ void k_nv_dense_reset(const int32_t *__restrict__ touched, const NvCo
     }
 }
 
+// The first sort pass reads each entry's batch-local id from the id table
+// (dense[v] - 1; the batch's few thousand nodes keep their words in cache).
 struct DenseLoader {
-    const uint32_t *keys;
-    __device__ __forceinline__ uint32_t key(int64_t i) const { return keys[i]; }
+    Items it;
+    const int32_t *dense;
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)(__ldg(dense + (int32_t)it.key(i)) - 1); }
     __device__ __forceinline__ uint32_t val(int64_t i) const { return (uint32_t)i; }
 };
 
@@ -872,36 +882,35 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         if ((rc = ensure(h, h->reloc, sizeof(Reloc) * (size_t)(runs_max + 1), true))) return rc;
         if ((rc = ensure(h, h->nv_tmp, sizeof(int32_t) * (size_t)(runs_max + 1), true))) return rc;
         const Items it = items_at(h, h->cur, new_lo);
-        // batch-local node ids (keys in run_of, which the run scan rewrites later)
+        // batch-local node ids (the first sort pass reads them from dense[])
         stage.next("node view: batch ids and sort");
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->ent_tmp, sizeof(Entry) * (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->nv_flags, (size_t)nbe, true))) return rc;
         cudaMemsetAsync(h->touched.p, 0xff, sizeof(int32_t) * (size_t)nbe, st);
-        uint32_t *dkeys = reinterpret_cast<uint32_t *>(h->run_of.as<int32_t>());
         k_nv_claim<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), h->touched.as<int32_t>(), dc);
-        k_nv_keys<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), dkeys);
         NvCounters *hd = static_cast<NvCounters *>(h->hstat);
         cudaMemcpyAsync(hd, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
         if ((rc = cuda_check(h, cudaStreamSynchronize(st), "node view ids"))) return rc;
         const int64_t n_ids = (int64_t)hd->n_dense;
-        // the ids live in keys and touched[] from here on: clear dense[] now,
-        // so no later exit of this call can leave ids behind
-        k_nv_dense_reset<<<grid_for(h, n_ids), 256, 0, st>>>(h->touched.as<int32_t>(), dc, h->dense.as<int32_t>());
         uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
         uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
         int launches = 0;
-        const DenseLoader dl{dkeys};
+        const DenseLoader dl{it, h->dense.as<int32_t>()};
         rep.ids = n_ids;
         rep.runs = n_ids;  // one run per distinct node of the batch
         rep.passes = (bits_for((uint64_t)(n_ids > 0 ? n_ids - 1 : 0)) + RADIX_BITS - 1) / RADIX_BITS;
         int r = radix_sort_launch<uint32_t>(dl, nbe, bits_for((uint64_t)(n_ids > 0 ? n_ids - 1 : 0)), kb, vb,
                                             h->hist.as<uint32_t>(), st, &launches);
-        if (r < 0) {  // a single distinct node: the batch order is already grouped
-            cudaMemcpyAsync(kb[0], dkeys, sizeof(uint32_t) * (size_t)nbe, cudaMemcpyDeviceToDevice, st);
+        if (r < 0) {  // a single distinct node (id 0): the batch order is already grouped
+            cudaMemsetAsync(kb[0], 0, sizeof(uint32_t) * (size_t)nbe, st);
             k_iota<<<grid_for(h, nbe), 256, 0, st>>>(vb[0], nbe);
             r = 0;
         }
+        // the ids live in the sorted keys and touched[] from here on (the
+        // first pass, the id table's only reader, is queued before): clear
+        // dense[], with no exit of this call between the claims and here
+        k_nv_dense_reset<<<grid_for(h, n_ids), 256, 0, st>>>(h->touched.as<int32_t>(), dc, h->dense.as<int32_t>());
         stage.next("node view: runs and regions");
         uint64_t *part = h->partials.as<uint64_t>();
         // the entries in sorted order, packed once (the runs and the scatter
@@ -923,7 +932,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
             h->g_cap, h->nrec.as<int4>(), h->ngr.as<NodeRange>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
             h->act.as<int32_t>(), h->nrec_n, h->reloc.as<Reloc>(), h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(),
             dc);
-        h->pending_launches += launches + 7;
+        h->pending_launches += launches + 6;
         // moves and scatter are queued without a round trip: they read the
         // move count on the device and do nothing when a pool overflowed
         // (the host sees that at the end and rebuilds the view)

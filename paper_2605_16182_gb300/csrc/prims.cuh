@@ -323,12 +323,17 @@ __global__ void k_scan_partials(uint64_t *partials, int nb);
 // (element c + k*THREADS + thread, so a warp touches consecutive elements) and
 // staged through shared memory, where each thread scans SCAN_ITEMS
 // consecutive values.
+// Shared-memory slot of staged element j: one pad slot per 16 (a thread's
+// SCAN_ITEMS consecutive 8-byte values sit 64 B apart from the next
+// thread's, which without the pad maps a half-warp onto two banks).
+__device__ __forceinline__ int scan_slot(int j) { return j + (j >> 4); }
+
 template <class Op>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_emit(Op op, int64_t n, int64_t per_blk,
                                                             const uint64_t *partials)
 {
     __shared__ uint64_t wt[33];
-    __shared__ uint64_t sv[SCAN_CHUNK];   // values, then exclusive prefixes
+    __shared__ uint64_t sv[SCAN_CHUNK + SCAN_CHUNK / 16];  // values, then exclusive prefixes
     const int64_t b0 = (int64_t)blockIdx.x * per_blk;
     const int64_t b1 = min(n, b0 + per_blk);
     uint64_t carry = partials[blockIdx.x];
@@ -337,14 +342,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_emit(Op op, int64_t n, in
         for (int k = 0; k < SCAN_ITEMS; k++) {
             const int j = k * SCAN_THREADS + threadIdx.x;
             const int64_t i = c + j;
-            sv[j] = (i < b1) ? op.value(i) : 0;
+            sv[scan_slot(j)] = (i < b1) ? op.value(i) : 0;
         }
         __syncthreads();
         uint64_t v[SCAN_ITEMS];
         uint64_t s = 0;
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; k++) {
-            v[k] = sv[threadIdx.x * SCAN_ITEMS + k];
+            v[k] = sv[scan_slot(threadIdx.x * SCAN_ITEMS + k)];
             s += v[k];
         }
         uint64_t tot;
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_emit(Op op, int64_t n, in
         ex += carry;
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; k++) {
-            sv[threadIdx.x * SCAN_ITEMS + k] = ex;
+            sv[scan_slot(threadIdx.x * SCAN_ITEMS + k)] = ex;
             ex += v[k];
         }
         __syncthreads();
@@ -361,8 +366,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_emit(Op op, int64_t n, in
             const int j = k * SCAN_THREADS + threadIdx.x;
             const int64_t i = c + j;
             if (i < b1) {
-                const uint64_t e = sv[j];
-                const uint64_t nx = (j + 1 < SCAN_CHUNK) ? sv[j + 1] : carry + tot;
+                const uint64_t e = sv[scan_slot(j)];
+                const uint64_t nx = (j + 1 < SCAN_CHUNK) ? sv[scan_slot(j + 1)] : carry + tot;
                 op.emit(i, nx - e, e);
             }
         }
