@@ -249,6 +249,10 @@ __global__ void __launch_bounds__(256) k_nv_evict_count(Items it, int64_t items,
     const int64_t per = (items + gridDim.x - 1) / gridDim.x;
     const int64_t b0 = (int64_t)blockIdx.x * per;
     const int64_t b1 = min(items, b0 + per);
+    // the warp's hot key (the first key that filled 8 or more lanes) and its
+    // running count, kept in registers (the same in every lane) and added to
+    // the counter once at the end
+    int32_t hot = -1, hot_cnt = 0;
     for (int64_t base = b0; base < b1; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
         int32_t v = -1;
@@ -260,6 +264,13 @@ __global__ void __launch_bounds__(256) k_nv_evict_count(Items it, int64_t items,
             }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, v);
+        if (hot < 0) {
+            // claim the hot key: the lowest lane of a group of 8 or more
+            const unsigned big = __ballot_sync(0xffffffffu, v >= 0 && __popc(peers) >= 8 && lane == __ffs(peers) - 1);
+            if (big) hot = __shfl_sync(0xffffffffu, v, __ffs(big) - 1);
+        }
+        hot_cnt += __popc(__ballot_sync(0xffffffffu, v >= 0 && v == hot));  // the same in every lane
+        if (v >= 0 && v == hot) continue;
         if (v >= 0 && lane == __ffs(peers) - 1) {
             const int32_t cnt = __popc(peers);
             const uint32_t h0 = ((uint32_t)v * 2654435761u) >> 21;  // 11 bits: EV_SLOTS
@@ -276,6 +287,7 @@ __global__ void __launch_bounds__(256) k_nv_evict_count(Items it, int64_t items,
             if (!done) ev_add(v, cnt, ev, ev_nodes, c);
         }
     }
+    if (lane == 0 && hot >= 0 && hot_cnt > 0) ev_add(hot, hot_cnt, ev, ev_nodes, c);
     __syncthreads();
     for (int i = threadIdx.x; i < EV_SLOTS; i += blockDim.x)
         if (s_key[i] >= 0) ev_add(s_key[i], s_cnt[i], ev, ev_nodes, c);
@@ -348,15 +360,26 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
 __global__ void k_nv_claim(Items it, int64_t nbe, int32_t *dense, int32_t *touched, NvCounters *c)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nbe; j += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = (int32_t)it.key(j);
-        const unsigned am = __activemask();
-        const unsigned peers = __match_any_sync(am, v);
-        // a stale 0 from the cached read only costs a compare-and-swap that fails
-        if (lane == __ffs(peers) - 1 && dense[v] == 0 && atomicCAS(&dense[v], 0, -1) == 0) {
-            const int32_t id = (int32_t)atomicAdd(&c->n_dense, 1ull);
-            touched[id] = v;
-            dense[v] = id + 1;
+    constexpr int U = 4;  // entries per thread whose ids are loaded together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count (every lane takes part in the match)
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < nbe;
+         base += stride * U) {
+        int32_t v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t j = base + u * stride + lane;
+            v[u] = j < nbe ? (int32_t)it.key(j) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const unsigned peers = __match_any_sync(0xffffffffu, v[u]);
+            // a stale 0 from the cached read only costs a compare-and-swap that fails
+            if (v[u] >= 0 && lane == __ffs(peers) - 1 && dense[v[u]] == 0 && atomicCAS(&dense[v[u]], 0, -1) == 0) {
+                const int32_t id = (int32_t)atomicAdd(&c->n_dense, 1ull);
+                touched[id] = v[u];
+                dense[v[u]] = id + 1;
+            }
         }
     }
 }

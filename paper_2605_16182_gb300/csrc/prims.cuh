@@ -431,14 +431,21 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(L ld, int64_t n, in
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t b0 = (int64_t)blockIdx.x * per_blk;
     const int64_t b1 = min(n, b0 + per_blk);
-    for (int64_t base = b0; base < b1; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const bool ok = i < b1;
-        const uint32_t d = ok ? (uint32_t)((ld.key(i) >> shift) & (RADIX - 1)) : 0xffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const int leader = __ffs(peers) - 1;
-        if (ok && lane == leader) h[w][d] += __popc(peers);
-        __syncwarp();
+    constexpr int U = 4;  // keys per thread loaded together (independent loads in flight)
+    for (int64_t base = b0; base < b1; base += (int64_t)U * blockDim.x) {
+        uint32_t d[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t i = base + u * blockDim.x + threadIdx.x;
+            d[u] = i < b1 ? (uint32_t)((ld.key(i) >> shift) & (RADIX - 1)) : 0xffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, d[u]);
+            const int leader = __ffs(peers) - 1;
+            if (d[u] != 0xffffu && lane == leader) h[w][d[u]] += __popc(peers);
+            __syncwarp();
+        }
     }
     __syncthreads();
     for (int d = threadIdx.x; d < RADIX; d += blockDim.x) {
