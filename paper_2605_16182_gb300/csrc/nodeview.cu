@@ -253,38 +253,47 @@ __global__ void __launch_bounds__(256) k_nv_evict_count(Items it, int64_t items,
     // running count, kept in registers (the same in every lane) and added to
     // the counter once at the end
     int32_t hot = -1, hot_cnt = 0;
-    for (int64_t base = b0; base < b1; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        int32_t v = -1;
-        if (i < b1) {
-            v = (int32_t)it.key(i);
-            if (v < 0 || v >= N) {
-                atomicOr(&c->status, 1ull << 0);
-                v = -1;
-            }
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, v);
-        if (hot < 0) {
-            // claim the hot key: the lowest lane of a group of 8 or more
-            const unsigned big = __ballot_sync(0xffffffffu, v >= 0 && __popc(peers) >= 8 && lane == __ffs(peers) - 1);
-            if (big) hot = __shfl_sync(0xffffffffu, v, __ffs(big) - 1);
-        }
-        hot_cnt += __popc(__ballot_sync(0xffffffffu, v >= 0 && v == hot));  // the same in every lane
-        if (v >= 0 && v == hot) continue;
-        if (v >= 0 && lane == __ffs(peers) - 1) {
-            const int32_t cnt = __popc(peers);
-            const uint32_t h0 = ((uint32_t)v * 2654435761u) >> 21;  // 11 bits: EV_SLOTS
-            bool done = false;
-            for (int p = 0; p < EV_PROBES && !done; p++) {
-                const int slot = (int)((h0 + (uint32_t)p) & (EV_SLOTS - 1));
-                int32_t k = s_key[slot];
-                if (k == -1) k = atomicCAS(&s_key[slot], -1, v);
-                if (k == -1 || k == v) {
-                    atomicAdd(&s_cnt[slot], cnt);
-                    done = true;
+    constexpr int U = 4;  // items per thread whose ids are loaded together
+    for (int64_t base = b0; base < b1; base += (int64_t)U * blockDim.x) {
+        int32_t vu[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t i = base + u * blockDim.x + threadIdx.x;
+            vu[u] = -1;
+            if (i < b1) {
+                vu[u] = (int32_t)it.key(i);
+                if (vu[u] < 0 || vu[u] >= N) {
+                    atomicOr(&c->status, 1ull << 0);
+                    vu[u] = -1;
                 }
             }
-            if (!done) ev_add(v, cnt, ev, ev_nodes, c);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int32_t v = vu[u];
+            const unsigned peers = __match_any_sync(0xffffffffu, v);
+            if (hot < 0) {
+                // claim the hot key: the lowest lane of a group of 8 or more
+                const unsigned big = __ballot_sync(0xffffffffu, v >= 0 && __popc(peers) >= 8 && lane == __ffs(peers) - 1);
+                if (big) hot = __shfl_sync(0xffffffffu, v, __ffs(big) - 1);
+            }
+            hot_cnt += __popc(__ballot_sync(0xffffffffu, v >= 0 && v == hot));  // the same in every lane
+            if (v >= 0 && v == hot) continue;  // the next item of this thread
+            if (v >= 0 && lane == __ffs(peers) - 1) {
+                const int32_t cnt = __popc(peers);
+                const uint32_t h0 = ((uint32_t)v * 2654435761u) >> 21;  // 11 bits: EV_SLOTS
+                bool done = false;
+                for (int p = 0; p < EV_PROBES && !done; p++) {
+                    const int slot = (int)((h0 + (uint32_t)p) & (EV_SLOTS - 1));
+                    int32_t k = s_key[slot];
+                    if (k == -1) k = atomicCAS(&s_key[slot], -1, v);
+                    if (k == -1 || k == v) {
+                        atomicAdd(&s_cnt[slot], cnt);
+                        done = true;
+                    }
+                }
+                if (!done) ev_add(v, cnt, ev, ev_nodes, c);
+            }
         }
     }
     if (lane == 0 && hot >= 0 && hot_cnt > 0) ev_add(hot, hot_cnt, ev, ev_nodes, c);
