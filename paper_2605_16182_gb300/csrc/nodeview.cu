@@ -572,47 +572,66 @@ __global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__res
     }
 }
 
-__global__ void k_nv_scatter(const Entry *__restrict__ E, int64_t nbe,
-                             const int32_t *__restrict__ run_of, const int32_t *__restrict__ fx,
-                             const int32_t *__restrict__ run_pos, const int32_t *__restrict__ run_g,
-                             const int32_t *__restrict__ run_de, const int32_t *__restrict__ run_dg,
-                             const int32_t *__restrict__ run_node, int64_t e_cap, int64_t g_cap, Entry *ent,
-                             int32_t *ngo, int64_t *ngts, NodeRange *ngr, NvCounters *c)
+__global__ void __launch_bounds__(256, 4)
+    k_nv_scatter(const Entry *__restrict__ E, int64_t nbe, const int32_t *__restrict__ run_of,
+                 const int32_t *__restrict__ fx, const int32_t *__restrict__ run_pos, const int32_t *__restrict__ run_g,
+                 const int32_t *__restrict__ run_de, const int32_t *__restrict__ run_dg,
+                 const int32_t *__restrict__ run_node, int64_t e_cap, int64_t g_cap, Entry *ent, int32_t *ngo,
+                 int64_t *ngts, NodeRange *ngr, NvCounters *c)
 {
     if (c->overflow) return;  // a pool could not serve a region: the batch rebuilds the view instead
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nbe; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = run_of[p];
-        const int32_t de = run_de[r];
-        const int32_t i = (int32_t)p - run_pos[r];
-        const int64_t e = (int64_t)de + i;
-        if (de < 0 || e >= e_cap) {
-            atomicOr(&c->status, 1ull << 3);
-            continue;
+    constexpr int U = 4;      // entries per thread whose loads are in flight together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < nbe; p0 += stride * U) {
+        int32_t rr[U], f0[U], f1[U];
+        Entry xs[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t p = p0 + u * stride;
+            if (p < nbe) {
+                rr[u] = run_of[p];
+                f0[u] = fx[p];
+                f1[u] = fx[p + 1];
+                xs[u] = E[p];
+            }
         }
-        const Entry x = E[p];
-        ent[e] = x;
-        // the node record's first / last group timestamps
-        if (p == run_pos[r]) {
-            const int32_t v = run_node[r];
-            if (ngr[v].g_lo == run_dg[r]) ngr[v].t_first = x.ts;  // no live group before the batch
-        }
-        if (p + 1 == run_pos[r + 1]) ngr[run_node[r]].t_last = x.ts;
-        if (fx[p + 1] != fx[p]) {
-            const int64_t g = (int64_t)run_dg[r] + (fx[p] - run_g[r]);
-            if (g < 0 || g >= g_cap) {
-                atomicOr(&c->status, 1ull << 4);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t p = p0 + u * stride;
+            if (p >= nbe) break;
+            const int32_t r = rr[u];
+            const int32_t de = run_de[r];
+            const int32_t i = (int32_t)p - run_pos[r];
+            const int64_t e = (int64_t)de + i;
+            if (de < 0 || e >= e_cap) {
+                atomicOr(&c->status, 1ull << 3);
                 continue;
             }
-            ngts[g] = x.ts;
-            ngo[g] = (int32_t)e;
-        }
-        if (p + 1 == run_pos[r + 1]) {  // the node's new end after its last group
-            const int64_t gs = (int64_t)run_dg[r] + (run_g[r + 1] - run_g[r]);
-            if (gs < 0 || gs >= g_cap) {
-                atomicOr(&c->status, 1ull << 5);
-                continue;
+            const Entry x = xs[u];
+            ent[e] = x;
+            // the node record's first / last group timestamps
+            if (p == run_pos[r]) {
+                const int32_t v = run_node[r];
+                if (ngr[v].g_lo == run_dg[r]) ngr[v].t_first = x.ts;  // no live group before the batch
             }
-            ngo[gs] = (int32_t)(e + 1);
+            if (p + 1 == run_pos[r + 1]) ngr[run_node[r]].t_last = x.ts;
+            if (f1[u] != f0[u]) {
+                const int64_t g = (int64_t)run_dg[r] + (f0[u] - run_g[r]);
+                if (g < 0 || g >= g_cap) {
+                    atomicOr(&c->status, 1ull << 4);
+                    continue;
+                }
+                ngts[g] = x.ts;
+                ngo[g] = (int32_t)e;
+            }
+            if (p + 1 == run_pos[r + 1]) {  // the node's new end after its last group
+                const int64_t gs = (int64_t)run_dg[r] + (run_g[r + 1] - run_g[r]);
+                if (gs < 0 || gs >= g_cap) {
+                    atomicOr(&c->status, 1ull << 5);
+                    continue;
+                }
+                ngo[gs] = (int32_t)(e + 1);
+            }
         }
     }
 }

@@ -525,19 +525,23 @@ __global__ void __launch_bounds__(SORT_THREADS, sizeof(K) == 4 ? 5 : 3) k_radix_
         uint32_t dd[SORT_ITEMS];
         uint32_t rk[SORT_ITEMS];
         const int64_t chunk = t0 + (int64_t)w * 32 * SORT_ITEMS;
+        // all SORT_ITEMS loads in flight before the ranking (whose warp
+        // barriers would otherwise hold each load until the previous rank)
 #pragma unroll
         for (int r = 0; r < SORT_ITEMS; r++) {
             const int64_t i = chunk + r * 32 + lane;
-            const bool ok = i < b1;
-            if (ok) {
+            if (i < b1) {
                 kk[r] = ld.key(i);
                 vv[r] = ld.val(i);
-                dd[r] = (uint32_t)((kk[r] >> shift) & (RADIX - 1));
             } else {
                 kk[r] = K(0);
                 vv[r] = 0;
-                dd[r] = 0xffffu;
             }
+        }
+#pragma unroll
+        for (int r = 0; r < SORT_ITEMS; r++) {
+            const bool ok = chunk + r * 32 + lane < b1;
+            dd[r] = ok ? (uint32_t)((kk[r] >> shift) & (RADIX - 1)) : 0xffffu;
             const uint32_t peers = __match_any_sync(0xffffffffu, dd[r]);
             const uint32_t pre = ok ? wcnt[w][dd[r]] : 0u;
             __syncwarp();
