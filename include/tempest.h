@@ -195,7 +195,10 @@ int tempest_set_stream(tempest_t *h, void *stream);
 /* Route device allocations through alloc(bytes, ctx) / release(ptr, ctx)
  * (e.g. a framework's caching allocator) and cap the handle's device memory
  * at hbm_budget bytes (0 = no cap).  Either callback may be NULL to restore
- * cudaMalloc / cudaFree.  Call before the first ingest. */
+ * cudaMalloc / cudaFree.  alloc must return device memory aligned to 256
+ * bytes, as cudaMalloc does (a call that gets another pointer releases it
+ * and fails with EINVAL, the handle unchanged).  Call before the first
+ * ingest. */
 int tempest_set_allocator(tempest_t *h, void *(*alloc)(size_t bytes, void *ctx),
                           void (*release)(void *ptr, void *ctx), void *ctx, size_t hbm_budget);
 

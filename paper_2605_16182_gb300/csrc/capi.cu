@@ -95,6 +95,11 @@ int ensure(tempest_t *h, DBuf &b, size_t bytes, bool headroom)
     if (h->alloc_fn) {
         p = h->alloc_fn(want, h->alloc_ctx);
         if (!p) return fail(h, TEMPEST_ENOMEM, "allocator callback returned NULL for %zu bytes", want);
+        if ((uintptr_t)p & 255) {  // kernels load 16-byte records and vectors from every buffer
+            if (h->release_fn) h->release_fn(p, h->alloc_ctx);
+            else cudaFree(p);
+            return fail(h, TEMPEST_EINVAL, "allocator callback returned %p, not 256-byte aligned", p);
+        }
     } else {
         const cudaError_t e = cudaMalloc(&p, want);
         if (e != cudaSuccess) {

@@ -419,29 +419,65 @@ struct DenseLoader {
 
 // Node runs and new groups of the batch's entries in (node, ts, arrival)
 // order (kb: batch-local node ids; the run and group starts come as one byte
-// per entry from k_nv_entries_runs, groups as of after the eviction).  The
-// two scan passes read that byte; gathering each timestamp through the
-// sort's index had cost four scattered loads per entry, and reading the
-// packed 16-byte entries 160 MB per pass for a 10M-edge batch.
-struct AppendRunOp {
+// per entry from k_nv_entries_runs, groups as of after the eviction: bit 0 a
+// run start, bit 1 a group start).  A byte scan: each thread reads 16 flags
+// with one load and writes its 16 run_of and fx values as four 16-byte
+// stores each (flags, run_of and fx 16-byte aligned).  Gathering each
+// timestamp through the sort's index had cost four scattered loads per
+// entry, reading the packed 16-byte entries 160 MB per pass for a 10M-edge
+// batch, and one byte per element through the generic scan 44 instructions
+// per element.
+struct AppendRunBytes {
+    const uint8_t *flags;
+    int64_t n;
     const uint32_t *kb;
-    const uint8_t *flags;  // k_nv_entries_runs: bit 0 run start, bit 1 group start
     const int32_t *touched;
     int32_t *run_of, *fx, *run_node, *run_pos, *run_g;
-    __device__ __forceinline__ uint64_t value(int64_t p) const
+    struct Stage {};
+    __host__ __device__ int64_t tiles() const { return n > 0 ? (n + BSCAN_TILE - 1) / BSCAN_TILE : 0; }
+    __device__ __forceinline__ uint4 load(int64_t u0) const
     {
-        const uint32_t f = flags[p];
-        return ((uint64_t)(f & 1u) << 32) | (uint64_t)((f >> 1) & 1u);
+        return u0 < n ? __ldg(reinterpret_cast<const uint4 *>(flags + u0)) : make_uint4(0, 0, 0, 0);
     }
-    __device__ __forceinline__ void emit(int64_t p, uint64_t v, uint64_t ex) const
+    __device__ __forceinline__ uint64_t sum16(uint4 w, int64_t u0) const
     {
-        const uint32_t r = (uint32_t)(ex >> 32) + (uint32_t)(v >> 32) - 1u;
-        run_of[p] = (int32_t)r;
-        fx[p] = (int32_t)(uint32_t)ex;
-        if (v >> 32) {
-            run_node[r] = touched[kb[p]];
-            run_pos[r] = (int32_t)p;
-            run_g[r] = (int32_t)(uint32_t)ex;
+        const uint32_t v = valid16(u0, 0, n);
+        return ((uint64_t)__popc(byte_bits16(w, 0) & v) << 32) | (uint64_t)__popc(byte_bits16(w, 1) & v);
+    }
+    __device__ __forceinline__ void emit16(uint4 w, int64_t u0, uint64_t ex, uint64_t, uint64_t, Stage &) const
+    {
+        const uint32_t v = valid16(u0, 0, n);
+        const uint32_t rm = byte_bits16(w, 0) & v, gm = byte_bits16(w, 1) & v;
+        uint32_t R = (uint32_t)(ex >> 32), G = (uint32_t)ex;
+        int32_t ro[16], fo[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const uint32_t rs = (rm >> k) & 1u;
+            R += rs;
+            ro[k] = (int32_t)(R - 1u);
+            fo[k] = (int32_t)G;
+            if (rs) {  // a node run starts here
+                const int64_t p = u0 + k;
+                run_node[R - 1u] = touched[kb[p]];
+                run_pos[R - 1u] = (int32_t)p;
+                run_g[R - 1u] = (int32_t)G;
+            }
+            G += (gm >> k) & 1u;
+        }
+        if (u0 + 16 <= n) {
+            int4 *o = reinterpret_cast<int4 *>(run_of + u0), *f = reinterpret_cast<int4 *>(fx + u0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                o[q] = make_int4(ro[4 * q], ro[4 * q + 1], ro[4 * q + 2], ro[4 * q + 3]);
+                f[q] = make_int4(fo[4 * q], fo[4 * q + 1], fo[4 * q + 2], fo[4 * q + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; k++)
+                if (u0 + k < n) {
+                    run_of[u0 + k] = ro[k];
+                    fx[u0 + k] = fo[k];
+                }
         }
     }
 };
@@ -971,9 +1007,10 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         k_nv_entries_runs<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], kb[r], it, nbe, slot_base(h, new_lo),
                                                             h->touched.as<int32_t>(), h->ngr.as<NodeRange>(), E,
                                                             rflags);
-        AppendRunOp op{kb[r], rflags, h->touched.as<int32_t>(), h->run_of.as<int32_t>(), h->fx.as<int32_t>(),
-                       h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(), h->run_g.as<int32_t>()};
-        const int nb = scan_launch(op, nbe, part, st);
+        AppendRunBytes op{rflags, nbe, kb[r], h->touched.as<int32_t>(), h->run_of.as<int32_t>(),
+                          h->fx.as<int32_t>(), h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
+                          h->run_g.as<int32_t>()};
+        const int nb = bscan_launch(op, part, st);
         // keep the run totals apart: the next scans reuse the partials
         uint64_t *tot = part + SCAN_MAX_BLOCKS + 1;
         cudaMemcpyAsync(tot, part + nb, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);

@@ -397,6 +397,108 @@ int scan_launch(const Op &op, int64_t n, uint64_t *partials, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
+// Two-level scans over one flag byte per element.  Each thread takes 16
+// consecutive bytes with one 16-byte load and evaluates their values in
+// registers (bit masks of the bytes), a block scans the thread sums, and the
+// op writes its outputs from registers.  Elements are addressed through a
+// virtual index u = i + a from a 16-byte aligned base (a = the flags'
+// misalignment), so every load is aligned; the bytes outside [a, a + n) are
+// masked, and the allocation must extend to the next 16-byte boundary after
+// the last element.  Op supplies
+//   __host__ __device__ int64_t tiles() const;           // tiles of BSCAN_TILE virtual elements
+//   __device__ uint4 load(int64_t u0) const;             // the 16 bytes at virtual index u0
+//   __device__ uint64_t sum16(uint4 w, int64_t u0) const;  // sum of their values
+//   __device__ void emit16(uint4 w, int64_t u0, uint64_t ex, uint64_t tile_ex, uint64_t tile_tot,
+//                          Stage &sm) const;             // ex: exclusive prefix of u0's first element
+//   struct Stage;                                        // the op's shared memory per block
+// emit16 is called by every thread of the block (it may synchronise).
+// ---------------------------------------------------------------------------
+constexpr int BSCAN_THREADS = 256;
+constexpr int BSCAN_TILE = BSCAN_THREADS * 16;
+
+// Bit k of the result is bit b of byte k of w.  (((x >> b) & 0x01010101) *
+// 0x10204080) >> 28 gathers the bit of byte q of x into bit q: the four
+// products that land in bits 28-31 are the wanted ones, and the others fall
+// on distinct lower bits, so no carry reaches them.
+__device__ __forceinline__ uint32_t byte_bits16(uint4 w, int b)
+{
+    const uint32_t m = 0x01010101u;
+    return ((((w.x >> b) & m) * 0x10204080u) >> 28) | (((((w.y >> b) & m) * 0x10204080u) >> 28) << 4) |
+           (((((w.z >> b) & m) * 0x10204080u) >> 28) << 8) | (((((w.w >> b) & m) * 0x10204080u) >> 28) << 12);
+}
+
+// Mask of the 16 virtual elements from u0 that fall in [a, a + n).
+__device__ __forceinline__ uint32_t valid16(int64_t u0, int64_t a, int64_t n)
+{
+    const int64_t lo = a - u0, hi = a + n - u0;
+    const uint32_t hm = hi >= 16 ? 0xffffu : (hi <= 0 ? 0u : (1u << hi) - 1u);
+    const uint32_t lm = lo <= 0 ? 0u : (lo >= 16 ? 0xffffu : (1u << lo) - 1u);
+    return hm & ~lm;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(BSCAN_THREADS) k_bscan_reduce(Op op, int64_t per, uint64_t *partials)
+{
+    __shared__ uint64_t wt[32];
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(op.tiles(), t0 + per);
+    uint64_t s = 0;
+    for (int64_t t = t0; t < t1; t += 2) {  // two loads in flight per thread
+        const int64_t u0 = t * BSCAN_TILE + 16 * threadIdx.x, u1 = u0 + BSCAN_TILE;
+        const uint4 w0 = op.load(u0);
+        const uint4 w1 = t + 1 < t1 ? op.load(u1) : make_uint4(0, 0, 0, 0);
+        s += op.sum16(w0, u0);
+        if (t + 1 < t1) s += op.sum16(w1, u1);
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) wt[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += wt[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+template <class Op>
+__global__ void __launch_bounds__(BSCAN_THREADS) k_bscan_emit(Op op, int64_t per, const uint64_t *partials)
+{
+    __shared__ uint64_t wt[33];
+    __shared__ typename Op::Stage sm;
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(op.tiles(), t0 + per);
+    uint64_t carry = partials[blockIdx.x];
+    uint4 w = t0 < t1 ? op.load(t0 * BSCAN_TILE + 16 * threadIdx.x) : make_uint4(0, 0, 0, 0);
+    for (int64_t t = t0; t < t1; t++) {
+        const int64_t u0 = t * BSCAN_TILE + 16 * threadIdx.x;
+        // the next tile's bytes in flight while this one is scanned
+        const uint4 wn = t + 1 < t1 ? op.load(u0 + BSCAN_TILE) : make_uint4(0, 0, 0, 0);
+        uint64_t tot;
+        const uint64_t ex = block_excl_scan<uint64_t>(op.sum16(w, u0), wt, tot);  // synchronises
+        op.emit16(w, u0, carry + ex, carry, tot, sm);
+        carry += tot;
+        w = wn;
+    }
+}
+
+// Host driver, as scan_launch: partials must hold SCAN_MAX_BLOCKS + 1
+// entries; the total ends in partials[nb] where nb is returned.
+template <class Op>
+int bscan_launch(const Op &op, uint64_t *partials, cudaStream_t st)
+{
+    const int64_t tiles = op.tiles();
+    if (tiles <= 0) {
+        cudaMemsetAsync(partials, 0, sizeof(uint64_t), st);
+        return 0;
+    }
+    int64_t nb = tiles < SCAN_MAX_BLOCKS ? tiles : SCAN_MAX_BLOCKS;
+    const int64_t per = (tiles + nb - 1) / nb;
+    nb = (tiles + per - 1) / per;
+    k_bscan_reduce<Op><<<(unsigned)nb, BSCAN_THREADS, 0, st>>>(op, per, partials);
+    k_scan_partials<<<1, 1024, 0, st>>>(partials, (int)nb);
+    k_bscan_emit<Op><<<(unsigned)nb, BSCAN_THREADS, 0, st>>>(op, per, partials);
+    return (int)nb;
+}
+
+// ---------------------------------------------------------------------------
 // Stable LSD radix sort of (key, value) pairs, 8-bit digits.
 // A Loader supplies the input of the first pass:
 //   __device__ K key(int64_t i) const;  __device__ uint32_t val(int64_t i) const;

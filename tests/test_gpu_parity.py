@@ -202,6 +202,38 @@ def test_mid_config_scaled_stream():
                 assert (g[1][lin_or_uni] == o[1][lin_or_uni]).all()
 
 
+@pytest.mark.parametrize("directed", [True, False])
+def test_large_batches_state(directed):
+    """Batches of 9M edges (18M index entries undirected): the flag scans and
+    sorts then give each block more than one tile, which smaller tests never
+    reach.  Sorted, sorted with a late prefix (the flags start off a 16-byte
+    boundary), and shuffled; state after every batch."""
+    n, w = 9_000_000, -12_000_000
+    spec = synth.StreamSpec("large-batches", 200_000, 3 * n, 1.6, 99, n, mean_gaps=[3, 1], switch_every=n // 3,
+                            window=w)
+    eng, orc = pair(w, directed)
+    rng = np.random.default_rng(17)
+    cut = None
+    for k, s, d, t in spec.batches():
+        s, d, t = s.numpy(), d.numpy(), t.numpy()
+        if k == 2:
+            # seven edges below the cut-off in force lead the sorted batch
+            t = t.copy()
+            t[:7] = cut - 5 - np.arange(7)[::-1]
+            st = ingest_both(eng, orc, s, d, t)
+            assert st["sorted_input"] == 1 and st["n_dropped_late"] == 7
+        elif k == 1:
+            p_ = rng.permutation(len(t))
+            st = ingest_both(eng, orc, s[p_], d[p_], t[p_])
+            assert st["sorted_input"] == 0
+        else:
+            st = ingest_both(eng, orc, s, d, t)
+            assert st["sorted_input"] == 1
+        assert_state_equal(eng.state(), orc.state(), "batch %d" % k)
+        cut = orc.counts()["cutoff"]
+    check_walks(eng, orc, 20_000, 12, seed=4, biases=(0,), scheds=(_lib.SCHED_LANE,))
+
+
 @pytest.mark.parametrize("share", [62, 0, 100, 37])
 def test_host_and_device_outputs_agree(share):
     """Walks into host buffers (part padded on the device and copied whole,
