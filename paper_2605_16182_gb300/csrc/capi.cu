@@ -221,7 +221,8 @@ static void free_all(tempest_t *h)
                     &h->big_node,  &h->big_t,     &h->big_c,     &h->tune_out,  &h->dense,     &h->touched,   &h->tg2,       &h->nbeg,
                     &h->pn_nodes,  &h->gw,        &h->gs,        &h->wref,      &h->w_cbase,   &h->w_ctot,
                     &h->w_coff,    &h->co_prev,   &h->pt,        &h->big_own,   &h->big_aux0,
-                    &h->big_aux1,  &h->big_bf,    &h->bkt_prev,  &h->nev,       &h->cmp_stage, &h->cmp_off};
+                    &h->big_aux1,  &h->big_bf,    &h->bkt_prev,  &h->nev,       &h->cmp_stage, &h->cmp_off,
+                    &h->ent_tmp,   &h->nv_flags,  &h->b_gflag,   &h->nv_tex};
     for (DBuf *b : bufs) release(h, *b);
 }
 

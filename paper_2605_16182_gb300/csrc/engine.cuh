@@ -172,6 +172,7 @@ struct tempest {
     tw::DBuf touched;  // int32: node of each batch-local id
     tw::DBuf ent_tmp;  // Entry: a batch's node view entries in (node, ts, arrival) order
     tw::DBuf nv_flags; // uint8 per batch entry: run start (bit 0), group start (bit 1)
+    tw::DBuf nv_tex;   // uint64 per BSCAN_TILE batch entries: runs (high) and groups (low) before the tile
     int64_t S = 0;     // nodes that own regions (for the bucket index)
     int64_t state_ver = 0;  // bumped by every ingest
     // an ingest that failed after changing the store restored the store's

@@ -472,18 +472,18 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 //                        unsorted and its timestamps are read instead)
 //   4 e + 104 u          eviction: endpoint ids read; per node its counter
 //                        (8) and its records (16 + 32) read and written
-//   8 E + 16 U           batch-local ids (ids read, keys written, id table)
+//   4 E + 16 U           batch-local ids (ids read, id table)
 //   20 P E               node sort passes (key read for the histogram, key
 //                        and value read and written by the scatter)
 //   41 E                 entries packed in sorted order (index and key
 //                        read, the store item's far end and time gathered,
 //                        16-byte entry and a run/group-start byte written)
-//   10 E + 148 R         runs (both scan passes read the start bytes, run
-//                        index written; per run its arrays, node record and
-//                        the region reservation)
+//   2 E + 148 R          runs (both scan passes read the start bytes; per
+//                        run its arrays, node record and the region
+//                        reservation)
 //   32 E_moved + 24 G_moved   region moves (entries, group starts and times)
-//   40 E + 12 G_added    scatter (run and group ids and the packed entry
-//                        read, the entry and new groups written)
+//   33 E + 12 G_added    scatter (the start byte and the packed entry read,
+//                        the entry and new groups written)
 // A full rebuild of the node view (after a merge or a pool exhaustion)
 // counts its whole sort and scatter over the live entries instead.
 static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, int64_t kept_old, int64_t m_new,
@@ -498,12 +498,12 @@ static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, 
         x += M * (8 + 20 * r.rb_passes + 32 + 32 + 32) + 12 * r.rb_groups + 104 * r.rb_nodes;
     } else {
         x += 4 * r.ev_entries + 104 * r.ev_nodes;
-        x += 8 * r.entries + 16 * r.ids;
+        x += 4 * r.entries + 16 * r.ids;
         x += 20 * r.passes * r.entries;
         x += 41 * r.entries;
-        x += 10 * r.entries + 148 * r.runs;
+        x += 2 * r.entries + 148 * r.runs;
         x += 32 * r.moved_e + 24 * r.moved_g;
-        x += 40 * r.entries + 12 * r.g_added;
+        x += 33 * r.entries + 12 * r.g_added;
     }
     return x;
 }

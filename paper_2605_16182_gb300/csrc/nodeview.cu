@@ -170,7 +170,7 @@ __global__ void k_nv_tail(int32_t *run_pos, int32_t *run_g, int32_t *fx, const u
     const int64_t R = (int64_t)(t >> 32);
     run_pos[R] = (int32_t)n;
     run_g[R] = (int32_t)(uint32_t)t;
-    fx[n] = (int32_t)(uint32_t)t;
+    if (fx) fx[n] = (int32_t)(uint32_t)t;
 }
 
 __global__ void k_nv_build_nodes(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
@@ -420,19 +420,20 @@ struct DenseLoader {
 // Node runs and new groups of the batch's entries in (node, ts, arrival)
 // order (kb: batch-local node ids; the run and group starts come as one byte
 // per entry from k_nv_entries_runs, groups as of after the eviction: bit 0 a
-// run start, bit 1 a group start).  A byte scan: each thread reads 16 flags
-// with one load and writes its 16 run_of and fx values as four 16-byte
-// stores each (flags, run_of and fx 16-byte aligned).  Gathering each
+// run start, bit 1 a group start).  A byte scan (each thread reads 16 flags
+// with one load) that writes the run records and each tile's prefix; the
+// scatter and the weight update derive every entry's run and group from the
+// same bytes (RunTile), so no per-entry array is written.  Gathering each
 // timestamp through the sort's index had cost four scattered loads per
-// entry, reading the packed 16-byte entries 160 MB per pass for a 10M-edge
-// batch, and one byte per element through the generic scan 44 instructions
-// per element.
+// entry, and the generic scan over one byte per element 44 instructions per
+// element.
 struct AppendRunBytes {
-    const uint8_t *flags;
+    const uint8_t *flags;  // 16-byte aligned
     int64_t n;
     const uint32_t *kb;
     const int32_t *touched;
-    int32_t *run_of, *fx, *run_node, *run_pos, *run_g;
+    int32_t *run_node, *run_pos, *run_g;
+    uint64_t *tile_prefix;  // per tile: runs (high) and groups (low) before it
     struct Stage {};
     __host__ __device__ int64_t tiles() const { return n > 0 ? (n + BSCAN_TILE - 1) / BSCAN_TILE : 0; }
     __device__ __forceinline__ uint4 load(int64_t u0) const
@@ -444,40 +445,24 @@ struct AppendRunBytes {
         const uint32_t v = valid16(u0, 0, n);
         return ((uint64_t)__popc(byte_bits16(w, 0) & v) << 32) | (uint64_t)__popc(byte_bits16(w, 1) & v);
     }
-    __device__ __forceinline__ void emit16(uint4 w, int64_t u0, uint64_t ex, uint64_t, uint64_t, Stage &) const
+    __device__ __forceinline__ void emit16(uint4 w, int64_t u0, uint64_t ex, uint64_t tile_ex, uint64_t,
+                                           Stage &) const
     {
+        if (threadIdx.x == 0) tile_prefix[u0 / BSCAN_TILE] = tile_ex;
         const uint32_t v = valid16(u0, 0, n);
-        const uint32_t rm = byte_bits16(w, 0) & v, gm = byte_bits16(w, 1) & v;
-        uint32_t R = (uint32_t)(ex >> 32), G = (uint32_t)ex;
-        int32_t ro[16], fo[16];
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-            const uint32_t rs = (rm >> k) & 1u;
-            R += rs;
-            ro[k] = (int32_t)(R - 1u);
-            fo[k] = (int32_t)G;
-            if (rs) {  // a node run starts here
-                const int64_t p = u0 + k;
-                run_node[R - 1u] = touched[kb[p]];
-                run_pos[R - 1u] = (int32_t)p;
-                run_g[R - 1u] = (int32_t)G;
-            }
-            G += (gm >> k) & 1u;
-        }
-        if (u0 + 16 <= n) {
-            int4 *o = reinterpret_cast<int4 *>(run_of + u0), *f = reinterpret_cast<int4 *>(fx + u0);
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                o[q] = make_int4(ro[4 * q], ro[4 * q + 1], ro[4 * q + 2], ro[4 * q + 3]);
-                f[q] = make_int4(fo[4 * q], fo[4 * q + 1], fo[4 * q + 2], fo[4 * q + 3]);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 16; k++)
-                if (u0 + k < n) {
-                    run_of[u0 + k] = ro[k];
-                    fx[u0 + k] = fo[k];
-                }
+        uint32_t rm = byte_bits16(w, 0) & v;
+        if (!rm) return;
+        const uint32_t gm = byte_bits16(w, 1) & v;
+        uint32_t R = (uint32_t)(ex >> 32);
+        const uint32_t G = (uint32_t)ex;
+        while (rm) {  // a node run starts at each set bit
+            const int k = __ffs(rm) - 1;
+            rm &= rm - 1;
+            const int64_t p = u0 + k;
+            run_node[R] = touched[kb[p]];
+            run_pos[R] = (int32_t)p;
+            run_g[R] = (int32_t)(G + (uint32_t)__popc(gm & ((1u << k) - 1u)));
+            R++;
         }
     }
 };
@@ -608,66 +593,71 @@ __global__ void k_nv_reloc(const Reloc *__restrict__ reloc, const int32_t *__res
     }
 }
 
-__global__ void __launch_bounds__(256, 4)
-    k_nv_scatter(const Entry *__restrict__ E, int64_t nbe, const int32_t *__restrict__ run_of,
-                 const int32_t *__restrict__ fx, const int32_t *__restrict__ run_pos, const int32_t *__restrict__ run_g,
-                 const int32_t *__restrict__ run_de, const int32_t *__restrict__ run_dg,
-                 const int32_t *__restrict__ run_node, int64_t e_cap, int64_t g_cap, Entry *ent, int32_t *ngo,
-                 int64_t *ngts, NodeRange *ngr, NvCounters *c)
+// Four blocks per tile of BSCAN_TILE entries, each writing a quarter (four
+// entries per thread, loaded before the tile's flags are scanned): each
+// entry's run and group come from the flag bytes (RunTile).  Short blocks
+// keep the last wave small (one block per tile left a fifth wave of a few
+// blocks at 10M entries).
+constexpr int SCATTER_SPLIT = 4;
+
+__global__ void __launch_bounds__(BSCAN_THREADS)
+    k_nv_scatter(const Entry *__restrict__ E, const uint8_t *__restrict__ flags, int64_t nbe,
+                 const uint64_t *__restrict__ tile_prefix, const int32_t *__restrict__ run_pos,
+                 const int32_t *__restrict__ run_g, const int32_t *__restrict__ run_de,
+                 const int32_t *__restrict__ run_dg, const int32_t *__restrict__ run_node, int64_t e_cap,
+                 int64_t g_cap, Entry *ent, int32_t *ngo, int64_t *ngts, NodeRange *ngr, NvCounters *c)
 {
     if (c->overflow) return;  // a pool could not serve a region: the batch rebuilds the view instead
-    constexpr int U = 4;      // entries per thread whose loads are in flight together
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < nbe; p0 += stride * U) {
-        int32_t rr[U], f0[U], f1[U];
-        Entry xs[U];
+    constexpr int U = 16 / SCATTER_SPLIT;
+    __shared__ RunTile sm;
+    const int64_t t = blockIdx.x / SCATTER_SPLIT, p0 = t * BSCAN_TILE;
+    const int k0 = (int)(blockIdx.x % SCATTER_SPLIT) * U;
+    Entry xs[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int64_t p = p0 + u * stride;
-            if (p < nbe) {
-                rr[u] = run_of[p];
-                f0[u] = fx[p];
-                f1[u] = fx[p + 1];
-                xs[u] = E[p];
-            }
+    for (int u = 0; u < U; u++) {
+        const int64_t p = p0 + (k0 + u) * BSCAN_THREADS + threadIdx.x;
+        if (p < nbe) xs[u] = E[p];
+    }
+    run_tile_load(sm, flags, nbe, t, tile_prefix[t]);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int j = (k0 + u) * BSCAN_THREADS + threadIdx.x;
+        const int64_t p = p0 + j;
+        if (p >= nbe) break;
+        const RunAt a = run_tile_at(sm, j);
+        const int32_t r = a.r;
+        const int32_t de = run_de[r];
+        const int32_t i = (int32_t)p - run_pos[r];
+        const int64_t e = (int64_t)de + i;
+        if (de < 0 || e >= e_cap) {
+            atomicOr(&c->status, 1ull << 3);
+            continue;
         }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int64_t p = p0 + u * stride;
-            if (p >= nbe) break;
-            const int32_t r = rr[u];
-            const int32_t de = run_de[r];
-            const int32_t i = (int32_t)p - run_pos[r];
-            const int64_t e = (int64_t)de + i;
-            if (de < 0 || e >= e_cap) {
-                atomicOr(&c->status, 1ull << 3);
+        const Entry x = xs[u];
+        ent[e] = x;
+        // the node record's first / last group timestamps
+        const bool last = p + 1 == run_pos[r + 1];
+        if (a.rs) {
+            const int32_t v = run_node[r];
+            if (ngr[v].g_lo == run_dg[r]) ngr[v].t_first = x.ts;  // no live group before the batch
+        }
+        if (last) ngr[run_node[r]].t_last = x.ts;
+        if (a.gs) {
+            const int64_t g = (int64_t)run_dg[r] + (a.g - run_g[r]);
+            if (g < 0 || g >= g_cap) {
+                atomicOr(&c->status, 1ull << 4);
                 continue;
             }
-            const Entry x = xs[u];
-            ent[e] = x;
-            // the node record's first / last group timestamps
-            if (p == run_pos[r]) {
-                const int32_t v = run_node[r];
-                if (ngr[v].g_lo == run_dg[r]) ngr[v].t_first = x.ts;  // no live group before the batch
+            ngts[g] = x.ts;
+            ngo[g] = (int32_t)e;
+        }
+        if (last) {  // the node's new end after its last group
+            const int64_t gs = (int64_t)run_dg[r] + (run_g[r + 1] - run_g[r]);
+            if (gs < 0 || gs >= g_cap) {
+                atomicOr(&c->status, 1ull << 5);
+                continue;
             }
-            if (p + 1 == run_pos[r + 1]) ngr[run_node[r]].t_last = x.ts;
-            if (f1[u] != f0[u]) {
-                const int64_t g = (int64_t)run_dg[r] + (f0[u] - run_g[r]);
-                if (g < 0 || g >= g_cap) {
-                    atomicOr(&c->status, 1ull << 4);
-                    continue;
-                }
-                ngts[g] = x.ts;
-                ngo[g] = (int32_t)e;
-            }
-            if (p + 1 == run_pos[r + 1]) {  // the node's new end after its last group
-                const int64_t gs = (int64_t)run_dg[r] + (run_g[r + 1] - run_g[r]);
-                if (gs < 0 || gs >= g_cap) {
-                    atomicOr(&c->status, 1ull << 5);
-                    continue;
-                }
-                ngo[gs] = (int32_t)(e + 1);
-            }
+            ngo[gs] = (int32_t)(e + 1);
         }
     }
 }
@@ -918,6 +908,8 @@ int nv_prepare_append(tempest_t *h, int64_t n_ev, int64_t nbk, int64_t N_old, in
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->ent_tmp, sizeof(Entry) * (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->nv_flags, (size_t)nbe, true))) return rc;
+        if ((rc = ensure(h, h->nv_tex, sizeof(uint64_t) * (size_t)((nbe + BSCAN_TILE - 1) / BSCAN_TILE), true)))
+            return rc;
     }
     return TEMPEST_OK;
 }
@@ -974,6 +966,8 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         if ((rc = ensure(h, h->touched, sizeof(int32_t) * (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->ent_tmp, sizeof(Entry) * (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->nv_flags, (size_t)nbe, true))) return rc;
+        if ((rc = ensure(h, h->nv_tex, sizeof(uint64_t) * (size_t)((nbe + BSCAN_TILE - 1) / BSCAN_TILE), true)))
+            return rc;
         cudaMemsetAsync(h->touched.p, 0xff, sizeof(int32_t) * (size_t)nbe, st);
         k_nv_claim<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), h->touched.as<int32_t>(), dc);
         NvCounters *hd = static_cast<NvCounters *>(h->hstat);
@@ -1007,14 +1001,13 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         k_nv_entries_runs<<<grid_for(h, nbe), 256, 0, st>>>(vb[r], kb[r], it, nbe, slot_base(h, new_lo),
                                                             h->touched.as<int32_t>(), h->ngr.as<NodeRange>(), E,
                                                             rflags);
-        AppendRunBytes op{rflags, nbe, kb[r], h->touched.as<int32_t>(), h->run_of.as<int32_t>(),
-                          h->fx.as<int32_t>(), h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
-                          h->run_g.as<int32_t>()};
+        AppendRunBytes op{rflags, nbe, kb[r], h->touched.as<int32_t>(), h->run_node.as<int32_t>(),
+                          h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), h->nv_tex.as<uint64_t>()};
         const int nb = bscan_launch(op, part, st);
         // keep the run totals apart: the next scans reuse the partials
         uint64_t *tot = part + SCAN_MAX_BLOCKS + 1;
         cudaMemcpyAsync(tot, part + nb, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
-        k_nv_tail<<<1, 1, 0, st>>>(h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), h->fx.as<int32_t>(), tot, nbe);
+        k_nv_tail<<<1, 1, 0, st>>>(h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), nullptr, tot, nbe);
         k_nv_reserve<<<grid_for(h, runs_max), 256, 0, st>>>(
             h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), tot, h->nv_shift, h->e_cap,
             h->g_cap, h->nrec.as<int4>(), h->ngr.as<NodeRange>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
@@ -1038,12 +1031,10 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
                                                        h->w_on && h->w_valid && h->gw.p ? h->gw.as<double>() : nullptr);
             h->pending_launches += 4;
         }
-        k_nv_scatter<<<grid_for(h, nbe), 256, 0, st>>>(E, nbe, h->run_of.as<int32_t>(),
-                                                       h->fx.as<int32_t>(), h->run_pos.as<int32_t>(),
-                                                       h->run_g.as<int32_t>(), h->run_de.as<int32_t>(),
-                                                       h->run_dg.as<int32_t>(), h->run_node.as<int32_t>(), h->e_cap,
-                                                       h->g_cap, h->ent.as<Entry>(), h->ngo.as<int32_t>(),
-                                                       h->ngts.as<int64_t>(), h->ngr.as<NodeRange>(), dc);
+        k_nv_scatter<<<(unsigned)(op.tiles() * SCATTER_SPLIT), BSCAN_THREADS, 0, st>>>(
+            E, rflags, nbe, h->nv_tex.as<uint64_t>(), h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(),
+            h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(), h->run_node.as<int32_t>(), h->e_cap, h->g_cap,
+            h->ent.as<Entry>(), h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->ngr.as<NodeRange>(), dc);
         h->pending_launches++;
         if ((rc = nv_append_weights(h, nbe))) return rc;
     }

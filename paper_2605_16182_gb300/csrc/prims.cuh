@@ -498,6 +498,54 @@ int bscan_launch(const Op &op, uint64_t *partials, cudaStream_t st)
     return (int)nb;
 }
 
+// Runs of a batch's sorted entries, one block per tile of BSCAN_TILE
+// entries.  From the entries' flag bytes (bit 0: a run starts, bit 1: a group
+// starts) and the tile's prefix (runs and groups before the tile, high and
+// low 32 bits), every entry's run and the batch's groups before it, for
+// loops over the tile's entries in any order.  Replaces two int32 arrays per
+// entry written by the run scan and read back by its consumers.
+struct RunTile {
+    uint32_t rm[BSCAN_THREADS], gm[BSCAN_THREADS];  // each thread's 16 entries: run / group start masks
+    uint64_t ex[BSCAN_THREADS];                     // prefix before each thread's first entry
+    uint64_t wt[33];
+};
+
+struct RunAt {
+    int32_t r;  // the entry's run
+    int32_t g;  // groups of the batch before it
+    bool rs, gs;  // it starts a run / a group
+};
+
+// Every thread of the block calls it (it synchronises).
+__device__ __forceinline__ void run_tile_load(RunTile &sm, const uint8_t *__restrict__ flags, int64_t n, int64_t t,
+                                              uint64_t tile_prefix)
+{
+    const int64_t u0 = t * BSCAN_TILE + 16 * threadIdx.x;
+    const uint4 w = u0 < n ? __ldg(reinterpret_cast<const uint4 *>(flags + u0)) : make_uint4(0, 0, 0, 0);
+    const uint32_t v = valid16(u0, 0, n);
+    const uint32_t rm = byte_bits16(w, 0) & v, gm = byte_bits16(w, 1) & v;
+    uint64_t tot;
+    const uint64_t ex = block_excl_scan<uint64_t>(((uint64_t)__popc(rm) << 32) | (uint64_t)__popc(gm), sm.wt, tot);
+    sm.rm[threadIdx.x] = rm;
+    sm.gm[threadIdx.x] = gm;
+    sm.ex[threadIdx.x] = tile_prefix + ex;
+    __syncthreads();
+}
+
+// Entry j of the tile (0 <= j < BSCAN_TILE).
+__device__ __forceinline__ RunAt run_tile_at(const RunTile &sm, int j)
+{
+    const int o = j >> 4, q = j & 15;
+    const uint32_t below = (1u << q) - 1u, rm = sm.rm[o], gm = sm.gm[o];
+    const uint64_t ex = sm.ex[o];
+    RunAt a;
+    a.rs = (rm >> q) & 1u;
+    a.gs = (gm >> q) & 1u;
+    a.r = (int32_t)((uint32_t)(ex >> 32) + (uint32_t)__popc(rm & below) + (a.rs ? 0u : 0xffffffffu));
+    a.g = (int32_t)((uint32_t)ex + (uint32_t)__popc(gm & below));
+    return a;
+}
+
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort of (key, value) pairs, 8-bit digits.
 // A Loader supplies the input of the first pass:

@@ -89,25 +89,32 @@ __global__ void __launch_bounds__(256) k_w_all(const int32_t *__restrict__ act, 
 // Groups the batch created (a flagged entry starts one) or grew (a run whose
 // first entry joined the node's last group): their weights.  A node without
 // live groups before the batch takes its first new group's time as
-// reference.  Runs after the scatter of the batch (ngo holds the new ends).
-__global__ void k_w_append(int64_t nbe, const int32_t *__restrict__ run_of, const int32_t *__restrict__ fx,
-                           const int32_t *__restrict__ run_pos, const int32_t *__restrict__ run_g,
-                           const int32_t *__restrict__ run_dg, const int32_t *__restrict__ run_node,
-                           const NodeRange *__restrict__ ngr, const int32_t *__restrict__ ngo,
-                           const int64_t *__restrict__ ngts, double lam, int64_t *wref, double *gw, NvCounters *cnt)
+// reference.  Runs after the scatter of the batch (ngo holds the new ends);
+// one block per tile of the batch's entries, whose runs and groups come from
+// the flag bytes (RunTile).
+__global__ void __launch_bounds__(BSCAN_THREADS)
+    k_w_append(const uint8_t *__restrict__ flags, int64_t nbe, const uint64_t *__restrict__ tile_prefix,
+               const int32_t *__restrict__ run_g, const int32_t *__restrict__ run_dg,
+               const int32_t *__restrict__ run_node, const NodeRange *__restrict__ ngr, const int32_t *__restrict__ ngo,
+               const int64_t *__restrict__ ngts, double lam, int64_t *wref, double *gw, NvCounters *cnt)
 {
     if (cnt->overflow) return;  // the batch rebuilds the view (and the weights) instead
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nbe; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = run_of[p];
-        const bool opens = fx[p + 1] != fx[p];
-        const bool first = p == run_pos[r];
+    __shared__ RunTile sm;
+    const int64_t t = blockIdx.x, p0 = t * BSCAN_TILE;
+    run_tile_load(sm, flags, nbe, t, tile_prefix[t]);
+    for (int k = 0; k < 16; k++) {
+        const int j = k * BSCAN_THREADS + threadIdx.x;
+        if (p0 + j >= nbe) break;
+        const RunAt a = run_tile_at(sm, j);
+        const bool opens = a.gs, first = a.rs;
         if (!opens && !first) continue;
+        const int32_t r = a.r;
         const int32_t v = run_node[r];
         const int32_t dg = run_dg[r];
         const bool was_empty = ngr[v].g_lo == dg;
         const int64_t ref = was_empty ? ngts[dg] : wref[v];
         if (first && was_empty) wref[v] = ref;
-        const int32_t g = opens ? dg + (fx[p] - run_g[r]) : dg - 1;  // else: the grown last group
+        const int32_t g = opens ? dg + (a.g - run_g[r]) : dg - 1;  // else: the grown last group
         const double e = lam * (double)(ngts[g] - ref);
         if (e > W_REBASE) atomicOr(&cnt->w_rebase, 1ull);
         gw[g] = (double)(ngo[g + 1] - ngo[g]) * exp(e);
@@ -246,11 +253,12 @@ int nv_append_weights(tempest_t *h, int64_t nbe)
         return TEMPEST_OK;
     }
     cudaStream_t st = h->stream;
-    const unsigned grid = (unsigned)std::min<int64_t>((nbe + 255) / 256, (int64_t)h->num_sms * 16);
-    k_w_append<<<grid, 256, 0, st>>>(nbe, h->run_of.as<int32_t>(), h->fx.as<int32_t>(), h->run_pos.as<int32_t>(),
-                               h->run_g.as<int32_t>(), h->run_dg.as<int32_t>(), h->run_node.as<int32_t>(),
-                               h->ngr.as<NodeRange>(), h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->lam_w,
-                               h->wref.as<int64_t>(), h->gw.as<double>(), h->nvc.as<NvCounters>());
+    const unsigned grid = (unsigned)((nbe + BSCAN_TILE - 1) / BSCAN_TILE);
+    k_w_append<<<grid, BSCAN_THREADS, 0, st>>>(h->nv_flags.as<uint8_t>(), nbe, h->nv_tex.as<uint64_t>(),
+                                               h->run_g.as<int32_t>(), h->run_dg.as<int32_t>(),
+                                               h->run_node.as<int32_t>(), h->ngr.as<NodeRange>(),
+                                               h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->lam_w,
+                                               h->wref.as<int64_t>(), h->gw.as<double>(), h->nvc.as<NvCounters>());
     h->pending_launches++;
     return cuda_check(h, cudaGetLastError(), "append weights");
 }

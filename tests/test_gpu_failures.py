@@ -7,6 +7,7 @@ state stays the oracle's state before the batch, the batch can be ingested
 again once memory is back, and the stream then ends in the oracle's state
 with the oracle's walks.  A failed walk call changes no state either.
 """
+import numpy as np
 import pytest
 import torch
 
@@ -288,3 +289,27 @@ def test_failed_ingest_keeps_the_node2vec_pair_table():
     agree, total, _ = compare_biased(g, o, o[3])
     assert total > 0 and agree / total >= MIN_HOP_AGREEMENT
     eng.close()
+
+
+def test_destroy_returns_every_allocation():
+    """After a stream with appends, evictions, rebuilds, walks in every form
+    and the weight and in-edge indexes, destroying the handle hands every
+    buffer it took from the allocator back to it."""
+    spec, batches = stream_batches()
+    eng, fa = engine(spec.window, True, backward=True)
+    eng.set_weight_rate(1e-3)
+    for b in batches:
+        ingest(eng, b)
+    for sched in (_lib.SCHED_LANE, _lib.SCHED_STREAM, _lib.SCHED_GRAPH, _lib.SCHED_COOP, _lib.SCHED_FULL_WALK):
+        eng.set_scheduler(sched)
+        eng.walks(2000, 8, bias=_lib.BIAS_EXP, seed=1)
+    eng.walks(2000, 8, bias=_lib.BIAS_EXP_WEIGHT, seed=2)
+    eng.walks(2000, 8, bias=_lib.BIAS_UNIFORM, seed=3, direction=1)
+    # walks into host buffers (device staging for the rows and the cells)
+    node, ts, ln = np.zeros((2000, 8), np.int32), np.zeros((2000, 8), np.int64), np.zeros(2000, np.int32)
+    _lib.tempest_walks(eng.h, 2000, 8, 1, 0, 4, node.ctypes.data, ts.ctypes.data, ln.ctypes.data)
+    torch.cuda.synchronize()
+    assert fa.live
+    eng.close()
+    assert not fa.live, "%d buffers (%d bytes) still held after destroy" % (len(fa.live), sum(fa.live.values()))
+
