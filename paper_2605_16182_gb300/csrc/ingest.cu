@@ -474,7 +474,9 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 //                        (8) and its records (16 + 32) read and written
 //   4 E + 16 U           batch-local ids (ids read, id table)
 //   20 P E               node sort passes (key read for the histogram, key
-//                        and value read and written by the scatter)
+//                        and value read and written by the scatter; the
+//                        first pass's histogram writes the keys its scatter
+//                        reads, and its values are the indices, read by none)
 //   41 E                 entries packed in sorted order (index and key
 //                        read, the store item's far end and time gathered,
 //                        16-byte entry and a run/group-start byte written)

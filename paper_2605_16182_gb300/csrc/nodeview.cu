@@ -254,20 +254,30 @@ __global__ void __launch_bounds__(256) k_nv_evict_count(Items it, int64_t items,
     // the counter once at the end
     int32_t hot = -1, hot_cnt = 0;
     constexpr int U = 4;  // items per thread whose ids are loaded together
+    // the next U items' ids are in flight while the current ones are counted
+    auto load = [&](int64_t base, int32_t *vu) {
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t i = base + u * blockDim.x + threadIdx.x;
+            vu[u] = i < b1 ? (int32_t)it.key(i) : 0;
+        }
+    };
+    int32_t vn[U];
+    load(b0, vn);
     for (int64_t base = b0; base < b1; base += (int64_t)U * blockDim.x) {
         int32_t vu[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            const int64_t i = base + u * blockDim.x + threadIdx.x;
             vu[u] = -1;
-            if (i < b1) {
-                vu[u] = (int32_t)it.key(i);
+            if (base + u * blockDim.x + threadIdx.x < b1) {
+                vu[u] = vn[u];
                 if (vu[u] < 0 || vu[u] >= N) {
                     atomicOr(&c->status, 1ull << 0);
                     vu[u] = -1;
                 }
             }
         }
+        load(base + (int64_t)U * blockDim.x, vn);
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int32_t v = vu[u];
@@ -408,12 +418,21 @@ __global__ void k_nv_dense_reset(const int32_t *__restrict__ touched, const NvCo
     }
 }
 
-// The first sort pass reads each entry's batch-local id from the id table
-// (dense[v] - 1; the batch's few thousand nodes keep their words in cache).
+// The first sort pass's histogram reads each entry's batch-local id from the
+// id table (dense[v] - 1; the batch's few thousand nodes keep their words in
+// cache) and keeps it in ids[]; the first scatter pass reads ids[] (the
+// table lookups had doubled that pass's time).
 struct DenseLoader {
     Items it;
     const int32_t *dense;
+    uint32_t *ids;
     __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)(__ldg(dense + (int32_t)it.key(i)) - 1); }
+    __device__ __forceinline__ void note(int64_t i, uint32_t k) const { ids[i] = k; }
+};
+
+struct NotedIdLoader {
+    const uint32_t *ids;
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return ids[i]; }
     __device__ __forceinline__ uint32_t val(int64_t i) const { return (uint32_t)i; }
 };
 
@@ -944,8 +963,8 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         for (cudaEvent_t &e : h->eev)
             if (!e) cudaEventCreate(&e);
         cudaEventRecord(h->eev[0], st);
-        // contiguous shares of at least 2048 items per block, at most 4 blocks per SM
-        const int64_t eg = std::max<int64_t>(1, std::min<int64_t>((ne + 2047) / 2048, 4 * (int64_t)h->num_sms));
+        // contiguous shares of at least 2048 items per block, at most 8 blocks per SM
+        const int64_t eg = std::max<int64_t>(1, std::min<int64_t>((ne + 2047) / 2048, 8 * (int64_t)h->num_sms));
         k_nv_evict_count<<<(unsigned)eg, 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
                                                        h->ev_nodes.as<int32_t>(), dc);
         k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
@@ -977,11 +996,14 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         uint32_t *kb[2] = {h->sk32[0].as<uint32_t>(), h->sk32[1].as<uint32_t>()};
         uint32_t *vb[2] = {h->sv[0].as<uint32_t>(), h->sv[1].as<uint32_t>()};
         int launches = 0;
-        const DenseLoader dl{it, h->dense.as<int32_t>()};
+        // the ids the first histogram pass notes go to the second key buffer,
+        // which the first scatter pass reads and the second one overwrites
+        const DenseLoader dl{it, h->dense.as<int32_t>(), kb[1]};
+        const NotedIdLoader nl{kb[1]};
         rep.ids = n_ids;
         rep.runs = n_ids;  // one run per distinct node of the batch
         rep.passes = (bits_for((uint64_t)(n_ids > 0 ? n_ids - 1 : 0)) + RADIX_BITS - 1) / RADIX_BITS;
-        int r = radix_sort_launch<uint32_t>(dl, nbe, bits_for((uint64_t)(n_ids > 0 ? n_ids - 1 : 0)), kb, vb,
+        int r = radix_sort_launch<uint32_t>(dl, nl, nbe, bits_for((uint64_t)(n_ids > 0 ? n_ids - 1 : 0)), kb, vb,
                                             h->hist.as<uint32_t>(), st, &launches);
         if (r < 0) {  // a single distinct node (id 0): the batch order is already grouped
             cudaMemsetAsync(kb[0], 0, sizeof(uint32_t) * (size_t)nbe, st);

@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace tw {
 
 // ---------------------------------------------------------------------------
@@ -563,6 +566,15 @@ constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int SORT_MAX_BLOCKS = 4096;  // one 2048-key tile per block up to 8M keys (part[] holds <= 256 chunks)
 
+// A loader whose key is computed (not read) may keep it: the histogram pass
+// calls note(i, key) for each element, and the first scatter pass can then
+// read the kept keys (radix_sort_launch's second loader).
+template <class L, class = void>
+struct loader_notes : std::false_type {};
+template <class L>
+struct loader_notes<L, std::void_t<decltype(std::declval<const L &>().note(int64_t(0), uint32_t(0)))>>
+    : std::true_type {};
+
 template <typename K>
 struct ArrayLoader {
     const K *k;
@@ -587,7 +599,12 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(L ld, int64_t n, in
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int64_t i = base + u * blockDim.x + threadIdx.x;
-            d[u] = i < b1 ? (uint32_t)((ld.key(i) >> shift) & (RADIX - 1)) : 0xffffu;
+            d[u] = 0xffffu;
+            if (i < b1) {
+                const K k = ld.key(i);
+                if constexpr (loader_notes<L>::value) ld.note(i, (uint32_t)k);
+                d[u] = (uint32_t)((k >> shift) & (RADIX - 1));
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -750,8 +767,21 @@ __global__ void __launch_bounds__(SORT_THREADS, sizeof(K) == 4 ? 5 : 3) k_radix_
 // input already has all keys equal in those bits; the caller then uses the
 // loader's data as is).  hist needs RADIX * nblocks + 1 + 2 * 128 u32 (at most
 // SORT_HIST_WORDS).
+template <typename K, class L, class L0>
+int radix_sort_launch(const L &ld, const L0 &ld0, int64_t n, int bits, K *k[2], uint32_t *v[2], uint32_t *hist,
+                      cudaStream_t st, int *launches);
+
 template <typename K, class L>
 int radix_sort_launch(const L &ld, int64_t n, int bits, K *k[2], uint32_t *v[2], uint32_t *hist,
+                      cudaStream_t st, int *launches)
+{
+    return radix_sort_launch<K, L, L>(ld, ld, n, bits, k, v, hist, st, launches);
+}
+
+// The same with the first scatter pass reading its input through ld0 (the
+// keys the first histogram pass noted, for instance).
+template <typename K, class L, class L0>
+int radix_sort_launch(const L &ld, const L0 &ld0, int64_t n, int bits, K *k[2], uint32_t *v[2], uint32_t *hist,
                       cudaStream_t st, int *launches)
 {
     if (n <= 0 || bits <= 0) return -1;
@@ -772,8 +802,8 @@ int radix_sort_launch(const L &ld, int64_t n, int bits, K *k[2], uint32_t *v[2],
             k_radix_hist<K, L><<<(unsigned)nb, SORT_THREADS, 0, st>>>(ld, n, per, shift, hist, (int)nb);
             k_hscan_local<<<hchunks, 1024, 0, st>>>(hist, hn, part);
             k_hscan_part<<<1, 1024, 0, st>>>(part, hchunks);
-            k_radix_scatter<K, L><<<(unsigned)nb, SORT_THREADS, 0, st>>>(ld, k[out], v[out], n, per, shift,
-                                                                          hist, part, (int)nb);
+            k_radix_scatter<K, L0><<<(unsigned)nb, SORT_THREADS, 0, st>>>(ld0, k[out], v[out], n, per, shift,
+                                                                           hist, part, (int)nb);
         } else {
             ArrayLoader<K> al{k[cur], v[cur]};
             k_radix_hist<K, ArrayLoader<K>><<<(unsigned)nb, SORT_THREADS, 0, st>>>(al, n, per, shift, hist,
