@@ -39,7 +39,11 @@ namespace tw {
 // four loads of each array in flight (grid-stride, unrolled); each warp and
 // then each block reduce in registers and shared memory, so the global
 // atomics are one set per block (per-warp atomics on the same six words
-// serialised at L2).
+// serialised at L2).  With os / od / ot set (the store's free tail, when it
+// has room for the whole batch) it also writes the batch there: a batch that
+// proves sorted, on time and wholly kept is then appended without a second
+// read (the store copies were 320 MB of traffic per 10M edges); otherwise
+// the append overwrites that free space.
 constexpr int STATS_THREADS = 256;
 constexpr int STATS_UNROLL = 4;
 
@@ -47,6 +51,7 @@ __global__ void __launch_bounds__(STATS_THREADS) k_batch_stats(const int32_t *__
                                                                const int32_t *__restrict__ dst,
                                                                const int64_t *__restrict__ ts, int64_t n,
                                                                int has_cut, long long cut, uint8_t *gflag,
+                                                               int32_t *os, int32_t *od, int64_t *ot,
                                                                IngestScratch *o)
 {
     long long tmin = LLONG_MAX, tmax = LLONG_MIN;
@@ -77,6 +82,11 @@ __global__ void __launch_bounds__(STATS_THREADS) k_batch_stats(const int32_t *__
             // a timestamp group starts here (against the batch's previous
             // edge; the first kept edge is compared with the store later)
             gflag[i0 + r * stride] = tp[r] != t[r] ? 1 : 0;
+            if (os) {  // the store's tail, in case the batch is appended as it is
+                os[i0 + r * stride] = a[r];
+                od[i0 + r * stride] = b[r];
+                ot[i0 + r * stride] = t[r];
+            }
         }
     }
 #pragma unroll
@@ -465,8 +475,10 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 //                        byte written per edge)
 //   P_ts (24 b) + 32 b   timestamp sort of an unsorted batch (8-byte key and
 //                        4-byte index read and written per pass), gather
-//   32 k                 store append (kept batch read, store written); a
-//                        merge instead reads both sides and writes the store
+//   32 k                 store append (kept batch read, store written; 16 k
+//                        when the batch statistics wrote the store as they
+//                        read the batch); a merge instead reads both sides
+//                        and writes the store
 //   2 k + 4 G_new        timestamp view (both scan passes read the kept
 //                        edges' group-start bytes; 16 k when the batch came
 //                        unsorted and its timestamps are read instead)
@@ -489,11 +501,12 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 // A full rebuild of the node view (after a merge or a pool exhaustion)
 // counts its whole sort and scatter over the live entries instead.
 static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, int64_t kept_old, int64_t m_new,
-                                  int ts_passes, bool append, bool ts_full, int64_t tg_added, int64_t G)
+                                  int ts_passes, bool append, bool store_fused, bool ts_full, int64_t tg_added,
+                                  int64_t G)
 {
     int64_t x = 17 * b;
     if (ts_passes > 0) x += ts_passes * 24 * b + 32 * b;
-    x += append ? 32 * k : 16 * (kept_old + k) + 16 * m_new;
+    x += append ? (store_fused ? 16 * k : 32 * k) : 16 * (kept_old + k) + 16 * m_new;
     x += ts_full ? 16 * m_new + 4 * G : (ts_passes > 0 ? 16 * k : 2 * k) + 4 * tg_added;
     if (r.rebuilt) {
         const int64_t M = r.rb_entries;
@@ -692,11 +705,18 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     // 1. batch statistics
     stage.next("ingest: batch statistics");
     k_init_scratch<<<1, 1, 0, st>>>(ds);
+    // the store's free tail takes the batch as it is read (used when the
+    // batch turns out to be appended whole; nothing reads that space else)
+    const bool spec = n > 0 && h->st_src[h->cur].p && h->s_hi + n <= h->s_cap;
+    const int64_t spec_at = h->s_hi;
     if (n > 0)
         k_batch_stats<<<std::min<unsigned>(grid_for(h, (n + STATS_UNROLL - 1) / STATS_UNROLL, STATS_THREADS),
                                            (unsigned)h->num_sms * 4),
-                        STATS_THREADS, 0, st>>>(src, dst, ts, n, h->has_cutoff, h->cutoff,
-                                                h->b_gflag.as<uint8_t>(), ds);
+                        STATS_THREADS, 0, st>>>(
+            src, dst, ts, n, h->has_cutoff, h->cutoff, h->b_gflag.as<uint8_t>(),
+            spec ? h->st_src[h->cur].as<int32_t>() + spec_at : nullptr,
+            spec ? h->st_dst[h->cur].as<int32_t>() + spec_at : nullptr,
+            spec ? h->st_ts[h->cur].as<int64_t>() + spec_at : nullptr, ds);
     // the window of a batch that turns out sorted (the usual stream), in the
     // same round trip
     const int mode = h->window > 0 ? 1 : (h->window < 0 ? 2 : 0);
@@ -807,6 +827,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     stage.next("ingest: store");
     *changing = true;
     int64_t new_lo = 0;  // first appended index
+    bool store_fused = false;  // the batch statistics already wrote the appended edges
     if (append) {
         if (h->s_hi + nbk > h->s_cap) {
             // move the kept range to the front of the other buffer
@@ -835,7 +856,8 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
             h->s_lo += i0;
         }
         new_lo = h->s_hi;
-        if (nbk > 0) {
+        store_fused = spec && sorted && late == 0 && j0 == 0 && old_buf == h->cur && h->s_hi == spec_at;
+        if (nbk > 0 && !store_fused) {
             int32_t *os = h->st_src[h->cur].as<int32_t>() + h->s_hi;
             int32_t *od = h->st_dst[h->cur].as<int32_t>() + h->s_hi;
             int64_t *ot = h->st_ts[h->cur].as<int64_t>() + h->s_hi;
@@ -978,8 +1000,8 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
         stats->evict_ms = (h->eev_valid && !nv_full && cudaEventElapsedTime(&ms, h->eev[0], h->eev[1]) == cudaSuccess)
                               ? (double)ms : 0.0;
         const int ts_passes = sorted ? 0 : (bits_for(span) + RADIX_BITS - 1) / RADIX_BITS;
-        stats->model_bytes = ingest_model_bytes(h->nv_rep, n, nbk, na, m_new, ts_passes, append, ts_full,
-                                                tg_added_now, h->G);
+        stats->model_bytes = ingest_model_bytes(h->nv_rep, n, nbk, na, m_new, ts_passes, append, store_fused,
+                                                ts_full, tg_added_now, h->G);
         stats->view_rebuilt = h->nv_rep.rebuilt ? 1 : 0;
         stats->reserved = 0;
     }
