@@ -384,7 +384,13 @@ enum {
     /* walks into host buffers: host threads that write the rows sent as
      * cells (0-256; 0, the default: the CPUs this process may run on, from
      * its affinity mask and cgroup CPU quota, at most 32) */
-    TEMPEST_TUNE_HOST_THREADS = 6
+    TEMPEST_TUNE_HOST_THREADS = 6,
+    /* ingest: how the node view finds what each node lost to eviction (Sec.
+     * 2.6): 0 (default) chooses, 1 counts the evicted edges' endpoints, 2
+     * has every active node search its own entries for the new store head
+     * (chosen when the active nodes are fewer than an eighth of the evicted
+     * entries) */
+    TEMPEST_TUNE_EVICT = 7
 };
 /* Set / read one knob.  EINVAL on an unknown knob or a value out of range. */
 int tempest_set_tuning(tempest_t *h, int knob, int64_t value);

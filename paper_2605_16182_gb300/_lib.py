@@ -27,7 +27,7 @@ N2V_MAX_TRIALS = 4096
 START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH, SCHED_LANE = 0, 1, 2, 3, 4
 (TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS, TUNE_PAD_PASS, TUNE_HOST_LINK_PCT,
- TUNE_HOST_THREADS) = 0, 1, 2, 3, 4, 5, 6
+ TUNE_HOST_THREADS, TUNE_EVICT) = 0, 1, 2, 3, 4, 5, 6, 7
 TUNE_FORMS = 1
 TUNE_PER_INGEST = 2
 TUNE_MAX_TRIALS = 48

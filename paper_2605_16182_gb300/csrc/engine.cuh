@@ -70,12 +70,14 @@ struct NvCounters {
     unsigned long long moved_e;       // live entries of the regions that move (a batch's report)
     unsigned long long moved_g;       // live groups of the regions that move
     unsigned long long g_added;       // groups the batch adds
+    unsigned long long ev_removed;    // entries the per-node eviction search removed
 };
 
 // What the node view did for one batch: the counts its algorithmic-bytes
 // model needs (see ingest_model_bytes).
 struct NvBatchReport {
     int64_t ev_entries = 0, ev_nodes = 0;              // evicted entries and the nodes that lost them
+    int64_t ev_scanned = 0;                             // active nodes searched instead of counting (0: counted)
     int64_t entries = 0, ids = 0, passes = 0, runs = 0;  // appended entries, distinct nodes, sort passes, node runs
     int64_t moved_e = 0, moved_g = 0, g_added = 0;     // region moves; groups added
     bool rebuilt = false;                               // the whole view was rebuilt instead
@@ -230,6 +232,7 @@ struct tempest {
     int64_t last_d2h = 0;      // bytes the last walk call copied device to host
     int host_link_pct = 62;    // percent of host-output rows copied whole (the rest expanded on the host)
     int host_threads = 0;      // host threads expanding those rows (0: the CPUs the process may use, <= 32)
+    int evict_mode = 0;        // node view eviction: 0 chooses, 1 counts evicted endpoints, 2 per-node search
 
     // Temporal Node2Vec: return / in-out parameters; the live-pair table kept
     // by ingest once q != 1 (pt_cap slots, a power of two; pt_ub bounds the

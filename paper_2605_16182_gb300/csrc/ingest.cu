@@ -483,7 +483,10 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 //                        edges' group-start bytes; 16 k when the batch came
 //                        unsorted and its timestamps are read instead)
 //   4 e + 104 u          eviction: endpoint ids read; per node its counter
-//                        (8) and its records (16 + 32) read and written
+//                        (8) and its records (16 + 32) read and written (32 A
+//                        + 96 u when the A active nodes search their own
+//                        entries instead: record and first entry read per
+//                        node, no ids read, no counter)
 //   4 E + 16 U           batch-local ids (ids read, id table)
 //   20 P E               node sort passes (key read for the histogram, key
 //                        and value read and written by the scatter; the
@@ -512,7 +515,7 @@ static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, 
         const int64_t M = r.rb_entries;
         x += M * (8 + 20 * r.rb_passes + 32 + 32 + 32) + 12 * r.rb_groups + 104 * r.rb_nodes;
     } else {
-        x += 4 * r.ev_entries + 104 * r.ev_nodes;
+        x += r.ev_scanned ? 32 * r.ev_scanned + 96 * r.ev_nodes : 4 * r.ev_entries + 104 * r.ev_nodes;
         x += 4 * r.entries + 16 * r.ids;
         x += 20 * r.passes * r.entries;
         x += 41 * r.entries;

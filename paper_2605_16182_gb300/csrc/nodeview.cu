@@ -312,6 +312,48 @@ __global__ void __launch_bounds__(256) k_nv_evict_count(Items it, int64_t items,
         if (s_key[i] >= 0) ev_add(s_key[i], s_cnt[i], ev, ev_nodes, c);
 }
 
+// Node v drops its entries before e_lo (r: its record) from the front of its
+// region; returns the groups it lost.
+__device__ __forceinline__ int32_t evict_node(int32_t v, int4 r, int32_t e_lo, int4 *nrec, NodeRange *ngr,
+                                              int32_t *ngo, const int64_t *__restrict__ ngts, int32_t *nev)
+{
+    const int32_t gx = ngr[v].g_lo, gy = ngr[v].g_hi;
+    int32_t ng;
+    if (e_lo == r.y) {
+        ng = gy;
+    } else {
+        // first group whose range ends after e_lo (ngo[gy] = r.y > e_lo):
+        // the group starts grow about linearly with the group index (a hub's
+        // groups hold about one entry each), so the first probes
+        // interpolate, then the search bisects
+        int32_t lo = gx, hi = gy - 1;
+        int64_t vlo = ngo[lo], vhi = ngo[hi + 1];  // start of group lo, end of group hi
+        for (int step = 0; lo < hi; step++) {
+            int32_t mid = lo + ((hi - lo) >> 1);
+            if (step < 4 && hi - lo > 16 && vhi > vlo) {
+                const int64_t est = lo + (e_lo - vlo) * (int64_t)(hi + 1 - lo) / (vhi - vlo);
+                mid = (int32_t)min(max(est, (int64_t)lo), (int64_t)(hi - 1));
+            }
+            const int32_t x = ngo[mid + 1];
+            if (x > e_lo) {
+                hi = mid;
+                vhi = x;
+            } else {
+                lo = mid + 1;
+                vlo = x;
+            }
+        }
+        ng = lo;
+        ngo[ng] = e_lo;  // the first kept group may have lost a prefix
+        ngr[v].t_first = ngts[ng];
+    }
+    nev[v] += ng - gx;  // the node's group numbering origin moves with it (time-bucket table reuse)
+    r.x = e_lo;
+    nrec[v] = r;
+    ngr[v].g_lo = ng;
+    return ng - gx;
+}
+
 // Every node that lost entries drops them from the front of its region.
 __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *ev, int4 *nrec, NodeRange *ngr,
                                  int32_t *ngo, const int64_t *__restrict__ ngts, int32_t *nev, NvCounters *c)
@@ -322,50 +364,75 @@ __global__ void k_nv_evict_apply(const int32_t *__restrict__ ev_nodes, int32_t *
         const int32_t v = ev_nodes[j];
         const int32_t k = ev[v];
         ev[v] = 0;
-        int4 r = nrec[v];
-        const int32_t gx = ngr[v].g_lo, gy = ngr[v].g_hi;
+        const int4 r = nrec[v];
         int32_t e_lo = r.x + k;
         if (k <= 0 || e_lo > r.y) {
             atomicOr(&c->status, 1ull << 1);
             e_lo = min(max(e_lo, r.x), r.y);
         }
-        int32_t ng;
-        if (e_lo == r.y) {
-            ng = gy;
-        } else {
-            // first group whose range ends after e_lo (ngo[gy] = r.y > e_lo):
-            // the group starts grow about linearly with the group index (a
-            // hub's groups hold about one entry each), so the first probes
-            // interpolate, then the search bisects
-            int32_t lo = gx, hi = gy - 1;
-            int64_t vlo = ngo[lo], vhi = ngo[hi + 1];  // start of group lo, end of group hi
-            for (int step = 0; lo < hi; step++) {
-                int32_t mid = lo + ((hi - lo) >> 1);
-                if (step < 4 && hi - lo > 16 && vhi > vlo) {
-                    const int64_t est = lo + (e_lo - vlo) * (int64_t)(hi + 1 - lo) / (vhi - vlo);
-                    mid = (int32_t)min(max(est, (int64_t)lo), (int64_t)(hi - 1));
-                }
-                const int32_t v = ngo[mid + 1];
-                if (v > e_lo) {
-                    hi = mid;
-                    vhi = v;
-                } else {
-                    lo = mid + 1;
-                    vlo = v;
-                }
-            }
-            ng = lo;
-            ngo[ng] = e_lo;  // the first kept group may have lost a prefix
-            ngr[v].t_first = ngts[ng];
-        }
-        removed += ng - gx;
-        nev[v] += ng - gx;  // the node's group numbering origin moves with it (time-bucket table reuse)
-        r.x = e_lo;
-        nrec[v] = r;
-        ngr[v].g_lo = ng;
+        removed += evict_node(v, r, e_lo, nrec, ngr, ngo, ngts, nev);
     }
     removed = warp_sum((unsigned long long)removed);
     if ((threadIdx.x & 31) == 0 && removed) atomicAdd((unsigned long long *)&c->gn_delta, (unsigned long long)-removed);
+}
+
+// The same eviction without reading the evicted edges, for streams whose
+// active nodes are far fewer than the evicted entries (a Zipf stream: tens
+// of thousands of nodes against 10M entries per batch): within a node the
+// entries ascend in store position, so each active node finds its first
+// entry at or after the new store head (cut) by a search over its own
+// entries, interpolating first (a hub's positions grow about linearly).
+// The entries removed are summed and checked against the evicted count.
+__global__ void k_nv_evict_scan(const int32_t *__restrict__ act, int64_t n_act, uint32_t cut,
+                                const Entry *__restrict__ ent, int4 *nrec, NodeRange *ngr, int32_t *ngo,
+                                const int64_t *__restrict__ ngts, int32_t *nev, NvCounters *c)
+{
+    long long removed_g = 0;
+    unsigned long long removed_e = 0, nodes = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_act; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = act[j];
+        const int4 r = nrec[v];
+        if (r.x >= r.y) continue;
+        auto rel = [&](int32_t e) { return (int32_t)((uint32_t)ent[e].slot - cut); };
+        const int32_t r0 = rel(r.x);
+        if (r0 >= 0) continue;  // its oldest entry is kept
+        int32_t e_lo;
+        const int32_t r1 = rel(r.y - 1);
+        if (r1 < 0) {
+            e_lo = r.y;  // every entry goes
+        } else {
+            // rel(lo) < 0 <= rel(hi)
+            int32_t lo = r.x, hi = r.y - 1;
+            int64_t vlo = r0, vhi = r1;
+            for (int step = 0; hi - lo > 1; step++) {
+                int32_t mid = lo + ((hi - lo) >> 1);
+                if (step < 4 && hi - lo > 16 && vhi > vlo) {
+                    const int64_t est = lo + (0 - vlo) * (int64_t)(hi - lo) / (vhi - vlo);
+                    mid = (int32_t)min(max(est, (int64_t)lo + 1), (int64_t)(hi - 1));
+                }
+                const int32_t x = rel(mid);
+                if (x < 0) {
+                    lo = mid;
+                    vlo = x;
+                } else {
+                    hi = mid;
+                    vhi = x;
+                }
+            }
+            e_lo = hi;
+        }
+        removed_e += (unsigned long long)(e_lo - r.x);
+        nodes++;
+        removed_g += evict_node(v, r, e_lo, nrec, ngr, ngo, ngts, nev);
+    }
+    removed_g = warp_sum((unsigned long long)removed_g);
+    removed_e = warp_sum(removed_e);
+    nodes = warp_sum(nodes);
+    if ((threadIdx.x & 31) == 0) {
+        if (removed_g) atomicAdd((unsigned long long *)&c->gn_delta, (unsigned long long)-removed_g);
+        if (removed_e) atomicAdd(&c->ev_removed, removed_e);
+        if (nodes) atomicAdd(&c->n_ev_nodes, nodes);
+    }
 }
 
 // Batch-local node ids, so that the batch's node sort needs only as many
@@ -963,16 +1030,27 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         for (cudaEvent_t &e : h->eev)
             if (!e) cudaEventCreate(&e);
         cudaEventRecord(h->eev[0], st);
-        // contiguous shares of at least 2048 items per block, at most 8 blocks per SM
-        const int64_t eg = std::max<int64_t>(1, std::min<int64_t>((ne + 2047) / 2048, 8 * (int64_t)h->num_sms));
-        k_nv_evict_count<<<(unsigned)eg, 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
-                                                       h->ev_nodes.as<int32_t>(), dc);
-        k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
-            h->ev_nodes.as<int32_t>(), h->ev.as<int32_t>(), h->nrec.as<int4>(), h->ngr.as<NodeRange>(),
-            h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->nev.as<int32_t>(), dc);
+        const bool scan = h->n_act > 0 && (h->evict_mode == 2 || (h->evict_mode == 0 && 8 * h->n_act < ne));
+        if (scan) {
+            // far fewer active nodes than evicted entries: each searches its
+            // own entries for the new store head instead
+            rep.ev_scanned = h->n_act;
+            k_nv_evict_scan<<<grid_for(h, h->n_act), 256, 0, st>>>(
+                h->act.as<int32_t>(), h->n_act, slot_base(h, h->s_lo), h->ent.as<Entry>(), h->nrec.as<int4>(),
+                h->ngr.as<NodeRange>(), h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->nev.as<int32_t>(), dc);
+            h->pending_launches += 1;
+        } else {
+            // contiguous shares of at least 2048 items per block, at most 8 blocks per SM
+            const int64_t eg = std::max<int64_t>(1, std::min<int64_t>((ne + 2047) / 2048, 8 * (int64_t)h->num_sms));
+            k_nv_evict_count<<<(unsigned)eg, 256, 0, st>>>(ei, ne, N_old, h->ev.as<int32_t>(),
+                                                           h->ev_nodes.as<int32_t>(), dc);
+            k_nv_evict_apply<<<grid_for(h, std::min(ne, N_old)), 256, 0, st>>>(
+                h->ev_nodes.as<int32_t>(), h->ev.as<int32_t>(), h->nrec.as<int4>(), h->ngr.as<NodeRange>(),
+                h->ngo.as<int32_t>(), h->ngts.as<int64_t>(), h->nev.as<int32_t>(), dc);
+            h->pending_launches += 2;
+        }
         cudaEventRecord(h->eev[1], st);
         h->eev_valid = true;
-        h->pending_launches += 2;
     }
     if (nbe > 0) {
         const int64_t runs_max = std::min(nbe, N);
@@ -1075,6 +1153,9 @@ int nv_append_finish(tempest_t *h, const NvCounters *hc, bool *rebuild)
         *rebuild = true;  // nothing was moved or scattered; the caller rebuilds the whole view
         return TEMPEST_OK;
     }
+    if (rep.ev_scanned && (int64_t)hc->ev_removed != rep.ev_entries)
+        return fail(h, TEMPEST_ECUDA, "node view: the eviction search removed %lld entries, %lld were evicted",
+                    (long long)hc->ev_removed, (long long)rep.ev_entries);
     h->Gn += (int64_t)hc->gn_delta;
     rep.ev_nodes = (int64_t)hc->n_ev_nodes;
     rep.moved_e = (int64_t)hc->moved_e;

@@ -142,6 +142,11 @@ int tempest_set_tuning(tempest_t *h, int knob, int64_t value)
                                                       (long long)value);
             h->host_threads = (int)value;
             return TEMPEST_OK;
+        case TEMPEST_TUNE_EVICT:
+            if (value < 0 || value > 2) return fail(h, TEMPEST_EINVAL, "tuning: eviction mode %lld is not 0, 1 or 2",
+                                                    (long long)value);
+            h->evict_mode = (int)value;
+            return TEMPEST_OK;
         default:
             return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
@@ -158,6 +163,7 @@ int tempest_get_tuning(tempest_t *h, int knob, int64_t *value)
         case TEMPEST_TUNE_PAD_PASS: *value = h->pad_pass; return TEMPEST_OK;
         case TEMPEST_TUNE_HOST_LINK_PCT: *value = h->host_link_pct; return TEMPEST_OK;
         case TEMPEST_TUNE_HOST_THREADS: *value = h->host_threads; return TEMPEST_OK;
+        case TEMPEST_TUNE_EVICT: *value = h->evict_mode; return TEMPEST_OK;
         default: return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
 }

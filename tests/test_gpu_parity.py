@@ -105,6 +105,28 @@ def test_random_streams_state_and_walks(directed, window):
         check_walks(eng, orc, 700, rng.choice([2, 3, 9]), policy=trial % 2, seed=trial)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("directed", [True, False])
+def test_eviction_modes_agree(mode, directed):
+    """Both ways of finding what each node lost to eviction (counting the
+    evicted endpoints; each active node searching its own entries for the
+    new store head), forced on streams where the other would be chosen:
+    duration and count windows, sorted, unsorted and late batches, hubs and
+    self-loops; state after every batch."""
+    rng = random.Random(4400 + mode * 10 + directed)
+    for trial, window in enumerate((-30, 40, -1, 7, -500)):
+        eng, orc = pair(window, directed)
+        eng.set_tuning(_lib.TUNE_EVICT, mode)
+        assert eng.get_tuning(_lib.TUNE_EVICT) == mode
+        for s, d, t in _stream(rng, rng.randrange(1, 7), rng.choice([6, 60, 900]),
+                               rng.choice([3, 50, 2000]), 60, rng.random() < 0.5):
+            ingest_both(eng, orc, s, d, t)
+            assert_state_equal(eng.state(), orc.state(), "mode %d window %d" % (mode, window))
+        check_walks(eng, orc, 500, 5, seed=trial, biases=(0,), scheds=(_lib.SCHED_LANE,))
+    with pytest.raises(_lib.TempestError):
+        eng.set_tuning(_lib.TUNE_EVICT, 3)
+
+
 def test_multi_tile_unsorted_batch_with_ragged_tail():
     # spans several radix-sort tiles and scan chunks, not a multiple of any
     rng = np.random.default_rng(5)
