@@ -26,7 +26,7 @@
 //      entries, group chunks of BKT_CHUNK groups), and a map gives every task
 //      its big node;
 //   3. one warp per task copies entries, or reads a chunk's group
-//      timestamps, each lane 32 consecutive groups in order: group g owns
+//      timestamps, 128 consecutive groups per round, four per lane: group g owns
 //      the entries k in (bucket(g - 1), bucket(g)] (it is the first group of
 //      those buckets) and the node's last group also (bucket(g), K] (value
 //      g1).  A group's lane writes its own few entries; a long run (a time
@@ -43,7 +43,6 @@ namespace tw {
 namespace {
 
 constexpr int BKT_SHORT_RUN = 4;     // table entries a group's own lane writes
-constexpr int BKT_ROUNDS = 4;        // rounds of 32 groups whose timestamps a warp loads together
 constexpr int32_t BKT_COPY = 2048;   // table entries per copy task
 
 // How a big node's table is built: the bucket width, and which part comes
@@ -210,7 +209,6 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
                                                   const int64_t *__restrict__ ngts, const int32_t *__restrict__ prev,
                                                   int gen, int64_t cap, int32_t *bkt, WalkCounters *chk)
 {
-    static_assert(BKT_CHUNK % (32 * BKT_ROUNDS) == 0, "a chunk is whole rounds");
     const int lane = threadIdx.x & 31;
     const int64_t nch = (int64_t)*tot;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -252,33 +250,52 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
         }
         const int32_t start = from + (local - copy_tasks) * BKT_CHUNK;
         const int32_t end = min(g1, start + BKT_CHUNK);
-        // rounds of 32 consecutive groups, one per lane (coalesced loads,
-        // BKT_ROUNDS rounds in flight); a group's predecessor bucket comes
-        // from the lane before it, lane 0's from the previous round (-1 at
-        // the node's first group)
-        int32_t kcarry = start == g0 ? -1 : (int32_t)((__ldg(ngts + start - 1) >> s) - bfirst);
-        for (int32_t gb = start; gb < end; gb += 32 * BKT_ROUNDS) {
-            int64_t tv[BKT_ROUNDS];
+        // four consecutive groups per lane (two 16-byte loads), from the
+        // 4-aligned group at or before start: 128 groups per warp round, the
+        // next round's loads issued before this one is processed.  A group's
+        // predecessor bucket comes from the group before it (the lane before
+        // for a lane's first group, the previous round's last for lane 0),
+        // -1 at the node's first group; the groups before start in the first
+        // quad are read only as predecessors
+        const int32_t ga = start & ~3;
+        int32_t kcarry = (ga == start && start > g0) ? (int32_t)((__ldg(ngts + start - 1) >> s) - bfirst) : -1;
+        auto load4 = [&](int32_t q, int64_t *t) {
+            if (q + 4 <= end) {
+                const longlong2 *p2 = reinterpret_cast<const longlong2 *>(ngts + q);
+                const longlong2 a = __ldg(p2), b = __ldg(p2 + 1);
+                t[0] = a.x;
+                t[1] = a.y;
+                t[2] = b.x;
+                t[3] = b.y;
+            } else {
 #pragma unroll
-            for (int x = 0; x < BKT_ROUNDS; x++) {
-                const int32_t g = gb + 32 * x + lane;
-                tv[x] = g < end ? __ldg(ngts + g) : 0;
+                for (int j = 0; j < 4; j++) t[j] = q + j < end ? __ldg(ngts + q + j) : 0;
             }
+        };
+        int64_t tv[4];
+        load4(ga + 4 * lane, tv);
+        for (int32_t gb = ga; gb < end; gb += 128) {
+            const int32_t q = gb + 4 * lane;
+            int64_t tn[4];
+            load4(q + 128, tn);
+            int32_t kq[4];
 #pragma unroll
-            for (int x = 0; x < BKT_ROUNDS; x++) {
-                const int32_t g = gb + 32 * x + lane;
-                const bool valid = g < end;  // the invalid lanes are the last ones of the chunk's last round
-                const int32_t kown = valid ? (int32_t)((tv[x] >> s) - bfirst) : 0;
-                int32_t kp = __shfl_up_sync(0xffffffffu, kown, 1);
-                if (lane == 0) kp = kcarry;
-                kcarry = __shfl_sync(0xffffffffu, kown, 31);
+            for (int j = 0; j < 4; j++) kq[j] = (int32_t)((tv[j] >> s) - bfirst);
+            int32_t prev = __shfl_up_sync(0xffffffffu, kq[3], 1);
+            if (lane == 0) prev = kcarry;
+            kcarry = __shfl_sync(0xffffffffu, kq[3], 31);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
                 // entries (kp, k] hold g; the last group adds (k, K] holding
                 // g1; entries below ncopy came from the previous table.  A
                 // short run (the common case) is written by its own lane,
                 // long runs (time gaps) by the whole warp
-                const int32_t k = valid ? kown : kp;
+                const int32_t g = q + j;
+                const bool valid = g >= start && g < end;
+                const int32_t kp = g == g0 ? -1 : (j == 0 ? prev : kq[j - 1]);
+                const int32_t k = kq[j];
                 const int32_t lo_k = max(kp + 1, ncopy);
-                const int32_t hi_k = (valid && g == g1 - 1) ? K : k;
+                const int32_t hi_k = g == g1 - 1 ? K : k;
                 const int32_t cnt = valid && hi_k >= lo_k ? hi_k - lo_k + 1 : 0;
                 if (cnt > 0 && cnt <= BKT_SHORT_RUN) {
                     for (int32_t kk = lo_k; kk <= hi_k; kk++) bkt[tb + kk] = kk <= k ? g : g1;
@@ -297,6 +314,8 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
                     }
                 }
             }
+#pragma unroll
+            for (int j = 0; j < 4; j++) tv[j] = tn[j];
         }
     }
 }

@@ -1065,7 +1065,6 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
         if ((rc = ensure(h, h->nv_flags, (size_t)nbe, true))) return rc;
         if ((rc = ensure(h, h->nv_tex, sizeof(uint64_t) * (size_t)((nbe + BSCAN_TILE - 1) / BSCAN_TILE), true)))
             return rc;
-        cudaMemsetAsync(h->touched.p, 0xff, sizeof(int32_t) * (size_t)nbe, st);
         k_nv_claim<<<grid_for(h, nbe), 256, 0, st>>>(it, nbe, h->dense.as<int32_t>(), h->touched.as<int32_t>(), dc);
         NvCounters *hd = static_cast<NvCounters *>(h->hstat);
         cudaMemcpyAsync(hd, dc, sizeof(NvCounters), cudaMemcpyDeviceToHost, st);
