@@ -36,6 +36,7 @@
 
 #include "engine.cuh"
 #include "prims.cuh"
+#include "sortscan.cuh"
 #include "walkcore.cuh"
 
 namespace tw {

@@ -14,6 +14,7 @@
 
 #include "engine.cuh"
 #include "prims.cuh"
+#include "sortscan.cuh"
 
 namespace tw {
 

@@ -17,6 +17,7 @@
 // forms do, so every form returns the same walks.
 #include "engine.cuh"
 #include "prims.cuh"
+#include "sortscan.cuh"
 #include "walkcore.cuh"
 
 namespace tw {

@@ -26,6 +26,7 @@
 
 #include "engine.cuh"
 #include "prims.cuh"
+#include "sortscan.cuh"
 
 namespace tw {
 

@@ -20,6 +20,7 @@
 
 #include "engine.cuh"
 #include "prims.cuh"
+#include "sortscan.cuh"
 
 namespace tw {
 

@@ -35,6 +35,7 @@
 // over a radix sort of all entries), leaving every region with slack.
 #include "engine.cuh"
 #include "prims.cuh"
+#include "sortscan.cuh"
 
 namespace tw {
 

@@ -24,6 +24,7 @@
 
 #include "engine.cuh"
 #include "prims.cuh"
+#include "sortscan.cuh"
 
 namespace tw {
 
