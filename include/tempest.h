@@ -137,7 +137,8 @@ typedef struct {
                               the node view counts its whole sort and
                               scatter over the live entries */
     int32_t view_rebuilt;  /* 1 when the batch rebuilt the node view whole */
-    int32_t reserved;
+    int32_t copied_ahead;  /* nodes that moved onto a copy of their live range
+                            * made in the batches before (no whole slide) */
 } tempest_ingest_stats;
 
 /* Per-call walk report (valid once the call's work has finished). */
@@ -390,7 +391,12 @@ enum {
      * has every active node search its own entries for the new store head
      * (chosen when the active nodes are fewer than an eighth of the evicted
      * entries) */
-    TEMPEST_TUNE_EVICT = 7
+    TEMPEST_TUNE_EVICT = 7,
+    /* ingest: live entries from which a node whose regions fill copies its
+     * live range to their front a share per batch in the 16 batches before,
+     * instead of in one batch (Sec. 2.6 sliding window), 16..2^30; default
+     * 2^20 */
+    TEMPEST_TUNE_MIRROR_MIN = 8
 };
 /* Set / read one knob.  EINVAL on an unknown knob or a value out of range. */
 int tempest_set_tuning(tempest_t *h, int knob, int64_t value);

@@ -27,7 +27,7 @@ N2V_MAX_TRIALS = 4096
 START_UNIFORM_EDGE, START_BIASED_TS, START_PER_NODE = 0, 1, 2
 SCHED_FULL_WALK, SCHED_COOP, SCHED_STREAM, SCHED_GRAPH, SCHED_LANE = 0, 1, 2, 3, 4
 (TUNE_BKT_LOG, TUNE_COOP_W_WARP, TUNE_COOP_MEGA, TUNE_STREAM_CTAS, TUNE_PAD_PASS, TUNE_HOST_LINK_PCT,
- TUNE_HOST_THREADS, TUNE_EVICT) = 0, 1, 2, 3, 4, 5, 6, 7
+ TUNE_HOST_THREADS, TUNE_EVICT, TUNE_MIRROR_MIN) = 0, 1, 2, 3, 4, 5, 6, 7, 8
 TUNE_FORMS = 1
 TUNE_PER_INGEST = 2
 TUNE_MAX_TRIALS = 48
@@ -64,7 +64,7 @@ class IngestStats(ctypes.Structure):
                 ("n_nodes", ctypes.c_int64), ("cutoff", ctypes.c_int64),
                 ("has_cutoff", ctypes.c_int32), ("sorted_input", ctypes.c_int32),
                 ("launches", ctypes.c_int64), ("evict_ms", ctypes.c_double),
-                ("model_bytes", ctypes.c_int64), ("view_rebuilt", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("model_bytes", ctypes.c_int64), ("view_rebuilt", ctypes.c_int32), ("copied_ahead", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

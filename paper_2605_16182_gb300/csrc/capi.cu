@@ -223,7 +223,7 @@ static void free_all(tempest_t *h)
                     &h->pn_nodes,  &h->gw,        &h->gs,        &h->wref,      &h->w_cbase,   &h->w_ctot,
                     &h->w_coff,    &h->co_prev,   &h->pt,        &h->big_own,   &h->big_aux0,
                     &h->big_aux1,  &h->big_bf,    &h->bkt_prev,  &h->nev,       &h->cmp_stage, &h->cmp_off,
-                    &h->ent_tmp,   &h->nv_flags,  &h->b_gflag,   &h->nv_tex};
+                    &h->ent_tmp,   &h->nv_flags,  &h->b_gflag,   &h->nv_tex,    &h->nv_mir};
     for (DBuf *b : bufs) release(h, *b);
 }
 

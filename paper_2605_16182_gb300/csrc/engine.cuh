@@ -71,6 +71,7 @@ struct NvCounters {
     unsigned long long moved_g;       // live groups of the regions that move
     unsigned long long g_added;       // groups the batch adds
     unsigned long long ev_removed;    // entries the per-node eviction search removed
+    unsigned long long mir_switched;  // nodes that moved onto their copy made ahead (group weights go stale)
 };
 
 // What the node view did for one batch: the counts its algorithmic-bytes
@@ -78,6 +79,7 @@ struct NvCounters {
 struct NvBatchReport {
     int64_t ev_entries = 0, ev_nodes = 0;              // evicted entries and the nodes that lost them
     int64_t ev_scanned = 0;                             // active nodes searched instead of counting (0: counted)
+    int64_t copied_ahead = 0;                           // nodes moved onto a copy made ahead
     int64_t entries = 0, ids = 0, passes = 0, runs = 0;  // appended entries, distinct nodes, sort passes, node runs
     int64_t moved_e = 0, moved_g = 0, g_added = 0;     // region moves; groups added
     bool rebuilt = false;                               // the whole view was rebuilt instead
@@ -88,6 +90,13 @@ struct NvBatchReport {
 struct Reloc {
     int32_t old_e, n_e, new_e;
     int32_t old_g, n_g, new_g;
+};
+
+// A big node's copy of its live range to the front of its own regions, made
+// a share per batch ahead of the batch that no longer fits: entries from
+// x_m and groups from g_m, c_e / c_g of them copied so far (node -1: free).
+struct NvMirror {
+    int32_t node, x_m, g_m, c_e, c_g, pad0, pad1, pad2;
 };
 
 // Device-side walk counters.
@@ -137,6 +146,11 @@ struct tempest {
     tw::DBuf st_src[2], st_dst[2], st_ts[2];
     int cur = 0;
     int64_t s_lo = 0, s_hi = 0, s_cap = 0, s_base = 0;
+    // store pre-copy: while on, the other buffer holds the absolute positions
+    // [smir_a0, smir_done) at index position - smir_a0, so that the move to it
+    // when the current buffer fills copies only what the last batches added
+    bool smir_on = false;
+    int64_t smir_a0 = 0, smir_done = 0;
     // timestamp-grouped view: absolute store position (modulo 2^32) of the
     // start of every group, live groups [tg_lo, tg_hi) with tg[tg_hi] the
     // absolute end; the first live group may start before the head (its
@@ -175,6 +189,7 @@ struct tempest {
     tw::DBuf ent_tmp;  // Entry: a batch's node view entries in (node, ts, arrival) order
     tw::DBuf nv_flags; // uint8 per batch entry: run start (bit 0), group start (bit 1)
     tw::DBuf nv_tex;   // uint64 per BSCAN_TILE batch entries: runs (high) and groups (low) before the tile
+    tw::DBuf nv_mir;   // NvMirror[NV_MIRRORS]: big nodes copying their live range ahead of a slide
     int64_t S = 0;     // nodes that own regions (for the bucket index)
     int64_t state_ver = 0;  // bumped by every ingest
     // an ingest that failed after changing the store restored the store's
@@ -233,6 +248,7 @@ struct tempest {
     int host_link_pct = 62;    // percent of host-output rows copied whole (the rest expanded on the host)
     int host_threads = 0;      // host threads expanding those rows (0: the CPUs the process may use, <= 32)
     int evict_mode = 0;        // node view eviction: 0 chooses, 1 counts evicted endpoints, 2 per-node search
+    int32_t mirror_min = 1 << 20;  // live entries from which a node copies its range ahead of a slide
 
     // Temporal Node2Vec: return / in-out parameters; the live-pair table kept
     // by ingest once q != 1 (pt_cap slots, a power of two; pt_ub bounds the

@@ -452,6 +452,11 @@ int ts_export(tempest_t *h, int32_t *out)
     return cuda_check(h, cudaGetLastError(), "export");
 }
 
+// Batches before a full store buffer during which each appending batch copies
+// a share of the live range to the other buffer (the move then copies only
+// the last share: no 3 GB copy in one batch of a 200M-edge window).
+constexpr int64_t STORE_PRECOPY = 6;
+
 // Store capacity a count window settles at (the live edges never exceed the
 // window by more than a tie group, so this is the size the store grows to):
 // allocating it once the live edges reach 1/16 of the window spares the
@@ -480,6 +485,9 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 //                        when the batch statistics wrote the store as they
 //                        read the batch); a merge instead reads both sides
 //                        and writes the store
+//   32 s + 8 t           live edges copied to the other store buffer (a move,
+//                        or a share of one copied ahead), live timestamp-view
+//                        starts moved to a larger buffer
 //   2 k + 4 G_new        timestamp view (both scan passes read the kept
 //                        edges' group-start bytes; 16 k when the batch came
 //                        unsorted and its timestamps are read instead)
@@ -506,9 +514,9 @@ static int64_t steady_store_cap(const tempest_t *h, int64_t m_new, int64_t nbk)
 // counts its whole sort and scatter over the live entries instead.
 static int64_t ingest_model_bytes(const NvBatchReport &r, int64_t b, int64_t k, int64_t kept_old, int64_t m_new,
                                   int ts_passes, bool append, bool store_fused, bool ts_full, int64_t tg_added,
-                                  int64_t G)
+                                  int64_t G, int64_t store_moved, int64_t ts_moved)
 {
-    int64_t x = 17 * b;
+    int64_t x = 17 * b + 32 * store_moved + 8 * ts_moved;
     if (ts_passes > 0) x += ts_passes * 24 * b + 32 * b;
     x += append ? (store_fused ? 16 * k : 32 * k) : 16 * (kept_old + k) + 16 * m_new;
     x += ts_full ? 16 * m_new + 4 * G : (ts_passes > 0 ? 16 * k : 2 * k) + 4 * tg_added;
@@ -573,6 +581,7 @@ void ingest_undo(tempest_t *h, const IngestUndo &u)
     h->S = u.S;
     h->has_cutoff = u.has_cutoff;
     h->cur = u.cur;
+    h->smir_on = false;  // the other buffer may have been written past the copy's record
     // the views may hold part of the undone batch: rebuilt from the store
     h->nv_ready = false;
     h->w_valid = false;
@@ -802,14 +811,21 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     const int64_t old_lo = h->s_lo;
     bool ts_full = !append || !h->tg.p || h->views_dirty;
     bool nv_full = !append || !h->nv_ready;
+    // an appending batch into a buffer that fills within STORE_PRECOPY
+    // batches copies a share of the live range to the other buffer (below)
+    const bool store_full = append && h->s_hi + nbk > h->s_cap;
+    const bool precopy = append && !store_full && nbk > 0 &&
+                         (h->smir_on || h->s_cap - h->s_hi < STORE_PRECOPY * nbk);
     {
         const int nxt = h->cur ^ 1;
-        if (append && h->s_hi + nbk > h->s_cap) {
+        if (store_full || precopy) {
             const int64_t cap = std::max<int64_t>(std::max<int64_t>(h->s_cap, 2 * m_new + m_new / 2 + nbk + 1024),
                                                   steady_store_cap(h, m_new, nbk));
+            const void *was = h->st_ts[nxt].p;
             if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
             if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
             if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap, true))) return rc;
+            if (h->st_ts[nxt].p != was) h->smir_on = false;  // a new buffer holds no copy
         } else if (!append) {
             const int64_t cap =
                 std::max<int64_t>(std::max<int64_t>(h->s_cap, 2 * m_new + 1024), steady_store_cap(h, m_new, nbk));
@@ -832,32 +848,59 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     *changing = true;
     int64_t new_lo = 0;  // first appended index
     bool store_fused = false;  // the batch statistics already wrote the appended edges
+    int64_t store_moved = 0;   // live edges copied to the other buffer by this batch
     if (append) {
-        if (h->s_hi + nbk > h->s_cap) {
-            // move the kept range to the front of the other buffer
-            const int nxt = h->cur ^ 1;
-            const int64_t cap = std::max<int64_t>(std::max<int64_t>(h->s_cap, 2 * m_new + m_new / 2 + nbk + 1024),
-                                                  steady_store_cap(h, m_new, nbk));
-            if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
-            if ((rc = ensure(h, h->st_dst[nxt], sizeof(int32_t) * (size_t)cap, true))) return rc;
-            if ((rc = ensure(h, h->st_ts[nxt], sizeof(int64_t) * (size_t)cap, true))) return rc;
-            if (na > 0) {
-                const int64_t a = h->s_lo + i0;
-                cudaMemcpyAsync(h->st_src[nxt].p, h->st_src[h->cur].as<int32_t>() + a, sizeof(int32_t) * (size_t)na,
-                                cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(h->st_dst[nxt].p, h->st_dst[h->cur].as<int32_t>() + a, sizeof(int32_t) * (size_t)na,
-                                cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(h->st_ts[nxt].p, h->st_ts[h->cur].as<int64_t>() + a, sizeof(int64_t) * (size_t)na,
-                                cudaMemcpyDeviceToDevice, st);
-            }
-            h->s_base += h->s_lo + i0;
+        // absolute positions of the kept range (after this batch's eviction)
+        const int64_t A_lo = h->s_base + h->s_lo + i0, A_hi = h->s_base + h->s_hi;
+        const int nxt = h->cur ^ 1;
+        // copies the absolute positions [a, b) of the current buffer to the
+        // other one, position p at index p - base
+        auto copy_out = [&](int64_t a, int64_t b, int64_t base) {
+            if (b <= a) return;
+            const int64_t from = a - h->s_base, to = a - base, k = b - a;
+            cudaMemcpyAsync(h->st_src[nxt].as<int32_t>() + to, h->st_src[h->cur].as<int32_t>() + from,
+                            sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(h->st_dst[nxt].as<int32_t>() + to, h->st_dst[h->cur].as<int32_t>() + from,
+                            sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(h->st_ts[nxt].as<int64_t>() + to, h->st_ts[h->cur].as<int64_t>() + from,
+                            sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToDevice, st);
+            store_moved += k;
+        };
+        if (store_full) {
+            // move the kept range to the other buffer: what the pre-copy
+            // already holds stays where it is, the rest is copied now
+            const int64_t ncap = std::min({(int64_t)(h->st_src[nxt].bytes / 4), (int64_t)(h->st_dst[nxt].bytes / 4),
+                                           (int64_t)(h->st_ts[nxt].bytes / 8)});
+            const bool held = h->smir_on && h->smir_a0 <= A_lo && A_hi - h->smir_a0 + nbk <= ncap;
+            const int64_t base = held ? h->smir_a0 : A_lo;
+            copy_out(held ? std::max(h->smir_done, A_lo) : A_lo, A_hi, base);
+            h->s_base = base;
             h->cur = nxt;
-            h->s_cap = std::min({(int64_t)(h->st_src[nxt].bytes / 4), (int64_t)(h->st_dst[nxt].bytes / 4),
-                                 (int64_t)(h->st_ts[nxt].bytes / 8)});
-            h->s_lo = 0;
-            h->s_hi = na;
+            h->s_cap = ncap;
+            h->s_lo = A_lo - base;
+            h->s_hi = A_hi - base;
+            h->smir_on = false;
         } else {
             h->s_lo += i0;
+            if (precopy) {
+                // a share of the rest, so that the copy catches up with the
+                // end by the time the buffer fills (appends that still fit,
+                // this one included).  It starts where the live range will
+                // start then, predicted from this batch's eviction with one
+                // batch of margin (the edges evicted before the move are not
+                // copied; a move whose live range starts earlier copies it
+                // all)
+                const int64_t fits = std::max<int64_t>(1, (h->s_cap - h->s_hi) / nbk);
+                if (!h->smir_on) {
+                    h->smir_on = true;
+                    h->smir_a0 = std::min(A_hi, A_lo + std::max<int64_t>(0, fits - 1) * i0);
+                    h->smir_done = h->smir_a0;
+                }
+                const int64_t from = std::max(h->smir_done, A_lo), rest = A_hi - from;
+                const int64_t share = (rest + fits - 1) / fits;
+                copy_out(from, from + share, h->smir_a0);
+                h->smir_done = from + share;
+            }
         }
         new_lo = h->s_hi;
         store_fused = spec && sorted && late == 0 && j0 == 0 && old_buf == h->cur && h->s_hi == spec_at;
@@ -872,6 +915,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
         h->s_hi += nbk;
     } else {
         const int nxt = h->cur ^ 1;
+        h->smir_on = false;  // the merge writes the other buffer
         const int64_t cap =
             std::max<int64_t>(std::max<int64_t>(h->s_cap, 2 * m_new + 1024), steady_store_cap(h, m_new, nbk));
         if ((rc = ensure(h, h->st_src[nxt], sizeof(int32_t) * (size_t)cap))) return rc;
@@ -905,9 +949,11 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
 
     // 6. timestamp view
     stage.next("ingest: timestamp view");
+    int64_t ts_moved = 0;
     if (!ts_full && (int64_t)(h->tg.bytes / sizeof(int32_t)) < h->tg_hi + nbk + 2) {
         // move the live starts [tg_lo, tg_hi] to the front of a larger buffer
         const int64_t live = h->tg_hi - h->tg_lo + 1;
+        ts_moved = live;
         const int64_t tcap = std::max<int64_t>(2 * (live + nbk) + 1024, steady_store_cap(h, m_new, nbk));
         if ((rc = ensure(h, h->tg2, sizeof(int32_t) * (size_t)tcap, true))) return rc;
         cudaMemcpyAsync(h->tg2.p, h->tg.as<int32_t>() + h->tg_lo, sizeof(int32_t) * (size_t)live,
@@ -1005,9 +1051,9 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
                               ? (double)ms : 0.0;
         const int ts_passes = sorted ? 0 : (bits_for(span) + RADIX_BITS - 1) / RADIX_BITS;
         stats->model_bytes = ingest_model_bytes(h->nv_rep, n, nbk, na, m_new, ts_passes, append, store_fused,
-                                                ts_full, tg_added_now, h->G);
+                                                ts_full, tg_added_now, h->G, store_moved, ts_moved);
         stats->view_rebuilt = h->nv_rep.rebuilt ? 1 : 0;
-        stats->reserved = 0;
+        stats->copied_ahead = (int32_t)h->nv_rep.copied_ahead;
     }
     return TEMPEST_OK;
 }

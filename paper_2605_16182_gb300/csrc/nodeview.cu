@@ -43,7 +43,14 @@ namespace {
 
 constexpr int RELOC_CHUNK = 1024;
 
-__device__ __forceinline__ int64_t region_cap(int64_t x, int shift) { return x + (x >> shift) + 16; }
+// Capacity of a region for x items: slack x >> shift, and half as much again
+// for a node of at least big_min entries (a hub slides back to the front of
+// its regions once its live range reaches their end; more slack makes that
+// rarer, and the copy ahead of it spans fewer of the batches).
+__device__ __forceinline__ int64_t region_cap(int64_t x, int shift, bool big)
+{
+    return x + (x >> shift) + (big ? (x >> (shift + 1)) : 0) + 16;
+}
 
 // The entry of store item i (directed: edge i under its source; undirected:
 // item 2p under src_p, item 2p + 1 under dst_p).
@@ -152,11 +159,13 @@ struct BuildRunOp {
 struct CapOp {
     const int32_t *run_pos, *run_g;
     int shift;
+    int32_t big_min;
     int32_t *run_de, *run_dg;
     __device__ __forceinline__ uint64_t value(int64_t r) const
     {
         const int64_t c = run_pos[r + 1] - run_pos[r], gc = run_g[r + 1] - run_g[r];
-        return ((uint64_t)(region_cap(gc, shift) + 1) << 32) | (uint64_t)region_cap(c, shift);
+        const bool big = c >= big_min;
+        return ((uint64_t)(region_cap(gc, shift, big) + 1) << 32) | (uint64_t)region_cap(c, shift, big);
     }
     __device__ __forceinline__ void emit(int64_t r, uint64_t, uint64_t ex) const
     {
@@ -177,13 +186,16 @@ __global__ void k_nv_tail(int32_t *run_pos, int32_t *run_g, int32_t *fx, const u
 __global__ void k_nv_build_nodes(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
                                  const int32_t *__restrict__ run_g, const int32_t *__restrict__ run_de,
                                  const int32_t *__restrict__ run_dg, const Entry *__restrict__ E, int64_t S,
-                                 int shift, int4 *nrec, NodeRange *ngr, int2 *nbeg, int32_t *ngo, int32_t *act)
+                                 int shift, int32_t big_min, int4 *nrec, NodeRange *ngr, int2 *nbeg, int32_t *ngo,
+                                 int32_t *act)
 {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < S; r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = run_node[r];
         const int32_t c = run_pos[r + 1] - run_pos[r], gc = run_g[r + 1] - run_g[r];
         const int32_t eb = run_de[r], gb = run_dg[r];
-        nrec[v] = make_int4(eb, eb + c, eb + (int32_t)region_cap(c, shift), gb + (int32_t)region_cap(gc, shift) + 1);
+        const bool big = c >= big_min;
+        nrec[v] = make_int4(eb, eb + c, eb + (int32_t)region_cap(c, shift, big),
+                            gb + (int32_t)region_cap(gc, shift, big) + 1);
         NodeRange x;
         x.g_lo = gb;
         x.g_hi = gb + gc;
@@ -558,11 +570,27 @@ struct AppendRunBytes {
 // the node's own regions can take its live items without overlapping them, a
 // move back to the regions' start (a sliding window's steady state: no pool
 // space is used); else fresh regions from the pools and a move.
+// Big nodes (a Zipf hub) slide their live range back to the front of their
+// regions every few dozen batches (a sliding window's steady state), a copy
+// of all their entries and groups in one batch.  Instead, in the batches
+// before the one that no longer fits, each copies a share of the range that
+// will then be live (from its predicted start) to the front, and the batch
+// that no longer fits copies the rest and moves the node onto the copy.
+constexpr int NV_MIRRORS = 64;               // big nodes copying ahead at once
+constexpr int64_t NV_MIRROR_BATCHES = 16;    // batches ahead of the slide
+
+__device__ __forceinline__ int mirror_find(const NvMirror *mir, int32_t v)
+{
+    for (int i = 0; i < NV_MIRRORS; i++)
+        if (mir[i].node == v) return i;
+    return -1;
+}
+
 __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
                              const int32_t *__restrict__ run_g, const uint64_t *__restrict__ tot, int shift,
                              int64_t e_cap, int64_t g_cap, int4 *nrec, NodeRange *ngr, int2 *nbeg, int32_t *ngo,
                              int32_t *act, int64_t act_cap, Reloc *reloc, int32_t *run_de, int32_t *run_dg,
-                             NvCounters *c)
+                             NvMirror *mir, int32_t mirror_min, NvCounters *c)
 {
     const int64_t R = (int64_t)(*tot >> 32);
     long long added = 0;
@@ -582,40 +610,114 @@ __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t
         if (!fresh && (int64_t)rec.y + cnt <= rec.z && (int64_t)g.y + gc + 1 <= rec.w) {
             d_e = rec.y;
             d_g = g.y;
+            if (live_e >= mirror_min) {
+                // batches like this one that fit, this one included
+                const int64_t fits = min((int64_t)(rec.z - rec.y) / max(cnt, 1),
+                                         (int64_t)(rec.w - g.y - 1) / max(gc, 1));
+                const int2 beg = nbeg[v];
+                int m = mirror_find(mir, v);
+                if (m < 0 && fits <= NV_MIRROR_BATCHES) {
+                    // the range live at the slide starts about fits - 1
+                    // batches of groups on (this batch's groups as the rate)
+                    const int32_t gm = (int32_t)min((int64_t)g.y, (int64_t)g.x + (fits - 1) * (int64_t)gc);
+                    const int32_t xm = gm < g.y ? ngo[gm] : rec.y;
+                    for (int i = (int)((uint32_t)v % NV_MIRRORS), k = 0; k < NV_MIRRORS && m < 0;
+                         k++, i = (i + 1) % NV_MIRRORS)
+                        if (atomicCAS(&mir[i].node, -1, v) == -1) {
+                            mir[i].x_m = xm;
+                            mir[i].g_m = gm;
+                            mir[i].c_e = 0;
+                            mir[i].c_g = 0;
+                            m = i;
+                        }
+                }
+                if (m >= 0) {
+                    // this batch's share, written below the live range only
+                    NvMirror q = mir[m];
+                    const int64_t fe = max(fits, (int64_t)1);
+                    int64_t se = ((int64_t)rec.y - (q.x_m + q.c_e) + fe - 1) / fe;
+                    int64_t sg = ((int64_t)g.y - (q.g_m + q.c_g) + fe - 1) / fe;
+                    se = max((int64_t)0, min(se, (int64_t)rec.x - (beg.x + q.c_e)));
+                    sg = max((int64_t)0, min(sg, (int64_t)g.x - (beg.y + q.c_g)));
+                    if (se > 0 || sg > 0) {
+                        atomicAdd(&c->moved_e, (unsigned long long)se);
+                        atomicAdd(&c->moved_g, (unsigned long long)sg);
+                        const unsigned long long t = atomicAdd(&c->n_reloc, 1ull);
+                        reloc[t] = Reloc{q.x_m + q.c_e, (int32_t)se, beg.x + q.c_e, q.g_m + q.c_g, (int32_t)sg,
+                                         beg.y + q.c_g};
+                        mir[m].c_e = q.c_e + (int32_t)se;
+                        mir[m].c_g = q.c_g + (int32_t)sg;
+                    }
+                }
+            }
             rec.y += cnt;
         } else {
             const int2 beg = fresh ? make_int2(0, 0) : nbeg[v];
-            const bool slide = !fresh && rec.x - beg.x >= live_e && g.x - beg.y >= live_g &&
-                               (int64_t)live_e + cnt <= rec.z - beg.x && (int64_t)live_g + gc + 1 <= rec.w - beg.y;
-            int64_t ecap, gcap;
-            unsigned long long eb, gb;
-            if (slide) {
-                eb = (unsigned long long)beg.x;
-                gb = (unsigned long long)beg.y;
-                ecap = rec.z - beg.x;
-                gcap = rec.w - beg.y;
-            } else {
-                ecap = region_cap((int64_t)live_e + cnt, shift);
-                gcap = region_cap((int64_t)live_g + gc, shift) + 1;
-                eb = atomicAdd(&c->e_top, (unsigned long long)ecap);
-                gb = atomicAdd(&c->g_top, (unsigned long long)gcap);
-                if ((int64_t)eb + ecap > e_cap || (int64_t)gb + gcap > g_cap) {
-                    atomicOr(&c->overflow, 1ull);
-                    run_de[r] = -1;
-                    continue;
+            bool switched = false;
+            // the regions change here: a copy made ahead (whatever the node's
+            // size now) is used or dropped
+            const int ms = fresh ? -1 : mirror_find(mir, v);
+            if (ms >= 0) {
+                // the copy made ahead holds [x_m, x_m + c_e) and [g_m, g_m + c_g)
+                const NvMirror q = mir[ms];
+                const int64_t ne = (int64_t)rec.y - q.x_m, ng = (int64_t)g.y - q.g_m;
+                if (q.x_m <= rec.x && q.g_m <= g.x && beg.x + ne <= (int64_t)q.x_m + q.c_e &&
+                    beg.y + ng <= (int64_t)q.g_m + q.c_g && ne + cnt <= (int64_t)rec.z - beg.x &&
+                    ng + gc + 1 <= (int64_t)rec.w - beg.y) {
+                    const int32_t re = (int32_t)(ne - q.c_e), rg = (int32_t)(ng - q.c_g);
+                    if (re > 0 || rg > 0) {
+                        atomicAdd(&c->moved_e, (unsigned long long)max(re, 0));
+                        atomicAdd(&c->moved_g, (unsigned long long)max(rg, 0));
+                        const unsigned long long t = atomicAdd(&c->n_reloc, 1ull);
+                        reloc[t] = Reloc{q.x_m + q.c_e, max(re, 0), beg.x + q.c_e, q.g_m + q.c_g, max(rg, 0),
+                                         beg.y + q.c_g};
+                    }
+                    const int32_t nx = beg.x + (rec.x - q.x_m), gx = beg.y + (g.x - q.g_m);
+                    // the first live group may have lost a prefix since it was copied
+                    ngo[gx] = nx;
+                    d_e = beg.x + (int32_t)ne;
+                    d_g = beg.y + (int32_t)ng;
+                    rec = make_int4(nx, d_e + cnt, rec.z, rec.w);
+                    g.x = gx;
+                    switched = true;
+                    atomicAdd(&c->mir_switched, 1ull);
                 }
-                nbeg[v] = make_int2((int32_t)eb, (int32_t)gb);
+                mir[ms].node = -1;
             }
-            if (live_e > 0 || live_g > 0) {
-                atomicAdd(&c->moved_e, (unsigned long long)live_e);
-                atomicAdd(&c->moved_g, (unsigned long long)live_g);
-                const unsigned long long t = atomicAdd(&c->n_reloc, 1ull);
-                reloc[t] = Reloc{rec.x, live_e, (int32_t)eb, g.x, live_g, (int32_t)gb};
+            if (!switched) {
+                const bool slide = !fresh && rec.x - beg.x >= live_e && g.x - beg.y >= live_g &&
+                                   (int64_t)live_e + cnt <= rec.z - beg.x && (int64_t)live_g + gc + 1 <= rec.w - beg.y;
+                int64_t ecap, gcap;
+                unsigned long long eb, gb;
+                if (slide) {
+                    eb = (unsigned long long)beg.x;
+                    gb = (unsigned long long)beg.y;
+                    ecap = rec.z - beg.x;
+                    gcap = rec.w - beg.y;
+                } else {
+                    const bool big = (int64_t)live_e + cnt >= mirror_min;
+                    ecap = region_cap((int64_t)live_e + cnt, shift, big);
+                    gcap = region_cap((int64_t)live_g + gc, shift, big) + 1;
+                    eb = atomicAdd(&c->e_top, (unsigned long long)ecap);
+                    gb = atomicAdd(&c->g_top, (unsigned long long)gcap);
+                    if ((int64_t)eb + ecap > e_cap || (int64_t)gb + gcap > g_cap) {
+                        atomicOr(&c->overflow, 1ull);
+                        run_de[r] = -1;
+                        continue;
+                    }
+                    nbeg[v] = make_int2((int32_t)eb, (int32_t)gb);
+                }
+                if (live_e > 0 || live_g > 0) {
+                    atomicAdd(&c->moved_e, (unsigned long long)live_e);
+                    atomicAdd(&c->moved_g, (unsigned long long)live_g);
+                    const unsigned long long t = atomicAdd(&c->n_reloc, 1ull);
+                    reloc[t] = Reloc{rec.x, live_e, (int32_t)eb, g.x, live_g, (int32_t)gb};
+                }
+                d_e = (int32_t)eb + live_e;
+                d_g = (int32_t)gb + live_g;
+                rec = make_int4((int32_t)eb, d_e + cnt, (int32_t)(eb + ecap), (int32_t)(gb + gcap));
+                g.x = (int32_t)gb;
             }
-            d_e = (int32_t)eb + live_e;
-            d_g = (int32_t)gb + live_g;
-            rec = make_int4((int32_t)eb, d_e + cnt, (int32_t)(eb + ecap), (int32_t)(gb + gcap));
-            g.x = (int32_t)gb;
         }
         g.y = d_g + gc;
         nrec[v] = rec;
@@ -889,6 +991,8 @@ int nv_build(tempest_t *h)
     int rc;
     if ((rc = nv_ensure_nodes(h, N))) return rc;
     if ((rc = ensure(h, h->nvc, sizeof(NvCounters)))) return rc;
+    if ((rc = ensure(h, h->nv_mir, sizeof(NvMirror) * NV_MIRRORS))) return rc;
+    cudaMemsetAsync(h->nv_mir.p, 0xff, sizeof(NvMirror) * NV_MIRRORS, st);  // no copies made ahead
     cudaMemsetAsync(h->nrec.p, 0, h->nrec.bytes, st);
     cudaMemsetAsync(h->ngr.p, 0, h->ngr.bytes, st);
     h->bkt_prev_ok = false;  // groups are renumbered: no table of an earlier build can be reused
@@ -924,11 +1028,11 @@ int nv_build(tempest_t *h)
     const int64_t S = (int64_t)(hp[0] >> 32), Gn = (int64_t)(uint32_t)hp[0];
     // region slack: halve it until the pools fit the int32 index range
     int shift = 0;
-    while (shift < 4 && (M + (M >> shift) + 16 * S + 1 >= (int64_t)INT32_MAX / 2 ||
-                         Gn + (Gn >> shift) + 17 * S + 1 >= (int64_t)INT32_MAX / 2))
+    while (shift < 4 && (M + (M >> shift) + (M >> (shift + 1)) + 16 * S + 1 >= (int64_t)INT32_MAX / 2 ||
+                         Gn + (Gn >> shift) + (Gn >> (shift + 1)) + 17 * S + 1 >= (int64_t)INT32_MAX / 2))
         shift++;
     h->nv_shift = shift;
-    CapOp cop{h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), shift, h->run_de.as<int32_t>(),
+    CapOp cop{h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), shift, h->mirror_min, h->run_de.as<int32_t>(),
               h->run_dg.as<int32_t>()};
     nb = scan_launch(cop, S, part, st);
     cudaMemcpyAsync(hp, part + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
@@ -948,7 +1052,8 @@ int nv_build(tempest_t *h)
     h->g_cap = std::min(h->g_cap, (int64_t)INT32_MAX - 1);
     k_nv_build_nodes<<<grid_for(h, S), 256, 0, st>>>(h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(),
                                                      h->run_g.as<int32_t>(), h->run_de.as<int32_t>(),
-                                                     h->run_dg.as<int32_t>(), E, S, shift, h->nrec.as<int4>(),
+                                                     h->run_dg.as<int32_t>(), E, S, shift, h->mirror_min,
+                                                     h->nrec.as<int4>(),
                                                      h->ngr.as<NodeRange>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
                                                      h->act.as<int32_t>());
     k_nv_build_scatter<<<grid_for(h, M), 256, 0, st>>>(E, h->run_of.as<int32_t>(), h->fx.as<int32_t>(),
@@ -1112,7 +1217,7 @@ int nv_append(tempest_t *h, const int32_t *ev_src, const int32_t *ev_dst, int64_
             h->run_node.as<int32_t>(), h->run_pos.as<int32_t>(), h->run_g.as<int32_t>(), tot, h->nv_shift, h->e_cap,
             h->g_cap, h->nrec.as<int4>(), h->ngr.as<NodeRange>(), h->nbeg.as<int2>(), h->ngo.as<int32_t>(),
             h->act.as<int32_t>(), h->nrec_n, h->reloc.as<Reloc>(), h->run_de.as<int32_t>(), h->run_dg.as<int32_t>(),
-            dc);
+            h->nv_mir.as<NvMirror>(), h->mirror_min, dc);
         h->pending_launches += launches + 6;
         // moves and scatter are queued without a round trip: they read the
         // move count on the device and do nothing when a pool overflowed
@@ -1162,6 +1267,10 @@ int nv_append_finish(tempest_t *h, const NvCounters *hc, bool *rebuild)
     rep.moved_g = (int64_t)hc->moved_g;
     rep.g_added = (int64_t)hc->g_added;
     if (hc->w_rebase) h->w_valid = false;  // a weight exponent grew large: move every reference
+    // a node moved onto its copy made ahead: group weights copied before their
+    // group grew are stale
+    if (hc->mir_switched) h->w_valid = false;
+    rep.copied_ahead = (int64_t)hc->mir_switched;
     h->n_act = (int64_t)hc->n_act;
     h->S = h->n_act;
     h->M = directed ? (h->s_hi - h->s_lo) : 2 * (h->s_hi - h->s_lo);

@@ -147,6 +147,11 @@ int tempest_set_tuning(tempest_t *h, int knob, int64_t value)
                                                     (long long)value);
             h->evict_mode = (int)value;
             return TEMPEST_OK;
+        case TEMPEST_TUNE_MIRROR_MIN:
+            if (value < 16 || value > (1 << 30))
+                return fail(h, TEMPEST_EINVAL, "tuning: copy-ahead threshold %lld outside [16, 2^30]", (long long)value);
+            h->mirror_min = (int32_t)value;
+            return TEMPEST_OK;
         default:
             return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
@@ -164,6 +169,7 @@ int tempest_get_tuning(tempest_t *h, int knob, int64_t *value)
         case TEMPEST_TUNE_HOST_LINK_PCT: *value = h->host_link_pct; return TEMPEST_OK;
         case TEMPEST_TUNE_HOST_THREADS: *value = h->host_threads; return TEMPEST_OK;
         case TEMPEST_TUNE_EVICT: *value = h->evict_mode; return TEMPEST_OK;
+        case TEMPEST_TUNE_MIRROR_MIN: *value = h->mirror_min; return TEMPEST_OK;
         default: return fail(h, TEMPEST_EINVAL, "tuning: unknown knob %d", knob);
     }
 }

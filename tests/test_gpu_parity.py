@@ -442,6 +442,71 @@ def test_sliding_window_moves_store_and_regions(directed):
     check_walks(eng, orc, 3000, 16, seed=1, biases=(0, 2))
 
 
+@pytest.mark.parametrize("window", [-700, -1500])
+@pytest.mark.parametrize("directed", [1, 0])
+def test_store_moves_with_copy_ahead(window, directed):
+    """Many store moves: in the batches before its buffer fills, each batch
+    copies a share of the live range to the other buffer, and the move then
+    copies the rest.  Batch sizes vary (empty ones included), some batches
+    arrive shuffled (merges, which write the other buffer and drop the copy
+    made ahead), some carry edges below the cut-off; state after every
+    batch."""
+    eng, orc = pair(window, directed)
+    rng = np.random.default_rng(31 + directed - window)
+    t = 0
+    for b in range(120):
+        n = int(rng.integers(0, 500)) if b % 17 else 0
+        s = rng.integers(0, 40, n).astype(np.int32)
+        d = rng.integers(0, 40, n).astype(np.int32)
+        ts = (t + np.sort(rng.integers(0, 2 * n + 1, n))).astype(np.int64)
+        if n:
+            t = int(ts[-1])
+        if n and b % 11 == 5:
+            ts = ts - int(rng.integers(0, 3 * n))  # some below the cut-off; arrival order kept
+        if n and b % 13 == 7:
+            p_ = rng.permutation(n)
+            s, d, ts = s[p_], d[p_], ts[p_]
+        ingest_both(eng, orc, s, d, ts)
+        assert_state_equal(eng.state(), orc.state(), "batch %d" % b)
+    check_walks(eng, orc, 2000, 12, seed=2, biases=(0,), scheds=(_lib.SCHED_LANE,))
+
+
+@pytest.mark.parametrize("window", [-3000, -900])
+@pytest.mark.parametrize("directed", [1, 0])
+def test_big_nodes_copy_ahead_of_slides(window, directed):
+    """A hub-dominated count window with the copy-ahead threshold at its
+    minimum: in the batches before a big node's regions fill, each batch
+    copies a share of the node's live range to their front and the batch
+    that no longer fits moves the node onto the copy (or falls back to the
+    whole slide); shuffled batches (merges) rebuild the view and drop every
+    copy.  State after every batch; walks, weight-based included (weights
+    copied before their group grew are recomputed)."""
+    eng, orc = _weight_pair(window, directed, 1e-3)
+    eng.set_tuning(_lib.TUNE_MIRROR_MIN, 16)
+    assert eng.get_tuning(_lib.TUNE_MIRROR_MIN) == 16
+    rng = np.random.default_rng(77 + directed - window)
+    t = 0
+    switched = 0
+    for b in range(160):
+        n = int(rng.integers(40, 360))
+        hub = rng.random(n)
+        s = np.where(hub < 0.6, 0, np.where(hub < 0.75, 1, rng.integers(2, 50, n))).astype(np.int32)
+        d = np.where(rng.random(n) < 0.3, 0, rng.integers(1, 50, n)).astype(np.int32)
+        ts = (t + np.sort(rng.integers(0, 2 * n, n))).astype(np.int64)
+        t = int(ts[-1])
+        if b % 53 == 40:
+            p_ = rng.permutation(n)
+            s, d, ts = s[p_], d[p_], ts[p_]
+        st = ingest_both(eng, orc, s, d, ts)
+        switched += st["copied_ahead"]
+        assert_state_equal(eng.state(), orc.state(), "batch %d" % b)
+        if b % 40 == 39:
+            check_walks(eng, orc, 2000, 10, seed=b, biases=(0, 3), scheds=(_lib.SCHED_LANE,))
+    assert switched >= 3  # the hub moved onto its copy made ahead more than once
+    with pytest.raises(_lib.TempestError):
+        eng.set_tuning(_lib.TUNE_MIRROR_MIN, 15)
+
+
 # ------------------------------------------------------------ PER_NODE starts
 @pytest.mark.parametrize("directed", [1, 0])
 def test_per_node_walks_all_forms(directed):
