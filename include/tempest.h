@@ -394,8 +394,9 @@ enum {
     TEMPEST_TUNE_EVICT = 7,
     /* ingest: live entries from which a node whose regions fill copies its
      * live range to their front a share per batch in the 16 batches before,
-     * instead of in one batch (Sec. 2.6 sliding window), 16..2^30; default
-     * 2^20 */
+     * instead of in one batch, and live edges from which the store copies its
+     * live range to its other buffer in the 6 batches before it fills (Sec.
+     * 2.6 sliding window), 16..2^30; default 2^20 */
     TEMPEST_TUNE_MIRROR_MIN = 8
 };
 /* Set / read one knob.  EINVAL on an unknown knob or a value out of range. */

@@ -454,7 +454,8 @@ int ts_export(tempest_t *h, int32_t *out)
 
 // Batches before a full store buffer during which each appending batch copies
 // a share of the live range to the other buffer (the move then copies only
-// the last share: no 3 GB copy in one batch of a 200M-edge window).
+// the last share: no 3 GB copy in one batch of a 200M-edge window), for live
+// ranges of at least the copy-ahead threshold (TEMPEST_TUNE_MIRROR_MIN).
 constexpr int64_t STORE_PRECOPY = 6;
 
 // Store capacity a count window settles at (the live edges never exceed the
@@ -814,7 +815,7 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     // an appending batch into a buffer that fills within STORE_PRECOPY
     // batches copies a share of the live range to the other buffer (below)
     const bool store_full = append && h->s_hi + nbk > h->s_cap;
-    const bool precopy = append && !store_full && nbk > 0 &&
+    const bool precopy = append && !store_full && nbk > 0 && na >= h->mirror_min &&
                          (h->smir_on || h->s_cap - h->s_hi < STORE_PRECOPY * nbk);
     {
         const int nxt = h->cur ^ 1;

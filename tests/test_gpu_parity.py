@@ -452,6 +452,7 @@ def test_store_moves_with_copy_ahead(window, directed):
     made ahead), some carry edges below the cut-off; state after every
     batch."""
     eng, orc = pair(window, directed)
+    eng.set_tuning(_lib.TUNE_MIRROR_MIN, 16)  # copy ahead from 16 live edges on
     rng = np.random.default_rng(31 + directed - window)
     t = 0
     for b in range(120):
