@@ -454,8 +454,8 @@ __global__ void k_nv_evict_scan(const int32_t *__restrict__ act, int64_t n_act, 
 // finds the node unclaimed takes it with a compare-and-swap (0 -> -1) before
 // it draws the next id (drawing first, as every racing warp of a hub would,
 // spends ids that no node keeps, and a sparser id range costs sort passes).
-// touched[id] names the node of each id; the keys follow in k_nv_keys, once
-// every claim is done.
+// touched[id] names the node of each id; the sort's first histogram pass
+// looks each entry's id up once every claim is done.
 __global__ void k_nv_claim(Items it, int64_t nbe, int32_t *dense, int32_t *touched, NvCounters *c)
 {
     const int lane = threadIdx.x & 31;
