@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -91,9 +92,17 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of what the walk kernels are compiled from: their sources and the
+    records they read from the handle header (Entry, NodeRange, WalkCounters),
+    not the handle's host-side fields."""
+    csrc = os.path.join(ROOT, "paper_2605_16182_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("walks.cu", "walkcore.cuh", "prims.cuh", "engine.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2605_16182_gb300", "csrc", f), "rb").read())
+    for f in ("walks.cu", "walkcore.cuh", "prims.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    eng = open(os.path.join(csrc, "engine.cuh")).read()
+    for name in ("Entry", "NodeRange", "WalkCounters"):
+        m = re.search(r"struct (?:__align__\(\d+\) )?%s \{.*?\n\};" % name, eng, re.S)
+        h.update((m.group(0) if m else name).encode())
     return h.hexdigest()[:16]
 
 
