@@ -151,6 +151,11 @@ struct tempest {
     // when the current buffer fills copies only what the last batches added
     bool smir_on = false;
     int64_t smir_a0 = 0, smir_done = 0;
+    // timestamp-view pre-copy, the same for the group starts: while on, tg2
+    // holds the positions [tmir_a0, tmir_done) of tg at index position -
+    // tmir_a0; tg_lo_step: groups the last batch evicted from the view
+    bool tmir_on = false;
+    int64_t tmir_a0 = 0, tmir_done = 0, tg_lo_step = 0;
     // timestamp-grouped view: absolute store position (modulo 2^32) of the
     // start of every group, live groups [tg_lo, tg_hi) with tg[tg_hi] the
     // absolute end; the first live group may start before the head (its

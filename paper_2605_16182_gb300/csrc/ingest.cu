@@ -583,6 +583,7 @@ void ingest_undo(tempest_t *h, const IngestUndo &u)
     h->has_cutoff = u.has_cutoff;
     h->cur = u.cur;
     h->smir_on = false;  // the other buffer may have been written past the copy's record
+    h->tmir_on = false;
     // the views may hold part of the undone batch: rebuilt from the store
     h->nv_ready = false;
     h->w_valid = false;
@@ -815,6 +816,13 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     // an appending batch into a buffer that fills within STORE_PRECOPY
     // batches copies a share of the live range to the other buffer (below)
     const bool store_full = append && h->s_hi + nbk > h->s_cap;
+    // the timestamp view's starts move to a larger buffer when the batch's
+    // cannot follow them; in the TS_PRECOPY batches before, each copies a
+    // share ahead (as the store)
+    const int64_t tg_room = (int64_t)(h->tg.bytes / sizeof(int32_t)) - h->tg_hi - 2;
+    const bool ts_move = !ts_full && tg_room < nbk;
+    const bool ts_precopy = !ts_full && !ts_move && nbk > 0 && h->tg_hi - h->tg_lo >= h->mirror_min &&
+                            (h->tmir_on || tg_room < STORE_PRECOPY * nbk);
     const bool precopy = append && !store_full && nbk > 0 && na >= h->mirror_min &&
                          (h->smir_on || h->s_cap - h->s_hi < STORE_PRECOPY * nbk);
     {
@@ -836,10 +844,12 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
         }
         if (ts_full) {
             if ((rc = ensure(h, h->tg, sizeof(int32_t) * (size_t)(2 * m_new + 1024), true))) return rc;
-        } else if ((int64_t)(h->tg.bytes / sizeof(int32_t)) < h->tg_hi + nbk + 2) {
+        } else if (ts_move || ts_precopy) {
             const int64_t live = h->tg_hi - h->tg_lo + 1;
             const int64_t tcap = std::max<int64_t>(2 * (live + nbk) + 1024, steady_store_cap(h, m_new, nbk));
+            const void *was = h->tg2.p;
             if ((rc = ensure(h, h->tg2, sizeof(int32_t) * (size_t)tcap, true))) return rc;
+            if (h->tg2.p != was) h->tmir_on = false;  // a new buffer holds no copy
         }
         if (!nv_full && (rc = nv_prepare_append(h, i0, nbk, N_old, N_new))) return rc;
     }
@@ -951,17 +961,39 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     // 6. timestamp view
     stage.next("ingest: timestamp view");
     int64_t ts_moved = 0;
-    if (!ts_full && (int64_t)(h->tg.bytes / sizeof(int32_t)) < h->tg_hi + nbk + 2) {
-        // move the live starts [tg_lo, tg_hi] to the front of a larger buffer
-        const int64_t live = h->tg_hi - h->tg_lo + 1;
-        ts_moved = live;
-        const int64_t tcap = std::max<int64_t>(2 * (live + nbk) + 1024, steady_store_cap(h, m_new, nbk));
-        if ((rc = ensure(h, h->tg2, sizeof(int32_t) * (size_t)tcap, true))) return rc;
-        cudaMemcpyAsync(h->tg2.p, h->tg.as<int32_t>() + h->tg_lo, sizeof(int32_t) * (size_t)live,
+    // copies the starts [a, b) of tg to tg2 at index position - base
+    auto tg_copy = [&](int64_t a, int64_t b, int64_t base) {
+        if (b <= a) return;
+        cudaMemcpyAsync(h->tg2.as<int32_t>() + (a - base), h->tg.as<int32_t>() + a, sizeof(int32_t) * (size_t)(b - a),
                         cudaMemcpyDeviceToDevice, st);
+        ts_moved += b - a;
+    };
+    if (ts_full) {
+        h->tmir_on = false;
+    } else if (ts_move) {
+        // move the live starts [tg_lo, tg_hi] to a larger buffer: what the
+        // copy made ahead holds stays where it is, the rest is copied now
+        const int64_t ncap = (int64_t)(h->tg2.bytes / sizeof(int32_t));
+        const bool held = h->tmir_on && h->tmir_a0 <= h->tg_lo && h->tg_hi - h->tmir_a0 + nbk + 2 <= ncap;
+        const int64_t base = held ? h->tmir_a0 : h->tg_lo;
+        tg_copy(held ? std::max(h->tmir_done, h->tg_lo) : h->tg_lo, h->tg_hi + 1, base);
         std::swap(h->tg, h->tg2);
-        h->tg_hi -= h->tg_lo;
-        h->tg_lo = 0;
+        h->tg_hi -= base;
+        h->tg_lo -= base;
+        h->tmir_on = false;
+    } else if (ts_precopy) {
+        // a share of the starts before the tail entry (the batch overwrites
+        // that one), from the predicted first live group at the move
+        const int64_t fits = std::max<int64_t>(1, tg_room / nbk);
+        if (!h->tmir_on) {
+            h->tmir_on = true;
+            h->tmir_a0 = std::min(h->tg_hi, h->tg_lo + std::max<int64_t>(0, fits - 1) * h->tg_lo_step);
+            h->tmir_done = h->tmir_a0;
+        }
+        const int64_t from = std::max(h->tmir_done, h->tg_lo), rest = h->tg_hi - from;
+        const int64_t share = (rest + fits - 1) / fits;
+        tg_copy(from, from + share, h->tmir_a0);
+        h->tmir_done = from + share;
     }
     if (ts_full) {
         if ((rc = ts_view_build(h))) return rc;
@@ -1027,7 +1059,9 @@ static int ingest_batch_impl(tempest_t *h, const int32_t *src_in, const int32_t 
     if (ts_full) {
         h->tg_lo = 0;
         h->tg_hi = hs->tg_added;
+        h->tg_lo_step = 0;
     } else {
+        h->tg_lo_step = hs->tg_lo - h->tg_lo;
         h->tg_lo = hs->tg_lo;
         h->tg_hi += hs->tg_added;
     }
