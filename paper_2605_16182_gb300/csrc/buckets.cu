@@ -29,10 +29,11 @@
 //      timestamps, 128 consecutive groups per round, four per lane: group g owns
 //      the entries k in (bucket(g - 1), bucket(g)] (it is the first group of
 //      those buckets) and the node's last group also (bucket(g), K] (value
-//      g1).  A group's lane writes its own few entries; a long run (a time
-//      gap that leaves many buckets empty) is written by the whole warp, 32
-//      entries per store.  Every entry is written once.
+//      g1).  The round's buckets go to shared memory and each lane finds the
+//      group of one entry by bisecting them, so a round's entries leave as
+//      consecutive stores, 32 per store.  Every entry is written once.
 #include <algorithm>
+#include <climits>
 
 #include "engine.cuh"
 #include "prims.cuh"
@@ -43,7 +44,6 @@ namespace tw {
 
 namespace {
 
-constexpr int BKT_SHORT_RUN = 4;     // table entries a group's own lane writes
 constexpr int32_t BKT_COPY = 2048;   // table entries per copy task
 
 // How a big node's table is built: the bucket width, and which part comes
@@ -192,14 +192,13 @@ __global__ void __launch_bounds__(256) k_bkt_owner(const int32_t *__restrict__ b
     }
 }
 
-// One warp per task (grid-stride).  A node's first tasks copy the buckets its
-// previous table already covers (entry + the node's renumbering delta, the
-// first clamped to the live groups); the rest fill the buckets of its groups
-// from `from` on: a BKT_CHUNK chunk in rounds of 32 consecutive groups (lane
-// i the round's group i), and group g writes the entries (bucket(g - 1),
-// bucket(g)] at or above the first uncopied bucket (the last group also
-// (bucket(g), K], value g_hi).  A node's first task writes its header and its
-// entry K.
+// One warp per task (grid-stride, 256-thread blocks).  A node's first tasks
+// copy the buckets its previous table already covers (entry + the node's
+// renumbering delta, the first clamped to the live groups); the rest fill the
+// buckets of its groups from `from` on, a BKT_CHUNK chunk each: entry k, at
+// or above the first uncopied bucket, is the first group of bucket >= k (the
+// node's last group's buckets after its own hold g_hi).  A node's first task
+// writes its header and its entry K.
 __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ big_node,
                                                   const int32_t *__restrict__ big_t,
                                                   const int32_t *__restrict__ big_c,
@@ -210,6 +209,7 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
                                                   const int64_t *__restrict__ ngts, const int32_t *__restrict__ prev,
                                                   int gen, int64_t cap, int32_t *bkt, WalkCounters *chk)
 {
+    __shared__ __align__(16) int32_t s_bkt[8][128];  // per warp: a round's group buckets
     const int lane = threadIdx.x & 31;
     const int64_t nch = (int64_t)*tot;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -251,23 +251,28 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
         }
         const int32_t start = from + (local - copy_tasks) * BKT_CHUNK;
         const int32_t end = min(g1, start + BKT_CHUNK);
-        // four consecutive groups per lane (two 16-byte loads), from the
-        // 4-aligned group at or before start: 128 groups per warp round, the
-        // next round's loads issued before this one is processed.  A group's
-        // predecessor bucket comes from the group before it (the lane before
-        // for a lane's first group, the previous round's last for lane 0),
-        // -1 at the node's first group; the groups before start in the first
-        // quad are read only as predecessors
+        // Rounds of 128 consecutive groups from the 4-aligned group at or
+        // before start, four per lane (two 16-byte loads; the next round's in
+        // flight), their buckets staged in shared memory.  Buckets are
+        // monotone in the group, so entry k (first group of bucket >= k) is
+        // found by each lane for its own k by bisecting the round's 128
+        // buckets, and a round's entries (the buckets after the last one
+        // written, up to its last group's) leave as consecutive stores: about
+        // 128 >> log_b of them per round, instead of each group writing its
+        // own run.  Groups before the node's first are masked; the node's
+        // other groups before start only bound the first entry (carry: the
+        // bucket of the group before start, -1 at the node's first group).
+        int32_t *sb = s_bkt[threadIdx.x >> 5];
         const int32_t ga = start & ~3;
-        int32_t kcarry = (ga == start && start > g0) ? (int32_t)((__ldg(ngts + start - 1) >> s) - bfirst) : -1;
+        int32_t carry = (start > g0 && ga == start) ? (int32_t)((__ldg(ngts + start - 1) >> s) - bfirst) : -1;
         auto load4 = [&](int32_t q, int64_t *t) {
             if (q + 4 <= end) {
                 const longlong2 *p2 = reinterpret_cast<const longlong2 *>(ngts + q);
-                const longlong2 a = __ldg(p2), b = __ldg(p2 + 1);
-                t[0] = a.x;
-                t[1] = a.y;
-                t[2] = b.x;
-                t[3] = b.y;
+                const longlong2 x = __ldg(p2), y = __ldg(p2 + 1);
+                t[0] = x.x;
+                t[1] = x.y;
+                t[2] = y.x;
+                t[3] = y.y;
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; j++) t[j] = q + j < end ? __ldg(ngts + q + j) : 0;
@@ -279,42 +284,36 @@ __global__ void __launch_bounds__(256) k_bkt_fill(const int32_t *__restrict__ bi
             const int32_t q = gb + 4 * lane;
             int64_t tn[4];
             load4(q + 128, tn);
-            int32_t kq[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) kq[j] = (int32_t)((tv[j] >> s) - bfirst);
-            int32_t prev = __shfl_up_sync(0xffffffffu, kq[3], 1);
-            if (lane == 0) prev = kcarry;
-            kcarry = __shfl_sync(0xffffffffu, kq[3], 31);
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                // entries (kp, k] hold g; the last group adds (k, K] holding
-                // g1; entries below ncopy came from the previous table.  A
-                // short run (the common case) is written by its own lane,
-                // long runs (time gaps) by the whole warp
-                const int32_t g = q + j;
-                const bool valid = g >= start && g < end;
-                const int32_t kp = g == g0 ? -1 : (j == 0 ? prev : kq[j - 1]);
-                const int32_t k = kq[j];
-                const int32_t lo_k = max(kp + 1, ncopy);
-                const int32_t hi_k = g == g1 - 1 ? K : k;
-                const int32_t cnt = valid && hi_k >= lo_k ? hi_k - lo_k + 1 : 0;
-                if (cnt > 0 && cnt <= BKT_SHORT_RUN) {
-                    for (int32_t kk = lo_k; kk <= hi_k; kk++) bkt[tb + kk] = kk <= k ? g : g1;
-                }
-                unsigned longs = __ballot_sync(0xffffffffu, cnt > BKT_SHORT_RUN);
-                while (longs) {  // 32 entries per store
-                    const int r = __ffs(longs) - 1;
-                    longs &= longs - 1;
-                    const int32_t r_lo = __shfl_sync(0xffffffffu, lo_k, r);
-                    const int32_t r_cnt = __shfl_sync(0xffffffffu, cnt, r);
-                    const int32_t r_k = __shfl_sync(0xffffffffu, k, r);
-                    const int32_t r_g = __shfl_sync(0xffffffffu, g, r);
-                    for (int32_t e = lane; e < r_cnt; e += 32) {
-                        const int32_t kk = r_lo + e;
-                        bkt[tb + kk] = kk <= r_k ? r_g : g1;
+            int4 kq;
+            kq.x = q < g0 ? INT_MIN : (int32_t)((tv[0] >> s) - bfirst);
+            kq.y = q + 1 < g0 ? INT_MIN : (int32_t)((tv[1] >> s) - bfirst);
+            kq.z = q + 2 < g0 ? INT_MIN : (int32_t)((tv[2] >> s) - bfirst);
+            kq.w = q + 3 < g0 ? INT_MIN : (int32_t)((tv[3] >> s) - bfirst);
+            __syncwarp();
+            reinterpret_cast<int4 *>(sb)[lane] = kq;
+            __syncwarp();
+            const int32_t last = min(end, gb + 128) - 1 - gb;  // the round's last group (index in the round)
+            if (gb == ga && start > g0 && ga < start) carry = sb[start - 1 - ga];
+            const int32_t hi = sb[last];
+            // the node's last group also owns the buckets after its own, up to K
+            const int32_t top = gb + last == g1 - 1 ? K : hi;
+            for (int32_t kb = max(carry + 1, ncopy); kb <= top; kb += 32) {
+                const int32_t k = kb + lane;
+                if (k <= top) {
+                    int32_t v = g1;
+                    if (k <= hi) {
+                        int32_t lo = 0, up = last;  // sb[last] = hi >= k
+                        while (lo < up) {
+                            const int32_t mid = (lo + up) >> 1;
+                            if (sb[mid] >= k) up = mid;
+                            else lo = mid + 1;
+                        }
+                        v = gb + lo;
                     }
+                    bkt[tb + k] = v;
                 }
             }
+            carry = hi;
 #pragma unroll
             for (int j = 0; j < 4; j++) tv[j] = tn[j];
         }
