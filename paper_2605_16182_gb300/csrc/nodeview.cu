@@ -579,11 +579,16 @@ struct AppendRunBytes {
 constexpr int NV_MIRRORS = 64;               // big nodes copying ahead at once
 constexpr int64_t NV_MIRROR_BATCHES = 16;    // batches ahead of the slide
 
+// The slot of node v, or -1.  All NV_MIRRORS loads issue together (an early
+// exit made them a chain of dependent L2 loads on the hub's thread, the
+// reserve kernel's critical path); only v's own thread writes v's slot.
 __device__ __forceinline__ int mirror_find(const NvMirror *mir, int32_t v)
 {
+    int found = -1;
+#pragma unroll
     for (int i = 0; i < NV_MIRRORS; i++)
-        if (mir[i].node == v) return i;
-    return -1;
+        if (__ldcg(&mir[i].node) == v) found = i;
+    return found;
 }
 
 __global__ void k_nv_reserve(const int32_t *__restrict__ run_node, const int32_t *__restrict__ run_pos,
