@@ -395,14 +395,14 @@ int prepare_walk_index(tempest_t *h)
         const BuildCtx bc{prev_ok ? h->bkt_prev.as<int32_t>() : nullptr, prev_gen, h->bkt_log, h->nev.as<int32_t>()};
         BigNodeOp op{h->act.as<int32_t>(), ngr, bc, gen, h->big_node.as<int32_t>(), h->big_t.as<int32_t>(),
                      h->big_aux0.as<int4>(), h->big_aux1.as<int4>(), h->big_bf.as<int64_t>()};
-        const int nblk = scan_launch(op, S, part, st);
+        const int nblk = scan_launch<BigNodeOp, 1>(op, S, part, st);
         // the big-node count and table size stay on the device (kept apart:
         // the next scan reuses the partials); sizes below use host bounds
         uint64_t *big_tot = part + SCAN_MAX_BLOCKS + 1;
         cudaMemcpyAsync(big_tot, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
         ChunkOp cop{h->big_node.as<int32_t>(), ngr, h->big_aux0.as<int4>(), h->big_aux1.as<int4>(),
                     h->big_c.as<int32_t>(), big_tot};
-        const int nblk2 = scan_launch(cop, S, part, st);
+        const int nblk2 = scan_launch<ChunkOp, 1>(cop, S, part, st);
         // the fill's consistency flag goes to the walk counters, which
         // every walk call zeroes before its kernels: read it here
         cudaMemsetAsync(h->wcnt.p, 0, sizeof(WalkCounters), st);

@@ -27,7 +27,7 @@ constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
 constexpr int SCAN_MAX_BLOCKS = 2048;
 
-template <class Op>
+template <class Op, int ITEMS>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Op op, int64_t n, int64_t per_blk,
                                                               uint64_t *partials)
 {
@@ -35,17 +35,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Op op, int64_t n, 
     const int64_t b0 = (int64_t)blockIdx.x * per_blk;
     const int64_t b1 = min(n, b0 + per_blk);
     uint64_t s = 0;
-    // SCAN_ITEMS values per thread per chunk, evaluated together (their
+    // ITEMS values per thread per chunk, evaluated together (their
     // loads are independent), in the striped order the emit pass reads
-    for (int64_t c = b0; c < b1; c += SCAN_CHUNK) {
-        uint64_t v[SCAN_ITEMS];
+    for (int64_t c = b0; c < b1; c += (SCAN_THREADS * ITEMS)) {
+        uint64_t v[ITEMS];
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++) {
+        for (int k = 0; k < ITEMS; k++) {
             const int64_t i = c + k * SCAN_THREADS + threadIdx.x;
             v[k] = (i < b1) ? op.value(i) : 0;
         }
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++) s += v[k];
+        for (int k = 0; k < ITEMS; k++) s += v[k];
     }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) wt[threadIdx.x >> 5] = s;
@@ -61,55 +61,55 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Op op, int64_t n, 
 // partials[nb] receives the total.
 __global__ void k_scan_partials(uint64_t *partials, int nb);
 
-// Each chunk of SCAN_CHUNK elements is read and written in striped order
-// (element c + k*THREADS + thread, so a warp touches consecutive elements) and
-// staged through shared memory, where each thread scans SCAN_ITEMS
+// Each chunk of SCAN_THREADS * ITEMS elements is read and written in striped
+// order (element c + k*THREADS + thread, so a warp touches consecutive
+// elements) and staged through shared memory, where each thread scans ITEMS
 // consecutive values.
 // Shared-memory slot of staged element j: one pad slot per 16 (a thread's
-// SCAN_ITEMS consecutive 8-byte values sit 64 B apart from the next
-// thread's, which without the pad maps a half-warp onto two banks).
+// ITEMS consecutive 8-byte values sit 64 B apart from the next thread's at
+// ITEMS = 8, which without the pad maps a half-warp onto two banks).
 __device__ __forceinline__ int scan_slot(int j) { return j + (j >> 4); }
 
-template <class Op>
+template <class Op, int ITEMS>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_emit(Op op, int64_t n, int64_t per_blk,
                                                             const uint64_t *partials)
 {
     __shared__ uint64_t wt[33];
-    __shared__ uint64_t sv[SCAN_CHUNK + SCAN_CHUNK / 16];  // values, then exclusive prefixes
+    __shared__ uint64_t sv[(SCAN_THREADS * ITEMS) + (SCAN_THREADS * ITEMS) / 16];  // values, then exclusive prefixes
     const int64_t b0 = (int64_t)blockIdx.x * per_blk;
     const int64_t b1 = min(n, b0 + per_blk);
     uint64_t carry = partials[blockIdx.x];
-    for (int64_t c = b0; c < b1; c += SCAN_CHUNK) {
+    for (int64_t c = b0; c < b1; c += (SCAN_THREADS * ITEMS)) {
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++) {
+        for (int k = 0; k < ITEMS; k++) {
             const int j = k * SCAN_THREADS + threadIdx.x;
             const int64_t i = c + j;
             sv[scan_slot(j)] = (i < b1) ? op.value(i) : 0;
         }
         __syncthreads();
-        uint64_t v[SCAN_ITEMS];
+        uint64_t v[ITEMS];
         uint64_t s = 0;
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++) {
-            v[k] = sv[scan_slot(threadIdx.x * SCAN_ITEMS + k)];
+        for (int k = 0; k < ITEMS; k++) {
+            v[k] = sv[scan_slot(threadIdx.x * ITEMS + k)];
             s += v[k];
         }
         uint64_t tot;
         uint64_t ex = block_excl_scan<uint64_t>(s, wt, tot);  // synchronises
         ex += carry;
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++) {
-            sv[scan_slot(threadIdx.x * SCAN_ITEMS + k)] = ex;
+        for (int k = 0; k < ITEMS; k++) {
+            sv[scan_slot(threadIdx.x * ITEMS + k)] = ex;
             ex += v[k];
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++) {
+        for (int k = 0; k < ITEMS; k++) {
             const int j = k * SCAN_THREADS + threadIdx.x;
             const int64_t i = c + j;
             if (i < b1) {
                 const uint64_t e = sv[scan_slot(j)];
-                const uint64_t nx = (j + 1 < SCAN_CHUNK) ? sv[scan_slot(j + 1)] : carry + tot;
+                const uint64_t nx = (j + 1 < (SCAN_THREADS * ITEMS)) ? sv[scan_slot(j + 1)] : carry + tot;
                 op.emit(i, nx - e, e);
             }
         }
@@ -119,22 +119,25 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_emit(Op op, int64_t n, in
 }
 
 // Host driver.  partials must hold SCAN_MAX_BLOCKS + 1 entries; the total
-// ends in partials[nb] where nb is returned.
-template <class Op>
+// ends in partials[nb] where nb is returned.  ITEMS: values per thread per
+// chunk; 1 for an op whose value() is a chain of dependent loads over a
+// modest n (more blocks in flight instead of more values per thread).
+template <class Op, int ITEMS = SCAN_ITEMS>
 int scan_launch(const Op &op, int64_t n, uint64_t *partials, cudaStream_t st)
 {
     if (n <= 0) {
         cudaMemsetAsync(partials, 0, sizeof(uint64_t), st);
         return 0;
     }
-    int64_t nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    constexpr int64_t CHUNK = (int64_t)SCAN_THREADS * ITEMS;
+    int64_t nb = (n + CHUNK - 1) / CHUNK;
     if (nb > SCAN_MAX_BLOCKS) nb = SCAN_MAX_BLOCKS;
     int64_t per = (n + nb - 1) / nb;
-    per = (per + SCAN_CHUNK - 1) / SCAN_CHUNK * SCAN_CHUNK;
+    per = (per + CHUNK - 1) / CHUNK * CHUNK;
     nb = (n + per - 1) / per;
-    k_scan_reduce<Op><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(op, n, per, partials);
+    k_scan_reduce<Op, ITEMS><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(op, n, per, partials);
     k_scan_partials<<<1, 1024, 0, st>>>(partials, (int)nb);
-    k_scan_emit<Op><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(op, n, per, partials);
+    k_scan_emit<Op, ITEMS><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(op, n, per, partials);
     return (int)nb;
 }
 
