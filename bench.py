@@ -358,7 +358,7 @@ def run_e2e(args, eng, feeder, n_walks, L, seed_base, bias_id, direction=0):
     hwts = torch.empty((n_walks, L), dtype=torch.int64).pin_memory()
     hln = torch.empty((n_walks,), dtype=torch.int32).pin_memory()
     hops, h2d, d2h, edges = 0, 0, 0, 0
-    ingest_calls, walk_calls = [], []
+    ingest_calls, walk_calls, walk_phases = [], [], []
     walk_fn = _lib.tempest_walks_backward if direction else _lib.tempest_walks
     for step in range(e2e_warm + e2e_steps):
         b0 = feeder.next
@@ -386,7 +386,9 @@ def run_e2e(args, eng, feeder, n_walks, L, seed_base, bias_id, direction=0):
             hops += int((hln.to(torch.int64) - 1).clamp(min=0).sum().item())
             # the bytes the call moved device to host (whole rows for a share
             # of the walks, each other walk's cells with its length and offset)
-            d2h += _lib.tempest_last_walk_stats(eng.h).d2h_bytes
+            ws = _lib.tempest_last_walk_stats(eng.h)
+            d2h += ws.d2h_bytes
+            walk_phases.append([round(x, 2) for x in ws.host_ms])
     threads = eng.get_tuning(_lib.TUNE_HOST_THREADS)
     cpus = host_cpus()
     walk_s = sum(walk_calls)
@@ -398,6 +400,10 @@ def run_e2e(args, eng, feeder, n_walks, L, seed_base, bias_id, direction=0):
                 walk_call_ms={"mean": 1e3 * walk_s / e2e_steps, "p50": 1e3 * percentile(walk_calls, 50),
                               "p99": 1e3 * percentile(walk_calls, 99)},
                 walk_calls_ms=[round(1e3 * x, 2) for x in walk_calls],
+                walk_call_phases_ms=walk_phases,
+                walk_call_phases="per call: until the compacted cells are on the host, host threads writing "
+                                 "rows and padding, then the wait for the copy of the device-padded rows",
+                ingest_calls_ms=[round(1e3 * x, 2) for x in ingest_calls],
                 host_threads=threads if threads > 0 else min(cpus, 32),
                 host_threads_rule="set" if threads > 0 else "the CPUs this process may use (affinity mask and "
                                                             "cgroup quota), at most 32",

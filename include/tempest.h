@@ -162,6 +162,14 @@ typedef struct {
                               and offsets and host threads write their rows
                               and padding, overlapped with the first copy
                               when the caller's buffers are pinned */
+    double host_ms[3];     /* that split's wall-clock phases (0 for other
+                              outputs): [0] from the call's start until the
+                              host part's cells, lengths and offsets are on
+                              the host (walk kernels, padding, compaction and
+                              their copies), [1] the host threads writing
+                              their rows and padding, [2] the wait after
+                              that for the copy of the rows padded on the
+                              device */
 } tempest_walk_stats;
 
 /* Create an engine.  window > 0: duration Delta in timestamp units, the

@@ -74,11 +74,12 @@ class WalkStats(ctypes.Structure):
     _fields_ = [("n_walks", ctypes.c_int64), ("hops", ctypes.c_int64),
                 ("model_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("tier_launches", ctypes.c_int64 * 5), ("kernel_ms", ctypes.c_double),
-                ("d2h_bytes", ctypes.c_int64)]
+                ("d2h_bytes", ctypes.c_int64), ("host_ms", ctypes.c_double * 3)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["tier_launches"] = list(self.tier_launches)
+        d["host_ms"] = list(self.host_ms)
         return d
 
 

@@ -485,6 +485,10 @@ static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, 
     rc = cuda_check(h, cudaEventSynchronize(ready), "walks (host outputs)");
     cudaEventDestroy(ready);
     if (rc) return rc;
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point a) { return std::chrono::duration<double, std::milli>(clk::now() - a).count(); };
+    h->last_ws.host_ms[0] = ms_since(h->walk_t0);
+    const clk::time_point t1 = clk::now();
     h->last_d2h = (int64_t)(sizeof(int32_t) * (size_t)n + sizeof(int64_t) * (size_t)nh + 12 * (size_t)tot +
                             (rowb + rowt) * (size_t)nd);
     // rows [nd, n) and their padding on the host, in parallel threads, while
@@ -527,7 +531,11 @@ static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, 
             for (auto &x : th) x.join();
         }
     }
-    return cuda_check(h, cudaStreamSynchronize(st), "walks (host outputs)");
+    h->last_ws.host_ms[1] = ms_since(t1);
+    const clk::time_point t2 = clk::now();
+    rc = cuda_check(h, cudaStreamSynchronize(st), "walks (host outputs)");
+    h->last_ws.host_ms[2] = ms_since(t2);
+    return rc;
 }
 
 static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_len, const int32_t *len_arr,
@@ -554,6 +562,7 @@ static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_
         return vh == h ? rc : fail(h, rc, "%s", vh->err.c_str());
     cudaStream_t st = h->stream;
     h->last_ws = tempest_walk_stats{};
+    h->walk_t0 = std::chrono::steady_clock::now();
     if (n_walks == 0) return TEMPEST_OK;
 
     // per-walk inputs: validate on the host when they are host arrays

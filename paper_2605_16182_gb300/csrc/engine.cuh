@@ -2,6 +2,8 @@
 // C ABI (capi.cu), ingest (ingest.cu) and walk generation (walks.cu).
 #pragma once
 
+#include <chrono>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -250,6 +252,7 @@ struct tempest {
     size_t hpin_bytes = 0;
     tw::DBuf cmp_off, cmp_stage;  // offsets and compacted cells of the rows on the device
     int64_t last_d2h = 0;      // bytes the last walk call copied device to host
+    std::chrono::steady_clock::time_point walk_t0;  // start of the running walk call (host clock)
     int host_link_pct = 62;    // percent of host-output rows copied whole (the rest expanded on the host)
     int host_threads = 0;      // host threads expanding those rows (0: the CPUs the process may use, <= 32)
     int evict_mode = 0;        // node view eviction: 0 chooses, 1 counts evicted endpoints, 2 per-node search
