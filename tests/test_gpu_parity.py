@@ -8,6 +8,8 @@ import json
 import os
 import random
 
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -274,13 +276,20 @@ def test_host_and_device_outputs_agree(share):
         node = np.full((n, L), 7, np.int32)
         ts = np.full((n, L), 7, np.int64)
         ln = np.full(n, 7, np.int32)
+        t0 = time.perf_counter()
         _lib.tempest_walks(eng.h, n, L, 1, 0, 11, node.ctypes.data, ts.ctypes.data, ln.ctypes.data)
+        call_ms = 1e3 * (time.perf_counter() - t0)
         assert np.array_equal(node, gd[0].cpu().numpy()) and np.array_equal(ts, gd[1].cpu().numpy())
         assert np.array_equal(ln, gd[2].cpu().numpy())
         ws = eng.last_walk_stats()
         nd = n * share // 100
         cells = int(ln[nd:].sum())
         assert ws["d2h_bytes"] == 4 * n + 8 * (n - nd) + 12 * cells + 12 * L * nd
+        # the call's host-visible phases: each measured, together within the call
+        assert all(x >= 0 for x in ws["host_ms"]) and ws["host_ms"][0] > 0
+        assert sum(ws["host_ms"]) <= call_ms
+    eng.walks(100, 5, bias=1, seed=3)  # device outputs: no phases
+    assert eng.last_walk_stats()["host_ms"] == [0.0, 0.0, 0.0]
         if n == 3000:
             o = orc.walks(n, L, bias=1, seed=11)
             assert_walks_bit_exact((node, ts, ln), o)
