@@ -161,7 +161,8 @@ typedef struct {
                               others travel as their walks' cells, lengths
                               and offsets and host threads write their rows
                               and padding, overlapped with the first copy
-                              when the caller's buffers are pinned */
+                              when the caller's buffers are pinned (rows of
+                              the band between them count where they went) */
     double host_ms[3];     /* that split's wall-clock phases (0 for other
                               outputs): [0] from the call's start until the
                               host part's cells, lengths and offsets are on
@@ -386,9 +387,13 @@ enum {
     /* TEMPEST_SCHED_LANE: 0 (default) the walker writes each row's padding
      * as its walk ends; 1 one streaming pass pads all rows after the walks */
     TEMPEST_TUNE_PAD_PASS = 4,
-    /* walks into host buffers: percent of the rows padded on the device and
-     * copied whole (0-100, default 62); the others travel as their walks'
-     * cells only and host threads write their rows and padding meanwhile */
+    /* walks into host buffers: percent of the rows padded on the device
+     * (0-100, default 62); the others travel as their walks' cells only and
+     * host threads write their rows and padding meanwhile.  Between 1 and 99
+     * the padded rows are a band that the copy takes a chunk at a time from
+     * below while the host threads, once their own rows are written, take it
+     * from above (its cells travel too); 100 copies every row whole, 0 sends
+     * every row as cells */
     TEMPEST_TUNE_HOST_LINK_PCT = 5,
     /* walks into host buffers: host threads that write the rows sent as
      * cells (0-256; 0, the default: the CPUs this process may run on, from

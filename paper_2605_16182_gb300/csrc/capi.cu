@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -429,15 +430,21 @@ int tempest_active_nodes_backward(tempest_t *h, int64_t *n) { return active_node
 // on the device and copied whole, while for the rest only each walk's cells
 // travel (gathered back to back on the device, with the lengths and offsets)
 // and host threads write those rows and their padding, during the copy of the
-// first part.
+// first part.  The first part is a band that either side may take: a copy
+// thread hands it to the copy engine a chunk at a time from its bottom, two
+// chunks ahead of the engine, and host threads that have written their own
+// rows take it from the top (its cells travel with the host part's), so a
+// copy that slows down (the link is shared with the host's other traffic)
+// leaves less of the call undone.
 
 static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, int64_t *d_ts, const int32_t *d_len,
                          int32_t *node, int64_t *ts, int32_t *len, bool dev_len)
 {
     cudaStream_t st = h->stream;
     int rc;
-    const int64_t nd = std::min<int64_t>(n, n * h->host_link_pct / 100);  // rows copied whole
-    const int64_t nh = n - nd;                                                          // rows the host writes
+    const int64_t nd = std::min<int64_t>(n, n * h->host_link_pct / 100);  // rows padded on the device
+    const int64_t nb = (nd > 0 && nd < n) ? 0 : nd;  // rows [nb, nd): the band either side takes
+    const int64_t nh = n - nb;                            // rows whose cells travel
     const size_t rowb = sizeof(int32_t) * (size_t)cap, rowt = sizeof(int64_t) * (size_t)cap;
     int64_t grid = (n + 255) / 256;
     const int64_t gcap = (int64_t)h->num_sms * 16;
@@ -447,7 +454,7 @@ static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, 
     if ((rc = ensure(h, h->cmp_off, sizeof(int64_t) * (size_t)(nh > 0 ? nh : 1) + 256, true))) return rc;
     int64_t *d_off = h->cmp_off.as<int64_t>();
     uint64_t *part = h->partials.as<uint64_t>();
-    const int32_t *hlen_d = d_len + nd;
+    const int32_t *hlen_d = d_len + nb;
     const int nblk = scan_launch(LenScanOp{hlen_d, cap, d_off}, nh, part, st);
     uint64_t *hp = static_cast<uint64_t *>(h->hstat);
     cudaMemcpyAsync(hp, part + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
@@ -460,7 +467,7 @@ static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, 
     int32_t *c_node = h->cmp_stage.as<int32_t>();
     int64_t *c_ts = reinterpret_cast<int64_t *>(h->cmp_stage.as<char>() + b_node);
     if (tot > 0)
-        k_compact_rows<<<(unsigned)grid, 256, 0, st>>>(d_node + nd * (int64_t)cap, d_ts + nd * (int64_t)cap, hlen_d,
+        k_compact_rows<<<(unsigned)grid, 256, 0, st>>>(d_node + nb * (int64_t)cap, d_ts + nb * (int64_t)cap, hlen_d,
                                                        d_off, nh, cap, c_node, c_ts);
     if ((rc = ensure_pinned(h, b_off + b_node + b_ts + b_len + 256))) return rc;
     char *hb = static_cast<char *>(h->hpin);
@@ -468,74 +475,143 @@ static int walks_to_host(tempest_t *h, int64_t n, int32_t cap, int32_t *d_node, 
     int32_t *h_node = reinterpret_cast<int32_t *>(hb + b_off);
     int64_t *h_ts = reinterpret_cast<int64_t *>(hb + b_off + b_node);
     int32_t *h_len = dev_len ? reinterpret_cast<int32_t *>(hb + b_off + b_node + b_ts) : len;
-    // the host part's inputs first, then the whole rows of the other part
+    // the host part's inputs first, then the whole rows
     cudaMemcpyAsync(h_len, d_len, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
     if (nh > 0) cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (size_t)nh, cudaMemcpyDeviceToHost, st);
     if (tot > 0) {
         cudaMemcpyAsync(h_node, c_node, sizeof(int32_t) * (size_t)tot, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(h_ts, c_ts, sizeof(int64_t) * (size_t)tot, cudaMemcpyDeviceToHost, st);
     }
-    cudaEvent_t ready;
-    if ((rc = cuda_check(h, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "walks (host event)"))) return rc;
-    cudaEventRecord(ready, st);
-    if (nd > 0) {
-        cudaMemcpyAsync(node, d_node, rowb * (size_t)nd, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(ts, d_ts, rowt * (size_t)nd, cudaMemcpyDeviceToHost, st);
+    cudaEvent_t ev[4] = {};  // [0]: the host part's inputs are on the host; [1..3]: the copy thread's chunks
+    for (cudaEvent_t &e : ev) {
+        if ((rc = cuda_check(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "walks (host event)"))) {
+            for (cudaEvent_t &x : ev)
+                if (x) cudaEventDestroy(x);
+            return rc;
+        }
     }
-    rc = cuda_check(h, cudaEventSynchronize(ready), "walks (host outputs)");
-    cudaEventDestroy(ready);
-    if (rc) return rc;
+    cudaEventRecord(ev[0], st);
+    if (nb > 0) {
+        cudaMemcpyAsync(node, d_node, rowb * (size_t)nb, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(ts, d_ts, rowt * (size_t)nb, cudaMemcpyDeviceToHost, st);
+    }
+    // the band: unclaimed rows [front, back), the copy thread's from the
+    // bottom in chunks of copy_chunk rows, the host threads' from the top in
+    // chunks of host_chunk rows
+    std::mutex mu;
+    int64_t front = nb, back = nd, band_copied = 0;
+    int copy_err = 0;
+    const int64_t band = nd - nb;
+    const int64_t copy_chunk = std::min<int64_t>(65536, std::max<int64_t>(256, band / 16));
+    const int64_t host_chunk = std::min<int64_t>(2048, std::max<int64_t>(64, band / 64));
+    auto claim_bottom = [&](int64_t &a, int64_t &b) {
+        std::lock_guard<std::mutex> g(mu);
+        if (front >= back) return false;
+        a = front;
+        b = std::min(back, front + copy_chunk);
+        front = b;
+        return true;
+    };
+    auto claim_top = [&](int64_t &a, int64_t &b) {
+        std::lock_guard<std::mutex> g(mu);
+        if (back <= front) return false;
+        b = back;
+        a = std::max(front, back - host_chunk);
+        back = a;
+        return true;
+    };
+    // the copy thread keeps two chunks queued behind the engine's current
+    // work, so that the rest of the band stays open to the host threads
+    auto copier = [&]() {
+        if (cudaSetDevice(h->device) != cudaSuccess) {
+            cudaGetLastError();
+            return;  // the host threads take the band
+        }
+        int64_t a, b;
+        for (int64_t i = 0;; i++) {
+            if (i >= 2 && cudaEventSynchronize(ev[1 + (i - 2) % 3]) != cudaSuccess) {
+                copy_err = 1;
+                break;
+            }
+            if (!claim_bottom(a, b)) break;
+            cudaMemcpyAsync(node + a * (int64_t)cap, d_node + a * (int64_t)cap, rowb * (size_t)(b - a),
+                            cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(ts + a * (int64_t)cap, d_ts + a * (int64_t)cap, rowt * (size_t)(b - a),
+                            cudaMemcpyDeviceToHost, st);
+            cudaEventRecord(ev[1 + i % 3], st);
+            band_copied += b - a;
+        }
+    };
+    std::thread cp;
+    if (band > 0) {
+        try {
+            cp = std::thread(copier);
+        } catch (...) {
+            // no copy thread: the host threads take the whole band
+        }
+    }
+    auto stop_copier = [&]() {
+        {
+            std::lock_guard<std::mutex> g(mu);
+            back = front;
+        }
+        if (cp.joinable()) cp.join();
+    };
+    rc = cuda_check(h, cudaEventSynchronize(ev[0]), "walks (host outputs)");
     using clk = std::chrono::steady_clock;
     auto ms_since = [](clk::time_point a) { return std::chrono::duration<double, std::milli>(clk::now() - a).count(); };
     h->last_ws.host_ms[0] = ms_since(h->walk_t0);
     const clk::time_point t1 = clk::now();
-    h->last_d2h = (int64_t)(sizeof(int32_t) * (size_t)n + sizeof(int64_t) * (size_t)nh + 12 * (size_t)tot +
-                            (rowb + rowt) * (size_t)nd);
-    // rows [nd, n) and their padding on the host, in parallel threads, while
-    // the copy engine moves rows [0, nd)
-    if (nh > 0) {
+    if (!rc) {
+        // rows [nd, n), then rows of the band from its top, in parallel
+        // threads (this one included) that take chunks of rows until none is
+        // left: a thread that the host deschedules (its CPUs are shared)
+        // delays one chunk, not a fixed share of the rows; a thread that
+        // cannot start (no exception crosses the C ABI) leaves its chunks to
+        // the others
+        auto expand = [&](int64_t a, int64_t b) {
+            expand_rows(a - nb, b - nb, cap, h_len + nb, h_off, h_node, h_ts, node + nb * (int64_t)cap,
+                        ts + nb * (int64_t)cap);
+        };
+        constexpr int64_t CHUNK = 2048;
+        std::atomic<int64_t> next{nd};
+        auto work = [&]() {
+            for (;;) {
+                const int64_t i0 = next.fetch_add(CHUNK, std::memory_order_relaxed);
+                if (i0 >= n) break;
+                expand(i0, std::min(n, i0 + CHUNK));
+            }
+            int64_t a, b;
+            while (claim_top(a, b)) expand(a, b);
+        };
         const int64_t want = h->host_threads > 0 ? h->host_threads : std::min(host_cpus(), 32);
         const int64_t nt = std::min<int64_t>(want, std::max<int64_t>(1, nh / 4096));
-        int32_t *node_h = node + nd * (int64_t)cap;
-        int64_t *ts_h = ts + nd * (int64_t)cap;
-        const int32_t *len_h = h_len + nd;
-        if (nt <= 1) {
-            expand_rows(0, nh, cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
-        } else {
-            // the threads (this one included) take chunks of rows from a
-            // shared counter until none is left: a thread that the host
-            // deschedules (its CPUs are shared) delays one chunk, not a
-            // fixed share of the rows; a thread that cannot start (no
-            // exception crosses the C ABI) leaves its chunks to the others
-            constexpr int64_t CHUNK = 2048;
-            std::atomic<int64_t> next{0};
-            auto work = [&]() {
-                for (;;) {
-                    const int64_t i0 = next.fetch_add(CHUNK, std::memory_order_relaxed);
-                    if (i0 >= nh) break;
-                    expand_rows(i0, std::min(nh, i0 + CHUNK), cap, len_h, h_off, h_node, h_ts, node_h, ts_h);
-                }
-            };
-            std::vector<std::thread> th;
+        std::vector<std::thread> th;
+        try {
+            th.reserve((size_t)nt);
+        } catch (...) {
+        }
+        for (int64_t k = 1; k < nt; k++) {
             try {
-                th.reserve((size_t)nt);
+                th.emplace_back(work);
             } catch (...) {
             }
-            for (int64_t k = 1; k < nt; k++) {
-                try {
-                    th.emplace_back(work);
-                } catch (...) {
-                }
-            }
-            work();
-            for (auto &x : th) x.join();
         }
+        work();
+        for (auto &x : th) x.join();
     }
     h->last_ws.host_ms[1] = ms_since(t1);
     const clk::time_point t2 = clk::now();
-    rc = cuda_check(h, cudaStreamSynchronize(st), "walks (host outputs)");
+    stop_copier();
+    const int rc2 = cuda_check(h, cudaStreamSynchronize(st), "walks (host outputs)");
+    for (cudaEvent_t &e : ev) cudaEventDestroy(e);
     h->last_ws.host_ms[2] = ms_since(t2);
-    return rc;
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (copy_err) return fail(h, TEMPEST_ECUDA, "walks (host outputs): the copy thread failed");
+    h->last_d2h = (int64_t)(sizeof(int32_t) * (size_t)n + sizeof(int64_t) * (size_t)nh + 12 * (size_t)tot +
+                            (rowb + rowt) * (size_t)(nb + band_copied));
+    return TEMPEST_OK;
 }
 
 static int walks_common(tempest_t *h, int64_t n_walks, int32_t cap, int32_t max_len, const int32_t *len_arr,
