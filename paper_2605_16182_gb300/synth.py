@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import Callable, Iterator, List, Optional
+from typing import Iterator, List, Optional
 
 import numpy as np
 import torch
